@@ -1,0 +1,505 @@
+/*
+ * Oracle for the finite element weak-form evaluator: plain, slow, FP64 CPU code.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the package smoke check and
+ * the CPU-baseline leg of the benchmark load this library.  The product path
+ * (the CUDA library and its binding) never calls it and shares no code with it:
+ * the reference element, the quadrature rule, the geometry mapping, the forms
+ * and the assembly are all written again here, independently, as the plain
+ * definitions that Cimrman, "Fast Evaluation of Finite Element Weak Forms Using
+ * Python Tensor Contraction Packages" (arXiv 2107.04121) states them.
+ *
+ * Every element loop is the nested cells x quadrature-points loop of
+ * Algorithm 1 (residual mode) and Algorithm 2 (matrix mode) of the paper, Sec. 4.1.
+ * The only parallelism is an OpenMP "parallel for" over elements; each element
+ * is computed with the same sequential loops whatever the thread count.
+ *
+ * Conventions the paper leaves open, fixed here:
+ *  - reference hexahedron [0,1]^3; order-p Lagrange nodes equispaced, numbered
+ *    lexicographically with x fastest: node (i,j,k) -> i + (p+1) j + (p+1)^2 k;
+ *  - Gauss-Legendre points on [0,1], same lexicographic order, weights sum to 1;
+ *  - vector element DOFs component-major: local index = comp * N + a
+ *    (the "cresf" output order of the elasticity expression, Sec. 5.3.3);
+ *  - global vector DOF index = ncomp * node + comp;
+ *  - Voigt order (11, 22, 33, 12, 13, 23) with engineering shear strains.
+ *
+ * Parity status: every function below is pinned by CPU tests against closed
+ * forms, exact rational integrals, library routines or invariants (see the
+ * pins in tests/test_oracle_pins.py).
+ */
+#define _USE_MATH_DEFINES
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846264338327950288
+#endif
+
+#define OR_OK 0
+#define OR_BAD_ARG -1
+/* A positive return value k means element k-1 had det J <= 0. */
+
+/* ------------------------------------------------------------------------ */
+/* Gauss-Legendre rule (oracle_gauss_1d): Newton iteration on P_n evaluated with the three-term
+ * recurrence (n+1) P_{n+1} = (2n+1) x P_n - n P_{n-1}, derivative from
+ * (1-x^2) P_n' = n (P_{n-1} - x P_n).  Points mapped from [-1,1] to [0,1]. */
+/* P_n(x) and P_{n-1}(x) by the three-term recurrence, starting at P_0 = 1, P_1 = x. */
+static void legendre_pair(int n, double x, double *pn_out, double *pm_out)
+{
+    double pm = 1.0, pn = x;
+    for (int k = 1; k < n; ++k) {
+        double next = ((2.0 * k + 1.0) * x * pn - k * pm) / (k + 1.0);
+        pm = pn;
+        pn = next;
+    }
+    *pn_out = pn;
+    *pm_out = pm;
+}
+
+int oracle_gauss_1d(int n, double *pts, double *wts)
+{
+    if (n < 1 || n > 64 || !pts || !wts) return OR_BAD_ARG;
+    for (int i = 0; i < n; ++i) {
+        /* initial guess for the i-th root, counted from the right end */
+        double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double pn, pm, dp;
+        for (int it = 0; it < 100; ++it) {
+            legendre_pair(n, x, &pn, &pm);
+            dp = n * (pm - x * pn) / (1.0 - x * x);
+            double dx = pn / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        legendre_pair(n, x, &pn, &pm);
+        dp = n * (pm - x * pn) / (1.0 - x * x);
+        double w = 2.0 / ((1.0 - x * x) * dp * dp);
+        /* ascending order on [0,1] */
+        pts[n - 1 - i] = 0.5 * (x + 1.0);
+        wts[n - 1 - i] = 0.5 * w;
+    }
+    return OR_OK;
+}
+
+/* 1-D Lagrange polynomial L_k on equispaced nodes t_m = m/p, m = 0..p:
+ * L_k(t) = prod_{m != k} (t - t_m) / (t_k - t_m); derivative by the product rule. */
+static double lagrange_1d(int p, int k, double t)
+{
+    double v = 1.0;
+    for (int m = 0; m <= p; ++m) {
+        if (m == k) continue;
+        v *= (t - (double)m / p) / ((double)(k - m) / p);
+    }
+    return v;
+}
+
+static double lagrange_1d_deriv(int p, int k, double t)
+{
+    double s = 0.0;
+    for (int l = 0; l <= p; ++l) {
+        if (l == k) continue;
+        double term = 1.0 / ((double)(k - l) / p);
+        for (int m = 0; m <= p; ++m) {
+            if (m == k || m == l) continue;
+            term *= (t - (double)m / p) / ((double)(k - m) / p);
+        }
+        s += term;
+    }
+    return s;
+}
+
+/* Tensor-product Lagrange basis of order p on the reference hexahedron,
+ * evaluated at n_pts points (n_pts, 3): phi (n_pts, N), dphi (n_pts, 3, N)
+ * with dphi[q][k][a] = d phi_a / d xi_k (Sec. 4.1, isoparametric basis). */
+int oracle_hex_basis(int p, int n_pts, const double *pts, double *phi, double *dphi)
+{
+    if (p < 1 || p > 8 || n_pts < 1 || !pts || !phi || !dphi) return OR_BAD_ARG;
+    int n1 = p + 1, N = n1 * n1 * n1;
+    for (int q = 0; q < n_pts; ++q) {
+        double x = pts[3 * q], y = pts[3 * q + 1], z = pts[3 * q + 2];
+        for (int k = 0; k < n1; ++k)
+            for (int j = 0; j < n1; ++j)
+                for (int i = 0; i < n1; ++i) {
+                    int a = i + n1 * j + n1 * n1 * k;
+                    double lx = lagrange_1d(p, i, x), ly = lagrange_1d(p, j, y), lz = lagrange_1d(p, k, z);
+                    double dx = lagrange_1d_deriv(p, i, x), dy = lagrange_1d_deriv(p, j, y),
+                           dz = lagrange_1d_deriv(p, k, z);
+                    phi[(size_t)q * N + a] = lx * ly * lz;
+                    dphi[((size_t)q * 3 + 0) * N + a] = dx * ly * lz;
+                    dphi[((size_t)q * 3 + 1) * N + a] = lx * dy * lz;
+                    dphi[((size_t)q * 3 + 2) * N + a] = lx * ly * dz;
+                }
+    }
+    return OR_OK;
+}
+
+/* Tensor-product Gauss rule with nq points per axis on [0,1]^3, lexicographic
+ * (x fastest): pts (nq^3, 3), w (nq^3). */
+int oracle_hex_quadrature(int nq, double *pts, double *w)
+{
+    if (nq < 1 || nq > 16 || !pts || !w) return OR_BAD_ARG;
+    double g[16], gw[16];
+    int rc = oracle_gauss_1d(nq, g, gw);
+    if (rc) return rc;
+    for (int k = 0; k < nq; ++k)
+        for (int j = 0; j < nq; ++j)
+            for (int i = 0; i < nq; ++i) {
+                int q = i + nq * j + nq * nq * k;
+                pts[3 * q] = g[i];
+                pts[3 * q + 1] = g[j];
+                pts[3 * q + 2] = g[k];
+                w[q] = gw[i] * gw[j] * gw[k];
+            }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry (Sec. 4.1): x(xi) = sum_a x^a phi_a(xi), J_ij = d x_i / d xi_j,
+ * d/dx_j = d/dxi_k (J^-1)_kj.  Per element e and quadrature point q:
+ *   wdetJ[e][q]     = w_q det J      (the "v.det" operand of Tab. suee)
+ *   G[e][q][j][a]   = sum_k dphi[q][k][a] (J^-1)_kj   (physical gradients, "bfg")
+ *   Jinv[e][q][k][j] (optional)
+ * det J by cofactor expansion along the first row; J^-1 = adj(J) / det J.
+ * Returns 0, or 1 + the first element index with det J <= 0. */
+long long oracle_geometry(long long n_elems, int N, int Q, const double *coords, const int32_t *conn,
+                          const double *dphi, const double *w, double *wdetJ, double *G, double *Jinv)
+{
+    if (n_elems < 0 || N < 1 || Q < 1 || !coords || !conn || !dphi || !w || !wdetJ) return OR_BAD_ARG;
+    long long first_bad = 0;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        for (int q = 0; q < Q; ++q) {
+            double J[3][3] = {{0}};
+            for (int a = 0; a < N; ++a) {
+                const double *X = coords + 3 * (size_t)conn[(size_t)e * N + a];
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) J[i][j] += X[i] * dphi[((size_t)q * 3 + j) * N + a];
+            }
+            double c00 = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+            double c01 = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+            double c02 = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+            double det = J[0][0] * c00 + J[0][1] * c01 + J[0][2] * c02;
+            if (!(det > 0.0)) {
+#pragma omp critical
+                {
+                    if (first_bad == 0 || e + 1 < first_bad) first_bad = e + 1;
+                }
+            }
+            /* adjugate: inv[i][j] = cofactor[j][i] / det */
+            double cof[3][3];
+            cof[0][0] = c00;
+            cof[0][1] = c01;
+            cof[0][2] = c02;
+            cof[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+            cof[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+            cof[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+            cof[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+            cof[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+            cof[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            double inv[3][3];
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) inv[i][j] = cof[j][i] / det;
+            wdetJ[(size_t)e * Q + q] = w[q] * det;
+            if (Jinv)
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) Jinv[(((size_t)e * Q + q) * 3 + i) * 3 + j] = inv[i][j];
+            if (G)
+                for (int j = 0; j < 3; ++j)
+                    for (int a = 0; a < N; ++a) {
+                        double s = 0.0;
+                        for (int k = 0; k < 3; ++k) s += dphi[((size_t)q * 3 + k) * N + a] * inv[k][j];
+                        G[(((size_t)e * Q + q) * 3 + j) * N + a] = s;
+                    }
+        }
+    }
+    return first_bad;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Matrix mode (Algorithm 2), weak Laplacian ('0.i,0.i', v, u), Tab. ewfd:
+ *   K[e][a][b] = c_e sum_q wdetJ[e][q] sum_j G[e][q][j][a] G[e][q][j][b]
+ * (the einsum 'cq,cqjd,cqje->cde' of Sec. 5.3.1).  coef may be NULL (c = 1). */
+int oracle_matrix_laplace(long long n_elems, int N, int Q, const double *wdetJ, const double *G,
+                          const double *coef, double *K)
+{
+    if (n_elems < 0 || !wdetJ || !G || !K) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double *Ke = K + (size_t)e * N * N;
+        for (int i = 0; i < N * N; ++i) Ke[i] = 0.0;
+        double c = coef ? coef[e] : 1.0;
+        for (int q = 0; q < Q; ++q) {
+            const double *Gq = G + ((size_t)e * Q + q) * 3 * N;
+            double wd = wdetJ[(size_t)e * Q + q];
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < N; ++b) {
+                    double s = 0.0;
+                    for (int j = 0; j < 3; ++j) s += Gq[j * N + a] * Gq[j * N + b];
+                    Ke[a * N + b] += wd * c * s;
+                }
+        }
+    }
+    return OR_OK;
+}
+
+/* Matrix mode, (vector) dot product / mass ('i,i', v, u), eq. (fe3c):
+ *   M[e][(r,a)][(s,b)] = c_e sum_q wdetJ phi_q,a phi_q,b delta_rs
+ * rows and columns component-major (comp * N + node).  ncomp = 1 is the scalar
+ * mass matrix; ncomp = D gives D diagonal copies of it (Sec. 4.2). */
+int oracle_matrix_mass(long long n_elems, int N, int Q, int ncomp, const double *wdetJ, const double *phi,
+                       const double *coef, double *K)
+{
+    if (n_elems < 0 || ncomp < 1 || !wdetJ || !phi || !K) return OR_BAD_ARG;
+    int n = ncomp * N;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double *Ke = K + (size_t)e * n * n;
+        for (int i = 0; i < n * n; ++i) Ke[i] = 0.0;
+        double c = coef ? coef[e] : 1.0;
+        for (int q = 0; q < Q; ++q) {
+            double wd = wdetJ[(size_t)e * Q + q];
+            for (int r = 0; r < ncomp; ++r)
+                for (int a = 0; a < N; ++a)
+                    for (int s = 0; s < ncomp; ++s)
+                        for (int b = 0; b < N; ++b) {
+                            double delta = (r == s) ? 1.0 : 0.0;
+                            Ke[(r * N + a) * n + s * N + b] += wd * c * phi[q * N + a] * phi[q * N + b] * delta;
+                        }
+        }
+    }
+    return OR_OK;
+}
+
+/* The 0/1 tensor Psg[i][j][I] of shape (3,3,6) that maps the displacement
+ * gradient du_i/dx_j to the Voigt strain vector e_I (engineering shear),
+ * order (11,22,33,12,13,23): e_I = sum_ij Psg[i][j][I] du_i/dx_j (Sec. 5.3.3). */
+static void voigt_psg(double Psg[3][3][6])
+{
+    memset(Psg, 0, sizeof(double) * 54);
+    Psg[0][0][0] = 1.0;
+    Psg[1][1][1] = 1.0;
+    Psg[2][2][2] = 1.0;
+    Psg[0][1][3] = 1.0;
+    Psg[1][0][3] = 1.0;
+    Psg[0][2][4] = 1.0;
+    Psg[2][0][4] = 1.0;
+    Psg[1][2][5] = 1.0;
+    Psg[2][1][5] = 1.0;
+}
+
+/* Isotropic elasticity matrix in the Voigt order above:
+ * D = lambda m m^T + mu diag(2,2,2,1,1,1), m = (1,1,1,0,0,0).  D (E,6,6). */
+int oracle_lame_to_D(long long n_elems, const double *lam, const double *mu, double *D)
+{
+    if (n_elems < 0 || !lam || !mu || !D) return OR_BAD_ARG;
+    for (long long e = 0; e < n_elems; ++e) {
+        double *De = D + (size_t)e * 36;
+        for (int I = 0; I < 6; ++I)
+            for (int K = 0; K < 6; ++K) {
+                double v = 0.0;
+                if (I < 3 && K < 3) v += lam[e];
+                if (I == K) v += (I < 3) ? 2.0 * mu[e] : mu[e];
+                De[I * 6 + K] = v;
+            }
+    }
+    return OR_OK;
+}
+
+/* Strain-displacement matrix B (6, 3N) at one quadrature point:
+ * B[I][(i,a)] = sum_j Psg[i][j][I] G[j][a]  (the "rjI,cqje" factor). */
+static void strain_matrix(int N, const double *Gq, double *B)
+{
+    double Psg[3][3][6];
+    voigt_psg(Psg);
+    for (int I = 0; I < 6; ++I)
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < N; ++a) {
+                double s = 0.0;
+                for (int j = 0; j < 3; ++j) s += Psg[i][j][I] * Gq[j * N + a];
+                B[(size_t)I * 3 * N + i * N + a] = s;
+            }
+}
+
+/* Matrix mode, linear elasticity ('IK,s(i:j)->I,s(k:l)->K', D, v, u), Sec. 5.3.3:
+ *   K[e][(i,a)][(k,b)] = sum_q wdetJ sum_{I,K} B[I][(i,a)] D[I][K] B[K][(k,b)]
+ * with D per element (E,6,6) (material layout cq0 with a constant q axis). */
+int oracle_matrix_elasticity(long long n_elems, int N, int Q, const double *wdetJ, const double *G,
+                             const double *D, double *K)
+{
+    if (n_elems < 0 || N > 512 || !wdetJ || !G || !D || !K) return OR_BAD_ARG;
+    int n = 3 * N;
+    int rc = OR_OK;
+#pragma omp parallel
+    {
+        double *B = (double *)malloc(sizeof(double) * 6 * n);
+        double *DB = (double *)malloc(sizeof(double) * 6 * n);
+        if (!B || !DB) {
+#pragma omp critical
+            rc = OR_BAD_ARG;
+        }
+#pragma omp for schedule(static)
+        for (long long e = 0; e < n_elems; ++e) {
+            if (!B || !DB) continue;
+            double *Ke = K + (size_t)e * n * n;
+            const double *De = D + (size_t)e * 36;
+            for (int i = 0; i < n * n; ++i) Ke[i] = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                strain_matrix(N, G + ((size_t)e * Q + q) * 3 * N, B);
+                double wd = wdetJ[(size_t)e * Q + q];
+                for (int I = 0; I < 6; ++I)
+                    for (int c = 0; c < n; ++c) {
+                        double s = 0.0;
+                        for (int L = 0; L < 6; ++L) s += De[I * 6 + L] * B[(size_t)L * n + c];
+                        DB[(size_t)I * n + c] = s;
+                    }
+                for (int r = 0; r < n; ++r)
+                    for (int c = 0; c < n; ++c) {
+                        double s = 0.0;
+                        for (int I = 0; I < 6; ++I) s += B[(size_t)I * n + r] * DB[(size_t)I * n + c];
+                        Ke[(size_t)r * n + c] += wd * s;
+                    }
+            }
+        }
+        free(B);
+        free(DB);
+    }
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Residual mode (Algorithm 1): the element DOFs are gathered from the global
+ * DOF vector u (ncomp * node + comp) through the connectivity, the integrand
+ * F is evaluated at each quadrature point and integrated with wdetJ. */
+
+/* Weak Laplacian: r[e][a] = c_e sum_q wdetJ sum_j G[j][a] (grad u_h)_j,
+ * (grad u_h)_j = sum_b G[j][b] u[conn[e][b]]. */
+int oracle_residual_laplace(long long n_elems, int N, int Q, const int32_t *conn, const double *wdetJ,
+                            const double *G, const double *coef, const double *u, double *r)
+{
+    if (n_elems < 0 || !conn || !wdetJ || !G || !u || !r) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double *re = r + (size_t)e * N;
+        for (int a = 0; a < N; ++a) re[a] = 0.0;
+        double c = coef ? coef[e] : 1.0;
+        for (int q = 0; q < Q; ++q) {
+            const double *Gq = G + ((size_t)e * Q + q) * 3 * N;
+            double grad[3] = {0.0, 0.0, 0.0};
+            for (int j = 0; j < 3; ++j)
+                for (int b = 0; b < N; ++b) grad[j] += Gq[j * N + b] * u[conn[(size_t)e * N + b]];
+            double wd = wdetJ[(size_t)e * Q + q];
+            for (int a = 0; a < N; ++a) {
+                double s = 0.0;
+                for (int j = 0; j < 3; ++j) s += Gq[j * N + a] * grad[j];
+                re[a] += wd * c * s;
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/* (Vector) dot product: r[e][(i,a)] = c_e sum_q wdetJ phi_a u_h,i,
+ * u_h,i = sum_b phi_b u[ncomp*conn[e][b] + i]. */
+int oracle_residual_mass(long long n_elems, int N, int Q, int ncomp, const int32_t *conn, const double *wdetJ,
+                         const double *phi, const double *coef, const double *u, double *r)
+{
+    if (n_elems < 0 || ncomp < 1 || ncomp > 3 || !conn || !wdetJ || !phi || !u || !r) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double *re = r + (size_t)e * ncomp * N;
+        for (int a = 0; a < ncomp * N; ++a) re[a] = 0.0;
+        double c = coef ? coef[e] : 1.0;
+        for (int q = 0; q < Q; ++q) {
+            double uh[3] = {0.0, 0.0, 0.0};
+            for (int i = 0; i < ncomp; ++i)
+                for (int b = 0; b < N; ++b)
+                    uh[i] += phi[q * N + b] * u[(size_t)ncomp * conn[(size_t)e * N + b] + i];
+            double wd = wdetJ[(size_t)e * Q + q];
+            for (int i = 0; i < ncomp; ++i)
+                for (int a = 0; a < N; ++a) re[i * N + a] += wd * c * phi[q * N + a] * uh[i];
+        }
+    }
+    return OR_OK;
+}
+
+/* Linear elasticity: r[e][(i,a)] = sum_q wdetJ sum_I B[I][(i,a)] sigma_I,
+ * sigma = D e(u_h), e(u_h)_K = sum_(k,b) B[K][(k,b)] u[3*conn[e][b] + k]. */
+int oracle_residual_elasticity(long long n_elems, int N, int Q, const int32_t *conn, const double *wdetJ,
+                               const double *G, const double *D, const double *u, double *r)
+{
+    if (n_elems < 0 || N > 512 || !conn || !wdetJ || !G || !D || !u || !r) return OR_BAD_ARG;
+    int n = 3 * N;
+    int rc = OR_OK;
+#pragma omp parallel
+    {
+        double *B = (double *)malloc(sizeof(double) * 6 * n);
+        double *ue = (double *)malloc(sizeof(double) * n);
+        if (!B || !ue) {
+#pragma omp critical
+            rc = OR_BAD_ARG;
+        }
+#pragma omp for schedule(static)
+        for (long long e = 0; e < n_elems; ++e) {
+            if (!B || !ue) continue;
+            double *re = r + (size_t)e * n;
+            const double *De = D + (size_t)e * 36;
+            for (int k = 0; k < 3; ++k)
+                for (int b = 0; b < N; ++b) ue[k * N + b] = u[3 * (size_t)conn[(size_t)e * N + b] + k];
+            for (int c = 0; c < n; ++c) re[c] = 0.0;
+            for (int q = 0; q < Q; ++q) {
+                strain_matrix(N, G + ((size_t)e * Q + q) * 3 * N, B);
+                double eps[6], sig[6];
+                for (int K = 0; K < 6; ++K) {
+                    double s = 0.0;
+                    for (int c = 0; c < n; ++c) s += B[(size_t)K * n + c] * ue[c];
+                    eps[K] = s;
+                }
+                for (int I = 0; I < 6; ++I) {
+                    double s = 0.0;
+                    for (int K = 0; K < 6; ++K) s += De[I * 6 + K] * eps[K];
+                    sig[I] = s;
+                }
+                double wd = wdetJ[(size_t)e * Q + q];
+                for (int c = 0; c < n; ++c) {
+                    double s = 0.0;
+                    for (int I = 0; I < 6; ++I) s += B[(size_t)I * n + c] * sig[I];
+                    re[c] += wd * s;
+                }
+            }
+        }
+        free(B);
+        free(ue);
+    }
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Assembly of element vectors into a global vector (outside the timed region
+ * of the paper, Sec. 6): g[ncomp*conn[e][a] + i] += r[e][i*N + a], summed
+ * sequentially in ascending (e, a, i) order.  accumulate = 0 zeroes g first. */
+int oracle_assemble(long long n_elems, int N, int ncomp, const int32_t *conn, const double *r, long long n_nodes,
+                    int accumulate, double *g)
+{
+    if (n_elems < 0 || ncomp < 1 || !conn || !r || !g) return OR_BAD_ARG;
+    if (!accumulate)
+        for (long long k = 0; k < n_nodes * ncomp; ++k) g[k] = 0.0;
+    for (long long e = 0; e < n_elems; ++e)
+        for (int a = 0; a < N; ++a)
+            for (int i = 0; i < ncomp; ++i) {
+                long long node = conn[(size_t)e * N + a];
+                if (node < 0 || node >= n_nodes) return OR_BAD_ARG;
+                g[ncomp * node + i] += r[(size_t)e * ncomp * N + i * N + a];
+            }
+    return OR_OK;
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

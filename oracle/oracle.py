@@ -1,0 +1,205 @@
+"""ctypes wrapper of the FP64 nested-loop oracle (oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the benchmark's
+CPU-baseline leg call it; the product path never does.  Every function is a
+plain definition from Cimrman, arXiv 2107.04121 (Sec. 4.1 geometry and
+Algorithms 1-2; Sec. 5.3 forms), see the comments in oracle.c.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (-O2, no fast-math, OpenMP over elements)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-std=c11", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.oracle_gauss_1d.argtypes = [ctypes.c_int, _D, _D]
+        L.oracle_hex_basis.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
+        L.oracle_hex_quadrature.argtypes = [ctypes.c_int, _D, _D]
+        L.oracle_geometry.restype = ctypes.c_longlong
+        L.oracle_geometry.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _D, _I, _D, _D, _D, _D, _D]
+        L.oracle_matrix_laplace.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        L.oracle_matrix_mass.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        L.oracle_lame_to_D.argtypes = [ctypes.c_longlong, _D, _D, _D]
+        L.oracle_matrix_elasticity.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        L.oracle_residual_laplace.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D, _D]
+        L.oracle_residual_mass.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I, _D, _D,
+                                           _D, _D, _D]
+        L.oracle_residual_elasticity.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D,
+                                                 _D]
+        L.oracle_assemble.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, ctypes.c_longlong,
+                                      ctypes.c_int, _D]
+        L.oracle_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_D)
+
+
+def _i(a):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_I)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError("oracle call failed with code %d" % rc)
+
+
+def num_threads() -> int:
+    return lib().oracle_num_threads()
+
+
+def gauss_1d(n: int):
+    """Gauss-Legendre points and weights on [0, 1], ascending."""
+    x = np.zeros(n)
+    w = np.zeros(n)
+    _check(lib().oracle_gauss_1d(n, _d(x), _d(w)))
+    return x, w
+
+
+def hex_quadrature(nq: int):
+    """Tensor Gauss rule on [0,1]^3, lexicographic x fastest: pts (nq^3, 3), w (nq^3)."""
+    pts = np.zeros((nq ** 3, 3))
+    w = np.zeros(nq ** 3)
+    _check(lib().oracle_hex_quadrature(nq, _d(pts), _d(w)))
+    return pts, w
+
+
+def hex_basis(p: int, pts):
+    """Order-p Lagrange basis on [0,1]^3 at pts: phi (n, N), dphi (n, 3, N)."""
+    pts = _f64(pts).reshape(-1, 3)
+    N = (p + 1) ** 3
+    phi = np.zeros((pts.shape[0], N))
+    dphi = np.zeros((pts.shape[0], 3, N))
+    _check(lib().oracle_hex_basis(p, pts.shape[0], _d(pts), _d(phi), _d(dphi)))
+    return phi, dphi
+
+
+class RefElement:
+    """Reference hexahedron of order p with an nq^3 Gauss rule."""
+
+    def __init__(self, p: int, nq: int):
+        self.p, self.nq = p, nq
+        self.pts, self.w = hex_quadrature(nq)
+        self.phi, self.dphi = hex_basis(p, self.pts)
+        self.N = (p + 1) ** 3
+        self.Q = nq ** 3
+
+
+def geometry(coords, conn, ref: RefElement, want_G=True, want_Jinv=False):
+    """wdetJ (E,Q), G (E,Q,3,N), Jinv (E,Q,3,3); raises on det J <= 0."""
+    coords = _f64(coords)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    E = conn.shape[0]
+    wdetJ = np.zeros((E, ref.Q))
+    G = np.zeros((E, ref.Q, 3, ref.N)) if want_G else None
+    Jinv = np.zeros((E, ref.Q, 3, 3)) if want_Jinv else None
+    bad = lib().oracle_geometry(E, ref.N, ref.Q, _d(coords), _i(conn), _d(ref.dphi), _d(ref.w), _d(wdetJ), _d(G),
+                                _d(Jinv))
+    if bad < 0:
+        raise RuntimeError("oracle_geometry: bad argument")
+    if bad > 0:
+        raise ValueError("non-positive det J in element %d" % (bad - 1))
+    return wdetJ, G, Jinv
+
+
+def matrix_laplace(wdetJ, G, coef=None):
+    E, Q, _, N = G.shape
+    K = np.zeros((E, N, N))
+    _check(lib().oracle_matrix_laplace(E, N, Q, _d(wdetJ), _d(G), _d(_f64(coef)), _d(K)))
+    return K
+
+
+def matrix_mass(wdetJ, phi, ncomp=1, coef=None):
+    E, Q = wdetJ.shape
+    N = phi.shape[1]
+    n = ncomp * N
+    K = np.zeros((E, n, n))
+    _check(lib().oracle_matrix_mass(E, N, Q, ncomp, _d(wdetJ), _d(_f64(phi)), _d(_f64(coef)), _d(K)))
+    return K
+
+
+def lame_to_D(lam, mu):
+    lam = _f64(lam)
+    mu = _f64(mu)
+    D = np.zeros((lam.shape[0], 6, 6))
+    _check(lib().oracle_lame_to_D(lam.shape[0], _d(lam), _d(mu), _d(D)))
+    return D
+
+
+def matrix_elasticity(wdetJ, G, D):
+    E, Q, _, N = G.shape
+    K = np.zeros((E, 3 * N, 3 * N))
+    _check(lib().oracle_matrix_elasticity(E, N, Q, _d(wdetJ), _d(G), _d(_f64(D)), _d(K)))
+    return K
+
+
+def residual_laplace(conn, wdetJ, G, u, coef=None):
+    E, Q, _, N = G.shape
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    r = np.zeros((E, N))
+    _check(lib().oracle_residual_laplace(E, N, Q, _i(conn), _d(wdetJ), _d(G), _d(_f64(coef)), _d(_f64(u)), _d(r)))
+    return r
+
+
+def residual_mass(conn, wdetJ, phi, u, ncomp=1, coef=None):
+    E, Q = wdetJ.shape
+    N = phi.shape[1]
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    r = np.zeros((E, ncomp * N))
+    _check(lib().oracle_residual_mass(E, N, Q, ncomp, _i(conn), _d(wdetJ), _d(_f64(phi)), _d(_f64(coef)),
+                                      _d(_f64(u)), _d(r)))
+    return r
+
+
+def residual_elasticity(conn, wdetJ, G, D, u):
+    E, Q, _, N = G.shape
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    r = np.zeros((E, 3 * N))
+    _check(lib().oracle_residual_elasticity(E, N, Q, _i(conn), _d(wdetJ), _d(G), _d(_f64(D)), _d(_f64(u)), _d(r)))
+    return r
+
+
+def assemble(conn, r, n_nodes, ncomp, g=None):
+    """g[ncomp*conn[e,a] + i] += r[e, i*N + a], ascending (e, a, i)."""
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    E, N = conn.shape
+    r = _f64(r).reshape(E, ncomp * N)
+    acc = 1 if g is not None else 0
+    out = np.zeros(n_nodes * ncomp) if g is None else _f64(g).copy()
+    _check(lib().oracle_assemble(E, N, ncomp, _i(conn), _d(r), n_nodes, acc, _d(out)))
+    return out

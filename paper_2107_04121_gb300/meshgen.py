@@ -1,0 +1,116 @@
+"""Seeded synthetic inputs: structured hexahedral meshes, materials and DOF vectors.
+
+This module only draws random numbers and lays out mesh topology; it holds none
+of the finite element arithmetic (no basis, quadrature, geometry mapping or
+form).  The same generators feed both the CUDA library and the FP64 oracle.
+
+Conventions (the paper, Sec. 6, uses a 1D bar of n x 1 x 1 hexahedra whose
+element-level work equals that of any other hex mesh of the same size):
+  * domain [0, Lx] x [0, Ly] x [0, Lz], nx * ny * nz hexahedra of order p;
+  * global nodes on the (nx p + 1) x (ny p + 1) x (nz p + 1) equispaced grid,
+    numbered x fastest;
+  * element (ex, ey, ez) has index ex + nx ey + nx ny ez, local node (i, j, k)
+    (x fastest, i + (p+1) j + (p+1)^2 k) maps to grid node (ex p + i, ey p + j, ez p + k);
+  * interior nodes (not on the boundary of the box) are moved by a uniform
+    random offset in [-a h, a h] per coordinate, h = node spacing on that axis;
+  * one numpy PCG64 stream per mesh, drawn in this order: the coordinate
+    offsets (n_nodes, 3) for all nodes (boundary draws discarded), then the
+    materials, then the DOF vector.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class HexMesh:
+    coords: np.ndarray  # (n_nodes, 3) float64
+    conn: np.ndarray  # (n_elems, (p+1)^3) int32
+    order: int
+    shape: tuple  # (nx, ny, nz)
+    rng: np.random.Generator  # positioned after the coordinate draws
+
+    @property
+    def n_nodes(self) -> int:
+        return self.coords.shape[0]
+
+    @property
+    def n_elems(self) -> int:
+        return self.conn.shape[0]
+
+    @property
+    def nodes_per_elem(self) -> int:
+        return self.conn.shape[1]
+
+
+def grid_node_count(nx: int, ny: int, nz: int, p: int) -> int:
+    return (nx * p + 1) * (ny * p + 1) * (nz * p + 1)
+
+
+def structured_hex(nx: int, ny: int, nz: int, p: int = 1, perturb: float = 0.0, seed: int = 0,
+                   lengths=(1.0, 1.0, 1.0)) -> HexMesh:
+    """Structured order-p hexahedral mesh with interior nodes perturbed."""
+    NX, NY, NZ = nx * p + 1, ny * p + 1, nz * p + 1
+    ix, iy, iz = np.meshgrid(np.arange(NX), np.arange(NY), np.arange(NZ), indexing="ij")
+    # x fastest: flatten in (z, y, x) order
+    ix = ix.transpose(2, 1, 0).ravel()
+    iy = iy.transpose(2, 1, 0).ravel()
+    iz = iz.transpose(2, 1, 0).ravel()
+    h = np.array([lengths[0] / (nx * p), lengths[1] / (ny * p), lengths[2] / (nz * p)])
+    coords = np.stack([ix * h[0], iy * h[1], iz * h[2]], axis=1).astype(np.float64)
+    rng = np.random.default_rng(seed)
+    offs = rng.uniform(-1.0, 1.0, size=(coords.shape[0], 3))
+    if perturb != 0.0:
+        interior = (ix > 0) & (ix < NX - 1) & (iy > 0) & (iy < NY - 1) & (iz > 0) & (iz < NZ - 1)
+        coords[interior] += perturb * offs[interior] * h[None, :]
+    n1 = p + 1
+    ex, ey, ez = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ex = ex.transpose(2, 1, 0).ravel()
+    ey = ey.transpose(2, 1, 0).ravel()
+    ez = ez.transpose(2, 1, 0).ravel()
+    li, lj, lk = np.meshgrid(np.arange(n1), np.arange(n1), np.arange(n1), indexing="ij")
+    li = li.transpose(2, 1, 0).ravel()
+    lj = lj.transpose(2, 1, 0).ravel()
+    lk = lk.transpose(2, 1, 0).ravel()
+    gx = ex[:, None] * p + li[None, :]
+    gy = ey[:, None] * p + lj[None, :]
+    gz = ez[:, None] * p + lk[None, :]
+    conn = (gx + NX * gy + NX * NY * gz).astype(np.int32)
+    return HexMesh(coords=coords, conn=np.ascontiguousarray(conn), order=p, shape=(nx, ny, nz), rng=rng)
+
+
+def lame_materials(mesh: HexMesh, lam_range=(0.5, 2.0), mu_range=(0.2, 1.0)):
+    """Per-element Lame parameters lambda ~ U[lam_range], mu ~ U[mu_range]."""
+    lam = mesh.rng.uniform(lam_range[0], lam_range[1], size=mesh.n_elems)
+    mu = mesh.rng.uniform(mu_range[0], mu_range[1], size=mesh.n_elems)
+    return lam, mu
+
+
+def normal_dofs(mesh: HexMesh, ncomp: int) -> np.ndarray:
+    """Global DOF vector u ~ N(0, 1), index ncomp * node + comp."""
+    return mesh.rng.standard_normal(mesh.n_nodes * ncomp)
+
+
+def bar_mesh(n_cells: int, p: int, seed: int = 0) -> HexMesh:
+    """The paper's benchmark mesh: a 1D bar of n x 1 x 1 hexahedra (Sec. 6)."""
+    return structured_hex(n_cells, 1, 1, p, 0.0, seed, lengths=(float(n_cells), 1.0, 1.0))
+
+
+# Named workloads --------------------------------------------------------------
+
+def laplace_q1_cube(n: int = 8, seed: int = 0):
+    """Weak Laplacian on an n^3 Q1 cube, interior nodes +-0.1h, u ~ N(0,1) per node."""
+    mesh = structured_hex(n, n, n, 1, 0.1, seed)
+    u = normal_dofs(mesh, 1)
+    return mesh, u
+
+
+def elasticity_q2_cube(n: int = 48, seed: int = 1, perturb: float = 0.15):
+    """Q2 linear elasticity on an n^3 cube, interior nodes +-0.15h,
+    lambda ~ U[0.5, 2], mu ~ U[0.2, 1] per element, u ~ N(0,1) per DOF."""
+    mesh = structured_hex(n, n, n, 2, perturb, seed)
+    lam, mu = lame_materials(mesh)
+    u = normal_dofs(mesh, 3)
+    return mesh, lam, mu, u

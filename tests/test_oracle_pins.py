@@ -1,0 +1,327 @@
+"""Pins of the FP64 oracle against what the mathematics and the paper fix.
+
+None of these re-types the oracle's formulas: each check uses a closed form,
+exact rational integration (tests/exact_fe.py), a library routine
+(numpy.polynomial.legendre.leggauss), an invariant of the forms, or values
+printed in the paper (tests/golden/).  Cimrman, arXiv 2107.04121.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_04121_gb300 import meshgen
+from tests import exact_fe
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# -- quadrature ----------------------------------------------------------------
+
+@pytest.mark.parametrize("n", list(range(1, 9)))
+def test_gauss_matches_leggauss(n):
+    x, w = oracle.gauss_1d(n)
+    xr, wr = np.polynomial.legendre.leggauss(n)
+    np.testing.assert_allclose(x, 0.5 * (xr + 1.0), rtol=0, atol=2e-15)
+    np.testing.assert_allclose(w, 0.5 * wr, rtol=0, atol=2e-15)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+def test_gauss_integrates_monomials_exactly(n):
+    x, w = oracle.gauss_1d(n)
+    for k in range(2 * n):
+        assert abs(np.dot(w, x ** k) - 1.0 / (k + 1)) < 1e-15
+    # degree 2n is not integrated exactly
+    assert abs(np.dot(w, x ** (2 * n)) - 1.0 / (2 * n + 1)) > 1e-8
+
+
+def test_hex_quadrature_lexicographic_x_fastest():
+    pts, w = oracle.hex_quadrature(3)
+    g, gw = np.polynomial.legendre.leggauss(3)
+    g, gw = 0.5 * (g + 1), 0.5 * gw
+    assert abs(w.sum() - 1.0) < 4e-15
+    np.testing.assert_allclose(pts[1], [g[1], g[0], g[0]], atol=1e-15)
+    np.testing.assert_allclose(pts[3], [g[0], g[1], g[0]], atol=1e-15)
+    np.testing.assert_allclose(pts[9], [g[0], g[0], g[1]], atol=1e-15)
+    np.testing.assert_allclose(w[13], gw[1] ** 3, atol=1e-15)
+
+
+# -- reference basis ------------------------------------------------------------
+
+def _ref_nodes(p):
+    n1 = p + 1
+    t = np.arange(n1) / p
+    return np.array([[t[i], t[j], t[k]] for k in range(n1) for j in range(n1) for i in range(n1)])
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_basis_is_nodal_and_partition_of_unity(p):
+    nodes = _ref_nodes(p)
+    phi, dphi = oracle.hex_basis(p, nodes)
+    np.testing.assert_allclose(phi, np.eye(nodes.shape[0]), atol=1e-13)
+    rng = np.random.default_rng(5)
+    x = rng.uniform(0, 1, (20, 3))
+    phi, dphi = oracle.hex_basis(p, x)
+    np.testing.assert_allclose(phi.sum(1), 1.0, atol=1e-13)
+    np.testing.assert_allclose(dphi.sum(2), 0.0, atol=1e-11)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_basis_gradient_matches_finite_differences(p):
+    rng = np.random.default_rng(6)
+    x = rng.uniform(0.1, 0.9, (6, 3))
+    phi, dphi = oracle.hex_basis(p, x)
+    h = 1e-6
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = h
+        fp, _ = oracle.hex_basis(p, x + e)
+        fm, _ = oracle.hex_basis(p, x - e)
+        np.testing.assert_allclose(dphi[:, k, :], (fp - fm) / (2 * h), atol=5e-8)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_basis_reproduces_tensor_polynomials(p):
+    # f = x^p y^(p-1) z + 2 lies in Q_p, so its interpolant is exact
+    f = lambda X: X[:, 0] ** p * X[:, 1] ** (p - 1) * X[:, 2] + 2.0
+    df = lambda X: np.stack([p * X[:, 0] ** (p - 1) * X[:, 1] ** (p - 1) * X[:, 2],
+                             (p - 1) * X[:, 0] ** p * X[:, 1] ** max(p - 2, 0) * X[:, 2] if p > 1 else 0 * X[:, 0],
+                             X[:, 0] ** p * X[:, 1] ** (p - 1)], 1)
+    nodes = _ref_nodes(p)
+    x = np.random.default_rng(7).uniform(0, 1, (15, 3))
+    phi, dphi = oracle.hex_basis(p, x)
+    np.testing.assert_allclose(phi @ f(nodes), f(x), atol=1e-12)
+    np.testing.assert_allclose(np.einsum("qkn,n->qk", dphi, f(nodes)), df(x), atol=1e-11)
+
+
+# -- closed forms on undistorted elements -----------------------------------------
+
+def test_q1_unit_cube_laplacian_closed_form():
+    """K^ab of the unit-cube Q1 Laplacian: 1/3 (same node), 0 (edge neighbour),
+    -1/12 (face diagonal), -1/12 (body diagonal); a cube of side h gives h K^."""
+    n = 8
+    mesh = meshgen.structured_hex(n, n, n, 1, 0.0, 0)
+    ref = oracle.RefElement(1, 2)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    K = oracle.matrix_laplace(wdetJ, G)
+    nodes = _ref_nodes(1)
+    diff = (np.abs(nodes[:, None, :] - nodes[None, :, :]) > 0.5).sum(-1)
+    Khat = np.select([diff == 0, diff == 1, diff == 2, diff == 3], [1 / 3, 0.0, -1 / 12, -1 / 12])
+    np.testing.assert_allclose(K, np.broadcast_to(Khat / n, K.shape), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_box_element_matches_exact_kronecker_integrals(p):
+    h = (0.5, 0.7, 1.3)
+    mesh = meshgen.structured_hex(1, 1, 1, p, 0.0, 0, lengths=h)
+    mesh.coords[:] += np.array([0.25, -1.0, 3.0])  # translation does not change the forms
+    ref = oracle.RefElement(p, p + 1)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    lam, mu = np.array([1.7]), np.array([0.6])
+    KL = oracle.matrix_laplace(wdetJ, G)[0]
+    KM = oracle.matrix_mass(wdetJ, ref.phi)[0]
+    KE = oracle.matrix_elasticity(wdetJ, G, oracle.lame_to_D(lam, mu))[0]
+    for got, want in [(KL, exact_fe.box_laplace(p, h)), (KM, exact_fe.box_mass(p, h)),
+                      (KE, exact_fe.box_elasticity(p, h, lam[0], mu[0]))]:
+        assert np.abs(got - want).max() <= 1e-13 * np.abs(want).max()
+
+
+def test_affine_element_geometry():
+    """An affine map x = A xi + t is reproduced exactly: J = A, det J = det A."""
+    rng = np.random.default_rng(8)
+    A = np.eye(3) + 0.3 * rng.standard_normal((3, 3))
+    if np.linalg.det(A) < 0:
+        A[:, 0] *= -1
+    t = rng.standard_normal(3)
+    for p in (1, 2, 3):
+        X = _ref_nodes(p) @ A.T + t
+        conn = np.arange(X.shape[0], dtype=np.int32)[None, :]
+        ref = oracle.RefElement(p, p + 1)
+        wdetJ, G, Jinv = oracle.geometry(X, conn, ref, want_Jinv=True)
+        np.testing.assert_allclose(wdetJ[0], ref.w * np.linalg.det(A), rtol=1e-13)
+        np.testing.assert_allclose(Jinv[0], np.broadcast_to(np.linalg.inv(A), Jinv[0].shape), atol=1e-13)
+        want_G = np.einsum("kj,qka->qja", np.linalg.inv(A), ref.dphi)
+        np.testing.assert_allclose(G[0], want_G, atol=1e-12)
+
+
+def test_inverted_element_is_reported():
+    mesh = meshgen.structured_hex(2, 2, 2, 1, 0.0, 0)
+    conn = mesh.conn.copy()
+    conn[3, [0, 1]] = conn[3, [1, 0]]  # mirror element 3
+    with pytest.raises(ValueError, match="element 3"):
+        oracle.geometry(mesh.coords, conn, oracle.RefElement(1, 2))
+
+
+# -- invariants on distorted meshes --------------------------------------------------
+
+@pytest.fixture(scope="module", params=[1, 2, 3])
+def distorted(request):
+    p = request.param
+    mesh = meshgen.structured_hex(3, 3, 3, p, 0.15, 11)
+    lam, mu = meshgen.lame_materials(mesh)
+    # det J of an order-p map has degree 3p - 1 per axis: a Gauss rule with
+    # 2 nq - 1 >= 3p - 1 integrates the element volumes exactly
+    nq = max(p + 1, (3 * p + 1) // 2)
+    ref = oracle.RefElement(p, nq)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    return mesh, ref, wdetJ, G, lam, mu
+
+
+def test_volumes_sum_to_one(distorted):
+    mesh, ref, wdetJ, G, lam, mu = distorted
+    assert abs(wdetJ.sum() - 1.0) < 1e-13
+    M = oracle.matrix_mass(wdetJ, ref.phi)
+    np.testing.assert_allclose(M.sum((1, 2)), wdetJ.sum(1), rtol=1e-13)
+
+
+def test_laplace_rows_sum_to_zero_and_symmetry(distorted):
+    mesh, ref, wdetJ, G, lam, mu = distorted
+    K = oracle.matrix_laplace(wdetJ, G)
+    scale = np.abs(K).max()
+    assert np.abs(K.sum(2)).max() < 1e-13 * scale
+    assert np.abs(K - K.transpose(0, 2, 1)).max() < 1e-14 * scale
+    # positive semi-definite with exactly one zero eigenvalue (constants)
+    ev = np.linalg.eigvalsh(K[0])
+    assert ev[0] > -1e-13 * scale and ev[1] > 1e-6 * scale
+
+
+def test_patch_test_linear_field(distorted):
+    mesh, ref, wdetJ, G, lam, mu = distorted
+    b = np.array([0.3, -1.2, 0.7])
+    u = mesh.coords @ b + 0.5
+    grad = np.einsum("eqja,ea->eqj", G, u[mesh.conn])
+    np.testing.assert_allclose(grad, np.broadcast_to(b, grad.shape), atol=1e-12)
+
+
+def test_elasticity_rigid_body_modes_and_symmetry(distorted):
+    mesh, ref, wdetJ, G, lam, mu = distorted
+    K = oracle.matrix_elasticity(wdetJ, G, oracle.lame_to_D(lam, mu))
+    X = mesh.coords[mesh.conn]  # (E, N, 3)
+    E, N = mesh.conn.shape
+    modes = []
+    for i in range(3):
+        m = np.zeros((E, 3, N))
+        m[:, i, :] = 1.0
+        modes.append(m)
+    for axis in range(3):  # rotations u = w x x
+        w = np.zeros(3)
+        w[axis] = 1.0
+        modes.append(np.cross(w, X).transpose(0, 2, 1))
+    scale = np.abs(K).max()
+    for m in modes:
+        Ku = np.einsum("eij,ej->ei", K, m.reshape(E, 3 * N))
+        assert np.abs(Ku).max() < 1e-12 * scale * max(1.0, np.abs(m).max())
+    assert np.abs(K - K.transpose(0, 2, 1)).max() < 1e-14 * scale
+    # exactly six zero eigenvalues
+    ev = np.linalg.eigvalsh(K[0])
+    assert np.all(np.abs(ev[:6]) < 1e-10 * scale) and ev[6] > 1e-6 * scale
+
+
+def test_residual_equals_matrix_times_dofs(distorted):
+    mesh, ref, wdetJ, G, lam, mu = distorted
+    rng = np.random.default_rng(9)
+    E, N = mesh.conn.shape
+    u1 = rng.standard_normal(mesh.n_nodes)
+    u3 = rng.standard_normal(3 * mesh.n_nodes)
+    ue3 = u3.reshape(-1, 3)[mesh.conn].transpose(0, 2, 1).reshape(E, 3 * N)  # component-major
+    coef = rng.uniform(0.5, 2.0, E)
+    D = oracle.lame_to_D(lam, mu)
+    cases = [
+        (oracle.matrix_laplace(wdetJ, G, coef), oracle.residual_laplace(mesh.conn, wdetJ, G, u1, coef), u1[mesh.conn]),
+        (oracle.matrix_mass(wdetJ, ref.phi, 1, coef), oracle.residual_mass(mesh.conn, wdetJ, ref.phi, u1, 1, coef),
+         u1[mesh.conn]),
+        (oracle.matrix_mass(wdetJ, ref.phi, 3), oracle.residual_mass(mesh.conn, wdetJ, ref.phi, u3, 3), ue3),
+        (oracle.matrix_elasticity(wdetJ, G, D), oracle.residual_elasticity(mesh.conn, wdetJ, G, D, u3), ue3),
+    ]
+    for K, r, ue in cases:
+        want = np.einsum("eij,ej->ei", K, ue)
+        assert np.abs(r - want).max() < 1e-12 * np.abs(want).max()
+
+
+def test_vector_mass_is_block_diagonal_scalar_mass(distorted):
+    mesh, ref, wdetJ, G, lam, mu = distorted
+    M1 = oracle.matrix_mass(wdetJ, ref.phi, 1)
+    M3 = oracle.matrix_mass(wdetJ, ref.phi, 3)
+    N = M1.shape[1]
+    for i in range(3):
+        for k in range(3):
+            blk = M3[:, i * N:(i + 1) * N, k * N:(k + 1) * N]
+            np.testing.assert_array_equal(blk, M1 if i == k else 0.0)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_assembled_laplace_residual_of_linear_field_vanishes_inside(p):
+    mesh = meshgen.structured_hex(3, 3, 3, p, 0.1, 12)
+    ref = oracle.RefElement(p, p + 1)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    u = mesh.coords @ np.array([1.0, -2.0, 0.5]) + 3.0
+    g = oracle.assemble(mesh.conn, oracle.residual_laplace(mesh.conn, wdetJ, G, u), mesh.n_nodes, 1)
+    X = mesh.coords
+    inside = np.all((X > 1e-9) & (X < 1 - 1e-9), axis=1)
+    assert inside.sum() > 0
+    assert np.abs(g[inside]).max() < 1e-12
+    assert np.abs(g[~inside]).max() > 1e-3
+
+
+def test_assemble_matches_brute_force_and_volume():
+    mesh = meshgen.structured_hex(4, 3, 2, 2, 0.1, 13)
+    ref = oracle.RefElement(2, 3)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    r = oracle.residual_mass(mesh.conn, wdetJ, ref.phi, np.ones(3 * mesh.n_nodes), 3)
+    g = oracle.assemble(mesh.conn, r, mesh.n_nodes, 3)
+    want = np.zeros(3 * mesh.n_nodes)
+    E, N = mesh.conn.shape
+    for e in range(E):
+        for a in range(N):
+            for i in range(3):
+                want[3 * mesh.conn[e, a] + i] += r[e, i * N + a]
+    np.testing.assert_array_equal(g, want)
+    # sum of the assembled mass action on a constant field is the volume per component
+    np.testing.assert_allclose(g.reshape(-1, 3).sum(0), 1.0, rtol=1e-13)
+    g2 = oracle.assemble(mesh.conn, r, mesh.n_nodes, 3, g)
+    np.testing.assert_allclose(g2, 2 * g, rtol=1e-15)
+
+
+# -- the paper's printed sizes --------------------------------------------------------
+
+def _tab_cdc():
+    rows = []
+    with open(os.path.join(GOLDEN, "tab_cdc.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                rows.append([float(x) for x in line.split()])
+    return rows
+
+
+def test_tab_cdc_sizes():
+    """Tab. cdc: bar-mesh DOF counts and FP64 output sizes of (n_c, n_dr[, n_dc]) arrays."""
+    for cells, p, nqp, ndofs, _, rs, Ms, rv, Mv in _tab_cdc():
+        cells, p = int(cells), int(p)
+        N = (p + 1) ** 3
+        assert (p + 1) ** 3 == nqp  # (p+1)^3 Gauss points
+        assert meshgen.grid_node_count(cells, 1, 1, p) == ndofs
+        mb = lambda n: round(n * 8 / 1e6, 1)
+        assert mb(cells * N) == rs
+        assert mb(cells * N * N) == Ms
+        assert mb(cells * 3 * N) == rv
+        assert mb(cells * 9 * N * N) == Mv
+    mesh = meshgen.bar_mesh(1024, 2)
+    assert mesh.n_nodes == 18441 and mesh.n_elems == 1024
+
+
+def test_printed_einsum_shapes():
+    """Operand and output shapes printed in Sec. 5.3 for 1024-cell meshes."""
+    ref2 = oracle.RefElement(2, 3)
+    mesh = meshgen.bar_mesh(4, 2)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref2)
+    assert G.shape[1:] == (27, 3, 27)  # cqjd (1024, 27, 3, 27)
+    assert oracle.matrix_laplace(wdetJ, G).shape[1:] == (27, 27)  # cde (1024, 27, 27)
+    ref1 = oracle.RefElement(1, 2)
+    mesh1 = meshgen.bar_mesh(4, 1)
+    w1, G1, _ = oracle.geometry(mesh1.coords, mesh1.conn, ref1)
+    M = oracle.matrix_mass(w1, ref1.phi, 3)
+    assert M.reshape(4, 3, 8, 3, 8).shape[1:] == (3, 8, 3, 8)  # crdse (1024, 3, 8, 3, 8)
+    D = oracle.lame_to_D(np.ones(4), np.ones(4))
+    assert D.shape[1:] == (6, 6)
+    assert oracle.matrix_elasticity(w1, G1, D).reshape(4, 3, 8, 3, 8).shape[1:] == (3, 8, 3, 8)  # cresf
