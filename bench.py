@@ -1,0 +1,433 @@
+#!/usr/bin/env python
+"""Benchmark of the finite element weak-form evaluator on one GB300.
+
+Workload: linear elasticity ('IK,s(i:j)->I,s(k:l)->K', Tab. ewfd of Cimrman,
+arXiv 2107.04121) with vector Q2 hexahedra (27 nodes, 81 x 81 element
+matrices) on a 48^3 cube, interior nodes perturbed by +-0.15h (seed 1), 3x3x3
+Gauss points, per-element Lame parameters lambda ~ U[0.5, 2], mu ~ U[0.2, 1],
+nodal DOFs u ~ N(0, 1).  Synthetic inputs; the paper's own timings use a
+1D bar of hexahedra with precomputed geometry on a CPU.
+
+One step = the whole hot path through the C ABI:
+  fe_geometry_update (FP64 J, det J, J^-1)  ->  fe_eval_matrix (K_e)
+  ->  fe_eval_residual (r_e)  ->  fe_assemble_vector (compensated FP32).
+The headline line is the mixed-precision path (FP64 geometry, FP32
+contraction); the plain FP64 path is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "elements/s + % roofline, Q2 elasticity K_e & r_e: mixed vs FP64 at rel err ≤1e-5"
+UNIT = "elements/s"
+Q2_N, Q2_Q = 27, 27
+# algorithmic bytes per element of the matrix kernel (FP32 path): read J^-1 and
+# w det J (27 qp x 10 floats), the Lame pair (2 doubles), write K_e (81 x 81 floats)
+MATRIX_BYTES_PER_ELEM_F32 = Q2_Q * 10 * 4 + 16 + 81 * 81 * 4
+MATRIX_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 16 + 81 * 81 * 8
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=48, help="cube edge in elements (48 -> 110,592 hexes)")
+    ap.add_argument("--prec", default="f32", help="contraction precision of the headline path")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="time the headline path only (no FP64 path, e2e, CPU baseline, error check)")
+    return ap.parse_args()
+
+
+# ---- distributed plumbing (replicas: every rank evaluates its own mesh) -------------
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks --------------------------------------------------------------------------
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        # under load: samples drawing more than the median power
+        pw = sorted(r[2] for r in rows)
+        thr = pw[len(pw) // 2]
+        load = [r for r in rows if r[2] >= thr] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "reasons": reasons, "samples": len(rows)}
+
+
+# ---- workload --------------------------------------------------------------------------
+
+class Workload:
+    def __init__(self, n, device):
+        import torch
+
+        from paper_2107_04121_gb300 import fe, meshgen
+        self.fe, self.torch = fe, torch
+        self.mesh, self.lam, self.mu, self.u = meshgen.elasticity_q2_cube(n, seed=1)
+        self.E = self.mesh.n_elems
+        self.ctx = fe.Context(device)
+        self.coords = torch.from_numpy(self.mesh.coords).to(device)
+        self.conn = torch.from_numpy(self.mesh.conn).to(device)
+        self.m = fe.Mesh(self.coords, self.conn)
+        self.pts, self.w, self.phi, self.dphi = fe.refbasis_hex(2, 3)
+        self.geom = fe.geometry(self.ctx, self.m, self.phi, self.dphi, self.w)
+        self.form = fe.elasticity_form(fe.MAT_LAME)
+        self.mat = torch.from_numpy(np.stack([self.lam, self.mu], 1)).to(device)
+        self.u64 = torch.from_numpy(self.u).to(device)
+        self.u32 = self.u64.float()
+        self.asm = fe.assembly_create(self.ctx, self.m)
+        self.bufs = {}
+        self.ctx.check()
+
+    def outputs(self, prec):
+        torch = self.torch
+        f64 = prec == "f64"
+        if prec not in self.bufs:
+            dt = torch.float64 if f64 else torch.float32
+            self.bufs[prec] = (torch.empty((self.E, 81, 81), dtype=dt, device="cuda"),
+                               torch.empty((self.E, 81), dtype=dt, device="cuda"),
+                               torch.zeros(self.mesh.n_nodes * 3, dtype=dt, device="cuda"))
+        return self.bufs[prec]
+
+    def drop(self, prec):
+        self.bufs.pop(prec, None)
+        self.torch.cuda.empty_cache()
+
+    def step(self, prec, mk_events=None):
+        fe = self.fe
+        K, r, g = self.outputs(prec)
+        u = self.u64 if prec == "f64" else self.u32
+        self.geom.update()
+        if mk_events:
+            mk_events[0].record()
+        fe.eval_matrix(self.ctx, self.form, self.geom, [self.mat, None, None], prec, out=K)
+        if mk_events:
+            mk_events[1].record()
+        fe.eval_residual(self.ctx, self.form, self.geom, [self.mat, None, u], prec, out=r)
+        fe.assemble_vector(self.ctx, self.asm, 3, r, prec, out=g,
+                           flags=0 if prec == "f64" else fe.ASSEMBLE_COMPENSATED)
+
+
+KERNELS_PER_STEP = 4  # geometry, matrix, residual, assembly
+
+
+def timed_steps(wl, prec, steps, warmup, ws, flush):
+    """Per-step CUDA-event times (ms) and matrix-kernel times (ms); L2 flushed between steps."""
+    torch = wl.torch
+    for _ in range(warmup):
+        wl.step(prec)
+    wl.ctx.check()
+    barrier(ws)
+    torch.cuda.synchronize()
+    ev = []
+    for _ in range(steps):
+        flush.zero_()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record()
+        wl.step(prec, (e[1], e[2]))
+        e[3].record()
+        ev.append(e)
+    torch.cuda.synchronize()
+    barrier(ws)
+    wl.ctx.check()
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    mat_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    return step_ms, mat_ms
+
+
+def sampled_errors(wl, precs):
+    """Relative errors against the FP64 oracle on sampled elements (first, last, 62 random)."""
+    import oracle
+    from tests.parity import rel_matrix_error, rel_vector_error
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([[0, wl.E - 1], rng.choice(wl.E, 62, replace=False)]))
+    ref = oracle.RefElement(2, 3)
+    conn = wl.mesh.conn[idx]
+    wdetJ, G, _ = oracle.geometry(wl.mesh.coords, conn, ref)
+    D = oracle.lame_to_D(wl.lam[idx], wl.mu[idx])
+    Kref = oracle.matrix_elasticity(wdetJ, G, D)
+    rref = oracle.residual_elasticity(conn, wdetJ, G, D, wl.u)
+    out = {}
+    it = wl.torch.from_numpy(idx).cuda()
+    for p in precs:
+        K, r, _ = wl.outputs(p)
+        out["K_" + p] = rel_matrix_error(K[it].double().cpu().numpy(), Kref)
+        out["r_" + p] = rel_vector_error(r[it].double().cpu().numpy(), rref)
+    return out, len(idx)
+
+
+def e2e_measure(wl, prec, steps):
+    """Same step through the public API with host buffers: pinned H2D of the inputs
+    (coordinates, connectivity, materials, DOFs) and D2H of every result (K_e, r_e,
+    assembled vector), all inside the CUDA-event timed region."""
+    torch = wl.torch
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    h_in = [pin(wl.mesh.coords), pin(wl.mesh.conn), pin(np.stack([wl.lam, wl.mu], 1)),
+            pin(wl.u.astype(np.float32) if prec != "f64" else wl.u)]
+    u_dev = wl.u32 if prec != "f64" else wl.u64
+    d_in = [wl.coords, wl.conn, wl.mat, u_dev]
+    K, r, g = wl.outputs(prec)
+    h_out = [torch.empty(K.shape, dtype=K.dtype).pin_memory(), torch.empty(r.shape, dtype=r.dtype).pin_memory(),
+             torch.empty(g.shape, dtype=g.dtype).pin_memory()]
+    h2d = sum(t.numel() * t.element_size() for t in h_in)
+    d2h = sum(t.numel() * t.element_size() for t in h_out)
+
+    def one():
+        for d, h in zip(d_in, h_in):
+            d.copy_(h, non_blocking=True)
+        wl.step(prec)
+        for h, d in zip(h_out, (K, r, g)):
+            h.copy_(d, non_blocking=True)
+
+    one()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        one()
+    b.record()
+    b.synchronize()
+    wl.ctx.check()
+    ms = a.elapsed_time(b) / steps
+    return {"value": wl.E / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+# ---- CPU oracle (baseline / reference arm) ------------------------------------------------
+
+def oracle_step(mesh, lam, mu, u, n_elems):
+    """One oracle step (geometry, K_e, r_e, assembly) on the first n_elems elements."""
+    import oracle
+    ref = oracle.RefElement(2, 3)
+    conn = np.ascontiguousarray(mesh.conn[:n_elems])
+    wdetJ, G, _ = oracle.geometry(mesh.coords, conn, ref)
+    D = oracle.lame_to_D(lam[:n_elems], mu[:n_elems])
+    oracle.matrix_elasticity(wdetJ, G, D)
+    r = oracle.residual_elasticity(conn, wdetJ, G, D, u)
+    oracle.assemble(conn, r, mesh.n_nodes, 3)
+
+
+def cpu_baseline(n, sample):
+    import oracle
+    from paper_2107_04121_gb300 import meshgen
+    mesh, lam, mu, u = meshgen.elasticity_q2_cube(n, seed=1)
+    oracle_step(mesh, lam, mu, u, 64)
+    t = time.perf_counter()
+    oracle_step(mesh, lam, mu, u, sample)
+    dt = time.perf_counter() - t
+    return {"value": sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "first %d of %d elements, one full oracle step (FP64 geometry, K_e, r_e, assembly), "
+                      "%.1f s" % (sample, mesh.n_elems, dt)}
+
+
+def cpu_info():
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return model
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2107_04121_gb300 import meshgen
+    mesh, lam, mu, u = meshgen.elasticity_q2_cube(args.n, seed=1)
+    sample = min(4096, mesh.n_elems)
+    for _ in range(args.warmup):
+        oracle_step(mesh, lam, mu, u, 64)
+    ts = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle_step(mesh, lam, mu, u, sample)
+        ts.append(time.perf_counter() - t)
+    ms = 1e3 * sum(ts) / len(ts)
+    value = sample / (ms / 1e3)
+    cores = oracle.num_threads()
+    desc = ("first %d of %d elements per step, FP64 nested-loop oracle (geometry, K_e, r_e, assembly), "
+            "%d OpenMP threads, %s" % (sample, mesh.n_elems, cores, cpu_info()))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "Q2 linear elasticity, %d^3 hexes, K_e (81x81) + r_e + assembly" % args.n,
+                       "sample_elements": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- main ------------------------------------------------------------------------------------
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        # the oracle arm runs on rank 0's host cores only; other ranks exit at once
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")))
+        return
+    ws, rank, local = dist_setup(args)
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # the oracle's OpenMP threads must not compete with the timed GPU region:
+    # time the CPU baseline first (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.skip_extras:
+        cpu = cpu_baseline(args.n, min(32768, args.n ** 3))
+
+    wl = Workload(args.n, local)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    prec = args.prec
+    with ClockSampler(local) as clk:
+        step_ms, mat_ms = timed_steps(wl, prec, args.steps, args.warmup, ws, flush)
+    total_ms = max_over_ranks(sum(step_ms), ws)
+    ms_per_step = total_ms / args.steps
+    value = ws * wl.E * args.steps / (total_ms / 1e3)
+    mat_avg = sum(mat_ms) / len(mat_ms)
+    bytes_alg = wl.E * (MATRIX_BYTES_PER_ELEM_F64 if prec == "f64" else MATRIX_BYTES_PER_ELEM_F32)
+    achieved = bytes_alg / (mat_avg / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": prec, "data": "synthetic",
+        "config": {"workload": "Q2 linear elasticity, %d^3 = %d hexes (27 nodes, 27 Gauss points), "
+                               "+-0.15h interior perturbation seed 1, per-element Lame lambda~U[0.5,2], "
+                               "mu~U[0.2,1], u~N(0,1); step = FP64 geometry + K_e (81x81) + r_e + "
+                               "compensated assembly" % (args.n, wl.E),
+                   "elements": wl.E, "geometry_dtype": "f64", "contraction_dtype": prec,
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
+        "roofline": {"kernel": "k_matrix (fe_eval_matrix, %s)" % prec, "bound": "hbm", "achieved": achieved,
+                     "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
+                     "traffic": None, "bytes_per_elem": bytes_alg / wl.E, "avg_ms": mat_avg},
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
+    }
+    line["clocks"] = clk.summary()
+    if not args.skip_extras:
+        wl.drop(prec)
+        # plain FP64 path, same step
+        f64_steps = 3
+        s64, m64 = timed_steps(wl, "f64", f64_steps, 1, ws, flush)
+        t64 = max_over_ranks(sum(s64), ws)
+        line["fp64_path"] = {"value": ws * wl.E * f64_steps / (t64 / 1e3), "unit": UNIT,
+                             "ms_per_step": t64 / f64_steps, "matrix_ms": sum(m64) / len(m64)}
+        errs, nsamp = sampled_errors(wl, ["f64"])
+        wl.drop("f64")
+        wl.step(prec)
+        e2, _ = sampled_errors(wl, [prec])
+        errs.update(e2)
+        errs["sampled_elements"] = nsamp
+        line["rel_err"] = errs
+        line["speedup_vs_fp64_path"] = value / line["fp64_path"]["value"]
+        if rank == 0:
+            line["e2e"] = e2e_measure(wl, prec, 3)
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,266 @@
+/*
+ * fe.h - C ABI of the GB300 finite element weak-form evaluator (libfe.so).
+ *
+ * The library evaluates multilinear finite element weak forms element by
+ * element on one GPU, following Cimrman, "Fast Evaluation of Finite Element
+ * Weak Forms Using Python Tensor Contraction Packages" (arXiv 2107.04121):
+ *
+ *   fe_geometry         reference mapping J, det J, J^-1 per element and
+ *                       quadrature point (Sec. 4.1; operand "v.det" and the
+ *                       gradients "bfg" of Tab. suee)
+ *   fe_form_compile     a weak form written in the generalized einsum notation
+ *                       (Tab. wfc, examples in Tab. ewfd) compiled to a kernel
+ *                       plan, cached in a handle (Algorithm 3, "transpile")
+ *   fe_eval_matrix      element matrices M[c, :, :] (Algorithm 2, "matrix" mode)
+ *   fe_eval_residual    element residuals r[c, :] (Algorithm 1, "residual" mode)
+ *   fe_assemble_vector  optional scatter-add of element vectors into a global
+ *                       vector (the assembly step that Sec. 6 leaves untimed)
+ *
+ * General conventions
+ *  - Every array argument is caller-owned memory; the library never frees it.
+ *    "device" arrays must be CUDA device memory of the context's device;
+ *    "host" arrays are ordinary host memory.  All arrays are C row-major and
+ *    contiguous.
+ *  - Handles returned through an out-pointer are owned by the caller and are
+ *    released with the matching *_free / fe_destroy call.
+ *  - Calls that take a cudaStream_t are asynchronous on that stream (0 = the
+ *    legacy default stream).  Argument, shape and expression errors are
+ *    detected on the host and returned synchronously; nothing is launched then.
+ *  - Problems found on the device (det J <= 0, a non-finite geometry value)
+ *    are recorded in a device status word of the context and reported by
+ *    fe_get_status.  No call aborts, traps or throws across the ABI.
+ *  - Reference hexahedron [0,1]^3.  Order-p Lagrange nodes are equispaced and
+ *    numbered lexicographically with x fastest: node (i,j,k) is
+ *    i + (p+1) j + (p+1)^2 k.  Quadrature points use the same order.
+ *  - Vector element DOFs are component-major: local row/column index
+ *    comp * n_basis + node (the "cresf" output order of Sec. 5.3.3, eq. fe1b).
+ *    Global DOF vectors are node-major: index ncomp * node + comp.
+ *  - Symmetric tensors use Voigt order (11, 22, 33, 12, 13, 23) with
+ *    engineering shear strains (the "s(i:j)->I" storage of Tab. wfc).
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* cudaStream_t without pulling in the CUDA headers. */
+typedef struct CUstream_st *fe_stream_t;
+
+typedef enum {
+    FE_OK = 0,
+    FE_ERR_INVALID_ARG = 1,      /* null pointer, negative size, bad flag */
+    FE_ERR_SHAPE = 2,            /* sizes that do not fit together or are not supported */
+    FE_ERR_UNSUPPORTED_SPEC = 3, /* expression outside the implemented set of forms */
+    FE_ERR_NONPOSITIVE_DETJ = 4, /* device: det J <= 0 in some element */
+    FE_ERR_NONFINITE = 5,        /* device: a non-finite geometry value */
+    FE_ERR_OOM = 6,              /* device allocation failed */
+    FE_ERR_CUDA = 7,             /* other CUDA runtime error */
+    FE_ERR_TIMEOUT = 8           /* a bounded device wait gave up */
+} fe_status;
+
+/* Arithmetic of the contraction.  The geometry (J, det J, J^-1) is always
+ * computed in FP64.  FE_F64 takes and returns float64 arrays; every other
+ * precision takes float32 DOF vectors and returns float32 element arrays.
+ *   FE_F64    FP64 throughout
+ *   FE_F32    FP32 FMA contraction of FP64-derived geometry
+ *   FE_TF32X3 tensor cores, TF32 operands split hi + lo, three products, FP32 accumulation
+ *   FE_BF16X3 tensor cores, BF16 operands split hi + lo, three products, FP32 accumulation
+ *   FE_BF16   tensor cores, plain BF16 operands, FP32 accumulation (reported, not recovered) */
+typedef enum { FE_F64 = 0, FE_F32 = 1, FE_TF32X3 = 2, FE_BF16X3 = 3, FE_BF16 = 4 } fe_precision;
+
+/* Operand roles of a weak form (Sec. 5.1): test function, unknown field,
+ * known field, material data. */
+typedef enum { FE_VIRTUAL = 0, FE_STATE = 1, FE_PARAMETER = 2, FE_MATERIAL = 3 } fe_role;
+
+/* Layout of a material operand (device float64 array, "cq0" layout of Tab. mls
+ * with a constant q axis):
+ *   FE_MAT_SCALAR  (n_elems)       one coefficient per element
+ *   FE_MAT_LAME    (n_elems, 2)    Lame pair (lambda, mu) per element; the elastic
+ *                                  matrix is D = lambda m m^T + mu diag(2,2,2,1,1,1),
+ *                                  m = (1,1,1,0,0,0)
+ *   FE_MAT_D66     (n_elems, 6, 6) elastic matrix D per element, Voigt order */
+typedef enum { FE_MAT_NONE = 0, FE_MAT_SCALAR = 1, FE_MAT_LAME = 2, FE_MAT_D66 = 3 } fe_material_kind;
+
+typedef struct {
+    fe_role role;
+    int ncomp;                 /* components of a field operand (1 or 3); ignored for materials */
+    fe_material_kind material; /* layout of a material operand; FE_MAT_NONE for fields */
+} fe_operand;
+
+/* Mesh: device arrays, caller-owned, valid for as long as any handle made from
+ * them is used.  coords (n_nodes, 3) float64; conn (n_elems, nodes_per_elem)
+ * int32 indices into coords. */
+typedef struct {
+    const double *coords;
+    long long n_nodes;
+    const int32_t *conn;
+    long long n_elems;
+    int nodes_per_elem;
+} fe_mesh;
+
+/* Reference basis tabulated at the quadrature points: host arrays.
+ * phi (n_qp, n_basis), dphi (n_qp, 3, n_basis) with dphi[q][k][a] = d phi_a / d xi_k.
+ * The same basis maps the geometry and approximates the fields (isoparametric
+ * elements, Sec. 4.1 footnote). */
+typedef struct {
+    int n_basis;
+    int n_qp;
+    const double *phi;
+    const double *dphi;
+} fe_refbasis;
+
+/* Quadrature rule on the reference element: host arrays points (n_qp, 3), weights (n_qp). */
+typedef struct {
+    int n_qp;
+    const double *points;
+    const double *weights;
+} fe_quadrature;
+
+typedef struct fe_ctx fe_ctx;
+typedef struct fe_geometry_h fe_geometry_h;
+typedef struct fe_form_h fe_form_h;
+typedef struct fe_assembly_h fe_assembly_h;
+
+/* ---- context ------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (makes it current for the calling
+ * thread).  The context owns a device status word.  Errors: FE_ERR_INVALID_ARG
+ * (null out), FE_ERR_CUDA (no such device), FE_ERR_OOM. */
+fe_status fe_create(int device, fe_ctx **out);
+fe_status fe_destroy(fe_ctx *ctx);
+
+/* Static string naming a status code; never NULL. */
+const char *fe_status_str(fe_status s);
+
+/* Wait for `stream`, read and clear the device status word.  Returns FE_OK or
+ * the first device-detected error since the last call; *bad_elem (optional)
+ * receives the smallest offending element index, or -1. */
+fe_status fe_get_status(fe_ctx *ctx, fe_stream_t stream, long long *bad_elem);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fe_version(void);
+
+/* Text of the last CUDA error seen by a libfe call on the calling thread
+ * (empty if none).  Static thread-local storage; never NULL. */
+const char *fe_last_error_message(void);
+
+/* ---- reference element (host) ----------------------------------------------- */
+
+/* Tabulate the order-p Lagrange basis of the reference hexahedron and the
+ * tensor-product Gauss-Legendre rule with nq points per axis (Tab. cdc uses
+ * nq = p + 1).  Host arrays of sizes points (nq^3, 3), weights (nq^3),
+ * phi (nq^3, (p+1)^3), dphi (nq^3, 3, (p+1)^3).  Any output pointer may be
+ * NULL.  Supports 1 <= p <= 4, 1 <= nq <= 10; otherwise FE_ERR_SHAPE. */
+fe_status fe_refbasis_hex(int p, int nq, double *points, double *weights, double *phi, double *dphi);
+
+/* ---- geometry ----------------------------------------------------------------- */
+
+/* Storage flags of fe_geometry. */
+#define FE_GEOM_STORE_F64 1u /* keep float64 J^-1 and w det J (needed by FE_F64 evaluation) */
+#define FE_GEOM_STORE_F32 2u /* keep float32 copies (needed by the other precisions) */
+
+/* Geometry of the reference mapping (Sec. 4.1): for every element e and
+ * quadrature point q, J = sum_a x_a (x) grad_xi phi_a(q), det J, J^-1 and
+ * w_q det J, computed in FP64 on the device.  The handle keeps J^-1 (E, Q, 3, 3)
+ * and w det J (E, Q) in the precisions `flags` asks for (0 means both) together
+ * with device copies of the reference tables; the physical gradients
+ * G[e][q][j][a] = sum_k dphi[q][k][a] (J^-1)_kj are formed inside the
+ * evaluation kernels.  The mesh arrays are borrowed: they must stay valid while
+ * the handle is used.  Supported: hexahedra with n_basis in {8, 27, 64} and
+ * n_qp <= 64.  det J <= 0 is recorded in the status word (fe_get_status).
+ * Errors: FE_ERR_INVALID_ARG, FE_ERR_SHAPE, FE_ERR_OOM, FE_ERR_CUDA. */
+fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis, const fe_quadrature *quad,
+                      unsigned flags, fe_geometry_h **out, fe_stream_t stream);
+fe_status fe_geometry_free(fe_geometry_h *geom);
+
+/* Recompute the geometry of `geom` in place from the current contents of its
+ * (borrowed) mesh arrays, e.g. after the nodal coordinates moved; no device
+ * memory is allocated.  Same kernel and status reporting as fe_geometry.
+ * Errors: FE_ERR_INVALID_ARG, FE_ERR_CUDA. */
+fe_status fe_geometry_update(fe_ctx *ctx, fe_geometry_h *geom, fe_stream_t stream);
+
+/* What fe_geometry_get copies out. */
+typedef enum { FE_GEOM_WDETJ = 0, FE_GEOM_JINV = 1, FE_GEOM_G = 2 } fe_geom_field;
+
+/* Copy a geometry field into the caller's device array: w det J (E, Q),
+ * J^-1 (E, Q, 3, 3) or the physical gradients G (E, Q, 3, N), as float64
+ * (prec FE_F64) or float32 (any other prec), from the stored copy of that
+ * precision.  Errors: FE_ERR_INVALID_ARG (copy not stored, null pointers). */
+fe_status fe_geometry_get(fe_ctx *ctx, const fe_geometry_h *geom, fe_geom_field field, fe_precision prec,
+                          void *out, fe_stream_t stream);
+
+/* ---- forms ---------------------------------------------------------------------- */
+
+/* Compile a weak form given in the generalized einsum notation of Tab. wfc
+ * (symbols 0, i, i.j, i:j, s(i:j)->I), one comma-separated subscript per
+ * operand, with the operands' roles and layouts.  Recognised forms (Tab. ewfd;
+ * index letters are free, operands may come in any order):
+ *   weak Laplacian        "0.i,0.i"                    (VIRTUAL, STATE), ncomp 1
+ *   weighted Laplacian    "0,0.i,0.i"                  (MATERIAL SCALAR, VIRTUAL, STATE)
+ *   dot product / mass    "i,i" (ncomp 1 or 3), "0,0"  (VIRTUAL, STATE)
+ *   weighted mass         "0,i,i", "0,0,0"             (MATERIAL SCALAR, VIRTUAL, STATE)
+ *   linear elasticity     "IK,s(i:j)->I,s(k:l)->K"     (MATERIAL LAME or D66, VIRTUAL, STATE), ncomp 3
+ * `ctx` may be NULL: compilation is host-only.  The handle caches the plan
+ * (Sec. 5.1: transpilation results are cached).  Errors: FE_ERR_INVALID_ARG
+ * (syntax, roles, sizes), FE_ERR_UNSUPPORTED_SPEC (a valid expression with no
+ * kernel). */
+fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_operand *ops, int n_ops, fe_form_h **out);
+fe_status fe_form_free(fe_form_h *form);
+
+/* Rows and columns of one element matrix of `form` for elements of n_basis
+ * nodes: ncomp * n_basis each. */
+fe_status fe_form_shape(const fe_form_h *form, int n_basis, int *n_rows, int *n_cols);
+
+/* args[k] is the device array of operand k of the compiled expression:
+ *   FE_VIRTUAL            NULL (the test function is what the rows enumerate)
+ *   FE_STATE, FE_PARAMETER global DOF vector (n_nodes * ncomp), float64 for
+ *                         FE_F64 else float32; not read in matrix mode
+ *   FE_MATERIAL           float64 array in the operand's fe_material_kind layout
+ */
+
+/* Matrix mode (Algorithm 2): K_out[e][r][c] = derivative of the form with
+ * respect to the DOFs of operand `diff_op` (which must be the FE_STATE operand),
+ * integrated with the quadrature of `geom`; K_out is a device array
+ * (n_elems, n_rows, n_cols), float64 for FE_F64 else float32.
+ * Errors: FE_ERR_INVALID_ARG, FE_ERR_SHAPE, FE_ERR_UNSUPPORTED_SPEC (e.g. a
+ * precision without a kernel for this form), FE_ERR_CUDA. */
+fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const void *const *args,
+                         int diff_op, fe_precision prec, void *K_out, fe_stream_t stream);
+
+/* Residual mode (Algorithm 1): r_out[e][r] = the form's action on the DOF
+ * vector of the FE_STATE operand, whose element values are gathered through
+ * the mesh connectivity; r_out is a device array (n_elems, n_rows), float64
+ * for FE_F64 else float32.  FE_TF32X3/FE_BF16X3/FE_BF16 evaluate residuals
+ * with the FE_F32 kernels.  Errors as fe_eval_matrix. */
+fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const void *const *args,
+                           fe_precision prec, void *r_out, fe_stream_t stream);
+
+/* ---- assembly ------------------------------------------------------------------- */
+
+/* Build the node -> (element, local node) incidence lists of a mesh on the
+ * device (CSR, each list in ascending element order) so that assembly is a
+ * deterministic gather.  The mesh arrays are borrowed.  Errors:
+ * FE_ERR_INVALID_ARG, FE_ERR_SHAPE (an index outside [0, n_nodes) is reported
+ * here), FE_ERR_OOM, FE_ERR_CUDA.  This call synchronizes `stream`. */
+fe_status fe_assembly_create(fe_ctx *ctx, const fe_mesh *mesh, fe_assembly_h **out, fe_stream_t stream);
+fe_status fe_assembly_free(fe_assembly_h *asm_h);
+
+#define FE_ASSEMBLE_ACCUMULATE 1u  /* add into global_out instead of overwriting it */
+#define FE_ASSEMBLE_COMPENSATED 2u /* float32: Neumaier-compensated sums (ignored for FE_F64) */
+
+/* global_out[ncomp * conn[e][a] + i] (+)= sum over incidences of r_e[e][i * N + a],
+ * summed per node in ascending (e, a) order, so results are bit-reproducible.
+ * r_e (n_elems, ncomp * N) and global_out (n_nodes * ncomp) are device arrays,
+ * float64 for FE_F64 else float32.  ncomp in {1, 3}. */
+fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *asm_h, int ncomp, const void *r_e, fe_precision prec,
+                             void *global_out, unsigned flags, fe_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FE_H */

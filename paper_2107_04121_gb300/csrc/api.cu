@@ -1,0 +1,348 @@
+// C ABI of libfe (declarations and argument contracts in include/fe.h).
+// Host-side argument validation, handle management and kernel dispatch.
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "fe_internal.h"
+
+cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
+                                  void *K, int sm_count, cudaStream_t s);
+cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
+                                void *K, int sm_count, cudaStream_t s);
+
+namespace {
+
+thread_local char g_last_error[256] = "";
+
+fe_status from_cuda(cudaError_t e, const char *where)
+{
+    if (e == cudaSuccess) return FE_OK;
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", where, cudaGetErrorString(e));
+    cudaGetLastError();  // clear a non-sticky error
+    return e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA;
+}
+
+inline cudaStream_t to_cuda(fe_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+template <typename T>
+cudaError_t dev_alloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, sizeof(T) * count);
+}
+
+bool valid_mesh(const fe_mesh *m)
+{
+    // an empty mesh may come with null arrays (zero-size device tensors)
+    return m && (m->n_elems == 0 || (m->coords && m->conn)) && m->n_nodes >= 0 && m->n_elems >= 0 &&
+           m->nodes_per_elem > 0 && m->n_nodes <= INT_MAX && m->n_elems * (long long)m->nodes_per_elem <= INT_MAX;
+}
+
+void free_geometry(fe_geometry_h *g)
+{
+    if (!g) return;
+    cudaFree(g->d_phi64);
+    cudaFree(g->d_dphi64);
+    cudaFree(g->d_w64);
+    cudaFree(g->d_phi32);
+    cudaFree(g->d_dphi32);
+    cudaFree(g->d_jinv64);
+    cudaFree(g->d_wdetj64);
+    cudaFree(g->d_jinv32);
+    cudaFree(g->d_wdetj32);
+    delete g;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fe_version(void) { return 100; }
+
+const char *fe_last_error_message(void) { return g_last_error; }
+
+const char *fe_status_str(fe_status s)
+{
+    switch (s) {
+    case FE_OK: return "FE_OK";
+    case FE_ERR_INVALID_ARG: return "FE_ERR_INVALID_ARG";
+    case FE_ERR_SHAPE: return "FE_ERR_SHAPE";
+    case FE_ERR_UNSUPPORTED_SPEC: return "FE_ERR_UNSUPPORTED_SPEC";
+    case FE_ERR_NONPOSITIVE_DETJ: return "FE_ERR_NONPOSITIVE_DETJ";
+    case FE_ERR_NONFINITE: return "FE_ERR_NONFINITE";
+    case FE_ERR_OOM: return "FE_ERR_OOM";
+    case FE_ERR_CUDA: return "FE_ERR_CUDA";
+    case FE_ERR_TIMEOUT: return "FE_ERR_TIMEOUT";
+    }
+    return "FE_ERR_UNKNOWN";
+}
+
+fe_status fe_create(int device, fe_ctx **out)
+{
+    if (!out) return FE_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        std::snprintf(g_last_error, sizeof(g_last_error), "fe_create: no CUDA device %d", device);
+        return FE_ERR_CUDA;
+    }
+    fe_status st = from_cuda(cudaSetDevice(device), "cudaSetDevice");
+    if (st) return st;
+    fe_ctx *c = new (std::nothrow) fe_ctx();
+    if (!c) return FE_ERR_OOM;
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    st = from_cuda(dev_alloc(&c->d_status, 2), "cudaMalloc(status)");
+    if (st) {
+        delete c;
+        return st;
+    }
+    const unsigned long long init[2] = {0ull, ULLONG_MAX};
+    st = from_cuda(cudaMemcpy(c->d_status, init, sizeof(init), cudaMemcpyHostToDevice), "status init");
+    if (st) {
+        cudaFree(c->d_status);
+        delete c;
+        return st;
+    }
+    *out = c;
+    return FE_OK;
+}
+
+fe_status fe_destroy(fe_ctx *ctx)
+{
+    if (!ctx) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaFree(ctx->d_status);
+    delete ctx;
+    return FE_OK;
+}
+
+fe_status fe_get_status(fe_ctx *ctx, fe_stream_t stream, long long *bad_elem)
+{
+    if (!ctx) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    fe_status st = from_cuda(cudaStreamSynchronize(to_cuda(stream)), "fe_get_status sync");
+    if (st) return st;
+    unsigned long long h[2];
+    st = from_cuda(cudaMemcpy(h, ctx->d_status, sizeof(h), cudaMemcpyDeviceToHost), "fe_get_status read");
+    if (st) return st;
+    const unsigned long long init[2] = {0ull, ULLONG_MAX};
+    st = from_cuda(cudaMemcpy(ctx->d_status, init, sizeof(init), cudaMemcpyHostToDevice), "fe_get_status reset");
+    if (st) return st;
+    if (bad_elem) *bad_elem = h[1] == ULLONG_MAX ? -1 : (long long)h[1];
+    return (fe_status)h[0];
+}
+
+// ---- geometry -----------------------------------------------------------------
+
+fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis, const fe_quadrature *quad,
+                      unsigned flags, fe_geometry_h **out, fe_stream_t stream)
+{
+    if (!ctx || !out || !valid_mesh(mesh) || !basis || !quad || !basis->phi || !basis->dphi || !quad->weights)
+        return FE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (flags & ~(FE_GEOM_STORE_F64 | FE_GEOM_STORE_F32)) return FE_ERR_INVALID_ARG;
+    if (flags == 0) flags = FE_GEOM_STORE_F64 | FE_GEOM_STORE_F32;
+    const int N = basis->n_basis, Q = basis->n_qp;
+    if (N != mesh->nodes_per_elem || quad->n_qp != Q || !fe_supported_nq(N, Q)) return FE_ERR_SHAPE;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = to_cuda(stream);
+    fe_geometry_h *g = new (std::nothrow) fe_geometry_h();
+    if (!g) return FE_ERR_OOM;
+    g->device = ctx->device;
+    g->mesh = *mesh;
+    g->N = N;
+    g->Q = Q;
+    g->flags = flags;
+    const long long E = mesh->n_elems;
+    std::vector<float> phi32((size_t)Q * N), dphi32((size_t)Q * 3 * N);
+    for (size_t i = 0; i < phi32.size(); ++i) phi32[i] = (float)basis->phi[i];
+    for (size_t i = 0; i < dphi32.size(); ++i) dphi32[i] = (float)basis->dphi[i];
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dev_alloc(&g->d_phi64, (size_t)Q * N);
+    if (e == cudaSuccess) e = dev_alloc(&g->d_dphi64, (size_t)Q * 3 * N);
+    if (e == cudaSuccess) e = dev_alloc(&g->d_w64, (size_t)Q);
+    if (e == cudaSuccess) e = dev_alloc(&g->d_phi32, (size_t)Q * N);
+    if (e == cudaSuccess) e = dev_alloc(&g->d_dphi32, (size_t)Q * 3 * N);
+    if (e == cudaSuccess && (flags & FE_GEOM_STORE_F64)) {
+        e = dev_alloc(&g->d_jinv64, (size_t)E * Q * 9);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_wdetj64, (size_t)E * Q);
+    }
+    if (e == cudaSuccess && (flags & FE_GEOM_STORE_F32)) {
+        e = dev_alloc(&g->d_jinv32, (size_t)E * Q * 9);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_wdetj32, (size_t)E * Q);
+    }
+    // the tables are tiny; synchronous copies keep the host buffers' lifetime simple
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_phi64, basis->phi, sizeof(double) * Q * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_dphi64, basis->dphi, sizeof(double) * Q * 3 * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_w64, quad->weights, sizeof(double) * Q, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->d_phi32, phi32.data(), sizeof(float) * Q * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->d_dphi32, dphi32.data(), sizeof(float) * Q * 3 * N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = fe_launch_geometry(g, ctx->d_status, s);
+    if (e != cudaSuccess) {
+        fe_status st = from_cuda(e, "fe_geometry");
+        free_geometry(g);
+        return st;
+    }
+    *out = g;
+    return FE_OK;
+}
+
+fe_status fe_geometry_update(fe_ctx *ctx, fe_geometry_h *geom, fe_stream_t stream)
+{
+    if (!ctx || !geom) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    return from_cuda(fe_launch_geometry(geom, ctx->d_status, to_cuda(stream)), "fe_geometry_update");
+}
+
+fe_status fe_geometry_free(fe_geometry_h *geom)
+{
+    if (!geom) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(geom->device);
+    free_geometry(geom);
+    return FE_OK;
+}
+
+fe_status fe_geometry_get(fe_ctx *ctx, const fe_geometry_h *g, fe_geom_field field, fe_precision prec, void *out,
+                          fe_stream_t stream)
+{
+    if (!ctx || !g || (!out && g->mesh.n_elems > 0)) return FE_ERR_INVALID_ARG;
+    const bool f64 = prec == FE_F64;
+    if (f64 ? !g->d_jinv64 : !g->d_jinv32) return FE_ERR_INVALID_ARG;
+    if (g->mesh.n_elems == 0) return FE_OK;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = to_cuda(stream);
+    const size_t es = f64 ? 8 : 4;
+    const long long E = g->mesh.n_elems;
+    cudaError_t e;
+    switch (field) {
+    case FE_GEOM_WDETJ:
+        e = cudaMemcpyAsync(out, f64 ? (const void *)g->d_wdetj64 : (const void *)g->d_wdetj32, es * E * g->Q,
+                            cudaMemcpyDeviceToDevice, s);
+        break;
+    case FE_GEOM_JINV:
+        e = cudaMemcpyAsync(out, f64 ? (const void *)g->d_jinv64 : (const void *)g->d_jinv32, es * E * g->Q * 9,
+                            cudaMemcpyDeviceToDevice, s);
+        break;
+    case FE_GEOM_G: e = fe_launch_geometry_G(g, f64, out, s); break;
+    default: return FE_ERR_INVALID_ARG;
+    }
+    return from_cuda(e, "fe_geometry_get");
+}
+
+// ---- evaluation ------------------------------------------------------------------
+
+static fe_status eval_common(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const void *const *args,
+                             fe_precision prec, void *out, fe_material_args *mat)
+{
+    const bool empty = g && g->mesh.n_elems == 0;
+    if (!ctx || !form || !g || (!out && !empty)) return FE_ERR_INVALID_ARG;
+    if (prec < FE_F64 || prec > FE_BF16) return FE_ERR_INVALID_ARG;
+    if (form->mat_op >= 0) {
+        if (!args || (!args[form->mat_op] && !empty)) return FE_ERR_INVALID_ARG;
+        mat->kind = form->mat;
+        mat->data = (const double *)args[form->mat_op];
+        mat->transposed = form->mat_transposed;
+    } else {
+        mat->kind = FE_MAT_NONE;
+        mat->data = nullptr;
+        mat->transposed = 0;
+    }
+    const bool f64 = prec == FE_F64;
+    if (f64 ? !g->d_jinv64 : !g->d_jinv32) return FE_ERR_INVALID_ARG;  // geometry copy not stored
+    cudaSetDevice(ctx->device);
+    return FE_OK;
+}
+
+fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const void *const *args,
+                         int diff_op, fe_precision prec, void *K_out, fe_stream_t stream)
+{
+    fe_material_args mat{};
+    fe_status st = eval_common(ctx, form, g, args, prec, K_out, &mat);
+    if (st) return st;
+    if (diff_op != form->state_op) return FE_ERR_INVALID_ARG;
+    cudaError_t e;
+    if (prec == FE_F64 || prec == FE_F32) {
+        e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, to_cuda(stream));
+    } else {
+        if (form->kind != FK_ELASTICITY || !(g->N == 27 && g->Q == 27)) return FE_ERR_UNSUPPORTED_SPEC;
+        e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, to_cuda(stream));
+    }
+    return from_cuda(e, "fe_eval_matrix");
+}
+
+fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const void *const *args,
+                           fe_precision prec, void *r_out, fe_stream_t stream)
+{
+    fe_material_args mat{};
+    fe_status st = eval_common(ctx, form, g, args, prec, r_out, &mat);
+    if (st) return st;
+    if (!args || (!args[form->state_op] && g->mesh.n_elems > 0)) return FE_ERR_INVALID_ARG;
+    cudaError_t e = fe_launch_residual(g, form, mat, prec == FE_F64, args[form->state_op], r_out, ctx->d_status,
+                                       to_cuda(stream));
+    return from_cuda(e, "fe_eval_residual");
+}
+
+// ---- assembly -----------------------------------------------------------------------
+
+fe_status fe_assembly_create(fe_ctx *ctx, const fe_mesh *mesh, fe_assembly_h **out, fe_stream_t stream)
+{
+    if (!ctx || !out || !valid_mesh(mesh)) return FE_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = to_cuda(stream);
+    fe_assembly_h *a = new (std::nothrow) fe_assembly_h();
+    if (!a) return FE_ERR_OOM;
+    a->device = ctx->device;
+    a->mesh = *mesh;
+    int *d_flag = nullptr;
+    cudaError_t e = dev_alloc(&a->d_offsets, (size_t)mesh->n_nodes + 1);
+    if (e == cudaSuccess) e = dev_alloc(&a->d_entries, (size_t)(mesh->n_elems * mesh->nodes_per_elem));
+    if (e == cudaSuccess) e = dev_alloc(&d_flag, 1);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = fe_launch_assembly_build(a, d_flag, s);
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_flag);
+    if (e != cudaSuccess || flag) {
+        fe_status st = e != cudaSuccess ? from_cuda(e, "fe_assembly_create") : FE_ERR_SHAPE;
+        if (flag) std::snprintf(g_last_error, sizeof(g_last_error), "fe_assembly_create: node index out of range");
+        cudaFree(a->d_offsets);
+        cudaFree(a->d_entries);
+        delete a;
+        return st;
+    }
+    *out = a;
+    return FE_OK;
+}
+
+fe_status fe_assembly_free(fe_assembly_h *a)
+{
+    if (!a) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(a->device);
+    cudaFree(a->d_offsets);
+    cudaFree(a->d_entries);
+    delete a;
+    return FE_OK;
+}
+
+fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *a, int ncomp, const void *r_e, fe_precision prec,
+                             void *global_out, unsigned flags, fe_stream_t stream)
+{
+    if (!ctx || !a || (ncomp != 1 && ncomp != 3)) return FE_ERR_INVALID_ARG;
+    if ((!r_e && a->mesh.n_elems > 0) || (!global_out && a->mesh.n_nodes > 0)) return FE_ERR_INVALID_ARG;
+    if (flags & ~(FE_ASSEMBLE_ACCUMULATE | FE_ASSEMBLE_COMPENSATED)) return FE_ERR_INVALID_ARG;
+    if (prec < FE_F64 || prec > FE_BF16) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    return from_cuda(fe_launch_assemble(a, ncomp, prec == FE_F64, r_e, global_out, flags, to_cuda(stream)),
+                     "fe_assemble_vector");
+}
+
+}  // extern "C"

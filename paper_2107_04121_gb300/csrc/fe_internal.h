@@ -1,0 +1,75 @@
+// Internal declarations of libfe: handle layouts, kernel launchers, status word.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fe.h"
+
+// ---------------------------------------------------------------------------
+// Device status word: [0] first error code (0 = none), [1] smallest offending
+// element index (ULLONG_MAX = none).  Kernels only ever atomically lower or
+// set it; fe_get_status reads and resets it.
+struct fe_ctx {
+    int device;
+    int sm_count;
+    unsigned long long *d_status;  // 2 words
+};
+
+// Geometry handle: FP64-derived reference-mapping data, element-outermost so
+// that a CTA working on consecutive elements reads one contiguous block.
+struct fe_geometry_h {
+    int device;
+    fe_mesh mesh;  // borrowed device pointers
+    int N, Q;
+    unsigned flags;
+    double *d_phi64, *d_dphi64, *d_w64;  // (Q,N), (Q,3,N), (Q)
+    float *d_phi32, *d_dphi32;
+    double *d_jinv64, *d_wdetj64;  // (E,Q,3,3), (E,Q)
+    float *d_jinv32, *d_wdetj32;
+};
+
+enum fe_form_kind { FK_LAPLACE = 0, FK_MASS = 1, FK_ELASTICITY = 2 };
+
+struct fe_form_h {
+    fe_form_kind kind;
+    int ncomp;       // components of the field operands
+    int n_ops;
+    int virtual_op;  // operand index of the test function
+    int state_op;    // operand index of the unknown
+    int mat_op;      // operand index of the material, -1 if none
+    fe_material_kind mat;
+    int mat_transposed;  // elasticity: material indices given as (u-index, v-index)
+};
+
+struct fe_assembly_h {
+    int device;
+    fe_mesh mesh;
+    int *d_offsets;  // (n_nodes + 1)
+    int *d_entries;  // (n_elems * N): e * N + a, ascending per node
+};
+
+// Materials handed to the kernels: always float64 device arrays.
+struct fe_material_args {
+    fe_material_kind kind;
+    const double *data;
+    int transposed;
+};
+
+// ---------------------------------------------------------------------------
+// Launchers (return cudaError_t of the launch; argument checks done by the API).
+cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *d_status, cudaStream_t s);
+cudaError_t fe_launch_geometry_G(const fe_geometry_h *g, bool f64, void *out, cudaStream_t s);
+cudaError_t fe_launch_matrix(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
+                             void *K, int sm_count, cudaStream_t s);
+cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
+                               const void *u, void *r, unsigned long long *status, cudaStream_t s);
+cudaError_t fe_launch_assembly_build(fe_assembly_h *a, int *d_flag, cudaStream_t s);
+cudaError_t fe_launch_assemble(const fe_assembly_h *a, int ncomp, bool f64, const void *r, void *out,
+                               unsigned flags, cudaStream_t s);
+
+// Which (N, Q) pairs have kernels.
+bool fe_supported_nq(int N, int Q);
+
+// Host reference element (refelem.cpp).
+int fe_host_gauss_legendre01(int n, double *x, double *w);

@@ -1,0 +1,152 @@
+// Assembly of element vectors into a global DOF vector (the step after
+// Algorithm 1 of Cimrman, arXiv 2107.04121, which Sec. 6 leaves untimed):
+//   g[ncomp * conn[e][a] + i] += r[e][i * N + a].
+//
+// Assembly is done as a gather, not a scatter: the node -> (e, a) incidence
+// lists (CSR, ascending element order) are built once per mesh, then one
+// thread per global DOF sums its contributions in that fixed order.  No
+// floating-point atomics: the result is bit-reproducible and, in FP64, equal to
+// a sequential ascending-(e, a) sum.  FP32 sums may be Neumaier-compensated.
+#include <cub/device/device_scan.cuh>
+
+#include "fe_device.cuh"
+
+namespace {
+
+__global__ void k_count(const int32_t *__restrict__ conn, long long total, long long n_nodes, int *cnt, int *flag)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long node = conn[i];
+        if (node < 0 || node >= n_nodes)
+            atomicExch(flag, 1);
+        else
+            atomicAdd(cnt + node, 1);
+    }
+}
+
+__global__ void k_fill(const int32_t *__restrict__ conn, long long total, long long n_nodes,
+                       const int *__restrict__ offsets, int *cursor, int *entries)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long node = conn[i];
+        if (node < 0 || node >= n_nodes) continue;
+        const int pos = offsets[node] + atomicAdd(cursor + node, 1);
+        entries[pos] = (int)i;
+    }
+}
+
+// Sort each incidence list ascending (lists are short: <= 8 for hex vertices).
+__global__ void k_sort(const int *__restrict__ offsets, long long n_nodes, int *entries)
+{
+    for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < n_nodes;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int b = offsets[n], e = offsets[n + 1];
+        for (int i = b + 1; i < e; ++i) {
+            const int v = entries[i];
+            int j = i - 1;
+            while (j >= b && entries[j] > v) {
+                entries[j + 1] = entries[j];
+                --j;
+            }
+            entries[j + 1] = v;
+        }
+    }
+}
+
+template <typename T, bool COMPENSATED>
+__global__ void k_gather(const int *__restrict__ offsets, const int *__restrict__ entries, long long n_nodes,
+                         int N, int ncomp, const T *__restrict__ r, T *__restrict__ out, bool accumulate)
+{
+    const long long total = n_nodes * ncomp;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const long long node = idx / ncomp;
+        const int comp = (int)(idx - node * ncomp);
+        const int b = offsets[node], e = offsets[node + 1];
+        T s = accumulate ? out[idx] : (T)0;
+        T c = 0;
+        for (int p = b; p < e; ++p) {
+            const int ent = entries[p];
+            const int el = ent / N, a = ent - el * N;
+            const T x = r[(long long)el * ncomp * N + comp * N + a];
+            if (COMPENSATED) {
+                // Neumaier: keep the rounding error of every addition in c
+                const T t = s + x;
+                if (fabs(s) >= fabs(x))
+                    c += (s - t) + x;
+                else
+                    c += (x - t) + s;
+                s = t;
+            } else {
+                s += x;
+            }
+        }
+        out[idx] = COMPENSATED ? s + c : s;
+    }
+}
+
+unsigned grid_for(long long n, int threads)
+{
+    long long b = (n + threads - 1) / threads;
+    if (b > 1048576) b = 1048576;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+// Builds a->d_offsets / a->d_entries; *d_flag is set to 1 on an out-of-range
+// node index.  Temporary buffers are stream-ordered allocations.
+cudaError_t fe_launch_assembly_build(fe_assembly_h *a, int *d_flag, cudaStream_t s)
+{
+    const long long n_nodes = a->mesh.n_nodes, total = a->mesh.n_elems * a->mesh.nodes_per_elem;
+    int *cnt = nullptr;
+    void *tmp = nullptr;
+    size_t tmp_bytes = 0;
+    cudaError_t err = cudaMallocAsync((void **)&cnt, sizeof(int) * (n_nodes + 1), s);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(cnt, 0, sizeof(int) * (n_nodes + 1), s);
+    if (err == cudaSuccess && total > 0) {
+        k_count<<<grid_for(total, 256), 256, 0, s>>>(a->mesh.conn, total, n_nodes, cnt, d_flag);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess)
+        err = cub::DeviceScan::ExclusiveSum(nullptr, tmp_bytes, cnt, a->d_offsets, (int)(n_nodes + 1), s);
+    if (err == cudaSuccess) err = cudaMallocAsync(&tmp, tmp_bytes > 0 ? tmp_bytes : 16, s);
+    if (err == cudaSuccess)
+        err = cub::DeviceScan::ExclusiveSum(tmp, tmp_bytes, cnt, a->d_offsets, (int)(n_nodes + 1), s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(cnt, 0, sizeof(int) * (n_nodes + 1), s);
+    if (err == cudaSuccess && total > 0) {
+        k_fill<<<grid_for(total, 256), 256, 0, s>>>(a->mesh.conn, total, n_nodes, a->d_offsets, cnt, a->d_entries);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess && n_nodes > 0) {
+        k_sort<<<grid_for(n_nodes, 256), 256, 0, s>>>(a->d_offsets, n_nodes, a->d_entries);
+        err = cudaGetLastError();
+    }
+    if (tmp) cudaFreeAsync(tmp, s);
+    cudaFreeAsync(cnt, s);
+    return err;
+}
+
+cudaError_t fe_launch_assemble(const fe_assembly_h *a, int ncomp, bool f64, const void *r, void *out,
+                               unsigned flags, cudaStream_t s)
+{
+    const long long total = a->mesh.n_nodes * ncomp;
+    if (total == 0) return cudaSuccess;
+    const bool acc = flags & FE_ASSEMBLE_ACCUMULATE;
+    const int N = a->mesh.nodes_per_elem;
+    const unsigned grid = grid_for(total, 256);
+    if (f64)
+        k_gather<double, false><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, a->mesh.n_nodes, N, ncomp,
+                                                     (const double *)r, (double *)out, acc);
+    else if (flags & FE_ASSEMBLE_COMPENSATED)
+        k_gather<float, true><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, a->mesh.n_nodes, N, ncomp,
+                                                   (const float *)r, (float *)out, acc);
+    else
+        k_gather<float, false><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, a->mesh.n_nodes, N, ncomp,
+                                                    (const float *)r, (float *)out, acc);
+    return cudaGetLastError();
+}

@@ -1,0 +1,131 @@
+// Reference hexahedron of libfe: order-p Lagrange basis and tensor Gauss rules,
+// tabulated on the host (the isoparametric basis of Sec. 4.1 of Cimrman,
+// arXiv 2107.04121; (p+1)^3 Gauss points per Tab. cdc).
+//
+// The Gauss-Legendre rule is computed by the Golub-Welsch method: the nodes are
+// the eigenvalues of the symmetric tridiagonal Jacobi matrix of the Legendre
+// recurrence (off-diagonal k / sqrt(4k^2 - 1)), the weights are 2 v_0^2 of the
+// normalised eigenvectors.  The eigenproblem is solved with cyclic Jacobi
+// rotations, which is plenty for n <= 10.
+#include <cmath>
+#include <cstring>
+
+#include "fe_internal.h"
+
+int fe_host_gauss_legendre01(int n, double *x, double *w)
+{
+    if (n < 1 || n > 16) return -1;
+    double A[16][16] = {{0}}, V[16][16] = {{0}};
+    for (int i = 0; i < n; ++i) V[i][i] = 1.0;
+    for (int k = 1; k < n; ++k) {
+        double b = k / std::sqrt(4.0 * k * k - 1.0);
+        A[k - 1][k] = A[k][k - 1] = b;
+    }
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = i + 1; j < n; ++j) off += A[i][j] * A[i][j];
+        if (off < 1e-34) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                if (A[p][q] == 0.0) continue;
+                // rotation that annihilates A[p][q]
+                double theta = (A[q][q] - A[p][p]) / (2.0 * A[p][q]);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // A <- A R
+                    double akp = A[k][p], akq = A[k][q];
+                    A[k][p] = c * akp - s * akq;
+                    A[k][q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // A <- R^T A
+                    double apk = A[p][k], aqk = A[q][k];
+                    A[p][k] = c * apk - s * aqk;
+                    A[q][k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {  // V <- V R
+                    double vkp = V[k][p], vkq = V[k][q];
+                    V[k][p] = c * vkp - s * vkq;
+                    V[k][q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    // sort eigenpairs ascending
+    int idx[16];
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    for (int i = 1; i < n; ++i)
+        for (int j = i; j > 0 && A[idx[j]][idx[j]] < A[idx[j - 1]][idx[j - 1]]; --j) {
+            int t = idx[j];
+            idx[j] = idx[j - 1];
+            idx[j - 1] = t;
+        }
+    for (int i = 0; i < n; ++i) {
+        int k = idx[i];
+        double v0 = V[0][k];
+        double nrm = 0.0;
+        for (int r = 0; r < n; ++r) nrm += V[r][k] * V[r][k];
+        x[i] = 0.5 * (A[k][k] + 1.0);
+        w[i] = v0 * v0 / nrm;  // 2 v0^2 on [-1,1], halved on [0,1]
+    }
+    // symmetric rule: enforce exact symmetry of points and weights
+    for (int i = 0; i < n / 2; ++i) {
+        double xm = 0.5 * (x[i] + (1.0 - x[n - 1 - i]));
+        double wm = 0.5 * (w[i] + w[n - 1 - i]);
+        x[i] = xm;
+        x[n - 1 - i] = 1.0 - xm;
+        w[i] = w[n - 1 - i] = wm;
+    }
+    if (n % 2) x[n / 2] = 0.5;
+    return 0;
+}
+
+// Lagrange polynomial k of the equispaced nodes {m/p} and its derivative at t.
+static void lagrange1d(int p, int k, double t, double *val, double *der)
+{
+    double tk = (double)k / p;
+    double v = 1.0, d = 0.0;
+    for (int m = 0; m <= p; ++m) {
+        if (m == k) continue;
+        double f = (t - (double)m / p) / (tk - (double)m / p);
+        double df = 1.0 / (tk - (double)m / p);
+        d = d * f + v * df;  // (v f)' = v' f + v f'
+        v = v * f;
+    }
+    *val = v;
+    *der = d;
+}
+
+extern "C" fe_status fe_refbasis_hex(int p, int nq, double *points, double *weights, double *phi, double *dphi)
+{
+    if (p < 1 || p > 4 || nq < 1 || nq > 10) return FE_ERR_SHAPE;
+    double g[16], gw[16];
+    if (fe_host_gauss_legendre01(nq, g, gw)) return FE_ERR_SHAPE;
+    const int n1 = p + 1, N = n1 * n1 * n1, Q = nq * nq * nq;
+    double L[10][5], dL[10][5];
+    for (int q = 0; q < nq; ++q)
+        for (int k = 0; k < n1; ++k) lagrange1d(p, k, g[q], &L[q][k], &dL[q][k]);
+    for (int qz = 0; qz < nq; ++qz)
+        for (int qy = 0; qy < nq; ++qy)
+            for (int qx = 0; qx < nq; ++qx) {
+                const int q = qx + nq * (qy + nq * qz);
+                if (points) {
+                    points[3 * q + 0] = g[qx];
+                    points[3 * q + 1] = g[qy];
+                    points[3 * q + 2] = g[qz];
+                }
+                if (weights) weights[q] = gw[qx] * gw[qy] * gw[qz];
+                for (int k = 0; k < n1; ++k)
+                    for (int j = 0; j < n1; ++j)
+                        for (int i = 0; i < n1; ++i) {
+                            const int a = i + n1 * (j + n1 * k);
+                            if (phi) phi[(size_t)q * N + a] = L[qx][i] * L[qy][j] * L[qz][k];
+                            if (dphi) {
+                                dphi[((size_t)q * 3 + 0) * N + a] = dL[qx][i] * L[qy][j] * L[qz][k];
+                                dphi[((size_t)q * 3 + 1) * N + a] = L[qx][i] * dL[qy][j] * L[qz][k];
+                                dphi[((size_t)q * 3 + 2) * N + a] = L[qx][i] * L[qy][j] * dL[qz][k];
+                            }
+                        }
+            }
+    (void)Q;
+    return FE_OK;
+}

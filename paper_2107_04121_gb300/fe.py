@@ -1,0 +1,404 @@
+"""Thin ctypes binding of libfe (include/fe.h): argument marshalling only.
+
+Device arrays are torch CUDA tensors (PyTorch supplies memory and streams);
+every step of the evaluation runs in the library's CUDA kernels.  There is no
+CPU fallback: if libfe.so is missing or no GPU is present, calls fail loudly.
+
+The names follow the C ABI: geometry (fe_geometry), form_compile
+(fe_form_compile), eval_matrix (fe_eval_matrix), eval_residual
+(fe_eval_residual), assembly_create / assemble_vector (fe_assemble_vector).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfe.so")
+
+# ---- enums (mirror include/fe.h) -------------------------------------------------
+FE_OK, FE_ERR_INVALID_ARG, FE_ERR_SHAPE, FE_ERR_UNSUPPORTED_SPEC = 0, 1, 2, 3
+FE_ERR_NONPOSITIVE_DETJ, FE_ERR_NONFINITE, FE_ERR_OOM, FE_ERR_CUDA, FE_ERR_TIMEOUT = 4, 5, 6, 7, 8
+F64, F32, TF32X3, BF16X3, BF16 = 0, 1, 2, 3, 4
+PRECISIONS = {"f64": F64, "f32": F32, "tf32x3": TF32X3, "bf16x3": BF16X3, "bf16": BF16}
+VIRTUAL, STATE, PARAMETER, MATERIAL = 0, 1, 2, 3
+MAT_NONE, MAT_SCALAR, MAT_LAME, MAT_D66 = 0, 1, 2, 3
+GEOM_STORE_F64, GEOM_STORE_F32 = 1, 2
+GEOM_WDETJ, GEOM_JINV, GEOM_G = 0, 1, 2
+ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
+
+EXPORTED = [
+    "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
+    "fe_refbasis_hex", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
+    "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_assembly_create", "fe_assembly_free",
+    "fe_assemble_vector",
+]
+
+
+class FEError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        lib = _lib
+        name = lib.fe_status_str(status).decode() if lib else str(status)
+        msg = lib.fe_last_error_message().decode() if lib else ""
+        super().__init__("%s failed: %s%s" % (where, name, (" (" + msg + ")") if msg else ""))
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("coords", ctypes.c_void_p), ("n_nodes", ctypes.c_longlong), ("conn", ctypes.c_void_p),
+                ("n_elems", ctypes.c_longlong), ("nodes_per_elem", ctypes.c_int)]
+
+
+class _RefBasis(ctypes.Structure):
+    _fields_ = [("n_basis", ctypes.c_int), ("n_qp", ctypes.c_int), ("phi", ctypes.c_void_p),
+                ("dphi", ctypes.c_void_p)]
+
+
+class _Quad(ctypes.Structure):
+    _fields_ = [("n_qp", ctypes.c_int), ("points", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
+
+
+class _Operand(ctypes.Structure):
+    _fields_ = [("role", ctypes.c_int), ("ncomp", ctypes.c_int), ("material", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libfe.so (built by paper_2107_04121_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libfe.so not found at %s: run `python -m paper_2107_04121_gb300.build` "
+                          "(there is no CPU fallback)" % path)
+    L = ctypes.CDLL(path)
+    vp, i, ll, st = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong, ctypes.c_int
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.fe_create.argtypes = [i, ctypes.POINTER(vp)]
+    L.fe_destroy.argtypes = [vp]
+    L.fe_status_str.argtypes = [st]
+    L.fe_status_str.restype = ctypes.c_char_p
+    L.fe_last_error_message.restype = ctypes.c_char_p
+    L.fe_get_status.argtypes = [vp, vp, ctypes.POINTER(ll)]
+    L.fe_refbasis_hex.argtypes = [i, i, dp, dp, dp, dp]
+    L.fe_geometry.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(_RefBasis), ctypes.POINTER(_Quad),
+                              ctypes.c_uint, ctypes.POINTER(vp), vp]
+    L.fe_geometry_update.argtypes = [vp, vp, vp]
+    L.fe_geometry_free.argtypes = [vp]
+    L.fe_geometry_get.argtypes = [vp, vp, i, i, vp, vp]
+    L.fe_form_compile.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(_Operand), i, ctypes.POINTER(vp)]
+    L.fe_form_free.argtypes = [vp]
+    L.fe_form_shape.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.fe_eval_matrix.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, i, vp, vp]
+    L.fe_eval_residual.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, vp, vp]
+    L.fe_assembly_create.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(vp), vp]
+    L.fe_assembly_free.argtypes = [vp]
+    L.fe_assemble_vector.argtypes = [vp, vp, i, vp, i, vp, ctypes.c_uint, vp]
+    for name in EXPORTED:
+        if name not in ("fe_status_str", "fe_last_error_message", "fe_version"):
+            getattr(L, name).restype = st
+    L.fe_version.restype = i
+    _lib = L
+    return L
+
+
+def _check(status, where):
+    if status != FE_OK:
+        raise FEError(status, where)
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must have dtype %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec(p):
+    return PRECISIONS[p] if isinstance(p, str) else int(p)
+
+
+# ---- reference element (host only) -----------------------------------------------
+
+def refbasis_hex(p: int, nq: int):
+    """Order-p hex Lagrange basis and nq^3 Gauss rule (fe_refbasis_hex):
+    points (Q,3), weights (Q), phi (Q,N), dphi (Q,3,N), numpy float64."""
+    L = load_library()
+    Q, N = nq ** 3, (p + 1) ** 3
+    pts, w, phi, dphi = np.zeros((Q, 3)), np.zeros(Q), np.zeros((Q, N)), np.zeros((Q, 3, N))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(L.fe_refbasis_hex(p, nq, pts.ctypes.data_as(dp), w.ctypes.data_as(dp), phi.ctypes.data_as(dp),
+                             dphi.ctypes.data_as(dp)), "fe_refbasis_hex")
+    return pts, w, phi, dphi
+
+
+# ---- context -------------------------------------------------------------------------
+
+class Context:
+    def __init__(self, device: int = 0):
+        L = load_library()
+        self._h = ctypes.c_void_p()
+        _check(L.fe_create(device, ctypes.byref(self._h)), "fe_create")
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def status(self, stream=None):
+        """(status code, smallest offending element or -1); synchronizes the stream."""
+        bad = ctypes.c_longlong(-1)
+        st = _lib.fe_get_status(self._h, _stream_ptr(stream), ctypes.byref(bad))
+        return st, bad.value
+
+    def check(self, stream=None):
+        st, bad = self.status(stream)
+        if st != FE_OK:
+            raise FEError(st, "device check (element %d)" % bad)
+
+    def close(self):
+        if self._h:
+            _lib.fe_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    """Borrowed device mesh: coords (n_nodes,3) float64, conn (n_elems,N) int32."""
+
+    def __init__(self, coords, conn):
+        import torch
+        self.coords, self.conn = coords, conn
+        _dev(coords, torch.float64, "coords")
+        _dev(conn, torch.int32, "conn")
+        if coords.dim() != 2 or coords.shape[1] != 3 or conn.dim() != 2:
+            raise ValueError("coords must be (n_nodes,3), conn (n_elems,N)")
+        self.struct = _Mesh(coords.data_ptr(), coords.shape[0], conn.data_ptr(), conn.shape[0], conn.shape[1])
+
+    @property
+    def n_nodes(self):
+        return self.coords.shape[0]
+
+    @property
+    def n_elems(self):
+        return self.conn.shape[0]
+
+    @property
+    def nodes_per_elem(self):
+        return self.conn.shape[1]
+
+
+class Geometry:
+    def __init__(self, ctx, mesh, handle, N, Q):
+        self.ctx, self.mesh, self._h, self.N, self.Q = ctx, mesh, handle, N, Q
+
+    def get(self, field: int, precision="f64", stream=None):
+        import torch
+        f64 = _prec(precision) == F64
+        E = self.mesh.n_elems
+        shape = {GEOM_WDETJ: (E, self.Q), GEOM_JINV: (E, self.Q, 3, 3), GEOM_G: (E, self.Q, 3, self.N)}[field]
+        out = torch.empty(shape, dtype=torch.float64 if f64 else torch.float32, device=self.mesh.coords.device)
+        _check(_lib.fe_geometry_get(self.ctx.handle, self._h, field, _prec(precision),
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "fe_geometry_get")
+        return out
+
+    def update(self, stream=None):
+        """fe_geometry_update: recompute in place from the mesh's current coordinates."""
+        _check(_lib.fe_geometry_update(self.ctx.handle, self._h, _stream_ptr(stream)), "fe_geometry_update")
+
+    def free(self):
+        if self._h:
+            _lib.fe_geometry_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def geometry(ctx: Context, mesh: Mesh, phi, dphi, weights, flags: int = 0, stream=None) -> Geometry:
+    """fe_geometry: FP64 J, det J, J^-1, w det J for every element and qp."""
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    dphi = np.ascontiguousarray(dphi, dtype=np.float64)
+    weights = np.ascontiguousarray(weights, dtype=np.float64)
+    Q, N = phi.shape
+    basis = _RefBasis(N, Q, phi.ctypes.data, dphi.ctypes.data)
+    quad = _Quad(Q, None, weights.ctypes.data)
+    h = ctypes.c_void_p()
+    _check(_lib.fe_geometry(ctx.handle, ctypes.byref(mesh.struct), ctypes.byref(basis), ctypes.byref(quad), flags,
+                            ctypes.byref(h), _stream_ptr(stream)), "fe_geometry")
+    return Geometry(ctx, mesh, h, N, Q)
+
+
+class Form:
+    def __init__(self, expr, operands, handle):
+        self.expr, self.operands, self._h = expr, operands, handle
+        self.state_op = [k for k, o in enumerate(operands) if o[0] == STATE][0]
+
+    def shape(self, n_basis):
+        r, c = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.fe_form_shape(self._h, n_basis, ctypes.byref(r), ctypes.byref(c)), "fe_form_shape")
+        return r.value, c.value
+
+    def free(self):
+        if self._h:
+            _lib.fe_form_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def form_compile(expr: str, operands, ctx: Context | None = None) -> Form:
+    """fe_form_compile.  operands: list of (role, ncomp, material_kind)."""
+    L = load_library()
+    arr = (_Operand * len(operands))(*[_Operand(r, n, m) for r, n, m in operands])
+    h = ctypes.c_void_p()
+    _check(L.fe_form_compile(ctx.handle if ctx else None, expr.encode(), arr, len(operands), ctypes.byref(h)),
+           "fe_form_compile(%r)" % expr)
+    return Form(expr, list(operands), h)
+
+
+_MAT_SIZE = {MAT_SCALAR: 1, MAT_LAME: 2, MAT_D66: 36}
+
+
+def _args(form: Form, args, geom: Geometry):
+    """Device pointers of the operands; checks materials (float64, one row per element)."""
+    import torch
+    if len(args) != len(form.operands):
+        raise ValueError("expected %d operands, got %d" % (len(form.operands), len(args)))
+    ptrs = (ctypes.c_void_p * len(form.operands))()
+    for k, (a, (role, ncomp, mk)) in enumerate(zip(args, form.operands)):
+        if role == MATERIAL:
+            _dev(a, torch.float64, "material operand %d" % k)
+            if a.numel() != geom.mesh.n_elems * _MAT_SIZE[mk]:
+                raise ValueError("material operand %d must have %d values per element" % (k, _MAT_SIZE[mk]))
+        ptrs[k] = None if a is None else a.data_ptr()
+    return ptrs
+
+
+def _out_dtype(precision):
+    import torch
+    return torch.float64 if _prec(precision) == F64 else torch.float32
+
+
+def eval_matrix(ctx: Context, form: Form, geom: Geometry, args, precision="f64", out=None, diff_op=None,
+                stream=None):
+    """fe_eval_matrix: element matrices (E, n_rows, n_cols)."""
+    import torch
+    nr, nc = form.shape(geom.N)
+    E = geom.mesh.n_elems
+    if out is None:
+        out = torch.empty((E, nr, nc), dtype=_out_dtype(precision), device=geom.mesh.coords.device)
+    _dev(out, _out_dtype(precision), "K_out")
+    if tuple(out.shape) != (E, nr, nc):
+        raise ValueError("K_out must have shape %s" % ((E, nr, nc),))
+    d = form.state_op if diff_op is None else diff_op
+    _check(_lib.fe_eval_matrix(ctx.handle, form._h, geom._h, _args(form, args, geom), d, _prec(precision),
+                               ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "fe_eval_matrix")
+    return out
+
+
+def eval_residual(ctx: Context, form: Form, geom: Geometry, args, precision="f64", out=None, stream=None):
+    """fe_eval_residual: element residuals (E, n_rows)."""
+    import torch
+    nr, _ = form.shape(geom.N)
+    E = geom.mesh.n_elems
+    if out is None:
+        out = torch.empty((E, nr), dtype=_out_dtype(precision), device=geom.mesh.coords.device)
+    _dev(out, _out_dtype(precision), "r_out")
+    if tuple(out.shape) != (E, nr):
+        raise ValueError("r_out must have shape %s" % ((E, nr),))
+    u = args[form.state_op]
+    _dev(u, _out_dtype(precision), "state DOF vector")
+    if u.numel() != geom.mesh.n_nodes * form.operands[form.state_op][1]:
+        raise ValueError("state DOF vector must have n_nodes * ncomp entries")
+    _check(_lib.fe_eval_residual(ctx.handle, form._h, geom._h, _args(form, args, geom), _prec(precision),
+                                 ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "fe_eval_residual")
+    return out
+
+
+class Assembly:
+    def __init__(self, ctx, mesh, handle):
+        self.ctx, self.mesh, self._h = ctx, mesh, handle
+
+    def free(self):
+        if self._h:
+            _lib.fe_assembly_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def assembly_create(ctx: Context, mesh: Mesh, stream=None) -> Assembly:
+    h = ctypes.c_void_p()
+    _check(_lib.fe_assembly_create(ctx.handle, ctypes.byref(mesh.struct), ctypes.byref(h), _stream_ptr(stream)),
+           "fe_assembly_create")
+    return Assembly(ctx, mesh, h)
+
+
+def assemble_vector(ctx: Context, asm: Assembly, ncomp: int, r_e, precision="f64", out=None, flags: int = 0,
+                    stream=None):
+    """fe_assemble_vector: deterministic gather of element vectors into (n_nodes*ncomp)."""
+    import torch
+    dt = _out_dtype(precision)
+    _dev(r_e, dt, "r_e")
+    if r_e.numel() != asm.mesh.n_elems * ncomp * asm.mesh.nodes_per_elem:
+        raise ValueError("r_e must be (n_elems, ncomp * nodes_per_elem)")
+    if out is None:
+        out = torch.zeros(asm.mesh.n_nodes * ncomp, dtype=dt, device=r_e.device)
+    _dev(out, dt, "global_out")
+    if out.numel() != asm.mesh.n_nodes * ncomp:
+        raise ValueError("global_out must have n_nodes * ncomp entries")
+    _check(_lib.fe_assemble_vector(ctx.handle, asm._h, ncomp, ctypes.c_void_p(r_e.data_ptr()), _prec(precision),
+                                   ctypes.c_void_p(out.data_ptr()), flags, _stream_ptr(stream)), "fe_assemble_vector")
+    return out
+
+
+# ---- named forms of Tab. ewfd ---------------------------------------------------------
+
+def laplace_form(weighted: bool = False) -> Form:
+    if weighted:
+        return form_compile("0,0.i,0.i", [(MATERIAL, 1, MAT_SCALAR), (VIRTUAL, 1, MAT_NONE), (STATE, 1, MAT_NONE)])
+    return form_compile("0.i,0.i", [(VIRTUAL, 1, MAT_NONE), (STATE, 1, MAT_NONE)])
+
+
+def mass_form(ncomp: int = 1, weighted: bool = False) -> Form:
+    ops = [(VIRTUAL, ncomp, MAT_NONE), (STATE, ncomp, MAT_NONE)]
+    if weighted:
+        return form_compile("0,i,i", [(MATERIAL, 1, MAT_SCALAR)] + ops)
+    return form_compile("i,i", ops)
+
+
+def elasticity_form(material: int = MAT_LAME) -> Form:
+    return form_compile("IK,s(i:j)->I,s(k:l)->K",
+                        [(MATERIAL, 1, material), (VIRTUAL, 3, MAT_NONE), (STATE, 3, MAT_NONE)])

@@ -24,3 +24,11 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="session")
+def libfe():
+    """Build (if needed) and load the CUDA library; no CPU fallback exists."""
+    from paper_2107_04121_gb300 import build, fe
+    build.build()
+    return fe.load_library()

@@ -1,0 +1,257 @@
+"""GPU parity: libfe (through the C ABI) against the FP64 oracle, element by
+element, on seeded meshes that span several CTA tiles and a ragged tail."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_04121_gb300 import fe, meshgen
+from tests.parity import TOL, Problem, rel_matrix_error, rel_vector_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(libfe):
+    c = fe.Context(0)
+    yield c
+    c.close()
+
+
+def _t(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+# ---- geometry ------------------------------------------------------------------
+
+@pytest.mark.parametrize("p,n", [(1, (5, 4, 3)), (2, (4, 3, 3)), (3, (2, 2, 3))])
+def test_geometry_matches_oracle(ctx, p, n):
+    mesh = meshgen.structured_hex(*n, p, 0.15, 21)
+    P = Problem(ctx, mesh, p, p + 1)
+    wdetJ, G, Jinv = oracle.geometry(mesh.coords, mesh.conn, P.ref, want_Jinv=True)
+    g_w = P.geom.get(fe.GEOM_WDETJ, "f64").cpu().numpy()
+    g_J = P.geom.get(fe.GEOM_JINV, "f64").cpu().numpy()
+    g_G = P.geom.get(fe.GEOM_G, "f64").cpu().numpy()
+    ctx.check()
+    assert np.abs(g_w - wdetJ).max() <= 1e-14 * np.abs(wdetJ).max()
+    assert np.abs(g_J - Jinv).max() <= 1e-13 * np.abs(Jinv).max()
+    assert np.abs(g_G - G).max() <= 1e-12 * np.abs(G).max()
+    # float32 copies are the float64 values rounded once
+    np.testing.assert_array_equal(P.geom.get(fe.GEOM_WDETJ, "f32").cpu().numpy(), g_w.astype(np.float32))
+    np.testing.assert_array_equal(P.geom.get(fe.GEOM_JINV, "f32").cpu().numpy(), g_J.astype(np.float32))
+
+
+def test_geometry_update_follows_moved_nodes(ctx):
+    mesh = meshgen.structured_hex(3, 3, 3, 2, 0.1, 22)
+    P = Problem(ctx, mesh, 2, 3)
+    rng = np.random.default_rng(23)
+    new = mesh.coords * np.array([1.5, 0.8, 1.1]) + 0.01 * rng.standard_normal(mesh.coords.shape)
+    P.coords_d.copy_(torch.from_numpy(new))
+    P.geom.update()
+    wdetJ, G, _ = oracle.geometry(new, mesh.conn, P.ref)
+    ctx.check()
+    g_G = P.geom.get(fe.GEOM_G, "f64").cpu().numpy()
+    assert np.abs(P.geom.get(fe.GEOM_WDETJ, "f64").cpu().numpy() - wdetJ).max() <= 1e-14 * np.abs(wdetJ).max()
+    assert np.abs(g_G - G).max() <= 1e-12 * np.abs(G).max()
+
+
+def test_nonpositive_detj_is_reported(ctx):
+    mesh = meshgen.structured_hex(3, 3, 2, 1, 0.0, 0)
+    mesh.conn[7, [0, 1]] = mesh.conn[7, [1, 0]]  # mirrored element
+    mesh.conn[12, [2, 3]] = mesh.conn[12, [3, 2]]
+    P = Problem(ctx, mesh, 1, 2)
+    st, bad = ctx.status()
+    assert st == fe.FE_ERR_NONPOSITIVE_DETJ and bad == 7
+    assert ctx.status() == (fe.FE_OK, -1)  # cleared
+
+
+# ---- matrix and residual modes ----------------------------------------------------
+
+def _case(ctx, kind, p, n, seed, material=fe.MAT_LAME):
+    mesh = meshgen.structured_hex(*n, p, 0.15, seed)
+    lam, mu = meshgen.lame_materials(mesh)
+    P = Problem(ctx, mesh, p, p + 1)
+    wdetJ, G, _ = P.oracle_geometry()
+    rng = np.random.default_rng(seed + 100)
+    E = mesh.n_elems
+    if kind == "laplace":
+        coef = rng.uniform(0.5, 2.0, E)
+        form = fe.laplace_form(weighted=True)
+        mat = coef
+        K = oracle.matrix_laplace(wdetJ, G, coef)
+        u = rng.standard_normal(mesh.n_nodes)
+        r = oracle.residual_laplace(mesh.conn, wdetJ, G, u, coef)
+        ncomp = 1
+    elif kind in ("mass1", "mass3"):
+        ncomp = 1 if kind == "mass1" else 3
+        coef = rng.uniform(0.5, 2.0, E)
+        form = fe.mass_form(ncomp, weighted=True)
+        mat = coef
+        K = oracle.matrix_mass(wdetJ, P.ref.phi, ncomp, coef)
+        u = rng.standard_normal(mesh.n_nodes * ncomp)
+        r = oracle.residual_mass(mesh.conn, wdetJ, P.ref.phi, u, ncomp, coef)
+    else:
+        ncomp = 3
+        form = fe.elasticity_form(material)
+        if material == fe.MAT_LAME:
+            mat = np.stack([lam, mu], 1)
+            D = oracle.lame_to_D(lam, mu)
+        else:  # general symmetric positive definite D per element
+            A = rng.standard_normal((E, 6, 6))
+            D = np.einsum("eij,ekj->eik", A, A) + 6 * np.eye(6)
+            mat = D
+        K = oracle.matrix_elasticity(wdetJ, G, D)
+        u = rng.standard_normal(mesh.n_nodes * 3)
+        r = oracle.residual_elasticity(mesh.conn, wdetJ, G, D, u)
+    return P, form, mat, u, K, r, ncomp
+
+
+CASES = [
+    ("laplace", 1, (5, 4, 3)), ("laplace", 2, (4, 3, 3)), ("laplace", 3, (2, 2, 3)),
+    ("mass1", 1, (5, 4, 3)), ("mass3", 2, (4, 3, 3)), ("mass1", 3, (2, 2, 3)),
+    ("elasticity", 1, (5, 4, 3)), ("elasticity", 2, (4, 4, 4)), ("elasticity", 3, (2, 2, 3)),
+]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kind,p,n", CASES)
+def test_matrix_and_residual_match_oracle(ctx, kind, p, n, prec):
+    P, form, mat, u, Kref, rref, ncomp = _case(ctx, kind, p, n, 31 + p)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    args = [None] * len(form.operands)
+    args[form.state_op] = _t(u, dt)
+    args[0] = _t(mat, torch.float64)  # the material is operand 0 in the named forms
+    K = fe.eval_matrix(ctx, form, P.geom, args, prec)
+    r = fe.eval_residual(ctx, form, P.geom, args, prec)
+    ctx.check()
+    ek = rel_matrix_error(K.cpu().numpy(), Kref)
+    er = rel_vector_error(r.cpu().numpy(), rref)
+    assert ek <= TOL[prec], ek
+    assert er <= TOL[prec], er
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_elasticity_general_D_and_transposed_spec(ctx, prec):
+    P, form, D, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (3, 3, 2), 41, fe.MAT_D66)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    K = fe.eval_matrix(ctx, form, P.geom, [_t(D, torch.float64), None, None], prec)
+    r = fe.eval_residual(ctx, form, P.geom, [_t(D, torch.float64), None, _t(u, dt)], prec)
+    assert rel_matrix_error(K.cpu().numpy(), Kref) <= TOL[prec]
+    assert rel_vector_error(r.cpu().numpy(), rref) <= TOL[prec]
+    # 'KI,...' names the material indices as (u, v): the kernel must use D^T
+    ft = fe.form_compile("KI,s(i:j)->I,s(k:l)->K", [(fe.MATERIAL, 1, fe.MAT_D66), (fe.VIRTUAL, 3, 0),
+                                                      (fe.STATE, 3, 0)])
+    Dt = np.ascontiguousarray(D.transpose(0, 2, 1))
+    Kt = fe.eval_matrix(ctx, ft, P.geom, [_t(Dt, torch.float64), None, None], prec)
+    assert rel_matrix_error(Kt.cpu().numpy(), Kref) <= TOL[prec]
+
+
+def test_laplace_q1_cube_config(ctx):
+    """Plain method, Laplace stiffness on the 8^3 Q1 cube (+-0.1h, seed 0), c = 1."""
+    mesh, u = meshgen.laplace_q1_cube(8, 0)
+    P = Problem(ctx, mesh, 1, 2)
+    wdetJ, G, _ = P.oracle_geometry()
+    form = fe.laplace_form()
+    K = fe.eval_matrix(ctx, form, P.geom, [None, None], "f64")
+    r = fe.eval_residual(ctx, form, P.geom, [None, _t(u, torch.float64)], "f64")
+    ctx.check()
+    assert K.shape == (512, 8, 8) and K.dtype == torch.float64 and r.shape == (512, 8)
+    assert rel_matrix_error(K.cpu().numpy(), oracle.matrix_laplace(wdetJ, G)) <= 1e-12
+    assert rel_vector_error(r.cpu().numpy(), oracle.residual_laplace(mesh.conn, wdetJ, G, u)) <= 1e-12
+
+
+def test_empty_mesh_is_a_no_op(ctx):
+    mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
+    coords = _t(mesh.coords, torch.float64)
+    conn = torch.zeros((0, 27), dtype=torch.int32, device="cuda")
+    m = fe.Mesh(coords, conn)
+    pts, w, phi, dphi = fe.refbasis_hex(2, 3)
+    g = fe.geometry(ctx, m, phi, dphi, w)
+    K = fe.eval_matrix(ctx, fe.elasticity_form(), g, [torch.zeros((0, 2), dtype=torch.float64, device="cuda"),
+                                                       None, None], "f32")
+    ctx.check()
+    assert K.shape == (0, 81, 81)
+
+
+def test_argument_errors(ctx):
+    mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
+    P = Problem(ctx, mesh, 2, 3)
+    form = fe.laplace_form()
+    with pytest.raises(fe.FEError) as ei:
+        fe.eval_matrix(ctx, form, P.geom, [None, None], "f64", diff_op=0)  # not the state operand
+    assert ei.value.status == fe.FE_ERR_INVALID_ARG
+    with pytest.raises(fe.FEError) as ei:  # no tensor-core kernel for the Laplacian
+        fe.eval_matrix(ctx, form, P.geom, [None, None], "bf16x3")
+    assert ei.value.status == fe.FE_ERR_UNSUPPORTED_SPEC
+    # unsupported (N, Q) pair
+    pts, w, phi, dphi = fe.refbasis_hex(2, 2)
+    with pytest.raises(fe.FEError) as ei:
+        fe.geometry(ctx, P.m, phi, dphi, w)
+    assert ei.value.status == fe.FE_ERR_SHAPE
+    # a geometry without the float32 copy cannot feed the float32 kernels
+    pts, w, phi, dphi = fe.refbasis_hex(2, 3)
+    g64 = fe.geometry(ctx, P.m, phi, dphi, w, flags=fe.GEOM_STORE_F64)
+    with pytest.raises(fe.FEError) as ei:
+        fe.eval_matrix(ctx, form, g64, [None, None], "f32")
+    assert ei.value.status == fe.FE_ERR_INVALID_ARG
+    ctx.check()
+
+
+# ---- assembly -------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p,ncomp", [(1, 1), (2, 3)])
+def test_assembly_fp64_is_bit_exact(ctx, p, ncomp):
+    mesh = meshgen.structured_hex(5, 4, 3, p, 0.1, 51)
+    rng = np.random.default_rng(52)
+    r = rng.standard_normal((mesh.n_elems, ncomp * mesh.nodes_per_elem))
+    want = oracle.assemble(mesh.conn, r, mesh.n_nodes, ncomp)
+    m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+    asm = fe.assembly_create(ctx, m)
+    got = fe.assemble_vector(ctx, asm, ncomp, _t(r, torch.float64), "f64").cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    g0 = rng.standard_normal(mesh.n_nodes * ncomp)
+    out = _t(g0, torch.float64)
+    fe.assemble_vector(ctx, asm, ncomp, _t(r, torch.float64), "f64", out=out, flags=fe.ASSEMBLE_ACCUMULATE)
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.assemble(mesh.conn, r, mesh.n_nodes, ncomp, g0))
+
+
+def test_assembly_fp32_compensated(ctx):
+    mesh = meshgen.structured_hex(6, 5, 4, 2, 0.1, 53)
+    rng = np.random.default_rng(54)
+    # large cancelling contributions make plain float32 sums lose digits
+    r = rng.standard_normal((mesh.n_elems, 81)) * 1e4
+    r[:, ::2] += 1e7
+    r[:, 1::2] -= 1e7
+    want = oracle.assemble(mesh.conn, r.astype(np.float32).astype(np.float64), mesh.n_nodes, 3)
+    m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+    asm = fe.assembly_create(ctx, m)
+    r32 = _t(r, torch.float32)
+    comp = fe.assemble_vector(ctx, asm, 3, r32, "f32", flags=fe.ASSEMBLE_COMPENSATED).cpu().numpy()
+    plain = fe.assemble_vector(ctx, asm, 3, r32, "f32").cpu().numpy()
+    scale = np.abs(r).max()
+    err_c = np.abs(comp - want).max() / scale
+    err_p = np.abs(plain - want).max() / scale
+    assert err_c <= 1e-7, err_c
+    assert err_c < err_p
+    again = fe.assemble_vector(ctx, asm, 3, r32, "f32", flags=fe.ASSEMBLE_COMPENSATED).cpu().numpy()
+    np.testing.assert_array_equal(comp, again)  # deterministic
+
+
+def test_assembly_rejects_out_of_range_nodes(ctx):
+    mesh = meshgen.structured_hex(2, 2, 2, 1, 0.0, 0)
+    conn = mesh.conn.copy()
+    conn[3, 2] = mesh.n_nodes + 5
+    m = fe.Mesh(_t(mesh.coords, torch.float64), _t(conn, torch.int32))
+    with pytest.raises(fe.FEError) as ei:
+        fe.assembly_create(ctx, m)
+    assert ei.value.status == fe.FE_ERR_SHAPE
+
+
+def test_results_are_deterministic(ctx):
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (4, 3, 3), 61)
+    args = [_t(mat, torch.float64), None, _t(u, torch.float32)]
+    K1 = fe.eval_matrix(ctx, form, P.geom, args, "f32")
+    K2 = fe.eval_matrix(ctx, form, P.geom, args, "f32")
+    r1 = fe.eval_residual(ctx, form, P.geom, args, "f32")
+    r2 = fe.eval_residual(ctx, form, P.geom, args, "f32")
+    assert torch.equal(K1, K2) and torch.equal(r1, r2)
