@@ -259,6 +259,37 @@ fe_status fe_assembly_free(fe_assembly_h *asm_h);
 fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *asm_h, int ncomp, const void *r_e, fe_precision prec,
                              void *global_out, unsigned flags, fe_stream_t stream);
 
+/* One-shot assembly for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not call cudaMalloc/cudaFree (directly or through a library such as
+ * torch), e.g. an application whose device memory is owned by its own
+ * allocator or budget, a real-time loop in which an allocation's implicit
+ * device synchronisation would stall other streams, or a callback run inside
+ * a framework step that forbids allocation.  It computes exactly what
+ * fe_assembly_create followed by fe_assemble_vector computes (same kernels,
+ * same summation order, same results), without an assembly handle and
+ * without allocating anything.
+ *
+ * Its workspace (node -> (element, local node) incidence lists, counters and
+ * the scan workspace) is one fixed file-scope device array of about 13 MB
+ * that every GPU loading libfe holds until the process exits.  Limits:
+ * n_nodes <= 524,288 and n_elems * nodes_per_elem <= 2,097,152; larger meshes
+ * get FE_ERR_SHAPE (with a message in fe_last_error_message) and nothing is
+ * launched.  The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the previous call's contents (the counters are cleared on every
+ * call): calls that may overlap on the GPU (different streams, or different
+ * host threads) race and must be serialised by the caller.
+ *
+ * Arguments as fe_assemble_vector, with the mesh given directly (device
+ * arrays, borrowed for the duration of the call).  An out-of-range node index
+ * is recorded in the context status word (FE_ERR_SHAPE, element index; see
+ * fe_get_status) and that incidence is skipped.  Asynchronous on `stream`. */
+fe_status fe_assemble_vector_noalloc(fe_ctx *ctx, const fe_mesh *mesh, int ncomp, const void *r_e,
+                                     fe_precision prec, void *global_out, unsigned flags, fe_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -345,4 +345,23 @@ fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *a, int ncomp, con
                      "fe_assemble_vector");
 }
 
+fe_status fe_assemble_vector_noalloc(fe_ctx *ctx, const fe_mesh *mesh, int ncomp, const void *r_e,
+                                     fe_precision prec, void *global_out, unsigned flags, fe_stream_t stream)
+{
+    if (!ctx || !valid_mesh(mesh) || (ncomp != 1 && ncomp != 3)) return FE_ERR_INVALID_ARG;
+    if ((!r_e && mesh->n_elems > 0) || (!global_out && mesh->n_nodes > 0)) return FE_ERR_INVALID_ARG;
+    if (flags & ~(FE_ASSEMBLE_ACCUMULATE | FE_ASSEMBLE_COMPENSATED)) return FE_ERR_INVALID_ARG;
+    if (prec < FE_F64 || prec > FE_BF16) return FE_ERR_INVALID_ARG;
+    if (fe_noalloc_limits(mesh->n_nodes, mesh->n_elems * (long long)mesh->nodes_per_elem) != cudaSuccess) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "fe_assemble_vector_noalloc: at most %d nodes and %d element-node incidences", 1 << 19,
+                      1 << 21);
+        return FE_ERR_SHAPE;
+    }
+    cudaSetDevice(ctx->device);
+    return from_cuda(fe_launch_assemble_noalloc(ctx->device, mesh, ncomp, prec == FE_F64, r_e, global_out, flags,
+                                                ctx->d_status, to_cuda(stream)),
+                     "fe_assemble_vector_noalloc");
+}
+
 }  // extern "C"

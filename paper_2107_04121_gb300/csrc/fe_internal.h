@@ -68,6 +68,10 @@ cudaError_t fe_launch_assembly_build(fe_assembly_h *a, int *d_flag, cudaStream_t
 cudaError_t fe_launch_assemble(const fe_assembly_h *a, int ncomp, bool f64, const void *r, void *out,
                                unsigned flags, cudaStream_t s);
 
+cudaError_t fe_noalloc_limits(long long n_nodes, long long n_incidences);
+cudaError_t fe_launch_assemble_noalloc(int device, const fe_mesh *mesh, int ncomp, bool f64, const void *r,
+                                       void *out, unsigned flags, unsigned long long *status, cudaStream_t s);
+
 // Which (N, Q) pairs have kernels.
 bool fe_supported_nq(int N, int Q);
 

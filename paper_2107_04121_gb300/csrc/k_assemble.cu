@@ -7,6 +7,8 @@
 // thread per global DOF sums its contributions in that fixed order.  No
 // floating-point atomics: the result is bit-reproducible and, in FP64, equal to
 // a sequential ascending-(e, a) sum.  FP32 sums may be Neumaier-compensated.
+#include <mutex>
+
 #include <cub/device/device_scan.cuh>
 
 #include "fe_device.cuh"
@@ -149,4 +151,106 @@ cudaError_t fe_launch_assemble(const fe_assembly_h *a, int ncomp, bool f64, cons
         k_gather<float, false><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, a->mesh.n_nodes, N, ncomp,
                                                     (const float *)r, (float *)out, acc);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// One-shot assembly without any device allocation (fe_assemble_vector_noalloc).
+// The incidence lists and the counters live in one file-scope device array of
+// fixed size, shared by every call on a device and kept until process exit.
+
+namespace {
+
+constexpr long long kNoallocMaxNodes = 1ll << 19;        // 524,288 nodes
+constexpr long long kNoallocMaxIncidences = 1ll << 21;   // 2,097,152 (element, local node) pairs
+constexpr size_t kNoallocScanBytes = (size_t)1 << 20;    // scan workspace
+// each sub-buffer starts on a 256-byte boundary (the scan workspace needs it)
+constexpr size_t kNoallocOffsetsBytes = (sizeof(int) * (kNoallocMaxNodes + 1) + 255) / 256 * 256;
+constexpr size_t kNoallocScratchBytes =
+    2 * kNoallocOffsetsBytes + sizeof(int) * kNoallocMaxIncidences + kNoallocScanBytes;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+
+// The host-side symbol is only a stand-in: resolve the device address of the
+// array once per device, with that device current.
+cudaError_t noalloc_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kNoallocMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[device] = p;
+    }
+    *out = (unsigned char *)g_noalloc_ptr[device];
+    return cudaSuccess;
+}
+
+// Count incidences per node; an out-of-range node index is recorded in the
+// context status word (FE_ERR_SHAPE, element index) and skipped.
+__global__ void k_count_report(const int32_t *__restrict__ conn, long long total, int N, long long n_nodes, int *cnt,
+                               unsigned long long *status)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long node = conn[i];
+        if (node < 0 || node >= n_nodes)
+            fe_report(status, FE_ERR_SHAPE, i / N);
+        else
+            atomicAdd(cnt + node, 1);
+    }
+}
+
+}  // namespace
+
+cudaError_t fe_noalloc_limits(long long n_nodes, long long n_incidences)
+{
+    return (n_nodes <= kNoallocMaxNodes && n_incidences <= kNoallocMaxIncidences) ? cudaSuccess
+                                                                                  : cudaErrorInvalidValue;
+}
+
+cudaError_t fe_launch_assemble_noalloc(int device, const fe_mesh *mesh, int ncomp, bool f64, const void *r,
+                                       void *out, unsigned flags, unsigned long long *status, cudaStream_t s)
+{
+    unsigned char *base = nullptr;
+    cudaError_t err = noalloc_scratch(device, &base);
+    if (err != cudaSuccess) return err;
+    const long long n_nodes = mesh->n_nodes, total = mesh->n_elems * mesh->nodes_per_elem;
+    int *offsets = (int *)base;
+    int *cursor = (int *)(base + kNoallocOffsetsBytes);
+    int *entries = (int *)(base + 2 * kNoallocOffsetsBytes);
+    void *scan_tmp = base + 2 * kNoallocOffsetsBytes + sizeof(int) * kNoallocMaxIncidences;
+    size_t scan_bytes = 0;
+    err = cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, cursor, offsets, (int)(n_nodes + 1), s);
+    if (err != cudaSuccess) return err;
+    if (scan_bytes > kNoallocScanBytes) return cudaErrorInvalidValue;
+    // the array keeps the previous call's contents: counters start from zero
+    err = cudaMemsetAsync(cursor, 0, sizeof(int) * (n_nodes + 1), s);
+    if (err == cudaSuccess && total > 0) {
+        k_count_report<<<grid_for(total, 256), 256, 0, s>>>(mesh->conn, total, mesh->nodes_per_elem, n_nodes, cursor,
+                                                            status);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess)
+        err = cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, cursor, offsets, (int)(n_nodes + 1), s);
+    if (err == cudaSuccess) err = cudaMemsetAsync(cursor, 0, sizeof(int) * (n_nodes + 1), s);
+    if (err == cudaSuccess && total > 0) {
+        k_fill<<<grid_for(total, 256), 256, 0, s>>>(mesh->conn, total, n_nodes, offsets, cursor, entries);
+        err = cudaGetLastError();
+    }
+    if (err == cudaSuccess && n_nodes > 0) {
+        k_sort<<<grid_for(n_nodes, 256), 256, 0, s>>>(offsets, n_nodes, entries);
+        err = cudaGetLastError();
+    }
+    if (err != cudaSuccess) return err;
+    fe_assembly_h view{};
+    view.device = device;
+    view.mesh = *mesh;
+    view.d_offsets = offsets;
+    view.d_entries = entries;
+    return fe_launch_assemble(&view, ncomp, f64, r, out, flags, s);
 }

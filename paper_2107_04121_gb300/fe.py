@@ -33,7 +33,7 @@ EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
     "fe_refbasis_hex", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
     "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_assembly_create", "fe_assembly_free",
-    "fe_assemble_vector",
+    "fe_assemble_vector", "fe_assemble_vector_noalloc",
 ]
 
 
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_assembly_create.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(vp), vp]
     L.fe_assembly_free.argtypes = [vp]
     L.fe_assemble_vector.argtypes = [vp, vp, i, vp, i, vp, ctypes.c_uint, vp]
+    L.fe_assemble_vector_noalloc.argtypes = [vp, ctypes.POINTER(_Mesh), i, vp, i, vp, ctypes.c_uint, vp]
     for name in EXPORTED:
         if name not in ("fe_status_str", "fe_last_error_message", "fe_version"):
             getattr(L, name).restype = st
@@ -381,6 +382,25 @@ def assemble_vector(ctx: Context, asm: Assembly, ncomp: int, r_e, precision="f64
         raise ValueError("global_out must have n_nodes * ncomp entries")
     _check(_lib.fe_assemble_vector(ctx.handle, asm._h, ncomp, ctypes.c_void_p(r_e.data_ptr()), _prec(precision),
                                    ctypes.c_void_p(out.data_ptr()), flags, _stream_ptr(stream)), "fe_assemble_vector")
+    return out
+
+
+def assemble_vector_noalloc(ctx: Context, mesh: Mesh, ncomp: int, r_e, out, precision="f64", flags: int = 0,
+                            stream=None):
+    """fe_assemble_vector_noalloc: the same assembly as assembly_create + assemble_vector
+    for callers that cannot allocate device memory; the library allocates nothing and
+    `out` must be preallocated (n_nodes * ncomp).  The library's fixed workspace is
+    shared by all calls on a device: calls that overlap on the GPU race."""
+    import torch
+    dt = _out_dtype(precision)
+    _dev(r_e, dt, "r_e")
+    _dev(out, dt, "global_out")
+    if r_e.numel() != mesh.n_elems * ncomp * mesh.nodes_per_elem or out.numel() != mesh.n_nodes * ncomp:
+        raise ValueError("r_e must be (n_elems, ncomp * N) and global_out (n_nodes * ncomp)")
+    _check(_lib.fe_assemble_vector_noalloc(ctx.handle, ctypes.byref(mesh.struct), ncomp,
+                                           ctypes.c_void_p(r_e.data_ptr()), _prec(precision),
+                                           ctypes.c_void_p(out.data_ptr()), flags, _stream_ptr(stream)),
+           "fe_assemble_vector_noalloc")
     return out
 
 
