@@ -15,238 +15,398 @@
 // the epilogue is lambda A_ik + mu A_ki + mu delta_ik tr A.
 //
 // A CTA takes EPB consecutive elements: it stages J^-1 and wdetJ (one
-// contiguous block, element-outermost layout), forms the physical gradients
-// G = J^-T grad_xi phi in shared memory, and each thread accumulates a TA x TB
-// node-pair tile (all nine direction pairs for elasticity) in registers.
+// contiguous block, element-outermost layout) and forms the physical gradients
+// G = J^-T grad_xi phi in shared memory, with every T-node group padded to a
+// 16-byte boundary so that a thread fetches its T gradients with one vector
+// load.  Element matrices are symmetric, so each thread owns one T x T node
+// tile of the upper tile triangle (all nine direction pairs for elasticity,
+// T*T*9 register accumulators) and writes it and its mirror image.  The
+// finished matrices are staged in shared memory (over the dead G buffer) and
+// streamed to HBM with coalesced 16-byte stores that bypass L2 residency
+// (st.global.cs), since K_e is written once and never re-read here.
 #include "fe_device.cuh"
 
 namespace {
 
-template <typename T, int N, int Q, int KIND, int TA, int TB, int EPB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_matrix_simt(const T *__restrict__ jinv, const T *__restrict__ wdetj,
-                                                         const T *__restrict__ dphi, const T *__restrict__ phi,
-                                                         long long E, int ncomp, fe_material_kind mkind,
-                                                         const double *__restrict__ mat, int mat_t,
-                                                         T *__restrict__ K)
+// Padded position of node a inside its group of T (groups start on 16 bytes).
+template <int T, typename S>
+__host__ __device__ constexpr int tile_pad()
 {
-    constexpr int NTA = N / TA, NTB = N / TB, NT = NTA * NTB;
-    constexpr bool GRAD = KIND != FK_MASS;
+    return (T * (int)sizeof(S) + 15) / 16 * 16 / (int)sizeof(S);
+}
+
+template <typename S, int T>
+struct TileVec {
+    // load T consecutive values starting at a 16-byte aligned address
+    __device__ __forceinline__ static void load(const S *p, S *v)
+    {
+#pragma unroll
+        for (int x = 0; x < T; ++x) v[x] = p[x];
+    }
+};
+template <>
+struct TileVec<float, 3> {
+    __device__ __forceinline__ static void load(const float *p, float *v)
+    {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+    }
+};
+template <>
+struct TileVec<float, 4> {
+    __device__ __forceinline__ static void load(const float *p, float *v)
+    {
+        const float4 q = *reinterpret_cast<const float4 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    }
+};
+template <>
+struct TileVec<float, 2> {
+    __device__ __forceinline__ static void load(const float *p, float *v)
+    {
+        const float2 q = *reinterpret_cast<const float2 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    }
+};
+template <>
+struct TileVec<double, 2> {
+    __device__ __forceinline__ static void load(const double *p, double *v)
+    {
+        const double2 q = *reinterpret_cast<const double2 *>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+    }
+};
+template <>
+struct TileVec<double, 4> {
+    __device__ __forceinline__ static void load(const double *p, double *v)
+    {
+        const double2 q0 = *reinterpret_cast<const double2 *>(p);
+        const double2 q1 = *reinterpret_cast<const double2 *>(p + 2);
+        v[0] = q0.x;
+        v[1] = q0.y;
+        v[2] = q1.x;
+        v[3] = q1.y;
+    }
+};
+template <>
+struct TileVec<double, 3> {
+    __device__ __forceinline__ static void load(const double *p, double *v)
+    {
+        const double2 q0 = *reinterpret_cast<const double2 *>(p);
+        v[0] = q0.x;
+        v[1] = q0.y;
+        v[2] = p[2];
+    }
+};
+
+// Shared-memory plan of one CTA (sizes in elements of S).
+template <typename S, int N, int Q, int KIND, int T, int EPB, bool STAGE>
+struct MatrixSmem {
+    static constexpr bool GRAD = KIND != FK_MASS;
+    static constexpr int TP = tile_pad<T, S>();
+    static constexpr int NP = (N / T) * TP;  // padded node count
+    static constexpr int G_SIZE = GRAD ? EPB * Q * 3 * NP : Q * NP;
+    static constexpr int NROW_MAX = (KIND == FK_LAPLACE ? 1 : 3) * N;
+    // staged matrices, +16 bytes to shift the chunk onto the global alignment
+    static constexpr int K_SIZE = STAGE ? EPB * NROW_MAX * NROW_MAX + 16 / (int)sizeof(S) : 0;
+    static constexpr int GK = G_SIZE > K_SIZE ? G_SIZE : K_SIZE;  // K staging reuses the G buffer
+    static constexpr int J_OFF = GK;
+    static constexpr int W_OFF = J_OFF + EPB * Q * 9;
+    static constexpr int C_OFF = W_OFF + EPB * Q;
+    static constexpr int TOTAL = C_OFF + EPB * 81;
+    static constexpr size_t BYTES = sizeof(S) * (size_t)TOTAL;
+};
+
+// MATK: 0 scalar coefficient (or none), 1 Lame pair, 2 general D (6x6 Voigt)
+template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, bool STAGE>
+__global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ jinv, const S *__restrict__ wdetj,
+                                                        const S *__restrict__ dphi, const S *__restrict__ phi,
+                                                        long long E, int ncomp, const double *__restrict__ mat,
+                                                        int mat_t, S *__restrict__ K)
+{
+    using P = MatrixSmem<S, N, Q, KIND, T, EPB, STAGE>;
+    constexpr bool GRAD = P::GRAD;
+    constexpr int TP = P::TP, NP = P::NP, NT = N / T, NU = NT * (NT + 1) / 2;
+    constexpr int NDIR = KIND == FK_ELASTICITY ? 3 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sG = reinterpret_cast<T *>(smem_raw);          // GRAD: [EPB][Q][3][N]; MASS: phi [Q][N]
-    T *sJ = sG + (GRAD ? EPB * Q * 3 * N : Q * N);    // [EPB][Q][9]
-    T *sW = sJ + EPB * Q * 9;                         // [EPB][Q]
-    T *sC = sW + EPB * Q;                             // [EPB][81] elasticity tensor or [EPB] coefficient
+    S *sm = reinterpret_cast<S *>(smem_raw);
+    S *sG = sm;
+    S *sK = sm;
+    S *sJ = sm + P::J_OFF;
+    S *sW = sm + P::W_OFF;
+    S *sC = sm + P::C_OFF;
 
     const int nrow = ncomp * N;
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
         const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
-        __syncthreads();
-        // stage J^-1, wdetJ (contiguous) and the material
-        if (GRAD)
+        __syncthreads();  // previous iteration's copy-out has finished reading sK
+        if constexpr (GRAD)
             for (int i = threadIdx.x; i < ne * Q * 9; i += THREADS) sJ[i] = jinv[e0 * Q * 9 + i];
         for (int i = threadIdx.x; i < ne * Q; i += THREADS) sW[i] = wdetj[e0 * Q + i];
-        if constexpr (KIND == FK_ELASTICITY) {
+        if constexpr (MATK == 2) {
             for (int i = threadIdx.x; i < ne * 81; i += THREADS) {
                 const int el = i / 81, t = i % 81;
                 const int ii = t / 27, jj = (t / 9) % 3, kk = (t / 3) % 3, ll = t % 3;
-                double c;
+                const int I = fe_voigt(ii, jj), Kv = fe_voigt(kk, ll);
                 const long long e = e0 + el;
-                if (mkind == FE_MAT_LAME) {
-                    const double lam = mat[2 * e], mu = mat[2 * e + 1];
-                    c = lam * (ii == jj) * (kk == ll) + mu * ((ii == kk) * (jj == ll) + (ii == ll) * (jj == kk));
-                } else {
-                    const int I = fe_voigt(ii, jj), Kv = fe_voigt(kk, ll);
-                    c = mat_t ? mat[e * 36 + Kv * 6 + I] : mat[e * 36 + I * 6 + Kv];
-                }
-                sC[i] = (T)c;
+                sC[i] = (S)(mat_t ? mat[e * 36 + Kv * 6 + I] : mat[e * 36 + I * 6 + Kv]);
             }
+        } else if constexpr (MATK == 1) {
+            for (int i = threadIdx.x; i < ne * 2; i += THREADS) sC[i] = (S)mat[e0 * 2 + i];
         } else {
-            for (int i = threadIdx.x; i < ne; i += THREADS) sC[i] = mat ? (T)mat[e0 + i] : (T)1;
+            for (int i = threadIdx.x; i < ne; i += THREADS) sC[i] = mat ? (S)mat[e0 + i] : (S)1;
         }
-        if (!GRAD)
-            for (int i = threadIdx.x; i < Q * N; i += THREADS) sG[i] = phi[i];
+        if constexpr (!GRAD)
+            for (int i = threadIdx.x; i < Q * N; i += THREADS) {
+                const int q = i / N, a = i % N;
+                sG[q * NP + (a / T) * TP + a % T] = phi[i];
+            }
         __syncthreads();
-        if (GRAD) {
-            // G[el][q][j][a] = sum_k dphi[q][k][a] Jinv[el][q][k][j]
+        if constexpr (GRAD) {
+            // G[el][q][j][a] = sum_k dphi[q][k][a] Jinv[el][q][k][j], padded node index
             for (int i = threadIdx.x; i < ne * Q * N; i += THREADS) {
                 const int a = i % N, q = (i / N) % Q, el = i / (N * Q);
-                const T g0 = dphi[(q * 3 + 0) * N + a], g1 = dphi[(q * 3 + 1) * N + a],
-                        g2 = dphi[(q * 3 + 2) * N + a];
-                const T *Ji = sJ + (el * Q + q) * 9;
-                T *Go = sG + ((el * Q + q) * 3) * N + a;
+                const S g0 = dphi[(q * 3 + 0) * N + a], g1 = dphi[(q * 3 + 1) * N + a], g2 = dphi[(q * 3 + 2) * N + a];
+                const S *Ji = sJ + (el * Q + q) * 9;
+                S *Go = sG + ((el * Q + q) * 3) * NP + (a / T) * TP + a % T;
 #pragma unroll
-                for (int j = 0; j < 3; ++j) Go[j * N] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
+                for (int j = 0; j < 3; ++j) Go[j * NP] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
             }
             __syncthreads();
         }
 
-        for (int wi = threadIdx.x; wi < ne * NT; wi += THREADS) {
-            const int el = wi / NT, tile = wi % NT;
-            const int a0 = (tile / NTB) * TA, b0 = (tile % NTB) * TB;
-            const T *Wq = sW + el * Q;
-            T *Ke = K + (e0 + el) * (long long)nrow * nrow;
-            if constexpr (KIND == FK_ELASTICITY) {
-                T acc[3][3][TA][TB];
+        // ---- accumulate the upper tile triangle in registers
+        const int wi = threadIdx.x;
+        const bool active = wi < ne * NU;
+        int el = 0, ta = 0, tb = 0;
+        S acc[NDIR][NDIR][T][T];
 #pragma unroll
-                for (int j = 0; j < 3; ++j)
+        for (int j = 0; j < NDIR; ++j)
 #pragma unroll
-                    for (int l = 0; l < 3; ++l)
+            for (int l = 0; l < NDIR; ++l)
 #pragma unroll
-                        for (int x = 0; x < TA; ++x)
+                for (int x = 0; x < T; ++x)
 #pragma unroll
-                            for (int y = 0; y < TB; ++y) acc[j][l][x][y] = 0;
-                const T *Ge = sG + el * Q * 3 * N;
-                for (int q = 0; q < Q; ++q) {
-                    const T wq = Wq[q];
-                    const T *Gq = Ge + q * 3 * N;
-                    T ga[3][TA], gb[3][TB];
+                    for (int y = 0; y < T; ++y) acc[j][l][x][y] = 0;
+        if (active) {
+            el = wi / NU;
+            int u = wi % NU;
+            // u -> (ta, tb), ta <= tb, row-major over the upper triangle
+            while (u >= NT - ta) {
+                u -= NT - ta;
+                ++ta;
+            }
+            tb = ta + u;
+            const S *Wq = sW + el * Q;
+            for (int q = 0; q < Q; ++q) {
+                const S wq = Wq[q];
+                const S *Gq = GRAD ? sG + (el * Q + q) * 3 * NP : sG + q * NP;
+                S ga[NDIR][T], gb[NDIR][T];
+                if constexpr (KIND == FK_LAPLACE) {
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
+                        S va[T], vb[T];
+                        TileVec<S, T>::load(Gq + j * NP + ta * TP, va);
+                        TileVec<S, T>::load(Gq + j * NP + tb * TP, vb);
 #pragma unroll
-                        for (int x = 0; x < TA; ++x) ga[j][x] = wq * Gq[j * N + a0 + x];
+                        for (int x = 0; x < T; ++x)
 #pragma unroll
-                        for (int y = 0; y < TB; ++y) gb[j][y] = Gq[j * N + b0 + y];
+                            for (int y = 0; y < T; ++y) acc[0][0][x][y] = fma(wq * va[x], vb[y], acc[0][0][x][y]);
                     }
-#pragma unroll
-                    for (int j = 0; j < 3; ++j)
-#pragma unroll
-                        for (int l = 0; l < 3; ++l)
-#pragma unroll
-                            for (int x = 0; x < TA; ++x)
-#pragma unroll
-                                for (int y = 0; y < TB; ++y) acc[j][l][x][y] = fma(ga[j][x], gb[l][y], acc[j][l][x][y]);
-                }
-                const T *C = sC + el * 81;
-                if (mkind == FE_MAT_LAME) {
-                    const T lam = C[0 * 27 + 0 * 9 + 1 * 3 + 1];   // C_0011 = lambda
-                    const T mu = C[0 * 27 + 1 * 9 + 0 * 3 + 1];    // C_0101 = mu
-#pragma unroll
-                    for (int x = 0; x < TA; ++x)
-#pragma unroll
-                        for (int y = 0; y < TB; ++y) {
-                            const T tr = acc[0][0][x][y] + acc[1][1][x][y] + acc[2][2][x][y];
-#pragma unroll
-                            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                                for (int k = 0; k < 3; ++k) {
-                                    T v = lam * acc[i][k][x][y] + mu * acc[k][i][x][y];
-                                    if (i == k) v += mu * tr;
-                                    Ke[(long long)(i * N + a0 + x) * nrow + k * N + b0 + y] = v;
-                                }
-                        }
                 } else {
 #pragma unroll
-                    for (int x = 0; x < TA; ++x)
+                    for (int j = 0; j < NDIR; ++j) {
+                        TileVec<S, T>::load(Gq + j * NP + ta * TP, ga[j]);
+                        TileVec<S, T>::load(Gq + j * NP + tb * TP, gb[j]);
 #pragma unroll
-                        for (int y = 0; y < TB; ++y)
+                        for (int x = 0; x < T; ++x) ga[j][x] *= wq;
+                    }
 #pragma unroll
-                            for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < NDIR; ++j)
 #pragma unroll
-                                for (int k = 0; k < 3; ++k) {
-                                    T v = 0;
+                        for (int l = 0; l < NDIR; ++l)
+#pragma unroll
+                            for (int x = 0; x < T; ++x)
+#pragma unroll
+                                for (int y = 0; y < T; ++y) acc[j][l][x][y] = fma(ga[j][x], gb[l][y], acc[j][l][x][y]);
+                }
+            }
+        }
+
+        // ---- epilogue: element-matrix entries of this tile and its mirror image
+        S *Kst = nullptr;
+        long long kbase = 0;
+        int shift = 0;
+        if constexpr (STAGE) {
+            __syncthreads();  // everyone is done reading G: reuse the buffer for K
+            kbase = e0 * (long long)nrow * nrow;
+            // stage at the same offset modulo 16 bytes as the global destination
+            shift = (int)(((unsigned long long)(K + kbase) % 16) / sizeof(S));
+            Kst = sK + shift;
+        }
+        auto put = [&](int r, int c, S v) {
+            if constexpr (STAGE)
+                Kst[(long long)el * nrow * nrow + r * nrow + c] = v;
+            else
+                K[(e0 + el) * (long long)nrow * nrow + (long long)r * nrow + c] = v;
+        };
+        if (active) {
+            const int a0 = ta * T, b0 = tb * T;
+            const bool mirror = ta != tb;
+            if constexpr (KIND == FK_ELASTICITY) {
+                const S *C = sC + el * 81;  // general D: C_ijkl read from shared memory
+                S lam = 0, mu = 0;
+                if constexpr (MATK == 1) {
+                    lam = sC[el * 2];
+                    mu = sC[el * 2 + 1];
+                }
+#pragma unroll
+                for (int x = 0; x < T; ++x)
+#pragma unroll
+                    for (int y = 0; y < T; ++y) {
+                        const S tr = acc[0][0][x][y] + acc[1][1][x][y] + acc[2][2][x][y];
+#pragma unroll
+                        for (int i = 0; i < 3; ++i)
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                S v;
+                                if constexpr (MATK == 1) {
+                                    v = lam * acc[i][k][x][y] + mu * acc[k][i][x][y];
+                                    if (i == k) v += mu * tr;
+                                } else {
+                                    v = 0;
 #pragma unroll
                                     for (int j = 0; j < 3; ++j)
 #pragma unroll
                                         for (int l = 0; l < 3; ++l) v = fma(C[i * 27 + j * 9 + k * 3 + l], acc[j][l][x][y], v);
-                                    Ke[(long long)(i * N + a0 + x) * nrow + k * N + b0 + y] = v;
                                 }
-                }
-            } else {
-                T acc[TA][TB];
+                                put(i * N + a0 + x, k * N + b0 + y, v);
+                                // K is symmetric for symmetric D; for a general D the
+                                // mirror entry is the transposed contraction
+                                if (mirror) {
+                                    S vt;
+                                    if constexpr (MATK == 1) {
+                                        vt = v;
+                                    } else {
+                                        vt = 0;
 #pragma unroll
-                for (int x = 0; x < TA; ++x)
+                                        for (int j = 0; j < 3; ++j)
 #pragma unroll
-                    for (int y = 0; y < TB; ++y) acc[x][y] = 0;
-                for (int q = 0; q < Q; ++q) {
-                    const T wq = Wq[q];
-                    if constexpr (KIND == FK_LAPLACE) {
-                        const T *Gq = sG + (el * Q + q) * 3 * N;
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) {
-                            T ga[TA], gb[TB];
-#pragma unroll
-                            for (int x = 0; x < TA; ++x) ga[x] = wq * Gq[j * N + a0 + x];
-#pragma unroll
-                            for (int y = 0; y < TB; ++y) gb[y] = Gq[j * N + b0 + y];
-#pragma unroll
-                            for (int x = 0; x < TA; ++x)
-#pragma unroll
-                                for (int y = 0; y < TB; ++y) acc[x][y] = fma(ga[x], gb[y], acc[x][y]);
-                        }
-                    } else {
-                        const T *Pq = sG + q * N;
-                        T pa[TA], pb[TB];
-#pragma unroll
-                        for (int x = 0; x < TA; ++x) pa[x] = wq * Pq[a0 + x];
-#pragma unroll
-                        for (int y = 0; y < TB; ++y) pb[y] = Pq[b0 + y];
-#pragma unroll
-                        for (int x = 0; x < TA; ++x)
-#pragma unroll
-                            for (int y = 0; y < TB; ++y) acc[x][y] = fma(pa[x], pb[y], acc[x][y]);
+                                            for (int l = 0; l < 3; ++l)
+                                                vt = fma(C[k * 27 + l * 9 + i * 3 + j], acc[j][l][x][y], vt);
+                                    }
+                                    put(k * N + b0 + y, i * N + a0 + x, vt);
+                                }
+                            }
                     }
-                }
-                const T c = sC[el];
-                for (int r = 0; r < ncomp; ++r)
-                    for (int s2 = 0; s2 < ncomp; ++s2)
+            } else {
+                const S c = sC[el];
 #pragma unroll
-                        for (int x = 0; x < TA; ++x)
+                for (int x = 0; x < T; ++x)
 #pragma unroll
-                            for (int y = 0; y < TB; ++y)
-                                Ke[(long long)(r * N + a0 + x) * nrow + s2 * N + b0 + y] = (r == s2) ? c * acc[x][y] : (T)0;
+                    for (int y = 0; y < T; ++y) {
+                        const S v = c * acc[0][0][x][y];
+                        for (int r = 0; r < ncomp; ++r)
+                            for (int s2 = 0; s2 < ncomp; ++s2) {
+                                const S vv = r == s2 ? v : (S)0;
+                                put(r * N + a0 + x, s2 * N + b0 + y, vv);
+                                if (mirror) put(s2 * N + b0 + y, r * N + a0 + x, vv);
+                            }
+                    }
             }
+        }
+        if constexpr (STAGE) {
+            __syncthreads();
+            // coalesced 16-byte streaming stores of the ne contiguous matrices
+            constexpr int V = 16 / (int)sizeof(S);
+            const long long total = (long long)ne * nrow * nrow;
+            const int head = (int)((V - shift) % V);  // scalars before the first aligned vector
+            S *Kg = K + kbase;
+            for (int i = threadIdx.x; i < head && i < total; i += THREADS) Kg[i] = Kst[i];
+            const long long nvec = (total - head) / V;
+            const float4 *src = reinterpret_cast<const float4 *>(Kst + head);
+            float4 *dst = reinterpret_cast<float4 *>(Kg + head);
+            for (long long i = threadIdx.x; i < nvec; i += THREADS) __stcs(dst + i, src[i]);
+            for (long long i = head + nvec * V + threadIdx.x; i < total; i += THREADS) Kg[i] = Kst[i];
         }
     }
 }
 
-template <typename T, int N, int Q, int KIND, int TA, int TB, int EPB, int THREADS>
-cudaError_t launch_simt(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, void *K, int sm_count,
-                        cudaStream_t s)
+template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, bool STAGE>
+cudaError_t launch_sym(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, void *K, int sm_count,
+                       cudaStream_t s)
 {
-    constexpr bool GRAD = KIND != FK_MASS;
-    const size_t smem = sizeof(T) * ((GRAD ? (size_t)EPB * Q * 3 * N : (size_t)Q * N) + (size_t)EPB * Q * 9 +
-                                     (size_t)EPB * Q + (size_t)EPB * 81);
-    auto kern = k_matrix_simt<T, N, Q, KIND, TA, TB, EPB, THREADS>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    using P = MatrixSmem<S, N, Q, KIND, T, EPB, STAGE>;
+    static_assert(EPB * (N / T) * (N / T + 1) / 2 <= THREADS, "one tile per thread");
+    static_assert(P::BYTES <= 227 * 1024, "shared memory plan exceeds one CTA's limit");
+    auto kern = k_matrix_sym<S, N, Q, KIND, MATK, T, EPB, THREADS, STAGE>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::BYTES);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, P::BYTES);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long E = g->mesh.n_elems;
     long long blocks = (E + EPB - 1) / EPB;
-    const long long cap = (long long)per_sm * sm_count * 8;
+    const long long cap = (long long)per_sm * sm_count * 4;
     if (blocks > cap) blocks = cap;
-    const bool f64 = sizeof(T) == 8;
-    const T *jinv = f64 ? (const T *)g->d_jinv64 : (const T *)g->d_jinv32;
-    const T *wdetj = f64 ? (const T *)g->d_wdetj64 : (const T *)g->d_wdetj32;
-    const T *dphi = f64 ? (const T *)g->d_dphi64 : (const T *)g->d_dphi32;
-    const T *phi = f64 ? (const T *)g->d_phi64 : (const T *)g->d_phi32;
-    kern<<<(unsigned)blocks, THREADS, smem, s>>>(jinv, wdetj, dphi, phi, E, f->ncomp, mat.kind, mat.data,
-                                                  mat.transposed, (T *)K);
+    const bool f64 = sizeof(S) == 8;
+    const S *jinv = f64 ? (const S *)g->d_jinv64 : (const S *)g->d_jinv32;
+    const S *wdetj = f64 ? (const S *)g->d_wdetj64 : (const S *)g->d_wdetj32;
+    const S *dphi = f64 ? (const S *)g->d_dphi64 : (const S *)g->d_dphi32;
+    const S *phi = f64 ? (const S *)g->d_phi64 : (const S *)g->d_phi32;
+    kern<<<(unsigned)blocks, THREADS, P::BYTES, s>>>(jinv, wdetj, dphi, phi, E, f->ncomp, mat.data, mat.transposed,
+                                                      (S *)K);
     return cudaGetLastError();
 }
 
-template <typename T>
+// Tile shapes: T x T node tiles, EPB elements per CTA, one upper-triangle tile
+// per thread; Laplace/mass (L) and elasticity (E) configured separately.
+// K is staged in shared memory unless it would not fit.
+template <typename S, int N, int Q, int T_L, int EPB_L, int THR_L, bool STAGE_L, int T_E, int EPB_E, int THR_E,
+          bool STAGE_E>
+cudaError_t dispatch_nq(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, void *K, int sm,
+                        cudaStream_t s)
+{
+    switch (f->kind) {
+    case FK_LAPLACE: return launch_sym<S, N, Q, FK_LAPLACE, 0, T_L, EPB_L, THR_L, STAGE_L>(g, f, mat, K, sm, s);
+    case FK_MASS: return launch_sym<S, N, Q, FK_MASS, 0, T_L, EPB_L, THR_L, STAGE_L>(g, f, mat, K, sm, s);
+    case FK_ELASTICITY:
+        if (mat.kind == FE_MAT_LAME)
+            return launch_sym<S, N, Q, FK_ELASTICITY, 1, T_E, EPB_E, THR_E, STAGE_E>(g, f, mat, K, sm, s);
+        return launch_sym<S, N, Q, FK_ELASTICITY, 2, T_E, EPB_E, THR_E, STAGE_E>(g, f, mat, K, sm, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename S>
 cudaError_t dispatch(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, void *K, int sm,
                      cudaStream_t s)
 {
     const int N = g->N, Q = g->Q;
-#define FE_CASE(NN, QQ, TA_, TB_, EPB_L, EPB_E, THR)                                                                 \
-    if (N == NN && Q == QQ) {                                                                                       \
-        switch (f->kind) {                                                                                          \
-        case FK_LAPLACE: return launch_simt<T, NN, QQ, FK_LAPLACE, TA_, TB_, EPB_L, THR>(g, f, mat, K, sm, s);       \
-        case FK_MASS: return launch_simt<T, NN, QQ, FK_MASS, TA_, TB_, EPB_L, THR>(g, f, mat, K, sm, s);             \
-        case FK_ELASTICITY: return launch_simt<T, NN, QQ, FK_ELASTICITY, TA_, TB_, EPB_E, THR>(g, f, mat, K, sm, s); \
-        }                                                                                                           \
+    constexpr bool D = sizeof(S) == 8;
+    // Q1: 2x2 tiles, 10 upper tiles per element, 12 elements per CTA
+    if (N == 8 && Q == 8) return dispatch_nq<S, 8, 8, 2, 12, 128, true, 2, 12, 128, true>(g, f, mat, K, sm, s);
+    if (N == 8 && Q == 27) return dispatch_nq<S, 8, 27, 2, 12, 128, true, 2, 12, 128, true>(g, f, mat, K, sm, s);
+    // Q2: 3x3 tiles, 45 upper tiles per element, 2 elements per 96-thread CTA;
+    // FP64 elasticity writes directly (2 x 52 KB of staging would leave one CTA per SM)
+    if (N == 27 && Q == 27) return dispatch_nq<S, 27, 27, 3, 2, 96, true, 3, 2, 96, !D>(g, f, mat, K, sm, s);
+    if (N == 27 && Q == 64) return dispatch_nq<S, 27, 64, 3, 2, 96, true, 3, 2, 96, false>(g, f, mat, K, sm, s);
+    // Q3: 4x4 tiles (136 per element) for FP32 and the scalar forms; FP64
+    // elasticity needs 2x2 tiles (528 per element) to keep 36 accumulators
+    if (N == 64 && Q == 64) {
+        if constexpr (D)
+            return dispatch_nq<S, 64, 64, 4, 1, 160, false, 2, 1, 544, false>(g, f, mat, K, sm, s);
+        else
+            return dispatch_nq<S, 64, 64, 4, 1, 160, true, 4, 1, 160, false>(g, f, mat, K, sm, s);
     }
-    FE_CASE(8, 8, 2, 2, 8, 8, 128)
-    FE_CASE(8, 27, 2, 2, 8, 4, 128)
-    FE_CASE(27, 27, 3, 3, 3, 3, 256)
-    FE_CASE(27, 64, 3, 3, 2, 1, 256)
-    // 4 x 4 FP64 tiles would need 288 accumulator registers: halve TB there
-    FE_CASE(64, 64, 4, (sizeof(T) == 8 ? 2 : 4), 1, 1, 256)
-#undef FE_CASE
     return cudaErrorInvalidValue;
 }
 
