@@ -153,8 +153,9 @@ class Workload:
         self.coords = torch.from_numpy(self.mesh.coords).to(device)
         self.conn = torch.from_numpy(self.mesh.conn).to(device)
         self.m = fe.Mesh(self.coords, self.conn)
-        self.pts, self.w, self.phi, self.dphi = fe.refbasis_hex(2, 3)
-        self.geom = fe.geometry(self.ctx, self.m, self.phi, self.dphi, self.w)
+        # each path keeps only the geometry copy it reads
+        self.geoms = {"f64": fe.hex_geometry(self.ctx, self.m, 2, 3, flags=fe.GEOM_STORE_F64),
+                      "f32": fe.hex_geometry(self.ctx, self.m, 2, 3, flags=fe.GEOM_STORE_F32)}
         self.form = fe.elasticity_form(fe.MAT_LAME)
         self.mat = torch.from_numpy(np.stack([self.lam, self.mu], 1)).to(device)
         self.u64 = torch.from_numpy(self.u).to(device)
@@ -181,13 +182,14 @@ class Workload:
         fe = self.fe
         K, r, g = self.outputs(prec)
         u = self.u64 if prec == "f64" else self.u32
-        self.geom.update()
+        geom = self.geoms["f64" if prec == "f64" else "f32"]
+        geom.update()
         if mk_events:
             mk_events[0].record()
-        fe.eval_matrix(self.ctx, self.form, self.geom, [self.mat, None, None], prec, out=K)
+        fe.eval_matrix(self.ctx, self.form, geom, [self.mat, None, None], prec, out=K)
         if mk_events:
             mk_events[1].record()
-        fe.eval_residual(self.ctx, self.form, self.geom, [self.mat, None, u], prec, out=r)
+        fe.eval_residual(self.ctx, self.form, geom, [self.mat, None, u], prec, out=r)
         fe.assemble_vector(self.ctx, self.asm, 3, r, prec, out=g,
                            flags=0 if prec == "f64" else fe.ASSEMBLE_COMPENSATED)
 

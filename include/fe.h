@@ -105,12 +105,22 @@ typedef struct {
 /* Reference basis tabulated at the quadrature points: host arrays.
  * phi (n_qp, n_basis), dphi (n_qp, 3, n_basis) with dphi[q][k][a] = d phi_a / d xi_k.
  * The same basis maps the geometry and approximates the fields (isoparametric
- * elements, Sec. 4.1 footnote). */
+ * elements, Sec. 4.1 footnote).
+ * Optional tensor-product factors (set b1d = d1d = NULL if the basis is not a
+ * tensor product): b1d (nq1d, n1d) and d1d (nq1d, n1d) hold the 1-D basis
+ * values and derivatives at the 1-D points, with phi[q][a] = b1d[qx][i]
+ * b1d[qy][j] b1d[qz][k] for a = i + n1d (j + n1d k), q = qx + nq1d (qy + nq1d qz).
+ * When given (and consistent with phi and dphi, which fe_geometry checks), the
+ * geometry kernel uses sum factorisation: about 3x fewer FP64 operations for Q2. */
 typedef struct {
     int n_basis;
     int n_qp;
     const double *phi;
     const double *dphi;
+    int n1d;
+    int nq1d;
+    const double *b1d;
+    const double *d1d;
 } fe_refbasis;
 
 /* Quadrature rule on the reference element: host arrays points (n_qp, 3), weights (n_qp). */
@@ -156,6 +166,11 @@ const char *fe_last_error_message(void);
  * phi (nq^3, (p+1)^3), dphi (nq^3, 3, (p+1)^3).  Any output pointer may be
  * NULL.  Supports 1 <= p <= 4, 1 <= nq <= 10; otherwise FE_ERR_SHAPE. */
 fe_status fe_refbasis_hex(int p, int nq, double *points, double *weights, double *phi, double *dphi);
+
+/* The 1-D factors of fe_refbasis_hex: host arrays b1d (nq, p+1) with the
+ * Lagrange basis values at the Gauss points on [0,1], d1d (nq, p+1) with their
+ * derivatives.  Same limits as fe_refbasis_hex. */
+fe_status fe_refbasis_hex_1d(int p, int nq, double *b1d, double *d1d);
 
 /* ---- geometry ----------------------------------------------------------------- */
 

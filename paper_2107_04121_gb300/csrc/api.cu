@@ -48,6 +48,8 @@ void free_geometry(fe_geometry_h *g)
     cudaFree(g->d_phi64);
     cudaFree(g->d_dphi64);
     cudaFree(g->d_w64);
+    cudaFree(g->d_b1d);
+    cudaFree(g->d_d1d);
     cudaFree(g->d_phi32);
     cudaFree(g->d_dphi32);
     cudaFree(g->d_jinv64);
@@ -150,6 +152,11 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
     if (flags == 0) flags = FE_GEOM_STORE_F64 | FE_GEOM_STORE_F32;
     const int N = basis->n_basis, Q = basis->n_qp;
     if (N != mesh->nodes_per_elem || quad->n_qp != Q || !fe_supported_nq(N, Q)) return FE_ERR_SHAPE;
+    const bool tensor = basis->b1d || basis->d1d;
+    if (tensor && (!basis->b1d || !basis->d1d || !fe_host_check_tensor_basis(basis))) {
+        std::snprintf(g_last_error, sizeof(g_last_error), "fe_geometry: 1-D factors do not reproduce phi/dphi");
+        return FE_ERR_INVALID_ARG;
+    }
     cudaSetDevice(ctx->device);
     cudaStream_t s = to_cuda(stream);
     fe_geometry_h *g = new (std::nothrow) fe_geometry_h();
@@ -169,6 +176,15 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
     if (e == cudaSuccess) e = dev_alloc(&g->d_w64, (size_t)Q);
     if (e == cudaSuccess) e = dev_alloc(&g->d_phi32, (size_t)Q * N);
     if (e == cudaSuccess) e = dev_alloc(&g->d_dphi32, (size_t)Q * 3 * N);
+    if (e == cudaSuccess && tensor) {
+        g->n1d = basis->n1d;
+        g->nq1d = basis->nq1d;
+        const size_t n = (size_t)basis->n1d * basis->nq1d;
+        e = dev_alloc(&g->d_b1d, n);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_d1d, n);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_b1d, basis->b1d, sizeof(double) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_d1d, basis->d1d, sizeof(double) * n, cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess && (flags & FE_GEOM_STORE_F64)) {
         e = dev_alloc(&g->d_jinv64, (size_t)E * Q * 9);
         if (e == cudaSuccess) e = dev_alloc(&g->d_wdetj64, (size_t)E * Q);

@@ -24,6 +24,8 @@ struct fe_geometry_h {
     int N, Q;
     unsigned flags;
     double *d_phi64, *d_dphi64, *d_w64;  // (Q,N), (Q,3,N), (Q)
+    int n1d, nq1d;                       // tensor-product factors (sum-factorised geometry)
+    double *d_b1d, *d_d1d;               // (nq1d, n1d) each, or null
     float *d_phi32, *d_dphi32;
     double *d_jinv64, *d_wdetj64;  // (E,Q,3,3), (E,Q)
     float *d_jinv32, *d_wdetj32;
@@ -77,3 +79,4 @@ bool fe_supported_nq(int N, int Q);
 
 // Host reference element (refelem.cpp).
 int fe_host_gauss_legendre01(int n, double *x, double *w);
+bool fe_host_check_tensor_basis(const fe_refbasis *b);

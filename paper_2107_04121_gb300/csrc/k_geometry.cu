@@ -2,16 +2,159 @@
 // arXiv 2107.04121): J_ik = sum_a x_a,i d phi_a / d xi_k, det J, J^-1 and
 // w_q det J for every element and quadrature point, in FP64.
 //
-// One thread per (element, quadrature point); consecutive threads share an
-// element, so the gathered nodal coordinates are broadcast within a warp and
-// served from L1.  The reference gradients (Q, 3, N) sit in shared memory.
-// The kernel is FP64-pipe bound on GB300 (about 9N + 40 FP64 operations per
-// thread against 80 bytes written).
+// Both kernels are FP64-pipe bound on GB300 (FP64 runs at 1/61 of the FP32
+// rate there), so what matters is the FP64 operation count:
+//  - k_geometry_sf (tensor-product bases): J by sum factorisation, three
+//    1-D contractions per coordinate and derivative direction, 2 n1 nq (n1^2 +
+//    n1 nq + nq^2)... for Q2 1,944 DFMA per element instead of 6,561;
+//  - k_geometry (any tabulated basis): one thread per (element, quadrature
+//    point), J = sum_a x_a (x) grad phi_a directly (9N DFMA per point).
+// Both finish each point with the same cofactor inverse (about 40 FP64
+// operations).
 #include "fe_device.cuh"
 
 namespace {
 
 constexpr int kGeomThreads = 256;
+
+// det J, J^-1 = adj(J) / det J and w det J at one quadrature point; stores the
+// float64 and/or float32 copies.  J[c][m] = d x_c / d xi_m.
+__device__ __forceinline__ void finish_point(const double J[3][3], double wq, long long e, long long idx,
+                                             double *__restrict__ jinv64, double *__restrict__ wdetj64,
+                                             float *__restrict__ jinv32, float *__restrict__ wdetj32,
+                                             unsigned long long *__restrict__ status)
+{
+    const double J00 = J[0][0], J01 = J[0][1], J02 = J[0][2], J10 = J[1][0], J11 = J[1][1], J12 = J[1][2],
+                 J20 = J[2][0], J21 = J[2][1], J22 = J[2][2];
+    const double c00 = J11 * J22 - J12 * J21;
+    const double c01 = J12 * J20 - J10 * J22;
+    const double c02 = J10 * J21 - J11 * J20;
+    const double det = J00 * c00 + J01 * c01 + J02 * c02;
+    if (!(det > 0.0) || !isfinite(det)) fe_report(status, isfinite(det) ? FE_ERR_NONPOSITIVE_DETJ : FE_ERR_NONFINITE, e);
+    const double r = 1.0 / det;
+    double inv[9];
+    inv[0] = c00 * r;
+    inv[3] = c01 * r;
+    inv[6] = c02 * r;
+    inv[1] = (J02 * J21 - J01 * J22) * r;
+    inv[4] = (J00 * J22 - J02 * J20) * r;
+    inv[7] = (J01 * J20 - J00 * J21) * r;
+    inv[2] = (J01 * J12 - J02 * J11) * r;
+    inv[5] = (J02 * J10 - J00 * J12) * r;
+    inv[8] = (J00 * J11 - J01 * J10) * r;
+    const double wd = wq * det;
+    if (jinv64) {
+        double *o = jinv64 + idx * 9;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) o[k] = inv[k];
+        wdetj64[idx] = wd;
+    }
+    if (jinv32) {
+        float *o = jinv32 + idx * 9;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) o[k] = (float)inv[k];
+        wdetj32[idx] = (float)wd;
+    }
+}
+
+// Sum-factorised geometry of tensor-product hexahedra: n1 nodes and nq points
+// per axis, b1d/d1d the 1-D basis values and derivatives (nq, n1).  Per element
+// and coordinate c, with X[k][j][i] the nodal values:
+//   U0 = B_x X, U1 = D_x X                          (contract i)
+//   V_DB = B_y U1, V_BD = D_y U0, V_BB = B_y U0     (contract j)
+//   J[c][0] = B_z V_DB, J[c][1] = B_z V_BD, J[c][2] = D_z V_BB   (contract k)
+template <int N1, int NQ, int EPB>
+__global__ void __launch_bounds__(kGeomThreads) k_geometry_sf(const double *__restrict__ coords,
+                                                              const int32_t *__restrict__ conn, long long E,
+                                                              long long n_nodes, const double *__restrict__ b1d,
+                                                              const double *__restrict__ d1d,
+                                                              const double *__restrict__ w,
+                                                              double *__restrict__ jinv64, double *__restrict__ wdetj64,
+                                                              float *__restrict__ jinv32, float *__restrict__ wdetj32,
+                                                              unsigned long long *__restrict__ status)
+{
+    constexpr int N = N1 * N1 * N1, Q = NQ * NQ * NQ;
+    static_assert(8 * (2 * NQ * N1 + EPB * (3 * N + 6 * N1 * N1 * NQ + 9 * N1 * NQ * NQ + 9 * Q)) <= 48 * 1024,
+                  "static shared memory above 48 KB");
+    __shared__ double sB[NQ][N1], sD[NQ][N1];
+    __shared__ double sX[EPB][3][N];              // [k][j][i]
+    __shared__ double sU[EPB][2][3][N1][N1][NQ];  // [k][j][qx]
+    __shared__ double sV[EPB][3][3][N1][NQ][NQ];  // [which][c][k][qy][qx]
+    __shared__ double sJ[EPB][Q][9];
+    for (int i = threadIdx.x; i < NQ * N1; i += blockDim.x) {
+        sB[i / N1][i % N1] = b1d[i];
+        sD[i / N1][i % N1] = d1d[i];
+    }
+    for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
+        const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * N; t += blockDim.x) {
+            const int el = t / N, a = t % N;
+            long long node = conn[(e0 + el) * N + a];
+            if ((unsigned long long)node >= (unsigned long long)n_nodes) {  // never read outside coords
+                fe_report(status, FE_ERR_SHAPE, e0 + el);
+                node = 0;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sX[el][c][a] = coords[3 * node + c];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 3 * N1 * N1 * NQ; t += blockDim.x) {
+            const int qx = t % NQ, j = (t / NQ) % N1, k = (t / (NQ * N1)) % N1, c = (t / (NQ * N1 * N1)) % 3,
+                      el = t / (NQ * N1 * N1 * 3);
+            const double *x = &sX[el][c][(k * N1 + j) * N1];
+            double u0 = 0.0, u1 = 0.0;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                u0 = fma(sB[qx][i], x[i], u0);
+                u1 = fma(sD[qx][i], x[i], u1);
+            }
+            sU[el][0][c][k][j][qx] = u0;
+            sU[el][1][c][k][j][qx] = u1;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 3 * N1 * NQ * NQ; t += blockDim.x) {
+            const int qx = t % NQ, qy = (t / NQ) % NQ, k = (t / (NQ * NQ)) % N1, c = (t / (NQ * NQ * N1)) % 3,
+                      el = t / (NQ * NQ * N1 * 3);
+            double vdb = 0.0, vbd = 0.0, vbb = 0.0;
+#pragma unroll
+            for (int j = 0; j < N1; ++j) {
+                const double u0 = sU[el][0][c][k][j][qx], u1 = sU[el][1][c][k][j][qx];
+                vdb = fma(sB[qy][j], u1, vdb);
+                vbd = fma(sD[qy][j], u0, vbd);
+                vbb = fma(sB[qy][j], u0, vbb);
+            }
+            sV[el][0][c][k][qy][qx] = vdb;
+            sV[el][1][c][k][qy][qx] = vbd;
+            sV[el][2][c][k][qy][qx] = vbb;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 3 * Q; t += blockDim.x) {
+            const int qx = t % NQ, qy = (t / NQ) % NQ, qz = (t / (NQ * NQ)) % NQ, c = (t / Q) % 3, el = t / (3 * Q);
+            double j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                j0 = fma(sB[qz][k], sV[el][0][c][k][qy][qx], j0);
+                j1 = fma(sB[qz][k], sV[el][1][c][k][qy][qx], j1);
+                j2 = fma(sD[qz][k], sV[el][2][c][k][qy][qx], j2);
+            }
+            double *Jo = sJ[el][qx + NQ * (qy + NQ * qz)] + c * 3;
+            Jo[0] = j0;
+            Jo[1] = j1;
+            Jo[2] = j2;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * Q; t += blockDim.x) {
+            const int el = t / Q, q = t % Q;
+            double J[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) J[c][m] = sJ[el][q][c * 3 + m];
+            finish_point(J, w[q], e0 + el, (e0 + el) * Q + q, jinv64, wdetj64, jinv32, wdetj32, status);
+        }
+    }
+}
 
 template <int N>
 __global__ void __launch_bounds__(kGeomThreads) k_geometry(const double *__restrict__ coords,
@@ -56,37 +199,8 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry(const double *__restr
             J21 = fma(x2, g1, J21);
             J22 = fma(x2, g2, J22);
         }
-        // cofactors and determinant (expansion along the first row)
-        const double c00 = J11 * J22 - J12 * J21;
-        const double c01 = J12 * J20 - J10 * J22;
-        const double c02 = J10 * J21 - J11 * J20;
-        const double det = J00 * c00 + J01 * c01 + J02 * c02;
-        if (!(det > 0.0) || !isfinite(det)) fe_report(status, isfinite(det) ? FE_ERR_NONPOSITIVE_DETJ : FE_ERR_NONFINITE, e);
-        const double r = 1.0 / det;
-        // J^-1 = adj(J) / det, adj = cof^T
-        double inv[9];
-        inv[0] = c00 * r;
-        inv[3] = c01 * r;
-        inv[6] = c02 * r;
-        inv[1] = (J02 * J21 - J01 * J22) * r;
-        inv[4] = (J00 * J22 - J02 * J20) * r;
-        inv[7] = (J01 * J20 - J00 * J21) * r;
-        inv[2] = (J01 * J12 - J02 * J11) * r;
-        inv[5] = (J02 * J10 - J00 * J12) * r;
-        inv[8] = (J00 * J11 - J01 * J10) * r;
-        const double wd = w[q] * det;
-        if (jinv64) {
-            double *o = jinv64 + idx * 9;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) o[k] = inv[k];
-            wdetj64[idx] = wd;
-        }
-        if (jinv32) {
-            float *o = jinv32 + idx * 9;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) o[k] = (float)inv[k];
-            wdetj32[idx] = (float)wd;
-        }
+        const double J[3][3] = {{J00, J01, J02}, {J10, J11, J12}, {J20, J21, J22}};
+        finish_point(J, w[q], e, idx, jinv64, wdetj64, jinv32, wdetj32, status);
     }
 }
 
@@ -128,11 +242,38 @@ cudaError_t launch_geom(const fe_geometry_h *g, unsigned long long *st, cudaStre
     return cudaGetLastError();
 }
 
+template <int N1, int NQ, int EPB>
+cudaError_t launch_geom_sf(const fe_geometry_h *g, unsigned long long *st, cudaStream_t s)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_geometry_sf<N1, NQ, EPB>, kGeomThreads, 0);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    long long blocks = (g->mesh.n_elems + EPB - 1) / EPB;
+    if (blocks > (long long)per_sm * sms * 8) blocks = (long long)per_sm * sms * 8;
+    const bool f64 = g->flags & FE_GEOM_STORE_F64, f32 = g->flags & FE_GEOM_STORE_F32;
+    k_geometry_sf<N1, NQ, EPB><<<(unsigned)blocks, kGeomThreads, 0, s>>>(
+        g->mesh.coords, g->mesh.conn, g->mesh.n_elems, g->mesh.n_nodes, g->d_b1d, g->d_d1d, g->d_w64,
+        f64 ? g->d_jinv64 : nullptr, f64 ? g->d_wdetj64 : nullptr, f32 ? g->d_jinv32 : nullptr,
+        f32 ? g->d_wdetj32 : nullptr, st);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *st, cudaStream_t s)
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
+    if (g->d_b1d) {
+        const int n1 = g->n1d, nq = g->nq1d;
+        if (n1 == 2 && nq == 2) return launch_geom_sf<2, 2, 16>(g, st, s);
+        if (n1 == 2 && nq == 3) return launch_geom_sf<2, 3, 8>(g, st, s);
+        if (n1 == 3 && nq == 3) return launch_geom_sf<3, 3, 8>(g, st, s);
+        if (n1 == 3 && nq == 4) return launch_geom_sf<3, 4, 4>(g, st, s);
+        if (n1 == 4 && nq == 4) return launch_geom_sf<4, 4, 2>(g, st, s);
+    }
     switch (g->N) {
     case 8: return launch_geom<8>(g, st, s);
     case 27: return launch_geom<27>(g, st, s);

@@ -129,3 +129,42 @@ extern "C" fe_status fe_refbasis_hex(int p, int nq, double *points, double *weig
     (void)Q;
     return FE_OK;
 }
+
+extern "C" fe_status fe_refbasis_hex_1d(int p, int nq, double *b1d, double *d1d)
+{
+    if (p < 1 || p > 4 || nq < 1 || nq > 10 || !b1d || !d1d) return p < 1 || p > 4 || nq < 1 || nq > 10
+                                                                          ? FE_ERR_SHAPE
+                                                                          : FE_ERR_INVALID_ARG;
+    double g[16], gw[16];
+    if (fe_host_gauss_legendre01(nq, g, gw)) return FE_ERR_SHAPE;
+    for (int q = 0; q < nq; ++q)
+        for (int k = 0; k <= p; ++k) lagrange1d(p, k, g[q], &b1d[q * (p + 1) + k], &d1d[q * (p + 1) + k]);
+    return FE_OK;
+}
+
+// Does the tensor product of the 1-D factors reproduce the 3-D tables?
+bool fe_host_check_tensor_basis(const fe_refbasis *b)
+{
+    const int n1 = b->n1d, nq = b->nq1d;
+    if (n1 < 1 || nq < 1 || n1 * n1 * n1 != b->n_basis || nq * nq * nq != b->n_qp) return false;
+    double scale = 0.0;
+    for (int i = 0; i < b->n_qp * 3 * b->n_basis; ++i) scale = std::fmax(scale, std::fabs(b->dphi[i]));
+    for (int i = 0; i < b->n_qp * b->n_basis; ++i) scale = std::fmax(scale, std::fabs(b->phi[i]));
+    const double tol = 1e-13 * (scale > 1.0 ? scale : 1.0);
+    for (int qz = 0; qz < nq; ++qz)
+        for (int qy = 0; qy < nq; ++qy)
+            for (int qx = 0; qx < nq; ++qx)
+                for (int k = 0; k < n1; ++k)
+                    for (int j = 0; j < n1; ++j)
+                        for (int i = 0; i < n1; ++i) {
+                            const int q = qx + nq * (qy + nq * qz), a = i + n1 * (j + n1 * k);
+                            const double bx = b->b1d[qx * n1 + i], by = b->b1d[qy * n1 + j], bz = b->b1d[qz * n1 + k];
+                            const double dx = b->d1d[qx * n1 + i], dy = b->d1d[qy * n1 + j], dz = b->d1d[qz * n1 + k];
+                            const size_t N = b->n_basis;
+                            if (std::fabs(b->phi[q * N + a] - bx * by * bz) > tol) return false;
+                            if (std::fabs(b->dphi[(q * 3 + 0) * N + a] - dx * by * bz) > tol) return false;
+                            if (std::fabs(b->dphi[(q * 3 + 1) * N + a] - bx * dy * bz) > tol) return false;
+                            if (std::fabs(b->dphi[(q * 3 + 2) * N + a] - bx * by * dz) > tol) return false;
+                        }
+    return true;
+}

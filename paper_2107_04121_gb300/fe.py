@@ -31,7 +31,7 @@ ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
 
 EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
-    "fe_refbasis_hex", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
+    "fe_refbasis_hex", "fe_refbasis_hex_1d", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
     "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_assembly_create", "fe_assembly_free",
     "fe_assemble_vector", "fe_assemble_vector_noalloc",
 ]
@@ -53,7 +53,8 @@ class _Mesh(ctypes.Structure):
 
 class _RefBasis(ctypes.Structure):
     _fields_ = [("n_basis", ctypes.c_int), ("n_qp", ctypes.c_int), ("phi", ctypes.c_void_p),
-                ("dphi", ctypes.c_void_p)]
+                ("dphi", ctypes.c_void_p), ("n1d", ctypes.c_int), ("nq1d", ctypes.c_int), ("b1d", ctypes.c_void_p),
+                ("d1d", ctypes.c_void_p)]
 
 
 class _Quad(ctypes.Structure):
@@ -85,6 +86,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_last_error_message.restype = ctypes.c_char_p
     L.fe_get_status.argtypes = [vp, vp, ctypes.POINTER(ll)]
     L.fe_refbasis_hex.argtypes = [i, i, dp, dp, dp, dp]
+    L.fe_refbasis_hex_1d.argtypes = [i, i, dp, dp]
     L.fe_geometry.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(_RefBasis), ctypes.POINTER(_Quad),
                               ctypes.c_uint, ctypes.POINTER(vp), vp]
     L.fe_geometry_update.argtypes = [vp, vp, vp]
@@ -146,6 +148,15 @@ def refbasis_hex(p: int, nq: int):
     _check(L.fe_refbasis_hex(p, nq, pts.ctypes.data_as(dp), w.ctypes.data_as(dp), phi.ctypes.data_as(dp),
                              dphi.ctypes.data_as(dp)), "fe_refbasis_hex")
     return pts, w, phi, dphi
+
+
+def refbasis_hex_1d(p: int, nq: int):
+    """1-D factors of refbasis_hex (fe_refbasis_hex_1d): b1d, d1d of shape (nq, p+1)."""
+    L = load_library()
+    b, d = np.zeros((nq, p + 1)), np.zeros((nq, p + 1))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(L.fe_refbasis_hex_1d(p, nq, b.ctypes.data_as(dp), d.ctypes.data_as(dp)), "fe_refbasis_hex_1d")
+    return b, d
 
 
 # ---- context -------------------------------------------------------------------------
@@ -239,18 +250,33 @@ class Geometry:
             pass
 
 
-def geometry(ctx: Context, mesh: Mesh, phi, dphi, weights, flags: int = 0, stream=None) -> Geometry:
-    """fe_geometry: FP64 J, det J, J^-1, w det J for every element and qp."""
+def geometry(ctx: Context, mesh: Mesh, phi, dphi, weights, flags: int = 0, stream=None, b1d=None,
+             d1d=None) -> Geometry:
+    """fe_geometry: FP64 J, det J, J^-1, w det J for every element and qp.
+    b1d/d1d (optional): tensor-product factors enabling the sum-factorised kernel."""
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     dphi = np.ascontiguousarray(dphi, dtype=np.float64)
     weights = np.ascontiguousarray(weights, dtype=np.float64)
     Q, N = phi.shape
-    basis = _RefBasis(N, Q, phi.ctypes.data, dphi.ctypes.data)
+    if b1d is not None:
+        b1d = np.ascontiguousarray(b1d, dtype=np.float64)
+        d1d = np.ascontiguousarray(d1d, dtype=np.float64)
+        basis = _RefBasis(N, Q, phi.ctypes.data, dphi.ctypes.data, b1d.shape[1], b1d.shape[0], b1d.ctypes.data,
+                          d1d.ctypes.data)
+    else:
+        basis = _RefBasis(N, Q, phi.ctypes.data, dphi.ctypes.data, 0, 0, None, None)
     quad = _Quad(Q, None, weights.ctypes.data)
     h = ctypes.c_void_p()
     _check(_lib.fe_geometry(ctx.handle, ctypes.byref(mesh.struct), ctypes.byref(basis), ctypes.byref(quad), flags,
                             ctypes.byref(h), _stream_ptr(stream)), "fe_geometry")
     return Geometry(ctx, mesh, h, N, Q)
+
+
+def hex_geometry(ctx: Context, mesh: Mesh, p: int, nq: int, flags: int = 0, stream=None) -> Geometry:
+    """fe_geometry with the library's order-p hex basis and nq^3 Gauss rule (tensor-product path)."""
+    pts, w, phi, dphi = refbasis_hex(p, nq)
+    b1d, d1d = refbasis_hex_1d(p, nq)
+    return geometry(ctx, mesh, phi, dphi, w, flags, stream, b1d, d1d)
 
 
 class Form:

@@ -32,8 +32,7 @@ class Problem:
         self.coords_d = torch.from_numpy(mesh.coords).to(device)
         self.conn_d = torch.from_numpy(mesh.conn).to(device)
         self.m = fe.Mesh(self.coords_d, self.conn_d)
-        pts, w, phi, dphi = fe.refbasis_hex(p, nq)
-        self.geom = fe.geometry(ctx, self.m, phi, dphi, w)
+        self.geom = fe.hex_geometry(ctx, self.m, p, nq)
         self.ref = oracle.RefElement(p, nq)
         self._ogeo = None
 

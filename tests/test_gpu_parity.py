@@ -41,6 +41,32 @@ def test_geometry_matches_oracle(ctx, p, n):
     np.testing.assert_array_equal(P.geom.get(fe.GEOM_JINV, "f32").cpu().numpy(), g_J.astype(np.float32))
 
 
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_direct_and_sum_factorised_geometry_agree(ctx, p):
+    """The generic kernel (tables only) and the tensor-product kernel compute the same map."""
+    mesh = meshgen.structured_hex(3, 2, 3, p, 0.15, 24)
+    P = Problem(ctx, mesh, p, p + 1)  # tensor-product path
+    pts, w, phi, dphi = fe.refbasis_hex(p, p + 1)
+    g_direct = fe.geometry(ctx, P.m, phi, dphi, w)
+    wdetJ, G, Jinv = oracle.geometry(mesh.coords, mesh.conn, P.ref, want_Jinv=True)
+    for g in (P.geom, g_direct):
+        assert np.abs(g.get(fe.GEOM_JINV, "f64").cpu().numpy() - Jinv).max() <= 1e-13 * np.abs(Jinv).max()
+        assert np.abs(g.get(fe.GEOM_WDETJ, "f64").cpu().numpy() - wdetJ).max() <= 1e-14 * np.abs(wdetJ).max()
+    ctx.check()
+
+
+def test_inconsistent_tensor_factors_are_rejected(ctx):
+    mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
+    P = Problem(ctx, mesh, 2, 3)
+    pts, w, phi, dphi = fe.refbasis_hex(2, 3)
+    b1d, d1d = fe.refbasis_hex_1d(2, 3)
+    d1d = d1d.copy()
+    d1d[1, 2] += 1e-6
+    with pytest.raises(fe.FEError) as ei:
+        fe.geometry(ctx, P.m, phi, dphi, w, b1d=b1d, d1d=d1d)
+    assert ei.value.status == fe.FE_ERR_INVALID_ARG
+
+
 def test_geometry_update_follows_moved_nodes(ctx):
     mesh = meshgen.structured_hex(3, 3, 3, 2, 0.1, 22)
     P = Problem(ctx, mesh, 2, 3)
@@ -165,8 +191,7 @@ def test_empty_mesh_is_a_no_op(ctx):
     coords = _t(mesh.coords, torch.float64)
     conn = torch.zeros((0, 27), dtype=torch.int32, device="cuda")
     m = fe.Mesh(coords, conn)
-    pts, w, phi, dphi = fe.refbasis_hex(2, 3)
-    g = fe.geometry(ctx, m, phi, dphi, w)
+    g = fe.hex_geometry(ctx, m, 2, 3)
     K = fe.eval_matrix(ctx, fe.elasticity_form(), g, [torch.zeros((0, 2), dtype=torch.float64, device="cuda"),
                                                        None, None], "f32")
     ctx.check()

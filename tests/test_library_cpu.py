@@ -44,6 +44,17 @@ def test_refbasis_matches_oracle_tables(libfe, p, nq):
     np.testing.assert_allclose(dphi, odphi, atol=1e-12)
 
 
+@pytest.mark.parametrize("p,nq", [(1, 2), (2, 3), (3, 4), (2, 5)])
+def test_refbasis_1d_factors_reproduce_3d_tables(libfe, p, nq):
+    pts, w, phi, dphi = fe.refbasis_hex(p, nq)
+    b, d = fe.refbasis_hex_1d(p, nq)
+    n1 = p + 1
+    want_phi = np.einsum("zk,yj,xi->zyxkji", b, b, b).reshape(nq ** 3, n1 ** 3)
+    np.testing.assert_allclose(phi, want_phi, atol=1e-14)
+    want_dx = np.einsum("zk,yj,xi->zyxkji", b, b, d).reshape(nq ** 3, n1 ** 3)
+    np.testing.assert_allclose(dphi[:, 0, :], want_dx, atol=1e-13)
+
+
 @pytest.mark.parametrize("n", range(1, 11))
 def test_library_gauss_rule_matches_leggauss(libfe, n):
     pts, w, _, _ = fe.refbasis_hex(1, n)
