@@ -106,16 +106,44 @@ struct TileVec<double, 3> {
     }
 };
 
+// Output paths of the element matrices:
+//   STAGE_DIRECT  scattered stores straight from registers
+//   STAGE_FULL    all EPB matrices staged in shared memory, copied out with
+//                 coalesced 16-byte stores
+//   STAGE_BULK    one component row block (N rows) at a time, double-buffered
+//                 in shared memory and written by asynchronous bulk copies
+//                 (cp.async.bulk), which overlap with the next block
+constexpr int STAGE_DIRECT = 0, STAGE_FULL = 1, STAGE_BULK = 2;
+
+__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, unsigned bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"((unsigned)__cvta_generic_to_shared(ssrc)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void bulk_wait_read()
+{
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(PENDING) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 // Shared-memory plan of one CTA (sizes in elements of S).
-template <typename S, int N, int Q, int KIND, int T, int EPB, bool STAGE>
+template <typename S, int N, int Q, int KIND, int T, int EPB, int STAGE>
 struct MatrixSmem {
     static constexpr bool GRAD = KIND != FK_MASS;
+    static constexpr int V = 16 / (int)sizeof(S);
     static constexpr int TP = tile_pad<T, S>();
     static constexpr int NP = (N / T) * TP;  // padded node count
     static constexpr int G_SIZE = GRAD ? EPB * Q * 3 * NP : Q * NP;
     static constexpr int NROW_MAX = (KIND == FK_LAPLACE ? 1 : 3) * N;
+    // bulk staging slot: one row block of one element, +16 bytes of alignment shift
+    static constexpr int SLOT = (N * NROW_MAX + V + V - 1) / V * V;
     // staged matrices, +16 bytes to shift the chunk onto the global alignment
-    static constexpr int K_SIZE = STAGE ? EPB * NROW_MAX * NROW_MAX + 16 / (int)sizeof(S) : 0;
+    static constexpr int K_SIZE = STAGE == STAGE_FULL   ? EPB * NROW_MAX * NROW_MAX + V
+                                  : STAGE == STAGE_BULK ? 2 * EPB * SLOT
+                                                        : 0;
     static constexpr int GK = G_SIZE > K_SIZE ? G_SIZE : K_SIZE;  // K staging reuses the G buffer
     static constexpr int J_OFF = GK;
     static constexpr int W_OFF = J_OFF + EPB * Q * 9;
@@ -125,7 +153,7 @@ struct MatrixSmem {
 };
 
 // MATK: 0 scalar coefficient (or none), 1 Lame pair, 2 general D (6x6 Voigt)
-template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, bool STAGE>
+template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, int STAGE>
 __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ jinv, const S *__restrict__ wdetj,
                                                         const S *__restrict__ dphi, const S *__restrict__ phi,
                                                         long long E, int ncomp, const double *__restrict__ mat,
@@ -146,6 +174,8 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
     const int nrow = ncomp * N;
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
         const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
+        if constexpr (STAGE == STAGE_BULK)
+            if (threadIdx.x == 0) bulk_wait_read<0>();  // staging (aliased with G) has been read out
         __syncthreads();  // previous iteration's copy-out has finished reading sK
         if constexpr (GRAD)
             for (int i = threadIdx.x; i < ne * Q * 9; i += THREADS) sJ[i] = jinv[e0 * Q * 9 + i];
@@ -241,32 +271,18 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
         }
 
         // ---- epilogue: element-matrix entries of this tile and its mirror image
-        S *Kst = nullptr;
-        long long kbase = 0;
-        int shift = 0;
-        if constexpr (STAGE) {
-            __syncthreads();  // everyone is done reading G: reuse the buffer for K
-            kbase = e0 * (long long)nrow * nrow;
-            // stage at the same offset modulo 16 bytes as the global destination
-            shift = (int)(((unsigned long long)(K + kbase) % 16) / sizeof(S));
-            Kst = sK + shift;
+        const int a0 = ta * T, b0 = tb * T;
+        const bool mirror = ta != tb;
+        S lam = 0, mu = 0;
+        if constexpr (KIND == FK_ELASTICITY && MATK == 1) {
+            lam = sC[el * 2];
+            mu = sC[el * 2 + 1];
         }
-        auto put = [&](int r, int c, S v) {
-            if constexpr (STAGE)
-                Kst[(long long)el * nrow * nrow + r * nrow + c] = v;
-            else
-                K[(e0 + el) * (long long)nrow * nrow + (long long)r * nrow + c] = v;
-        };
-        if (active) {
-            const int a0 = ta * T, b0 = tb * T;
-            const bool mirror = ta != tb;
+        // entry (r, c) = ((i, a0+x), (k, b0+y)) of the tile and its mirror entry
+        // ((k, b0+y), (i, a0+x)); emit(i, k, x, y, v, vt) receives both values
+        auto for_entries = [&](auto &&emit) {
             if constexpr (KIND == FK_ELASTICITY) {
                 const S *C = sC + el * 81;  // general D: C_ijkl read from shared memory
-                S lam = 0, mu = 0;
-                if constexpr (MATK == 1) {
-                    lam = sC[el * 2];
-                    mu = sC[el * 2 + 1];
-                }
 #pragma unroll
                 for (int x = 0; x < T; ++x)
 #pragma unroll
@@ -276,34 +292,23 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
                         for (int i = 0; i < 3; ++i)
 #pragma unroll
                             for (int k = 0; k < 3; ++k) {
-                                S v;
+                                S v, vt;
                                 if constexpr (MATK == 1) {
                                     v = lam * acc[i][k][x][y] + mu * acc[k][i][x][y];
                                     if (i == k) v += mu * tr;
+                                    vt = v;  // symmetric D: K is symmetric
                                 } else {
                                     v = 0;
+                                    vt = 0;
 #pragma unroll
                                     for (int j = 0; j < 3; ++j)
 #pragma unroll
-                                        for (int l = 0; l < 3; ++l) v = fma(C[i * 27 + j * 9 + k * 3 + l], acc[j][l][x][y], v);
+                                        for (int l = 0; l < 3; ++l) {
+                                            v = fma(C[i * 27 + j * 9 + k * 3 + l], acc[j][l][x][y], v);
+                                            vt = fma(C[k * 27 + l * 9 + i * 3 + j], acc[j][l][x][y], vt);
+                                        }
                                 }
-                                put(i * N + a0 + x, k * N + b0 + y, v);
-                                // K is symmetric for symmetric D; for a general D the
-                                // mirror entry is the transposed contraction
-                                if (mirror) {
-                                    S vt;
-                                    if constexpr (MATK == 1) {
-                                        vt = v;
-                                    } else {
-                                        vt = 0;
-#pragma unroll
-                                        for (int j = 0; j < 3; ++j)
-#pragma unroll
-                                            for (int l = 0; l < 3; ++l)
-                                                vt = fma(C[k * 27 + l * 9 + i * 3 + j], acc[j][l][x][y], vt);
-                                    }
-                                    put(k * N + b0 + y, i * N + a0 + x, vt);
-                                }
+                                emit(i, k, x, y, v, vt);
                             }
                     }
             } else {
@@ -314,32 +319,90 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
                     for (int y = 0; y < T; ++y) {
                         const S v = c * acc[0][0][x][y];
                         for (int r = 0; r < ncomp; ++r)
-                            for (int s2 = 0; s2 < ncomp; ++s2) {
-                                const S vv = r == s2 ? v : (S)0;
-                                put(r * N + a0 + x, s2 * N + b0 + y, vv);
-                                if (mirror) put(s2 * N + b0 + y, r * N + a0 + x, vv);
-                            }
+                            for (int s2 = 0; s2 < ncomp; ++s2) emit(r, s2, x, y, r == s2 ? v : (S)0, r == s2 ? v : (S)0);
                     }
             }
-        }
-        if constexpr (STAGE) {
-            __syncthreads();
-            // coalesced 16-byte streaming stores of the ne contiguous matrices
-            constexpr int V = 16 / (int)sizeof(S);
-            const long long total = (long long)ne * nrow * nrow;
-            const int head = (int)((V - shift) % V);  // scalars before the first aligned vector
-            S *Kg = K + kbase;
-            for (int i = threadIdx.x; i < head && i < total; i += THREADS) Kg[i] = Kst[i];
-            const long long nvec = (total - head) / V;
-            const float4 *src = reinterpret_cast<const float4 *>(Kst + head);
-            float4 *dst = reinterpret_cast<float4 *>(Kg + head);
-            for (long long i = threadIdx.x; i < nvec; i += THREADS) __stcs(dst + i, src[i]);
-            for (long long i = head + nvec * V + threadIdx.x; i < total; i += THREADS) Kg[i] = Kst[i];
+        };
+
+        if constexpr (STAGE == STAGE_BULK) {
+            // one component row block per pass, double-buffered, drained by bulk copies
+            constexpr int V = P::V;
+            const int nblk = ncomp;
+            const int blk_len = N * nrow;  // elements of one row block of one matrix
+            auto shift_of = [&](int e_l, int pb) {
+                const S *gd = K + (e0 + e_l) * (long long)nrow * nrow + (long long)pb * blk_len;
+                return (int)(((unsigned long long)gd % 16) / sizeof(S));
+            };
+            for (int pb = 0; pb < nblk; ++pb) {
+                const int buf = pb & 1;
+                if (pb >= 2 && threadIdx.x == 0) bulk_wait_read<1>();  // buffer of pass pb-2 drained
+                __syncthreads();  // pass 0: everyone is done reading G
+                if (active) {
+                    S *slot = sK + (buf * EPB + el) * P::SLOT + shift_of(el, pb);
+                    for_entries([&](int i, int k, int x, int y, S v, S vt) {
+                        if (i == pb) slot[(a0 + x) * nrow + k * N + b0 + y] = v;
+                        if (mirror && k == pb) slot[(b0 + y) * nrow + i * N + a0 + x] = vt;
+                    });
+                }
+                fence_proxy_async();  // make the staged values visible to the bulk-copy engine
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    for (int e_l = 0; e_l < ne; ++e_l) {
+                        const int sh = shift_of(e_l, pb);
+                        const S *src = sK + (buf * EPB + e_l) * P::SLOT + sh;
+                        S *dst = K + (e0 + e_l) * (long long)nrow * nrow + (long long)pb * blk_len;
+                        const int head = (V - sh) % V < blk_len ? (V - sh) % V : blk_len;
+                        const int body = (blk_len - head) / V * V;
+                        for (int t = 0; t < head; ++t) dst[t] = src[t];
+                        for (int t = head + body; t < blk_len; ++t) dst[t] = src[t];
+                        if (body > 0) bulk_store(dst + head, src + head, (unsigned)(body * sizeof(S)));
+                    }
+                    bulk_commit();
+                }
+            }
+        } else {
+            S *Kst = nullptr;
+            long long kbase = 0;
+            int shift = 0;
+            if constexpr (STAGE == STAGE_FULL) {
+                __syncthreads();  // everyone is done reading G: reuse the buffer for K
+                kbase = e0 * (long long)nrow * nrow;
+                // stage at the same offset modulo 16 bytes as the global destination
+                shift = (int)(((unsigned long long)(K + kbase) % 16) / sizeof(S));
+                Kst = sK + shift;
+            }
+            auto put = [&](int r, int c, S v) {
+                if constexpr (STAGE == STAGE_FULL)
+                    Kst[(long long)el * nrow * nrow + r * nrow + c] = v;
+                else
+                    K[(e0 + el) * (long long)nrow * nrow + (long long)r * nrow + c] = v;
+            };
+            if (active)
+                for_entries([&](int i, int k, int x, int y, S v, S vt) {
+                    put(i * N + a0 + x, k * N + b0 + y, v);
+                    if (mirror) put(k * N + b0 + y, i * N + a0 + x, vt);
+                });
+            if constexpr (STAGE == STAGE_FULL) {
+                __syncthreads();
+                // coalesced 16-byte streaming stores of the ne contiguous matrices
+                constexpr int V = 16 / (int)sizeof(S);
+                const long long total = (long long)ne * nrow * nrow;
+                const int head = (int)((V - shift) % V);  // scalars before the first aligned vector
+                S *Kg = K + kbase;
+                for (int i = threadIdx.x; i < head && i < total; i += THREADS) Kg[i] = Kst[i];
+                const long long nvec = (total - head) / V;
+                const float4 *src = reinterpret_cast<const float4 *>(Kst + head);
+                float4 *dst = reinterpret_cast<float4 *>(Kg + head);
+                for (long long i = threadIdx.x; i < nvec; i += THREADS) __stcs(dst + i, src[i]);
+                for (long long i = head + nvec * V + threadIdx.x; i < total; i += THREADS) Kg[i] = Kst[i];
+            }
         }
     }
+    if constexpr (STAGE == STAGE_BULK)
+        if (threadIdx.x == 0) bulk_wait_read<0>();  // shared memory must outlive the copies' reads
 }
 
-template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, bool STAGE>
+template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, int STAGE>
 cudaError_t launch_sym(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, void *K, int sm_count,
                        cudaStream_t s)
 {
@@ -370,8 +433,8 @@ cudaError_t launch_sym(const fe_geometry_h *g, const fe_form_h *f, fe_material_a
 // Tile shapes: T x T node tiles, EPB elements per CTA, one upper-triangle tile
 // per thread; Laplace/mass (L) and elasticity (E) configured separately.
 // K is staged in shared memory unless it would not fit.
-template <typename S, int N, int Q, int T_L, int EPB_L, int THR_L, bool STAGE_L, int T_E, int EPB_E, int THR_E,
-          bool STAGE_E>
+template <typename S, int N, int Q, int T_L, int EPB_L, int THR_L, int STAGE_L, int T_E, int EPB_E, int THR_E,
+          int STAGE_E>
 cudaError_t dispatch_nq(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, void *K, int sm,
                         cudaStream_t s)
 {
@@ -392,20 +455,21 @@ cudaError_t dispatch(const fe_geometry_h *g, const fe_form_h *f, fe_material_arg
 {
     const int N = g->N, Q = g->Q;
     constexpr bool D = sizeof(S) == 8;
+    constexpr int B = STAGE_BULK;
     // Q1: 2x2 tiles, 10 upper tiles per element, 12 elements per CTA
-    if (N == 8 && Q == 8) return dispatch_nq<S, 8, 8, 2, 12, 128, true, 2, 12, 128, true>(g, f, mat, K, sm, s);
-    if (N == 8 && Q == 27) return dispatch_nq<S, 8, 27, 2, 12, 128, true, 2, 12, 128, true>(g, f, mat, K, sm, s);
-    // Q2: 3x3 tiles, 45 upper tiles per element, 2 elements per 96-thread CTA;
-    // FP64 elasticity writes directly (2 x 52 KB of staging would leave one CTA per SM)
-    if (N == 27 && Q == 27) return dispatch_nq<S, 27, 27, 3, 2, 96, true, 3, 2, 96, !D>(g, f, mat, K, sm, s);
-    if (N == 27 && Q == 64) return dispatch_nq<S, 27, 64, 3, 2, 96, true, 3, 2, 96, false>(g, f, mat, K, sm, s);
+    if (N == 8 && Q == 8) return dispatch_nq<S, 8, 8, 2, 12, 128, B, 2, 12, 128, B>(g, f, mat, K, sm, s);
+    if (N == 8 && Q == 27) return dispatch_nq<S, 8, 27, 2, 12, 128, B, 2, 12, 128, B>(g, f, mat, K, sm, s);
+    // Q2: 3x3 tiles, 45 upper tiles per element, 2 elements per 96-thread CTA
+    if (N == 27 && Q == 27) return dispatch_nq<S, 27, 27, 3, 2, 96, B, 3, 2, 96, B>(g, f, mat, K, sm, s);
+    if (N == 27 && Q == 64) return dispatch_nq<S, 27, 64, 3, 2, 96, B, 3, 2, 96, B>(g, f, mat, K, sm, s);
     // Q3: 4x4 tiles (136 per element) for FP32 and the scalar forms; FP64
-    // elasticity needs 2x2 tiles (528 per element) to keep 36 accumulators
+    // elasticity needs 2x2 tiles (528 per element) to keep 36 accumulators and
+    // writes directly (a 64 x 192 FP64 row block per buffer would not fit)
     if (N == 64 && Q == 64) {
         if constexpr (D)
-            return dispatch_nq<S, 64, 64, 4, 1, 160, false, 2, 1, 544, false>(g, f, mat, K, sm, s);
+            return dispatch_nq<S, 64, 64, 4, 1, 160, B, 2, 1, 544, STAGE_DIRECT>(g, f, mat, K, sm, s);
         else
-            return dispatch_nq<S, 64, 64, 4, 1, 160, true, 4, 1, 160, false>(g, f, mat, K, sm, s);
+            return dispatch_nq<S, 64, 64, 4, 1, 160, B, 4, 1, 160, B>(g, f, mat, K, sm, s);
     }
     return cudaErrorInvalidValue;
 }
