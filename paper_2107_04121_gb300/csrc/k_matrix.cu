@@ -148,7 +148,8 @@ struct MatrixSmem {
     static constexpr int J_OFF = GK;
     static constexpr int W_OFF = J_OFF + EPB * Q * 9;
     static constexpr int C_OFF = W_OFF + EPB * Q;
-    static constexpr int TOTAL = C_OFF + EPB * 81;
+    static constexpr int D_OFF = C_OFF + EPB * 81;      // reference gradients (Q, 3, N), loaded once
+    static constexpr int TOTAL = D_OFF + (GRAD ? Q * 3 * N : 0);
     static constexpr size_t BYTES = sizeof(S) * (size_t)TOTAL;
 };
 
@@ -170,6 +171,9 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
     S *sJ = sm + P::J_OFF;
     S *sW = sm + P::W_OFF;
     S *sC = sm + P::C_OFF;
+    S *sD = sm + P::D_OFF;
+    if constexpr (GRAD)
+        for (int i = threadIdx.x; i < Q * 3 * N; i += THREADS) sD[i] = dphi[i];
 
     const int nrow = ncomp * N;
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
@@ -200,14 +204,24 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
             }
         __syncthreads();
         if constexpr (GRAD) {
-            // G[el][q][j][a] = sum_k dphi[q][k][a] Jinv[el][q][k][j], padded node index
-            for (int i = threadIdx.x; i < ne * Q * N; i += THREADS) {
-                const int a = i % N, q = (i / N) % Q, el = i / (N * Q);
-                const S g0 = dphi[(q * 3 + 0) * N + a], g1 = dphi[(q * 3 + 1) * N + a], g2 = dphi[(q * 3 + 2) * N + a];
-                const S *Ji = sJ + (el * Q + q) * 9;
-                S *Go = sG + ((el * Q + q) * 3) * NP + (a / T) * TP + a % T;
+            // scaled physical gradients sqrt(w det J) G[el][q][j][a], G = J^-T grad_xi phi,
+            // padded node index; the Gram blocks then need no weight in the inner loop
+            // (w det J > 0 is checked by the geometry kernel)
+            for (int i = threadIdx.x; i < ne * Q; i += THREADS) {
+                const int el = i / Q, q = i % Q;
+                const S sw = sqrt(sW[i]);
+                S Ji[9];
 #pragma unroll
-                for (int j = 0; j < 3; ++j) Go[j * NP] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
+                for (int t = 0; t < 9; ++t) Ji[t] = sw * sJ[i * 9 + t];
+                const S *D0 = sD + q * 3 * N;
+                S *Go = sG + ((el * Q + q) * 3) * NP;
+#pragma unroll 3
+                for (int a = 0; a < N; ++a) {
+                    const S g0 = D0[a], g1 = D0[N + a], g2 = D0[2 * N + a];
+                    const int pa = (a / T) * TP + a % T;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) Go[j * NP + pa] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
+                }
             }
             __syncthreads();
         }
@@ -235,8 +249,8 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
             }
             tb = ta + u;
             const S *Wq = sW + el * Q;
+#pragma unroll 9
             for (int q = 0; q < Q; ++q) {
-                const S wq = Wq[q];
                 const S *Gq = GRAD ? sG + (el * Q + q) * 3 * NP : sG + q * NP;
                 S ga[NDIR][T], gb[NDIR][T];
                 if constexpr (KIND == FK_LAPLACE) {
@@ -248,15 +262,17 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
 #pragma unroll
                         for (int x = 0; x < T; ++x)
 #pragma unroll
-                            for (int y = 0; y < T; ++y) acc[0][0][x][y] = fma(wq * va[x], vb[y], acc[0][0][x][y]);
+                            for (int y = 0; y < T; ++y) acc[0][0][x][y] = fma(va[x], vb[y], acc[0][0][x][y]);
                     }
                 } else {
+                    const S wq = GRAD ? (S)1 : Wq[q];
 #pragma unroll
                     for (int j = 0; j < NDIR; ++j) {
                         TileVec<S, T>::load(Gq + j * NP + ta * TP, ga[j]);
                         TileVec<S, T>::load(Gq + j * NP + tb * TP, gb[j]);
+                        if constexpr (!GRAD)
 #pragma unroll
-                        for (int x = 0; x < T; ++x) ga[j][x] *= wq;
+                            for (int x = 0; x < T; ++x) ga[j][x] *= wq;
                     }
 #pragma unroll
                     for (int j = 0; j < NDIR; ++j)
@@ -333,16 +349,67 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
                 const S *gd = K + (e0 + e_l) * (long long)nrow * nrow + (long long)pb * blk_len;
                 return (int)(((unsigned long long)gd % 16) / sizeof(S));
             };
+            // entry ((i, a0+x), (k, b0+y)) of the elasticity matrix and of its mirror
+            auto kval = [&](int i, int k, int x, int y) -> S {
+                if constexpr (MATK == 1) {
+                    S v = lam * acc[i][k][x][y] + mu * acc[k][i][x][y];
+                    if (i == k) v += mu * (acc[0][0][x][y] + acc[1][1][x][y] + acc[2][2][x][y]);
+                    return v;
+                } else {
+                    const S *C = sC + el * 81;
+                    S v = 0;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int l = 0; l < 3; ++l) v = fma(C[i * 27 + j * 9 + k * 3 + l], acc[j][l][x][y], v);
+                    return v;
+                }
+            };
+            auto kval_t = [&](int i, int k, int x, int y) -> S {
+                if constexpr (MATK == 1) {
+                    return kval(i, k, x, y);
+                } else {
+                    const S *C = sC + el * 81;
+                    S v = 0;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+#pragma unroll
+                        for (int l = 0; l < 3; ++l) v = fma(C[k * 27 + l * 9 + i * 3 + j], acc[j][l][x][y], v);
+                    return v;
+                }
+            };
             for (int pb = 0; pb < nblk; ++pb) {
                 const int buf = pb & 1;
                 if (pb >= 2 && threadIdx.x == 0) bulk_wait_read<1>();  // buffer of pass pb-2 drained
                 __syncthreads();  // pass 0: everyone is done reading G
                 if (active) {
                     S *slot = sK + (buf * EPB + el) * P::SLOT + shift_of(el, pb);
-                    for_entries([&](int i, int k, int x, int y, S v, S vt) {
-                        if (i == pb) slot[(a0 + x) * nrow + k * N + b0 + y] = v;
-                        if (mirror && k == pb) slot[(b0 + y) * nrow + i * N + a0 + x] = vt;
-                    });
+                    if constexpr (KIND == FK_ELASTICITY) {
+                        // rows of block pb: direct entries with i == pb, mirror entries with k == pb
+#pragma unroll
+                        for (int pc = 0; pc < 3; ++pc) {
+                            if (pc != pb) continue;
+#pragma unroll
+                            for (int x = 0; x < T; ++x)
+#pragma unroll
+                                for (int y = 0; y < T; ++y)
+#pragma unroll
+                                    for (int k = 0; k < 3; ++k) slot[(a0 + x) * nrow + k * N + b0 + y] = kval(pc, k, x, y);
+                            if (mirror)
+#pragma unroll
+                                for (int y = 0; y < T; ++y)
+#pragma unroll
+                                    for (int x = 0; x < T; ++x)
+#pragma unroll
+                                        for (int i = 0; i < 3; ++i)
+                                            slot[(b0 + y) * nrow + i * N + a0 + x] = kval_t(i, pc, x, y);
+                        }
+                    } else {
+                        for_entries([&](int i, int k, int x, int y, S v, S vt) {
+                            if (i == pb) slot[(a0 + x) * nrow + k * N + b0 + y] = v;
+                            if (mirror && k == pb) slot[(b0 + y) * nrow + i * N + a0 + x] = vt;
+                        });
+                    }
                 }
                 fence_proxy_async();  // make the staged values visible to the bulk-copy engine
                 __syncthreads();
