@@ -241,6 +241,10 @@ fe_status fe_form_shape(const fe_form_h *form, int n_basis, int *n_rows, int *n_
  * respect to the DOFs of operand `diff_op` (which must be the FE_STATE operand),
  * integrated with the quadrature of `geom`; K_out is a device array
  * (n_elems, n_rows, n_cols), float64 for FE_F64 else float32.
+ * FE_F64 and FE_F32 cover every form and element; the tensor-core precisions
+ * (FE_TF32X3, FE_BF16X3, FE_BF16) cover linear elasticity with FE_MAT_LAME
+ * materials on 27-node hexahedra with 27 points.  A tensor-core wait that
+ * times out is reported as FE_ERR_TIMEOUT through fe_get_status.
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_SHAPE, FE_ERR_UNSUPPORTED_SPEC (e.g. a
  * precision without a kernel for this form), FE_ERR_CUDA. */
 fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const void *const *args,

@@ -11,7 +11,7 @@
 cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
                                   void *K, int sm_count, cudaStream_t s);
 cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
-                                void *K, int sm_count, cudaStream_t s);
+                                void *K, int sm_count, unsigned long long *status, cudaStream_t s);
 
 namespace {
 
@@ -287,8 +287,10 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
     if (prec == FE_F64 || prec == FE_F32) {
         e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, to_cuda(stream));
     } else {
-        if (form->kind != FK_ELASTICITY || !(g->N == 27 && g->Q == 27)) return FE_ERR_UNSUPPORTED_SPEC;
-        e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, to_cuda(stream));
+        // tensor-core kernels: Q2 elasticity (27 nodes, 27 points) with Lame materials
+        if (form->kind != FK_ELASTICITY || form->mat != FE_MAT_LAME || !(g->N == 27 && g->Q == 27))
+            return FE_ERR_UNSUPPORTED_SPEC;
+        e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, ctx->d_status, to_cuda(stream));
     }
     return from_cuda(e, "fe_eval_matrix");
 }

@@ -172,6 +172,38 @@ def test_elasticity_general_D_and_transposed_spec(ctx, prec):
     assert rel_matrix_error(Kt.cpu().numpy(), Kref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4), ("bf16", 2e-2)])
+def test_tensor_core_elasticity_matches_oracle(ctx, prec, tol):
+    """tcgen05 split-precision paths (Q2, Lame): TF32x3 within the FP32 tolerance;
+    BF16x3 and raw BF16 against their stated bounds."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (4, 4, 5), 81)
+    args = [_t(mat, torch.float64), None, None]
+    K = fe.eval_matrix(ctx, form, P.geom, args, prec)
+    K32 = fe.eval_matrix(ctx, form, P.geom, args, "f32")
+    ctx.check()
+    err = rel_matrix_error(K.cpu().numpy(), Kref)
+    assert err <= tol, err
+    assert rel_matrix_error(K32.cpu().numpy(), Kref) <= TOL["f32"]
+    # symmetric like the exact matrix
+    Kh = K.cpu().numpy()
+    assert np.abs(Kh - Kh.transpose(0, 2, 1)).max() <= 10 * tol * np.abs(Kh).max()
+
+
+def test_tensor_core_paths_reject_other_forms(ctx):
+    mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
+    P = Problem(ctx, mesh, 2, 3)
+    D = np.tile(np.eye(6), (mesh.n_elems, 1, 1))
+    with pytest.raises(fe.FEError) as ei:
+        fe.eval_matrix(ctx, fe.elasticity_form(fe.MAT_D66), P.geom, [_t(D, torch.float64), None, None], "tf32x3")
+    assert ei.value.status == fe.FE_ERR_UNSUPPORTED_SPEC
+    mesh1 = meshgen.structured_hex(2, 2, 2, 1, 0.0, 0)
+    P1 = Problem(ctx, mesh1, 1, 2)
+    lm = np.ones((mesh1.n_elems, 2))
+    with pytest.raises(fe.FEError) as ei:
+        fe.eval_matrix(ctx, fe.elasticity_form(), P1.geom, [_t(lm, torch.float64), None, None], "bf16x3")
+    assert ei.value.status == fe.FE_ERR_UNSUPPORTED_SPEC
+
+
 def test_laplace_q1_cube_config(ctx):
     """Plain method, Laplace stiffness on the 8^3 Q1 cube (+-0.1h, seed 0), c = 1."""
     mesh, u = meshgen.laplace_q1_cube(8, 0)
