@@ -47,7 +47,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=48, help="cube edge in elements (48 -> 110,592 hexes)")
-    ap.add_argument("--prec", default="f32", help="contraction precision of the headline path")
+    ap.add_argument("--prec", default="auto",
+                    help="contraction precision of the headline path; auto = fastest of the ladder within 1e-5")
     ap.add_argument("--skip-extras", action="store_true",
                     help="time the headline path only (no FP64 path, e2e, CPU baseline, error check)")
     return ap.parse_args()
@@ -195,6 +196,35 @@ class Workload:
 
 
 KERNELS_PER_STEP = 4  # geometry, matrix, residual, assembly
+LADDER = ["f32", "tf32x3", "bf16x3", "bf16"]
+DEFAULT_MIXED = "bf16x3"
+
+
+def precision_ladder(wl, flush, ref, reps=5):
+    """Matrix-kernel time and sampled error against the oracle for each contraction
+    precision of the mixed path (FP64 geometry in every case)."""
+    torch = wl.torch
+    out = {}
+    for p in LADDER:
+        K, r, g = wl.outputs(p)
+        geom = wl.geoms["f32"]
+        for _ in range(2):
+            wl.fe.eval_matrix(wl.ctx, wl.form, geom, [wl.mat, None, None], p, out=K)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            wl.fe.eval_matrix(wl.ctx, wl.form, geom, [wl.mat, None, None], p, out=K)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        wl.step(p)
+        errs, _ = sampled_errors(wl, [p], ref)
+        out[p] = {"matrix_ms": statistics.median(ts), "rel_err_K": errs.get("K_" + p), "rel_err_r": errs.get("r_" + p)}
+        wl.drop(p)
+    wl.ctx.check()
+    return out
 
 
 def timed_steps(wl, prec, steps, warmup, ws, flush):
@@ -221,18 +251,13 @@ def timed_steps(wl, prec, steps, warmup, ws, flush):
     return step_ms, mat_ms
 
 
-def sampled_errors(wl, precs):
-    """Relative errors against the FP64 oracle on sampled elements (first, last, 62 random)."""
-    import oracle
+def sampled_errors(wl, precs, ref):
+    """Relative errors of the GPU outputs on the sampled elements of `ref`
+    (computed by the oracle in the CPU-baseline leg)."""
+    if ref is None:
+        return {}, 0
     from tests.parity import rel_matrix_error, rel_vector_error
-    rng = np.random.default_rng(7)
-    idx = np.unique(np.concatenate([[0, wl.E - 1], rng.choice(wl.E, 62, replace=False)]))
-    ref = oracle.RefElement(2, 3)
-    conn = wl.mesh.conn[idx]
-    wdetJ, G, _ = oracle.geometry(wl.mesh.coords, conn, ref)
-    D = oracle.lame_to_D(wl.lam[idx], wl.mu[idx])
-    Kref = oracle.matrix_elasticity(wdetJ, G, D)
-    rref = oracle.residual_elasticity(conn, wdetJ, G, D, wl.u)
+    idx, Kref, rref = ref
     out = {}
     it = wl.torch.from_numpy(idx).cuda()
     for p in precs:
@@ -295,6 +320,9 @@ def oracle_step(mesh, lam, mu, u, n_elems):
 
 
 def cpu_baseline(n, sample):
+    """The CPU-baseline leg: the FP64 oracle timed on the host cores on a bounded
+    sample, and its element matrices and residuals on 64 sampled elements (first,
+    last, 62 seeded), against which the GPU outputs are checked."""
     import oracle
     from paper_2107_04121_gb300 import meshgen
     mesh, lam, mu, u = meshgen.elasticity_q2_cube(n, seed=1)
@@ -302,9 +330,17 @@ def cpu_baseline(n, sample):
     t = time.perf_counter()
     oracle_step(mesh, lam, mu, u, sample)
     dt = time.perf_counter() - t
-    return {"value": sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    base = {"value": sample / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "first %d of %d elements, one full oracle step (FP64 geometry, K_e, r_e, assembly), "
                       "%.1f s" % (sample, mesh.n_elems, dt)}
+    rng = np.random.default_rng(7)
+    E = mesh.n_elems
+    idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, min(62, E), replace=False)]))
+    conn = mesh.conn[idx]
+    wdetJ, G, _ = oracle.geometry(mesh.coords, conn, oracle.RefElement(2, 3))
+    D = oracle.lame_to_D(lam[idx], mu[idx])
+    ref = (idx, oracle.matrix_elasticity(wdetJ, G, D), oracle.residual_elasticity(conn, wdetJ, G, D, u))
+    return base, ref
 
 
 def cpu_info():
@@ -373,13 +409,21 @@ def main():
 
     # the oracle's OpenMP threads must not compete with the timed GPU region:
     # time the CPU baseline first (rank 0, N = 1 only)
-    cpu = None
+    cpu, ref = None, None
     if rank == 0 and ws == 1 and not args.skip_extras:
-        cpu = cpu_baseline(args.n, min(32768, args.n ** 3))
+        cpu, ref = cpu_baseline(args.n, min(32768, args.n ** 3))
 
     wl = Workload(args.n, local)
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    ladder = None
     prec = args.prec
+    if prec == "auto":
+        ladder = precision_ladder(wl, flush, ref)
+        if ref is not None:
+            ok = [p for p in LADDER if ladder[p]["rel_err_K"] <= 1e-5 and ladder[p]["rel_err_r"] <= 1e-5]
+            prec = min(ok, key=lambda p: ladder[p]["matrix_ms"])
+        else:
+            prec = DEFAULT_MIXED  # no oracle sample on this rank: the precision the N = 1 run selects
     with ClockSampler(local) as clk:
         step_ms, mat_ms = timed_steps(wl, prec, args.steps, args.warmup, ws, flush)
     total_ms = max_over_ranks(sum(step_ms), ws)
@@ -391,12 +435,12 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": prec, "data": "synthetic",
+        "dtype": "f32" if prec != "f64" else "f64", "data": "synthetic",
         "config": {"workload": "Q2 linear elasticity, %d^3 = %d hexes (27 nodes, 27 Gauss points), "
                                "+-0.15h interior perturbation seed 1, per-element Lame lambda~U[0.5,2], "
                                "mu~U[0.2,1], u~N(0,1); step = FP64 geometry + K_e (81x81) + r_e + "
                                "compensated assembly" % (args.n, wl.E),
-                   "elements": wl.E, "geometry_dtype": "f64", "contraction_dtype": prec,
+                   "elements": wl.E, "geometry_dtype": "f64", "contraction": prec,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
         "roofline": {"kernel": "k_matrix (fe_eval_matrix, %s)" % prec, "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
@@ -404,6 +448,8 @@ def main():
         "gpu_launches": KERNELS_PER_STEP * args.steps,
     }
     line["clocks"] = clk.summary()
+    if ladder is not None:
+        line["precision_ladder"] = ladder
     if not args.skip_extras:
         wl.drop(prec)
         # plain FP64 path, same step
@@ -412,10 +458,10 @@ def main():
         t64 = max_over_ranks(sum(s64), ws)
         line["fp64_path"] = {"value": ws * wl.E * f64_steps / (t64 / 1e3), "unit": UNIT,
                              "ms_per_step": t64 / f64_steps, "matrix_ms": sum(m64) / len(m64)}
-        errs, nsamp = sampled_errors(wl, ["f64"])
+        errs, nsamp = sampled_errors(wl, ["f64"], ref)
         wl.drop("f64")
         wl.step(prec)
-        e2, _ = sampled_errors(wl, [prec])
+        e2, _ = sampled_errors(wl, [prec], ref)
         errs.update(e2)
         errs["sampled_elements"] = nsamp
         line["rel_err"] = errs

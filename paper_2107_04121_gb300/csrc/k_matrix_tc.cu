@@ -13,16 +13,23 @@
 // K = 32 (points, zero padded).  Because A is a Gram matrix, one operand
 // buffer serves as both the A and the B operand (K-major, no swizzle).
 //
-// One CTA of four warps per element at a time:
-//   (a) stage sqrt(w det J) J^-1 of the element (FP32 copy of the FP64 geometry)
-//   (b) build X = (sqrt(w det J) J^-T grad_xi phi), split into hi/lo operands
-//   (c) one thread issues the MMAs and commits them to an mbarrier
-//   (d) all threads wait on the mbarrier (bounded; a timeout is reported)
-//   (e) warps 0-2 load their 32 accumulator lanes (rows j = warp) from tensor
-//       memory and publish them to shared memory
-//   (f) each thread forms one row of K_e, which needs the transposed block
-//       A_ik[b][a] and the diagonal blocks from the other warps
-//   (g) the 26,244-byte element matrix is written by one bulk copy
+// Warp-specialised pipeline, two operand buffers and two accumulators per CTA:
+//   producer warps 3-5, element n into buffer n % 2:
+//     (a) stage sqrt(w det J) J^-1 of the element (FP32 copy of the FP64 geometry)
+//     (b) build X = sqrt(w det J) J^-T grad_xi phi, split into hi/lo operands
+//     (c) one thread issues the MMAs and commits them to full[n % 2]
+//   consumer warps 0-2, element n from buffer n % 2:
+//     (d) wait full[n % 2] (bounded; a timeout is reported, never trapped)
+//     (e) load accumulator rows j = warp (lanes a) from tensor memory and
+//         publish the diagonal block A_jj and one off-diagonal block A_j,j+1
+//         to the exchange area, which reuses the operand buffer
+//     (f) K is symmetric: warp i forms the diagonal block K_ii (which needs
+//         the other warps' diagonal blocks) and the off-diagonal block
+//         K_i,i+1 (which needs its own transposed block A_i,i+1[b][a]), and
+//         writes K_i+1,i = K_i,i+1^T as columns
+//     (g) the 26,244-byte element matrix is written by one bulk copy, and
+//         empty[n % 2] hands the buffer and the accumulator back
+// so the operand build and MMAs of element n+1 overlap the epilogue of n.
 #include <cuda_bf16.h>
 
 #include "fe_device.cuh"
@@ -187,82 +194,135 @@ __device__ __forceinline__ void operand_tile(const float *__restrict__ dp, const
     }
 }
 
-// Row (i, a) of K_e, k-th column block: lambda A_ik[a][.] + mu A_ik[.][a]
-// (+ mu trace for k = i), read from the exchange buffer before any store.
+// Diagonal block of K_e for row (i, a): own A_ii[a][.] from registers, the
+// other warps' diagonal blocks from the exchange area; all reads before stores.
 template <int STRIDE>
-__device__ __forceinline__ void k_row_block(const float *own, const float *__restrict__ trc,
-                                            const float *__restrict__ o1, const float *__restrict__ o2, bool diag,
-                                            float lam, float mu, float *__restrict__ out)
+__device__ __forceinline__ void diag_block(const float *own, const float *__restrict__ d1,
+                                           const float *__restrict__ d2, float lam, float mu,
+                                           float *__restrict__ out)
+{
+    float t[TC_N];
+#pragma unroll
+    for (int b = 0; b < TC_N; ++b) t[b] = d1[b] + d2[b];
+#pragma unroll
+    for (int b = 0; b < TC_N; ++b) out[b] = fmaf(lam + 2.0f * mu, own[b], mu * t[b]);
+}
+
+// Off-diagonal block K_ik of row (i, a) and its mirror column K_ki[.][a]:
+// v[b] = lambda A_ik[a][b] + mu A_ik[b][a], written to the row and to the column.
+template <int STRIDE>
+__device__ __forceinline__ void offdiag_block(const float *own, const float *__restrict__ trc, float lam, float mu,
+                                              float *__restrict__ row, float *__restrict__ col)
 {
     float t[TC_N];
 #pragma unroll
     for (int b = 0; b < TC_N; ++b) t[b] = trc[b * STRIDE];
-    if (diag) {
 #pragma unroll
-        for (int b = 0; b < TC_N; ++b) t[b] = fmaf(mu, own[b] + o1[b] + o2[b], mu * t[b]) + lam * own[b];
-    } else {
+    for (int b = 0; b < TC_N; ++b) t[b] = fmaf(lam, own[b], mu * t[b]);
 #pragma unroll
-        for (int b = 0; b < TC_N; ++b) t[b] = fmaf(lam, own[b], mu * t[b]);
-    }
+    for (int b = 0; b < TC_N; ++b) row[b] = t[b];
 #pragma unroll
-    for (int b = 0; b < TC_N; ++b) out[b] = t[b];
+    for (int b = 0; b < TC_N; ++b) col[b * TC_NROW] = t[b];
+}
+
+template <int I>
+__device__ __forceinline__ void publish_blocks(const float *d, float *__restrict__ e0, float *__restrict__ e1)
+{
+#pragma unroll
+    for (int b = 0; b < TC_N; ++b) e0[b] = d[32 * I + b];
+#pragma unroll
+    for (int b = 0; b < TC_N; ++b) e1[b] = d[32 * ((I + 1) % 3) + b];
+}
+
+// Blocks K_ii and K_i,i+1 of row (I, a) and the mirror column of K_i+1,i.
+template <int I, int STRIDE>
+__device__ __forceinline__ void epilogue_rows(const float *d, const float *ex, int a, float lam, float mu,
+                                              float *kst)
+{
+    constexpr int Kb = (I + 1) % 3, Mb = (I + 2) % 3;
+    // K_ii[a][b] = (lambda + mu) A_ii[a][b] + mu (A_ii + A_kk + A_mm)[a][b]
+    diag_block<STRIDE>(d + 32 * I, ex + ((Kb * 2) * TC_N + a) * STRIDE, ex + ((Mb * 2) * TC_N + a) * STRIDE, lam,
+                       mu, kst + (I * TC_N + a) * TC_NROW + I * TC_N);
+    // K_ik[a][b] = lambda A_ik[a][b] + mu A_ik[b][a]; K_ki[b][a] = K_ik[a][b]
+    offdiag_block<STRIDE>(d + 32 * Kb, ex + ((I * 2 + 1) * TC_N) * STRIDE + a, lam, mu,
+                          kst + (I * TC_N + a) * TC_NROW + Kb * TC_N, kst + (Kb * TC_N) * TC_NROW + I * TC_N + a);
 }
 
 template <int MODE>
 struct TcSmem {
     static constexpr int EB = MODE == TC_TF32X3 ? 4 : 2;
     using L = OpLayout<EB>;
+    // per buffer: hi and lo operands; the exchange area [3 warps][2 blocks][27][33]
+    // floats of the epilogue reuses them once the buffer's MMAs have completed
+    static constexpr int EX_STRIDE = 33;
+    static constexpr int EX_BYTES = 6 * TC_N * EX_STRIDE * 4;
+    static constexpr int BUF = ((2 * L::BYTES > EX_BYTES ? 2 * L::BYTES : EX_BYTES) + 1023) / 1024 * 1024;
     static constexpr int HI = 0;
     static constexpr int LO = L::BYTES;
-    // the exchange buffer [3][3][27][33] floats reuses the operand buffers,
-    // which are dead once the MMAs have completed
-    static constexpr int EX = 0;
-    static constexpr int EX_STRIDE = 33;
-    static constexpr int EX_BYTES = 9 * TC_N * EX_STRIDE * 4;
-    static constexpr int OPEX = (2 * L::BYTES > EX_BYTES ? 2 * L::BYTES : EX_BYTES + 15) / 16 * 16;
-    static constexpr int KS = OPEX;                                    // K staging: 6561 + 4 floats
+    static constexpr int KS = 2 * BUF;                                  // K staging: 6561 + 4 floats
     static constexpr int KS_BYTES = (TC_NROW * TC_NROW + 4) * 4;
-    static constexpr int JW = (KS + KS_BYTES + 15) / 16 * 16;          // sqrt(w det J) J^-1: 27 x 9 floats
-    static constexpr int DP = JW + TC_Q * 9 * 4;                       // grad_xi phi: 27 x 3 x 27 floats
-    static constexpr int MISC = (DP + TC_Q * 3 * TC_N * 4 + 15) / 16 * 16;  // mbarrier, tmem slot, lambda/mu, flag
-    static constexpr int BYTES = MISC + 32;
+    static constexpr int JW = (KS + KS_BYTES + 15) / 16 * 16;          // [2][27][9] sqrt(w det J) J^-1
+    static constexpr int LM = JW + 2 * TC_Q * 9 * 4;                   // [2][2] lambda, mu
+    static constexpr int DP = LM + 16;                                 // grad_xi phi: 27 x 3 x 27 floats
+    static constexpr int MISC = (DP + TC_Q * 3 * TC_N * 4 + 15) / 16 * 16;  // 4 mbarriers, tmem slot, abort
+    static constexpr int BYTES = MISC + 48;
 };
 
-// Prefetched geometry of one element: 27 x 9 J^-1 entries, 27 weights, the Lame pair.
-constexpr int TC_PF = (TC_Q * 9 + TC_THREADS - 1) / TC_THREADS;  // 2 per thread
+constexpr int TC_CONS = 96;               // consumer threads (warps 0-2)
+constexpr int TC_PROD = 96;               // producer threads (warps 3-5)
+constexpr int TC_THREADS_WS = TC_CONS + TC_PROD;
+constexpr int TC_BAR_PROD = 1, TC_BAR_CONS = 2;  // named barriers
+
+__device__ __forceinline__ void named_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// Wait on an mbarrier phase, giving up after TC_WAIT_CYCLES or when the CTA aborts.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag || clock64() - t0 > TC_WAIT_CYCLES) return false;
+    }
+    return true;
+}
 
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS) k_matrix_tc(const float *__restrict__ jinv,
-                                                         const float *__restrict__ wdetj,
-                                                         const float *__restrict__ dphi, long long E,
-                                                         const double *__restrict__ lame, float *__restrict__ K,
-                                                         unsigned long long *__restrict__ status)
+__global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__restrict__ jinv,
+                                                                 const float *__restrict__ wdetj,
+                                                                 const float *__restrict__ dphi, long long E,
+                                                                 const double *__restrict__ lame,
+                                                                 float *__restrict__ K,
+                                                                 unsigned long long *__restrict__ status)
 {
     using P = TcSmem<MODE>;
     using L = typename P::L;
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char *opHi = smem + P::HI;
-    unsigned char *opLo = smem + P::LO;
-    float *ex = reinterpret_cast<float *>(smem + P::EX);
     float *ks = reinterpret_cast<float *>(smem + P::KS);
     float *sJw = reinterpret_cast<float *>(smem + P::JW);
+    float *sLM = reinterpret_cast<float *>(smem + P::LM);
     float *sDp = reinterpret_cast<float *>(smem + P::DP);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + P::MISC);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + P::MISC + 8);
-    float *sLM = reinterpret_cast<float *>(smem + P::MISC + 16);
-    int *abort_flag = reinterpret_cast<int *>(smem + P::MISC + 24);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + P::MISC);       // [2]
+    uint64_t *empty = reinterpret_cast<uint64_t *>(smem + P::MISC + 16); // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + P::MISC + 32);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + P::MISC + 36);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int i = tid; i < TC_Q * 3 * TC_N; i += TC_THREADS) sDp[i] = dphi[i];
+    for (int i = tid; i < TC_Q * 3 * TC_N; i += TC_THREADS_WS) sDp[i] = dphi[i];
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1) : "memory");
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(full + b)), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(empty + b)), "r"(1) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(TC_TMEM_COLS)
+                     "r"(2 * TC_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -271,150 +331,206 @@ __global__ void __launch_bounds__(TC_THREADS) k_matrix_tc(const float *__restric
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // prefetch registers: this thread's share of the next element's geometry
-    float pj[TC_PF], pw[TC_PF];
-    double plm = 0.0;
-    auto prefetch = [&](long long e) {
-        if (e >= E) return;
+    if (warp >= 3) {
+        // ------------------------------------------------------------ producer
+        const int ptid = tid - TC_CONS, pw = warp - 3;
+        constexpr int NPF = (TC_Q * 9 + TC_PROD - 1) / TC_PROD;  // 3 per thread
+        float pj[NPF], pwt[NPF];
+        double plm = 0.0;
+        auto prefetch = [&](long long e) {
+            if (e >= E) return;
 #pragma unroll
-        for (int u = 0; u < TC_PF; ++u) {
-            const int t = tid + u * TC_THREADS;
-            if (t < TC_Q * 9) {
-                pj[u] = jinv[e * TC_Q * 9 + t];
-                pw[u] = wdetj[e * TC_Q + t / 9];
-            }
-        }
-        if (tid < 2) plm = lame[2 * e + tid];
-    };
-    prefetch(blockIdx.x);
-
-    uint32_t phase = 0;
-    for (long long e = blockIdx.x; e < E; e += gridDim.x, phase ^= 1) {
-        // (a) geometry of the element, then start fetching the next one
-#pragma unroll
-        for (int u = 0; u < TC_PF; ++u) {
-            const int t = tid + u * TC_THREADS;
-            if (t < TC_Q * 9) sJw[t] = sqrtf(pw[u]) * pj[u];
-        }
-        if (tid < 2) sLM[tid] = (float)plm;
-        prefetch(e + gridDim.x);
-        __syncthreads();
-
-        // (b) X[(j,a)][q] = sum_k dphi[q][k][a] sqrt(w) Jinv[q][k][j], split into hi/lo.
-        // Lane (r, seg) of a tile owns node a = 8 g + r and the points of its 4-byte
-        // segment; it writes the same position of the three row blocks j, so every
-        // warp store covers one 128-byte core matrix.  Padding (a >= 27, q >= 27) is
-        // written as zero: the buffer held the previous element's exchange data.
-        {
-            constexpr int SEGV = 4 / P::EB;  // K values per 4-byte segment: 1 (tf32) or 2 (bf16)
-            constexpr int NCH = TC_KPAD / L::CHUNK;
-            const int r = lane >> 2, seg = lane & 3;
-            static_assert((4 * NCH) % 4 == 0, "tiles split evenly over the four warps");
-#pragma unroll
-            for (int it = 0; it < NCH; ++it) {
-                const int tile = warp + 4 * it;
-                const int g = tile / NCH, c = tile % NCH;
-                const int a = 8 * g + r, q0 = c * L::CHUNK + seg * SEGV;
-                const int off[3] = {L::offset(a, q0), L::offset(32 + a, q0), L::offset(64 + a, q0)};
-                operand_tile<MODE, SEGV, L::CHUNK>(sDp, sJw, a, q0, opHi, opLo, off);
-            }
-        }
-        fence_async_smem();  // operand writes -> tensor-core (async) proxy
-        __syncthreads();
-
-        // (c) MMA chain: D = sum over K steps of hi*hi (+ hi*lo + lo*hi)
-        if (tid == 0) {
-            tc_fence_after();
-            constexpr int KSTEP_BYTES = 2 * L::LBO;  // one MMA consumes two 16-byte K chunks
-            constexpr int NSTEP = TC_KPAD / (2 * L::CHUNK);
-            const uint32_t hi = smem_u32(opHi), lo = smem_u32(opLo);
-#pragma unroll
-            for (int s = 0; s < NSTEP; ++s) {
-                const uint64_t dh = smem_desc(hi + s * KSTEP_BYTES, L::LBO, L::SBO);
-                mma<MODE>(tmem, dh, dh, s > 0 ? 1u : 0u);
-                if constexpr (MODE != TC_BF16) {
-                    const uint64_t dl = smem_desc(lo + s * KSTEP_BYTES, L::LBO, L::SBO);
-                    mma<MODE>(tmem, dh, dl, 1u);
-                    mma<MODE>(tmem, dl, dh, 1u);
+            for (int u = 0; u < NPF; ++u) {
+                const int t = ptid + u * TC_PROD;
+                if (t < TC_Q * 9) {
+                    pj[u] = jinv[e * TC_Q * 9 + t];
+                    pwt[u] = wdetj[e * TC_Q + t / 9];
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(mbar))
-                         : "memory");
-        }
-
-        // (d) wait for the accumulator (bounded by time)
-        {
-            const long long t0 = clock64();
-            bool ok = false;
-            while (!(ok = mbar_try_wait(smem_u32(mbar), phase)) && clock64() - t0 < TC_WAIT_CYCLES) {
+            if (ptid < 2) plm = lame[2 * e + ptid];
+        };
+        prefetch(blockIdx.x);
+        constexpr int SEGV = 4 / P::EB;            // points per 4-byte segment: 1 (tf32) or 2 (bf16)
+        constexpr int NCH = TC_KPAD / L::CHUNK;    // K chunks: 8 (tf32) or 4 (bf16)
+        constexpr int PCH = (NCH + 2) / 3;         // chunks per producer warp
+        const int r = lane >> 2, seg = lane & 3;
+        float dreg[PCH][4][SEGV][3];
+#pragma unroll
+        for (int ci = 0; ci < PCH; ++ci)
+#pragma unroll
+            for (int g = 0; g < 4; ++g)
+#pragma unroll
+                for (int v = 0; v < SEGV; ++v) {
+                    const int q = (pw + 3 * ci) * L::CHUNK + seg * SEGV + v, a = 8 * g + r;
+                    const bool ok = q < TC_Q && a < TC_N && pw + 3 * ci < NCH;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) dreg[ci][g][v][k] = ok ? sDp[(q * 3 + k) * TC_N + a] : 0.0f;
+                }
+        int n = 0;
+        for (long long e = blockIdx.x; e < E; e += gridDim.x, ++n) {
+            const int b = n & 1;
+            unsigned char *opHi = smem + b * P::BUF + P::HI;
+            unsigned char *opLo = smem + b * P::BUF + P::LO;
+            float *jw = sJw + b * TC_Q * 9;
+            // the buffer and its accumulator are free once element n-2's epilogue is done
+            if (n >= 2) {
+                if (ptid == 0 && !mbar_wait_bounded(smem_u32(empty + b), ((n >> 1) - 1) & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    fe_report(status, FE_ERR_TIMEOUT, e);
+                }
+                named_sync(TC_BAR_PROD, TC_PROD);
+                if (*abort_flag) break;
+                tc_fence_after();
             }
-            if (!ok) {
+            // (a) geometry of the element, then start fetching the next one
+#pragma unroll
+            for (int u = 0; u < NPF; ++u) {
+                const int t = ptid + u * TC_PROD;
+                if (t < TC_Q * 9) jw[t] = sqrtf(pwt[u]) * pj[u];
+            }
+            if (ptid < 2) sLM[2 * b + ptid] = (float)plm;
+            prefetch(e + gridDim.x);
+            named_sync(TC_BAR_PROD, TC_PROD);
+
+            // (b) X[(j,a)][q] split into hi/lo: lane (r, seg) owns node a = 8 g + r and
+            // the points of its 4-byte segment, for the three row blocks j; warp pw
+            // takes the K chunks c = pw, pw + 3, ...  The reference gradients of these
+            // (q, a) pairs live in registers for the whole kernel; sqrt(w det J) J^-1
+            // of a point is read once per chunk.  Valid rows get zeros past the last
+            // point (the buffer held the exchange data of element n-2).
+#pragma unroll
+            for (int ci = 0; ci < PCH; ++ci) {
+                const int c = pw + 3 * ci;
+                if (c >= NCH) break;
+                const int q0 = c * L::CHUNK + seg * SEGV;
+                float J[SEGV][9];
+#pragma unroll
+                for (int v = 0; v < SEGV; ++v) {
+                    const int q = q0 + v < TC_Q ? q0 + v : 0;
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) J[v][t] = jw[q * 9 + t];
+                }
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    const int a = 8 * g + r;
+                    if (a >= TC_N) continue;
+                    uint32_t hv[3] = {0, 0, 0}, lv[3] = {0, 0, 0};
+#pragma unroll
+                    for (int v = 0; v < SEGV; ++v) {
+                        if (q0 + v >= TC_Q) continue;
+                        const float *dd = dreg[ci][g][v];
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            uint32_t h, l;
+                            split<MODE>(dd[0] * J[v][j] + dd[1] * J[v][3 + j] + dd[2] * J[v][6 + j], h, l);
+                            hv[j] |= h << (16 * v);
+                            lv[j] |= l << (16 * v);
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const int off = L::offset(32 * j + a, q0);
+                        *reinterpret_cast<uint32_t *>(opHi + off) = hv[j];
+                        if constexpr (MODE != TC_BF16) *reinterpret_cast<uint32_t *>(opLo + off) = lv[j];
+                    }
+                }
+            }
+            fence_async_smem();  // operand writes -> tensor-core (async) proxy
+            named_sync(TC_BAR_PROD, TC_PROD);
+
+            // (c) MMA chain into accumulator b: D = sum over K steps of hi*hi (+ hi*lo + lo*hi)
+            if (ptid == 0) {
+                tc_fence_after();
+                constexpr int KSTEP_BYTES = 2 * L::LBO;  // one MMA consumes two 16-byte K chunks
+                constexpr int NSTEP = TC_KPAD / (2 * L::CHUNK);
+                const uint32_t hi = smem_u32(opHi), lo = smem_u32(opLo);
+                const uint32_t d_tmem = tmem + b * TC_TMEM_COLS;
+#pragma unroll
+                for (int s = 0; s < NSTEP; ++s) {
+                    const uint64_t dh = smem_desc(hi + s * KSTEP_BYTES, L::LBO, L::SBO);
+                    mma<MODE>(d_tmem, dh, dh, s > 0 ? 1u : 0u);
+                    if constexpr (MODE != TC_BF16) {
+                        const uint64_t dl = smem_desc(lo + s * KSTEP_BYTES, L::LBO, L::SBO);
+                        mma<MODE>(d_tmem, dh, dl, 1u);
+                        mma<MODE>(d_tmem, dl, dh, 1u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(full + b))
+                             : "memory");
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ consumer
+        const int ctid = tid;
+        int n = 0;
+        for (long long e = blockIdx.x; e < E; e += gridDim.x, ++n) {
+            const int b = n & 1;
+            float *ex = reinterpret_cast<float *>(smem + b * P::BUF);
+            // (d) accumulator of element n complete
+            if (ctid == 0 && !mbar_wait_bounded(smem_u32(full + b), (n >> 1) & 1, abort_flag)) {
                 *abort_flag = 1;
                 fe_report(status, FE_ERR_TIMEOUT, e);
             }
-        }
-        tc_fence_after();
-        __syncthreads();
-        if (*abort_flag) break;
+            named_sync(TC_BAR_CONS, TC_CONS);
+            if (*abort_flag) break;
+            tc_fence_after();
 
-        // (e) accumulator rows (j = warp, a = lane) stay in registers and are
-        // published to the exchange buffer ex[j][l][a][b] (over the operands)
-        float d[TC_NCOL];
-        if (warp < 3) {
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
-            tmem_ld32(taddr, d);
-            tmem_ld32(taddr + 32, d + 32);
-            tmem_ld32(taddr + 64, d + 64);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            // (e) rows (j = warp, a = lane) of accumulator b -> registers -> exchange area
+            float d[TC_NCOL];
+            {
+                const uint32_t taddr = tmem + b * TC_TMEM_COLS + ((uint32_t)(32 * warp) << 16);
+                tmem_ld32(taddr, d);
+                tmem_ld32(taddr + 32, d + 32);
+                tmem_ld32(taddr + 64, d + 64);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (lane < TC_N) {
+                    // ex[w][0] = A_ww, ex[w][1] = A_w,w+1 (rows a, columns b)
+                    float *e0 = ex + ((warp * 2 + 0) * TC_N + lane) * P::EX_STRIDE;
+                    float *e1 = ex + ((warp * 2 + 1) * TC_N + lane) * P::EX_STRIDE;
+                    if (warp == 0) publish_blocks<0>(d, e0, e1);
+                    else if (warp == 1) publish_blocks<1>(d, e0, e1);
+                    else publish_blocks<2>(d, e0, e1);
+                }
+            }
+            tc_fence_before();
+            if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // staging drained
+            named_sync(TC_BAR_CONS, TC_CONS);
+
+            // (f) blocks K_ii and K_i,i+1 of row (i = warp, a = lane), and K_i+1,i as columns
+            const float *dst0 = K + e * (long long)(TC_NROW * TC_NROW);
+            const int shift = (int)(((unsigned long long)dst0 % 16) / 4);
+            float *kst = ks + shift;
             if (lane < TC_N) {
-#pragma unroll
-                for (int l = 0; l < 3; ++l)
-#pragma unroll
-                    for (int b = 0; b < TC_N; ++b) ex[((warp * 3 + l) * TC_N + lane) * P::EX_STRIDE + b] = d[32 * l + b];
+                const float lam = sLM[2 * b], mu = sLM[2 * b + 1];
+                // one code path per warp keeps every register index static
+                if (warp == 0) epilogue_rows<0, P::EX_STRIDE>(d, ex, lane, lam, mu, kst);
+                else if (warp == 1) epilogue_rows<1, P::EX_STRIDE>(d, ex, lane, lam, mu, kst);
+                else epilogue_rows<2, P::EX_STRIDE>(d, ex, lane, lam, mu, kst);
+            }
+            fence_async_smem();
+            named_sync(TC_BAR_CONS, TC_CONS);
+
+            // (g) one bulk copy per element matrix; buffer b goes back to the producers
+            if (ctid == 0) {
+                float *dst = K + e * (long long)(TC_NROW * TC_NROW);
+                constexpr int LEN = TC_NROW * TC_NROW;
+                const int head = (4 - shift) % 4;
+                const int body = (LEN - head) / 4 * 4;
+                for (int t = 0; t < head; ++t) dst[t] = kst[t];
+                for (int t = head + body; t < LEN; ++t) dst[t] = kst[t];
+                bulk_store(dst + head, kst + head, (unsigned)(body * 4));
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(empty + b)) : "memory");
             }
         }
-        tc_fence_before();
-        if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // staging drained
-        __syncthreads();
-
-        // (f) row (i = warp, a = lane) of K_e into the staging buffer
-        const float *dst0 = K + e * (long long)(TC_NROW * TC_NROW);
-        const int shift = (int)(((unsigned long long)dst0 % 16) / 4);
-        float *kst = ks + shift;
-        if (warp < 3 && lane < TC_N) {
-            const int i = warp, a = lane;
-            const float lam = sLM[0], mu = sLM[1];
-            float *row = kst + (i * TC_N + a) * TC_NROW;
-            const float *o1 = ex + ((((i + 1) % 3) * 4) * TC_N + a) * P::EX_STRIDE;  // A_jj[a][.] of the other warps
-            const float *o2 = ex + ((((i + 2) % 3) * 4) * TC_N + a) * P::EX_STRIDE;
-#pragma unroll
-            for (int k = 0; k < 3; ++k)
-                k_row_block<P::EX_STRIDE>(d + 32 * k,                                    // A_ik[a][.] (registers)
-                                          ex + ((i * 3 + k) * TC_N) * P::EX_STRIDE + a,  // A_ik[.][a]
-                                          o1, o2, k == i, lam, mu, row + k * TC_N);
-        }
-        fence_async_smem();
-        __syncthreads();
-
-        // (g) one bulk copy per element matrix (scalar head/tail to reach 16-byte alignment)
-        if (tid == 0) {
-            float *dst = K + e * (long long)(TC_NROW * TC_NROW);
-            constexpr int LEN = TC_NROW * TC_NROW;
-            const int head = (4 - shift) % 4;
-            const int body = (LEN - head) / 4 * 4;
-            for (int t = 0; t < head; ++t) dst[t] = kst[t];
-            for (int t = head + body; t < LEN; ++t) dst[t] = kst[t];
-            bulk_store(dst + head, kst + head, (unsigned)(body * 4));
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        }
+        if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
-    if (tid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_TMEM_COLS)
                      : "memory");
 }
 
@@ -439,13 +555,13 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
     err = cudaFuncGetAttributes(&fa, kern);
     if (err != cudaSuccess) return err;
     int per_sm = smem_sm / (P::BYTES + 1024);
-    const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * TC_THREADS);
+    const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * TC_THREADS_WS);
     if (by_regs < per_sm) per_sm = by_regs;
-    if (per_sm * TC_TMEM_COLS > 512) per_sm = 512 / TC_TMEM_COLS;
+    if (per_sm * 2 * TC_TMEM_COLS > 512) per_sm = 512 / (2 * TC_TMEM_COLS);
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long blocks = (long long)per_sm * sm_count;
     if (blocks > g->mesh.n_elems) blocks = g->mesh.n_elems;
-    kern<<<(unsigned)blocks, TC_THREADS, P::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->mesh.n_elems,
+    kern<<<(unsigned)blocks, TC_THREADS_WS, P::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->mesh.n_elems,
                                                         mat.data, (float *)K, status);
     return cudaGetLastError();
 }
