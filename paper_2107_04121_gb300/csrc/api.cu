@@ -50,6 +50,8 @@ void free_geometry(fe_geometry_h *g)
     cudaFree(g->d_w64);
     cudaFree(g->d_b1d);
     cudaFree(g->d_d1d);
+    cudaFree(g->d_b1d32);
+    cudaFree(g->d_d1d32);
     cudaFree(g->d_phi32);
     cudaFree(g->d_dphi32);
     cudaFree(g->d_jinv64);
@@ -184,6 +186,15 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
         if (e == cudaSuccess) e = dev_alloc(&g->d_d1d, n);
         if (e == cudaSuccess) e = cudaMemcpy(g->d_b1d, basis->b1d, sizeof(double) * n, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(g->d_d1d, basis->d1d, sizeof(double) * n, cudaMemcpyHostToDevice);
+        std::vector<float> b32(n), d32(n);
+        for (size_t t = 0; t < n; ++t) {
+            b32[t] = (float)basis->b1d[t];
+            d32[t] = (float)basis->d1d[t];
+        }
+        if (e == cudaSuccess) e = dev_alloc(&g->d_b1d32, n);
+        if (e == cudaSuccess) e = dev_alloc(&g->d_d1d32, n);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_b1d32, b32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(g->d_d1d32, d32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess && (flags & FE_GEOM_STORE_F64)) {
         e = dev_alloc(&g->d_jinv64, (size_t)E * Q * 9);

@@ -26,6 +26,7 @@ struct fe_geometry_h {
     double *d_phi64, *d_dphi64, *d_w64;  // (Q,N), (Q,3,N), (Q)
     int n1d, nq1d;                       // tensor-product factors (sum-factorised geometry)
     double *d_b1d, *d_d1d;               // (nq1d, n1d) each, or null
+    float *d_b1d32, *d_d1d32;
     float *d_phi32, *d_dphi32;
     double *d_jinv64, *d_wdetj64;  // (E,Q,3,3), (E,Q)
     float *d_jinv32, *d_wdetj32;

@@ -166,6 +166,349 @@ __global__ void __launch_bounds__(THREADS) k_residual(const T *__restrict__ jinv
     }
 }
 
+// Sum-factorised residual for tensor-product hexahedra (n1 nodes, nq points per
+// axis; B/D the 1-D basis values/derivatives at the points, (nq, n1)).  Per
+// element and component c with nodal values U[k][j][i]:
+//   phase 1  u_h or grad_xi u_h at the points by three 1-D contractions
+//            (x: B, D; y: B, D; z: B, D), as in the geometry kernel
+//   point    the flux F (mass: c wdetJ u_h; Laplace: c wdetJ J^-1 J^-T g;
+//            elasticity: wdetJ J^-1 sigma with sigma = D e(u_h))
+//   phase 2  r[a] = sum_q sum_m F_m(q) d phi_a / d xi_m (q) by the transposed
+//            contractions (z, y, x)
+// Each thread computes one whole 1-D line of a stage (n1 or nq outputs) with
+// the 1-D tables in registers; EPB elements per CTA, barriers between stages.
+template <typename T, int N1, int NQ, int KIND, int MATK, int EPB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_residual_sf(const T *__restrict__ jinv, const T *__restrict__ wdetj,
+                                                         const T *__restrict__ b1d, const T *__restrict__ d1d,
+                                                         const int32_t *__restrict__ conn, long long E, int ncomp,
+                                                         const double *__restrict__ mat, int mat_t,
+                                                         const T *__restrict__ u, T *__restrict__ r,
+                                                         long long n_nodes, unsigned long long *__restrict__ status)
+{
+    constexpr int N = N1 * N1 * N1, Q = NQ * NQ * NQ;
+    constexpr bool GRAD = KIND != FK_MASS;
+    constexpr int NC = KIND == FK_LAPLACE ? 1 : 3;  // max components
+    constexpr int NM = GRAD ? 3 : 1;                // derivative directions carried
+    constexpr int LX = N1 * N1 * NQ, LY = N1 * NQ * NQ;
+    __shared__ T sU[EPB][NC][N];
+    __shared__ T sX[EPB][NC][GRAD ? 2 : 1][LX];  // stage x (phase 1) / stage y^T (phase 2)
+    __shared__ T sY[EPB][NC][NM][LY];            // stage y (phase 1) / stage z^T (phase 2)
+    __shared__ T sQ[EPB][NC][NM][Q];             // point values: gradients, then fluxes
+    __shared__ T sJ[EPB][Q][9];
+    __shared__ T sW[EPB][Q];
+    __shared__ T sM[EPB][36];
+    T B[NQ][N1], D[NQ][N1];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            B[q][i] = b1d[q * N1 + i];
+            D[q][i] = d1d[q * N1 + i];
+        }
+    const int nc = ncomp;
+    for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
+        const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
+        __syncthreads();
+        if constexpr (GRAD)
+            for (int t = threadIdx.x; t < ne * Q * 9; t += THREADS) (&sJ[0][0][0])[t] = jinv[e0 * Q * 9 + t];
+        for (int t = threadIdx.x; t < ne * Q; t += THREADS) (&sW[0][0])[t] = wdetj[e0 * Q + t];
+        for (int t = threadIdx.x; t < ne * N; t += THREADS) {
+            const int el = t / N, a = t % N;
+            const long long node = conn[(e0 + el) * N + a];
+            const bool ok = (unsigned long long)node < (unsigned long long)n_nodes;  // never read outside u
+            if (!ok) fe_report(status, FE_ERR_SHAPE, e0 + el);
+            for (int c = 0; c < nc; ++c) sU[el][c][a] = ok ? u[node * nc + c] : (T)0;
+        }
+        if constexpr (MATK == 2) {
+            for (int t = threadIdx.x; t < ne * 36; t += THREADS) {
+                const int el = t / 36, I = (t % 36) / 6, Kv = t % 6;
+                const long long e = e0 + el;
+                sM[el][t % 36] = (T)(mat_t ? mat[e * 36 + Kv * 6 + I] : mat[e * 36 + I * 6 + Kv]);
+            }
+        } else if constexpr (MATK == 1) {
+            for (int t = threadIdx.x; t < ne * 2; t += THREADS) sM[t / 2][t % 2] = (T)mat[e0 * 2 + t];
+        } else {
+            for (int t = threadIdx.x; t < ne; t += THREADS) sM[t][0] = mat ? (T)mat[e0 + t] : (T)1;
+        }
+        __syncthreads();
+        // ---- phase 1, x: line (el, c, k, j) -> sX[0] = B_x U, sX[1] = D_x U at qx = 0..nq-1
+        for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
+            const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
+            T x[N1];
+#pragma unroll
+            for (int i = 0; i < N1; ++i) x[i] = sU[el][c][kj * N1 + i];
+#pragma unroll
+            for (int qx = 0; qx < NQ; ++qx) {
+                T v0 = 0, v1 = 0;
+#pragma unroll
+                for (int i = 0; i < N1; ++i) {
+                    v0 = fma(B[qx][i], x[i], v0);
+                    if constexpr (GRAD) v1 = fma(D[qx][i], x[i], v1);
+                }
+                sX[el][c][0][kj * NQ + qx] = v0;
+                if constexpr (GRAD) sX[el][c][1][kj * NQ + qx] = v1;
+            }
+        }
+        __syncthreads();
+        // ---- phase 1, y: line (el, c, k, qx) -> at qy: [0] B_y B_x, [1] D_y B_x, [2] B_y D_x
+        for (int t = threadIdx.x; t < ne * nc * N1 * NQ; t += THREADS) {
+            const int qx = t % NQ, k = (t / NQ) % N1, c = (t / (NQ * N1)) % nc, el = t / (NQ * N1 * nc);
+            T a0[N1], a1[N1];
+#pragma unroll
+            for (int j = 0; j < N1; ++j) {
+                a0[j] = sX[el][c][0][(k * N1 + j) * NQ + qx];
+                if constexpr (GRAD) a1[j] = sX[el][c][1][(k * N1 + j) * NQ + qx];
+            }
+#pragma unroll
+            for (int qy = 0; qy < NQ; ++qy) {
+                T v0 = 0, v1 = 0, v2 = 0;
+#pragma unroll
+                for (int j = 0; j < N1; ++j) {
+                    v0 = fma(B[qy][j], a0[j], v0);
+                    if constexpr (GRAD) {
+                        v1 = fma(D[qy][j], a0[j], v1);
+                        v2 = fma(B[qy][j], a1[j], v2);
+                    }
+                }
+                const int o = (k * NQ + qy) * NQ + qx;
+                sY[el][c][0][o] = v0;
+                if constexpr (GRAD) {
+                    sY[el][c][1][o] = v1;
+                    sY[el][c][2][o] = v2;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- phase 1, z: line (el, c, qy, qx) -> sQ[m] at qz = d u_c / d xi_m (or u_c)
+        for (int t = threadIdx.x; t < ne * nc * NQ * NQ; t += THREADS) {
+            const int qx = t % NQ, qy = (t / NQ) % NQ, c = (t / (NQ * NQ)) % nc, el = t / (NQ * NQ * nc);
+            T y0[N1], y1[N1], y2[N1];
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                const int o = (k * NQ + qy) * NQ + qx;
+                y0[k] = sY[el][c][0][o];
+                if constexpr (GRAD) {
+                    y1[k] = sY[el][c][1][o];
+                    y2[k] = sY[el][c][2][o];
+                }
+            }
+#pragma unroll
+            for (int qz = 0; qz < NQ; ++qz) {
+                const int q = (qz * NQ + qy) * NQ + qx;
+                T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+                for (int k = 0; k < N1; ++k) {
+                    if constexpr (GRAD) {
+                        gx = fma(B[qz][k], y2[k], gx);
+                        gy = fma(B[qz][k], y1[k], gy);
+                        gz = fma(D[qz][k], y0[k], gz);
+                    } else {
+                        gx = fma(B[qz][k], y0[k], gx);
+                    }
+                }
+                sQ[el][c][0][q] = gx;
+                if constexpr (GRAD) {
+                    sQ[el][c][1][q] = gy;
+                    sQ[el][c][2][q] = gz;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- pointwise flux, in place: F_c,m(q) with r = sum_q sum_m F_c,m dphi_a/dxi_m
+        for (int t = threadIdx.x; t < ne * Q; t += THREADS) {
+            const int el = t / Q, q = t % Q;
+            const T wd = sW[el][q];
+            if constexpr (KIND == FK_MASS) {
+                const T cw = sM[el][0] * wd;
+                for (int c = 0; c < nc; ++c) sQ[el][c][0][q] *= cw;
+            } else {
+                T Ji[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) Ji[k] = sJ[el][q][k];
+                T H[NC][3];  // physical gradient H[c][j] = sum_m g[c][m] Jinv[m][j]
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const T g0 = sQ[el][c][0][q], g1 = sQ[el][c][1][q], g2 = sQ[el][c][2][q];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) H[c][j] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
+                }
+                T S[NC][3];
+                if constexpr (KIND == FK_LAPLACE) {
+                    const T cw = sM[el][0] * wd;
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) S[0][j] = cw * H[0][j];
+                } else if constexpr (MATK == 1) {
+                    // isotropic: sigma = lambda tr(e) I + 2 mu e
+                    const T lam = sM[el][0] * wd, mu = sM[el][1] * wd;
+                    const T tr = lam * (H[0][0] + H[1][1] + H[2][2]);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) S[i][j] = mu * (H[i][j] + H[j][i]) + (i == j ? tr : (T)0);
+                } else {
+                    const T *Dm = sM[el];
+                    const T eps[6] = {H[0][0], H[1][1], H[2][2], H[0][1] + H[1][0], H[0][2] + H[2][0],
+                                      H[1][2] + H[2][1]};
+                    T sig[6];
+#pragma unroll
+                    for (int I = 0; I < 6; ++I) {
+                        T acc = 0;
+#pragma unroll
+                        for (int Kv = 0; Kv < 6; ++Kv) acc = fma(Dm[I * 6 + Kv], eps[Kv], acc);
+                        sig[I] = wd * acc;
+                    }
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) S[i][j] = sig[fe_voigt(i, j)];
+                }
+#pragma unroll
+                for (int c = 0; c < NC; ++c)
+#pragma unroll
+                    for (int m = 0; m < 3; ++m)
+                        sQ[el][c][m][q] = S[c][0] * Ji[m * 3] + S[c][1] * Ji[m * 3 + 1] + S[c][2] * Ji[m * 3 + 2];
+            }
+        }
+        __syncthreads();
+        // ---- phase 2, z^T: line (el, c, qy, qx) -> at k: [0] B_z F_x, [1] B_z F_y, [2] D_z F_z
+        for (int t = threadIdx.x; t < ne * nc * NQ * NQ; t += THREADS) {
+            const int qx = t % NQ, qy = (t / NQ) % NQ, c = (t / (NQ * NQ)) % nc, el = t / (NQ * NQ * nc);
+            T f0[NQ], f1[NQ], f2[NQ];
+#pragma unroll
+            for (int qz = 0; qz < NQ; ++qz) {
+                const int q = (qz * NQ + qy) * NQ + qx;
+                f0[qz] = sQ[el][c][0][q];
+                if constexpr (GRAD) {
+                    f1[qz] = sQ[el][c][1][q];
+                    f2[qz] = sQ[el][c][2][q];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                T v0 = 0, v1 = 0, v2 = 0;
+#pragma unroll
+                for (int qz = 0; qz < NQ; ++qz) {
+                    v0 = fma(B[qz][k], f0[qz], v0);
+                    if constexpr (GRAD) {
+                        v1 = fma(B[qz][k], f1[qz], v1);
+                        v2 = fma(D[qz][k], f2[qz], v2);
+                    }
+                }
+                const int o = (k * NQ + qy) * NQ + qx;
+                sY[el][c][0][o] = v0;
+                if constexpr (GRAD) {
+                    sY[el][c][1][o] = v1;
+                    sY[el][c][2][o] = v2;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- phase 2, y^T: line (el, c, k, qx) -> at j: [0] B_y [0], [1] D_y [1] + B_y [2]
+        for (int t = threadIdx.x; t < ne * nc * N1 * NQ; t += THREADS) {
+            const int qx = t % NQ, k = (t / NQ) % N1, c = (t / (NQ * N1)) % nc, el = t / (NQ * N1 * nc);
+            T y0[NQ], y1[NQ], y2[NQ];
+#pragma unroll
+            for (int qy = 0; qy < NQ; ++qy) {
+                const int o = (k * NQ + qy) * NQ + qx;
+                y0[qy] = sY[el][c][0][o];
+                if constexpr (GRAD) {
+                    y1[qy] = sY[el][c][1][o];
+                    y2[qy] = sY[el][c][2][o];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < N1; ++j) {
+                T v0 = 0, v1 = 0;
+#pragma unroll
+                for (int qy = 0; qy < NQ; ++qy) {
+                    v0 = fma(B[qy][j], y0[qy], v0);
+                    if constexpr (GRAD) v1 = fma(D[qy][j], y1[qy], fma(B[qy][j], y2[qy], v1));
+                }
+                sX[el][c][0][(k * N1 + j) * NQ + qx] = v0;
+                if constexpr (GRAD) sX[el][c][1][(k * N1 + j) * NQ + qx] = v1;
+            }
+        }
+        __syncthreads();
+        // ---- phase 2, x^T: line (el, c, k, j) -> r at i = D_x [0] + B_x [1] (mass: B_x [0])
+        for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
+            const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
+            T x0[NQ], x1[NQ];
+#pragma unroll
+            for (int qx = 0; qx < NQ; ++qx) {
+                x0[qx] = sX[el][c][0][kj * NQ + qx];
+                if constexpr (GRAD) x1[qx] = sX[el][c][1][kj * NQ + qx];
+            }
+            T *ro = r + (e0 + el) * (long long)nc * N + c * N + kj * N1;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                T v = 0;
+#pragma unroll
+                for (int qx = 0; qx < NQ; ++qx) {
+                    if constexpr (GRAD)
+                        v = fma(D[qx][i], x0[qx], fma(B[qx][i], x1[qx], v));
+                    else
+                        v = fma(B[qx][i], x0[qx], v);
+                }
+                ro[i] = v;
+            }
+        }
+    }
+}
+
+template <typename T, int N1, int NQ, int KIND, int MATK, int EPB>
+cudaError_t launch_res_sf(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
+                          unsigned long long *st, cudaStream_t s)
+{
+    constexpr int THREADS = 256;
+    auto kern = k_residual_sf<T, N1, NQ, KIND, MATK, EPB, THREADS>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const long long E = g->mesh.n_elems;
+    long long blocks = (E + EPB - 1) / EPB;
+    const long long cap = (long long)per_sm * sms * 4;
+    if (blocks > cap) blocks = cap;
+    const bool f64 = sizeof(T) == 8;
+    kern<<<(unsigned)blocks, THREADS, 0, s>>>(
+        f64 ? (const T *)g->d_jinv64 : (const T *)g->d_jinv32, f64 ? (const T *)g->d_wdetj64 : (const T *)g->d_wdetj32,
+        f64 ? (const T *)g->d_b1d : (const T *)g->d_b1d32, f64 ? (const T *)g->d_d1d : (const T *)g->d_d1d32,
+        g->mesh.conn, E, f->ncomp, mat.data, mat.transposed, (const T *)u, (T *)r, g->mesh.n_nodes, st);
+    return cudaGetLastError();
+}
+
+template <typename T, int N1, int NQ, int EPB_S, int EPB_V>
+cudaError_t dispatch_sf_kind(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
+                             unsigned long long *st, cudaStream_t s)
+{
+    switch (f->kind) {
+    case FK_LAPLACE: return launch_res_sf<T, N1, NQ, FK_LAPLACE, 0, EPB_S>(g, f, mat, u, r, st, s);
+    case FK_MASS: return launch_res_sf<T, N1, NQ, FK_MASS, 0, EPB_S>(g, f, mat, u, r, st, s);
+    case FK_ELASTICITY:
+        if (mat.kind == FE_MAT_LAME) return launch_res_sf<T, N1, NQ, FK_ELASTICITY, 1, EPB_V>(g, f, mat, u, r, st, s);
+        return launch_res_sf<T, N1, NQ, FK_ELASTICITY, 2, EPB_V>(g, f, mat, u, r, st, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Tensor-product bases with their 1-D factors: sum-factorised kernel; element
+// counts per CTA keep the static shared memory under 48 KB.
+template <typename T>
+cudaError_t dispatch_sf(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
+                        unsigned long long *st, cudaStream_t s)
+{
+    const int n1 = g->n1d, nq = g->nq1d;
+    constexpr bool D = sizeof(T) == 8;
+    if (n1 == 2 && nq == 2) return dispatch_sf_kind<T, 2, 2, 16, 8>(g, f, mat, u, r, st, s);
+    if (n1 == 2 && nq == 3) return dispatch_sf_kind<T, 2, 3, 8, 4>(g, f, mat, u, r, st, s);
+    if (n1 == 3 && nq == 3) return dispatch_sf_kind<T, 3, 3, (D ? 4 : 8), (D ? 2 : 6)>(g, f, mat, u, r, st, s);
+    if (n1 == 3 && nq == 4) return dispatch_sf_kind<T, 3, 4, (D ? 2 : 4), (D ? 1 : 2)>(g, f, mat, u, r, st, s);
+    if (n1 == 4 && nq == 4) return dispatch_sf_kind<T, 4, 4, (D ? 2 : 4), 1>(g, f, mat, u, r, st, s);
+    return cudaErrorInvalidValue;
+}
+
 template <typename T, int N, int Q, int KIND, int EPB>
 cudaError_t launch_res(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
                        unsigned long long *st, cudaStream_t s)
@@ -224,5 +567,7 @@ cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_ma
                                const void *u, void *r, unsigned long long *st, cudaStream_t s)
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
+    if (g->d_b1d)
+        return f64 ? dispatch_sf<double>(g, f, mat, u, r, st, s) : dispatch_sf<float>(g, f, mat, u, r, st, s);
     return f64 ? dispatch<double>(g, f, mat, u, r, st, s) : dispatch<float>(g, f, mat, u, r, st, s);
 }
