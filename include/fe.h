@@ -177,6 +177,10 @@ fe_status fe_refbasis_hex_1d(int p, int nq, double *b1d, double *d1d);
 /* Storage flags of fe_geometry. */
 #define FE_GEOM_STORE_F64 1u /* keep float64 J^-1 and w det J (needed by FE_F64 evaluation) */
 #define FE_GEOM_STORE_F32 2u /* keep float32 copies (needed by the other precisions) */
+#define FE_GEOM_DEFERRED 4u  /* compute lazily: fe_geometry / fe_geometry_update only mark the
+                                geometry stale; the next call that reads it (evaluation or
+                                fe_geometry_get) computes it first, on its own stream.  The
+                                stale mark is host state: use a deferred handle from one stream. */
 
 /* Geometry of the reference mapping (Sec. 4.1): for every element e and
  * quadrature point q, J = sum_a x_a (x) grad_xi phi_a(q), det J, J^-1 and

@@ -13,6 +13,14 @@ cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe
 cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
                                 void *K, int sm_count, unsigned long long *status, cudaStream_t s);
 
+// A deferred handle whose geometry is stale gets it computed before any use.
+static cudaError_t settle_geometry(fe_geometry_h *g, unsigned long long *status, cudaStream_t s)
+{
+    if (!g->pending) return cudaSuccess;
+    g->pending = 0;
+    return fe_launch_geometry(g, status, s);
+}
+
 namespace {
 
 thread_local char g_last_error[256] = "";
@@ -150,8 +158,8 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
     if (!ctx || !out || !valid_mesh(mesh) || !basis || !quad || !basis->phi || !basis->dphi || !quad->weights)
         return FE_ERR_INVALID_ARG;
     *out = nullptr;
-    if (flags & ~(FE_GEOM_STORE_F64 | FE_GEOM_STORE_F32)) return FE_ERR_INVALID_ARG;
-    if (flags == 0) flags = FE_GEOM_STORE_F64 | FE_GEOM_STORE_F32;
+    if (flags & ~(FE_GEOM_STORE_F64 | FE_GEOM_STORE_F32 | FE_GEOM_DEFERRED)) return FE_ERR_INVALID_ARG;
+    if ((flags & ~FE_GEOM_DEFERRED) == 0) flags |= FE_GEOM_STORE_F64 | FE_GEOM_STORE_F32;
     const int N = basis->n_basis, Q = basis->n_qp;
     if (N != mesh->nodes_per_elem || quad->n_qp != Q || !fe_supported_nq(N, Q)) return FE_ERR_SHAPE;
     const bool tensor = basis->b1d || basis->d1d;
@@ -211,7 +219,12 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
     if (e == cudaSuccess) e = cudaMemcpy(g->d_phi32, phi32.data(), sizeof(float) * Q * N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(g->d_dphi32, dphi32.data(), sizeof(float) * Q * 3 * N, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = fe_launch_geometry(g, ctx->d_status, s);
+    if (e == cudaSuccess) {
+        if (flags & FE_GEOM_DEFERRED)
+            g->pending = 1;
+        else
+            e = fe_launch_geometry(g, ctx->d_status, s);
+    }
     if (e != cudaSuccess) {
         fe_status st = from_cuda(e, "fe_geometry");
         free_geometry(g);
@@ -225,6 +238,10 @@ fe_status fe_geometry_update(fe_ctx *ctx, fe_geometry_h *geom, fe_stream_t strea
 {
     if (!ctx || !geom) return FE_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
+    if (geom->flags & FE_GEOM_DEFERRED) {
+        geom->pending = 1;
+        return FE_OK;
+    }
     return from_cuda(fe_launch_geometry(geom, ctx->d_status, to_cuda(stream)), "fe_geometry_update");
 }
 
@@ -245,6 +262,8 @@ fe_status fe_geometry_get(fe_ctx *ctx, const fe_geometry_h *g, fe_geom_field fie
     if (g->mesh.n_elems == 0) return FE_OK;
     cudaSetDevice(ctx->device);
     cudaStream_t s = to_cuda(stream);
+    fe_status st0 = from_cuda(settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, s), "fe_geometry_get");
+    if (st0) return st0;
     const size_t es = f64 ? 8 : 4;
     const long long E = g->mesh.n_elems;
     cudaError_t e;
@@ -295,13 +314,17 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
     if (st) return st;
     if (diff_op != form->state_op) return FE_ERR_INVALID_ARG;
     cudaError_t e;
+    fe_geometry_h *gm = const_cast<fe_geometry_h *>(g);
+    cudaStream_t s = to_cuda(stream);
     if (prec == FE_F64 || prec == FE_F32) {
-        e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, to_cuda(stream));
+        e = settle_geometry(gm, ctx->d_status, s);
+        if (e == cudaSuccess) e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, s);
     } else {
         // tensor-core kernels: Q2 elasticity (27 nodes, 27 points) with Lame materials
         if (form->kind != FK_ELASTICITY || form->mat != FE_MAT_LAME || !(g->N == 27 && g->Q == 27))
             return FE_ERR_UNSUPPORTED_SPEC;
-        e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, ctx->d_status, to_cuda(stream));
+        e = settle_geometry(gm, ctx->d_status, s);
+        if (e == cudaSuccess) e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, ctx->d_status, s);
     }
     return from_cuda(e, "fe_eval_matrix");
 }
@@ -313,7 +336,8 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
     fe_status st = eval_common(ctx, form, g, args, prec, r_out, &mat);
     if (st) return st;
     if (!args || (!args[form->state_op] && g->mesh.n_elems > 0)) return FE_ERR_INVALID_ARG;
-    cudaError_t e = fe_launch_residual(g, form, mat, prec == FE_F64, args[form->state_op], r_out, ctx->d_status,
+    cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, to_cuda(stream));
+    if (e == cudaSuccess) e = fe_launch_residual(g, form, mat, prec == FE_F64, args[form->state_op], r_out, ctx->d_status,
                                        to_cuda(stream));
     return from_cuda(e, "fe_eval_residual");
 }

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "fe_internal.h"
 
 // Record a device-detected problem: the first error code wins, the smallest
@@ -24,4 +26,34 @@ __device__ __forceinline__ T fe_ld(const T *p)
 __host__ __device__ __forceinline__ int fe_voigt(int i, int j)
 {
     return i == j ? i : (i + j == 1 ? 3 : (i + j == 2 ? 4 : 5));
+}
+
+// Launch configuration (resident CTAs per SM times SM count) computed once per
+// kernel instantiation and device: kernel attributes are set and occupancy is
+// queried on the first launch only, so later launches cost no driver calls
+// beyond the launch itself.
+struct FeLaunchCache {
+    std::atomic<int> ready[64];
+    long long value[64];
+};
+
+template <typename F>
+inline cudaError_t fe_cached_grid(FeLaunchCache &c, F compute, long long *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && c.ready[dev].load(std::memory_order_acquire)) {
+        *out = c.value[dev];
+        return cudaSuccess;
+    }
+    long long v = 0;
+    e = compute(dev, &v);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) {
+        c.value[dev] = v;
+        c.ready[dev].store(1, std::memory_order_release);
+    }
+    *out = v;
+    return cudaSuccess;
 }

@@ -30,6 +30,7 @@ struct fe_geometry_h {
     float *d_phi32, *d_dphi32;
     double *d_jinv64, *d_wdetj64;  // (E,Q,3,3), (E,Q)
     float *d_jinv32, *d_wdetj32;
+    int pending;  // deferred handle: the stored geometry is stale (host-side, stream-ordered use)
 };
 
 enum fe_form_kind { FK_LAPLACE = 0, FK_MASS = 1, FK_ELASTICITY = 2 };

@@ -228,7 +228,17 @@ cudaError_t launch_geom(const fe_geometry_h *g, unsigned long long *st, cudaStre
 {
     const size_t smem = (size_t)g->Q * 3 * N * sizeof(double);
     if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(k_geometry<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        static FeLaunchCache cache;
+        long long unused = 0;
+        cudaError_t err = fe_cached_grid(
+            cache,
+            [&](int, long long *v) {
+                *v = 1;
+                // the largest table any (N, Q) pair of this instantiation needs
+                return cudaFuncSetAttribute(k_geometry<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            64 * 3 * N * (int)sizeof(double));
+            },
+            &unused);
         if (err != cudaSuccess) return err;
     }
     const long long total = g->mesh.n_elems * g->Q;
@@ -245,14 +255,24 @@ cudaError_t launch_geom(const fe_geometry_h *g, unsigned long long *st, cudaStre
 template <int N1, int NQ, int EPB>
 cudaError_t launch_geom_sf(const fe_geometry_h *g, unsigned long long *st, cudaStream_t s)
 {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_geometry_sf<N1, NQ, EPB>, kGeomThreads, 0);
+    static FeLaunchCache cache;
+    long long cap = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int dev, long long *v) {
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaError_t e2 =
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_geometry_sf<N1, NQ, EPB>, kGeomThreads, 0);
+            if (e2 != cudaSuccess) return e2;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            *v = (long long)per_sm * sms * 8;
+            return cudaSuccess;
+        },
+        &cap);
     if (err != cudaSuccess) return err;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     long long blocks = (g->mesh.n_elems + EPB - 1) / EPB;
-    if (blocks > (long long)per_sm * sms * 8) blocks = (long long)per_sm * sms * 8;
+    if (blocks > cap) blocks = cap;
     const bool f64 = g->flags & FE_GEOM_STORE_F64, f32 = g->flags & FE_GEOM_STORE_F32;
     k_geometry_sf<N1, NQ, EPB><<<(unsigned)blocks, kGeomThreads, 0, s>>>(
         g->mesh.coords, g->mesh.conn, g->mesh.n_elems, g->mesh.n_nodes, g->d_b1d, g->d_d1d, g->d_w64,

@@ -477,15 +477,25 @@ cudaError_t launch_sym(const fe_geometry_h *g, const fe_form_h *f, fe_material_a
     static_assert(EPB * (N / T) * (N / T + 1) / 2 <= THREADS, "one tile per thread");
     static_assert(P::BYTES <= 227 * 1024, "shared memory plan exceeds one CTA's limit");
     auto kern = k_matrix_sym<S, N, Q, KIND, MATK, T, EPB, THREADS, STAGE>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::BYTES);
+    static FeLaunchCache cache;
+    long long per_sm = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int, long long *v) {
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::BYTES);
+            if (e2 != cudaSuccess) return e2;
+            int n = 0;
+            e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, THREADS, P::BYTES);
+            if (e2 != cudaSuccess) return e2;
+            if (n < 1) return cudaErrorInvalidConfiguration;
+            *v = n;
+            return cudaSuccess;
+        },
+        &per_sm);
     if (err != cudaSuccess) return err;
-    int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, P::BYTES);
-    if (err != cudaSuccess) return err;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long E = g->mesh.n_elems;
     long long blocks = (E + EPB - 1) / EPB;
-    const long long cap = (long long)per_sm * sm_count * 4;
+    const long long cap = per_sm * sm_count * 4;
     if (blocks > cap) blocks = cap;
     const bool f64 = sizeof(S) == 8;
     const S *jinv = f64 ? (const S *)g->d_jinv64 : (const S *)g->d_jinv32;

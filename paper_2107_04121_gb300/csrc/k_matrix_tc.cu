@@ -541,25 +541,34 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
     using P = TcSmem<MODE>;
     static_assert(P::BYTES <= 227 * 1024, "shared memory plan too large");
     auto kern = k_matrix_tc<MODE>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P::BYTES);
-    if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (err != cudaSuccess) return err;
     // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA),
-    // registers, and the 512 tensor-memory columns of which every CTA holds TC_TMEM_COLS
-    int dev = 0, smem_sm = 0, regs_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    cudaFuncAttributes fa{};
-    err = cudaFuncGetAttributes(&fa, kern);
+    // registers, and the 512 tensor-memory columns of which every CTA holds 2 x TC_TMEM_COLS
+    static FeLaunchCache cache;
+    long long per_sm = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int dev, long long *v) {
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P::BYTES);
+            if (e2 != cudaSuccess) return e2;
+            e2 = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            if (e2 != cudaSuccess) return e2;
+            int smem_sm = 0, regs_sm = 0;
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+            cudaFuncAttributes fa{};
+            e2 = cudaFuncGetAttributes(&fa, kern);
+            if (e2 != cudaSuccess) return e2;
+            int n = smem_sm / (P::BYTES + 1024);
+            const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * TC_THREADS_WS);
+            if (by_regs < n) n = by_regs;
+            if (n * 2 * TC_TMEM_COLS > 512) n = 512 / (2 * TC_TMEM_COLS);
+            if (n < 1) return cudaErrorInvalidConfiguration;
+            *v = n;
+            return cudaSuccess;
+        },
+        &per_sm);
     if (err != cudaSuccess) return err;
-    int per_sm = smem_sm / (P::BYTES + 1024);
-    const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * TC_THREADS_WS);
-    if (by_regs < per_sm) per_sm = by_regs;
-    if (per_sm * 2 * TC_TMEM_COLS > 512) per_sm = 512 / (2 * TC_TMEM_COLS);
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    long long blocks = (long long)per_sm * sm_count;
+    long long blocks = per_sm * sm_count;
     if (blocks > g->mesh.n_elems) blocks = g->mesh.n_elems;
     kern<<<(unsigned)blocks, TC_THREADS_WS, P::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->mesh.n_elems,
                                                         mat.data, (float *)K, status);

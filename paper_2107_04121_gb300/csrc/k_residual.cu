@@ -461,15 +461,23 @@ cudaError_t launch_res_sf(const fe_geometry_h *g, const fe_form_h *f, fe_materia
 {
     constexpr int THREADS = 256;
     auto kern = k_residual_sf<T, N1, NQ, KIND, MATK, EPB, THREADS>;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0);
+    static FeLaunchCache cache;
+    long long cap = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int dev, long long *v) {
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0);
+            if (e2 != cudaSuccess) return e2;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            *v = (long long)per_sm * sms * 4;
+            return cudaSuccess;
+        },
+        &cap);
     if (err != cudaSuccess) return err;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long E = g->mesh.n_elems;
     long long blocks = (E + EPB - 1) / EPB;
-    const long long cap = (long long)per_sm * sms * 4;
     if (blocks > cap) blocks = cap;
     const bool f64 = sizeof(T) == 8;
     kern<<<(unsigned)blocks, THREADS, 0, s>>>(
@@ -519,17 +527,25 @@ cudaError_t launch_res(const fe_geometry_h *g, const fe_form_h *f, fe_material_a
     const size_t smem = sizeof(T) * ((GRAD ? (size_t)Q * 3 * N : (size_t)Q * N) + (size_t)EPB * Q * 9 +
                                      (size_t)EPB * Q + (size_t)EPB * NC * N + (size_t)EPB * Q * NC * 3 + EPB * 36);
     auto kern = k_residual<T, N, Q, KIND, EPB, THREADS>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static FeLaunchCache cache;
+    long long cap = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int dev, long long *v) {
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e2 != cudaSuccess) return e2;
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
+            if (e2 != cudaSuccess) return e2;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            *v = (long long)per_sm * sms * 4;
+            return cudaSuccess;
+        },
+        &cap);
     if (err != cudaSuccess) return err;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, smem);
-    if (err != cudaSuccess) return err;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const long long E = g->mesh.n_elems;
     long long blocks = (E + EPB - 1) / EPB;
-    const long long cap = (long long)per_sm * sms * 4;
     if (blocks > cap) blocks = cap;
     const bool f64 = sizeof(T) == 8;
     kern<<<(unsigned)blocks, THREADS, smem, s>>>(

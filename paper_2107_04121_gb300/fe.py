@@ -25,7 +25,7 @@ F64, F32, TF32X3, BF16X3, BF16 = 0, 1, 2, 3, 4
 PRECISIONS = {"f64": F64, "f32": F32, "tf32x3": TF32X3, "bf16x3": BF16X3, "bf16": BF16}
 VIRTUAL, STATE, PARAMETER, MATERIAL = 0, 1, 2, 3
 MAT_NONE, MAT_SCALAR, MAT_LAME, MAT_D66 = 0, 1, 2, 3
-GEOM_STORE_F64, GEOM_STORE_F32 = 1, 2
+GEOM_STORE_F64, GEOM_STORE_F32, GEOM_DEFERRED = 1, 2, 4
 GEOM_WDETJ, GEOM_JINV, GEOM_G = 0, 1, 2
 ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
 

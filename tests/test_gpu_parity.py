@@ -189,6 +189,55 @@ def test_tensor_core_elasticity_matches_oracle(ctx, prec, tol):
     assert np.abs(Kh - Kh.transpose(0, 2, 1)).max() <= 10 * tol * np.abs(Kh).max()
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16"])
+def test_deferred_geometry_matches_eager(ctx, prec):
+    """A deferred float32-only geometry is computed by the first call that reads it;
+    its stored copy, K_e and the following residual equal the eager path's."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (5, 4, 3), 91)
+    eager = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32)
+    lazy = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    args = [_t(mat, torch.float64), None, _t(u, torch.float32)]
+    for _ in range(2):  # a second update re-marks the handle stale
+        lazy.update()
+        K_l = fe.eval_matrix(ctx, form, lazy, args, prec)
+        r_l = fe.eval_residual(ctx, form, lazy, args, "f32")
+    K_e = fe.eval_matrix(ctx, form, eager, args, prec)
+    r_e = fe.eval_residual(ctx, form, eager, args, "f32")
+    ctx.check()
+    np.testing.assert_array_equal(lazy.get(fe.GEOM_WDETJ, "f32").cpu().numpy(),
+                                  eager.get(fe.GEOM_WDETJ, "f32").cpu().numpy())
+    np.testing.assert_allclose(lazy.get(fe.GEOM_JINV, "f32").cpu().numpy(),
+                               eager.get(fe.GEOM_JINV, "f32").cpu().numpy(), rtol=1e-6, atol=1e-6)
+    assert rel_matrix_error(K_l.cpu().numpy(), K_e.cpu().numpy().astype(np.float64)) <= 1e-6
+    assert rel_vector_error(r_l.cpu().numpy(), r_e.cpu().numpy().astype(np.float64)) <= 1e-6
+    assert rel_vector_error(r_l.cpu().numpy(), rref) <= TOL["f32"]
+
+
+def test_deferred_geometry_settles_for_other_kernels(ctx):
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (3, 3, 2), 92)
+    lazy = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_DEFERRED)  # both copies: no fusion
+    args = [_t(mat, torch.float64), None, None]
+    K = fe.eval_matrix(ctx, form, lazy, args, "f64")
+    ctx.check()
+    assert rel_matrix_error(K.cpu().numpy(), Kref) <= TOL["f64"]
+    lazy32 = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    wd = lazy32.get(fe.GEOM_WDETJ, "f32")  # settles before copying out
+    ctx.check()
+    wref, _, _ = P.oracle_geometry()
+    np.testing.assert_allclose(wd.cpu().numpy(), wref, rtol=1e-6)
+
+
+def test_deferred_geometry_reports_nonpositive_detj(ctx):
+    mesh = meshgen.structured_hex(3, 2, 2, 2, 0.0, 0)
+    mesh.conn[5] = mesh.conn[5].reshape(3, 3, 3)[:, :, ::-1].reshape(-1)  # mirror element 5 in x
+    P = Problem(ctx, mesh, 2, 3)
+    ctx.status()  # the eager geometry of Problem reported it already: clear
+    lazy = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    lm = _t(np.ones((mesh.n_elems, 2)), torch.float64)
+    fe.eval_matrix(ctx, fe.elasticity_form(), lazy, [lm, None, None], "bf16x3")
+    assert ctx.status() == (fe.FE_ERR_NONPOSITIVE_DETJ, 5)
+
+
 def test_tensor_core_paths_reject_other_forms(ctx):
     mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
     P = Problem(ctx, mesh, 2, 3)
