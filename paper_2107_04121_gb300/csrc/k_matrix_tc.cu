@@ -43,6 +43,8 @@ constexpr int TC_NCOL = 96;      // MMA columns
 constexpr int TC_KPAD = 32;      // quadrature points, padded
 constexpr int TC_TMEM_COLS = 128;
 constexpr int TC_NROW = 3 * TC_N;  // 81
+constexpr int TC_JW_STRIDE = 12;  // floats per point of the staged sqrt(w det J) J^-1 (16-byte rows)
+constexpr int TC_EX_STRIDE = 36;  // floats per row of the exchange blocks (16-byte rows)
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;  // about two seconds at 2 GHz
 
 enum TcMode { TC_TF32X3 = 0, TC_BF16X3 = 1, TC_BF16 = 2 };
@@ -155,6 +157,22 @@ __device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo)
     }
 }
 
+// Two values in bf16 (x1 in the upper half, x0 in the lower), with the bf16
+// rounding of the residuals x - hi in lo: hi + lo carries about 16 bits of x.
+__device__ __forceinline__ uint32_t pack_bf16x2(float x1, float x0)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+    return r;
+}
+
+__device__ __forceinline__ void split_bf16x2(float x1, float x0, uint32_t &hi, uint32_t &lo)
+{
+    hi = pack_bf16x2(x1, x0);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+    lo = pack_bf16x2(x1 - h1, x0 - h0);
+}
+
 // One operand tile of phase (b): this lane's node a and points q of its 4-byte
 // segment, for the three gradient rows j.  All shared-memory reads happen
 // before the stores (the buffers do not alias).
@@ -201,9 +219,16 @@ __device__ __forceinline__ void diag_block(const float *own, const float *__rest
                                            const float *__restrict__ d2, float lam, float mu,
                                            float *__restrict__ out)
 {
-    float t[TC_N];
+    static_assert(STRIDE % 4 == 0, "exchange rows must be 16-byte aligned");
+    float t[28];
 #pragma unroll
-    for (int b = 0; b < TC_N; ++b) t[b] = d1[b] + d2[b];
+    for (int c = 0; c < 7; ++c) {
+        const float4 x = reinterpret_cast<const float4 *>(d1)[c], y = reinterpret_cast<const float4 *>(d2)[c];
+        t[4 * c] = x.x + y.x;
+        t[4 * c + 1] = x.y + y.y;
+        t[4 * c + 2] = x.z + y.z;
+        t[4 * c + 3] = x.w + y.w;
+    }
 #pragma unroll
     for (int b = 0; b < TC_N; ++b) out[b] = fmaf(lam + 2.0f * mu, own[b], mu * t[b]);
 }
@@ -225,13 +250,18 @@ __device__ __forceinline__ void offdiag_block(const float *own, const float *__r
     for (int b = 0; b < TC_N; ++b) col[b * TC_NROW] = t[b];
 }
 
+// 28 columns per block (the last is padding) as 16-byte stores
 template <int I>
 __device__ __forceinline__ void publish_blocks(const float *d, float *__restrict__ e0, float *__restrict__ e1)
 {
+    constexpr int J = 32 * I, K1 = 32 * ((I + 1) % 3);
 #pragma unroll
-    for (int b = 0; b < TC_N; ++b) e0[b] = d[32 * I + b];
+    for (int c = 0; c < 7; ++c)
+        reinterpret_cast<float4 *>(e0)[c] = make_float4(d[J + 4 * c], d[J + 4 * c + 1], d[J + 4 * c + 2], d[J + 4 * c + 3]);
 #pragma unroll
-    for (int b = 0; b < TC_N; ++b) e1[b] = d[32 * ((I + 1) % 3) + b];
+    for (int c = 0; c < 7; ++c)
+        reinterpret_cast<float4 *>(e1)[c] =
+            make_float4(d[K1 + 4 * c], d[K1 + 4 * c + 1], d[K1 + 4 * c + 2], d[K1 + 4 * c + 3]);
 }
 
 // Blocks K_ii and K_i,i+1 of row (I, a) and the mirror column of K_i+1,i.
@@ -252,17 +282,17 @@ template <int MODE>
 struct TcSmem {
     static constexpr int EB = MODE == TC_TF32X3 ? 4 : 2;
     using L = OpLayout<EB>;
-    // per buffer: hi and lo operands; the exchange area [3 warps][2 blocks][27][33]
+    // per buffer: hi and lo operands; the exchange area [3 warps][2 blocks][27][36]
     // floats of the epilogue reuses them once the buffer's MMAs have completed
-    static constexpr int EX_STRIDE = 33;
+    static constexpr int EX_STRIDE = TC_EX_STRIDE;
     static constexpr int EX_BYTES = 6 * TC_N * EX_STRIDE * 4;
     static constexpr int BUF = ((2 * L::BYTES > EX_BYTES ? 2 * L::BYTES : EX_BYTES) + 1023) / 1024 * 1024;
     static constexpr int HI = 0;
     static constexpr int LO = L::BYTES;
     static constexpr int KS = 2 * BUF;                                  // K staging: 6561 + 4 floats
     static constexpr int KS_BYTES = (TC_NROW * TC_NROW + 4) * 4;
-    static constexpr int JW = (KS + KS_BYTES + 15) / 16 * 16;          // [2][27][9] sqrt(w det J) J^-1
-    static constexpr int LM = JW + 2 * TC_Q * 9 * 4;                   // [2][2] lambda, mu
+    static constexpr int JW = (KS + KS_BYTES + 15) / 16 * 16;          // [2][27][12] sqrt(w det J) J^-1
+    static constexpr int LM = JW + 2 * TC_Q * TC_JW_STRIDE * 4;        // [2][2] lambda, mu
     static constexpr int DP = LM + 16;                                 // grad_xi phi: 27 x 3 x 27 floats
     static constexpr int MISC = (DP + TC_Q * 3 * TC_N * 4 + 15) / 16 * 16;  // 4 mbarriers, tmem slot, abort
     static constexpr int BYTES = MISC + 48;
@@ -371,7 +401,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
             const int b = n & 1;
             unsigned char *opHi = smem + b * P::BUF + P::HI;
             unsigned char *opLo = smem + b * P::BUF + P::LO;
-            float *jw = sJw + b * TC_Q * 9;
+            float *jw = sJw + b * TC_Q * TC_JW_STRIDE;
             // the buffer and its accumulator are free once element n-2's epilogue is done
             if (n >= 2) {
                 if (ptid == 0 && !mbar_wait_bounded(smem_u32(empty + b), ((n >> 1) - 1) & 1, abort_flag)) {
@@ -386,7 +416,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
 #pragma unroll
             for (int u = 0; u < NPF; ++u) {
                 const int t = ptid + u * TC_PROD;
-                if (t < TC_Q * 9) jw[t] = sqrtf(pwt[u]) * pj[u];
+                if (t < TC_Q * 9) jw[(t / 9) * TC_JW_STRIDE + t % 9] = sqrtf(pwt[u]) * pj[u];
             }
             if (ptid < 2) sLM[2 * b + ptid] = (float)plm;
             prefetch(e + gridDim.x);
@@ -403,29 +433,40 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
                 const int c = pw + 3 * ci;
                 if (c >= NCH) break;
                 const int q0 = c * L::CHUNK + seg * SEGV;
-                float J[SEGV][9];
+                float J[SEGV][12];
 #pragma unroll
                 for (int v = 0; v < SEGV; ++v) {
                     const int q = q0 + v < TC_Q ? q0 + v : 0;
+                    const float4 *jq = reinterpret_cast<const float4 *>(jw + q * TC_JW_STRIDE);
 #pragma unroll
-                    for (int t = 0; t < 9; ++t) J[v][t] = jw[q * 9 + t];
+                    for (int t = 0; t < 3; ++t) {
+                        const float4 x = jq[t];
+                        J[v][4 * t] = x.x;
+                        J[v][4 * t + 1] = x.y;
+                        J[v][4 * t + 2] = x.z;
+                        J[v][4 * t + 3] = x.w;
+                    }
                 }
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     const int a = 8 * g + r;
                     if (a >= TC_N) continue;
-                    uint32_t hv[3] = {0, 0, 0}, lv[3] = {0, 0, 0};
+                    // X values of the lane's points (zero past the last point)
+                    float x[SEGV][3];
 #pragma unroll
                     for (int v = 0; v < SEGV; ++v) {
-                        if (q0 + v >= TC_Q) continue;
                         const float *dd = dreg[ci][g][v];
 #pragma unroll
-                        for (int j = 0; j < 3; ++j) {
-                            uint32_t h, l;
-                            split<MODE>(dd[0] * J[v][j] + dd[1] * J[v][3 + j] + dd[2] * J[v][6 + j], h, l);
-                            hv[j] |= h << (16 * v);
-                            lv[j] |= l << (16 * v);
-                        }
+                        for (int j = 0; j < 3; ++j)
+                            x[v][j] = q0 + v < TC_Q ? dd[0] * J[v][j] + dd[1] * J[v][3 + j] + dd[2] * J[v][6 + j]
+                                                    : 0.0f;
+                    }
+                    uint32_t hv[3], lv[3];
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        if constexpr (MODE == TC_TF32X3) split<MODE>(x[0][j], hv[j], lv[j]);
+                        else if constexpr (MODE == TC_BF16X3) split_bf16x2(x[1][j], x[0][j], hv[j], lv[j]);
+                        else hv[j] = pack_bf16x2(x[1][j], x[0][j]);
                     }
 #pragma unroll
                     for (int j = 0; j < 3; ++j) {
