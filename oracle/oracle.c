@@ -475,6 +475,95 @@ int oracle_residual_elasticity(long long n_elems, int N, int Q, const int32_t *c
 }
 
 /* ------------------------------------------------------------------------ */
+/* Navier-Stokes convective term 'i,i.j,j' (Eq. fe2, Tab. ewfd):
+ *   c(v, u, w) = int v_i (du_i/dx_j) w_j,
+ * with a gradient operand u and an advection operand w, both vector fields
+ * gathered through conn (u[3*node + i]); for the non-linear term w = u.
+ * At a point: u_h,i = sum_b phi_b u_(i,b), (grad u_h)_ij = sum_b u_(i,b) G[j][b]. */
+static void convect_point(int N, const double *phi_q, const double *Gq, const double *ue, const double *we,
+                          double gu[3][3], double wh[3])
+{
+    for (int i = 0; i < 3; ++i) {
+        wh[i] = 0.0;
+        for (int b = 0; b < N; ++b) wh[i] += phi_q[b] * we[i * N + b];
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int b = 0; b < N; ++b) s += ue[i * N + b] * Gq[j * N + b];
+            gu[i][j] = s;
+        }
+    }
+}
+
+static void gather_vec(int N, const int32_t *conn_e, const double *u, double *ue)
+{
+    for (int i = 0; i < 3; ++i)
+        for (int b = 0; b < N; ++b) ue[i * N + b] = u[3 * (size_t)conn_e[b] + i];
+}
+
+/* Residual mode: r[e][(i,a)] = sum_q wdetJ phi_a sum_j (grad u_h)_ij w_h,j. */
+int oracle_residual_convect(long long n_elems, int N, int Q, const int32_t *conn, const double *wdetJ,
+                            const double *phi, const double *G, const double *u, const double *w, double *r)
+{
+    if (n_elems < 0 || N < 1 || N > 512 || !conn || !wdetJ || !phi || !G || !u || !w || !r) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double ue[3 * 512], we[3 * 512];
+        gather_vec(N, conn + (size_t)e * N, u, ue);
+        gather_vec(N, conn + (size_t)e * N, w, we);
+        double *re = r + (size_t)e * 3 * N;
+        for (int c = 0; c < 3 * N; ++c) re[c] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            double gu[3][3], wh[3];
+            convect_point(N, phi + (size_t)q * N, G + ((size_t)e * Q + q) * 3 * N, ue, we, gu, wh);
+            const double wd = wdetJ[(size_t)e * Q + q];
+            for (int i = 0; i < 3; ++i) {
+                const double s = gu[i][0] * wh[0] + gu[i][1] * wh[1] + gu[i][2] * wh[2];
+                for (int a = 0; a < N; ++a) re[i * N + a] += wd * phi[(size_t)q * N + a] * s;
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/* Matrix mode, the two terms of Eq. fe4: the derivative with respect to the
+ * gradient operand (wrt_u) and to the advection operand (wrt_w),
+ *   K[e][(i,a),(k,b)] = sum_q wdetJ phi_a [ wrt_u delta_ik (w_h . grad phi_b)
+ *                                          + wrt_w (du_h,i/dx_k) phi_b ];
+ * with w = u and both flags set this is the Jacobian of the non-linear term. */
+int oracle_matrix_convect(long long n_elems, int N, int Q, const int32_t *conn, const double *wdetJ,
+                          const double *phi, const double *G, const double *u, const double *w, int wrt_u, int wrt_w,
+                          double *K)
+{
+    if (n_elems < 0 || N < 1 || N > 512 || !conn || !wdetJ || !phi || !G || !u || !w || !K) return OR_BAD_ARG;
+    const int n = 3 * N;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double ue[3 * 512], we[3 * 512];
+        gather_vec(N, conn + (size_t)e * N, u, ue);
+        gather_vec(N, conn + (size_t)e * N, w, we);
+        double *Ke = K + (size_t)e * n * n;
+        for (long long c = 0; c < (long long)n * n; ++c) Ke[c] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            const double *Gq = G + ((size_t)e * Q + q) * 3 * N;
+            const double *ph = phi + (size_t)q * N;
+            double gu[3][3], wh[3];
+            convect_point(N, ph, Gq, ue, we, gu, wh);
+            const double wd = wdetJ[(size_t)e * Q + q];
+            for (int i = 0; i < 3; ++i)
+                for (int a = 0; a < N; ++a)
+                    for (int k = 0; k < 3; ++k)
+                        for (int b = 0; b < N; ++b) {
+                            double v = 0.0;
+                            if (wrt_u && i == k) v += wh[0] * Gq[b] + wh[1] * Gq[N + b] + wh[2] * Gq[2 * N + b];
+                            if (wrt_w) v += gu[i][k] * ph[b];
+                            Ke[(size_t)(i * N + a) * n + k * N + b] += wd * ph[a] * v;
+                        }
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Assembly of element vectors into a global vector (outside the timed region
  * of the paper, Sec. 6): g[ncomp*conn[e][a] + i] += r[e][i*N + a], summed
  * sequentially in ascending (e, a, i) order.  accumulate = 0 zeroes g first. */

@@ -51,6 +51,10 @@ def lib():
                                            _D, _D, _D]
         L.oracle_residual_elasticity.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D,
                                                  _D]
+        L.oracle_residual_convect.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D, _D,
+                                              _D]
+        L.oracle_matrix_convect.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D, _D,
+                                            ctypes.c_int, ctypes.c_int, _D]
         L.oracle_assemble.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, ctypes.c_longlong,
                                       ctypes.c_int, _D]
         L.oracle_num_threads.restype = ctypes.c_int
@@ -192,6 +196,31 @@ def residual_elasticity(conn, wdetJ, G, D, u):
     r = np.zeros((E, 3 * N))
     _check(lib().oracle_residual_elasticity(E, N, Q, _i(conn), _d(wdetJ), _d(G), _d(_f64(D)), _d(_f64(u)), _d(r)))
     return r
+
+
+def residual_convect(conn, wdetJ, phi, G, u, w=None):
+    """Convective term 'i,i.j,j' (Eq. fe2): r[e, i*N+a] = sum_q wdetJ phi_a (grad u_h)_ij w_h,j;
+    w defaults to u (the non-linear term)."""
+    E, Q, _, N = G.shape
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    u = _f64(u)
+    w = u if w is None else _f64(w)
+    r = np.zeros((E, 3 * N))
+    _check(lib().oracle_residual_convect(E, N, Q, _i(conn), _d(wdetJ), _d(_f64(phi)), _d(G), _d(u), _d(w), _d(r)))
+    return r
+
+
+def matrix_convect(conn, wdetJ, phi, G, u, w=None, wrt_u=True, wrt_w=True):
+    """Derivative of the convective term (Eq. fe4) with respect to the gradient
+    operand u (wrt_u) and/or the advection operand w (wrt_w); w defaults to u."""
+    E, Q, _, N = G.shape
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    u = _f64(u)
+    w = u if w is None else _f64(w)
+    K = np.zeros((E, 3 * N, 3 * N))
+    _check(lib().oracle_matrix_convect(E, N, Q, _i(conn), _d(wdetJ), _d(_f64(phi)), _d(G), _d(u), _d(w),
+                                       int(bool(wrt_u)), int(bool(wrt_w)), _d(K)))
+    return K
 
 
 def assemble(conn, r, n_nodes, ncomp, g=None):

@@ -104,3 +104,45 @@ def box_elasticity(p, h, lam, mu):
                         blk += C * P[j][l]
             K[i * N:(i + 1) * N, kk * N:(kk + 1) * N] = blk
     return K
+
+
+def moments_1d(p):
+    """Exact 1-D integrals over [0, 1] with the test function L_a first:
+    m_ab = int L_a L_b, d_ab = int L_a L_b', xm_ab = int t L_a L_b, xd_ab = int t L_a L_b'."""
+    L = lagrange_polys(p)
+    dL = [_pder(x) for x in L]
+    t = [Fraction(0), Fraction(1)]
+    n = p + 1
+    m = [[_pint01(_pmul(L[a], L[b])) for b in range(n)] for a in range(n)]
+    d = [[_pint01(_pmul(L[a], dL[b])) for b in range(n)] for a in range(n)]
+    xm = [[_pint01(_pmul(t, _pmul(L[a], L[b]))) for b in range(n)] for a in range(n)]
+    xd = [[_pint01(_pmul(t, _pmul(L[a], dL[b]))) for b in range(n)] for a in range(n)]
+    f = lambda M: np.array([[float(x) for x in row] for row in M])
+    return f(m), f(d), f(xm), f(xd)
+
+
+def box_convection(p, h, x0, A, c):
+    """C_ab = int_box phi_a (w . grad phi_b) for the linear field w(x) = A x + c on
+    the box x0 + [0,h0]x[0,h1]x[0,h2], from separable 1-D integrals: on axis e the
+    factor is m h_e, or d on the differentiated axis (the 1/h and h cancel), and
+    x_d = x0_d + h_d t contributes x0_d (factor) + h_d (the t-moment factor)."""
+    m, d, xm, xd = moments_1d(p)
+    h = np.asarray(h, dtype=float)
+    x0 = np.asarray(x0, dtype=float)
+
+    def factors(j):
+        return [d if e == j else m * h[e] for e in range(3)]
+
+    N = (p + 1) ** 3
+    C = np.zeros((N, N))
+    for j in range(3):
+        base = factors(j)
+        Ij = _kron3(*base)
+        C += (c[j] + sum(A[j, dd] * x0[dd] for dd in range(3))) * Ij
+        for dd in range(3):
+            if A[j, dd] == 0.0:
+                continue
+            fac = list(base)
+            fac[dd] = xd if dd == j else xm * h[dd]
+            C += A[j, dd] * h[dd] * _kron3(*fac)
+    return C

@@ -325,3 +325,123 @@ def test_printed_einsum_shapes():
     D = oracle.lame_to_D(np.ones(4), np.ones(4))
     assert D.shape[1:] == (6, 6)
     assert oracle.matrix_elasticity(w1, G1, D).reshape(4, 3, 8, 3, 8).shape[1:] == (3, 8, 3, 8)  # cresf
+
+
+# -- Navier-Stokes convective term 'i,i.j,j' (Eq. fe2, fe4) ------------------------
+
+def _box_linear_field(p, seed):
+    rng = np.random.default_rng(seed)
+    h = (0.5, 0.7, 1.3)
+    x0 = np.array([0.25, -1.0, 3.0])
+    mesh = meshgen.structured_hex(1, 1, 1, p, 0.0, 0, lengths=h)
+    mesh.coords[:] += x0
+    A = rng.standard_normal((3, 3))
+    c = rng.standard_normal(3)
+    u = (mesh.coords @ A.T + c).reshape(-1)  # u[3 node + i] = (A x + c)_i
+    return mesh, h, x0, A, c, u
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_convect_box_linear_field_closed_form(p):
+    """On a box with the linear field u = A x + c (w = u): the residual is
+    int phi_a (A (A x + c))_i = M (nodal values of A(Ax + c)), the derivative with
+    respect to the advection operand is A_ik M, and with respect to the gradient
+    operand delta_ik int phi_a (u . grad phi_b), all from exact 1-D integrals."""
+    mesh, h, x0, A, c, u = _box_linear_field(p, 21 + p)
+    ref = oracle.RefElement(p, p + 1)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    N = ref.N
+    M = exact_fe.box_mass(p, h)
+    nodal = mesh.coords[mesh.conn[0]] @ A.T + c        # (N, 3): u at the element's nodes
+    accel = nodal @ A.T                                # (A u)(x_node) = A (A x + c)
+    r_want = np.concatenate([M @ accel[:, i] for i in range(3)])
+    r = oracle.residual_convect(mesh.conn, wdetJ, ref.phi, G, u)[0]
+    assert np.abs(r - r_want).max() <= 1e-13 * np.abs(r_want).max()
+    Kw = oracle.matrix_convect(mesh.conn, wdetJ, ref.phi, G, u, wrt_u=False, wrt_w=True)[0]
+    Ku = oracle.matrix_convect(mesh.conn, wdetJ, ref.phi, G, u, wrt_u=True, wrt_w=False)[0]
+    Kw_want = np.kron(A, M)
+    Cb = exact_fe.box_convection(p, h, x0, A, c)
+    Ku_want = np.kron(np.eye(3), Cb)
+    assert np.abs(Kw - Kw_want).max() <= 1e-13 * np.abs(Kw_want).max()
+    assert np.abs(Ku - Ku_want).max() <= 1e-13 * np.abs(Ku_want).max()
+
+
+@pytest.fixture(scope="module", params=[1, 2])
+def convect_case(request):
+    p = request.param
+    mesh = meshgen.structured_hex(2, 2, 2, p, 0.15, 31)
+    rng = np.random.default_rng(32)
+    u = rng.standard_normal(3 * mesh.n_nodes)
+    w = rng.standard_normal(3 * mesh.n_nodes)
+    ref = oracle.RefElement(p, p + 1)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    return mesh, ref, wdetJ, G, u, w
+
+
+def _element_dofs(conn, v):
+    """v_e[e, i*N + a] = v[3 conn[e, a] + i]."""
+    return np.concatenate([v[3 * conn + i] for i in range(3)], axis=1)
+
+
+def test_convect_jacobian_is_exact_central_difference(convect_case):
+    """r(u) is quadratic in u, so a central difference of any step is exact up to
+    rounding: (r(u + s d) - r(u - s d)) / 2s = K(u) d_e."""
+    mesh, ref, wdetJ, G, u, w = convect_case
+    d = np.random.default_rng(33).standard_normal(u.shape)
+    s = 0.5
+    rp = oracle.residual_convect(mesh.conn, wdetJ, ref.phi, G, u + s * d)
+    rm = oracle.residual_convect(mesh.conn, wdetJ, ref.phi, G, u - s * d)
+    K = oracle.matrix_convect(mesh.conn, wdetJ, ref.phi, G, u)
+    got = np.einsum("erc,ec->er", K, _element_dofs(mesh.conn, d))
+    fd = (rp - rm) / (2 * s)
+    assert np.abs(got - fd).max() <= 1e-12 * np.abs(fd).max()
+
+
+def test_convect_degree_two_homogeneity(convect_case):
+    """Euler's relation for a form quadratic in u: K(u) u_e = 2 r(u)."""
+    mesh, ref, wdetJ, G, u, w = convect_case
+    K = oracle.matrix_convect(mesh.conn, wdetJ, ref.phi, G, u)
+    r = oracle.residual_convect(mesh.conn, wdetJ, ref.phi, G, u)
+    got = np.einsum("erc,ec->er", K, _element_dofs(mesh.conn, u))
+    assert np.abs(got - 2 * r).max() <= 1e-12 * np.abs(r).max()
+
+
+def test_convect_partial_derivatives_are_the_linear_actions(convect_case):
+    """With distinct operands the form is linear in each: the derivative with
+    respect to the gradient operand applied to u_e, and the one with respect to
+    the advection operand applied to w_e, both give r(u, w); the two terms add
+    up to the full derivative."""
+    mesh, ref, wdetJ, G, u, w = convect_case
+    r = oracle.residual_convect(mesh.conn, wdetJ, ref.phi, G, u, w)
+    Ku = oracle.matrix_convect(mesh.conn, wdetJ, ref.phi, G, u, w, wrt_u=True, wrt_w=False)
+    Kw = oracle.matrix_convect(mesh.conn, wdetJ, ref.phi, G, u, w, wrt_u=False, wrt_w=True)
+    Kb = oracle.matrix_convect(mesh.conn, wdetJ, ref.phi, G, u, w)
+    sc = np.abs(r).max()
+    assert np.abs(np.einsum("erc,ec->er", Ku, _element_dofs(mesh.conn, u)) - r).max() <= 1e-12 * sc
+    assert np.abs(np.einsum("erc,ec->er", Kw, _element_dofs(mesh.conn, w)) - r).max() <= 1e-12 * sc
+    assert np.abs(Ku + Kw - Kb).max() <= 1e-13 * np.abs(Kb).max()
+
+
+def test_convect_rows_of_advection_block_sum_to_zero(convect_case):
+    """sum_b grad phi_b = 0 (partition of unity): every row of the derivative with
+    respect to the gradient operand sums to zero within its diagonal block, and
+    its off-diagonal blocks vanish."""
+    mesh, ref, wdetJ, G, u, w = convect_case
+    N = ref.N
+    Ku = oracle.matrix_convect(mesh.conn, wdetJ, ref.phi, G, u, w, wrt_u=True, wrt_w=False)
+    sc = np.abs(Ku).max()
+    for i in range(3):
+        for k in range(3):
+            blk = Ku[:, i * N:(i + 1) * N, k * N:(k + 1) * N]
+            if i == k:
+                assert np.abs(blk.sum(2)).max() <= 1e-13 * sc
+            else:
+                assert np.abs(blk).max() == 0.0
+
+
+def test_convect_constant_advection_of_constant_field_vanishes(convect_case):
+    """A constant field has no gradient: r(u = const) = 0 on distorted elements."""
+    mesh, ref, wdetJ, G, u, w = convect_case
+    uc = np.tile(np.array([0.3, -1.2, 2.0]), mesh.n_nodes)
+    r = oracle.residual_convect(mesh.conn, wdetJ, ref.phi, G, uc, w)
+    assert np.abs(r).max() <= 1e-13
