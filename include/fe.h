@@ -223,6 +223,12 @@ fe_status fe_geometry_get(fe_ctx *ctx, const fe_geometry_h *geom, fe_geom_field 
  *   dot product / mass    "i,i" (ncomp 1 or 3), "0,0"  (VIRTUAL, STATE)
  *   weighted mass         "0,i,i", "0,0,0"             (MATERIAL SCALAR, VIRTUAL, STATE)
  *   linear elasticity     "IK,s(i:j)->I,s(k:l)->K"     (MATERIAL LAME or D66, VIRTUAL, STATE), ncomp 3
+ *   Navier-Stokes         "i,i.j,j"                    (VIRTUAL, u, w), ncomp 3: int v_i (du_i/dx_j) w_j
+ *   convection (Eq. fe2)  u and w each STATE or PARAMETER (at least one STATE);
+ *                         (VIRTUAL, STATE, STATE) is the non-linear term with
+ *                         w = u, whose matrix is the two-term derivative of
+ *                         Eq. fe4; tensor-product hexahedra only (the basis
+ *                         must carry its 1-D factors)
  * `ctx` may be NULL: compilation is host-only.  The handle caches the plan
  * (Sec. 5.1: transpilation results are cached).  Errors: FE_ERR_INVALID_ARG
  * (syntax, roles, sizes), FE_ERR_UNSUPPORTED_SPEC (a valid expression with no
@@ -237,12 +243,15 @@ fe_status fe_form_shape(const fe_form_h *form, int n_basis, int *n_rows, int *n_
 /* args[k] is the device array of operand k of the compiled expression:
  *   FE_VIRTUAL            NULL (the test function is what the rows enumerate)
  *   FE_STATE, FE_PARAMETER global DOF vector (n_nodes * ncomp), float64 for
- *                         FE_F64 else float32; not read in matrix mode
+ *                         FE_F64 else float32; in matrix mode read only by
+ *                         forms that are not linear in the state (convection)
  *   FE_MATERIAL           float64 array in the operand's fe_material_kind layout
  */
 
 /* Matrix mode (Algorithm 2): K_out[e][r][c] = derivative of the form with
- * respect to the DOFs of operand `diff_op` (which must be the FE_STATE operand),
+ * respect to the DOFs of operand `diff_op` (which must be an FE_STATE operand;
+ * where several operands are FE_STATE they are one unknown and the derivative
+ * sums over them, as Eq. fe4 does for the convective term),
  * integrated with the quadrature of `geom`; K_out is a device array
  * (n_elems, n_rows, n_cols), float64 for FE_F64 else float32.
  * FE_F64 and FE_F32 cover every form and element; the tensor-core precisions
@@ -255,7 +264,7 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
                          int diff_op, fe_precision prec, void *K_out, fe_stream_t stream);
 
 /* Residual mode (Algorithm 1): r_out[e][r] = the form's action on the DOF
- * vector of the FE_STATE operand, whose element values are gathered through
+ * vectors of its FE_STATE and FE_PARAMETER operands, whose element values are gathered through
  * the mesh connectivity; r_out is a device array (n_elems, n_rows), float64
  * for FE_F64 else float32.  FE_TF32X3/FE_BF16X3/FE_BF16 evaluate residuals
  * with the FE_F32 kernels.  Errors as fe_eval_matrix. */

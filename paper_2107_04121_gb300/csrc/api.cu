@@ -312,10 +312,24 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
     fe_material_args mat{};
     fe_status st = eval_common(ctx, form, g, args, prec, K_out, &mat);
     if (st) return st;
-    if (diff_op != form->state_op) return FE_ERR_INVALID_ARG;
     cudaError_t e;
     fe_geometry_h *gm = const_cast<fe_geometry_h *>(g);
     cudaStream_t s = to_cuda(stream);
+    if (form->kind == FK_CONVECT) {
+        // derivative with respect to the unknown: every FE_STATE operand (Eq. fe4)
+        const bool ok_diff = (diff_op == form->grad_op && form->wrt_grad) || (diff_op == form->adv_op && form->wrt_adv);
+        if (!ok_diff) return FE_ERR_INVALID_ARG;
+        if (prec != FE_F64 && prec != FE_F32) return FE_ERR_UNSUPPORTED_SPEC;
+        if (!fe_convect_supported(g)) return FE_ERR_UNSUPPORTED_SPEC;
+        const bool empty = g->mesh.n_elems == 0;
+        if (!args || (!empty && (!args[form->grad_op] || !args[form->adv_op]))) return FE_ERR_INVALID_ARG;
+        e = settle_geometry(gm, ctx->d_status, s);
+        if (e == cudaSuccess)
+            e = fe_launch_convect(g, prec == FE_F64, args[form->grad_op], args[form->adv_op], form->wrt_grad,
+                                  form->wrt_adv, K_out, nullptr, ctx->d_status, s);
+        return from_cuda(e, "fe_eval_matrix");
+    }
+    if (diff_op != form->state_op) return FE_ERR_INVALID_ARG;
     if (prec == FE_F64 || prec == FE_F32) {
         e = settle_geometry(gm, ctx->d_status, s);
         if (e == cudaSuccess) e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, s);
@@ -335,6 +349,17 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
     fe_material_args mat{};
     fe_status st = eval_common(ctx, form, g, args, prec, r_out, &mat);
     if (st) return st;
+    if (form->kind == FK_CONVECT) {
+        if (!fe_convect_supported(g)) return FE_ERR_UNSUPPORTED_SPEC;
+        const bool empty = g->mesh.n_elems == 0;
+        if (!args || (!empty && (!args[form->grad_op] || !args[form->adv_op]))) return FE_ERR_INVALID_ARG;
+        cudaStream_t s = to_cuda(stream);
+        cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, s);
+        if (e == cudaSuccess)
+            e = fe_launch_convect(g, prec == FE_F64, args[form->grad_op], args[form->adv_op], 0, 0, nullptr, r_out,
+                                  ctx->d_status, s);
+        return from_cuda(e, "fe_eval_residual");
+    }
     if (!args || (!args[form->state_op] && g->mesh.n_elems > 0)) return FE_ERR_INVALID_ARG;
     cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, to_cuda(stream));
     if (e == cudaSuccess) e = fe_launch_residual(g, form, mat, prec == FE_F64, args[form->state_op], r_out, ctx->d_status,

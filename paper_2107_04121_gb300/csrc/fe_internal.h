@@ -33,7 +33,7 @@ struct fe_geometry_h {
     int pending;  // deferred handle: the stored geometry is stale (host-side, stream-ordered use)
 };
 
-enum fe_form_kind { FK_LAPLACE = 0, FK_MASS = 1, FK_ELASTICITY = 2 };
+enum fe_form_kind { FK_LAPLACE = 0, FK_MASS = 1, FK_ELASTICITY = 2, FK_CONVECT = 3 };
 
 struct fe_form_h {
     fe_form_kind kind;
@@ -44,6 +44,11 @@ struct fe_form_h {
     int mat_op;      // operand index of the material, -1 if none
     fe_material_kind mat;
     int mat_transposed;  // elasticity: material indices given as (u-index, v-index)
+    // convective term 'i,i.j,j': operand of the gradient (u) and of the advection
+    // velocity (w); the matrix is the derivative with respect to every FE_STATE
+    // operand among them (both for the non-linear term, Eq. fe4)
+    int grad_op, adv_op;
+    int wrt_grad, wrt_adv;
 };
 
 struct fe_assembly_h {
@@ -68,6 +73,12 @@ cudaError_t fe_launch_matrix(const fe_geometry_h *g, const fe_form_h *f, fe_mate
                              void *K, int sm_count, cudaStream_t s);
 cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
                                const void *u, void *r, unsigned long long *status, cudaStream_t s);
+// Convective term on tensor-product hexahedra (sum factorisation): residual
+// (K == nullptr) or matrix (r == nullptr) of 'i,i.j,j' with gradient operand u
+// and advection operand w (global DOF vectors, 3 per node).
+cudaError_t fe_launch_convect(const fe_geometry_h *g, bool f64, const void *u, const void *w, int wrt_grad,
+                              int wrt_adv, void *K, void *r, unsigned long long *status, cudaStream_t s);
+bool fe_convect_supported(const fe_geometry_h *g);
 cudaError_t fe_launch_assembly_build(fe_assembly_h *a, int *d_flag, cudaStream_t s);
 cudaError_t fe_launch_assemble(const fe_assembly_h *a, int ncomp, bool f64, const void *r, void *out,
                                unsigned flags, cudaStream_t s);

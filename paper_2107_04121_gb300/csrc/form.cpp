@@ -105,7 +105,8 @@ extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_ope
     if ((int)parts.size() != n_ops) return FE_ERR_INVALID_ARG;
 
     std::vector<Sub> subs(n_ops);
-    int iv = -1, is = -1, im = -1;
+    int iv = -1, im = -1;
+    std::vector<int> states, params;
     for (int k = 0; k < n_ops; ++k) {
         const fe_operand &op = ops[k];
         if (op.role == FE_MATERIAL) {
@@ -125,16 +126,52 @@ extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_ope
                 if (iv >= 0) return FE_ERR_UNSUPPORTED_SPEC;
                 iv = k;
             } else if (op.role == FE_STATE) {
-                if (is >= 0) return FE_ERR_UNSUPPORTED_SPEC;
-                is = k;
+                states.push_back(k);
             } else {
-                return FE_ERR_UNSUPPORTED_SPEC;  // known fields: no kernel yet
+                params.push_back(k);
             }
         } else {
             return FE_ERR_INVALID_ARG;
         }
     }
-    if (iv < 0 || is < 0) return FE_ERR_UNSUPPORTED_SPEC;  // 'eval' mode / missing unknown
+    if (iv < 0 || states.empty()) return FE_ERR_UNSUPPORTED_SPEC;  // 'eval' mode / missing unknown
+
+    // Navier-Stokes convection v_i (du_i/dx_j) w_j: a vector test function, one
+    // gradient operand with the same component letter and one advection operand
+    // carrying the derivative letter; u and w are each FE_STATE or FE_PARAMETER
+    if (im < 0 && n_ops == 3 && states.size() + params.size() == 2 && subs[iv].kind == SK_VEC && ops[iv].ncomp == 3) {
+        int og = -1, oa = -1;
+        for (int k = 0; k < n_ops; ++k) {
+            if (k == iv) continue;
+            if (subs[k].kind == SK_VEC_GRAD) og = k;
+            else if (subs[k].kind == SK_VEC) oa = k;
+        }
+        if (og >= 0 && oa >= 0 && ops[og].ncomp == 3 && ops[oa].ncomp == 3) {
+            const Sub &V = subs[iv], &Gs = subs[og], &A = subs[oa];
+            if (Gs.a == V.a && A.a == Gs.b && Gs.a != Gs.b) {
+                fe_form_h f{};
+                f.kind = FK_CONVECT;
+                f.n_ops = n_ops;
+                f.virtual_op = iv;
+                f.state_op = states[0];
+                f.mat_op = -1;
+                f.mat = FE_MAT_NONE;
+                f.ncomp = 3;
+                f.grad_op = og;
+                f.adv_op = oa;
+                f.wrt_grad = ops[og].role == FE_STATE;
+                f.wrt_adv = ops[oa].role == FE_STATE;
+                fe_form_h *h = new (std::nothrow) fe_form_h(f);
+                if (!h) return FE_ERR_OOM;
+                *out = h;
+                return FE_OK;
+            }
+        }
+        return FE_ERR_UNSUPPORTED_SPEC;
+    }
+    // the linear forms: one unknown, no known fields
+    if (states.size() != 1 || !params.empty()) return FE_ERR_UNSUPPORTED_SPEC;
+    const int is = states[0];
 
     const Sub &V = subs[iv], &S = subs[is];
     const int nc = ops[iv].ncomp;
@@ -148,6 +185,7 @@ extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_ope
     f.mat = im >= 0 ? ops[im].material : FE_MAT_NONE;
     f.ncomp = nc;
     f.mat_transposed = 0;
+    f.grad_op = f.adv_op = -1;
     bool ok = false;
     const bool scalar_mat = im < 0 || (subs[im].letters.empty() && ops[im].material == FE_MAT_SCALAR);
 

@@ -314,8 +314,9 @@ def form_compile(expr: str, operands, ctx: Context | None = None) -> Form:
 _MAT_SIZE = {MAT_SCALAR: 1, MAT_LAME: 2, MAT_D66: 36}
 
 
-def _args(form: Form, args, geom: Geometry):
-    """Device pointers of the operands; checks materials (float64, one row per element)."""
+def _args(form: Form, args, geom: Geometry, dtype=None):
+    """Device pointers of the operands; checks materials (float64, one row per
+    element) and, given their dtype, the DOF vectors of field operands."""
     import torch
     if len(args) != len(form.operands):
         raise ValueError("expected %d operands, got %d" % (len(form.operands), len(args)))
@@ -325,6 +326,10 @@ def _args(form: Form, args, geom: Geometry):
             _dev(a, torch.float64, "material operand %d" % k)
             if a.numel() != geom.mesh.n_elems * _MAT_SIZE[mk]:
                 raise ValueError("material operand %d must have %d values per element" % (k, _MAT_SIZE[mk]))
+        elif role in (STATE, PARAMETER) and a is not None and dtype is not None:
+            _dev(a, dtype, "DOF vector of operand %d" % k)
+            if a.numel() != geom.mesh.n_nodes * ncomp:
+                raise ValueError("DOF vector of operand %d must have n_nodes * %d entries" % (k, ncomp))
         ptrs[k] = None if a is None else a.data_ptr()
     return ptrs
 
@@ -346,7 +351,8 @@ def eval_matrix(ctx: Context, form: Form, geom: Geometry, args, precision="f64",
     if tuple(out.shape) != (E, nr, nc):
         raise ValueError("K_out must have shape %s" % ((E, nr, nc),))
     d = form.state_op if diff_op is None else diff_op
-    _check(_lib.fe_eval_matrix(ctx.handle, form._h, geom._h, _args(form, args, geom), d, _prec(precision),
+    _check(_lib.fe_eval_matrix(ctx.handle, form._h, geom._h, _args(form, args, geom, _out_dtype(precision)), d,
+                               _prec(precision),
                                ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "fe_eval_matrix")
     return out
 
@@ -361,11 +367,11 @@ def eval_residual(ctx: Context, form: Form, geom: Geometry, args, precision="f64
     _dev(out, _out_dtype(precision), "r_out")
     if tuple(out.shape) != (E, nr):
         raise ValueError("r_out must have shape %s" % ((E, nr),))
-    u = args[form.state_op]
-    _dev(u, _out_dtype(precision), "state DOF vector")
-    if u.numel() != geom.mesh.n_nodes * form.operands[form.state_op][1]:
-        raise ValueError("state DOF vector must have n_nodes * ncomp entries")
-    _check(_lib.fe_eval_residual(ctx.handle, form._h, geom._h, _args(form, args, geom), _prec(precision),
+    for k, (role, _, _) in enumerate(form.operands):
+        if role in (STATE, PARAMETER) and args[k] is None:
+            raise ValueError("operand %d needs its DOF vector in residual mode" % k)
+    _check(_lib.fe_eval_residual(ctx.handle, form._h, geom._h, _args(form, args, geom, _out_dtype(precision)),
+                                 _prec(precision),
                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "fe_eval_residual")
     return out
 
@@ -443,6 +449,13 @@ def mass_form(ncomp: int = 1, weighted: bool = False) -> Form:
     if weighted:
         return form_compile("0,i,i", [(MATERIAL, 1, MAT_SCALAR)] + ops)
     return form_compile("i,i", ops)
+
+
+def convect_form(advection: int = STATE, gradient: int = STATE) -> Form:
+    """Navier-Stokes convection 'i,i.j,j' with operands (v, u, w): the gradient
+    operand u and the advection operand w are each STATE or PARAMETER; both
+    STATE (the default) is the non-linear term, whose matrix is Eq. fe4."""
+    return form_compile("i,i.j,j", [(VIRTUAL, 3, MAT_NONE), (gradient, 3, MAT_NONE), (advection, 3, MAT_NONE)])
 
 
 def elasticity_form(material: int = MAT_LAME) -> Form:

@@ -114,3 +114,20 @@ def elasticity_q2_cube(n: int = 48, seed: int = 1, perturb: float = 0.15):
     lam, mu = lame_materials(mesh)
     u = normal_dofs(mesh, 3)
     return mesh, lam, mu, u
+
+
+def smooth_vector_field(mesh: HexMesh) -> np.ndarray:
+    """u_i(node) = a_i sin(pi x) cos(pi y) with amplitudes a ~ N(0, 1) in R^3 drawn
+    from the mesh's generator; global index 3 * node + i."""
+    a = mesh.rng.standard_normal(3)
+    x, y = mesh.coords[:, 0], mesh.coords[:, 1]
+    s = np.sin(np.pi * x) * np.cos(np.pi * y)
+    return (s[:, None] * a[None, :]).reshape(-1)
+
+
+def convect_q2_cube(n: int = 64, seed: int = 3, perturb: float = 0.1):
+    """Q2 Navier-Stokes convection on an n^3 cube, interior nodes +-0.1h,
+    with the smooth velocity field of smooth_vector_field."""
+    mesh = structured_hex(n, n, n, 2, perturb, seed)
+    u = smooth_vector_field(mesh)
+    return mesh, u

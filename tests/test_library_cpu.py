@@ -70,7 +70,7 @@ def test_refbasis_rejects_unsupported(libfe):
     assert libfe.fe_refbasis_hex(2, 11, None, None, None, None) == fe.FE_ERR_SHAPE
 
 
-V, S, M = fe.VIRTUAL, fe.STATE, fe.MATERIAL
+V, S, M, PA = fe.VIRTUAL, fe.STATE, fe.MATERIAL, fe.PARAMETER
 NONE, SC, LAME, D66 = fe.MAT_NONE, fe.MAT_SCALAR, fe.MAT_LAME, fe.MAT_D66
 
 
@@ -87,6 +87,10 @@ NONE, SC, LAME, D66 = fe.MAT_NONE, fe.MAT_SCALAR, fe.MAT_LAME, fe.MAT_D66
     ("AB,s(p:q)->A,s(r:t)->B", [(M, 1, D66), (V, 3, NONE), (S, 3, NONE)], 24),
     ("KI,s(i:j)->I,s(k:l)->K", [(M, 1, D66), (V, 3, NONE), (S, 3, NONE)], 24),
     ("s(k:l)->K,IK,s(i:j)->I", [(S, 3, NONE), (M, 1, LAME), (V, 3, NONE)], 24),
+    ("i,i.j,j", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], 24),
+    ("i,i.j,j", [(V, 3, NONE), (S, 3, NONE), (PA, 3, NONE)], 24),
+    ("i,i.j,j", [(V, 3, NONE), (PA, 3, NONE), (S, 3, NONE)], 24),
+    ("a,b,a.b", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], 24),
 ])
 def test_form_compile_accepts_tab_ewfd_forms(libfe, expr, ops, shape):
     f = fe.form_compile(expr, ops)
@@ -94,8 +98,12 @@ def test_form_compile_accepts_tab_ewfd_forms(libfe, expr, ops, shape):
 
 
 @pytest.mark.parametrize("expr,ops,code", [
-    # valid notation, no kernel: Navier-Stokes convection, weighted dot, Stokes, divergence
-    ("i,i.j,j", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
+    # valid notation, no kernel: weighted dot, Stokes, divergence, ...
+    ("i,i.j,j", [(V, 3, NONE), (PA, 3, NONE), (PA, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),  # eval mode
+    ("i,i.j,i", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
+    ("j,i.j,i", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
+    ("i,i.i,i", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
+    ("i,i,i", [(V, 3, NONE), (S, 3, NONE), (PA, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
     ("ij,i,j", [(M, 1, D66), (V, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
     ("i.i,0", [(V, 3, NONE), (S, 1, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
     ("i.i", [(V, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
@@ -108,6 +116,7 @@ def test_form_compile_accepts_tab_ewfd_forms(libfe, expr, ops, shape):
     ("s(i:j->I,s(k:l)->K", [(V, 3, NONE), (S, 3, NONE)], fe.FE_ERR_INVALID_ARG),
     ("0.i,0.i", [(V, 3, NONE), (S, 3, NONE)], fe.FE_ERR_INVALID_ARG),  # scalar symbol on a vector field
     ("i,i", [(V, 2, NONE), (S, 2, NONE)], fe.FE_ERR_INVALID_ARG),
+    ("i,i.j,0", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], fe.FE_ERR_INVALID_ARG),  # scalar symbol, vector field
     ("0.i,0.i", [(V, 1, LAME), (S, 1, NONE)], fe.FE_ERR_INVALID_ARG),
 ])
 def test_form_compile_rejects(libfe, expr, ops, code):
