@@ -40,6 +40,22 @@ MATRIX_BYTES_PER_ELEM_F32 = Q2_Q * 10 * 4 + 16 + 81 * 81 * 4
 MATRIX_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 16 + 81 * 81 * 8
 
 
+# Navier-Stokes convection 'i,i.j,j' (Eq. fe2) on a 64^3 Q2 cube, +-0.1h seed 3,
+# u = a sin(pi x) cos(pi y): residual and the Eq. fe4 derivative K_e(u).
+CONVECT_N = 64
+# algorithmic bytes per element of the convective matrix kernel: J^-1 and w det J
+# (27 points x 10 values), the 27 x 3 gathered velocities, the connectivity,
+# and the K_e write (81 x 81)
+CV_BYTES_PER_ELEM_F32 = Q2_Q * 10 * 4 + 81 * 4 + 27 * 4 + 81 * 81 * 4
+CV_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 81 * 8 + 27 * 4 + 81 * 81 * 8
+# floating-point operations per element of the sum-factorised convective matrix
+# kernel (3x3x3 points, both terms; FMA = 2): interpolation x, y, z stages
+# 972 + 1458 + 1944, pointwise 1944, weight contractions z, y 6804 + 20412,
+# last contraction and row assembly 56862
+CV_FLOPS_PER_ELEM = 972 + 1458 + 1944 + 1944 + 6804 + 20412 + 56862
+FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -47,6 +63,9 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=48, help="cube edge in elements (48 -> 110,592 hexes)")
+    ap.add_argument("--workload", choices=["elasticity", "convection"], default="elasticity",
+                    help="convection: time only the Navier-Stokes convection workload on an n^3 cube "
+                         "(both precisions, no oracle), one JSON line")
     ap.add_argument("--prec", default="auto",
                     help="contraction precision of the headline path; auto = fastest of the ladder within 1e-5")
     ap.add_argument("--skip-extras", action="store_true",
@@ -251,12 +270,26 @@ def timed_steps(wl, prec, steps, warmup, ws, flush):
     return step_ms, mat_ms
 
 
+def rel_matrix_error(K, Kref):
+    """max over elements of ||K_e - K_e^ref||_F / ||K_e^ref||_F."""
+    K = np.asarray(K, dtype=np.float64)
+    num = np.sqrt(((K - Kref) ** 2).sum((1, 2)))
+    den = np.sqrt((Kref ** 2).sum((1, 2)))
+    return float((num / den).max()) if len(den) else 0.0
+
+
+def rel_vector_error(r, rref):
+    """||r - r_ref||_2 / ||r_ref||_2 over the whole array."""
+    r = np.asarray(r, dtype=np.float64).ravel()
+    rref = np.asarray(rref).ravel()
+    return float(np.linalg.norm(r - rref) / np.linalg.norm(rref))
+
+
 def sampled_errors(wl, precs, ref):
     """Relative errors of the GPU outputs on the sampled elements of `ref`
     (computed by the oracle in the CPU-baseline leg)."""
     if ref is None:
         return {}, 0
-    from tests.parity import rel_matrix_error, rel_vector_error
     idx, Kref, rref = ref
     out = {}
     it = wl.torch.from_numpy(idx).cuda()
@@ -305,6 +338,82 @@ def e2e_measure(wl, prec, steps):
             "d2h_bytes_per_step": d2h}
 
 
+class ConvectWorkload:
+    """Navier-Stokes convection, one step = FP64 geometry -> K_e(u) (Eq. fe4) ->
+    r_e(u) (Eq. fe2) -> assembled residual (compensated FP32 / FP64)."""
+
+    def __init__(self, n, device):
+        import torch
+
+        from paper_2107_04121_gb300 import fe, meshgen
+        self.fe, self.torch = fe, torch
+        self.mesh, self.u = meshgen.convect_q2_cube(n, seed=3)
+        self.E = self.mesh.n_elems
+        self.ctx = fe.Context(device)
+        self.coords = torch.from_numpy(self.mesh.coords).to(device)
+        self.conn = torch.from_numpy(self.mesh.conn).to(device)
+        self.m = fe.Mesh(self.coords, self.conn)
+        self.geoms = {"f64": fe.hex_geometry(self.ctx, self.m, 2, 3, flags=fe.GEOM_STORE_F64),
+                      "f32": fe.hex_geometry(self.ctx, self.m, 2, 3, flags=fe.GEOM_STORE_F32)}
+        self.form = fe.convect_form()
+        self.u64 = torch.from_numpy(self.u).to(device)
+        self.u32 = self.u64.float()
+        self.asm = fe.assembly_create(self.ctx, self.m)
+        self.bufs = {}
+        self.ctx.check()
+
+    outputs = Workload.outputs
+    drop = Workload.drop
+
+    def step(self, prec, mk_events=None):
+        fe = self.fe
+        K, r, g = self.outputs(prec)
+        u = self.u64 if prec == "f64" else self.u32
+        geom = self.geoms[prec]
+        geom.update()
+        if mk_events:
+            mk_events[0].record()
+        fe.eval_matrix(self.ctx, self.form, geom, [None, u, u], prec, out=K)
+        if mk_events:
+            mk_events[1].record()
+        fe.eval_residual(self.ctx, self.form, geom, [None, u, u], prec, out=r)
+        fe.assemble_vector(self.ctx, self.asm, 3, r, prec, out=g,
+                           flags=0 if prec == "f64" else fe.ASSEMBLE_COMPENSATED)
+
+
+def convect_measure(n, device, ws, flush, ref, hbm_peak, steps=5, warmup=3):
+    """FP32 and FP64 steps of the convection workload, the roofline of its matrix
+    kernel (HBM for FP32, the FP64 pipe for FP64) and sampled errors against the
+    oracle (reference computed in the CPU-baseline leg)."""
+    cw = ConvectWorkload(n, device)
+    out = {"workload": "Navier-Stokes convection 'i,i.j,j', Q2 hexahedra, %d^3 = %d elements, +-0.1h seed 3, "
+                       "u = a sin(pi x) cos(pi y); step = FP64 geometry + K_e(u) (Eq. fe4) + r_e(u) + "
+                       "assembly" % (n, cw.E), "elements": cw.E}
+    for prec in ("f32", "f64"):
+        st, mt = timed_steps(cw, prec, steps, warmup, ws, flush)
+        t = max_over_ranks(sum(st), ws)
+        mat = sum(mt) / len(mt)
+        d = {"value": ws * cw.E * steps / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps, "matrix_ms": mat}
+        if prec == "f32":
+            ach = cw.E * CV_BYTES_PER_ELEM_F32 / (mat / 1e3) / 1e9
+            d["roofline"] = {"kernel": "k_convect_sf (matrix, f32)", "bound": "hbm", "achieved": ach,
+                             "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
+                             "bytes_per_elem": CV_BYTES_PER_ELEM_F32}
+        else:
+            ach = cw.E * CV_FLOPS_PER_ELEM / (mat / 1e3) / 1e12
+            d["roofline"] = {"kernel": "k_convect_sf (matrix, f64)", "bound": "fp64", "achieved": ach,
+                             "peak": FP64_PEAK_TFLOPS_NOMINAL, "peak_source": "nominal", "unit": "TFLOP/s",
+                             "frac": ach / FP64_PEAK_TFLOPS_NOMINAL, "flops_per_elem": CV_FLOPS_PER_ELEM}
+        if ref is not None:
+            errs, ns = sampled_errors(cw, [prec], ref)
+            d["rel_err_K"], d["rel_err_r"], d["sampled_elements"] = errs["K_" + prec], errs["r_" + prec], ns
+        out[prec] = d
+        cw.drop(prec)
+    cw.ctx.check()
+    cw.ctx.close()
+    return out
+
+
 # ---- CPU oracle (baseline / reference arm) ------------------------------------------------
 
 def oracle_step(mesh, lam, mu, u, n_elems):
@@ -323,7 +432,8 @@ def cpu_baseline(n, min_seconds=10.0):
     """The CPU-baseline leg: the FP64 oracle timed on the host cores over whole
     steps of the full workload, repeated until at least `min_seconds` have passed
     (the sample), and its element matrices and residuals on 64 sampled elements
-    (first, last, 62 seeded), against which the GPU outputs are checked."""
+    (first, last, 62 seeded), against which the GPU outputs are checked, and the
+    same sampled reference for the convection workload."""
     import oracle
     from paper_2107_04121_gb300 import meshgen
     mesh, lam, mu, u = meshgen.elasticity_q2_cube(n, seed=1)
@@ -345,7 +455,22 @@ def cpu_baseline(n, min_seconds=10.0):
     wdetJ, G, _ = oracle.geometry(mesh.coords, conn, oracle.RefElement(2, 3))
     D = oracle.lame_to_D(lam[idx], mu[idx])
     ref = (idx, oracle.matrix_elasticity(wdetJ, G, D), oracle.residual_elasticity(conn, wdetJ, G, D, u))
-    return base, ref
+    return base, ref, convect_reference(CONVECT_N)
+
+
+def convect_reference(n):
+    """CPU-baseline leg, convection workload: the oracle's K_e(u) and r_e(u) on 64
+    sampled elements (first, last, 62 seeded)."""
+    import oracle
+    from paper_2107_04121_gb300 import meshgen
+    mesh, u = meshgen.convect_q2_cube(n, seed=3)
+    E = mesh.n_elems
+    rng = np.random.default_rng(9)
+    idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, min(62, E), replace=False)]))
+    ref = oracle.RefElement(2, 3)
+    conn = mesh.conn[idx]
+    wdetJ, G, _ = oracle.geometry(mesh.coords, conn, ref)
+    return (idx, oracle.matrix_convect(conn, wdetJ, ref.phi, G, u), oracle.residual_convect(conn, wdetJ, ref.phi, G, u))
 
 
 def cpu_info():
@@ -412,14 +537,24 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    if args.workload == "convection":
+        res = convect_measure(args.n, local, ws, flush, None, hbm_peak, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"workload": "convection", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+                              **res}), flush=True)
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
     # the oracle's OpenMP threads must not compete with the timed GPU region:
     # time the CPU baseline first (rank 0, N = 1 only)
-    cpu, ref = None, None
+    cpu, ref, cv_ref = None, None, None
     if rank == 0 and ws == 1 and not args.skip_extras:
-        cpu, ref = cpu_baseline(args.n)
+        cpu, ref, cv_ref = cpu_baseline(args.n)
 
     wl = Workload(args.n, local)
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     ladder = None
     prec = args.prec
     if prec == "auto":
@@ -473,6 +608,10 @@ def main():
         line["speedup_vs_fp64_path"] = value / line["fp64_path"]["value"]
         if rank == 0:
             line["e2e"] = e2e_measure(wl, prec, 3)
+        # the Navier-Stokes convection workload (Eq. fe2, fe4), same device
+        for p in list(wl.bufs):
+            wl.drop(p)
+        line["convective"] = convect_measure(CONVECT_N, local, ws, flush, cv_ref, hbm_peak)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
