@@ -564,6 +564,90 @@ int oracle_matrix_convect(long long n_elems, int N, int Q, const int32_t *conn, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* Adjoint of the assembled isotropic elasticity residual.  The paper states the
+ * residual (Algorithm 1, form 'IK,s(i:j)->I,s(k:l)->K'); the derivatives below
+ * are derived here.  For a scalar objective of the assembled residual R with
+ * adjoint vector rbar = dObjective/dR (for J = |R|^2 / 2, rbar = R), the
+ * objective's derivative is rbar . dR = sum_e int sigma(u) : eps(rbar) dx in
+ * each parameter, with lambda_e, mu_e entering sigma = lambda tr(eps) I + 2 mu eps
+ * and the node positions entering the integration domain (det J) and the
+ * physical gradients.  Per element:
+ *   d/d lambda_e = sum_q wdetJ div(u_h) div(rbar_h)
+ *   d/d mu_e     = sum_q wdetJ 2 eps(u_h) : eps(rbar_h)
+ *   d/d x_(a,m)  = sum_q wdetJ [ f G[m][a] - sum_j M_mj G[j][a] ],
+ *       f = sigma(u_h) : eps(rbar_h),
+ *       M = (grad rbar_h)^T sigma(u_h) + (grad u_h)^T sigma(rbar_h)
+ * (from d(det J) = det J sum_a G_a . dx_a and d(grad v) = -(grad v)(grad dV) for a
+ * node displacement field dV).  dX_e is written component-major, dX_e[e][m*N + a],
+ * the layout of a vector element residual, so that it assembles like one. */
+static void grad_at(int N, const double *Gq, const double *ve, double gv[3][3])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double s = 0.0;
+            for (int b = 0; b < N; ++b) s += ve[i * N + b] * Gq[j * N + b];
+            gv[i][j] = s;
+        }
+}
+
+static void lame_stress(double lam, double mu, double g[3][3], double sig[3][3])
+{
+    const double tr = g[0][0] + g[1][1] + g[2][2];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) sig[i][j] = mu * (g[i][j] + g[j][i]) + (i == j ? lam * tr : 0.0);
+}
+
+int oracle_adjoint_elasticity(long long n_elems, int N, int Q, const int32_t *conn, const double *wdetJ,
+                              const double *G, const double *lam, const double *mu, const double *u,
+                              const double *rbar, double *dlam, double *dmu, double *dX)
+{
+    if (n_elems < 0 || N < 1 || N > 512 || !conn || !wdetJ || !G || !lam || !mu || !u || !rbar) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double ue[3 * 512], be[3 * 512];
+        gather_vec(N, conn + (size_t)e * N, u, ue);
+        gather_vec(N, conn + (size_t)e * N, rbar, be);
+        double sl = 0.0, sm = 0.0;
+        double *dxe = dX ? dX + (size_t)e * 3 * N : NULL;
+        if (dxe)
+            for (int c = 0; c < 3 * N; ++c) dxe[c] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            const double *Gq = G + ((size_t)e * Q + q) * 3 * N;
+            const double wd = wdetJ[(size_t)e * Q + q];
+            double gu[3][3], gb[3][3], su[3][3], sb[3][3];
+            grad_at(N, Gq, ue, gu);
+            grad_at(N, Gq, be, gb);
+            const double divu = gu[0][0] + gu[1][1] + gu[2][2], divb = gb[0][0] + gb[1][1] + gb[2][2];
+            double ee = 0.0; /* eps(u) : eps(rbar) */
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) ee += 0.25 * (gu[i][j] + gu[j][i]) * (gb[i][j] + gb[j][i]);
+            sl += wd * divu * divb;
+            sm += wd * 2.0 * ee;
+            if (!dxe) continue;
+            lame_stress(lam[e], mu[e], gu, su);
+            lame_stress(lam[e], mu[e], gb, sb);
+            const double f = lam[e] * divu * divb + 2.0 * mu[e] * ee;
+            double M[3][3];
+            for (int m = 0; m < 3; ++m)
+                for (int j = 0; j < 3; ++j) {
+                    double s = 0.0;
+                    for (int i = 0; i < 3; ++i) s += gb[i][m] * su[i][j] + gu[i][m] * sb[i][j];
+                    M[m][j] = s;
+                }
+            for (int m = 0; m < 3; ++m)
+                for (int a = 0; a < N; ++a) {
+                    double s = f * Gq[m * N + a];
+                    for (int j = 0; j < 3; ++j) s -= M[m][j] * Gq[j * N + a];
+                    dxe[m * N + a] += wd * s;
+                }
+        }
+        if (dlam) dlam[e] = sl;
+        if (dmu) dmu[e] = sm;
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Assembly of element vectors into a global vector (outside the timed region
  * of the paper, Sec. 6): g[ncomp*conn[e][a] + i] += r[e][i*N + a], summed
  * sequentially in ascending (e, a, i) order.  accumulate = 0 zeroes g first. */

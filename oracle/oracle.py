@@ -55,6 +55,8 @@ def lib():
                                               _D]
         L.oracle_matrix_convect.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D, _D,
                                             ctypes.c_int, ctypes.c_int, _D]
+        L.oracle_adjoint_elasticity.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D,
+                                                _D, _D, _D, _D, _D]
         L.oracle_assemble.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, ctypes.c_longlong,
                                       ctypes.c_int, _D]
         L.oracle_num_threads.restype = ctypes.c_int
@@ -221,6 +223,35 @@ def matrix_convect(conn, wdetJ, phi, G, u, w=None, wrt_u=True, wrt_w=True):
     _check(lib().oracle_matrix_convect(E, N, Q, _i(conn), _d(wdetJ), _d(_f64(phi)), _d(G), _d(u), _d(w),
                                        int(bool(wrt_u)), int(bool(wrt_w)), _d(K)))
     return K
+
+
+def adjoint_elasticity_terms(conn, wdetJ, G, lam, mu, u, rbar):
+    """Per-element derivatives of sum_e rbar_e . r_e for the isotropic elasticity
+    residual: (dlam (E,), dmu (E,), dX_e (E, 3*N) component-major); see oracle.c."""
+    E, Q, _, N = G.shape
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    dlam, dmu, dX = np.zeros(E), np.zeros(E), np.zeros((E, 3 * N))
+    _check(lib().oracle_adjoint_elasticity(E, N, Q, _i(conn), _d(wdetJ), _d(G), _d(_f64(lam)), _d(_f64(mu)),
+                                           _d(_f64(u)), _d(_f64(rbar)), _d(dlam), _d(dmu), _d(dX)))
+    return dlam, dmu, dX
+
+
+def elasticity_objective(coords, conn, ref: RefElement, lam, mu, u):
+    """J = |R|^2 / 2 with R the assembled isotropic elasticity residual (3 per node)."""
+    wdetJ, G, _ = geometry(coords, conn, ref)
+    r = residual_elasticity(conn, wdetJ, G, lame_to_D(lam, mu), u)
+    R = assemble(conn, r, np.asarray(coords).shape[0], 3)
+    return 0.5 * float(R @ R), R
+
+
+def elasticity_objective_gradient(coords, conn, ref: RefElement, lam, mu, u):
+    """J and its gradient with respect to lambda_e, mu_e and the node coordinates
+    (n_nodes, 3): rbar = R, per-element terms, dX_e assembled over the mesh."""
+    J, R = elasticity_objective(coords, conn, ref, lam, mu, u)
+    wdetJ, G, _ = geometry(coords, conn, ref)
+    dlam, dmu, dXe = adjoint_elasticity_terms(conn, wdetJ, G, lam, mu, u, R)
+    dX = assemble(conn, dXe, np.asarray(coords).shape[0], 3).reshape(-1, 3)
+    return J, dlam, dmu, dX
 
 
 def assemble(conn, r, n_nodes, ncomp, g=None):

@@ -445,3 +445,75 @@ def test_convect_constant_advection_of_constant_field_vanishes(convect_case):
     uc = np.tile(np.array([0.3, -1.2, 2.0]), mesh.n_nodes)
     r = oracle.residual_convect(mesh.conn, wdetJ, ref.phi, G, uc, w)
     assert np.abs(r).max() <= 1e-13
+
+
+# -- adjoint of the assembled elasticity residual, J = |R|^2 / 2 ----------------------
+
+@pytest.fixture(scope="module")
+def adjoint_case():
+    mesh = meshgen.structured_hex(2, 2, 3, 2, 0.1, 4)
+    lam, mu = meshgen.lame_materials(mesh)
+    u = meshgen.normal_dofs(mesh, 3)
+    ref = oracle.RefElement(2, 3)
+    J, dlam, dmu, dX = oracle.elasticity_objective_gradient(mesh.coords, mesh.conn, ref, lam, mu, u)
+    return mesh, ref, lam, mu, u, J, dlam, dmu, dX
+
+
+def test_adjoint_material_gradient_is_exact_central_difference(adjoint_case):
+    """R is linear in (lambda, mu), so J is quadratic and a central difference of
+    any step equals the directional derivative up to rounding."""
+    mesh, ref, lam, mu, u, J, dlam, dmu, dX = adjoint_case
+    rng = np.random.default_rng(41)
+    for _ in range(3):
+        dl, dm = rng.standard_normal(lam.shape), rng.standard_normal(mu.shape)
+        s = 0.1
+        Jp, _ = oracle.elasticity_objective(mesh.coords, mesh.conn, ref, lam + s * dl, mu + s * dm, u)
+        Jm, _ = oracle.elasticity_objective(mesh.coords, mesh.conn, ref, lam - s * dl, mu - s * dm, u)
+        fd = (Jp - Jm) / (2 * s)
+        an = dlam @ dl + dmu @ dm
+        assert abs(fd - an) <= 1e-12 * abs(J), (fd, an)
+
+
+def test_adjoint_coordinate_gradient_matches_central_difference(adjoint_case):
+    """The shape derivative against central differences of the objective in
+    seeded unit directions over all node coordinates (step 1e-6, O(h^2))."""
+    mesh, ref, lam, mu, u, J, dlam, dmu, dX = adjoint_case
+    rng = np.random.default_rng(42)
+    for _ in range(5):
+        d = rng.standard_normal(mesh.coords.shape)
+        d /= np.linalg.norm(d)
+        h = 1e-6
+        Jp, _ = oracle.elasticity_objective(mesh.coords + h * d, mesh.conn, ref, lam, mu, u)
+        Jm, _ = oracle.elasticity_objective(mesh.coords - h * d, mesh.conn, ref, lam, mu, u)
+        fd = (Jp - Jm) / (2 * h)
+        an = float((dX * d).sum())
+        assert abs(fd - an) <= 1e-7 * np.linalg.norm(dX), (fd, an)
+
+
+def test_adjoint_coordinate_gradient_is_translation_invariant(adjoint_case):
+    """J does not change when every node moves by the same vector: the node
+    gradients sum to zero in each direction."""
+    mesh, ref, lam, mu, u, J, dlam, dmu, dX = adjoint_case
+    assert np.abs(dX.sum(0)).max() <= 1e-12 * np.abs(dX).sum()
+
+
+def test_adjoint_material_gradient_closed_form_on_homogeneous_stretch():
+    """One box element, u = uniform stretch e (u = diag(e) x): grad u = diag(e) at
+    every point, and with rbar = R the per-element terms are wdetJ-weighted
+    products; check d/dlambda = sum_q wdetJ div(u) div(rbar_h) against a direct
+    evaluation of rbar's divergence through the exact box integrals."""
+    h = (0.5, 0.7, 1.3)
+    mesh = meshgen.structured_hex(1, 1, 1, 2, 0.0, 0, lengths=h)
+    e = np.array([0.3, -0.2, 0.5])
+    u = (mesh.coords * e).reshape(-1)
+    ref = oracle.RefElement(2, 3)
+    lam, mu = np.array([1.3]), np.array([0.7])
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    # a given adjoint field rbar: a second linear field, so div(rbar_h) = trace(Bm)
+    Bm = np.array([[0.2, 0.1, 0.0], [0.0, -0.4, 0.3], [0.5, 0.0, 0.1]])
+    rbar = (mesh.coords @ Bm.T).reshape(-1)
+    dlam, dmu, _ = oracle.adjoint_elasticity_terms(mesh.conn, wdetJ, G, lam, mu, u, rbar)
+    vol = h[0] * h[1] * h[2]
+    epsb = 0.5 * (Bm + Bm.T)
+    assert abs(dlam[0] - vol * e.sum() * np.trace(Bm)) <= 1e-13
+    assert abs(dmu[0] - vol * 2 * (np.diag(e) * epsb).sum()) <= 1e-13
