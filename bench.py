@@ -56,6 +56,11 @@ CV_FLOPS_PER_ELEM = 972 + 1458 + 1944 + 1944 + 6804 + 20412 + 56862
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
 
 
+# Adjoint: J = |R|^2 / 2 of the assembled Q2 elasticity residual on a 32^3 cube
+# (+-0.1h, seed 4), gradients in lambda_e, mu_e, X and u through torch.autograd.
+ADJOINT_N = 32
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,6 +419,79 @@ def convect_measure(n, device, ws, flush, ref, hbm_peak, steps=5, warmup=3):
     return out
 
 
+def adjoint_measure(n, device, flush, ref, steps=5, warmup=3):
+    """One gradient step = forward (FP64 geometry, r_e, assembly, J) + backward
+    (geometry recomputed, adjoint kernel, assembly of dX, K Rbar for du), in FP32
+    and FP64, with the adjoint kernel timed alone; errors against the oracle
+    gradient (computed in the CPU-baseline leg)."""
+    import torch
+
+    from paper_2107_04121_gb300 import autograd as fad
+    from paper_2107_04121_gb300 import fe, meshgen
+    mesh, lam, mu, u = meshgen.elasticity_q2_cube(n, seed=4, perturb=0.1)
+    ctx = fe.Context(device)
+    out = {"workload": "J = |R|^2/2 of the assembled Q2 elasticity residual, %d^3 = %d hexes, +-0.1h seed 4; "
+                       "step = forward + backward (d/dlambda, d/dmu, d/dX, d/du)" % (n, mesh.n_elems),
+           "elements": mesh.n_elems}
+    for prec in ("f32", "f64"):
+        X = torch.from_numpy(mesh.coords).to(device)
+        conn = torch.from_numpy(mesh.conn).to(device)
+        prob = fad.ElasticityProblem(ctx, X, conn, 2, 3, prec)
+        dt = prob.dtype
+        lam_t = torch.from_numpy(lam).to(device, dt).requires_grad_()
+        mu_t = torch.from_numpy(mu).to(device, dt).requires_grad_()
+        u_t = torch.from_numpy(u).to(device, dt).requires_grad_()
+        X.requires_grad_()
+
+        def one():
+            for t in (lam_t, mu_t, X, u_t):
+                t.grad = None
+            R = fad.assembled_elasticity_residual(prob, lam_t, mu_t, X, u_t)
+            Jv = 0.5 * (R.double() * R.double()).sum()
+            Jv.backward()
+            return Jv
+
+        for _ in range(warmup):
+            one()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            one()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        # the adjoint kernel alone
+        mat = torch.stack([lam_t.detach(), mu_t.detach()], 1).double().contiguous()
+        rbar = torch.randn(3 * mesh.n_nodes, dtype=dt, device=device)
+        kt = []
+        for i in range(warmup + steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fe.eval_residual_adjoint(ctx, prob.form, prob.geom, [mat, None, u_t.detach()], rbar, prec)
+            b.record()
+            b.synchronize()
+            if i >= warmup:
+                kt.append(a.elapsed_time(b))
+        ctx.check()
+        ms = statistics.median(ts)
+        d = {"value": mesh.n_elems / (ms / 1e3), "unit": UNIT + " (gradient steps x elements)", "ms_per_step": ms,
+             "adjoint_kernel_ms": statistics.median(kt)}
+        if ref is not None:
+            one()
+            Jref, dl, dm, dX = ref
+            rel = lambda a, b: float(np.linalg.norm(np.asarray(a, dtype=np.float64) - b) / np.linalg.norm(b))
+            d["rel_err"] = {"lambda": rel(lam_t.grad.cpu().numpy(), dl), "mu": rel(mu_t.grad.cpu().numpy(), dm),
+                            "X": rel(X.grad.cpu().numpy(), dX)}
+        out[prec] = d
+        del prob
+    ctx.close()
+    return out
+
+
 # ---- CPU oracle (baseline / reference arm) ------------------------------------------------
 
 def oracle_step(mesh, lam, mu, u, n_elems):
@@ -455,7 +533,15 @@ def cpu_baseline(n, min_seconds=10.0):
     wdetJ, G, _ = oracle.geometry(mesh.coords, conn, oracle.RefElement(2, 3))
     D = oracle.lame_to_D(lam[idx], mu[idx])
     ref = (idx, oracle.matrix_elasticity(wdetJ, G, D), oracle.residual_elasticity(conn, wdetJ, G, D, u))
-    return base, ref, convect_reference(CONVECT_N)
+    return base, ref, (convect_reference(CONVECT_N), adjoint_reference(ADJOINT_N))
+
+
+def adjoint_reference(n):
+    """CPU-baseline leg, adjoint workload: the oracle's J and gradient."""
+    import oracle
+    from paper_2107_04121_gb300 import meshgen
+    mesh, lam, mu, u = meshgen.elasticity_q2_cube(n, seed=4, perturb=0.1)
+    return oracle.elasticity_objective_gradient(mesh.coords, mesh.conn, oracle.RefElement(2, 3), lam, mu, u)
 
 
 def convect_reference(n):
@@ -550,9 +636,9 @@ def main():
 
     # the oracle's OpenMP threads must not compete with the timed GPU region:
     # time the CPU baseline first (rank 0, N = 1 only)
-    cpu, ref, cv_ref = None, None, None
+    cpu, ref, cv_ref, ad_ref = None, None, None, None
     if rank == 0 and ws == 1 and not args.skip_extras:
-        cpu, ref, cv_ref = cpu_baseline(args.n)
+        cpu, ref, (cv_ref, ad_ref) = cpu_baseline(args.n)
 
     wl = Workload(args.n, local)
     ladder = None
@@ -612,6 +698,7 @@ def main():
         for p in list(wl.bufs):
             wl.drop(p)
         line["convective"] = convect_measure(CONVECT_N, local, ws, flush, cv_ref, hbm_peak)
+        line["adjoint"] = adjoint_measure(ADJOINT_N, local, flush, ad_ref)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:

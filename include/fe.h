@@ -271,6 +271,30 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
 fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const void *const *args,
                            fe_precision prec, void *r_out, fe_stream_t stream);
 
+/* Adjoint of residual mode (a vector-Jacobian product).  For an adjoint DOF
+ * vector rbar (n_nodes * 3, device array, float64 for FE_F64 else float32),
+ * e.g. rbar = dObjective/dR for an objective of the assembled residual R, the
+ * derivatives of rbar . R(u; lambda, mu, X), element by element:
+ *   d_mat  (n_elems, 2): [d/d lambda_e, d/d mu_e], the layout of the
+ *          FE_MAT_LAME material operand (NULL: not computed)
+ *   d_x_e  (n_elems, 3 * N): d/d x of the element's nodes, component-major
+ *          [m * N + a] like a vector element residual; fe_assemble_vector with
+ *          ncomp 3 sums it into d/dX (n_nodes, 3) (NULL: not computed)
+ * with d/d lambda_e = sum_q w det J div(u_h) div(rbar_h), d/d mu_e = sum_q
+ * w det J 2 eps(u_h) : eps(rbar_h), and the coordinate term from d(det J) and
+ * d(J^-1) (the shape derivative of sum_e int sigma(u_h) : eps(rbar_h)).
+ * The paper has no counterpart: it differentiates forms with respect to DOFs
+ * only (Eq. fe4); this is the reverse mode of its residual (Algorithm 1) in the
+ * material and geometry inputs.  Supported: linear elasticity with FE_MAT_LAME
+ * materials (material letters in (v, u) order) on tensor-product hexahedra
+ * whose basis carries its 1-D factors, FE_F64 or FE_F32 (outputs of that
+ * dtype).  args as fe_eval_residual.  Errors: FE_ERR_INVALID_ARG (both outputs
+ * NULL, missing arrays), FE_ERR_UNSUPPORTED_SPEC (other forms, precisions or
+ * elements), FE_ERR_CUDA. */
+fe_status fe_eval_residual_adjoint(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom,
+                                   const void *const *args, const void *rbar, fe_precision prec, void *d_mat,
+                                   void *d_x_e, fe_stream_t stream);
+
 /* ---- assembly ------------------------------------------------------------------- */
 
 /* Build the node -> (element, local node) incidence lists of a mesh on the

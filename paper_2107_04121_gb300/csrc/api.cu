@@ -367,6 +367,28 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
     return from_cuda(e, "fe_eval_residual");
 }
 
+fe_status fe_eval_residual_adjoint(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g,
+                                   const void *const *args, const void *rbar, fe_precision prec, void *d_mat,
+                                   void *d_x_e, fe_stream_t stream)
+{
+    fe_material_args mat{};
+    const bool empty = g && g->mesh.n_elems == 0;
+    if (!d_mat && !d_x_e && !empty) return FE_ERR_INVALID_ARG;
+    fe_status st = eval_common(ctx, form, g, args, prec, d_mat ? d_mat : d_x_e, &mat);
+    if (st) return st;
+    if (form->kind != FK_ELASTICITY || form->mat != FE_MAT_LAME || form->mat_transposed)
+        return FE_ERR_UNSUPPORTED_SPEC;
+    if (prec != FE_F64 && prec != FE_F32) return FE_ERR_UNSUPPORTED_SPEC;
+    if (!fe_convect_supported(g)) return FE_ERR_UNSUPPORTED_SPEC;  // same sum-factorised (n1d, nq1d) set
+    if (!empty && (!args[form->state_op] || !rbar)) return FE_ERR_INVALID_ARG;
+    cudaStream_t s = to_cuda(stream);
+    cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, s);
+    if (e == cudaSuccess)
+        e = fe_launch_adjoint(g, prec == FE_F64, mat.data, args[form->state_op], rbar, d_mat, d_x_e, ctx->d_status,
+                              s);
+    return from_cuda(e, "fe_eval_residual_adjoint");
+}
+
 // ---- assembly -----------------------------------------------------------------------
 
 fe_status fe_assembly_create(fe_ctx *ctx, const fe_mesh *mesh, fe_assembly_h **out, fe_stream_t stream)

@@ -79,6 +79,12 @@ cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_ma
 cudaError_t fe_launch_convect(const fe_geometry_h *g, bool f64, const void *u, const void *w, int wrt_grad,
                               int wrt_adv, void *K, void *r, unsigned long long *status, cudaStream_t s);
 bool fe_convect_supported(const fe_geometry_h *g);
+// Adjoint of the isotropic elasticity residual (sum factorisation, same (n1d,
+// nq1d) pairs as the convective kernels): d(rbar . R)/d(lambda_e, mu_e) into
+// dmat (E, 2) and per-element coordinate derivatives into dxe (E, 3 N); either
+// may be null.
+cudaError_t fe_launch_adjoint(const fe_geometry_h *g, bool f64, const double *lame, const void *u,
+                              const void *rbar, void *dmat, void *dxe, unsigned long long *status, cudaStream_t s);
 cudaError_t fe_launch_assembly_build(fe_assembly_h *a, int *d_flag, cudaStream_t s);
 cudaError_t fe_launch_assemble(const fe_assembly_h *a, int ncomp, bool f64, const void *r, void *out,
                                unsigned flags, cudaStream_t s);

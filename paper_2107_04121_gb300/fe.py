@@ -32,7 +32,8 @@ ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
 EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
     "fe_refbasis_hex", "fe_refbasis_hex_1d", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
-    "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_assembly_create", "fe_assembly_free",
+    "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_eval_residual_adjoint", "fe_assembly_create",
+    "fe_assembly_free",
     "fe_assemble_vector", "fe_assemble_vector_noalloc",
 ]
 
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_form_shape.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i)]
     L.fe_eval_matrix.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, i, vp, vp]
     L.fe_eval_residual.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, vp, vp]
+    L.fe_eval_residual_adjoint.argtypes = [vp, vp, vp, ctypes.POINTER(vp), vp, i, vp, vp, vp]
     L.fe_assembly_create.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(vp), vp]
     L.fe_assembly_free.argtypes = [vp]
     L.fe_assemble_vector.argtypes = [vp, vp, i, vp, i, vp, ctypes.c_uint, vp]
@@ -374,6 +376,30 @@ def eval_residual(ctx: Context, form: Form, geom: Geometry, args, precision="f64
                                  _prec(precision),
                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "fe_eval_residual")
     return out
+
+
+def eval_residual_adjoint(ctx: Context, form: Form, geom: Geometry, args, rbar, precision="f64", d_mat=None,
+                          d_x_e=None, want_mat=True, want_x=True, stream=None):
+    """fe_eval_residual_adjoint: derivatives of rbar . R with respect to the Lame
+    pairs, d_mat (E, 2), and the element node coordinates, d_x_e (E, 3 N)
+    component-major (assemble with assemble_vector(ncomp=3) for (n_nodes, 3))."""
+    import torch
+    dt = _out_dtype(precision)
+    E, dev = geom.mesh.n_elems, geom.mesh.coords.device
+    if want_mat and d_mat is None:
+        d_mat = torch.empty((E, 2), dtype=dt, device=dev)
+    if want_x and d_x_e is None:
+        d_x_e = torch.empty((E, 3 * geom.N), dtype=dt, device=dev)
+    for t, name in ((d_mat, "d_mat"), (d_x_e, "d_x_e"), (rbar, "rbar")):
+        if t is not None:
+            _dev(t, dt, name)
+    if rbar.numel() != 3 * geom.mesh.n_nodes:
+        raise ValueError("rbar must have n_nodes * 3 entries")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    _check(_lib.fe_eval_residual_adjoint(ctx.handle, form._h, geom._h, _args(form, args, geom, dt), ptr(rbar),
+                                         _prec(precision), ptr(d_mat), ptr(d_x_e), _stream_ptr(stream)),
+           "fe_eval_residual_adjoint")
+    return d_mat, d_x_e
 
 
 class Assembly:
