@@ -172,6 +172,21 @@ fe_status fe_refbasis_hex(int p, int nq, double *points, double *weights, double
  * derivatives.  Same limits as fe_refbasis_hex. */
 fe_status fe_refbasis_hex_1d(int p, int nq, double *b1d, double *d1d);
 
+/* Lagrange basis of order p (1..3) on the reference tetrahedron
+ * {x, y, z >= 0, x + y + z <= 1} at the points of the Grundmann-Moller rule of
+ * index s (0..6, exact for degree 2s + 1; negative weights occur for s >= 1).
+ * Nodes are the lattice points (i, j, k) / p with i + j + k <= p, numbered with
+ * x fastest: N = (p+1)(p+2)(p+3)/6 (4, 10, 20).  The basis is the barycentric
+ * product prod_m prod_{t < a_m} (p l_m - t) / (t + 1) (l = barycentric
+ * coordinates, a = the node's barycentric multi-index).  The rule's points are
+ * listed by GM level i and then by composition; its weights sum to the volume
+ * 1/6.  Output arrays as fe_refbasis_hex with Q = fe_gm_rule_size(s) points;
+ * any may be NULL.  Errors: FE_ERR_SHAPE.  (The rule of index p is the one of
+ * "order 2p" for the P_p mixed-mesh workload: 5, 15, 35 points.) */
+fe_status fe_refbasis_tet(int p, int s, double *points, double *weights, double *phi, double *dphi);
+/* Number of points of the Grundmann-Moller rule of index s (0..6), -1 otherwise. */
+int fe_gm_rule_size(int s);
+
 /* ---- geometry ----------------------------------------------------------------- */
 
 /* Storage flags of fe_geometry. */

@@ -162,6 +162,108 @@ int oracle_hex_quadrature(int nq, double *pts, double *w)
  *   Jinv[e][q][k][j] (optional)
  * det J by cofactor expansion along the first row; J^-1 = adj(J) / det J.
  * Returns 0, or 1 + the first element index with det J <= 0. */
+/* ------------------------------------------------------------------------ */
+/* Reference tetrahedron T = {x, y, z >= 0, x + y + z <= 1}, barycentric
+ * coordinates L = (1 - x - y - z, x, y, z).
+ *
+ * Grundmann-Moller rule of index s (Grundmann & Moller 1978), degree 2s + 1:
+ * level i = 0..s carries the weight (-1)^i 2^(-2s) (2s + 4 - 2i)^(2s+1) /
+ * (i! (2s + 4 - i)!) at the barycentric points (2 b + 1) / (2s + 4 - 2i) for
+ * every b in N^4 with |b| = s - i.  Points are listed level by level, and within
+ * a level with b_0 slowest and b_3 fastest, each b_k descending from its
+ * largest possible value; Cartesian point = (L1, L2, L3). */
+static double factorial(int n)
+{
+    double f = 1.0;
+    for (int k = 2; k <= n; ++k) f *= k;
+    return f;
+}
+
+int oracle_gm_rule(int s, double *pts, double *w)
+{
+    if (s < 0 || s > 6) return OR_BAD_ARG;
+    int count = 0;
+    for (int i = 0; i <= s; ++i) {
+        const int m = s - i;
+        const int den = 2 * s + 4 - 2 * i;
+        const double wi = ((i & 1) ? -1.0 : 1.0) * pow(2.0, -2.0 * s) * pow((double)den, 2.0 * s + 1.0) /
+                          (factorial(i) * factorial(2 * s + 4 - i));
+        for (int b0 = m; b0 >= 0; --b0)
+            for (int b1 = m - b0; b1 >= 0; --b1)
+                for (int b2 = m - b0 - b1; b2 >= 0; --b2) {
+                    const int b3 = m - b0 - b1 - b2;
+                    if (pts) {
+                        pts[3 * count + 0] = (2.0 * b1 + 1.0) / den;
+                        pts[3 * count + 1] = (2.0 * b2 + 1.0) / den;
+                        pts[3 * count + 2] = (2.0 * b3 + 1.0) / den;
+                    }
+                    if (w) w[count] = wi;
+                    ++count;
+                }
+    }
+    return count;
+}
+
+/* Order-p Lagrange basis on T: nodes at the lattice points (i, j, k)/p,
+ * i + j + k <= p, x fastest (k slowest); the node with barycentric indices
+ * a = (p - i - j - k, i, j, k) has phi_a = prod_m S_{a_m}(L_m) with the
+ * Silvester factor S_n(L) = prod_{t=0}^{n-1} (p L - t) / (t + 1). */
+static double silvester(int p, int n, double L)
+{
+    double v = 1.0;
+    for (int t = 0; t < n; ++t) v *= (p * L - t) / (t + 1.0);
+    return v;
+}
+
+static double silvester_deriv(int p, int n, double L)
+{
+    /* product rule over the n linear factors */
+    double s = 0.0;
+    for (int r = 0; r < n; ++r) {
+        double v = p / (r + 1.0);
+        for (int t = 0; t < n; ++t)
+            if (t != r) v *= (p * L - t) / (t + 1.0);
+        s += v;
+    }
+    return s;
+}
+
+int oracle_tet_basis(int p, int n_pts, const double *pts, double *phi, double *dphi)
+{
+    if (p < 1 || p > 3 || n_pts < 0 || !pts) return OR_BAD_ARG;
+    const int N = (p + 1) * (p + 2) * (p + 3) / 6;
+    for (int q = 0; q < n_pts; ++q) {
+        const double x = pts[3 * q], y = pts[3 * q + 1], z = pts[3 * q + 2];
+        const double L[4] = {1.0 - x - y - z, x, y, z};
+        /* dL_m / dx_c */
+        const double dL[4][3] = {{-1, -1, -1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+        int a = 0;
+        for (int k = 0; k <= p; ++k)
+            for (int j = 0; j <= p - k; ++j)
+                for (int i = 0; i <= p - k - j; ++i, ++a) {
+                    const int A[4] = {p - i - j - k, i, j, k};
+                    double S[4], dS[4];
+                    for (int m = 0; m < 4; ++m) {
+                        S[m] = silvester(p, A[m], L[m]);
+                        dS[m] = silvester_deriv(p, A[m], L[m]);
+                    }
+                    if (phi) phi[q * N + a] = S[0] * S[1] * S[2] * S[3];
+                    if (dphi)
+                        for (int c = 0; c < 3; ++c) {
+                            double g = 0.0;
+                            for (int m = 0; m < 4; ++m) {
+                                double t = dS[m] * dL[m][c];
+                                for (int o = 0; o < 4; ++o)
+                                    if (o != m) t *= S[o];
+                                g += t;
+                            }
+                            dphi[(q * 3 + c) * N + a] = g;
+                        }
+                }
+    }
+    return OR_OK;
+}
+
 long long oracle_geometry(long long n_elems, int N, int Q, const double *coords, const int32_t *conn,
                           const double *dphi, const double *w, double *wdetJ, double *G, double *Jinv)
 {

@@ -40,6 +40,8 @@ def lib():
         L.oracle_gauss_1d.argtypes = [ctypes.c_int, _D, _D]
         L.oracle_hex_basis.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
         L.oracle_hex_quadrature.argtypes = [ctypes.c_int, _D, _D]
+        L.oracle_gm_rule.argtypes = [ctypes.c_int, _D, _D]
+        L.oracle_tet_basis.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D, _D]
         L.oracle_geometry.restype = ctypes.c_longlong
         L.oracle_geometry.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _D, _I, _D, _D, _D, _D, _D]
         L.oracle_matrix_laplace.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
@@ -113,6 +115,36 @@ def hex_basis(p: int, pts):
     dphi = np.zeros((pts.shape[0], 3, N))
     _check(lib().oracle_hex_basis(p, pts.shape[0], _d(pts), _d(phi), _d(dphi)))
     return phi, dphi
+
+
+def gm_rule(s: int):
+    """Grundmann-Moller rule of index s on the reference tetrahedron: points (Q,3), weights (Q)."""
+    Q = lib().oracle_gm_rule(s, None, None)
+    if Q < 0:
+        raise ValueError("bad GM index")
+    pts, w = np.zeros((Q, 3)), np.zeros(Q)
+    lib().oracle_gm_rule(s, _d(pts), _d(w))
+    return pts, w
+
+
+def tet_basis(p: int, pts):
+    pts = _f64(pts)
+    Q = pts.shape[0]
+    N = (p + 1) * (p + 2) * (p + 3) // 6
+    phi, dphi = np.zeros((Q, N)), np.zeros((Q, 3, N))
+    _check(lib().oracle_tet_basis(p, Q, _d(pts), _d(phi), _d(dphi)))
+    return phi, dphi
+
+
+class RefTet:
+    """Reference tetrahedron of order p with the Grundmann-Moller rule of index s."""
+
+    def __init__(self, p: int, s: int):
+        self.p, self.s = p, s
+        self.pts, self.w = gm_rule(s)
+        self.phi, self.dphi = tet_basis(p, self.pts)
+        self.N = (p + 1) * (p + 2) * (p + 3) // 6
+        self.Q = self.pts.shape[0]
 
 
 class RefElement:

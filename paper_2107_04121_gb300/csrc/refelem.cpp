@@ -168,3 +168,103 @@ bool fe_host_check_tensor_basis(const fe_refbasis *b)
                         }
     return true;
 }
+
+// ---------------------------------------------------------------------------
+// Reference tetrahedron {x, y, z >= 0, x + y + z <= 1} with barycentric
+// coordinates l0 = 1 - x - y - z, l1 = x, l2 = y, l3 = z.
+//
+// Grundmann-Moller rule of index s (Grundmann & Moller, SIAM J. Numer. Anal.
+// 15 (1978)), exact for polynomials of degree 2s + 1: with d = 2s + 1 and n = 3,
+//   Q f = sum_{i=0}^{s} (-1)^i 2^{-2s} (d + n - 2i)^d / (i! (d + n - i)!)
+//         sum_{|beta| = s - i} f( (2 beta + 1) / (d + n - 2i) ),
+// beta running over the 4-part compositions of s - i (barycentric point
+// coordinates); the weights integrate over the tetrahedron itself (sum 1/6).
+// Points are listed by i, then by beta in lexicographic order (beta_0 slowest).
+static int gm_points(int s, double *pts, double *wts)
+{
+    const int d = 2 * s + 1, n = 3;
+    int np = 0;
+    for (int i = 0; i <= s; ++i) {
+        const int m = s - i, den = d + n - 2 * i;
+        // (-1)^i 2^{-2s} den^d / (i! (d + n - i)!)
+        double w = (i % 2 ? -1.0 : 1.0) * std::ldexp(1.0, -2 * s);
+        for (int t = 0; t < d; ++t) w *= den;
+        for (int t = 2; t <= i; ++t) w /= t;
+        for (int t = 2; t <= d + n - i; ++t) w /= t;
+        for (int b0 = m; b0 >= 0; --b0)
+            for (int b1 = m - b0; b1 >= 0; --b1)
+                for (int b2 = m - b0 - b1; b2 >= 0; --b2) {
+                    const int b3 = m - b0 - b1 - b2;
+                    if (pts) {
+                        pts[3 * np + 0] = (2.0 * b1 + 1.0) / den;
+                        pts[3 * np + 1] = (2.0 * b2 + 1.0) / den;
+                        pts[3 * np + 2] = (2.0 * b3 + 1.0) / den;
+                    }
+                    if (wts) wts[np] = w;
+                    ++np;
+                }
+    }
+    return np;
+}
+
+// 1-D factor of the barycentric Lagrange basis: prod_{t < n} (p l - t) / (t + 1)
+// and its derivative with respect to l.
+static void bary_factor(int p, int n, double l, double *val, double *der)
+{
+    double v = 1.0, dv = 0.0;
+    for (int t = 0; t < n; ++t) {
+        const double f = (p * l - t) / (t + 1.0), df = p / (t + 1.0);
+        dv = dv * f + v * df;
+        v *= f;
+    }
+    *val = v;
+    *der = dv;
+}
+
+extern "C" int fe_gm_rule_size(int s)
+{
+    if (s < 0 || s > 6) return -1;
+    return gm_points(s, nullptr, nullptr);
+}
+
+extern "C" fe_status fe_refbasis_tet(int p, int s, double *points, double *weights, double *phi, double *dphi)
+{
+    if (p < 1 || p > 3 || s < 0 || s > 6) return FE_ERR_SHAPE;
+    double qp[3 * 512], qw[512];
+    const int Q = gm_points(s, qp, qw);
+    const int N = (p + 1) * (p + 2) * (p + 3) / 6;
+    int idx[20][4];  // barycentric multi-indices of the lattice nodes, x fastest
+    int a = 0;
+    for (int k = 0; k <= p; ++k)
+        for (int j = 0; j <= p - k; ++j)
+            for (int i = 0; i <= p - k - j; ++i) {
+                idx[a][0] = p - i - j - k;
+                idx[a][1] = i;
+                idx[a][2] = j;
+                idx[a][3] = k;
+                ++a;
+            }
+    for (int q = 0; q < Q; ++q) {
+        const double x = qp[3 * q], y = qp[3 * q + 1], z = qp[3 * q + 2];
+        const double l[4] = {1.0 - x - y - z, x, y, z};
+        if (points)
+            for (int c = 0; c < 3; ++c) points[3 * q + c] = qp[3 * q + c];
+        if (weights) weights[q] = qw[q];
+        for (int b = 0; b < N; ++b) {
+            double f[4], df[4];
+            for (int m = 0; m < 4; ++m) bary_factor(p, idx[b][m], l[m], &f[m], &df[m]);
+            if (phi) phi[(size_t)q * N + b] = f[0] * f[1] * f[2] * f[3];
+            if (dphi)
+                for (int c = 0; c < 3; ++c) {
+                    // d l0 / dx_c = -1, d l_(c+1) / dx_c = 1
+                    double g = -df[0] * f[1] * f[2] * f[3];
+                    double t = df[c + 1];
+                    for (int m = 1; m < 4; ++m)
+                        if (m != c + 1) t *= f[m];
+                    g += t * f[0];
+                    dphi[((size_t)q * 3 + c) * N + b] = g;
+                }
+        }
+    }
+    return FE_OK;
+}

@@ -517,3 +517,123 @@ def test_adjoint_material_gradient_closed_form_on_homogeneous_stretch():
     epsb = 0.5 * (Bm + Bm.T)
     assert abs(dlam[0] - vol * e.sum() * np.trace(Bm)) <= 1e-13
     assert abs(dmu[0] - vol * 2 * (np.diag(e) * epsb).sum()) <= 1e-13
+
+
+# -- tetrahedra: Grundmann-Moller rules and Lagrange bases ----------------------------
+
+from math import factorial as _fact
+
+
+@pytest.mark.parametrize("s", [0, 1, 2, 3, 4])
+def test_gm_rule_integrates_monomials_exactly(s):
+    """int_T x^a y^b z^c = a! b! c! / (a + b + c + 3)! for a + b + c <= 2s + 1."""
+    pts, w = oracle.gm_rule(s)
+    assert len(w) == {0: 1, 1: 5, 2: 15, 3: 35, 4: 70}[s]
+    deg = 2 * s + 1
+    for a in range(deg + 1):
+        for b in range(deg + 1 - a):
+            for c in range(deg + 1 - a - b):
+                exact = _fact(a) * _fact(b) * _fact(c) / _fact(a + b + c + 3)
+                got = float((w * pts[:, 0] ** a * pts[:, 1] ** b * pts[:, 2] ** c).sum())
+                assert abs(got - exact) <= 1e-15 + 1e-13 * exact, (s, a, b, c)
+
+
+def _tet_nodes(p):
+    return np.array([(i / p, j / p, k / p) for k in range(p + 1) for j in range(p + 1 - k)
+                     for i in range(p + 1 - k - j)])
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_tet_basis_nodal_partition_and_reproduction(p):
+    X = _tet_nodes(p)
+    N = len(X)
+    assert N == (p + 1) * (p + 2) * (p + 3) // 6
+    phi, dphi = oracle.tet_basis(p, X)
+    np.testing.assert_allclose(phi, np.eye(N), atol=1e-14)
+    pts, _ = oracle.gm_rule(3)
+    phi, dphi = oracle.tet_basis(p, pts)
+    np.testing.assert_allclose(phi.sum(1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(dphi.sum(2), 0.0, atol=1e-12)
+    # every polynomial of degree <= p is reproduced by its nodal interpolant
+    for a in range(p + 1):
+        for b in range(p + 1 - a):
+            for c in range(p + 1 - a - b):
+                f = lambda x: x[..., 0] ** a * x[..., 1] ** b * x[..., 2] ** c
+                np.testing.assert_allclose(phi @ f(X), f(pts), atol=1e-13)
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_tet_basis_gradient_matches_finite_differences(p):
+    pts = np.array([[0.2, 0.3, 0.1], [0.05, 0.6, 0.25], [0.4, 0.1, 0.35]])
+    phi, dphi = oracle.tet_basis(p, pts)
+    h = 1e-6
+    for c in range(3):
+        e = np.zeros(3)
+        e[c] = h
+        fp, _ = oracle.tet_basis(p, pts + e)
+        fm, _ = oracle.tet_basis(p, pts - e)
+        np.testing.assert_allclose(dphi[:, c, :], (fp - fm) / (2 * h), atol=1e-8)
+
+
+def _random_tet(seed):
+    rng = np.random.default_rng(seed)
+    V = rng.standard_normal((4, 3))
+    if np.linalg.det(V[1:] - V[0]) < 0:
+        V[[2, 3]] = V[[3, 2]]
+    return V
+
+
+def _tet_element(p, V):
+    """Node coordinates of the straight-sided order-p tet on vertices V."""
+    X = _tet_nodes(p)
+    L = np.stack([1 - X.sum(1), X[:, 0], X[:, 1], X[:, 2]], 1)
+    return L @ V
+
+
+def test_p1_tet_closed_forms():
+    """P1: K_ab = V grad(l_a) . grad(l_b), M_ab = V (1 + delta_ab) / 20."""
+    Vx = _random_tet(71)
+    ref = oracle.RefTet(1, 1)
+    conn = np.arange(4, dtype=np.int32)[None, :]
+    wdetJ, G, _ = oracle.geometry(Vx, conn, ref)
+    vol = abs(np.linalg.det(Vx[1:] - Vx[0])) / 6
+    A = np.vstack([np.ones(4), Vx.T])            # l = A^-1 [1, x]
+    gl = np.linalg.inv(A)[:, 1:]                 # grad l_a (4, 3)
+    K = oracle.matrix_laplace(wdetJ, G)[0]
+    M = oracle.matrix_mass(wdetJ, ref.phi)[0]
+    np.testing.assert_allclose(K, vol * gl @ gl.T, rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(M, vol * (1 + np.eye(4)) / 20, rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_higher_order_tet_invariants(p):
+    Vx = _random_tet(72 + p)
+    X = _tet_element(p, Vx)
+    conn = np.arange(len(X), dtype=np.int32)[None, :]
+    ref = oracle.RefTet(p, p)
+    wdetJ, G, _ = oracle.geometry(X, conn, ref)
+    vol = abs(np.linalg.det(Vx[1:] - Vx[0])) / 6
+    K = oracle.matrix_laplace(wdetJ, G)[0]
+    M = oracle.matrix_mass(wdetJ, ref.phi)[0]
+    assert abs(wdetJ.sum() - vol) <= 1e-13 * vol
+    assert np.abs(K.sum(1)).max() <= 1e-12 * np.abs(K).max()
+    np.testing.assert_allclose(K, K.T, atol=1e-13 * np.abs(K).max())
+    assert abs(M.sum() - vol) <= 1e-13 * vol
+    # the mass integrand phi_a phi_b (degree 2p) is integrated exactly by the
+    # index-p rule: a rule of higher index gives the same matrix
+    ref_hi = oracle.RefTet(p, p + 2)
+    wd_hi, _, _ = oracle.geometry(X, conn, ref_hi)
+    M_hi = oracle.matrix_mass(wd_hi, ref_hi.phi)[0]
+    np.testing.assert_allclose(M, M_hi, atol=1e-14 * np.abs(M).max())
+    # elasticity annihilates the six rigid-body modes
+    lam, mu = np.array([1.4]), np.array([0.6])
+    KE = oracle.matrix_elasticity(wdetJ, G, oracle.lame_to_D(lam, mu))[0]
+    N = len(X)
+    for mode in range(6):
+        v = np.zeros((3, N))
+        if mode < 3:
+            v[mode] = 1.0
+        else:
+            a, b = [(0, 1), (1, 2), (0, 2)][mode - 3]
+            v[a], v[b] = -X[:, b], X[:, a]
+        assert np.abs(KE @ v.reshape(-1)).max() <= 1e-12 * np.abs(KE).max()
