@@ -298,6 +298,9 @@ cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *st, c
     case 8: return launch_geom<8>(g, st, s);
     case 27: return launch_geom<27>(g, st, s);
     case 64: return launch_geom<64>(g, st, s);
+    case 4: return launch_geom<4>(g, st, s);
+    case 10: return launch_geom<10>(g, st, s);
+    case 20: return launch_geom<20>(g, st, s);
     default: return cudaErrorInvalidValue;
     }
 }

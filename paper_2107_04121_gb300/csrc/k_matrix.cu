@@ -542,6 +542,16 @@ cudaError_t dispatch(const fe_geometry_h *g, const fe_form_h *f, fe_material_arg
     // Q3: 4x4 tiles (136 per element) for FP32 and the scalar forms; FP64
     // elasticity needs 2x2 tiles (528 per element) to keep 36 accumulators and
     // writes directly (a 64 x 192 FP64 row block per buffer would not fit)
+    // tetrahedra: P1 2x2 tiles (3 per element), P2 2x2 tiles (15 per element),
+    // P3 4x4 tiles (15 per element; FP64 elasticity 2x2, 55 per element)
+    if (N == 4 && Q == 5) return dispatch_nq<S, 4, 5, 2, 32, 96, B, 2, 32, 96, B>(g, f, mat, K, sm, s);
+    if (N == 10 && Q == 15) return dispatch_nq<S, 10, 15, 2, 8, 128, B, 2, 8, 128, B>(g, f, mat, K, sm, s);
+    if (N == 20 && Q == 35) {
+        if constexpr (D)
+            return dispatch_nq<S, 20, 35, 4, 8, 128, B, 2, 2, 128, B>(g, f, mat, K, sm, s);
+        else
+            return dispatch_nq<S, 20, 35, 4, 8, 128, B, 4, 8, 128, B>(g, f, mat, K, sm, s);
+    }
     if (N == 64 && Q == 64) {
         if constexpr (D)
             return dispatch_nq<S, 64, 64, 4, 1, 160, B, 2, 1, 544, STAGE_DIRECT>(g, f, mat, K, sm, s);
@@ -555,7 +565,9 @@ cudaError_t dispatch(const fe_geometry_h *g, const fe_form_h *f, fe_material_arg
 
 bool fe_supported_nq(int N, int Q)
 {
-    return (N == 8 && (Q == 8 || Q == 27)) || (N == 27 && (Q == 27 || Q == 64)) || (N == 64 && Q == 64);
+    return (N == 8 && (Q == 8 || Q == 27)) || (N == 27 && (Q == 27 || Q == 64)) || (N == 64 && Q == 64) ||
+           // P1, P2, P3 tetrahedra with the Grundmann-Moller rules of index p (5, 15, 35 points)
+           (N == 4 && Q == 5) || (N == 10 && Q == 15) || (N == 20 && Q == 35);
 }
 
 cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,

@@ -573,6 +573,9 @@ cudaError_t dispatch(const fe_geometry_h *g, const fe_form_h *f, fe_material_arg
     FE_CASE(27, 27, 8)
     FE_CASE(27, 64, 4)
     FE_CASE(64, 64, 2)
+    FE_CASE(4, 5, 32)
+    FE_CASE(10, 15, 16)
+    FE_CASE(20, 35, 8)
 #undef FE_CASE
     return cudaErrorInvalidValue;
 }

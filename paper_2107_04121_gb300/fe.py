@@ -31,7 +31,7 @@ ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
 
 EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
-    "fe_refbasis_hex", "fe_refbasis_hex_1d", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
+    "fe_refbasis_hex", "fe_refbasis_hex_1d", "fe_refbasis_tet", "fe_gm_rule_size", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
     "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_eval_residual_adjoint", "fe_assembly_create",
     "fe_assembly_free",
     "fe_assemble_vector", "fe_assemble_vector_noalloc",
@@ -88,6 +88,8 @@ def load_library(path: str = LIB_PATH):
     L.fe_get_status.argtypes = [vp, vp, ctypes.POINTER(ll)]
     L.fe_refbasis_hex.argtypes = [i, i, dp, dp, dp, dp]
     L.fe_refbasis_hex_1d.argtypes = [i, i, dp, dp]
+    L.fe_refbasis_tet.argtypes = [i, i, dp, dp, dp, dp]
+    L.fe_gm_rule_size.argtypes = [i]
     L.fe_geometry.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(_RefBasis), ctypes.POINTER(_Quad),
                               ctypes.c_uint, ctypes.POINTER(vp), vp]
     L.fe_geometry_update.argtypes = [vp, vp, vp]
@@ -159,6 +161,21 @@ def refbasis_hex_1d(p: int, nq: int):
     dp = ctypes.POINTER(ctypes.c_double)
     _check(L.fe_refbasis_hex_1d(p, nq, b.ctypes.data_as(dp), d.ctypes.data_as(dp)), "fe_refbasis_hex_1d")
     return b, d
+
+
+def refbasis_tet(p: int, s: int):
+    """Order-p tetrahedron Lagrange basis at the Grundmann-Moller rule of index s
+    (fe_refbasis_tet): points (Q,3), weights (Q), phi (Q,N), dphi (Q,3,N)."""
+    L = load_library()
+    Q = L.fe_gm_rule_size(s)
+    if Q < 0:
+        raise ValueError("Grundmann-Moller index must be in 0..6")
+    N = (p + 1) * (p + 2) * (p + 3) // 6
+    pts, w, phi, dphi = np.zeros((Q, 3)), np.zeros(Q), np.zeros((Q, N)), np.zeros((Q, 3, N))
+    dp = ctypes.POINTER(ctypes.c_double)
+    _check(L.fe_refbasis_tet(p, s, pts.ctypes.data_as(dp), w.ctypes.data_as(dp), phi.ctypes.data_as(dp),
+                             dphi.ctypes.data_as(dp)), "fe_refbasis_tet")
+    return pts, w, phi, dphi
 
 
 # ---- context -------------------------------------------------------------------------
@@ -279,6 +296,13 @@ def hex_geometry(ctx: Context, mesh: Mesh, p: int, nq: int, flags: int = 0, stre
     pts, w, phi, dphi = refbasis_hex(p, nq)
     b1d, d1d = refbasis_hex_1d(p, nq)
     return geometry(ctx, mesh, phi, dphi, w, flags, stream, b1d, d1d)
+
+
+def tet_geometry(ctx: Context, mesh: Mesh, p: int, s: int = None, flags: int = 0, stream=None) -> Geometry:
+    """fe_geometry with the library's order-p tetrahedron basis and the
+    Grundmann-Moller rule of index s (default p: exact for degree 2p + 1)."""
+    pts, w, phi, dphi = refbasis_tet(p, p if s is None else s)
+    return geometry(ctx, mesh, phi, dphi, w, flags, stream)
 
 
 class Form:

@@ -131,3 +131,116 @@ def convect_q2_cube(n: int = 64, seed: int = 3, perturb: float = 0.1):
     mesh = structured_hex(n, n, n, 2, perturb, seed)
     u = smooth_vector_field(mesh)
     return mesh, u
+
+
+# ---- tetrahedral meshes ---------------------------------------------------------------
+
+@dataclasses.dataclass
+class TetMesh:
+    coords: np.ndarray  # (n_nodes, 3) float64
+    conn: np.ndarray  # (n_elems, N) int32, N = (p+1)(p+2)(p+3)/6
+    order: int
+    rng: np.random.Generator
+
+    n_nodes = HexMesh.n_nodes
+    n_elems = HexMesh.n_elems
+    nodes_per_elem = HexMesh.nodes_per_elem
+
+
+def _lattice(p: int):
+    """Barycentric multi-indices (a0, a1, a2, a3) of the order-p lattice nodes,
+    x fastest: node (i, j, k)/p has a = (p - i - j - k, i, j, k)."""
+    return np.array([(p - i - j - k, i, j, k) for k in range(p + 1) for j in range(p + 1 - k)
+                     for i in range(p + 1 - k - j)], dtype=np.int64)
+
+
+def delaunay_tets(target: int, rng: np.random.Generator, points_per_tet: float = 1 / 6.55):
+    """`target` positively oriented tetrahedra of the Delaunay triangulation of
+    ceil(target * points_per_tet) uniform points in the unit cube (more points,
+    drawn from the same stream, are appended while the triangulation has fewer
+    than `target` tetrahedra): tets sorted lexicographically by their sorted
+    vertex ids, the first `target` kept (independent of the triangulator's
+    output order)."""
+    from scipy.spatial import Delaunay
+    n_pts = int(np.ceil(target * points_per_tet)) + 4
+    pts = rng.uniform(0.0, 1.0, size=(n_pts, 3))
+    while True:
+        simp = Delaunay(pts).simplices.astype(np.int64)
+        v = pts[simp]
+        vol6 = np.einsum("ij,ij->i", np.cross(v[:, 1] - v[:, 0], v[:, 2] - v[:, 0]), v[:, 3] - v[:, 0])
+        neg = vol6 < 0
+        simp[neg] = simp[neg][:, [0, 1, 3, 2]]
+        simp = simp[np.abs(vol6) > 1e-15]
+        if len(simp) >= target:
+            break
+        pts = np.concatenate([pts, rng.uniform(0.0, 1.0, size=(len(pts) // 10 + 8, 3))], 0)
+    key = np.sort(simp, axis=1)
+    simp = simp[np.lexsort(key.T[::-1])]
+    return pts, simp[:target]
+
+
+def tet_mesh(target: int, p: int, rng: np.random.Generator) -> TetMesh:
+    """Order-p straight-sided tetrahedra of a Delaunay mesh (delaunay_tets).
+    Global nodes: the triangulation's vertices (only those used, renumbered in
+    order of first use by the sorted tets), then p - 1 nodes per edge, then one
+    node per face for p = 3; edge and face nodes are shared by neighbouring
+    elements.  An edge node is keyed by (smaller vertex id, larger vertex id,
+    its barycentric index at the larger one)."""
+    pts, simp = delaunay_tets(target, rng)
+    used, inv = np.unique(simp.ravel(), return_inverse=True)
+    simp = inv.reshape(simp.shape)
+    vx = pts[used]
+    L = _lattice(p)                              # (N, 4)
+    E, N = len(simp), len(L)
+    nz = (L > 0)
+    kind = nz.sum(1)                             # 1 vertex, 2 edge, 3 face
+    conn = np.empty((E, N), dtype=np.int64)
+    coords_parts = [vx]
+    base = len(vx)
+    # vertex nodes
+    for a in np.where(kind == 1)[0]:
+        conn[:, a] = simp[:, int(np.argmax(L[a]))]
+    # edge nodes
+    ea = np.where(kind == 2)[0]
+    if len(ea):
+        ends = np.array([np.where(nz[a])[0] for a in ea])           # local vertex pair per edge node
+        g0, g1 = simp[:, ends[:, 0]], simp[:, ends[:, 1]]             # (E, n_edge_nodes)
+        k0, k1 = L[ea, ends[:, 0]], L[ea, ends[:, 1]]
+        lo, hi = np.minimum(g0, g1), np.maximum(g0, g1)
+        k_hi = np.where(g1 > g0, k1[None, :], k0[None, :])            # index at the larger vertex
+        keys = np.stack([lo.ravel(), hi.ravel(), k_hi.ravel()], 1)
+        uk, einv = np.unique(keys, axis=0, return_inverse=True)
+        conn[:, ea] = base + einv.reshape(E, len(ea))
+        xe = (vx[uk[:, 0]] * (p - uk[:, 2:3]) + vx[uk[:, 1]] * uk[:, 2:3]) / p
+        coords_parts.append(xe)
+        base += len(uk)
+    # face nodes (p = 3: barycentric (1, 1, 1, 0) patterns)
+    fa = np.where(kind == 3)[0]
+    if len(fa):
+        tri = np.array([np.where(nz[a])[0] for a in fa])
+        keys = np.sort(np.stack([simp[:, tri[:, 0]], simp[:, tri[:, 1]], simp[:, tri[:, 2]]], 2), axis=2)
+        uk, finv = np.unique(keys.reshape(-1, 3), axis=0, return_inverse=True)
+        conn[:, fa] = base + finv.reshape(E, len(fa))
+        coords_parts.append(vx[uk].mean(1))
+        base += len(uk)
+    coords = np.concatenate(coords_parts, 0)
+    return TetMesh(coords=np.ascontiguousarray(coords), conn=np.ascontiguousarray(conn.astype(np.int32)), order=p,
+                   rng=rng)
+
+
+def mixed_mesh_groups(scale: float = 1.0, seed: int = 2):
+    """The mixed-element workload: P1, P2, P3 tetrahedra (200k, 120k, 40k,
+    Delaunay meshes drawn from one stream of seed `seed` in that order) and Q1,
+    Q2, Q3 hexahedra (60k = 50x40x30, 30k = 40x30x25, 8k = 20x20x20, +-0.1h,
+    seeds seed + 10 + p); `scale` < 1 shrinks every group (tests).  Returns a
+    list of (name, mesh) in that order; each mesh carries its generator for the
+    materials."""
+    rng = np.random.default_rng(seed)
+    groups = []
+    for p, target in ((1, 200_000), (2, 120_000), (3, 40_000)):
+        groups.append(("P%d" % p, tet_mesh(max(8, int(round(target * scale))), p, rng)))
+    for p, shape in ((1, (50, 40, 30)), (2, (40, 30, 25)), (3, (20, 20, 20))):
+        f = scale ** (1.0 / 3.0)
+        sh = tuple(max(1, int(round(n * f))) for n in shape)
+        groups.append(("Q%d" % p, structured_hex(*sh, p, 0.1, seed + 10 + p)))
+    return groups

@@ -1,0 +1,78 @@
+"""GPU parity on tetrahedral meshes (P1-P3, Grundmann-Moller rules of index p):
+geometry, matrix and residual modes of the Tab. ewfd forms against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_04121_gb300 import fe, meshgen
+from tests.parity import TOL, rel_matrix_error, rel_vector_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(libfe):
+    c = fe.Context(0)
+    yield c
+    c.close()
+
+
+def _t(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+# element counts leave a ragged last CTA for every tile configuration
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["laplace", "mass", "elasticity"])
+@pytest.mark.parametrize("p,E", [(1, 301), (2, 157), (3, 83)])
+def test_tet_matrix_and_residual_match_oracle(ctx, p, E, kind, prec):
+    mesh = meshgen.tet_mesh(E, p, np.random.default_rng(80 + p))
+    ref = oracle.RefTet(p, p)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    rng = np.random.default_rng(81)
+    m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+    geom = fe.tet_geometry(ctx, m, p)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    if kind == "laplace":
+        coef = rng.uniform(0.5, 2.0, E)
+        form = fe.laplace_form(weighted=True)
+        mat, nc = coef, 1
+        Kref = oracle.matrix_laplace(wdetJ, G, coef)
+        u = rng.standard_normal(mesh.n_nodes)
+        rref = oracle.residual_laplace(mesh.conn, wdetJ, G, u, coef)
+    elif kind == "mass":
+        coef = rng.uniform(0.5, 2.0, E)
+        form = fe.mass_form(1, weighted=True)
+        mat, nc = coef, 1
+        Kref = oracle.matrix_mass(wdetJ, ref.phi, 1, coef)
+        u = rng.standard_normal(mesh.n_nodes)
+        rref = oracle.residual_mass(mesh.conn, wdetJ, ref.phi, u, 1, coef)
+    else:
+        lam, mu = meshgen.lame_materials(mesh)
+        form = fe.elasticity_form(fe.MAT_LAME)
+        mat, nc = np.stack([lam, mu], 1), 3
+        D = oracle.lame_to_D(lam, mu)
+        Kref = oracle.matrix_elasticity(wdetJ, G, D)
+        u = rng.standard_normal(3 * mesh.n_nodes)
+        rref = oracle.residual_elasticity(mesh.conn, wdetJ, G, D, u)
+    args = [_t(mat, torch.float64), None, _t(u, dt)]
+    K = fe.eval_matrix(ctx, form, geom, args, prec)
+    r = fe.eval_residual(ctx, form, geom, args, prec)
+    wd = geom.get(fe.GEOM_WDETJ, prec)
+    ctx.check()
+    assert rel_vector_error(wd.cpu().numpy(), wdetJ) <= TOL[prec]
+    assert rel_matrix_error(K.cpu().numpy(), Kref) <= TOL[prec]
+    assert rel_vector_error(r.cpu().numpy(), rref) <= TOL[prec]
+
+
+def test_tet_refbasis_matches_oracle(libfe):
+    for p in (1, 2, 3):
+        for s in (0, 1, 2, 3, 4):
+            pts, w, phi, dphi = fe.refbasis_tet(p, s)
+            opts, ow = oracle.gm_rule(s)
+            ophi, odphi = oracle.tet_basis(p, opts)
+            np.testing.assert_allclose(pts, opts, atol=1e-15)
+            np.testing.assert_allclose(w, ow, rtol=1e-13, atol=1e-16)
+            np.testing.assert_allclose(phi, ophi, atol=1e-13)
+            np.testing.assert_allclose(dphi, odphi, atol=1e-12)

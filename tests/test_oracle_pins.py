@@ -637,3 +637,41 @@ def test_higher_order_tet_invariants(p):
             a, b = [(0, 1), (1, 2), (0, 2)][mode - 3]
             v[a], v[b] = -X[:, b], X[:, a]
         assert np.abs(KE @ v.reshape(-1)).max() <= 1e-12 * np.abs(KE).max()
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_tet_mesh_patch_test(p):
+    """On the conforming Delaunay mesh the assembled Laplace residual of a linear
+    field vanishes at every node off the mesh boundary (the P_p space holds
+    linear fields and the rule of index p integrates the products exactly)."""
+    mesh = meshgen.tet_mesh(600, p, np.random.default_rng(5))
+    ref = oracle.RefTet(p, p)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    u = mesh.coords @ np.array([0.7, -1.3, 0.4]) + 0.2
+    r = oracle.residual_laplace(mesh.conn, wdetJ, G, u)
+    R = oracle.assemble(mesh.conn, r, mesh.n_nodes, 1)
+    X = mesh.coords
+    # boundary of the triangulated domain (the points' convex hull): faces of one
+    # tet only; every node on such a face (its barycentric index at the opposite
+    # vertex is 0) is a boundary node
+    L = np.array([(p - i - j - k, i, j, k) for k in range(p + 1) for j in range(p + 1 - k)
+                  for i in range(p + 1 - k - j)])
+    vert = [int(np.argmax(L[:, m])) for m in range(4)]        # local vertex nodes
+    faces = {}
+    for e, c in enumerate(mesh.conn):
+        for m in range(4):
+            key = tuple(sorted(c[vert[o]] for o in range(4) if o != m))
+            faces.setdefault(key, []).append((e, m))
+    inside = np.ones(mesh.n_nodes, dtype=bool)
+    for lst in faces.values():
+        if len(lst) == 1:
+            e, m = lst[0]
+            inside[mesh.conn[e][L[:, m] == 0]] = False
+    assert inside.sum() > 10
+    # zero up to the rounding of the summed terms K_ab u_b (slivers of a Delaunay
+    # mesh give large entries that cancel)
+    K = oracle.matrix_laplace(wdetJ, G)
+    scale = (np.abs(K) * np.abs(u[mesh.conn])[:, None, :]).sum(2).max()
+    assert np.abs(R[inside]).max() <= 1e-13 * scale
+    vol = sum(abs(np.linalg.det(X[c[vert[1:]]] - X[c[vert[0]]])) / 6 for c in mesh.conn)
+    assert abs(wdetJ.sum() - vol) <= 1e-12
