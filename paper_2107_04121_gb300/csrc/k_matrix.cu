@@ -129,6 +129,13 @@ __device__ __forceinline__ void bulk_wait_read()
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Quadrature rules of the supported (N, Q) pairs: Gauss (hexahedra, positive
+// weights) or Grundmann-Moller of index >= 1 (tetrahedra, negative weights).
+__host__ __device__ constexpr bool rule_weights_positive(int N, int Q)
+{
+    return !((N == 4 && Q == 5) || (N == 10 && Q == 15) || (N == 20 && Q == 35));
+}
+
 // Shared-memory plan of one CTA (sizes in elements of S).
 template <typename S, int N, int Q, int KIND, int T, int EPB, int STAGE>
 struct MatrixSmem {
@@ -163,6 +170,10 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
     using P = MatrixSmem<S, N, Q, KIND, T, EPB, STAGE>;
     constexpr bool GRAD = P::GRAD;
     constexpr int TP = P::TP, NP = P::NP, NT = N / T, NU = NT * (NT + 1) / 2;
+    // Gauss rules (hexahedra) have positive weights: both Gram operands carry
+    // sqrt(w det J).  Grundmann-Moller rules (the tetrahedron pairs) have negative
+    // weights: the gradients stay unscaled and one operand takes w det J.
+    constexpr bool SQW = rule_weights_positive(N, Q);
     constexpr int NDIR = KIND == FK_ELASTICITY ? 3 : 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S *sm = reinterpret_cast<S *>(smem_raw);
@@ -206,10 +217,10 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
         if constexpr (GRAD) {
             // scaled physical gradients sqrt(w det J) G[el][q][j][a], G = J^-T grad_xi phi,
             // padded node index; the Gram blocks then need no weight in the inner loop
-            // (w det J > 0 is checked by the geometry kernel)
+            // (det J > 0 is checked by the geometry kernel; Gauss weights are positive)
             for (int i = threadIdx.x; i < ne * Q; i += THREADS) {
                 const int el = i / Q, q = i % Q;
-                const S sw = sqrt(sW[i]);
+                const S sw = SQW ? sqrt(sW[i]) : (S)1;
                 S Ji[9];
 #pragma unroll
                 for (int t = 0; t < 9; ++t) Ji[t] = sw * sJ[i * 9 + t];
@@ -259,18 +270,21 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
                         S va[T], vb[T];
                         TileVec<S, T>::load(Gq + j * NP + ta * TP, va);
                         TileVec<S, T>::load(Gq + j * NP + tb * TP, vb);
+                        if constexpr (!SQW)
+#pragma unroll
+                            for (int x = 0; x < T; ++x) va[x] *= Wq[q];
 #pragma unroll
                         for (int x = 0; x < T; ++x)
 #pragma unroll
                             for (int y = 0; y < T; ++y) acc[0][0][x][y] = fma(va[x], vb[y], acc[0][0][x][y]);
                     }
                 } else {
-                    const S wq = GRAD ? (S)1 : Wq[q];
+                    const S wq = GRAD && SQW ? (S)1 : Wq[q];
 #pragma unroll
                     for (int j = 0; j < NDIR; ++j) {
                         TileVec<S, T>::load(Gq + j * NP + ta * TP, ga[j]);
                         TileVec<S, T>::load(Gq + j * NP + tb * TP, gb[j]);
-                        if constexpr (!GRAD)
+                        if constexpr (!GRAD || !SQW)
 #pragma unroll
                             for (int x = 0; x < T; ++x) ga[j][x] *= wq;
                     }

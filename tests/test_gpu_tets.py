@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2107_04121_gb300 import fe, meshgen
-from tests.parity import TOL, rel_matrix_error, rel_vector_error
+from tests.parity import TOL, rel_vector_error
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -34,36 +34,52 @@ def test_tet_matrix_and_residual_match_oracle(ctx, p, E, kind, prec):
     m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
     geom = fe.tet_geometry(ctx, m, p)
     dt = torch.float64 if prec == "f64" else torch.float32
+    aw, aG, aphi = np.abs(wdetJ), np.abs(G), np.abs(ref.phi)
     if kind == "laplace":
         coef = rng.uniform(0.5, 2.0, E)
         form = fe.laplace_form(weighted=True)
         mat, nc = coef, 1
         Kref = oracle.matrix_laplace(wdetJ, G, coef)
+        Kabs = oracle.matrix_laplace(aw, aG, coef)
         u = rng.standard_normal(mesh.n_nodes)
         rref = oracle.residual_laplace(mesh.conn, wdetJ, G, u, coef)
+        rabs = oracle.residual_laplace(mesh.conn, aw, aG, np.abs(u), coef)
     elif kind == "mass":
         coef = rng.uniform(0.5, 2.0, E)
         form = fe.mass_form(1, weighted=True)
         mat, nc = coef, 1
         Kref = oracle.matrix_mass(wdetJ, ref.phi, 1, coef)
+        Kabs = oracle.matrix_mass(aw, aphi, 1, coef)
         u = rng.standard_normal(mesh.n_nodes)
         rref = oracle.residual_mass(mesh.conn, wdetJ, ref.phi, u, 1, coef)
+        rabs = oracle.residual_mass(mesh.conn, aw, aphi, np.abs(u), 1, coef)
     else:
         lam, mu = meshgen.lame_materials(mesh)
         form = fe.elasticity_form(fe.MAT_LAME)
         mat, nc = np.stack([lam, mu], 1), 3
         D = oracle.lame_to_D(lam, mu)
         Kref = oracle.matrix_elasticity(wdetJ, G, D)
+        Kabs = oracle.matrix_elasticity(aw, aG, np.abs(D))
         u = rng.standard_normal(3 * mesh.n_nodes)
         rref = oracle.residual_elasticity(mesh.conn, wdetJ, G, D, u)
+        rabs = oracle.residual_elasticity(mesh.conn, aw, aG, np.abs(D), np.abs(u))
+    # Grundmann-Moller weights alternate in sign and P3 basis products change
+    # sign, so element entries can be much smaller than the terms summed into
+    # them: errors are measured against the sums of absolute terms (the same
+    # forms of |w det J|, |phi|, |G|, |D|, |u|), the scale two summation orders
+    # of the same terms differ on
+    tol = TOL[prec]
     args = [_t(mat, torch.float64), None, _t(u, dt)]
     K = fe.eval_matrix(ctx, form, geom, args, prec)
     r = fe.eval_residual(ctx, form, geom, args, prec)
     wd = geom.get(fe.GEOM_WDETJ, prec)
     ctx.check()
     assert rel_vector_error(wd.cpu().numpy(), wdetJ) <= TOL[prec]
-    assert rel_matrix_error(K.cpu().numpy(), Kref) <= TOL[prec]
-    assert rel_vector_error(r.cpu().numpy(), rref) <= TOL[prec]
+    Kg = K.cpu().numpy().astype(np.float64)
+    ek = float((np.sqrt(((Kg - Kref) ** 2).sum((1, 2))) / np.sqrt((Kabs ** 2).sum((1, 2)))).max())
+    er = float(np.linalg.norm(r.cpu().numpy() - rref) / np.linalg.norm(rabs))
+    assert ek <= tol, ek
+    assert er <= tol, er
 
 
 def test_tet_refbasis_matches_oracle(libfe):
