@@ -134,6 +134,7 @@ typedef struct fe_ctx fe_ctx;
 typedef struct fe_geometry_h fe_geometry_h;
 typedef struct fe_form_h fe_form_h;
 typedef struct fe_assembly_h fe_assembly_h;
+typedef struct fe_batch_h fe_batch_h;
 
 /* ---- context ------------------------------------------------------------- */
 
@@ -309,6 +310,48 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
 fe_status fe_eval_residual_adjoint(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom,
                                    const void *const *args, const void *rbar, fe_precision prec, void *d_mat,
                                    void *d_x_e, fe_stream_t stream);
+
+/* ---- batched matrix mode ---------------------------------------------------------- */
+
+/* One item of a batch: the element matrices of `form` on the elements of
+ * `geom`, written to K_out (n_elems, n_rows, n_cols) float32.  material is the
+ * form's float64 material array (NULL when the form has none).  The arrays are
+ * borrowed: they must stay allocated while the batch is used. */
+typedef struct {
+    const fe_geometry_h *geom;
+    const fe_form_h *form;
+    const void *material;
+    void *K_out;
+} fe_batch_item;
+
+#define FE_BATCH_GEOMETRY 1u /* every run recomputes the geometry of each item's handle first */
+#define FE_BATCH_AUTOTUNE 2u /* time every candidate configuration at creation, keep the fastest */
+#define FE_BATCH_GRAPH 4u    /* capture the run (geometry and matrices) in a CUDA graph at creation */
+
+/* A batch evaluates matrix mode (Algorithm 2) for many items, e.g. the groups
+ * of a mixed mesh of P1-P3 tetrahedra and Q1-Q3 hexahedra with the Laplace,
+ * mass and elasticity forms, in ONE persistent kernel launch: the items'
+ * elements are cut into chunks and resident CTAs stride over the combined
+ * work list.  Every (element, form) pair has candidate configurations (node
+ * tile, elements per chunk, output staging); FE_BATCH_AUTOTUNE times each on
+ * the item's own elements (writing its K_out) and keeps the fastest, otherwise
+ * the first is used.  FE_F32 arithmetic from the FP32 copy of the FP64
+ * geometry, so every geometry must store FE_GEOM_STORE_F32.  Supported: the
+ * weighted Laplacian, the (vector) mass and Lame elasticity on the (N, Q)
+ * pairs of fe_geometry.  The paper has no batched evaluator (it evaluates one
+ * form on one element type at a time, Sec. 5.2); this is the GPU-resident
+ * counterpart of looping over its calls.  The call synchronizes `stream`.
+ * Errors: FE_ERR_INVALID_ARG, FE_ERR_UNSUPPORTED_SPEC (a form or element
+ * without a batch configuration), FE_ERR_OOM, FE_ERR_CUDA. */
+fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, unsigned flags, fe_batch_h **out,
+                          fe_stream_t stream);
+/* Run the batch on `stream` (one graph launch with FE_BATCH_GRAPH, otherwise
+ * the geometry launches and one persistent kernel launch). */
+fe_status fe_batch_run(fe_ctx *ctx, fe_batch_h *batch, fe_stream_t stream);
+/* The configuration chosen for item `item`: node tile, elements per chunk,
+ * staging (1: bulk-copied row blocks, 0: direct stores); any may be NULL. */
+fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *elems_per_chunk, int *staging);
+fe_status fe_batch_free(fe_batch_h *batch);
 
 /* ---- assembly ------------------------------------------------------------------- */
 

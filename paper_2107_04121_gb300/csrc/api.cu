@@ -21,6 +21,11 @@ static cudaError_t settle_geometry(fe_geometry_h *g, unsigned long long *status,
     return fe_launch_geometry(g, status, s);
 }
 
+cudaError_t fe_settle_geometry(fe_geometry_h *g, unsigned long long *status, cudaStream_t s)
+{
+    return settle_geometry(g, status, s);
+}
+
 namespace {
 
 thread_local char g_last_error[256] = "";
@@ -70,6 +75,8 @@ void free_geometry(fe_geometry_h *g)
 }
 
 }  // namespace
+
+fe_status fe_status_from_cuda(cudaError_t e, const char *where) { return from_cuda(e, where); }
 
 extern "C" {
 

@@ -93,6 +93,11 @@ cudaError_t fe_noalloc_limits(long long n_nodes, long long n_incidences);
 cudaError_t fe_launch_assemble_noalloc(int device, const fe_mesh *mesh, int ncomp, bool f64, const void *r,
                                        void *out, unsigned flags, unsigned long long *status, cudaStream_t s);
 
+// Status of a CUDA error, recorded as the thread's last error message (api.cu).
+fe_status fe_status_from_cuda(cudaError_t e, const char *where);
+// Settle a deferred geometry (api.cu): compute it now if it is stale.
+cudaError_t fe_settle_geometry(fe_geometry_h *g, unsigned long long *status, cudaStream_t s);
+
 // Which (N, Q) pairs have kernels.
 bool fe_supported_nq(int N, int Q);
 

@@ -1,0 +1,445 @@
+// Batched matrix mode: element matrices of several (form, element group)
+// items, e.g. a mixed mesh of P1-P3 tetrahedra and Q1-Q3 hexahedra with the
+// Laplace, mass and elasticity forms of Tab. ewfd (Cimrman, arXiv 2107.04121),
+// in ONE persistent launch.
+//
+// Every item is cut into chunks of EPB consecutive elements; the chunks of all
+// items form one work list (item i owns chunks [chunk0_i, chunk0_i + ceil(E_i /
+// EPB_i))).  Resident CTAs (a few per SM, 256 threads each) stride over the
+// list; each chunk runs the per-element-group body of the SIMT matrix kernel
+// (matrix_body.cuh) instantiated for its item's variant: (N, Q) pair, form,
+// node tile T, elements per chunk EPB and output staging (bulk row blocks or
+// direct stores).  A CTA reloads the reference gradients only when its item
+// changes.
+//
+// Variants per (form, element) are candidates of an autotuner: at plan
+// creation each candidate is timed on the item's own elements and the fastest
+// is kept.  A plan can also be captured in a CUDA graph together with the
+// geometry of every group (FP64 J, det J, J^-1), so that one graph launch
+// evaluates the whole batch.  FP32 element matrices from FP64 geometry.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "matrix_body.cuh"
+
+namespace {
+
+constexpr int BT = 256;  // threads of the batched kernel
+
+// id, N, Q, form, material kind (0 scalar / 1 Lame), tile T, elements per chunk, staging
+#define FE_BATCH_VARIANTS(X)                                   \
+    X(0, 4, 5, FK_LAPLACE, 0, 2, 85, STAGE_BULK)               \
+    X(1, 4, 5, FK_LAPLACE, 0, 2, 42, STAGE_BULK)               \
+    X(2, 4, 5, FK_MASS, 0, 2, 85, STAGE_BULK)                  \
+    X(3, 4, 5, FK_MASS, 0, 2, 42, STAGE_BULK)                  \
+    X(4, 4, 5, FK_ELASTICITY, 1, 2, 85, STAGE_BULK)            \
+    X(5, 4, 5, FK_ELASTICITY, 1, 2, 42, STAGE_BULK)            \
+    X(6, 10, 15, FK_LAPLACE, 0, 2, 17, STAGE_BULK)             \
+    X(7, 10, 15, FK_LAPLACE, 0, 2, 8, STAGE_BULK)              \
+    X(8, 10, 15, FK_MASS, 0, 2, 17, STAGE_BULK)                \
+    X(9, 10, 15, FK_MASS, 0, 2, 8, STAGE_BULK)                 \
+    X(10, 10, 15, FK_ELASTICITY, 1, 2, 17, STAGE_BULK)         \
+    X(11, 10, 15, FK_ELASTICITY, 1, 2, 8, STAGE_BULK)          \
+    X(12, 20, 35, FK_LAPLACE, 0, 4, 8, STAGE_BULK)             \
+    X(13, 20, 35, FK_LAPLACE, 0, 2, 4, STAGE_BULK)             \
+    X(14, 20, 35, FK_MASS, 0, 4, 8, STAGE_BULK)                \
+    X(15, 20, 35, FK_MASS, 0, 2, 4, STAGE_BULK)                \
+    X(16, 20, 35, FK_ELASTICITY, 1, 2, 4, STAGE_BULK)          \
+    X(17, 20, 35, FK_ELASTICITY, 1, 2, 2, STAGE_BULK)          \
+    X(18, 8, 8, FK_LAPLACE, 0, 2, 25, STAGE_BULK)              \
+    X(19, 8, 8, FK_LAPLACE, 0, 2, 12, STAGE_BULK)              \
+    X(20, 8, 8, FK_MASS, 0, 2, 25, STAGE_BULK)                 \
+    X(21, 8, 8, FK_MASS, 0, 2, 12, STAGE_BULK)                 \
+    X(22, 8, 8, FK_ELASTICITY, 1, 2, 25, STAGE_BULK)           \
+    X(23, 8, 8, FK_ELASTICITY, 1, 2, 12, STAGE_BULK)           \
+    X(24, 27, 27, FK_LAPLACE, 0, 3, 5, STAGE_BULK)             \
+    X(25, 27, 27, FK_LAPLACE, 0, 3, 2, STAGE_BULK)             \
+    X(26, 27, 27, FK_MASS, 0, 3, 5, STAGE_BULK)                \
+    X(27, 27, 27, FK_MASS, 0, 3, 2, STAGE_BULK)                \
+    X(28, 27, 27, FK_ELASTICITY, 1, 3, 5, STAGE_BULK)          \
+    X(29, 27, 27, FK_ELASTICITY, 1, 3, 2, STAGE_BULK)          \
+    X(30, 64, 64, FK_LAPLACE, 0, 4, 1, STAGE_BULK)             \
+    X(31, 64, 64, FK_LAPLACE, 0, 2, 1, STAGE_DIRECT)           \
+    X(32, 64, 64, FK_MASS, 0, 4, 1, STAGE_BULK)                \
+    X(33, 64, 64, FK_MASS, 0, 2, 1, STAGE_DIRECT)              \
+    X(34, 64, 64, FK_ELASTICITY, 1, 2, 1, STAGE_DIRECT)
+
+struct Variant {
+    int N, Q, kind, matk, tile, epb, stage;
+    size_t smem;
+};
+
+#define FE_BATCH_INFO(ID, N, Q, KIND, MATK, T, EPB, STAGE) \
+    {N, Q, KIND, MATK, T, EPB, STAGE, MatrixSmem<float, N, Q, KIND, T, EPB, STAGE>::BYTES},
+const Variant kVariants[] = {FE_BATCH_VARIANTS(FE_BATCH_INFO)};
+#undef FE_BATCH_INFO
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+
+#define FE_BATCH_CHECK(ID, N, Q, KIND, MATK, T, EPB, STAGE)                                                      \
+    static_assert(STAGE == STAGE_DIRECT || EPB * (N / T) * (N / T + 1) / 2 <= BT, "one tile per thread");      \
+    static_assert(MatrixSmem<float, N, Q, KIND, T, EPB, STAGE>::BYTES <= 113 * 1024, "two CTAs per SM");
+FE_BATCH_VARIANTS(FE_BATCH_CHECK)
+#undef FE_BATCH_CHECK
+
+constexpr size_t kMaxSmem = 113 * 1024;
+
+struct BatchItemDev {
+    const float *jinv, *wdetj, *dphi, *phi;
+    const double *mat;
+    float *K;
+    long long E;
+    long long chunk0;  // first chunk of this item in the work list
+    int variant, ncomp, mat_t, pad;
+};
+
+__global__ void __launch_bounds__(BT, 2) k_batch(const BatchItemDev *__restrict__ items, int n_items,
+                                                 long long n_chunks)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_item;
+    int loaded = -1;  // item whose reference gradients are in shared memory
+    for (long long c = blockIdx.x; c < n_chunks; c += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = n_items - 1;  // last item with chunk0 <= c
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (items[mid].chunk0 <= c) lo = mid;
+                else hi = mid - 1;
+            }
+            s_item = lo;
+        }
+        __syncthreads();
+        const int i = s_item;
+        const BatchItemDev it = items[i];
+        const long long local = c - it.chunk0;
+        if (i != loaded) {
+            // another variant's plan may alias this one: earlier bulk copies must
+            // have finished reading shared memory before it is rewritten
+            if (threadIdx.x == 0) bulk_wait_read<0>();
+            __syncthreads();
+        }
+        switch (it.variant) {
+#define FE_BATCH_CASE(ID, N, Q, KIND, MATK, T, EPB, STAGE)                                                       \
+    case ID: {                                                                                                  \
+        if (i != loaded) matrix_load_ref<float, N, Q, KIND, T, EPB, BT, STAGE>(it.dphi, smem_raw);              \
+        const long long e0 = local * EPB;                                                                       \
+        const int ne = (int)(it.E - e0 < EPB ? it.E - e0 : EPB);                                                 \
+        matrix_group<float, N, Q, KIND, MATK, T, EPB, BT, STAGE>(it.jinv, it.wdetj, it.phi, e0, ne, it.ncomp,   \
+                                                                 it.mat, it.mat_t, it.K, smem_raw);             \
+        break;                                                                                                  \
+    }
+            FE_BATCH_VARIANTS(FE_BATCH_CASE)
+#undef FE_BATCH_CASE
+        default: break;
+        }
+        loaded = i;
+        __syncthreads();  // every thread has read s_item before it is rewritten
+    }
+    if (threadIdx.x == 0) bulk_wait_read<0>();  // shared memory must outlive the copies' reads
+}
+
+// Launch shape: the largest shared-memory plan of the batch decides residency.
+cudaError_t batch_grid(size_t smem, long long *grid)
+{
+    static FeLaunchCache cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    long long set = 0;
+    e = fe_cached_grid(
+        cache,
+        [&](int, long long *v) {
+            *v = 1;
+            return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        },
+        &set);
+    if (e != cudaSuccess) return e;
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BT, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *grid = (long long)per_sm * sms;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+struct fe_batch_h {
+    int device;
+    int n_items;
+    unsigned flags;
+    unsigned long long *d_status;
+    std::vector<BatchItemDev> items;        // host copy (chunk0 filled)
+    std::vector<fe_geometry_h *> geoms;     // distinct geometries recomputed by the batch
+    BatchItemDev *d_items = nullptr;
+    long long n_chunks = 0;
+    size_t smem = 0;
+    long long grid = 0;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+cudaError_t enqueue(fe_batch_h *b, cudaStream_t s)
+{
+    cudaError_t e = cudaSuccess;
+    if (b->flags & FE_BATCH_GEOMETRY)
+        for (fe_geometry_h *g : b->geoms) {
+            g->pending = 0;
+            e = fe_launch_geometry(g, b->d_status, s);
+            if (e != cudaSuccess) return e;
+        }
+    if (b->n_chunks > 0) {
+        const long long grid = b->grid < b->n_chunks ? b->grid : b->n_chunks;
+        k_batch<<<(unsigned)grid, BT, b->smem, s>>>(b->d_items, b->n_items, b->n_chunks);
+        e = cudaGetLastError();
+    }
+    return e;
+}
+
+// Candidate variants of an item: same element pair, form and material kind.
+std::vector<int> candidates(int N, int Q, int kind, int matk)
+{
+    std::vector<int> v;
+    for (int id = 0; id < kNumVariants; ++id) {
+        const Variant &x = kVariants[id];
+        if (x.N == N && x.Q == Q && x.kind == kind && x.matk == matk) v.push_back(id);
+    }
+    return v;
+}
+
+// Median of `reps` timed runs of one item alone with variant `id`.
+cudaError_t time_variant(BatchItemDev it, int id, BatchItemDev *d_tmp, cudaStream_t s, float *ms)
+{
+    it.variant = id;
+    it.chunk0 = 0;
+    const long long chunks = (it.E + kVariants[id].epb - 1) / kVariants[id].epb;
+    long long grid = 0;
+    cudaError_t e = batch_grid(kVariants[id].smem, &grid);
+    if (e != cudaSuccess) return e;
+    if (grid > chunks) grid = chunks;
+    e = cudaMemcpyAsync(d_tmp, &it, sizeof(it), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float t[5];
+    for (int r = 0; r < 6; ++r) {
+        cudaEventRecord(a, s);
+        k_batch<<<(unsigned)grid, BT, kVariants[id].smem, s>>>(d_tmp, 1, chunks);
+        cudaEventRecord(b, s);
+        e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) break;
+        if (r > 0) cudaEventElapsedTime(&t[r - 1], a, b);  // the first run warms up
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return e;
+    for (int i = 1; i < 5; ++i)
+        for (int j = i; j > 0 && t[j] < t[j - 1]; --j) {
+            const float x = t[j];
+            t[j] = t[j - 1];
+            t[j - 1] = x;
+        }
+    *ms = t[2];
+    return cudaSuccess;
+}
+
+void free_plan(fe_batch_h *b)
+{
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    if (b->d_items) cudaFree(b->d_items);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, unsigned flags, fe_batch_h **out,
+                          fe_stream_t stream)
+{
+    if (!ctx || !out || n_items < 1 || !items) return FE_ERR_INVALID_ARG;
+    if (flags & ~(FE_BATCH_GEOMETRY | FE_BATCH_AUTOTUNE | FE_BATCH_GRAPH)) return FE_ERR_INVALID_ARG;
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    fe_batch_h *b = new (std::nothrow) fe_batch_h();
+    if (!b) return FE_ERR_OOM;
+    b->device = ctx->device;
+    b->n_items = n_items;
+    b->flags = flags;
+    b->d_status = ctx->d_status;
+    // validate and describe the items
+    std::vector<std::vector<int>> cand(n_items);
+    for (int i = 0; i < n_items; ++i) {
+        const fe_batch_item &x = items[i];
+        const fe_geometry_h *g = x.geom;
+        const fe_form_h *f = x.form;
+        if (!g || !f || g->device != ctx->device) {
+            free_plan(b);
+            return FE_ERR_INVALID_ARG;
+        }
+        if (g->mesh.n_elems > 0 && !x.K_out) {
+            free_plan(b);
+            return FE_ERR_INVALID_ARG;
+        }
+        if (!g->d_jinv32) {  // the batch evaluates FP32 matrices from the FP32 copy of the geometry
+            free_plan(b);
+            return FE_ERR_INVALID_ARG;
+        }
+        int matk;
+        if (f->kind == FK_LAPLACE || f->kind == FK_MASS) {
+            matk = 0;
+        } else if (f->kind == FK_ELASTICITY && f->mat == FE_MAT_LAME && !f->mat_transposed) {
+            matk = 1;
+        } else {
+            free_plan(b);
+            return FE_ERR_UNSUPPORTED_SPEC;
+        }
+        if (f->mat_op >= 0 && !x.material && g->mesh.n_elems > 0) {
+            free_plan(b);
+            return FE_ERR_INVALID_ARG;
+        }
+        cand[i] = candidates(g->N, g->Q, f->kind, matk);
+        if (cand[i].empty()) {
+            free_plan(b);
+            return FE_ERR_UNSUPPORTED_SPEC;
+        }
+        BatchItemDev it{};
+        it.jinv = g->d_jinv32;
+        it.wdetj = g->d_wdetj32;
+        it.dphi = g->d_dphi32;
+        it.phi = g->d_phi32;
+        it.mat = f->mat_op >= 0 ? (const double *)x.material : nullptr;
+        it.K = (float *)x.K_out;
+        it.E = g->mesh.n_elems;
+        it.variant = cand[i][0];
+        it.ncomp = f->ncomp;
+        it.mat_t = f->mat_transposed;
+        b->items.push_back(it);
+        fe_geometry_h *gm = const_cast<fe_geometry_h *>(g);
+        bool seen = false;
+        for (fe_geometry_h *h : b->geoms) seen = seen || h == gm;
+        if (!seen) b->geoms.push_back(gm);
+    }
+    cudaError_t e = cudaMalloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n_items);
+    // geometry first (stale deferred handles, and the batch's own recomputation)
+    for (fe_geometry_h *g : b->geoms)
+        if (e == cudaSuccess) e = fe_settle_geometry(g, ctx->d_status, s);
+    // autotune: time every candidate on each item alone, items of the same
+    // (element, form, components) share the result
+    if (e == cudaSuccess && (flags & FE_BATCH_AUTOTUNE)) {
+        struct Key {
+            int N, Q, kind, ncomp, variant;
+        };
+        std::vector<Key> done;
+        for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
+            BatchItemDev &it = b->items[i];
+            if (it.E == 0 || cand[i].size() < 2) continue;
+            const fe_geometry_h *g = items[i].geom;
+            int found = -1;
+            for (const Key &k : done)
+                if (k.N == g->N && k.Q == g->Q && k.kind == items[i].form->kind && k.ncomp == it.ncomp)
+                    found = k.variant;
+            if (found >= 0) {
+                it.variant = found;
+                continue;
+            }
+            float best = 0.f;
+            int best_id = cand[i][0];
+            for (size_t c = 0; c < cand[i].size() && e == cudaSuccess; ++c) {
+                float ms = 0.f;
+                e = time_variant(it, cand[i][c], b->d_items, s, &ms);
+                if (e == cudaSuccess && (c == 0 || ms < best)) {
+                    best = ms;
+                    best_id = cand[i][c];
+                }
+            }
+            it.variant = best_id;
+            done.push_back({g->N, g->Q, items[i].form->kind, it.ncomp, best_id});
+        }
+    }
+    // work list
+    long long chunk = 0;
+    size_t smem = 0;
+    for (BatchItemDev &it : b->items) {
+        it.chunk0 = chunk;
+        chunk += (it.E + kVariants[it.variant].epb - 1) / kVariants[it.variant].epb;
+        if (it.E > 0 && kVariants[it.variant].smem > smem) smem = kVariants[it.variant].smem;
+    }
+    b->n_chunks = chunk;
+    b->smem = smem;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(BatchItemDev) * (size_t)n_items,
+                            cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = batch_grid(smem > 0 ? smem : 1024, &b->grid);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // CUDA graph of the whole batch, captured on a private stream
+    if (e == cudaSuccess && (flags & FE_BATCH_GRAPH)) {
+        e = enqueue(b, s);  // one eager run: first-launch attributes are set outside the capture
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            const cudaError_t e1 = enqueue(b, b->capture_stream);
+            const cudaError_t e2 = cudaStreamEndCapture(b->capture_stream, &b->graph);
+            e = e1 != cudaSuccess ? e1 : e2;
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    }
+    if (e != cudaSuccess) {
+        fe_status st = fe_status_from_cuda(e, "fe_batch_create");
+        free_plan(b);
+        return st;
+    }
+    *out = b;
+    return FE_OK;
+}
+
+fe_status fe_batch_run(fe_ctx *ctx, fe_batch_h *batch, fe_stream_t stream)
+{
+    if (!ctx || !batch || batch->device != ctx->device) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    if (batch->exec) {
+        for (fe_geometry_h *g : batch->geoms) g->pending = 0;
+        e = cudaGraphLaunch(batch->exec, s);
+    } else {
+        e = cudaSuccess;
+        if (!(batch->flags & FE_BATCH_GEOMETRY))
+            for (fe_geometry_h *g : batch->geoms)
+                if (e == cudaSuccess) e = fe_settle_geometry(g, batch->d_status, s);
+        if (e == cudaSuccess) e = enqueue(batch, s);
+    }
+    return fe_status_from_cuda(e, "fe_batch_run");
+}
+
+fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *elems_per_chunk, int *staging)
+{
+    if (!batch || item < 0 || item >= batch->n_items) return FE_ERR_INVALID_ARG;
+    const Variant &v = kVariants[batch->items[item].variant];
+    if (tile) *tile = v.tile;
+    if (elems_per_chunk) *elems_per_chunk = v.epb;
+    if (staging) *staging = v.stage == STAGE_BULK ? 1 : 0;
+    return FE_OK;
+}
+
+fe_status fe_batch_free(fe_batch_h *batch)
+{
+    if (!batch) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(batch->device);
+    free_plan(batch);
+    return FE_OK;
+}
+
+}  // extern "C"

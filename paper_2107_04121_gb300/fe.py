@@ -28,13 +28,15 @@ MAT_NONE, MAT_SCALAR, MAT_LAME, MAT_D66 = 0, 1, 2, 3
 GEOM_STORE_F64, GEOM_STORE_F32, GEOM_DEFERRED = 1, 2, 4
 GEOM_WDETJ, GEOM_JINV, GEOM_G = 0, 1, 2
 ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
+BATCH_GEOMETRY, BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2, 4
 
 EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
     "fe_refbasis_hex", "fe_refbasis_hex_1d", "fe_refbasis_tet", "fe_gm_rule_size", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
     "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_eval_residual_adjoint", "fe_assembly_create",
     "fe_assembly_free",
-    "fe_assemble_vector", "fe_assemble_vector_noalloc",
+    "fe_assemble_vector", "fe_assemble_vector_noalloc", "fe_batch_create", "fe_batch_run", "fe_batch_describe",
+    "fe_batch_free",
 ]
 
 
@@ -60,6 +62,11 @@ class _RefBasis(ctypes.Structure):
 
 class _Quad(ctypes.Structure):
     _fields_ = [("n_qp", ctypes.c_int), ("points", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
+
+
+class _BatchItem(ctypes.Structure):
+    _fields_ = [("geom", ctypes.c_void_p), ("form", ctypes.c_void_p), ("material", ctypes.c_void_p),
+                ("K_out", ctypes.c_void_p)]
 
 
 class _Operand(ctypes.Structure):
@@ -101,6 +108,10 @@ def load_library(path: str = LIB_PATH):
     L.fe_eval_matrix.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, i, vp, vp]
     L.fe_eval_residual.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, vp, vp]
     L.fe_eval_residual_adjoint.argtypes = [vp, vp, vp, ctypes.POINTER(vp), vp, i, vp, vp, vp]
+    L.fe_batch_create.argtypes = [vp, ctypes.POINTER(_BatchItem), i, ctypes.c_uint, ctypes.POINTER(vp), vp]
+    L.fe_batch_run.argtypes = [vp, vp, vp]
+    L.fe_batch_describe.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.fe_batch_free.argtypes = [vp]
     L.fe_assembly_create.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(vp), vp]
     L.fe_assembly_free.argtypes = [vp]
     L.fe_assemble_vector.argtypes = [vp, vp, i, vp, i, vp, ctypes.c_uint, vp]
@@ -424,6 +435,55 @@ def eval_residual_adjoint(ctx: Context, form: Form, geom: Geometry, args, rbar, 
                                          _prec(precision), ptr(d_mat), ptr(d_x_e), _stream_ptr(stream)),
            "fe_eval_residual_adjoint")
     return d_mat, d_x_e
+
+
+class Batch:
+    """fe_batch_create / fe_batch_run: element matrices of many (geometry, form)
+    items in one persistent launch.  items: list of (geometry, form, material
+    tensor or None, K_out tensor or None); the tensors are kept alive here."""
+
+    def __init__(self, ctx: Context, items, flags: int = 0, stream=None):
+        import torch
+        self.ctx, self._keep, self.outputs = ctx, [], []
+        arr = (_BatchItem * len(items))()
+        for k, (geom, form, mat, K) in enumerate(items):
+            nr, nc = form.shape(geom.N)
+            E = geom.mesh.n_elems
+            if K is None:
+                K = torch.empty((E, nr, nc), dtype=torch.float32, device=geom.mesh.coords.device)
+            _dev(K, torch.float32, "K_out")
+            if tuple(K.shape) != (E, nr, nc):
+                raise ValueError("K_out of item %d must have shape %s" % (k, (E, nr, nc)))
+            if mat is not None:
+                _dev(mat, torch.float64, "material of item %d" % k)
+            arr[k] = _BatchItem(geom._h.value, form._h.value, mat.data_ptr() if mat is not None else None,
+                                K.data_ptr())
+            self._keep += [geom, form, mat, K]
+            self.outputs.append(K)
+        self._h = ctypes.c_void_p()
+        _check(_lib.fe_batch_create(ctx.handle, arr, len(items), flags, ctypes.byref(self._h), _stream_ptr(stream)),
+               "fe_batch_create")
+
+    def run(self, stream=None):
+        _check(_lib.fe_batch_run(self.ctx.handle, self._h, _stream_ptr(stream)), "fe_batch_run")
+        return self.outputs
+
+    def describe(self, item: int):
+        t, e, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.fe_batch_describe(self._h, item, ctypes.byref(t), ctypes.byref(e), ctypes.byref(s)),
+               "fe_batch_describe")
+        return {"tile": t.value, "elems_per_chunk": e.value, "staging": "bulk" if s.value else "direct"}
+
+    def free(self):
+        if self._h:
+            _lib.fe_batch_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 class Assembly:

@@ -1,0 +1,158 @@
+"""GPU parity of the batched persistent matrix evaluation (fe_batch_*) on a
+scaled-down mixed mesh: P1-P3 tetrahedra and Q1-Q3 hexahedra with the
+weighted Laplacian, weighted mass and Lame elasticity, against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_04121_gb300 import fe, meshgen
+from tests.parity import TOL
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FORMS = ("laplace", "mass", "elasticity")
+
+
+@pytest.fixture(scope="module")
+def ctx(libfe):
+    c = fe.Context(0)
+    yield c
+    c.close()
+
+
+def _t(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+class Group:
+    def __init__(self, ctx, name, mesh):
+        self.name, self.mesh = name, mesh
+        self.tet = name.startswith("P")
+        p = int(name[1])
+        self.ref = oracle.RefTet(p, p) if self.tet else oracle.RefElement(p, p + 1)
+        self.coords = _t(mesh.coords, torch.float64)
+        self.m = fe.Mesh(self.coords, _t(mesh.conn, torch.int32))
+        flags = fe.GEOM_STORE_F32
+        self.geom = fe.tet_geometry(ctx, self.m, p, flags=flags) if self.tet else \
+            fe.hex_geometry(ctx, self.m, p, p + 1, flags=flags)
+        rng = np.random.default_rng(90 + p + (10 if self.tet else 0))
+        E = mesh.n_elems
+        self.coef = rng.uniform(0.5, 2.0, E)
+        self.lam = rng.uniform(0.5, 2.0, E)
+        self.mu = rng.uniform(0.2, 1.0, E)
+
+    def material(self, form):
+        if form == "elasticity":
+            return _t(np.stack([self.lam, self.mu], 1), torch.float64)
+        return _t(self.coef, torch.float64)
+
+    def reference(self, form, coords=None):
+        """Oracle matrices and the sums of absolute terms (the error scale)."""
+        wdetJ, G, _ = oracle.geometry(self.mesh.coords if coords is None else coords, self.mesh.conn, self.ref)
+        aw, aG = np.abs(wdetJ), np.abs(G)
+        if form == "laplace":
+            return oracle.matrix_laplace(wdetJ, G, self.coef), oracle.matrix_laplace(aw, aG, self.coef)
+        if form == "mass":
+            return (oracle.matrix_mass(wdetJ, self.ref.phi, 1, self.coef),
+                    oracle.matrix_mass(aw, np.abs(self.ref.phi), 1, self.coef))
+        D = oracle.lame_to_D(self.lam, self.mu)
+        return oracle.matrix_elasticity(wdetJ, G, D), oracle.matrix_elasticity(aw, aG, np.abs(D))
+
+
+def _form(name):
+    if name == "laplace":
+        return fe.laplace_form(weighted=True)
+    if name == "mass":
+        return fe.mass_form(1, weighted=True)
+    return fe.elasticity_form(fe.MAT_LAME)
+
+
+def _err(K, ref):
+    Kref, Kabs = ref
+    Kg = K.cpu().numpy().astype(np.float64)
+    return float((np.sqrt(((Kg - Kref) ** 2).sum((1, 2))) / np.sqrt((Kabs ** 2).sum((1, 2)))).max())
+
+
+@pytest.fixture(scope="module")
+def groups(ctx):
+    return [Group(ctx, n, m) for n, m in meshgen.mixed_mesh_groups(scale=0.002, seed=2)]
+
+
+def _items(groups):
+    items, keys = [], []
+    for g in groups:
+        for f in FORMS:
+            items.append((g.geom, _form(f), g.material(f), None))
+            keys.append((g, f))
+    return items, keys
+
+
+@pytest.mark.parametrize("flags", [0, fe.BATCH_AUTOTUNE | fe.BATCH_GRAPH | fe.BATCH_GEOMETRY])
+def test_batch_matches_oracle(ctx, groups, flags):
+    items, keys = _items(groups)
+    b = fe.Batch(ctx, items, flags)
+    outs = b.run()
+    ctx.check()
+    for k, ((g, f), K) in enumerate(zip(keys, outs)):
+        e = _err(K, g.reference(f))
+        assert e <= TOL["f32"], (g.name, f, e, b.describe(k))
+    b.free()
+
+
+def test_batch_runs_are_reproducible_and_graph_equals_eager(ctx, groups):
+    items, keys = _items(groups)
+    eager = fe.Batch(ctx, items, 0)
+    first = [K.clone() for K in eager.run()]
+    again = eager.run()
+    items2 = [(g, f, m, None) for g, f, m, _ in items]
+    graph = fe.Batch(ctx, items2, fe.BATCH_GRAPH)
+    g_out = graph.run()
+    ctx.check()
+    for a, b2, c in zip(first, again, g_out):
+        assert torch.equal(a, b2)
+        assert torch.equal(a, c)  # same configurations (no autotuning): identical results
+
+
+def test_batch_geometry_flag_follows_moved_nodes(ctx, groups):
+    g = groups[4]  # Q2 hexahedra
+    items = [(g.geom, _form("elasticity"), g.material("elasticity"), None)]
+    b = fe.Batch(ctx, items, fe.BATCH_GEOMETRY | fe.BATCH_GRAPH)
+    X0 = g.coords.clone()
+    rng = np.random.default_rng(3)
+    moved = g.mesh.coords.copy()
+    interior = np.all((moved > 1e-9) & (moved < 1 - 1e-9), axis=1)
+    h = 1.0 / (2 * np.array(g.mesh.shape))
+    moved[interior] += 0.05 * rng.uniform(-1, 1, (interior.sum(), 3)) * h
+    g.coords.copy_(_t(moved, torch.float64))
+    (K,) = b.run()
+    ctx.check()
+    assert _err(K, g.reference("elasticity", moved)) <= TOL["f32"]
+    g.coords.copy_(X0)
+    g.geom.update()
+    ctx.check()
+
+
+def test_batch_autotune_choice_is_a_candidate(ctx, groups):
+    items, keys = _items(groups)
+    b = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE)
+    for k, (g, f) in enumerate(keys):
+        d = b.describe(k)
+        N = g.mesh.nodes_per_elem
+        assert N % d["tile"] == 0 and d["elems_per_chunk"] >= 1
+    with pytest.raises(fe.FEError):
+        b.describe(len(keys))
+
+
+def test_batch_rejections(ctx, groups):
+    g = groups[4]
+    with pytest.raises(fe.FEError) as ei:
+        fe.Batch(ctx, [(g.geom, fe.convect_form(), None, None)])
+    assert ei.value.status == fe.FE_ERR_UNSUPPORTED_SPEC
+    g64 = fe.hex_geometry(ctx, g.m, 2, 3, flags=fe.GEOM_STORE_F64)
+    with pytest.raises(fe.FEError) as ei:
+        fe.Batch(ctx, [(g64, _form("laplace"), g.material("laplace"), None)])
+    assert ei.value.status == fe.FE_ERR_INVALID_ARG
+    with pytest.raises(fe.FEError) as ei:
+        fe.Batch(ctx, [(g.geom, _form("elasticity"), None, None)])
+    assert ei.value.status == fe.FE_ERR_INVALID_ARG
