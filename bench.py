@@ -61,6 +61,12 @@ FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
 ADJOINT_N = 32
 
 
+# Mixed mesh: P1/P2/P3 tetrahedra (200k/120k/40k, Delaunay, GM rules of index p)
+# and Q1/Q2/Q3 hexahedra (60k/30k/8k, +-0.1h), weighted Laplace, weighted mass
+# and Lame elasticity matrices of every group in one persistent launch.
+MIXED_FORMS = ("laplace", "mass", "elasticity")
+
+
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -68,9 +74,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=48, help="cube edge in elements (48 -> 110,592 hexes)")
-    ap.add_argument("--workload", choices=["elasticity", "convection"], default="elasticity",
-                    help="convection: time only the Navier-Stokes convection workload on an n^3 cube "
-                         "(both precisions, no oracle), one JSON line")
+    ap.add_argument("--workload", choices=["elasticity", "convection", "mixed"], default="elasticity",
+                    help="convection: only the Navier-Stokes convection workload on an n^3 cube (both "
+                         "precisions); mixed: only the mixed-mesh batch; no oracle, one JSON line")
+    ap.add_argument("--scale", type=float, default=1.0, help="mixed workload: scale of every group")
     ap.add_argument("--prec", default="auto",
                     help="contraction precision of the headline path; auto = fastest of the ladder within 1e-5")
     ap.add_argument("--skip-extras", action="store_true",
@@ -492,6 +499,105 @@ def adjoint_measure(n, device, flush, ref, steps=5, warmup=3):
     return out
 
 
+def mixed_setup(scale, device):
+    import torch
+
+    from paper_2107_04121_gb300 import fe, meshgen
+    ctx = fe.Context(device)
+    groups = []
+    for name, mesh in meshgen.mixed_mesh_groups(scale, seed=2):
+        p = int(name[1])
+        coords = torch.from_numpy(mesh.coords).to(device)
+        m = fe.Mesh(coords, torch.from_numpy(mesh.conn).to(device))
+        geom = (fe.tet_geometry(ctx, m, p, flags=fe.GEOM_STORE_F32) if name[0] == "P" else
+                fe.hex_geometry(ctx, m, p, p + 1, flags=fe.GEOM_STORE_F32))
+        rng = np.random.default_rng(100 + p + (10 if name[0] == "P" else 0))
+        coef = rng.uniform(0.5, 2.0, mesh.n_elems)
+        lam, mu = rng.uniform(0.5, 2.0, mesh.n_elems), rng.uniform(0.2, 1.0, mesh.n_elems)
+        groups.append({"name": name, "mesh": mesh, "m": m, "geom": geom, "coef": coef, "lam": lam, "mu": mu,
+                       "mats": {"laplace": torch.from_numpy(coef).to(device),
+                                "mass": torch.from_numpy(coef).to(device),
+                                "elasticity": torch.from_numpy(np.stack([lam, mu], 1)).to(device)}})
+    forms = {"laplace": fe.laplace_form(weighted=True), "mass": fe.mass_form(1, weighted=True),
+             "elasticity": fe.elasticity_form(fe.MAT_LAME)}
+    return ctx, groups, forms
+
+
+def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
+    """The mixed-mesh batch: one CUDA-graph launch = FP64 geometry of the six
+    groups + the persistent matrix kernel over all 18 (group, form) items,
+    autotuned; beside it the same work as separate per-item launches, and the
+    persistent kernel alone against the HBM roofline."""
+    import torch
+
+    from paper_2107_04121_gb300 import fe
+    ctx, groups, forms = mixed_setup(scale, device)
+    items = [(g["geom"], forms[f], g["mats"][f], None) for g in groups for f in MIXED_FORMS]
+    t0 = time.perf_counter()
+    batch = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_GRAPH | fe.BATCH_GEOMETRY)
+    plan_s = time.perf_counter() - t0
+    mats_only = fe.Batch(ctx, [(g, f, m, K) for (g, f, m, _), K in zip(items, batch.outputs)], fe.BATCH_AUTOTUNE)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    def separate():
+        for g in groups:
+            g["geom"].update()
+        for (g, f, m, _), K in zip(items, batch.outputs):
+            fe.eval_matrix(ctx, f, g, [m, None, None], "f32", out=K)
+
+    ms_graph = timed(batch.run)
+    ms_kernel = timed(mats_only.run)
+    ms_sep = timed(separate)
+    ctx.check()
+    n_el = sum(g["mesh"].n_elems for g in groups)
+    # algorithmic bytes of the persistent kernel: per item and element, J^-1 and
+    # w det J (FP32, Q x 10 values), the material (8 or 16 B) and the K_e write
+    kbytes = 0
+    for (g, f, m, _), K in zip(items, batch.outputs):
+        E = K.shape[0]
+        kbytes += E * (g.Q * 10 * 4 + m.element_size() * m.numel() // max(E, 1) + K[0].numel() * 4)
+    out = {"workload": "mixed mesh: P1/P2/P3 tets %s, Q1/Q2/Q3 hexes %s; weighted Laplace + weighted mass + Lame "
+                       "elasticity matrices, FP32 from FP64 geometry" % (
+                           "/".join(str(g["mesh"].n_elems) for g in groups[:3]),
+                           "/".join(str(g["mesh"].n_elems) for g in groups[3:])),
+           "elements": n_el, "items": len(items), "plan_seconds": plan_s,
+           "graph_ms": ms_graph, "value": n_el / (ms_graph / 1e3), "unit": UNIT + " (all 3 forms per element)",
+           "persistent_kernel_ms": ms_kernel, "separate_launches_ms": ms_sep,
+           "roofline": {"kernel": "k_batch (persistent, 18 items)", "bound": "hbm",
+                        "achieved": kbytes / (ms_kernel / 1e3) / 1e9, "unit": "GB/s", "bytes": kbytes},
+           "configs": {"%s/%s" % (items_g["name"], f): batch.describe(k)
+                       for k, (items_g, f) in enumerate((g, f) for g in groups for f in MIXED_FORMS)}}
+    if ref is not None:
+        errs = {}
+        for gi, g in enumerate(groups):
+            idx, refs = ref[gi]
+            it = torch.from_numpy(idx).cuda()
+            for fi, f in enumerate(MIXED_FORMS):
+                Kref, Kabs = refs[f]
+                K = batch.outputs[gi * len(MIXED_FORMS) + fi][it].double().cpu().numpy()
+                e = float((np.sqrt(((K - Kref) ** 2).sum((1, 2))) / np.sqrt((Kabs ** 2).sum((1, 2)))).max())
+                errs["%s/%s" % (g["name"], f)] = e
+        out["rel_err_vs_abs_terms"] = errs
+    batch.free()
+    mats_only.free()
+    ctx.close()
+    return out
+
+
 # ---- CPU oracle (baseline / reference arm) ------------------------------------------------
 
 def oracle_step(mesh, lam, mu, u, n_elems):
@@ -533,7 +639,33 @@ def cpu_baseline(n, min_seconds=10.0):
     wdetJ, G, _ = oracle.geometry(mesh.coords, conn, oracle.RefElement(2, 3))
     D = oracle.lame_to_D(lam[idx], mu[idx])
     ref = (idx, oracle.matrix_elasticity(wdetJ, G, D), oracle.residual_elasticity(conn, wdetJ, G, D, u))
-    return base, ref, (convect_reference(CONVECT_N), adjoint_reference(ADJOINT_N))
+    return base, ref, (convect_reference(CONVECT_N), adjoint_reference(ADJOINT_N), mixed_reference())
+
+
+def mixed_reference(scale=1.0, per_group=16):
+    """CPU-baseline leg, mixed mesh: the oracle's matrices of the three forms
+    on sampled elements of every group, with the sums of absolute terms."""
+    import oracle
+    from paper_2107_04121_gb300 import meshgen
+    out = []
+    for name, mesh in meshgen.mixed_mesh_groups(scale, seed=2):
+        p = int(name[1])
+        ref = oracle.RefTet(p, p) if name[0] == "P" else oracle.RefElement(p, p + 1)
+        rng = np.random.default_rng(100 + p + (10 if name[0] == "P" else 0))
+        coef = rng.uniform(0.5, 2.0, mesh.n_elems)
+        lam, mu = rng.uniform(0.5, 2.0, mesh.n_elems), rng.uniform(0.2, 1.0, mesh.n_elems)
+        E = mesh.n_elems
+        idx = np.unique(np.concatenate([[0, E - 1], np.random.default_rng(11).choice(E, per_group, replace=False)]))
+        wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn[idx], ref)
+        aw, aG = np.abs(wdetJ), np.abs(G)
+        D = oracle.lame_to_D(lam[idx], mu[idx])
+        out.append((idx, {"laplace": (oracle.matrix_laplace(wdetJ, G, coef[idx]),
+                                      oracle.matrix_laplace(aw, aG, coef[idx])),
+                          "mass": (oracle.matrix_mass(wdetJ, ref.phi, 1, coef[idx]),
+                                   oracle.matrix_mass(aw, np.abs(ref.phi), 1, coef[idx])),
+                          "elasticity": (oracle.matrix_elasticity(wdetJ, G, D),
+                                         oracle.matrix_elasticity(aw, aG, np.abs(D)))}))
+    return out
 
 
 def adjoint_reference(n):
@@ -624,10 +756,14 @@ def main():
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    if args.workload == "convection":
-        res = convect_measure(args.n, local, ws, flush, None, hbm_peak, args.steps, args.warmup)
+    if args.workload in ("convection", "mixed"):
+        if args.workload == "convection":
+            res = convect_measure(args.n, local, ws, flush, None, hbm_peak, args.steps, args.warmup)
+        else:
+            res = mixed_measure(local, flush, None, args.steps, args.warmup, args.scale)
+            res["roofline"].update({"peak": hbm_peak, "frac": res["roofline"]["achieved"] / hbm_peak})
         if rank == 0:
-            print(json.dumps({"workload": "convection", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            print(json.dumps({"workload": args.workload, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
                               **res}), flush=True)
         if ws > 1:
             import torch.distributed as dist
@@ -636,9 +772,9 @@ def main():
 
     # the oracle's OpenMP threads must not compete with the timed GPU region:
     # time the CPU baseline first (rank 0, N = 1 only)
-    cpu, ref, cv_ref, ad_ref = None, None, None, None
+    cpu, ref, cv_ref, ad_ref, mx_ref = None, None, None, None, None
     if rank == 0 and ws == 1 and not args.skip_extras:
-        cpu, ref, (cv_ref, ad_ref) = cpu_baseline(args.n)
+        cpu, ref, (cv_ref, ad_ref, mx_ref) = cpu_baseline(args.n)
 
     wl = Workload(args.n, local)
     ladder = None
@@ -699,6 +835,8 @@ def main():
             wl.drop(p)
         line["convective"] = convect_measure(CONVECT_N, local, ws, flush, cv_ref, hbm_peak)
         line["adjoint"] = adjoint_measure(ADJOINT_N, local, flush, ad_ref)
+        line["mixed"] = mixed_measure(local, flush, mx_ref)
+        line["mixed"]["roofline"].update({"peak": hbm_peak, "frac": line["mixed"]["roofline"]["achieved"] / hbm_peak})
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if rank == 0:
