@@ -8,6 +8,8 @@
 
 namespace {
 
+__host__ __device__ constexpr int gcd_const(int a, int b) { return b == 0 ? a : gcd_const(b, a % b); }
+
 // Padded position of node a inside its group of T: groups start on 16 bytes,
 // except FP32 pairs, which are read as float2 and need only 8.
 template <int T, typename S>
@@ -198,20 +200,43 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
             // scaled physical gradients sqrt(w det J) G[el][q][j][a], G = J^-T grad_xi phi,
             // padded node index; the Gram blocks then need no weight in the inner loop
             // (det J > 0 is checked by the geometry kernel; Gauss weights are positive)
-            for (int i = threadIdx.x; i < ne * Q; i += THREADS) {
-                const int el = i / Q, q = i % Q;
-                const S sw = SQW ? sqrt(sW[i]) : (S)1;
-                S Ji[9];
+            if constexpr (SQW)
+                for (int i = threadIdx.x; i < ne * Q; i += THREADS) {
+                    const S sw = sqrt(sW[i]);
 #pragma unroll
-                for (int t = 0; t < 9; ++t) Ji[t] = sw * sJ[i * 9 + t];
-                const S *D0 = sD + q * 3 * N;
-                S *Go = sG + ((el * Q + q) * 3) * NP;
-#pragma unroll 3
-                for (int a = 0; a < N; ++a) {
+                    for (int t = 0; t < 9; ++t) sJ[i * 9 + t] *= sw;
+                }
+            __syncthreads();
+            // A thread per point looping over the nodes is cheapest, but its lanes are
+            // 3 NP words apart: where that stride shares 8 or more banks (Q1, Q3) one
+            // (element, point, node) per thread, nodes fastest, keeps the reads of the
+            // reference gradients and the writes of G on consecutive banks instead
+            constexpr bool BY_NODE = gcd_const(3 * NP, 32) >= 8;
+            if constexpr (BY_NODE) {
+                for (int i = threadIdx.x; i < ne * Q * N; i += THREADS) {
+                    const int a = i % N, eq = i / N, q = eq % Q;
+                    const S *Ji = sJ + eq * 9;
+                    const S *D0 = sD + q * 3 * N;
                     const S g0 = D0[a], g1 = D0[N + a], g2 = D0[2 * N + a];
-                    const int pa = (a / T) * TP + a % T;
+                    S *Go = sG + eq * 3 * NP + (a / T) * TP + a % T;
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) Go[j * NP + pa] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
+                    for (int j = 0; j < 3; ++j) Go[j * NP] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
+                }
+            } else {
+                for (int i = threadIdx.x; i < ne * Q; i += THREADS) {
+                    const int q = i % Q;
+                    S Ji[9];
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) Ji[t] = sJ[i * 9 + t];
+                    const S *D0 = sD + q * 3 * N;
+                    S *Go = sG + i * 3 * NP;
+#pragma unroll 3
+                    for (int a = 0; a < N; ++a) {
+                        const S g0 = D0[a], g1 = D0[N + a], g2 = D0[2 * N + a];
+                        const int pa = (a / T) * TP + a % T;
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) Go[j * NP + pa] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
+                    }
                 }
             }
             __syncthreads();
@@ -238,12 +263,16 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
         if (active) {
             el = wi / NU;
             int u = wi % NU;
-            // u -> (ta, tb), ta <= tb, row-major over the upper triangle
-            while (u >= NT - ta) {
-                u -= NT - ta;
-                ++ta;
+            // u -> (ta, tb), ta <= tb, along the diagonals d = tb - ta: neighbouring
+            // threads differ in both tile indices, so neither the tile's rows nor its
+            // mirror's rows share a shared-memory bank across a warp
+            int d = 0;
+            while (u >= NT - d) {
+                u -= NT - d;
+                ++d;
             }
-            tb = ta + u;
+            ta = u;
+            tb = u + d;
             const S *Wq = sW + el * Q;
 #pragma unroll 9
             for (int q = 0; q < Q; ++q) {
