@@ -666,6 +666,236 @@ int oracle_matrix_convect(long long n_elems, int N, int Q, const int32_t *conn, 
 }
 
 /* ------------------------------------------------------------------------ */
+/* The remaining weak forms of Tab. ewfd, element by element at every point:
+ *   weighted dot  'ij,i,j'  (M, v, u):  v_i M_ij u_j
+ *   Stokes        'i.i,0'   (v, p):     div(v) p
+ *   transposed    'i.i,0'   (u, q):     q div(u)
+ *   divergence    'i.i'     (v):        div(v)
+ * M is a 3x3 matrix per element (row-major).  Field DOFs are gathered through
+ * conn: vector u[3*node + i], scalar p[node]. */
+static void gather_scalar(int N, const int32_t *conn_e, const double *p, double *pe)
+{
+    for (int b = 0; b < N; ++b) pe[b] = p[conn_e[b]];
+}
+
+/* Matrix of the weighted dot product: K[(i,a),(j,b)] = M_ij sum_q wdetJ phi_a phi_b. */
+int oracle_matrix_wdot(long long n_elems, int N, int Q, const double *wdetJ, const double *phi, const double *M,
+                       double *K)
+{
+    if (n_elems < 0 || !wdetJ || !phi || !M || !K) return OR_BAD_ARG;
+    const int n = 3 * N;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e)
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < N; ++a)
+                for (int j = 0; j < 3; ++j)
+                    for (int b = 0; b < N; ++b) {
+                        double s = 0.0;
+                        for (int q = 0; q < Q; ++q)
+                            s += wdetJ[(size_t)e * Q + q] * phi[(size_t)q * N + a] * phi[(size_t)q * N + b];
+                        K[(size_t)e * n * n + (size_t)(i * N + a) * n + j * N + b] = M[(size_t)e * 9 + i * 3 + j] * s;
+                    }
+    return OR_OK;
+}
+
+/* Residual of the weighted dot product: r[(i,a)] = sum_q wdetJ phi_a sum_j M_ij u_h,j. */
+int oracle_residual_wdot(long long n_elems, int N, int Q, const int32_t *conn, const double *wdetJ,
+                         const double *phi, const double *M, const double *u, double *r)
+{
+    if (n_elems < 0 || N > 512 || !conn || !wdetJ || !phi || !M || !u || !r) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double ue[3 * 512];
+        gather_vec(N, conn + (size_t)e * N, u, ue);
+        double *re = r + (size_t)e * 3 * N;
+        for (int c = 0; c < 3 * N; ++c) re[c] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            double uh[3] = {0, 0, 0};
+            for (int j = 0; j < 3; ++j)
+                for (int b = 0; b < N; ++b) uh[j] += phi[(size_t)q * N + b] * ue[j * N + b];
+            const double wd = wdetJ[(size_t)e * Q + q];
+            for (int i = 0; i < 3; ++i) {
+                double mu = 0.0;
+                for (int j = 0; j < 3; ++j) mu += M[(size_t)e * 9 + i * 3 + j] * uh[j];
+                for (int a = 0; a < N; ++a) re[i * N + a] += wd * phi[(size_t)q * N + a] * mu;
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/* Stokes coupling matrix: B[(i,a), b] = sum_q wdetJ G[i][a] phi_b (rows 3N, columns N);
+ * the transposed coupling 'i.i,0' (u, q) has the matrix B^T. */
+int oracle_matrix_stokes(long long n_elems, int N, int Q, const double *wdetJ, const double *G, const double *phi,
+                         double *B)
+{
+    if (n_elems < 0 || !wdetJ || !G || !phi || !B) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e)
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < N; ++b) {
+                    double s = 0.0;
+                    for (int q = 0; q < Q; ++q)
+                        s += wdetJ[(size_t)e * Q + q] * G[(((size_t)e * Q + q) * 3 + i) * N + a] * phi[(size_t)q * N + b];
+                    B[(size_t)e * 3 * N * N + (size_t)(i * N + a) * N + b] = s;
+                }
+    return OR_OK;
+}
+
+/* Stokes residual r[(i,a)] = sum_q wdetJ G[i][a] p_h with p_h = sum_b phi_b p_b;
+ * with p = NULL the divergence form 'i.i' (v): r[(i,a)] = sum_q wdetJ G[i][a]. */
+int oracle_residual_stokes(long long n_elems, int N, int Q, const int32_t *conn, const double *wdetJ,
+                           const double *G, const double *phi, const double *p, double *r)
+{
+    if (n_elems < 0 || N > 512 || !conn || !wdetJ || !G || !phi || !r) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double pe[512];
+        if (p) gather_scalar(N, conn + (size_t)e * N, p, pe);
+        double *re = r + (size_t)e * 3 * N;
+        for (int c = 0; c < 3 * N; ++c) re[c] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            double ph = 1.0;
+            if (p) {
+                ph = 0.0;
+                for (int b = 0; b < N; ++b) ph += phi[(size_t)q * N + b] * pe[b];
+            }
+            const double wd = wdetJ[(size_t)e * Q + q];
+            for (int i = 0; i < 3; ++i)
+                for (int a = 0; a < N; ++a) re[i * N + a] += wd * G[(((size_t)e * Q + q) * 3 + i) * N + a] * ph;
+        }
+    }
+    return OR_OK;
+}
+
+/* Transposed Stokes residual r[a] = sum_q wdetJ phi_a div(u_h). */
+int oracle_residual_stokes_t(long long n_elems, int N, int Q, const int32_t *conn, const double *wdetJ,
+                             const double *G, const double *phi, const double *u, double *r)
+{
+    if (n_elems < 0 || N > 512 || !conn || !wdetJ || !G || !phi || !u || !r) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double ue[3 * 512];
+        gather_vec(N, conn + (size_t)e * N, u, ue);
+        double *re = r + (size_t)e * N;
+        for (int a = 0; a < N; ++a) re[a] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            double div = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int b = 0; b < N; ++b) div += ue[i * N + b] * G[(((size_t)e * Q + q) * 3 + i) * N + b];
+            const double wd = wdetJ[(size_t)e * Q + q];
+            for (int a = 0; a < N; ++a) re[a] += wd * phi[(size_t)q * N + a] * div;
+        }
+    }
+    return OR_OK;
+}
+
+/* 'eval' mode: the integral over each element of a form whose operands all
+ * carry DOFs (Sec. 5.1, evaluation modes), out (E, n_out):
+ *   kind 0 Laplace      c sum_q wdetJ grad u . grad w           (scalar fields)
+ *   kind 1 dot / mass   c sum_q wdetJ u . w                     (ncomp 1 or 3)
+ *   kind 2 elasticity   sum_q wdetJ e(u)^T D e(w)               (Voigt, engineering shear)
+ *   kind 3 weighted dot sum_q wdetJ u_i M_ij w_j
+ *   kind 4 Stokes       sum_q wdetJ div(u) p                    (w = p scalar)
+ *   kind 5 divergence   sum_q wdetJ div(u)
+ *   kind 6 Cauchy stress sum_q wdetJ D e(u)                     (6 values)
+ *   kind 7 convection   sum_q wdetJ u_i (d w_i / d x_j) z_j     (three vector fields)
+ * coef: per-element scalar (kinds 0, 1; NULL = 1); mat: D (E,6,6) for 2, 6,
+ * M (E,3,3) for 3. */
+int oracle_eval_form(int kind, long long n_elems, int N, int Q, int ncomp, const int32_t *conn, const double *wdetJ,
+                     const double *G, const double *phi, const double *coef, const double *mat, const double *u,
+                     const double *w, const double *z, double *out)
+{
+    if (kind < 0 || kind > 7 || n_elems < 0 || N > 512 || !conn || !wdetJ || !G || !phi || !u || !out)
+        return OR_BAD_ARG;
+    const int n_out = kind == 6 ? 6 : 1;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double ue[3 * 512], we[3 * 512], ze[3 * 512];
+        const int32_t *ce = conn + (size_t)e * N;
+        const int cu = (kind == 0 || (kind == 1 && ncomp == 1)) ? 1 : 3;
+        for (int i = 0; i < cu; ++i)
+            for (int b = 0; b < N; ++b) ue[i * N + b] = u[(size_t)cu * ce[b] + i];
+        if (w) {
+            const int cw = (kind == 0 || kind == 4 || (kind == 1 && ncomp == 1)) ? 1 : 3;
+            for (int i = 0; i < cw; ++i)
+                for (int b = 0; b < N; ++b) we[i * N + b] = w[(size_t)cw * ce[b] + i];
+        }
+        if (z)
+            for (int i = 0; i < 3; ++i)
+                for (int b = 0; b < N; ++b) ze[i * N + b] = z[(size_t)3 * ce[b] + i];
+        double acc[6] = {0, 0, 0, 0, 0, 0};
+        for (int q = 0; q < Q; ++q) {
+            const double *Gq = G + ((size_t)e * Q + q) * 3 * N;
+            const double *pq = phi + (size_t)q * N;
+            const double wd = wdetJ[(size_t)e * Q + q];
+            double uv[3] = {0, 0, 0}, wv[3] = {0, 0, 0}, zv[3] = {0, 0, 0}, gu[3][3] = {{0}}, gw[3][3] = {{0}};
+            for (int i = 0; i < 3; ++i)
+                for (int b = 0; b < N; ++b) {
+                    if (i < cu) {
+                        uv[i] += pq[b] * ue[i * N + b];
+                        for (int j = 0; j < 3; ++j) gu[i][j] += ue[i * N + b] * Gq[j * N + b];
+                    }
+                    if (w && (i < 3)) {
+                        const int cw = (kind == 0 || kind == 4 || (kind == 1 && ncomp == 1)) ? 1 : 3;
+                        if (i < cw) {
+                            wv[i] += pq[b] * we[i * N + b];
+                            for (int j = 0; j < 3; ++j) gw[i][j] += we[i * N + b] * Gq[j * N + b];
+                        }
+                    }
+                    if (z) zv[i] += pq[b] * ze[i * N + b];
+                }
+            const double c = coef ? coef[e] : 1.0;
+            const double *Me = mat ? mat + (size_t)e * (kind == 3 ? 9 : 36) : NULL;
+            double eu[6] = {gu[0][0], gu[1][1], gu[2][2], gu[0][1] + gu[1][0], gu[0][2] + gu[2][0], gu[1][2] + gu[2][1]};
+            double ew[6] = {gw[0][0], gw[1][1], gw[2][2], gw[0][1] + gw[1][0], gw[0][2] + gw[2][0], gw[1][2] + gw[2][1]};
+            switch (kind) {
+            case 0: acc[0] += wd * c * (gu[0][0] * gw[0][0] + gu[0][1] * gw[0][1] + gu[0][2] * gw[0][2]); break;
+            case 1: {
+                double s = 0.0;
+                for (int i = 0; i < cu; ++i) s += uv[i] * wv[i];
+                acc[0] += wd * c * s;
+                break;
+            }
+            case 2: {
+                double s = 0.0;
+                for (int I = 0; I < 6; ++I)
+                    for (int K = 0; K < 6; ++K) s += eu[I] * Me[I * 6 + K] * ew[K];
+                acc[0] += wd * s;
+                break;
+            }
+            case 3: {
+                double s = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) s += uv[i] * Me[i * 3 + j] * wv[j];
+                acc[0] += wd * s;
+                break;
+            }
+            case 4: acc[0] += wd * (gu[0][0] + gu[1][1] + gu[2][2]) * wv[0]; break;
+            case 5: acc[0] += wd * (gu[0][0] + gu[1][1] + gu[2][2]); break;
+            case 6:
+                for (int I = 0; I < 6; ++I) {
+                    double s = 0.0;
+                    for (int K = 0; K < 6; ++K) s += Me[I * 6 + K] * eu[K];
+                    acc[I] += wd * s;
+                }
+                break;
+            case 7: {
+                double s = 0.0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) s += uv[i] * gw[i][j] * zv[j];
+                acc[0] += wd * s;
+                break;
+            }
+            }
+        }
+        for (int m = 0; m < n_out; ++m) out[(size_t)e * n_out + m] = acc[m];
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Adjoint of the assembled isotropic elasticity residual.  The paper states the
  * residual (Algorithm 1, form 'IK,s(i:j)->I,s(k:l)->K'); the derivatives below
  * are derived here.  For a scalar objective of the assembled residual R with

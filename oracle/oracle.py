@@ -59,6 +59,14 @@ def lib():
                                             ctypes.c_int, ctypes.c_int, _D]
         L.oracle_adjoint_elasticity.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D,
                                                 _D, _D, _D, _D, _D]
+        L.oracle_matrix_wdot.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        L.oracle_residual_wdot.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D, _D]
+        L.oracle_matrix_stokes.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _D, _D, _D, _D]
+        L.oracle_residual_stokes.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D, _D]
+        L.oracle_residual_stokes_t.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D,
+                                               _D]
+        L.oracle_eval_form.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I,
+                                       _D, _D, _D, _D, _D, _D, _D, _D, _D]
         L.oracle_assemble.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, ctypes.c_longlong,
                                       ctypes.c_int, _D]
         L.oracle_num_threads.restype = ctypes.c_int
@@ -284,6 +292,68 @@ def elasticity_objective_gradient(coords, conn, ref: RefElement, lam, mu, u):
     dlam, dmu, dXe = adjoint_elasticity_terms(conn, wdetJ, G, lam, mu, u, R)
     dX = assemble(conn, dXe, np.asarray(coords).shape[0], 3).reshape(-1, 3)
     return J, dlam, dmu, dX
+
+
+def matrix_wdot(wdetJ, phi, M):
+    """Weighted dot product 'ij,i,j': K[(i,a),(j,b)] = M_ij sum_q wdetJ phi_a phi_b."""
+    E, Q = wdetJ.shape
+    N = phi.shape[1]
+    K = np.zeros((E, 3 * N, 3 * N))
+    _check(lib().oracle_matrix_wdot(E, N, Q, _d(wdetJ), _d(_f64(phi)), _d(_f64(M)), _d(K)))
+    return K
+
+
+def residual_wdot(conn, wdetJ, phi, M, u):
+    E, Q = wdetJ.shape
+    N = phi.shape[1]
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    r = np.zeros((E, 3 * N))
+    _check(lib().oracle_residual_wdot(E, N, Q, _i(conn), _d(wdetJ), _d(_f64(phi)), _d(_f64(M)), _d(_f64(u)), _d(r)))
+    return r
+
+
+def matrix_stokes(wdetJ, G, phi):
+    """Stokes coupling 'i.i,0' (v, p): B[(i,a), b] = sum_q wdetJ G[i][a] phi_b; the
+    transposed coupling (u, q) has B^T."""
+    E, Q, _, N = G.shape
+    B = np.zeros((E, 3 * N, N))
+    _check(lib().oracle_matrix_stokes(E, N, Q, _d(wdetJ), _d(G), _d(_f64(phi)), _d(B)))
+    return B
+
+
+def residual_stokes(conn, wdetJ, G, phi, p=None):
+    """r[(i,a)] = sum_q wdetJ G[i][a] p_h; p = None: the divergence form 'i.i'."""
+    E, Q, _, N = G.shape
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    r = np.zeros((E, 3 * N))
+    _check(lib().oracle_residual_stokes(E, N, Q, _i(conn), _d(wdetJ), _d(G), _d(_f64(phi)),
+                                        _d(_f64(p) if p is not None else None), _d(r)))
+    return r
+
+
+def residual_stokes_t(conn, wdetJ, G, phi, u):
+    """r[a] = sum_q wdetJ phi_a div(u_h)."""
+    E, Q, _, N = G.shape
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    r = np.zeros((E, N))
+    _check(lib().oracle_residual_stokes_t(E, N, Q, _i(conn), _d(wdetJ), _d(G), _d(_f64(phi)), _d(_f64(u)), _d(r)))
+    return r
+
+
+EVAL_KINDS = {"laplace": 0, "mass": 1, "elasticity": 2, "wdot": 3, "stokes": 4, "div": 5, "cauchy": 6,
+              "convect": 7}
+
+
+def eval_form(kind, conn, wdetJ, G, phi, u, w=None, z=None, coef=None, mat=None, ncomp=3):
+    """'eval' mode integrals per element (E, 1) or (E, 6) for the Cauchy stress."""
+    E, Q, _, N = G.shape
+    k = EVAL_KINDS[kind]
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    out = np.zeros((E, 6 if kind == "cauchy" else 1))
+    f = lambda a: _d(_f64(a)) if a is not None else _d(None)
+    _check(lib().oracle_eval_form(k, E, N, Q, ncomp, _i(conn), _d(wdetJ), _d(G), _d(_f64(phi)), f(coef), f(mat),
+                                  _d(_f64(u)), f(w), f(z), _d(out)))
+    return out
 
 
 def assemble(conn, r, n_nodes, ncomp, g=None):

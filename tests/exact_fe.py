@@ -146,3 +146,11 @@ def box_convection(p, h, x0, A, c):
             fac[dd] = xd if dd == j else xm * h[dd]
             C += A[j, dd] * h[dd] * _kron3(*fac)
     return C
+
+
+def box_stokes_blocks(p, h):
+    """B_i[a][b] = int_box (d phi_a / d x_i) phi_b, i = 0, 1, 2: on axis i the
+    derivative factor int L_a' L_b (the 1/h and h cancel), m h elsewhere."""
+    m, d, xm, xd = moments_1d(p)
+    h = np.asarray(h, dtype=float)
+    return [_kron3(*[d.T if e == i else m * h[e] for e in range(3)]) for i in range(3)]

@@ -675,3 +675,90 @@ def test_tet_mesh_patch_test(p):
     assert np.abs(R[inside]).max() <= 1e-13 * scale
     vol = sum(abs(np.linalg.det(X[c[vert[1:]]] - X[c[vert[0]]])) / 6 for c in mesh.conn)
     assert abs(wdetJ.sum() - vol) <= 1e-12
+
+
+# -- remaining Tab. ewfd forms and eval mode --------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_stokes_wdot_divergence_on_box_match_exact_integrals(p):
+    h = (0.5, 0.7, 1.3)
+    mesh = meshgen.structured_hex(1, 1, 1, p, 0.0, 0, lengths=h)
+    mesh.coords[:] += np.array([0.25, -1.0, 3.0])
+    ref = oracle.RefElement(p, p + 1)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    N = ref.N
+    Bs = exact_fe.box_stokes_blocks(p, h)
+    B = oracle.matrix_stokes(wdetJ, G, ref.phi)[0]
+    want = np.concatenate(Bs, 0)
+    assert np.abs(B - want).max() <= 1e-13 * np.abs(want).max()
+    # divergence: int d phi_a / d x_i = sum_b B_i[a][b] (partition of unity)
+    rd = oracle.residual_stokes(mesh.conn, wdetJ, G, ref.phi)[0]
+    np.testing.assert_allclose(rd, want.sum(1), atol=1e-13)
+    # Stokes with a linear pressure: B applied to its nodal values
+    rng = np.random.default_rng(3)
+    pl = mesh.coords @ rng.standard_normal(3) + 0.5
+    rs = oracle.residual_stokes(mesh.conn, wdetJ, G, ref.phi, pl)[0]
+    np.testing.assert_allclose(rs, want @ pl[mesh.conn[0]], atol=1e-12)
+    # transposed coupling: r_T = sum_i B_i^T u_i
+    u = rng.standard_normal(3 * mesh.n_nodes)
+    rt = oracle.residual_stokes_t(mesh.conn, wdetJ, G, ref.phi, u)[0]
+    ue = u.reshape(-1, 3)[mesh.conn[0]]
+    np.testing.assert_allclose(rt, sum(Bs[i].T @ ue[:, i] for i in range(3)), atol=1e-12)
+    # weighted dot: M kron the exact mass matrix, and its residual K u
+    M = rng.standard_normal((1, 3, 3))
+    K = oracle.matrix_wdot(wdetJ, ref.phi, M)[0]
+    Kw = np.kron(M[0], exact_fe.box_mass(p, h))
+    assert np.abs(K - Kw).max() <= 1e-13 * np.abs(Kw).max()
+    rw = oracle.residual_wdot(mesh.conn, wdetJ, ref.phi, M, u)[0]
+    np.testing.assert_allclose(rw, Kw @ np.concatenate([ue[:, i] for i in range(3)]), atol=1e-12)
+
+
+def test_eval_mode_linear_fields_on_distorted_mesh(distorted):
+    """Integrals over the unit cube (total volume 1) of products of linear
+    fields, whose integrands are constants: the element values sum to them."""
+    mesh, ref, wdetJ, G, lam, mu = distorted
+    rng = np.random.default_rng(8)
+    A, Bm = rng.standard_normal((3, 3)), rng.standard_normal((3, 3))
+    a, b, c, d = (rng.standard_normal(3) for _ in range(4))
+    X = mesh.coords
+    ev = lambda kind, u, **kw: oracle.eval_form(kind, mesh.conn, wdetJ, G, ref.phi, u, **kw).sum(0)
+    # scalar Laplace: grad(a.x) . grad(b.x) = a . b
+    assert abs(ev("laplace", X @ a, w=X @ b)[0] - a @ b) <= 1e-12
+    # dot products of constants
+    assert abs(ev("mass", np.full(mesh.n_nodes, 2.0), w=np.full(mesh.n_nodes, 3.0), ncomp=1)[0] - 6.0) <= 1e-12
+    uc, wc = np.tile(c, mesh.n_nodes), np.tile(d, mesh.n_nodes)
+    assert abs(ev("mass", uc, w=wc)[0] - c @ d) <= 1e-12
+    Mw = np.broadcast_to(A, (mesh.n_elems, 3, 3)).copy()
+    assert abs(ev("wdot", uc, w=wc, mat=Mw)[0] - c @ A @ d) <= 1e-12
+    # linear vector fields u = A x, w = B x: eps(u) = sym(A) (engineering shear in Voigt)
+    uA, wB = (X @ A.T).reshape(-1), (X @ Bm.T).reshape(-1)
+    voigt = lambda F: np.array([F[0, 0], F[1, 1], F[2, 2], F[0, 1] + F[1, 0], F[0, 2] + F[2, 0], F[1, 2] + F[2, 1]])
+    D = oracle.lame_to_D(lam, mu)
+    got = oracle.eval_form("elasticity", mesh.conn, wdetJ, G, ref.phi, uA, w=wB, mat=D)[:, 0]
+    want = np.einsum("i,eij,j->e", voigt(A), D, voigt(Bm)) * wdetJ.sum(1)
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-14)
+    cau = oracle.eval_form("cauchy", mesh.conn, wdetJ, G, ref.phi, uA, mat=D)
+    np.testing.assert_allclose(cau, np.einsum("eij,j->ei", D, voigt(A)) * wdetJ.sum(1)[:, None], rtol=1e-11,
+                               atol=1e-14)
+    assert abs(ev("div", uA)[0] - np.trace(A)) <= 1e-12
+    assert abs(ev("stokes", uA, w=np.full(mesh.n_nodes, 2.0))[0] - 2 * np.trace(A)) <= 1e-12
+    # convection u_i (d w_i / d x_j) z_j with constant u, z and w = B x: c^T B d
+    assert abs(ev("convect", uc, w=wB, z=wc)[0] - c @ Bm @ d) <= 1e-12
+
+
+def test_eval_mode_equals_bilinear_form_of_the_matrices(distorted):
+    """eval(u, w) = w_e . K_e u_e for the Laplacian and elasticity, element by element."""
+    mesh, ref, wdetJ, G, lam, mu = distorted
+    rng = np.random.default_rng(9)
+    u, w = rng.standard_normal(mesh.n_nodes), rng.standard_normal(mesh.n_nodes)
+    K = oracle.matrix_laplace(wdetJ, G)
+    e1 = oracle.eval_form("laplace", mesh.conn, wdetJ, G, ref.phi, u, w=w)[:, 0]
+    np.testing.assert_allclose(e1, np.einsum("ea,eab,eb->e", w[mesh.conn], K, u[mesh.conn]), rtol=1e-11,
+                               atol=1e-13)
+    u3, w3 = rng.standard_normal(3 * mesh.n_nodes), rng.standard_normal(3 * mesh.n_nodes)
+    D = oracle.lame_to_D(lam, mu)
+    KE = oracle.matrix_elasticity(wdetJ, G, D)
+    e2 = oracle.eval_form("elasticity", mesh.conn, wdetJ, G, ref.phi, u3, w=w3, mat=D)[:, 0]
+    ue = np.concatenate([u3[3 * mesh.conn + i] for i in range(3)], 1)
+    we = np.concatenate([w3[3 * mesh.conn + i] for i in range(3)], 1)
+    np.testing.assert_allclose(e2, np.einsum("ea,eab,eb->e", we, KE, ue), rtol=1e-11, atol=1e-13)
