@@ -82,8 +82,9 @@ typedef enum { FE_VIRTUAL = 0, FE_STATE = 1, FE_PARAMETER = 2, FE_MATERIAL = 3 }
  *   FE_MAT_LAME    (n_elems, 2)    Lame pair (lambda, mu) per element; the elastic
  *                                  matrix is D = lambda m m^T + mu diag(2,2,2,1,1,1),
  *                                  m = (1,1,1,0,0,0)
- *   FE_MAT_D66     (n_elems, 6, 6) elastic matrix D per element, Voigt order */
-typedef enum { FE_MAT_NONE = 0, FE_MAT_SCALAR = 1, FE_MAT_LAME = 2, FE_MAT_D66 = 3 } fe_material_kind;
+ *   FE_MAT_D66     (n_elems, 6, 6) elastic matrix D per element, Voigt order
+ *   FE_MAT_M33     (n_elems, 3, 3) matrix M per element, row-major (weighted dot product) */
+typedef enum { FE_MAT_NONE = 0, FE_MAT_SCALAR = 1, FE_MAT_LAME = 2, FE_MAT_D66 = 3, FE_MAT_M33 = 4 } fe_material_kind;
 
 typedef struct {
     fe_role role;
@@ -239,12 +240,22 @@ fe_status fe_geometry_get(fe_ctx *ctx, const fe_geometry_h *geom, fe_geom_field 
  *   dot product / mass    "i,i" (ncomp 1 or 3), "0,0"  (VIRTUAL, STATE)
  *   weighted mass         "0,i,i", "0,0,0"             (MATERIAL SCALAR, VIRTUAL, STATE)
  *   linear elasticity     "IK,s(i:j)->I,s(k:l)->K"     (MATERIAL LAME or D66, VIRTUAL, STATE), ncomp 3
+ *   weighted dot product  "ij,i,j"                     (MATERIAL M33, VIRTUAL, STATE), ncomp 3
+ *   Stokes coupling       "i.i,0"                      (VIRTUAL vector, STATE scalar): int div(v) p
+ *   transposed coupling   "i.i,0"                      (STATE vector, VIRTUAL scalar): int q div(u)
+ *   divergence            "i.i"                        (VIRTUAL vector): int div(v), residual only
+ *   Cauchy stress         "IK,s(k:l)->K"               (MATERIAL LAME or D66, field): eval only
  *   Navier-Stokes         "i,i.j,j"                    (VIRTUAL, u, w), ncomp 3: int v_i (du_i/dx_j) w_j
  *   convection (Eq. fe2)  u and w each STATE or PARAMETER (at least one STATE);
  *                         (VIRTUAL, STATE, STATE) is the non-linear term with
  *                         w = u, whose matrix is the two-term derivative of
  *                         Eq. fe4; tensor-product hexahedra only (the basis
  *                         must carry its 1-D factors)
+ * Every form may also be compiled with no VIRTUAL operand, all its fields
+ * being FE_STATE or FE_PARAMETER: it is then an 'eval' form (Sec. 5.1,
+ * evaluation modes) for fe_eval_integral, the first field taking the test
+ * function's place.  Stokes coupling and its transpose use one basis for both
+ * fields (equal order).
  * `ctx` may be NULL: compilation is host-only.  The handle caches the plan
  * (Sec. 5.1: transpilation results are cached).  Errors: FE_ERR_INVALID_ARG
  * (syntax, roles, sizes), FE_ERR_UNSUPPORTED_SPEC (a valid expression with no
@@ -252,8 +263,11 @@ fe_status fe_geometry_get(fe_ctx *ctx, const fe_geometry_h *geom, fe_geom_field 
 fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_operand *ops, int n_ops, fe_form_h **out);
 fe_status fe_form_free(fe_form_h *form);
 
-/* Rows and columns of one element matrix of `form` for elements of n_basis
- * nodes: ncomp * n_basis each. */
+/* Rows and columns of one element matrix (rows: residual length) of `form`
+ * for elements of n_basis nodes: the test field's components times n_basis,
+ * the unknown's components times n_basis (0 for the divergence form, which
+ * has no unknown).  For an eval form: n_rows = values per element (1, or 6 for
+ * the Cauchy stress), n_cols = 0. */
 fe_status fe_form_shape(const fe_form_h *form, int n_basis, int *n_rows, int *n_cols);
 
 /* args[k] is the device array of operand k of the compiled expression:
@@ -310,6 +324,18 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
 fe_status fe_eval_residual_adjoint(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom,
                                    const void *const *args, const void *rbar, fe_precision prec, void *d_mat,
                                    void *d_x_e, fe_stream_t stream);
+
+/* 'eval' mode (Sec. 5.1): the integral over every element of an eval form,
+ * out (n_elems, n_rows of fe_form_shape) float64 for FE_F64 else float32,
+ * computed in that precision (FE_TF32X3/FE_BF16X3/FE_BF16 evaluate as FE_F32).
+ * args as fe_eval_residual (every field operand needs its DOF vector); the
+ * total over the mesh is the sum of the element values.  Forms: the weighted
+ * Laplacian, dot/mass, elasticity, weighted dot product, Stokes coupling,
+ * divergence, Cauchy stress (6 values: int D e(u), Voigt order) and the
+ * convective term.  Errors: FE_ERR_INVALID_ARG (a form with a test function,
+ * missing arrays), FE_ERR_SHAPE, FE_ERR_CUDA. */
+fe_status fe_eval_integral(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const void *const *args,
+                           fe_precision prec, void *out, fe_stream_t stream);
 
 /* ---- batched matrix mode ---------------------------------------------------------- */
 

@@ -336,7 +336,16 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
                                   form->wrt_adv, K_out, nullptr, ctx->d_status, s);
         return from_cuda(e, "fe_eval_matrix");
     }
+    if (form->eval || form->kind == FK_DIV || form->kind == FK_CAUCHY) return FE_ERR_INVALID_ARG;  // no unknown
     if (diff_op != form->state_op) return FE_ERR_INVALID_ARG;
+    if (form->kind == FK_WDOT || form->kind == FK_STOKES || form->kind == FK_STOKES_T) {
+        if (prec != FE_F64 && prec != FE_F32) return FE_ERR_UNSUPPORTED_SPEC;
+        e = settle_geometry(gm, ctx->d_status, s);
+        if (e == cudaSuccess)
+            e = fe_launch_generic(g, form, mat, prec == FE_F64, 1, nullptr, nullptr, nullptr, K_out, ctx->d_status,
+                                  s);
+        return from_cuda(e, "fe_eval_matrix");
+    }
     if (prec == FE_F64 || prec == FE_F32) {
         e = settle_geometry(gm, ctx->d_status, s);
         if (e == cudaSuccess) e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, s);
@@ -356,6 +365,17 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
     fe_material_args mat{};
     fe_status st = eval_common(ctx, form, g, args, prec, r_out, &mat);
     if (st) return st;
+    if (form->eval || form->kind == FK_CAUCHY) return FE_ERR_INVALID_ARG;  // no test function
+    if (form->kind == FK_WDOT || form->kind == FK_STOKES || form->kind == FK_STOKES_T || form->kind == FK_DIV) {
+        const bool empty = g->mesh.n_elems == 0;
+        const void *u = form->op_b >= 0 && args ? args[form->op_b] : nullptr;
+        if (form->kind != FK_DIV && !empty && !u) return FE_ERR_INVALID_ARG;
+        cudaStream_t s = to_cuda(stream);
+        cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, s);
+        if (e == cudaSuccess)
+            e = fe_launch_generic(g, form, mat, prec == FE_F64, 0, nullptr, u, nullptr, r_out, ctx->d_status, s);
+        return from_cuda(e, "fe_eval_residual");
+    }
     if (form->kind == FK_CONVECT) {
         if (!fe_convect_supported(g)) return FE_ERR_UNSUPPORTED_SPEC;
         const bool empty = g->mesh.n_elems == 0;
@@ -372,6 +392,28 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
     if (e == cudaSuccess) e = fe_launch_residual(g, form, mat, prec == FE_F64, args[form->state_op], r_out, ctx->d_status,
                                        to_cuda(stream));
     return from_cuda(e, "fe_eval_residual");
+}
+
+fe_status fe_eval_integral(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const void *const *args,
+                           fe_precision prec, void *out, fe_stream_t stream)
+{
+    fe_material_args mat{};
+    fe_status st = eval_common(ctx, form, g, args, prec, out, &mat);
+    if (st) return st;
+    if (!form->eval) return FE_ERR_INVALID_ARG;
+    const bool empty = g->mesh.n_elems == 0;
+    // fields in the kernel's slots; for the convective form the gradient and
+    // the advection operands
+    const int ob = form->kind == FK_CONVECT ? form->grad_op : form->op_b;
+    const int oc = form->kind == FK_CONVECT ? form->adv_op : form->op_c;
+    const void *f0 = args ? args[form->op_a] : nullptr;
+    const void *f1 = ob >= 0 && args ? args[ob] : nullptr;
+    const void *f2 = oc >= 0 && args ? args[oc] : nullptr;
+    if (!empty && (!f0 || (ob >= 0 && !f1) || (oc >= 0 && !f2))) return FE_ERR_INVALID_ARG;
+    cudaStream_t s = to_cuda(stream);
+    cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, s);
+    if (e == cudaSuccess) e = fe_launch_generic(g, form, mat, prec == FE_F64, 2, f0, f1, f2, out, ctx->d_status, s);
+    return from_cuda(e, "fe_eval_integral");
 }
 
 fe_status fe_eval_residual_adjoint(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g,

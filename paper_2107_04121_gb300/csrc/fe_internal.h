@@ -33,7 +33,17 @@ struct fe_geometry_h {
     int pending;  // deferred handle: the stored geometry is stale (host-side, stream-ordered use)
 };
 
-enum fe_form_kind { FK_LAPLACE = 0, FK_MASS = 1, FK_ELASTICITY = 2, FK_CONVECT = 3 };
+enum fe_form_kind {
+    FK_LAPLACE = 0,
+    FK_MASS = 1,
+    FK_ELASTICITY = 2,
+    FK_CONVECT = 3,
+    FK_WDOT = 4,      // 'ij,i,j'
+    FK_STOKES = 5,    // 'i.i,0' with the vector test function
+    FK_STOKES_T = 6,  // 'i.i,0' with the scalar test function
+    FK_DIV = 7,       // 'i.i'
+    FK_CAUCHY = 8     // 'IK,s(k:l)->K', eval only
+};
 
 struct fe_form_h {
     fe_form_kind kind;
@@ -49,6 +59,12 @@ struct fe_form_h {
     // operand among them (both for the non-linear term, Eq. fe4)
     int grad_op, adv_op;
     int wrt_grad, wrt_adv;
+    // 'eval' form (no test function): the first field plays the test slot;
+    // field operand indices in expression order (test slot, unknown, third)
+    int eval;
+    int op_a, op_b, op_c;
+    int ncomp_test, ncomp_trial;  // rows / columns of one element matrix per node
+    int n_out;                    // values per element in eval mode
 };
 
 struct fe_assembly_h {
@@ -79,6 +95,13 @@ cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_ma
 cudaError_t fe_launch_convect(const fe_geometry_h *g, bool f64, const void *u, const void *w, int wrt_grad,
                               int wrt_adv, void *K, void *r, unsigned long long *status, cudaStream_t s);
 bool fe_convect_supported(const fe_geometry_h *g);
+// Generic kernels (runtime N, Q) of the remaining forms and of eval mode:
+// mode 0 residual (out (E, ncomp_test N)), 1 matrix (out (E, rows, cols)),
+// 2 eval (out (E, n_out)).  f0, f1, f2: the DOF vectors of the form's field
+// operands op_a, op_b, op_c (null where absent).
+cudaError_t fe_launch_generic(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64, int mode,
+                              const void *f0, const void *f1, const void *f2, void *out, unsigned long long *status,
+                              cudaStream_t s);
 // Adjoint of the isotropic elasticity residual (sum factorisation, same (n1d,
 // nq1d) pairs as the convective kernels): d(rbar . R)/d(lambda_e, mu_e) into
 // dmat (E, 2) and per-element coordinate derivatives into dxe (E, 3 N); either

@@ -111,7 +111,8 @@ extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_ope
         const fe_operand &op = ops[k];
         if (op.role == FE_MATERIAL) {
             if (!parse_material(parts[k], subs[k])) return FE_ERR_INVALID_ARG;
-            if (op.material != FE_MAT_SCALAR && op.material != FE_MAT_LAME && op.material != FE_MAT_D66)
+            if (op.material != FE_MAT_SCALAR && op.material != FE_MAT_LAME && op.material != FE_MAT_D66 &&
+                op.material != FE_MAT_M33)
                 return FE_ERR_INVALID_ARG;
             if (im >= 0) return FE_ERR_UNSUPPORTED_SPEC;
             im = k;
@@ -134,59 +135,96 @@ extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_ope
             return FE_ERR_INVALID_ARG;
         }
     }
-    if (iv < 0 || states.empty()) return FE_ERR_UNSUPPORTED_SPEC;  // 'eval' mode / missing unknown
-
-    // Navier-Stokes convection v_i (du_i/dx_j) w_j: a vector test function, one
-    // gradient operand with the same component letter and one advection operand
-    // carrying the derivative letter; u and w are each FE_STATE or FE_PARAMETER
-    if (im < 0 && n_ops == 3 && states.size() + params.size() == 2 && subs[iv].kind == SK_VEC && ops[iv].ncomp == 3) {
-        int og = -1, oa = -1;
-        for (int k = 0; k < n_ops; ++k) {
-            if (k == iv) continue;
-            if (subs[k].kind == SK_VEC_GRAD) og = k;
-            else if (subs[k].kind == SK_VEC) oa = k;
-        }
-        if (og >= 0 && oa >= 0 && ops[og].ncomp == 3 && ops[oa].ncomp == 3) {
-            const Sub &V = subs[iv], &Gs = subs[og], &A = subs[oa];
-            if (Gs.a == V.a && A.a == Gs.b && Gs.a != Gs.b) {
-                fe_form_h f{};
-                f.kind = FK_CONVECT;
-                f.n_ops = n_ops;
-                f.virtual_op = iv;
-                f.state_op = states[0];
-                f.mat_op = -1;
-                f.mat = FE_MAT_NONE;
-                f.ncomp = 3;
-                f.grad_op = og;
-                f.adv_op = oa;
-                f.wrt_grad = ops[og].role == FE_STATE;
-                f.wrt_adv = ops[oa].role == FE_STATE;
-                fe_form_h *h = new (std::nothrow) fe_form_h(f);
-                if (!h) return FE_ERR_OOM;
-                *out = h;
-                return FE_OK;
-            }
-        }
-        return FE_ERR_UNSUPPORTED_SPEC;
-    }
-    // the linear forms: one unknown, no known fields
-    if (states.size() != 1 || !params.empty()) return FE_ERR_UNSUPPORTED_SPEC;
-    const int is = states[0];
-
-    const Sub &V = subs[iv], &S = subs[is];
-    const int nc = ops[iv].ncomp;
-    if (ops[is].ncomp != nc) return FE_ERR_UNSUPPORTED_SPEC;
+    // field operands in expression order; without a test function the form is
+    // an 'eval' form and its first field takes the test function's place
+    std::vector<int> fields;
+    for (int k = 0; k < n_ops; ++k)
+        if (ops[k].role != FE_MATERIAL) fields.push_back(k);
+    if (fields.empty()) return FE_ERR_UNSUPPORTED_SPEC;
+    const bool eval = iv < 0;
+    const int ia = eval ? fields[0] : iv;
+    std::vector<int> rest;
+    for (int k : fields)
+        if (k != ia) rest.push_back(k);
 
     fe_form_h f{};
     f.n_ops = n_ops;
     f.virtual_op = iv;
-    f.state_op = is;
+    f.state_op = states.empty() ? -1 : states[0];
     f.mat_op = im;
     f.mat = im >= 0 ? ops[im].material : FE_MAT_NONE;
-    f.ncomp = nc;
+    f.ncomp = ops[ia].ncomp;
     f.mat_transposed = 0;
     f.grad_op = f.adv_op = -1;
+    f.eval = eval;
+    f.op_a = ia;
+    f.op_b = rest.empty() ? -1 : rest[0];
+    f.op_c = rest.size() > 1 ? rest[1] : -1;
+    f.ncomp_test = ops[ia].ncomp;
+    f.ncomp_trial = rest.empty() ? 0 : ops[rest[0]].ncomp;
+    f.n_out = 1;
+    const Sub &V = subs[ia];
     bool ok = false;
+
+    auto finish = [&]() -> fe_status {
+        fe_form_h *h = new (std::nothrow) fe_form_h(f);
+        if (!h) return FE_ERR_OOM;
+        *out = h;
+        return FE_OK;
+    };
+
+    // Navier-Stokes convection v_i (du_i/dx_j) w_j: a vector test slot, one
+    // gradient operand with its component letter and one advection operand
+    // carrying the derivative letter; u and w are each FE_STATE or FE_PARAMETER
+    if (im < 0 && rest.size() == 2 && V.kind == SK_VEC && ops[ia].ncomp == 3) {
+        int og = -1, oa = -1;
+        for (int k : rest) {
+            if (subs[k].kind == SK_VEC_GRAD) og = k;
+            else if (subs[k].kind == SK_VEC) oa = k;
+        }
+        if (og >= 0 && oa >= 0 && ops[og].ncomp == 3 && ops[oa].ncomp == 3) {
+            const Sub &Gs = subs[og], &A = subs[oa];
+            if (Gs.a == V.a && A.a == Gs.b && Gs.a != Gs.b) {
+                f.kind = FK_CONVECT;
+                f.grad_op = og;
+                f.adv_op = oa;
+                f.wrt_grad = ops[og].role == FE_STATE;
+                f.wrt_adv = ops[oa].role == FE_STATE;
+                f.state_op = states.empty() ? -1 : states[0];
+                f.ncomp_trial = 3;
+                if (!eval && states.empty()) return FE_ERR_UNSUPPORTED_SPEC;
+                return finish();
+            }
+        }
+        return FE_ERR_UNSUPPORTED_SPEC;
+    }
+    // divergence div(v): a single vector field with the trace symbol
+    if (im < 0 && rest.empty()) {
+        if (V.kind == SK_VEC_GRAD && V.a == V.b && ops[ia].ncomp == 3) {
+            f.kind = FK_DIV;
+            return finish();
+        }
+        return FE_ERR_UNSUPPORTED_SPEC;
+    }
+    // Cauchy stress D_IK e_K(u): evaluated only (it has no test function)
+    if (im >= 0 && rest.empty()) {
+        const std::string &L = subs[im].letters;
+        if (eval && V.kind == SK_VOIGT && ops[ia].ncomp == 3 && L.size() == 2 && L[0] != L[1] &&
+            (ops[im].material == FE_MAT_LAME || ops[im].material == FE_MAT_D66) && V.a != V.b && V.a != V.c &&
+            V.b != V.c && (L[1] == V.c || L[0] == V.c)) {
+            f.kind = FK_CAUCHY;
+            f.mat_transposed = L[0] == V.c;
+            f.n_out = 6;
+            return finish();
+        }
+        return FE_ERR_UNSUPPORTED_SPEC;
+    }
+    if (rest.size() != 1) return FE_ERR_UNSUPPORTED_SPEC;
+    // bilinear forms: the weak forms need one unknown and no known field
+    const int ib = rest[0];
+    if (!eval && (states.size() != 1 || !params.empty() || states[0] != ib)) return FE_ERR_UNSUPPORTED_SPEC;
+    const Sub &S = subs[ib];
+    const int nc = ops[ia].ncomp;
     const bool scalar_mat = im < 0 || (subs[im].letters.empty() && ops[im].material == FE_MAT_SCALAR);
 
     // weak Laplacian: grad v . grad u, with an optional scalar coefficient
@@ -195,13 +233,37 @@ extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_ope
         ok = true;
     }
     // dot product / mass: v_i u_i or scalar v u, optional scalar coefficient
-    if (!ok && scalar_mat &&
+    if (!ok && scalar_mat && ops[ib].ncomp == nc &&
         ((V.kind == SK_SCALAR && S.kind == SK_SCALAR) || (V.kind == SK_VEC && S.kind == SK_VEC && V.a == S.a))) {
         f.kind = FK_MASS;
         ok = true;
     }
+    // weighted dot product v_i M_ij u_j
+    if (!ok && im >= 0 && ops[im].material == FE_MAT_M33 && V.kind == SK_VEC && S.kind == SK_VEC && V.a != S.a &&
+        nc == 3 && ops[ib].ncomp == 3) {
+        const std::string &L = subs[im].letters;
+        if (L.size() == 2 && L[0] == V.a && L[1] == S.a) {
+            f.kind = FK_WDOT;
+            ok = true;
+        } else if (L.size() == 2 && L[0] == S.a && L[1] == V.a) {
+            f.kind = FK_WDOT;
+            f.mat_transposed = 1;
+            ok = true;
+        }
+    }
+    // Stokes coupling div(v) p and its transpose q div(u)
+    if (!ok && im < 0 && V.kind == SK_VEC_GRAD && V.a == V.b && nc == 3 && S.kind == SK_SCALAR &&
+        ops[ib].ncomp == 1) {
+        f.kind = FK_STOKES;
+        ok = true;
+    }
+    if (!ok && im < 0 && V.kind == SK_SCALAR && nc == 1 && S.kind == SK_VEC_GRAD && S.a == S.b &&
+        ops[ib].ncomp == 3) {
+        f.kind = FK_STOKES_T;
+        ok = true;
+    }
     // linear elasticity: D_IK e_I(v) e_K(u) in Voigt storage
-    if (!ok && im >= 0 && V.kind == SK_VOIGT && S.kind == SK_VOIGT && nc == 3 &&
+    if (!ok && im >= 0 && V.kind == SK_VOIGT && S.kind == SK_VOIGT && nc == 3 && ops[ib].ncomp == 3 &&
         (ops[im].material == FE_MAT_LAME || ops[im].material == FE_MAT_D66) && subs[im].letters.size() == 2) {
         const std::string &L = subs[im].letters;
         // the symmetric-gradient letters are bound inside s(...): all four distinct,
@@ -223,10 +285,7 @@ extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_ope
         }
     }
     if (!ok) return FE_ERR_UNSUPPORTED_SPEC;
-    fe_form_h *h = new (std::nothrow) fe_form_h(f);
-    if (!h) return FE_ERR_OOM;
-    *out = h;
-    return FE_OK;
+    return finish();
 }
 
 extern "C" fe_status fe_form_free(fe_form_h *form)
@@ -238,7 +297,12 @@ extern "C" fe_status fe_form_free(fe_form_h *form)
 extern "C" fe_status fe_form_shape(const fe_form_h *form, int n_basis, int *n_rows, int *n_cols)
 {
     if (!form || n_basis < 1) return FE_ERR_INVALID_ARG;
-    if (n_rows) *n_rows = form->ncomp * n_basis;
-    if (n_cols) *n_cols = form->ncomp * n_basis;
+    if (form->eval) {
+        if (n_rows) *n_rows = form->n_out;
+        if (n_cols) *n_cols = 0;
+        return FE_OK;
+    }
+    if (n_rows) *n_rows = form->ncomp_test * n_basis;
+    if (n_cols) *n_cols = form->kind == FK_DIV ? 0 : form->ncomp_trial * n_basis;
     return FE_OK;
 }

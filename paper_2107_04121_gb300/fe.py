@@ -24,7 +24,7 @@ FE_ERR_NONPOSITIVE_DETJ, FE_ERR_NONFINITE, FE_ERR_OOM, FE_ERR_CUDA, FE_ERR_TIMEO
 F64, F32, TF32X3, BF16X3, BF16 = 0, 1, 2, 3, 4
 PRECISIONS = {"f64": F64, "f32": F32, "tf32x3": TF32X3, "bf16x3": BF16X3, "bf16": BF16}
 VIRTUAL, STATE, PARAMETER, MATERIAL = 0, 1, 2, 3
-MAT_NONE, MAT_SCALAR, MAT_LAME, MAT_D66 = 0, 1, 2, 3
+MAT_NONE, MAT_SCALAR, MAT_LAME, MAT_D66, MAT_M33 = 0, 1, 2, 3, 4
 GEOM_STORE_F64, GEOM_STORE_F32, GEOM_DEFERRED = 1, 2, 4
 GEOM_WDETJ, GEOM_JINV, GEOM_G = 0, 1, 2
 ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
@@ -33,7 +33,8 @@ BATCH_GEOMETRY, BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2, 4
 EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
     "fe_refbasis_hex", "fe_refbasis_hex_1d", "fe_refbasis_tet", "fe_gm_rule_size", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
-    "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_eval_residual_adjoint", "fe_assembly_create",
+    "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_eval_integral", "fe_eval_residual_adjoint",
+    "fe_assembly_create",
     "fe_assembly_free",
     "fe_assemble_vector", "fe_assemble_vector_noalloc", "fe_batch_create", "fe_batch_run", "fe_batch_describe",
     "fe_batch_free",
@@ -108,6 +109,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_eval_matrix.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, i, vp, vp]
     L.fe_eval_residual.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, vp, vp]
     L.fe_eval_residual_adjoint.argtypes = [vp, vp, vp, ctypes.POINTER(vp), vp, i, vp, vp, vp]
+    L.fe_eval_integral.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, vp, vp]
     L.fe_batch_create.argtypes = [vp, ctypes.POINTER(_BatchItem), i, ctypes.c_uint, ctypes.POINTER(vp), vp]
     L.fe_batch_run.argtypes = [vp, vp, vp]
     L.fe_batch_describe.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -319,7 +321,8 @@ def tet_geometry(ctx: Context, mesh: Mesh, p: int, s: int = None, flags: int = 0
 class Form:
     def __init__(self, expr, operands, handle):
         self.expr, self.operands, self._h = expr, operands, handle
-        self.state_op = [k for k, o in enumerate(operands) if o[0] == STATE][0]
+        states = [k for k, o in enumerate(operands) if o[0] == STATE]
+        self.state_op = states[0] if states else None
 
     def shape(self, n_basis):
         r, c = ctypes.c_int(), ctypes.c_int()
@@ -348,7 +351,7 @@ def form_compile(expr: str, operands, ctx: Context | None = None) -> Form:
     return Form(expr, list(operands), h)
 
 
-_MAT_SIZE = {MAT_SCALAR: 1, MAT_LAME: 2, MAT_D66: 36}
+_MAT_SIZE = {MAT_SCALAR: 1, MAT_LAME: 2, MAT_D66: 36, MAT_M33: 9}
 
 
 def _args(form: Form, args, geom: Geometry, dtype=None):
@@ -410,6 +413,23 @@ def eval_residual(ctx: Context, form: Form, geom: Geometry, args, precision="f64
     _check(_lib.fe_eval_residual(ctx.handle, form._h, geom._h, _args(form, args, geom, _out_dtype(precision)),
                                  _prec(precision),
                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "fe_eval_residual")
+    return out
+
+
+def eval_integral(ctx: Context, form: Form, geom: Geometry, args, precision="f64", out=None, stream=None):
+    """fe_eval_integral ('eval' mode): element integrals (E, n_values) of a form
+    whose operands all carry DOFs."""
+    import torch
+    nv, _ = form.shape(geom.N)
+    E = geom.mesh.n_elems
+    if out is None:
+        out = torch.empty((E, nv), dtype=_out_dtype(precision), device=geom.mesh.coords.device)
+    _dev(out, _out_dtype(precision), "out")
+    if tuple(out.shape) != (E, nv):
+        raise ValueError("out must have shape %s" % ((E, nv),))
+    _check(_lib.fe_eval_integral(ctx.handle, form._h, geom._h, _args(form, args, geom, _out_dtype(precision)),
+                                 _prec(precision), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "fe_eval_integral")
     return out
 
 

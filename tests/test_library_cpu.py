@@ -91,23 +91,42 @@ NONE, SC, LAME, D66 = fe.MAT_NONE, fe.MAT_SCALAR, fe.MAT_LAME, fe.MAT_D66
     ("i,i.j,j", [(V, 3, NONE), (S, 3, NONE), (PA, 3, NONE)], 24),
     ("i,i.j,j", [(V, 3, NONE), (PA, 3, NONE), (S, 3, NONE)], 24),
     ("a,b,a.b", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], 24),
+    ("ij,i,j", [(M, 1, fe.MAT_M33), (V, 3, NONE), (S, 3, NONE)], 24),
+    ("ji,i,j", [(M, 1, fe.MAT_M33), (V, 3, NONE), (S, 3, NONE)], 24),
 ])
 def test_form_compile_accepts_tab_ewfd_forms(libfe, expr, ops, shape):
     f = fe.form_compile(expr, ops)
     assert f.shape(8) == (shape, shape)
 
 
+@pytest.mark.parametrize("expr,ops,shape", [
+    ("i.i,0", [(V, 3, NONE), (S, 1, NONE)], (24, 8)),          # Stokes coupling (v, p)
+    ("i.i,0", [(S, 3, NONE), (V, 1, NONE)], (8, 24)),          # transposed coupling (u, q)
+    ("0,i.i", [(V, 1, NONE), (S, 3, NONE)], (8, 24)),
+    ("i.i", [(V, 3, NONE)], (24, 0)),                          # divergence: residual only
+    # eval forms: no test function
+    ("0.i,0.i", [(PA, 1, NONE), (PA, 1, NONE)], (1, 0)),
+    ("i,i", [(S, 3, NONE), (PA, 3, NONE)], (1, 0)),
+    ("IK,s(i:j)->I,s(k:l)->K", [(M, 1, LAME), (PA, 3, NONE), (PA, 3, NONE)], (1, 0)),
+    ("IK,s(k:l)->K", [(M, 1, D66), (PA, 3, NONE)], (6, 0)),    # Cauchy stress
+    ("i.i", [(PA, 3, NONE)], (1, 0)),
+    ("i,i.j,j", [(PA, 3, NONE), (PA, 3, NONE), (PA, 3, NONE)], (1, 0)),
+])
+def test_form_compile_accepts_mixed_and_eval_forms(libfe, expr, ops, shape):
+    f = fe.form_compile(expr, ops)
+    assert f.shape(8) == shape
 @pytest.mark.parametrize("expr,ops,code", [
-    # valid notation, no kernel: weighted dot, Stokes, divergence, ...
-    ("i,i.j,j", [(V, 3, NONE), (PA, 3, NONE), (PA, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),  # eval mode
+    # valid notation, no kernel
+    ("i,i.j,j", [(V, 3, NONE), (PA, 3, NONE), (PA, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),  # no unknown
     ("i,i.j,i", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
     ("j,i.j,i", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
     ("i,i.i,i", [(V, 3, NONE), (S, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
     ("i,i,i", [(V, 3, NONE), (S, 3, NONE), (PA, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
-    ("ij,i,j", [(M, 1, D66), (V, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
-    ("i.i,0", [(V, 3, NONE), (S, 1, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
-    ("i.i", [(V, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
-    ("IK,s(k:l)->K", [(M, 1, D66), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),  # Cauchy stress: eval only
+    ("ij,i,j", [(M, 1, D66), (V, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),  # needs M33
+    ("ij,i,j", [(M, 1, fe.MAT_M33), (V, 3, NONE), (PA, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),  # no unknown
+    ("i.j,0", [(V, 3, NONE), (S, 1, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
+    ("i.i", [(V, 1, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
+    ("IK,s(k:l)->K", [(M, 1, D66), (V, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),  # Cauchy stress: eval only
     ("0.i,0.j", [(V, 1, NONE), (S, 1, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
     ("IK,s(i:j)->I,s(i:j)->K", [(M, 1, LAME), (V, 3, NONE), (S, 3, NONE)], fe.FE_ERR_UNSUPPORTED_SPEC),
     # malformed
