@@ -312,11 +312,14 @@ def sampled_errors(wl, precs, ref):
     return out, len(idx)
 
 
-def e2e_measure(wl, prec, steps):
+def e2e_measure(wl, prec, steps, chunks=8):
     """Same step through the public API with host buffers: pinned H2D of the inputs
     (coordinates, connectivity, materials, DOFs) and D2H of every result (K_e, r_e,
-    assembled vector), all inside the CUDA-event timed region."""
-    torch = wl.torch
+    assembled vector), all inside the CUDA-event timed region.  The mesh is
+    evaluated in `chunks` element ranges (geometry views) so that the transfer of
+    one range's K_e, on a second stream, overlaps the evaluation of the next: the
+    step is bound by the device-to-host link."""
+    torch, fe = wl.torch, wl.fe
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     h_in = [pin(wl.mesh.coords), pin(wl.mesh.conn), pin(np.stack([wl.lam, wl.mu], 1)),
             pin(wl.u.astype(np.float32) if prec != "f64" else wl.u)]
@@ -327,13 +330,34 @@ def e2e_measure(wl, prec, steps):
              torch.empty(g.shape, dtype=g.dtype).pin_memory()]
     h2d = sum(t.numel() * t.element_size() for t in h_in)
     d2h = sum(t.numel() * t.element_size() for t in h_out)
+    geom = wl.geoms["f64" if prec == "f64" else "f32"]
+    E = wl.E
+    EC = (E + chunks - 1) // chunks
+    ranges = [(e0, min(E, e0 + EC)) for e0 in range(0, E, EC)]
+    views = [geom.view(e0, e1 - e0) for e0, e1 in ranges]
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
 
     def one():
         for d, h in zip(d_in, h_in):
             d.copy_(h, non_blocking=True)
-        wl.step(prec)
-        for h, d in zip(h_out, (K, r, g)):
-            h.copy_(d, non_blocking=True)
+        for (e0, e1), v in zip(ranges, views):
+            v.update()  # FP64 geometry of this element range
+            fe.eval_matrix(wl.ctx, wl.form, v, [wl.mat[e0:e1], None, None], prec, out=K[e0:e1])
+            ev = torch.cuda.Event()
+            ev.record(comp)
+            copy.wait_event(ev)
+            with torch.cuda.stream(copy):
+                h_out[0][e0:e1].copy_(K[e0:e1], non_blocking=True)
+        fe.eval_residual(wl.ctx, wl.form, geom, [wl.mat, None, u_dev], prec, out=r)
+        fe.assemble_vector(wl.ctx, wl.asm, 3, r, prec, out=g, flags=0 if prec == "f64" else fe.ASSEMBLE_COMPENSATED)
+        ev = torch.cuda.Event()
+        ev.record(comp)
+        copy.wait_event(ev)
+        with torch.cuda.stream(copy):
+            h_out[1].copy_(r, non_blocking=True)
+            h_out[2].copy_(g, non_blocking=True)
+        comp.wait_stream(copy)
 
     one()
     torch.cuda.synchronize()
@@ -346,8 +370,12 @@ def e2e_measure(wl, prec, steps):
     b.synchronize()
     wl.ctx.check()
     ms = a.elapsed_time(b) / steps
+    for v in views:
+        v.free()
     return {"value": wl.E / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h}
+            "d2h_bytes_per_step": d2h, "chunks": len(ranges),
+            "note": "bound by the device-to-host link (about 194 GB/s for pinned copies and for SM stores to "
+                    "host memory on this machine)"}
 
 
 class ConvectWorkload:

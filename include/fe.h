@@ -213,6 +213,17 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
                       unsigned flags, fe_geometry_h **out, fe_stream_t stream);
 fe_status fe_geometry_free(fe_geometry_h *geom);
 
+/* A handle for the elements [e_begin, e_begin + e_count) of `parent` that
+ * aliases its stored geometry (no copy, no allocation of device memory): every
+ * evaluation call takes it like any geometry, and fe_geometry_update on it
+ * recomputes only its range.  Useful to evaluate a mesh in chunks, e.g. to
+ * overlap the transfer of one chunk's element matrices with the evaluation of
+ * the next.  The parent must outlive the view and must not be deferred; free
+ * the view with fe_geometry_free (which then frees nothing else).  Errors:
+ * FE_ERR_INVALID_ARG (range outside the parent, deferred parent), FE_ERR_OOM. */
+fe_status fe_geometry_view(fe_ctx *ctx, const fe_geometry_h *parent, long long e_begin, long long e_count,
+                           fe_geometry_h **out);
+
 /* Recompute the geometry of `geom` in place from the current contents of its
  * (borrowed) mesh arrays, e.g. after the nodal coordinates moved; no device
  * memory is allocated.  Same kernel and status reporting as fe_geometry.

@@ -58,6 +58,10 @@ bool valid_mesh(const fe_mesh *m)
 void free_geometry(fe_geometry_h *g)
 {
     if (!g) return;
+    if (g->is_view) {
+        delete g;
+        return;
+    }
     cudaFree(g->d_phi64);
     cudaFree(g->d_dphi64);
     cudaFree(g->d_w64);
@@ -238,6 +242,28 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
         return st;
     }
     *out = g;
+    return FE_OK;
+}
+
+fe_status fe_geometry_view(fe_ctx *ctx, const fe_geometry_h *parent, long long e_begin, long long e_count,
+                           fe_geometry_h **out)
+{
+    if (!ctx || !parent || !out || e_begin < 0 || e_count < 0 || e_begin + e_count > parent->mesh.n_elems)
+        return FE_ERR_INVALID_ARG;
+    if (parent->flags & FE_GEOM_DEFERRED) return FE_ERR_INVALID_ARG;  // views share computed storage
+    *out = nullptr;
+    fe_geometry_h *v = new (std::nothrow) fe_geometry_h(*parent);
+    if (!v) return FE_ERR_OOM;
+    const int N = parent->N, Q = parent->Q;
+    v->is_view = 1;
+    v->pending = 0;
+    v->mesh.conn = parent->mesh.conn ? parent->mesh.conn + e_begin * N : nullptr;
+    v->mesh.n_elems = e_count;
+    if (v->d_jinv64) v->d_jinv64 += e_begin * Q * 9;
+    if (v->d_wdetj64) v->d_wdetj64 += e_begin * Q;
+    if (v->d_jinv32) v->d_jinv32 += e_begin * Q * 9;
+    if (v->d_wdetj32) v->d_wdetj32 += e_begin * Q;
+    *out = v;
     return FE_OK;
 }
 

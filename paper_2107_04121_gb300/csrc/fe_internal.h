@@ -31,6 +31,7 @@ struct fe_geometry_h {
     double *d_jinv64, *d_wdetj64;  // (E,Q,3,3), (E,Q)
     float *d_jinv32, *d_wdetj32;
     int pending;  // deferred handle: the stored geometry is stale (host-side, stream-ordered use)
+    int is_view;  // aliases a parent's storage for a range of its elements (owns nothing)
 };
 
 enum fe_form_kind {

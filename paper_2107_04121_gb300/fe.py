@@ -32,7 +32,8 @@ BATCH_GEOMETRY, BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2, 4
 
 EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
-    "fe_refbasis_hex", "fe_refbasis_hex_1d", "fe_refbasis_tet", "fe_gm_rule_size", "fe_geometry", "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
+    "fe_refbasis_hex", "fe_refbasis_hex_1d", "fe_refbasis_tet", "fe_gm_rule_size", "fe_geometry", "fe_geometry_view",
+    "fe_geometry_update", "fe_geometry_free", "fe_geometry_get", "fe_form_compile", "fe_form_free",
     "fe_form_shape", "fe_eval_matrix", "fe_eval_residual", "fe_eval_integral", "fe_eval_residual_adjoint",
     "fe_assembly_create",
     "fe_assembly_free",
@@ -101,6 +102,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_geometry.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(_RefBasis), ctypes.POINTER(_Quad),
                               ctypes.c_uint, ctypes.POINTER(vp), vp]
     L.fe_geometry_update.argtypes = [vp, vp, vp]
+    L.fe_geometry_view.argtypes = [vp, vp, ctypes.c_longlong, ctypes.c_longlong, ctypes.POINTER(vp)]
     L.fe_geometry_free.argtypes = [vp]
     L.fe_geometry_get.argtypes = [vp, vp, i, i, vp, vp]
     L.fe_form_compile.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(_Operand), i, ctypes.POINTER(vp)]
@@ -269,6 +271,17 @@ class Geometry:
     def update(self, stream=None):
         """fe_geometry_update: recompute in place from the mesh's current coordinates."""
         _check(_lib.fe_geometry_update(self.ctx.handle, self._h, _stream_ptr(stream)), "fe_geometry_update")
+
+    def view(self, e_begin: int, e_count: int) -> "Geometry":
+        """fe_geometry_view: the elements [e_begin, e_begin + e_count), aliasing this
+        handle's storage (keep this handle alive while the view is used)."""
+        h = ctypes.c_void_p()
+        _check(_lib.fe_geometry_view(self.ctx.handle, self._h, e_begin, e_count, ctypes.byref(h)),
+               "fe_geometry_view")
+        sub = Mesh(self.mesh.coords, self.mesh.conn[e_begin:e_begin + e_count])
+        g = Geometry(self.ctx, sub, h, self.N, self.Q)
+        g._parent = self
+        return g
 
     def free(self):
         if self._h:

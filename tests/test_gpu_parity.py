@@ -362,3 +362,28 @@ def test_results_are_deterministic(ctx):
     r1 = fe.eval_residual(ctx, form, P.geom, args, "f32")
     r2 = fe.eval_residual(ctx, form, P.geom, args, "f32")
     assert torch.equal(K1, K2) and torch.equal(r1, r2)
+
+
+def test_geometry_views_evaluate_element_ranges(ctx):
+    """A view over an element range aliases the parent's geometry: its matrices
+    and residuals equal the parent's on that range bit for bit, and updating a
+    view recomputes its range only."""
+    mesh = meshgen.structured_hex(5, 4, 3, 2, 0.15, 7)
+    lam, mu = meshgen.lame_materials(mesh)
+    P = Problem(ctx, mesh, 2, 3)
+    form = fe.elasticity_form(fe.MAT_LAME)
+    mat = _t(np.stack([lam, mu], 1), torch.float64)
+    u = _t(meshgen.normal_dofs(mesh, 3), torch.float32)
+    K = fe.eval_matrix(ctx, form, P.geom, [mat, None, None], "f32")
+    r = fe.eval_residual(ctx, form, P.geom, [mat, None, u], "f32")
+    for e0, n in ((0, 7), (7, 30), (37, mesh.n_elems - 37)):
+        v = P.geom.view(e0, n)
+        v.update()
+        Kv = fe.eval_matrix(ctx, form, v, [mat[e0:e0 + n], None, None], "f32")
+        rv = fe.eval_residual(ctx, form, v, [mat[e0:e0 + n], None, u], "f32")
+        ctx.check()
+        assert torch.equal(Kv, K[e0:e0 + n])
+        assert torch.equal(rv, r[e0:e0 + n])
+        v.free()
+    with pytest.raises(fe.FEError):
+        P.geom.view(mesh.n_elems - 2, 3)
