@@ -44,7 +44,7 @@ constexpr int TC_KPAD = 32;      // quadrature points, padded
 constexpr int TC_TMEM_COLS = 128;
 constexpr int TC_NROW = 3 * TC_N;  // 81
 constexpr int TC_JW_STRIDE = 12;  // floats per point of the staged sqrt(w det J) J^-1 (16-byte rows)
-constexpr int TC_EX_STRIDE = 36;  // floats per row of the exchange blocks (16-byte rows)
+constexpr int TC_EX_STRIDE = 28;  // floats per row of the exchange blocks (16-byte rows, conflict-free float4)
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;  // about two seconds at 2 GHz
 
 enum TcMode { TC_TF32X3 = 0, TC_BF16X3 = 1, TC_BF16 = 2 };
@@ -250,31 +250,31 @@ __device__ __forceinline__ void offdiag_block(const float *own, const float *__r
     for (int b = 0; b < TC_N; ++b) col[b * TC_NROW] = t[b];
 }
 
-// 28 columns per block (the last is padding) as 16-byte stores
-template <int I>
+// The two accumulator blocks a consumer warp uses are in registers: d[0..31] =
+// its diagonal block A_II, d[32..63] = A_I,I+1.  28 columns per block (the last
+// is padding) go to the exchange area as 16-byte stores.
 __device__ __forceinline__ void publish_blocks(const float *d, float *__restrict__ e0, float *__restrict__ e1)
 {
-    constexpr int J = 32 * I, K1 = 32 * ((I + 1) % 3);
 #pragma unroll
     for (int c = 0; c < 7; ++c)
-        reinterpret_cast<float4 *>(e0)[c] = make_float4(d[J + 4 * c], d[J + 4 * c + 1], d[J + 4 * c + 2], d[J + 4 * c + 3]);
+        reinterpret_cast<float4 *>(e0)[c] = make_float4(d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
 #pragma unroll
     for (int c = 0; c < 7; ++c)
         reinterpret_cast<float4 *>(e1)[c] =
-            make_float4(d[K1 + 4 * c], d[K1 + 4 * c + 1], d[K1 + 4 * c + 2], d[K1 + 4 * c + 3]);
+            make_float4(d[32 + 4 * c], d[32 + 4 * c + 1], d[32 + 4 * c + 2], d[32 + 4 * c + 3]);
 }
 
-// Blocks K_ii and K_i,i+1 of row (I, a) and the mirror column of K_i+1,i.
-template <int I, int STRIDE>
-__device__ __forceinline__ void epilogue_rows(const float *d, const float *ex, int a, float lam, float mu,
+// Blocks K_ii and K_i,i+1 of row (i, a) and the mirror column of K_i+1,i.
+template <int STRIDE>
+__device__ __forceinline__ void epilogue_rows(int I, const float *d, const float *ex, int a, float lam, float mu,
                                               float *kst)
 {
-    constexpr int Kb = (I + 1) % 3, Mb = (I + 2) % 3;
+    const int Kb = I == 2 ? 0 : I + 1, Mb = I == 0 ? 2 : I - 1;
     // K_ii[a][b] = (lambda + mu) A_ii[a][b] + mu (A_ii + A_kk + A_mm)[a][b]
-    diag_block<STRIDE>(d + 32 * I, ex + ((Kb * 2) * TC_N + a) * STRIDE, ex + ((Mb * 2) * TC_N + a) * STRIDE, lam,
-                       mu, kst + (I * TC_N + a) * TC_NROW + I * TC_N);
+    diag_block<STRIDE>(d, ex + ((Kb * 2) * TC_N + a) * STRIDE, ex + ((Mb * 2) * TC_N + a) * STRIDE, lam, mu,
+                       kst + (I * TC_N + a) * TC_NROW + I * TC_N);
     // K_ik[a][b] = lambda A_ik[a][b] + mu A_ik[b][a]; K_ki[b][a] = K_ik[a][b]
-    offdiag_block<STRIDE>(d + 32 * Kb, ex + ((I * 2 + 1) * TC_N) * STRIDE + a, lam, mu,
+    offdiag_block<STRIDE>(d + 32, ex + ((I * 2 + 1) * TC_N) * STRIDE + a, lam, mu,
                           kst + (I * TC_N + a) * TC_NROW + Kb * TC_N, kst + (Kb * TC_N) * TC_NROW + I * TC_N + a);
 }
 
@@ -282,7 +282,7 @@ template <int MODE>
 struct TcSmem {
     static constexpr int EB = MODE == TC_TF32X3 ? 4 : 2;
     using L = OpLayout<EB>;
-    // per buffer: hi and lo operands; the exchange area [3 warps][2 blocks][27][36]
+    // per buffer: hi and lo operands; the exchange area [3 warps][2 blocks][27][28]
     // floats of the epilogue reuses them once the buffer's MMAs have completed
     static constexpr int EX_STRIDE = TC_EX_STRIDE;
     static constexpr int EX_BYTES = 6 * TC_N * EX_STRIDE * 4;
@@ -291,11 +291,20 @@ struct TcSmem {
     static constexpr int LO = L::BYTES;
     static constexpr int KS = 2 * BUF;                                  // K staging: 6561 + 4 floats
     static constexpr int KS_BYTES = (TC_NROW * TC_NROW + 4) * 4;
+    // grad_xi phi (27 x 3 x 27 floats) is read into the producers' registers before
+    // the first element, and the first K staging write waits for the first MMA:
+    // the table lives in the staging area
+    static constexpr int DP = KS;
+    static_assert(TC_Q * 3 * TC_N * 4 <= KS_BYTES, "reference gradients fit the staging area");
     static constexpr int JW = (KS + KS_BYTES + 15) / 16 * 16;          // [2][27][12] sqrt(w det J) J^-1
     static constexpr int LM = JW + 2 * TC_Q * TC_JW_STRIDE * 4;        // [2][2] lambda, mu
-    static constexpr int DP = LM + 16;                                 // grad_xi phi: 27 x 3 x 27 floats
-    static constexpr int MISC = (DP + TC_Q * 3 * TC_N * 4 + 15) / 16 * 16;  // 4 mbarriers, tmem slot, abort
-    static constexpr int BYTES = MISC + 48;
+    // full[2], empty[2], tmem slot, abort flag, accfree[2]
+    static constexpr int MISC = (LM + 16 + 15) / 16 * 16;
+    static constexpr int BYTES = MISC + 64;
+    // accumulators in tensor memory: one when three CTAs fit an SM (the MMAs of
+    // element n+1 wait only for element n's read-out; the other CTAs hide it),
+    // two when only two CTAs fit (512 columns per SM)
+    static constexpr int NACC = 3 * (BYTES + 1024) <= 228 * 1024 ? 1 : 2;
 };
 
 constexpr int TC_CONS = 96;               // consumer threads (warps 0-2)
@@ -319,7 +328,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__restrict__ jinv,
+__global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_matrix_tc(const float *__restrict__ jinv,
                                                                  const float *__restrict__ wdetj,
                                                                  const float *__restrict__ dphi, long long E,
                                                                  const double *__restrict__ lame,
@@ -337,6 +346,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
     uint64_t *empty = reinterpret_cast<uint64_t *>(smem + P::MISC + 16); // [2]
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + P::MISC + 32);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + P::MISC + 36);
+    uint64_t *accfree = reinterpret_cast<uint64_t *>(smem + P::MISC + 40);  // [NACC] accumulator read out
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -347,12 +357,15 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(full + b)), "r"(1) : "memory");
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(empty + b)), "r"(1) : "memory");
         }
+#pragma unroll
+        for (int b = 0; b < P::NACC; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(accfree + b)), "r"(1) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(2 * TC_TMEM_COLS)
+                     "r"(P::NACC * TC_TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -479,13 +492,21 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
             fence_async_smem();  // operand writes -> tensor-core (async) proxy
             named_sync(TC_BAR_PROD, TC_PROD);
 
-            // (c) MMA chain into accumulator b: D = sum over K steps of hi*hi (+ hi*lo + lo*hi)
+            // (c) MMA chain into the accumulator once the consumers have read out
+            // element n-1's: D = sum over K steps of hi*hi (+ hi*lo + lo*hi)
+            const int acc = n % P::NACC;
             if (ptid == 0) {
+                if (n >= P::NACC && !mbar_wait_bounded(smem_u32(accfree + acc), (n / P::NACC - 1) & 1, abort_flag)) {
+                    *abort_flag = 1;
+                    fe_report(status, FE_ERR_TIMEOUT, e);
+                }
+            }
+            if (ptid == 0 && !*abort_flag) {
                 tc_fence_after();
                 constexpr int KSTEP_BYTES = 2 * L::LBO;  // one MMA consumes two 16-byte K chunks
                 constexpr int NSTEP = TC_KPAD / (2 * L::CHUNK);
                 const uint32_t hi = smem_u32(opHi), lo = smem_u32(opLo);
-                const uint32_t d_tmem = tmem + b * TC_TMEM_COLS;
+                const uint32_t d_tmem = tmem + acc * TC_TMEM_COLS;
 #pragma unroll
                 for (int s = 0; s < NSTEP; ++s) {
                     const uint64_t dh = smem_desc(hi + s * KSTEP_BYTES, L::LBO, L::SBO);
@@ -517,24 +538,28 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
             if (*abort_flag) break;
             tc_fence_after();
 
-            // (e) rows (j = warp, a = lane) of accumulator b -> registers -> exchange area
-            float d[TC_NCOL];
+            // (e) rows (j = warp, a = lane) of the accumulator: the two blocks this warp
+            // uses (A_jj, A_j,j+1) -> registers; the accumulator is then handed back
+            // to the producers, and the blocks go to the exchange area
+            float d[64];
             {
-                const uint32_t taddr = tmem + b * TC_TMEM_COLS + ((uint32_t)(32 * warp) << 16);
-                tmem_ld32(taddr, d);
-                tmem_ld32(taddr + 32, d + 32);
-                tmem_ld32(taddr + 64, d + 64);
+                const int jn = warp == 2 ? 0 : warp + 1;
+                const uint32_t taddr = tmem + (n % P::NACC) * TC_TMEM_COLS + ((uint32_t)(32 * warp) << 16);
+                tmem_ld32(taddr + 32 * warp, d);
+                tmem_ld32(taddr + 32 * jn, d + 32);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (lane < TC_N) {
-                    // ex[w][0] = A_ww, ex[w][1] = A_w,w+1 (rows a, columns b)
-                    float *e0 = ex + ((warp * 2 + 0) * TC_N + lane) * P::EX_STRIDE;
-                    float *e1 = ex + ((warp * 2 + 1) * TC_N + lane) * P::EX_STRIDE;
-                    if (warp == 0) publish_blocks<0>(d, e0, e1);
-                    else if (warp == 1) publish_blocks<1>(d, e0, e1);
-                    else publish_blocks<2>(d, e0, e1);
-                }
             }
             tc_fence_before();
+            named_sync(TC_BAR_CONS, TC_CONS);
+            if (ctid == 0)
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(accfree + n % P::NACC))
+                             : "memory");
+            if (lane < TC_N) {
+                // ex[w][0] = A_ww, ex[w][1] = A_w,w+1 (rows a, columns b)
+                float *e0 = ex + ((warp * 2 + 0) * TC_N + lane) * P::EX_STRIDE;
+                float *e1 = ex + ((warp * 2 + 1) * TC_N + lane) * P::EX_STRIDE;
+                publish_blocks(d, e0, e1);
+            }
             if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // staging drained
             named_sync(TC_BAR_CONS, TC_CONS);
 
@@ -544,10 +569,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
             float *kst = ks + shift;
             if (lane < TC_N) {
                 const float lam = sLM[2 * b], mu = sLM[2 * b + 1];
-                // one code path per warp keeps every register index static
-                if (warp == 0) epilogue_rows<0, P::EX_STRIDE>(d, ex, lane, lam, mu, kst);
-                else if (warp == 1) epilogue_rows<1, P::EX_STRIDE>(d, ex, lane, lam, mu, kst);
-                else epilogue_rows<2, P::EX_STRIDE>(d, ex, lane, lam, mu, kst);
+                epilogue_rows<P::EX_STRIDE>(warp, d, ex, lane, lam, mu, kst);
             }
             fence_async_smem();
             named_sync(TC_BAR_CONS, TC_CONS);
@@ -571,7 +593,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS, 2) k_matrix_tc(const float *__r
     __syncthreads();
     tc_fence_after();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_TMEM_COLS)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(P::NACC * TC_TMEM_COLS)
                      : "memory");
 }
 
@@ -583,7 +605,7 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
     static_assert(P::BYTES <= 227 * 1024, "shared memory plan too large");
     auto kern = k_matrix_tc<MODE>;
     // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA),
-    // registers, and the 512 tensor-memory columns of which every CTA holds 2 x TC_TMEM_COLS
+    // registers, and the 512 tensor-memory columns of which every CTA holds TC_TMEM_COLS
     static FeLaunchCache cache;
     long long per_sm = 0;
     cudaError_t err = fe_cached_grid(
@@ -602,7 +624,7 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
             int n = smem_sm / (P::BYTES + 1024);
             const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * TC_THREADS_WS);
             if (by_regs < n) n = by_regs;
-            if (n * 2 * TC_TMEM_COLS > 512) n = 512 / (2 * TC_TMEM_COLS);
+            if (n * P::NACC * TC_TMEM_COLS > 512) n = 512 / (P::NACC * TC_TMEM_COLS);
             if (n < 1) return cudaErrorInvalidConfiguration;
             *v = n;
             return cudaSuccess;
