@@ -31,6 +31,25 @@ __device__ __forceinline__ void finish_point(const double J[3][3], double wq, lo
     const double c02 = J10 * J21 - J11 * J20;
     const double det = J00 * c00 + J01 * c01 + J02 * c02;
     if (!(det > 0.0) || !isfinite(det)) fe_report(status, isfinite(det) ? FE_ERR_NONPOSITIVE_DETJ : FE_ERR_NONFINITE, e);
+    if (!jinv64) {
+        // only the float32 copy is kept: J, det J and the cofactors are FP64 (they
+        // carry the cancellation of distorted elements), the quotient that is
+        // stored in float32 is formed in float32 (a few float32 ulps instead of
+        // one; it saves the FP64 reciprocal and 10 FP64 multiplies per point)
+        const float rf = 1.0f / (float)det;
+        float *o = jinv32 + idx * 9;
+        o[0] = (float)c00 * rf;
+        o[3] = (float)c01 * rf;
+        o[6] = (float)c02 * rf;
+        o[1] = (float)(J02 * J21 - J01 * J22) * rf;
+        o[4] = (float)(J00 * J22 - J02 * J20) * rf;
+        o[7] = (float)(J01 * J20 - J00 * J21) * rf;
+        o[2] = (float)(J01 * J12 - J02 * J11) * rf;
+        o[5] = (float)(J02 * J10 - J00 * J12) * rf;
+        o[8] = (float)(J00 * J11 - J01 * J10) * rf;
+        wdetj32[idx] = (float)wq * (float)det;
+        return;
+    }
     const double r = 1.0 / det;
     double inv[9];
     inv[0] = c00 * r;
