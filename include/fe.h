@@ -367,9 +367,11 @@ typedef struct {
 
 /* A batch evaluates matrix mode (Algorithm 2) for many items, e.g. the groups
  * of a mixed mesh of P1-P3 tetrahedra and Q1-Q3 hexahedra with the Laplace,
- * mass and elasticity forms, in ONE persistent kernel launch: the items'
- * elements are cut into chunks and resident CTAs stride over the combined
- * work list.  Every (element, form) pair has candidate configurations (node
+ * mass and elasticity forms, in persistent kernels: the items' elements are
+ * cut into chunks and resident CTAs stride over a work list.  One persistent
+ * kernel per register class of the chosen configurations (at most three:
+ * light, heavy, and 4x4-tile Q3 elasticity, 3, 2 and 1 CTAs per SM), the
+ * classes running concurrently on forked streams.  Every (element, form) pair has candidate configurations (node
  * tile, elements per chunk, output staging); FE_BATCH_AUTOTUNE times each on
  * the item's own elements (writing its K_out) and keeps the fastest, otherwise
  * the first is used.  FE_F32 arithmetic from the FP32 copy of the FP64

@@ -14,9 +14,15 @@
 //
 // Variants per (form, element) are candidates of an autotuner: at plan
 // creation each candidate is timed on the item's own elements and the fastest
-// is kept.  A plan can also be captured in a CUDA graph together with the
-// geometry of every group (FP64 J, det J, J^-1), so that one graph launch
-// evaluates the whole batch.  FP32 element matrices from FP64 geometry.
+// is kept.  Registers and shared memory are allocated per kernel, so one kernel
+// holding every variant would run all of them at the occupancy of the heaviest
+// (Q2 elasticity with 3x3 tiles: 128 registers).  The variants are therefore
+// split in two classes, each with its own persistent kernel: "light" (at most
+// 85 registers and 75 KB of shared memory: 3 CTAs per SM) and "heavy" (2 CTAs
+// per SM); the two run concurrently on two streams.  A plan can be captured in
+// a CUDA graph together with the geometry of every group (FP64 J, det J, J^-1),
+// so that one graph launch evaluates the whole batch.  FP32 element matrices
+// from FP64 geometry.
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -28,62 +34,67 @@ namespace {
 
 constexpr int BT = 256;  // threads of the batched kernel
 
-// id, N, Q, form, material kind (0 scalar / 1 Lame), tile T, elements per chunk, staging
-#define FE_BATCH_VARIANTS(X)                                   \
-    X(0, 4, 5, FK_LAPLACE, 0, 2, 85, STAGE_BULK)               \
-    X(1, 4, 5, FK_LAPLACE, 0, 2, 42, STAGE_BULK)               \
-    X(2, 4, 5, FK_MASS, 0, 2, 85, STAGE_BULK)                  \
-    X(3, 4, 5, FK_MASS, 0, 2, 42, STAGE_BULK)                  \
-    X(4, 4, 5, FK_ELASTICITY, 1, 2, 85, STAGE_BULK)            \
-    X(5, 4, 5, FK_ELASTICITY, 1, 2, 42, STAGE_BULK)            \
-    X(6, 10, 15, FK_LAPLACE, 0, 2, 17, STAGE_BULK)             \
-    X(7, 10, 15, FK_LAPLACE, 0, 2, 8, STAGE_BULK)              \
-    X(8, 10, 15, FK_MASS, 0, 2, 17, STAGE_BULK)                \
-    X(9, 10, 15, FK_MASS, 0, 2, 8, STAGE_BULK)                 \
-    X(10, 10, 15, FK_ELASTICITY, 1, 2, 17, STAGE_BULK)         \
-    X(11, 10, 15, FK_ELASTICITY, 1, 2, 8, STAGE_BULK)          \
-    X(12, 20, 35, FK_LAPLACE, 0, 4, 8, STAGE_BULK)             \
-    X(13, 20, 35, FK_LAPLACE, 0, 2, 4, STAGE_BULK)             \
-    X(14, 20, 35, FK_MASS, 0, 4, 8, STAGE_BULK)                \
-    X(15, 20, 35, FK_MASS, 0, 2, 4, STAGE_BULK)                \
-    X(16, 20, 35, FK_ELASTICITY, 1, 2, 4, STAGE_BULK)          \
-    X(17, 20, 35, FK_ELASTICITY, 1, 2, 2, STAGE_BULK)          \
-    X(18, 8, 8, FK_LAPLACE, 0, 2, 25, STAGE_BULK)              \
-    X(19, 8, 8, FK_LAPLACE, 0, 2, 12, STAGE_BULK)              \
-    X(20, 8, 8, FK_MASS, 0, 2, 25, STAGE_BULK)                 \
-    X(21, 8, 8, FK_MASS, 0, 2, 12, STAGE_BULK)                 \
-    X(22, 8, 8, FK_ELASTICITY, 1, 2, 25, STAGE_BULK)           \
-    X(23, 8, 8, FK_ELASTICITY, 1, 2, 12, STAGE_BULK)           \
-    X(24, 27, 27, FK_LAPLACE, 0, 3, 5, STAGE_BULK)             \
-    X(25, 27, 27, FK_LAPLACE, 0, 3, 2, STAGE_BULK)             \
-    X(26, 27, 27, FK_MASS, 0, 3, 5, STAGE_BULK)                \
-    X(27, 27, 27, FK_MASS, 0, 3, 2, STAGE_BULK)                \
-    X(28, 27, 27, FK_ELASTICITY, 1, 3, 5, STAGE_BULK)          \
-    X(29, 27, 27, FK_ELASTICITY, 1, 3, 2, STAGE_BULK)          \
-    X(30, 64, 64, FK_LAPLACE, 0, 4, 1, STAGE_BULK)             \
-    X(31, 64, 64, FK_LAPLACE, 0, 2, 1, STAGE_DIRECT)           \
-    X(32, 64, 64, FK_MASS, 0, 4, 1, STAGE_BULK)                \
-    X(33, 64, 64, FK_MASS, 0, 2, 1, STAGE_DIRECT)              \
-    X(34, 64, 64, FK_ELASTICITY, 1, 2, 1, STAGE_DIRECT)
+// id, class (0 light / 1 heavy), N, Q, form, material kind (0 scalar / 1 Lame),
+// tile T, elements per chunk, staging
+#define FE_BATCH_VARIANTS(X)                                      \
+    X(0, 0, 4, 5, FK_LAPLACE, 0, 2, 42, STAGE_BULK)               \
+    X(1, 0, 4, 5, FK_LAPLACE, 0, 2, 21, STAGE_BULK)               \
+    X(2, 0, 4, 5, FK_MASS, 0, 2, 42, STAGE_BULK)                  \
+    X(3, 0, 4, 5, FK_MASS, 0, 2, 21, STAGE_BULK)                  \
+    X(4, 0, 4, 5, FK_ELASTICITY, 1, 2, 42, STAGE_BULK)            \
+    X(5, 0, 4, 5, FK_ELASTICITY, 1, 2, 21, STAGE_BULK)            \
+    X(6, 0, 10, 15, FK_LAPLACE, 0, 2, 17, STAGE_BULK)             \
+    X(7, 0, 10, 15, FK_LAPLACE, 0, 2, 8, STAGE_BULK)              \
+    X(8, 0, 10, 15, FK_MASS, 0, 2, 17, STAGE_BULK)                \
+    X(9, 0, 10, 15, FK_MASS, 0, 2, 8, STAGE_BULK)                 \
+    X(10, 0, 10, 15, FK_ELASTICITY, 1, 2, 17, STAGE_BULK)         \
+    X(11, 0, 10, 15, FK_ELASTICITY, 1, 2, 8, STAGE_BULK)          \
+    X(12, 0, 20, 35, FK_LAPLACE, 0, 2, 4, STAGE_BULK)             \
+    X(13, 0, 20, 35, FK_LAPLACE, 0, 2, 2, STAGE_BULK)             \
+    X(14, 0, 20, 35, FK_MASS, 0, 2, 4, STAGE_BULK)                \
+    X(15, 0, 20, 35, FK_MASS, 0, 2, 2, STAGE_BULK)                \
+    X(16, 0, 20, 35, FK_ELASTICITY, 1, 2, 4, STAGE_BULK)          \
+    X(17, 0, 20, 35, FK_ELASTICITY, 1, 2, 2, STAGE_BULK)          \
+    X(18, 0, 8, 8, FK_LAPLACE, 0, 2, 25, STAGE_BULK)              \
+    X(19, 0, 8, 8, FK_LAPLACE, 0, 2, 12, STAGE_BULK)              \
+    X(20, 0, 8, 8, FK_MASS, 0, 2, 25, STAGE_BULK)                 \
+    X(21, 0, 8, 8, FK_MASS, 0, 2, 12, STAGE_BULK)                 \
+    X(22, 0, 8, 8, FK_ELASTICITY, 1, 2, 25, STAGE_BULK)           \
+    X(23, 0, 8, 8, FK_ELASTICITY, 1, 2, 12, STAGE_BULK)           \
+    X(24, 0, 27, 27, FK_LAPLACE, 0, 3, 5, STAGE_BULK)             \
+    X(25, 0, 27, 27, FK_LAPLACE, 0, 3, 2, STAGE_BULK)             \
+    X(26, 0, 27, 27, FK_MASS, 0, 3, 2, STAGE_BULK)                \
+    X(27, 0, 27, 27, FK_MASS, 0, 3, 1, STAGE_BULK)                \
+    X(28, 1, 27, 27, FK_ELASTICITY, 1, 3, 5, STAGE_BULK)          \
+    X(29, 1, 27, 27, FK_ELASTICITY, 1, 3, 2, STAGE_BULK)          \
+    X(30, 1, 64, 64, FK_LAPLACE, 0, 4, 1, STAGE_BULK)             \
+    X(31, 1, 64, 64, FK_LAPLACE, 0, 2, 1, STAGE_DIRECT)           \
+    X(32, 1, 64, 64, FK_MASS, 0, 4, 1, STAGE_BULK)                \
+    X(33, 0, 64, 64, FK_MASS, 0, 2, 1, STAGE_DIRECT)              \
+    X(34, 1, 64, 64, FK_ELASTICITY, 1, 2, 1, STAGE_DIRECT)       \
+    X(35, 2, 64, 64, FK_ELASTICITY, 1, 4, 1, STAGE_BULK)
 
 struct Variant {
-    int N, Q, kind, matk, tile, epb, stage;
+    int cls, N, Q, kind, matk, tile, epb, stage;
     size_t smem;
 };
 
-#define FE_BATCH_INFO(ID, N, Q, KIND, MATK, T, EPB, STAGE) \
-    {N, Q, KIND, MATK, T, EPB, STAGE, MatrixSmem<float, N, Q, KIND, T, EPB, STAGE>::BYTES},
+#define FE_BATCH_INFO(ID, CLS, N, Q, KIND, MATK, T, EPB, STAGE) \
+    {CLS, N, Q, KIND, MATK, T, EPB, STAGE, MatrixSmem<float, N, Q, KIND, T, EPB, STAGE>::BYTES},
 const Variant kVariants[] = {FE_BATCH_VARIANTS(FE_BATCH_INFO)};
 #undef FE_BATCH_INFO
 constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
-#define FE_BATCH_CHECK(ID, N, Q, KIND, MATK, T, EPB, STAGE)                                                      \
+// shared memory per CTA of each class: 3 (light), 2 (heavy) or 1 (4x4-tile
+// elasticity of Q3: 144 accumulators per thread) CTAs per SM
+constexpr int kClasses = 3;
+constexpr size_t kMaxSmem[kClasses] = {75 * 1024, 113 * 1024, 226 * 1024};  // + the kernel's static bytes <= 227 KB
+
+#define FE_BATCH_CHECK(ID, CLS, N, Q, KIND, MATK, T, EPB, STAGE)                                                 \
     static_assert(STAGE == STAGE_DIRECT || EPB * (N / T) * (N / T + 1) / 2 <= BT, "one tile per thread");      \
-    static_assert(MatrixSmem<float, N, Q, KIND, T, EPB, STAGE>::BYTES <= 113 * 1024, "two CTAs per SM");
+    static_assert(MatrixSmem<float, N, Q, KIND, T, EPB, STAGE>::BYTES <= kMaxSmem[CLS], "class cap");
 FE_BATCH_VARIANTS(FE_BATCH_CHECK)
 #undef FE_BATCH_CHECK
-
-constexpr size_t kMaxSmem = 113 * 1024;
 
 struct BatchItemDev {
     const float *jinv, *wdetj, *dphi, *phi;
@@ -94,8 +105,9 @@ struct BatchItemDev {
     int variant, ncomp, mat_t, pad;
 };
 
-__global__ void __launch_bounds__(BT, 2) k_batch(const BatchItemDev *__restrict__ items, int n_items,
-                                                 long long n_chunks)
+template <int CLS>
+__global__ void __launch_bounds__(BT, CLS == 0 ? 3 : (CLS == 1 ? 2 : 1)) k_batch(const BatchItemDev *__restrict__ items, int n_items,
+                                                           long long n_chunks)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_item;
@@ -121,15 +133,16 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BatchItemDev *__restrict_
             __syncthreads();
         }
         switch (it.variant) {
-#define FE_BATCH_CASE(ID, N, Q, KIND, MATK, T, EPB, STAGE)                                                       \
-    case ID: {                                                                                                  \
-        if (i != loaded) matrix_load_ref<float, N, Q, KIND, T, EPB, BT, STAGE>(it.dphi, smem_raw);              \
-        const long long e0 = local * EPB;                                                                       \
-        const int ne = (int)(it.E - e0 < EPB ? it.E - e0 : EPB);                                                 \
-        matrix_group<float, N, Q, KIND, MATK, T, EPB, BT, STAGE>(it.jinv, it.wdetj, it.phi, e0, ne, it.ncomp,   \
-                                                                 it.mat, it.mat_t, it.K, smem_raw);             \
-        break;                                                                                                  \
-    }
+#define FE_BATCH_CASE(ID, VCLS, N, Q, KIND, MATK, T, EPB, STAGE)                                                 \
+    case ID:                                                                                                    \
+        if constexpr (VCLS == CLS) {                                                                            \
+            if (i != loaded) matrix_load_ref<float, N, Q, KIND, T, EPB, BT, STAGE>(it.dphi, smem_raw);          \
+            const long long e0 = local * EPB;                                                                   \
+            const int ne = (int)(it.E - e0 < EPB ? it.E - e0 : EPB);                                             \
+            matrix_group<float, N, Q, KIND, MATK, T, EPB, BT, STAGE>(it.jinv, it.wdetj, it.phi, e0, ne,         \
+                                                                     it.ncomp, it.mat, it.mat_t, it.K, smem_raw); \
+        }                                                                                                       \
+        break;
             FE_BATCH_VARIANTS(FE_BATCH_CASE)
 #undef FE_BATCH_CASE
         default: break;
@@ -140,7 +153,8 @@ __global__ void __launch_bounds__(BT, 2) k_batch(const BatchItemDev *__restrict_
     if (threadIdx.x == 0) bulk_wait_read<0>();  // shared memory must outlive the copies' reads
 }
 
-// Launch shape: the largest shared-memory plan of the batch decides residency.
+// Launch shape of class CLS for a shared-memory plan of `smem` bytes.
+template <int CLS>
 cudaError_t batch_grid(size_t smem, long long *grid)
 {
     static FeLaunchCache cache;
@@ -152,17 +166,29 @@ cudaError_t batch_grid(size_t smem, long long *grid)
         cache,
         [&](int, long long *v) {
             *v = 1;
-            return cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+            return cudaFuncSetAttribute(k_batch<CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)kMaxSmem[CLS]);
         },
         &set);
     if (e != cudaSuccess) return e;
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, BT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<CLS>, BT, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     *grid = (long long)per_sm * sms;
     return cudaSuccess;
+}
+
+cudaError_t launch_class(int cls, const BatchItemDev *items, int n, long long chunks, size_t smem, long long grid,
+                         cudaStream_t s)
+{
+    if (n == 0 || chunks == 0) return cudaSuccess;
+    if (grid > chunks) grid = chunks;
+    if (cls == 0) k_batch<0><<<(unsigned)grid, BT, smem, s>>>(items, n, chunks);
+    else if (cls == 1) k_batch<1><<<(unsigned)grid, BT, smem, s>>>(items, n, chunks);
+    else k_batch<2><<<(unsigned)grid, BT, smem, s>>>(items, n, chunks);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -172,12 +198,17 @@ struct fe_batch_h {
     int n_items;
     unsigned flags;
     unsigned long long *d_status;
-    std::vector<BatchItemDev> items;        // host copy (chunk0 filled)
-    std::vector<fe_geometry_h *> geoms;     // distinct geometries recomputed by the batch
+    std::vector<BatchItemDev> items;     // in the caller's order; chunk0 relative to the item's class
+    std::vector<int> pos;                // device position of each item (grouped by class)
+    std::vector<fe_geometry_h *> geoms;  // distinct geometries recomputed by the batch
     BatchItemDev *d_items = nullptr;
-    long long n_chunks = 0;
-    size_t smem = 0;
-    long long grid = 0;
+    int n_cls[kClasses] = {0, 0, 0};
+    int first[kClasses] = {0, 0, 0};  // device position of each class's first item
+    long long chunks[kClasses] = {0, 0, 0};
+    size_t smem[kClasses] = {0, 0, 0};
+    long long grid[kClasses] = {0, 0, 0};
+    cudaStream_t side[kClasses - 1] = {nullptr, nullptr};  // classes 1, 2 run here, concurrently
+    cudaEvent_t fork = nullptr, join[kClasses - 1] = {nullptr, nullptr};
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -194,10 +225,25 @@ cudaError_t enqueue(fe_batch_h *b, cudaStream_t s)
             e = fe_launch_geometry(g, b->d_status, s);
             if (e != cudaSuccess) return e;
         }
-    if (b->n_chunks > 0) {
-        const long long grid = b->grid < b->n_chunks ? b->grid : b->n_chunks;
-        k_batch<<<(unsigned)grid, BT, b->smem, s>>>(b->d_items, b->n_items, b->n_chunks);
-        e = cudaGetLastError();
+    // class 0 on the caller's stream, classes 1 and 2 forked onto side streams
+    int used = 0;
+    for (int c = 1; c < kClasses; ++c) used += b->chunks[c] > 0;
+    if (used > 0) {
+        e = cudaEventRecord(b->fork, s);
+        for (int c = 1; c < kClasses && e == cudaSuccess; ++c) {
+            if (b->chunks[c] == 0) continue;
+            e = cudaStreamWaitEvent(b->side[c - 1], b->fork, 0);
+            if (e == cudaSuccess)
+                e = launch_class(c, b->d_items + b->first[c], b->n_cls[c], b->chunks[c], b->smem[c], b->grid[c],
+                                 b->side[c - 1]);
+        }
+    }
+    if (e == cudaSuccess)
+        e = launch_class(0, b->d_items + b->first[0], b->n_cls[0], b->chunks[0], b->smem[0], b->grid[0], s);
+    for (int c = 1; c < kClasses && e == cudaSuccess; ++c) {
+        if (b->chunks[c] == 0) continue;
+        e = cudaEventRecord(b->join[c - 1], b->side[c - 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[c - 1], 0);
     }
     return e;
 }
@@ -213,16 +259,21 @@ std::vector<int> candidates(int N, int Q, int kind, int matk)
     return v;
 }
 
-// Median of `reps` timed runs of one item alone with variant `id`.
+cudaError_t class_grid(int cls, size_t smem, long long *grid)
+{
+    return cls == 0 ? batch_grid<0>(smem, grid) : cls == 1 ? batch_grid<1>(smem, grid) : batch_grid<2>(smem, grid);
+}
+
+// Median of five timed runs (after one warm-up) of one item alone with variant `id`.
 cudaError_t time_variant(BatchItemDev it, int id, BatchItemDev *d_tmp, cudaStream_t s, float *ms)
 {
+    const Variant &v = kVariants[id];
     it.variant = id;
     it.chunk0 = 0;
-    const long long chunks = (it.E + kVariants[id].epb - 1) / kVariants[id].epb;
+    const long long chunks = (it.E + v.epb - 1) / v.epb;
     long long grid = 0;
-    cudaError_t e = batch_grid(kVariants[id].smem, &grid);
+    cudaError_t e = class_grid(v.cls, v.smem, &grid);
     if (e != cudaSuccess) return e;
-    if (grid > chunks) grid = chunks;
     e = cudaMemcpyAsync(d_tmp, &it, sizeof(it), cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return e;
     cudaEvent_t a, b;
@@ -231,11 +282,11 @@ cudaError_t time_variant(BatchItemDev it, int id, BatchItemDev *d_tmp, cudaStrea
     float t[5];
     for (int r = 0; r < 6; ++r) {
         cudaEventRecord(a, s);
-        k_batch<<<(unsigned)grid, BT, kVariants[id].smem, s>>>(d_tmp, 1, chunks);
+        e = launch_class(v.cls, d_tmp, 1, chunks, v.smem, grid, s);
         cudaEventRecord(b, s);
-        e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
         if (e != cudaSuccess) break;
-        if (r > 0) cudaEventElapsedTime(&t[r - 1], a, b);  // the first run warms up
+        if (r > 0) cudaEventElapsedTime(&t[r - 1], a, b);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -256,6 +307,11 @@ void free_plan(fe_batch_h *b)
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->capture_stream) cudaStreamDestroy(b->capture_stream);
+    for (int c = 0; c < kClasses - 1; ++c) {
+        if (b->side[c]) cudaStreamDestroy(b->side[c]);
+        if (b->join[c]) cudaEventDestroy(b->join[c]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->d_items) cudaFree(b->d_items);
     delete b;
 }
@@ -284,35 +340,23 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         const fe_batch_item &x = items[i];
         const fe_geometry_h *g = x.geom;
         const fe_form_h *f = x.form;
-        if (!g || !f || g->device != ctx->device) {
-            free_plan(b);
-            return FE_ERR_INVALID_ARG;
+        fe_status bad = FE_OK;
+        int matk = 0;
+        if (!g || !f || g->device != ctx->device) bad = FE_ERR_INVALID_ARG;
+        else if (g->mesh.n_elems > 0 && !x.K_out) bad = FE_ERR_INVALID_ARG;
+        else if (!g->d_jinv32) bad = FE_ERR_INVALID_ARG;  // the batch reads the FP32 copy of the geometry
+        else if (f->eval) bad = FE_ERR_INVALID_ARG;
+        else if (f->kind == FK_LAPLACE || f->kind == FK_MASS) matk = 0;
+        else if (f->kind == FK_ELASTICITY && f->mat == FE_MAT_LAME && !f->mat_transposed) matk = 1;
+        else bad = FE_ERR_UNSUPPORTED_SPEC;
+        if (bad == FE_OK && f->mat_op >= 0 && !x.material && g->mesh.n_elems > 0) bad = FE_ERR_INVALID_ARG;
+        if (bad == FE_OK) {
+            cand[i] = candidates(g->N, g->Q, f->kind, matk);
+            if (cand[i].empty()) bad = FE_ERR_UNSUPPORTED_SPEC;
         }
-        if (g->mesh.n_elems > 0 && !x.K_out) {
+        if (bad != FE_OK) {
             free_plan(b);
-            return FE_ERR_INVALID_ARG;
-        }
-        if (!g->d_jinv32) {  // the batch evaluates FP32 matrices from the FP32 copy of the geometry
-            free_plan(b);
-            return FE_ERR_INVALID_ARG;
-        }
-        int matk;
-        if (f->kind == FK_LAPLACE || f->kind == FK_MASS) {
-            matk = 0;
-        } else if (f->kind == FK_ELASTICITY && f->mat == FE_MAT_LAME && !f->mat_transposed) {
-            matk = 1;
-        } else {
-            free_plan(b);
-            return FE_ERR_UNSUPPORTED_SPEC;
-        }
-        if (f->mat_op >= 0 && !x.material && g->mesh.n_elems > 0) {
-            free_plan(b);
-            return FE_ERR_INVALID_ARG;
-        }
-        cand[i] = candidates(g->N, g->Q, f->kind, matk);
-        if (cand[i].empty()) {
-            free_plan(b);
-            return FE_ERR_UNSUPPORTED_SPEC;
+            return bad;
         }
         BatchItemDev it{};
         it.jinv = g->d_jinv32;
@@ -332,10 +376,15 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         if (!seen) b->geoms.push_back(gm);
     }
     cudaError_t e = cudaMalloc(&b->d_items, sizeof(BatchItemDev) * (size_t)n_items);
-    // geometry first (stale deferred handles, and the batch's own recomputation)
+    for (int c = 0; c < kClasses - 1 && e == cudaSuccess; ++c) {
+        e = cudaStreamCreateWithFlags(&b->side[c], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[c], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    // geometry first (stale deferred handles)
     for (fe_geometry_h *g : b->geoms)
         if (e == cudaSuccess) e = fe_settle_geometry(g, ctx->d_status, s);
-    // autotune: time every candidate on each item alone, items of the same
+    // autotune: time every candidate on each item alone; items of the same
     // (element, form, components) share the result
     if (e == cudaSuccess && (flags & FE_BATCH_AUTOTUNE)) {
         struct Key {
@@ -368,20 +417,27 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
             done.push_back({g->N, g->Q, items[i].form->kind, it.ncomp, best_id});
         }
     }
-    // work list
-    long long chunk = 0;
-    size_t smem = 0;
-    for (BatchItemDev &it : b->items) {
-        it.chunk0 = chunk;
-        chunk += (it.E + kVariants[it.variant].epb - 1) / kVariants[it.variant].epb;
-        if (it.E > 0 && kVariants[it.variant].smem > smem) smem = kVariants[it.variant].smem;
+    // work lists: one per class, the items grouped by class on the device
+    std::vector<BatchItemDev> dev;
+    b->pos.assign(n_items, 0);
+    for (int cls = 0; cls < kClasses; ++cls) {
+        b->first[cls] = (int)dev.size();
+        for (int i = 0; i < n_items; ++i) {
+            BatchItemDev &it = b->items[i];
+            const Variant &v = kVariants[it.variant];
+            if (v.cls != cls) continue;
+            it.chunk0 = b->chunks[cls];
+            b->chunks[cls] += (it.E + v.epb - 1) / v.epb;
+            if (it.E > 0 && v.smem > b->smem[cls]) b->smem[cls] = v.smem;
+            b->pos[i] = (int)dev.size();
+            dev.push_back(it);
+            ++b->n_cls[cls];
+        }
     }
-    b->n_chunks = chunk;
-    b->smem = smem;
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(BatchItemDev) * (size_t)n_items,
-                            cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = batch_grid(smem > 0 ? smem : 1024, &b->grid);
+        e = cudaMemcpyAsync(b->d_items, dev.data(), sizeof(BatchItemDev) * (size_t)n_items, cudaMemcpyHostToDevice, s);
+    for (int cls = 0; cls < kClasses && e == cudaSuccess; ++cls)
+        if (b->chunks[cls] > 0) e = class_grid(cls, b->smem[cls] > 0 ? b->smem[cls] : 1024, &b->grid[cls]);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     // CUDA graph of the whole batch, captured on a private stream
     if (e == cudaSuccess && (flags & FE_BATCH_GRAPH)) {
