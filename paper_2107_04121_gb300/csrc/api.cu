@@ -69,6 +69,7 @@ void free_geometry(fe_geometry_h *g)
     cudaFree(g->d_d1d);
     cudaFree(g->d_b1d32);
     cudaFree(g->d_d1d32);
+    cudaFree(g->d_dq);
     cudaFree(g->d_phi32);
     cudaFree(g->d_dphi32);
     cudaFree(g->d_jinv64);
@@ -214,6 +215,12 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
         if (e == cudaSuccess) e = dev_alloc(&g->d_d1d32, n);
         if (e == cudaSuccess) e = cudaMemcpy(g->d_b1d32, b32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
         if (e == cudaSuccess) e = cudaMemcpy(g->d_d1d32, d32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+        double dq[64];
+        if (e == cudaSuccess && basis->n1d == basis->nq1d &&
+            fe_host_collocation_derivative(basis->n1d, basis->b1d, basis->d1d, dq)) {
+            e = dev_alloc(&g->d_dq, n);
+            if (e == cudaSuccess) e = cudaMemcpy(g->d_dq, dq, sizeof(double) * n, cudaMemcpyHostToDevice);
+        }
     }
     if (e == cudaSuccess && (flags & FE_GEOM_STORE_F64)) {
         e = dev_alloc(&g->d_jinv64, (size_t)E * Q * 9);

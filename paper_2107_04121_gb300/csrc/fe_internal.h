@@ -27,6 +27,7 @@ struct fe_geometry_h {
     int n1d, nq1d;                       // tensor-product factors (sum-factorised geometry)
     double *d_b1d, *d_d1d;               // (nq1d, n1d) each, or null
     float *d_b1d32, *d_d1d32;
+    double *d_dq;  // (nq1d, nq1d) collocation derivative on the points when n1d == nq1d, or null
     float *d_phi32, *d_dphi32;
     double *d_jinv64, *d_wdetj64;  // (E,Q,3,3), (E,Q)
     float *d_jinv32, *d_wdetj32;
@@ -128,3 +129,4 @@ bool fe_supported_nq(int N, int Q);
 // Host reference element (refelem.cpp).
 int fe_host_gauss_legendre01(int n, double *x, double *w);
 bool fe_host_check_tensor_basis(const fe_refbasis *b);
+bool fe_host_collocation_derivative(int n, const double *b1d, const double *d1d, double *dq);

@@ -7,6 +7,9 @@
 //  - k_geometry_sf (tensor-product bases): J by sum factorisation, three
 //    1-D contractions per coordinate and derivative direction, 2 n1 nq (n1^2 +
 //    n1 nq + nq^2)... for Q2 1,944 DFMA per element instead of 6,561;
+//  - k_geometry_co (tensor-product bases with n1 == nq): x interpolated to
+//    the points, then the collocation derivative on the points (1,458 DFMA
+//    per Q2 element);
 //  - k_geometry (any tabulated basis): one thread per (element, quadrature
 //    point), J = sum_a x_a (x) grad phi_a directly (9N DFMA per point).
 // Both finish each point with the same cofactor inverse (about 40 FP64
@@ -175,6 +178,97 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry_sf(const double *__re
     }
 }
 
+// Collocation form of the sum-factorised geometry, for n1 == nq: along one
+// axis the nq Gauss points fix a polynomial of degree n1 - 1, so the derivative
+// at the points is Dq (point values), Dq = D B^-1 (nq x nq).  Per element:
+//   P = B_z B_y B_x X       (x at the points: three 1-D contractions, 3 N n1 DFMA)
+//   J[c][m] = Dq along axis m of P[c]   (3 N n1 DFMA, fused with the inverse)
+// For Q2 that is 1,458 DFMA per element instead of 1,944, and J never passes
+// through shared memory.
+template <int N1, int EPB>
+__global__ void __launch_bounds__(kGeomThreads) k_geometry_co(const double *__restrict__ coords,
+                                                              const int32_t *__restrict__ conn, long long E,
+                                                              long long n_nodes, const double *__restrict__ b1d,
+                                                              const double *__restrict__ dq,
+                                                              const double *__restrict__ w,
+                                                              double *__restrict__ jinv64, double *__restrict__ wdetj64,
+                                                              float *__restrict__ jinv32, float *__restrict__ wdetj32,
+                                                              unsigned long long *__restrict__ status)
+{
+    constexpr int N = N1 * N1 * N1;
+    static_assert(8 * (2 * N1 * N1 + EPB * 3 * 3 * N) <= 48 * 1024, "static shared memory above 48 KB");
+    __shared__ double sB[N1][N1], sDq[N1][N1];
+    __shared__ double sX[EPB][3][N];  // nodal x [c][k][j][i], then x at the points [c][qz][qy][qx]
+    __shared__ double sU[EPB][3][N];  // [c][k][j][qx]
+    __shared__ double sV[EPB][3][N];  // [c][k][qy][qx]
+    for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) {
+        sB[i / N1][i % N1] = b1d[i];
+        sDq[i / N1][i % N1] = dq[i];
+    }
+    for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
+        const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * N; t += blockDim.x) {
+            const int el = t / N, a = t % N;
+            long long node = conn[(e0 + el) * N + a];
+            if ((unsigned long long)node >= (unsigned long long)n_nodes) {  // never read outside coords
+                fe_report(status, FE_ERR_SHAPE, e0 + el);
+                node = 0;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) sX[el][c][a] = coords[3 * node + c];
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x) {  // contract i
+            const int qx = t % N1, kj = (t / N1) % (N1 * N1), c = (t / N) % 3, el = t / (3 * N);
+            const double *x = &sX[el][c][kj * N1];
+            double u = 0.0;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) u = fma(sB[qx][i], x[i], u);
+            sU[el][c][kj * N1 + qx] = u;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x) {  // contract j
+            const int qx = t % N1, qy = (t / N1) % N1, k = (t / (N1 * N1)) % N1, c = (t / N) % 3, el = t / (3 * N);
+            const double *x = &sU[el][c][k * N1 * N1 + qx];
+            double v = 0.0;
+#pragma unroll
+            for (int j = 0; j < N1; ++j) v = fma(sB[qy][j], x[j * N1], v);
+            sV[el][c][(k * N1 + qy) * N1 + qx] = v;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x) {  // contract k
+            const int qxy = t % (N1 * N1), qz = (t / (N1 * N1)) % N1, c = (t / N) % 3, el = t / (3 * N);
+            const double *x = &sV[el][c][qxy];
+            double p = 0.0;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) p = fma(sB[qz][k], x[k * N1 * N1], p);
+            sX[el][c][qz * N1 * N1 + qxy] = p;
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * N; t += blockDim.x) {
+            const int el = t / N, q = t % N;
+            const int qx = q % N1, qy = (q / N1) % N1, qz = q / (N1 * N1);
+            double J[3][3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double *P = sX[el][c];
+                double j0 = 0.0, j1 = 0.0, j2 = 0.0;
+#pragma unroll
+                for (int p = 0; p < N1; ++p) {
+                    j0 = fma(sDq[qx][p], P[(qz * N1 + qy) * N1 + p], j0);
+                    j1 = fma(sDq[qy][p], P[(qz * N1 + p) * N1 + qx], j1);
+                    j2 = fma(sDq[qz][p], P[(p * N1 + qy) * N1 + qx], j2);
+                }
+                J[c][0] = j0;
+                J[c][1] = j1;
+                J[c][2] = j2;
+            }
+            finish_point(J, w[q], e0 + el, (e0 + el) * N + q, jinv64, wdetj64, jinv32, wdetj32, status);
+        }
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(kGeomThreads) k_geometry(const double *__restrict__ coords,
                                                            const int32_t *__restrict__ conn, long long E,
@@ -300,6 +394,35 @@ cudaError_t launch_geom_sf(const fe_geometry_h *g, unsigned long long *st, cudaS
     return cudaGetLastError();
 }
 
+template <int N1, int EPB>
+cudaError_t launch_geom_co(const fe_geometry_h *g, unsigned long long *st, cudaStream_t s)
+{
+    static FeLaunchCache cache;
+    long long cap = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int dev, long long *v) {
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaError_t e2 =
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_geometry_co<N1, EPB>, kGeomThreads, 0);
+            if (e2 != cudaSuccess) return e2;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            *v = (long long)per_sm * sms * 8;
+            return cudaSuccess;
+        },
+        &cap);
+    if (err != cudaSuccess) return err;
+    long long blocks = (g->mesh.n_elems + EPB - 1) / EPB;
+    if (blocks > cap) blocks = cap;
+    const bool f64 = g->flags & FE_GEOM_STORE_F64, f32 = g->flags & FE_GEOM_STORE_F32;
+    k_geometry_co<N1, EPB><<<(unsigned)blocks, kGeomThreads, 0, s>>>(
+        g->mesh.coords, g->mesh.conn, g->mesh.n_elems, g->mesh.n_nodes, g->d_b1d, g->d_dq, g->d_w64,
+        f64 ? g->d_jinv64 : nullptr, f64 ? g->d_wdetj64 : nullptr, f32 ? g->d_jinv32 : nullptr,
+        f32 ? g->d_wdetj32 : nullptr, st);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *st, cudaStream_t s)
@@ -307,6 +430,11 @@ cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *st, c
     if (g->mesh.n_elems == 0) return cudaSuccess;
     if (g->d_b1d) {
         const int n1 = g->n1d, nq = g->nq1d;
+        if (g->d_dq && n1 == nq) {
+            if (n1 == 2) return launch_geom_co<2, 32>(g, st, s);
+            if (n1 == 3) return launch_geom_co<3, 9>(g, st, s);
+            if (n1 == 4) return launch_geom_co<4, 4>(g, st, s);
+        }
         if (n1 == 2 && nq == 2) return launch_geom_sf<2, 2, 16>(g, st, s);
         if (n1 == 2 && nq == 3) return launch_geom_sf<2, 3, 8>(g, st, s);
         if (n1 == 3 && nq == 3) return launch_geom_sf<3, 3, 8>(g, st, s);

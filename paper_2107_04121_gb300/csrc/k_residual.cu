@@ -511,7 +511,7 @@ cudaError_t dispatch_sf(const fe_geometry_h *g, const fe_form_h *f, fe_material_
     constexpr bool D = sizeof(T) == 8;
     if (n1 == 2 && nq == 2) return dispatch_sf_kind<T, 2, 2, 16, 8>(g, f, mat, u, r, st, s);
     if (n1 == 2 && nq == 3) return dispatch_sf_kind<T, 2, 3, 8, 4>(g, f, mat, u, r, st, s);
-    if (n1 == 3 && nq == 3) return dispatch_sf_kind<T, 3, 3, (D ? 4 : 8), (D ? 2 : 6)>(g, f, mat, u, r, st, s);
+    if (n1 == 3 && nq == 3) return dispatch_sf_kind<T, 3, 3, (D ? 4 : 8), (D ? 2 : 9)>(g, f, mat, u, r, st, s);
     if (n1 == 3 && nq == 4) return dispatch_sf_kind<T, 3, 4, (D ? 2 : 4), (D ? 1 : 2)>(g, f, mat, u, r, st, s);
     if (n1 == 4 && nq == 4) return dispatch_sf_kind<T, 4, 4, (D ? 2 : 4), 1>(g, f, mat, u, r, st, s);
     return cudaErrorInvalidValue;

@@ -8,6 +8,7 @@
 // normalised eigenvectors.  The eigenproblem is solved with cyclic Jacobi
 // rotations, which is plenty for n <= 10.
 #include <cmath>
+#include <utility>
 #include <cstring>
 
 #include "fe_internal.h"
@@ -140,6 +141,63 @@ extern "C" fe_status fe_refbasis_hex_1d(int p, int nq, double *b1d, double *d1d)
     for (int q = 0; q < nq; ++q)
         for (int k = 0; k <= p; ++k) lagrange1d(p, k, g[q], &b1d[q * (p + 1) + k], &d1d[q * (p + 1) + k]);
     return FE_OK;
+}
+
+// Collocation derivative on the quadrature points of one axis, n1 == nq:
+// the nq point values of a polynomial of degree n1 - 1 determine it, so its
+// derivatives at the points are Dq (values at the points) with Dq = D B^-1
+// (B, D: (nq, n1) values and derivatives of the 1-D nodal basis).  Gauss-Jordan
+// with partial pivoting in FP64; false when B is (numerically) singular or the
+// product does not reproduce D.
+bool fe_host_collocation_derivative(int n, const double *b1d, const double *d1d, double *dq)
+{
+    if (n < 1 || n > 8) return false;
+    double A[8][8], Ainv[8][8];
+    for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+            A[r][c] = b1d[r * n + c];
+            Ainv[r][c] = r == c ? 1.0 : 0.0;
+        }
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+        if (!(std::fabs(A[piv][c]) > 1e-12)) return false;
+        for (int k = 0; k < n; ++k) {
+            std::swap(A[c][k], A[piv][k]);
+            std::swap(Ainv[c][k], Ainv[piv][k]);
+        }
+        const double inv = 1.0 / A[c][c];
+        for (int k = 0; k < n; ++k) {
+            A[c][k] *= inv;
+            Ainv[c][k] *= inv;
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[r][c];
+            if (f == 0.0) continue;
+            for (int k = 0; k < n; ++k) {
+                A[r][k] -= f * A[c][k];
+                Ainv[r][k] -= f * Ainv[c][k];
+            }
+        }
+    }
+    // B is (point, node); B^-1 maps point values to nodal values: dq = D B^-1
+    double scale = 1.0;
+    for (int i = 0; i < n * n; ++i) scale = std::fmax(scale, std::fabs(d1d[i]));
+    for (int q = 0; q < n; ++q)
+        for (int p = 0; p < n; ++p) {
+            double s = 0.0;
+            for (int k = 0; k < n; ++k) s += d1d[q * n + k] * Ainv[k][p];
+            dq[q * n + p] = s;
+        }
+    for (int q = 0; q < n; ++q)
+        for (int k = 0; k < n; ++k) {
+            double s = 0.0;
+            for (int p = 0; p < n; ++p) s += dq[q * n + p] * b1d[p * n + k];
+            if (std::fabs(s - d1d[q * n + k]) > 1e-12 * scale) return false;
+        }
+    return true;
 }
 
 // Does the tensor product of the 1-D factors reproduce the 3-D tables?

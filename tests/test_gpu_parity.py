@@ -24,10 +24,13 @@ def _t(a, dt):
 
 # ---- geometry ------------------------------------------------------------------
 
-@pytest.mark.parametrize("p,n", [(1, (5, 4, 3)), (2, (4, 3, 3)), (3, (2, 2, 3))])
-def test_geometry_matches_oracle(ctx, p, n):
+# (p, nq): n1 == nq takes the collocation kernel (x at the points, then the
+# derivative on the points), n1 != nq the three-stage sum factorisation
+@pytest.mark.parametrize("p,nq,n", [(1, 2, (5, 4, 3)), (2, 3, (4, 3, 3)), (3, 4, (2, 2, 3)),
+                                    (1, 3, (4, 3, 3)), (2, 4, (3, 3, 2))])
+def test_geometry_matches_oracle(ctx, p, nq, n):
     mesh = meshgen.structured_hex(*n, p, 0.15, 21)
-    P = Problem(ctx, mesh, p, p + 1)
+    P = Problem(ctx, mesh, p, nq)
     wdetJ, G, Jinv = oracle.geometry(mesh.coords, mesh.conn, P.ref, want_Jinv=True)
     g_w = P.geom.get(fe.GEOM_WDETJ, "f64").cpu().numpy()
     g_J = P.geom.get(fe.GEOM_JINV, "f64").cpu().numpy()
@@ -41,12 +44,12 @@ def test_geometry_matches_oracle(ctx, p, n):
     np.testing.assert_array_equal(P.geom.get(fe.GEOM_JINV, "f32").cpu().numpy(), g_J.astype(np.float32))
 
 
-@pytest.mark.parametrize("p", [1, 2, 3])
-def test_direct_and_sum_factorised_geometry_agree(ctx, p):
-    """The generic kernel (tables only) and the tensor-product kernel compute the same map."""
+@pytest.mark.parametrize("p,nq", [(1, 2), (2, 3), (3, 4), (2, 4)])
+def test_direct_and_sum_factorised_geometry_agree(ctx, p, nq):
+    """The generic kernel (tables only) and the tensor-product kernels compute the same map."""
     mesh = meshgen.structured_hex(3, 2, 3, p, 0.15, 24)
-    P = Problem(ctx, mesh, p, p + 1)  # tensor-product path
-    pts, w, phi, dphi = fe.refbasis_hex(p, p + 1)
+    P = Problem(ctx, mesh, p, nq)  # tensor-product path
+    pts, w, phi, dphi = fe.refbasis_hex(p, nq)
     g_direct = fe.geometry(ctx, P.m, phi, dphi, w)
     wdetJ, G, Jinv = oracle.geometry(mesh.coords, mesh.conn, P.ref, want_Jinv=True)
     for g in (P.geom, g_direct):
