@@ -54,6 +54,10 @@ CV_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 81 * 8 + 27 * 4 + 81 * 81 * 8
 # last contraction and row assembly 56862
 CV_FLOPS_PER_ELEM = 972 + 1458 + 1944 + 1944 + 6804 + 20412 + 56862
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
+# FP64 operations (an FMA counts 2) of the collocation geometry of one Q2 element:
+# three 1-D interpolations (3 x 243 FMA), J on the points (729 FMA), per point
+# 9 cofactors (mul + FMA each) and det J (mul + 2 FMA)
+GEOMETRY_FLOPS_PER_ELEM_Q2 = 2 * (3 * 243 + 729) + Q2_Q * (9 * 3 + 5)
 
 
 # Adjoint: J = |R|^2 / 2 of the assembled Q2 elasticity residual on a 32^3 cube
@@ -185,9 +189,11 @@ class Workload:
         self.coords = torch.from_numpy(self.mesh.coords).to(device)
         self.conn = torch.from_numpy(self.mesh.conn).to(device)
         self.m = fe.Mesh(self.coords, self.conn)
-        # each path keeps only the geometry copy it reads
+        # each path keeps only the geometry copy it reads; the mixed step uses a
+        # deferred float32-only handle, whose geometry the residual kernel computes
         self.geoms = {"f64": fe.hex_geometry(self.ctx, self.m, 2, 3, flags=fe.GEOM_STORE_F64),
-                      "f32": fe.hex_geometry(self.ctx, self.m, 2, 3, flags=fe.GEOM_STORE_F32)}
+                      "f32": fe.hex_geometry(self.ctx, self.m, 2, 3, flags=fe.GEOM_STORE_F32),
+                      "f32d": fe.hex_geometry(self.ctx, self.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)}
         self.form = fe.elasticity_form(fe.MAT_LAME)
         self.mat = torch.from_numpy(np.stack([self.lam, self.mu], 1)).to(device)
         self.u64 = torch.from_numpy(self.u).to(device)
@@ -210,23 +216,37 @@ class Workload:
         self.bufs.pop(prec, None)
         self.torch.cuda.empty_cache()
 
-    def step(self, prec, mk_events=None):
+    PARTS = ("geometry_and_residual", "matrix", "assembly")
+
+    def step(self, prec, ev=None):
+        """One step; `ev` (optional) gets four CUDA events recorded at the start,
+        after the geometry + residual, after the matrix and after the assembly."""
         fe = self.fe
         K, r, g = self.outputs(prec)
-        u = self.u64 if prec == "f64" else self.u32
-        geom = self.geoms["f64" if prec == "f64" else "f32"]
-        geom.update()
-        if mk_events:
-            mk_events[0].record()
+        rec = (lambda i: ev[i].record()) if ev else (lambda i: None)
+        rec(0)
+        if prec == "f64":
+            geom = self.geoms["f64"]
+            geom.update()
+            fe.eval_residual(self.ctx, self.form, geom, [self.mat, None, self.u64], prec, out=r)
+        else:
+            # stale deferred geometry: the residual kernel computes it (FP64) and
+            # stores the float32 copy that the matrix kernel reads
+            geom = self.geoms["f32d"]
+            geom.update()
+            fe.eval_residual(self.ctx, self.form, geom, [self.mat, None, self.u32], prec, out=r)
+        rec(1)
         fe.eval_matrix(self.ctx, self.form, geom, [self.mat, None, None], prec, out=K)
-        if mk_events:
-            mk_events[1].record()
-        fe.eval_residual(self.ctx, self.form, geom, [self.mat, None, u], prec, out=r)
+        rec(2)
         fe.assemble_vector(self.ctx, self.asm, 3, r, prec, out=g,
                            flags=0 if prec == "f64" else fe.ASSEMBLE_COMPENSATED)
+        rec(3)
 
 
-KERNELS_PER_STEP = 4  # geometry, matrix, residual, assembly
+def kernels_per_step(prec):
+    # FP64: geometry, residual, matrix, assembly; mixed: geometry + residual in
+    # one kernel, matrix, assembly
+    return 4 if prec == "f64" else 3
 LADDER = ["f32", "tf32x3", "bf16x3", "bf16"]
 DEFAULT_MIXED = "bf16x3"
 
@@ -259,7 +279,8 @@ def precision_ladder(wl, flush, ref, reps=5):
 
 
 def timed_steps(wl, prec, steps, warmup, ws, flush):
-    """Per-step CUDA-event times (ms) and matrix-kernel times (ms); L2 flushed between steps."""
+    """Per-step CUDA-event times (ms), matrix-kernel times (ms) and the mean
+    time of each part of the step; L2 flushed between steps."""
     torch = wl.torch
     for _ in range(warmup):
         wl.step(prec)
@@ -270,16 +291,15 @@ def timed_steps(wl, prec, steps, warmup, ws, flush):
     for _ in range(steps):
         flush.zero_()
         e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        e[0].record()
-        wl.step(prec, (e[1], e[2]))
-        e[3].record()
+        wl.step(prec, e)
         ev.append(e)
     torch.cuda.synchronize()
     barrier(ws)
     wl.ctx.check()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
     mat_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    return step_ms, mat_ms
+    parts = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev) for i, name in enumerate(wl.PARTS)}
+    return step_ms, mat_ms, parts
 
 
 def rel_matrix_error(K, Kref):
@@ -405,20 +425,23 @@ class ConvectWorkload:
     outputs = Workload.outputs
     drop = Workload.drop
 
-    def step(self, prec, mk_events=None):
+    PARTS = ("geometry", "matrix", "residual_and_assembly")
+
+    def step(self, prec, ev=None):
         fe = self.fe
         K, r, g = self.outputs(prec)
         u = self.u64 if prec == "f64" else self.u32
+        rec = (lambda i: ev[i].record()) if ev else (lambda i: None)
         geom = self.geoms[prec]
+        rec(0)
         geom.update()
-        if mk_events:
-            mk_events[0].record()
+        rec(1)
         fe.eval_matrix(self.ctx, self.form, geom, [None, u, u], prec, out=K)
-        if mk_events:
-            mk_events[1].record()
+        rec(2)
         fe.eval_residual(self.ctx, self.form, geom, [None, u, u], prec, out=r)
         fe.assemble_vector(self.ctx, self.asm, 3, r, prec, out=g,
                            flags=0 if prec == "f64" else fe.ASSEMBLE_COMPENSATED)
+        rec(3)
 
 
 def convect_measure(n, device, ws, flush, ref, hbm_peak, steps=5, warmup=3):
@@ -430,7 +453,7 @@ def convect_measure(n, device, ws, flush, ref, hbm_peak, steps=5, warmup=3):
                        "u = a sin(pi x) cos(pi y); step = FP64 geometry + K_e(u) (Eq. fe4) + r_e(u) + "
                        "assembly" % (n, cw.E), "elements": cw.E}
     for prec in ("f32", "f64"):
-        st, mt = timed_steps(cw, prec, steps, warmup, ws, flush)
+        st, mt, _ = timed_steps(cw, prec, steps, warmup, ws, flush)
         t = max_over_ranks(sum(st), ws)
         mat = sum(mt) / len(mt)
         d = {"value": ws * cw.E * steps / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps, "matrix_ms": mat}
@@ -815,7 +838,7 @@ def main():
         else:
             prec = DEFAULT_MIXED  # no oracle sample on this rank: the precision the N = 1 run selects
     with ClockSampler(local) as clk:
-        step_ms, mat_ms = timed_steps(wl, prec, args.steps, args.warmup, ws, flush)
+        step_ms, mat_ms, parts = timed_steps(wl, prec, args.steps, args.warmup, ws, flush)
     total_ms = max_over_ranks(sum(step_ms), ws)
     ms_per_step = total_ms / args.steps
     value = ws * wl.E * args.steps / (total_ms / 1e3)
@@ -828,15 +851,24 @@ def main():
         "dtype": "f32" if prec != "f64" else "f64", "data": "synthetic",
         "config": {"workload": "Q2 linear elasticity, %d^3 = %d hexes (27 nodes, 27 Gauss points), "
                                "+-0.15h interior perturbation seed 1, per-element Lame lambda~U[0.5,2], "
-                               "mu~U[0.2,1], u~N(0,1); step = FP64 geometry + K_e (81x81) + r_e + "
-                               "compensated assembly" % (args.n, wl.E),
+                               "mu~U[0.2,1], u~N(0,1); step = FP64 geometry (computed by the residual "
+                               "kernel) + r_e + K_e (81x81) + compensated assembly" % (args.n, wl.E),
                    "elements": wl.E, "geometry_dtype": "f64", "contraction": prec,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
         "roofline": {"kernel": "k_matrix (fe_eval_matrix, %s)" % prec, "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
                      "traffic": None, "bytes_per_elem": bytes_alg / wl.E, "avg_ms": mat_avg},
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": kernels_per_step(prec) * args.steps,
+        "step_parts_ms": parts,
     }
+    if prec != "f64":
+        # the kernel that computes the FP64 geometry and the residual: FP64-bound
+        gf = wl.E * GEOMETRY_FLOPS_PER_ELEM_Q2 / (parts["geometry_and_residual"] / 1e3) / 1e12
+        line["roofline_geometry_residual"] = {
+            "kernel": "k_residual_geo (FP64 geometry + r_e, f32)", "bound": "fp64", "achieved": gf,
+            "peak": FP64_PEAK_TFLOPS_NOMINAL, "peak_source": "nominal", "unit": "TFLOP/s",
+            "frac": gf / FP64_PEAK_TFLOPS_NOMINAL, "flops_per_elem": GEOMETRY_FLOPS_PER_ELEM_Q2,
+            "avg_ms": parts["geometry_and_residual"]}
     line["clocks"] = clk.summary()
     if ladder is not None:
         line["precision_ladder"] = ladder
@@ -844,10 +876,10 @@ def main():
         wl.drop(prec)
         # plain FP64 path, same step
         f64_steps = 3
-        s64, m64 = timed_steps(wl, "f64", f64_steps, 1, ws, flush)
+        s64, m64, p64 = timed_steps(wl, "f64", f64_steps, 1, ws, flush)
         t64 = max_over_ranks(sum(s64), ws)
         line["fp64_path"] = {"value": ws * wl.E * f64_steps / (t64 / 1e3), "unit": UNIT,
-                             "ms_per_step": t64 / f64_steps, "matrix_ms": sum(m64) / len(m64)}
+                             "ms_per_step": t64 / f64_steps, "matrix_ms": sum(m64) / len(m64), "parts_ms": p64}
         errs, nsamp = sampled_errors(wl, ["f64"], ref)
         wl.drop("f64")
         wl.step(prec)

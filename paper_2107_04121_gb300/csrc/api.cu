@@ -421,7 +421,16 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
         return from_cuda(e, "fe_eval_residual");
     }
     if (!args || (!args[form->state_op] && g->mesh.n_elems > 0)) return FE_ERR_INVALID_ARG;
-    cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, to_cuda(stream));
+    fe_geometry_h *gm = const_cast<fe_geometry_h *>(g);
+    cudaError_t e;
+    if (gm->pending && prec != FE_F64 && fe_residual_geometry_fusable(gm, form)) {  // float32 residual kernels
+        // a stale deferred handle that keeps only the float32 copy: the residual
+        // kernel computes the FP64 geometry of its elements and stores the copy
+        e = fe_launch_residual_geometry(gm, form, mat, args[form->state_op], r_out, ctx->d_status, to_cuda(stream));
+        if (e == cudaSuccess) gm->pending = 0;
+        return from_cuda(e, "fe_eval_residual");
+    }
+    e = settle_geometry(gm, ctx->d_status, to_cuda(stream));
     if (e == cudaSuccess) e = fe_launch_residual(g, form, mat, prec == FE_F64, args[form->state_op], r_out, ctx->d_status,
                                        to_cuda(stream));
     return from_cuda(e, "fe_eval_residual");

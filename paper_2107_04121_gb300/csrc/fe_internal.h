@@ -91,6 +91,12 @@ cudaError_t fe_launch_matrix(const fe_geometry_h *g, const fe_form_h *f, fe_mate
                              void *K, int sm_count, cudaStream_t s);
 cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
                                const void *u, void *r, unsigned long long *status, cudaStream_t s);
+// Residual of a stale float32-only deferred geometry with the geometry computed
+// in the same kernel (tensor-product bases with n1 == nq); stores the float32
+// copy of the handle.
+bool fe_residual_geometry_fusable(const fe_geometry_h *g, const fe_form_h *f);
+cudaError_t fe_launch_residual_geometry(fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u,
+                                        void *r, unsigned long long *st, cudaStream_t s);
 // Convective term on tensor-product hexahedra (sum factorisation): residual
 // (K == nullptr) or matrix (r == nullptr) of 'i,i.j,j' with gradient operand u
 // and advection operand w (global DOF vectors, 3 per node).

@@ -14,7 +14,7 @@
 //    point), J = sum_a x_a (x) grad phi_a directly (9N DFMA per point).
 // Both finish each point with the same cofactor inverse (about 40 FP64
 // operations).
-#include "fe_device.cuh"
+#include "geometry_body.cuh"
 
 namespace {
 
@@ -27,54 +27,44 @@ __device__ __forceinline__ void finish_point(const double J[3][3], double wq, lo
                                              float *__restrict__ jinv32, float *__restrict__ wdetj32,
                                              unsigned long long *__restrict__ status)
 {
-    const double J00 = J[0][0], J01 = J[0][1], J02 = J[0][2], J10 = J[1][0], J11 = J[1][1], J12 = J[1][2],
-                 J20 = J[2][0], J21 = J[2][1], J22 = J[2][2];
-    const double c00 = J11 * J22 - J12 * J21;
-    const double c01 = J12 * J20 - J10 * J22;
-    const double c02 = J10 * J21 - J11 * J20;
-    const double det = J00 * c00 + J01 * c01 + J02 * c02;
-    if (!(det > 0.0) || !isfinite(det)) fe_report(status, isfinite(det) ? FE_ERR_NONPOSITIVE_DETJ : FE_ERR_NONFINITE, e);
+    const double *Jf = &J[0][0];
     if (!jinv64) {
         // only the float32 copy is kept: J, det J and the cofactors are FP64 (they
         // carry the cancellation of distorted elements), the quotient that is
         // stored in float32 is formed in float32 (a few float32 ulps instead of
         // one; it saves the FP64 reciprocal and 10 FP64 multiplies per point)
-        const float rf = 1.0f / (float)det;
-        float *o = jinv32 + idx * 9;
-        o[0] = (float)c00 * rf;
-        o[3] = (float)c01 * rf;
-        o[6] = (float)c02 * rf;
-        o[1] = (float)(J02 * J21 - J01 * J22) * rf;
-        o[4] = (float)(J00 * J22 - J02 * J20) * rf;
-        o[7] = (float)(J01 * J20 - J00 * J21) * rf;
-        o[2] = (float)(J01 * J12 - J02 * J11) * rf;
-        o[5] = (float)(J02 * J10 - J00 * J12) * rf;
-        o[8] = (float)(J00 * J11 - J01 * J10) * rf;
-        wdetj32[idx] = (float)wq * (float)det;
+        float o[9], wd;
+        const double det = geo_point_f32(Jf, wq, o, wd);
+        const int bad = geo_det_status(det);
+        if (bad) fe_report(status, bad, e);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) jinv32[idx * 9 + k] = o[k];
+        wdetj32[idx] = wd;
         return;
     }
-    const double r = 1.0 / det;
+    double C[9];  // C[r][k]: J^-1[k][r] = C[r][k] / det J
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) C[r * 3 + k] = geo_cofactor(Jf, r, k);
+    const double det = geo_det(Jf, C[0], C[1], C[2]);
+    const int bad = geo_det_status(det);
+    if (bad) fe_report(status, bad, e);
+    const double rr = 1.0 / det;
     double inv[9];
-    inv[0] = c00 * r;
-    inv[3] = c01 * r;
-    inv[6] = c02 * r;
-    inv[1] = (J02 * J21 - J01 * J22) * r;
-    inv[4] = (J00 * J22 - J02 * J20) * r;
-    inv[7] = (J01 * J20 - J00 * J21) * r;
-    inv[2] = (J01 * J12 - J02 * J11) * r;
-    inv[5] = (J02 * J10 - J00 * J12) * r;
-    inv[8] = (J00 * J11 - J01 * J10) * r;
-    const double wd = wq * det;
-    if (jinv64) {
-        double *o = jinv64 + idx * 9;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) o[k] = inv[k];
-        wdetj64[idx] = wd;
-    }
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) inv[k * 3 + r] = __dmul_rn(C[r * 3 + k], rr);
+    const double wd = __dmul_rn(wq, det);
+    double *o = jinv64 + idx * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) o[k] = inv[k];
+    wdetj64[idx] = wd;
     if (jinv32) {
-        float *o = jinv32 + idx * 9;
+        float *o32 = jinv32 + idx * 9;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) o[k] = (float)inv[k];
+        for (int k = 0; k < 9; ++k) o32[k] = (float)inv[k];
         wdetj32[idx] = (float)wd;
     }
 }
@@ -219,51 +209,20 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry_co(const double *__re
             for (int c = 0; c < 3; ++c) sX[el][c][a] = coords[3 * node + c];
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x) {  // contract i
-            const int qx = t % N1, kj = (t / N1) % (N1 * N1), c = (t / N) % 3, el = t / (3 * N);
-            const double *x = &sX[el][c][kj * N1];
-            double u = 0.0;
-#pragma unroll
-            for (int i = 0; i < N1; ++i) u = fma(sB[qx][i], x[i], u);
-            sU[el][c][kj * N1 + qx] = u;
-        }
+        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x)  // contract i
+            geo_stage_x<N1>(t % (3 * N), sX[t / (3 * N)][0], sU[t / (3 * N)][0], &sB[0][0]);
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x) {  // contract j
-            const int qx = t % N1, qy = (t / N1) % N1, k = (t / (N1 * N1)) % N1, c = (t / N) % 3, el = t / (3 * N);
-            const double *x = &sU[el][c][k * N1 * N1 + qx];
-            double v = 0.0;
-#pragma unroll
-            for (int j = 0; j < N1; ++j) v = fma(sB[qy][j], x[j * N1], v);
-            sV[el][c][(k * N1 + qy) * N1 + qx] = v;
-        }
+        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x)  // contract j
+            geo_stage_y<N1>(t % (3 * N), sU[t / (3 * N)][0], sV[t / (3 * N)][0], &sB[0][0]);
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x) {  // contract k
-            const int qxy = t % (N1 * N1), qz = (t / (N1 * N1)) % N1, c = (t / N) % 3, el = t / (3 * N);
-            const double *x = &sV[el][c][qxy];
-            double p = 0.0;
-#pragma unroll
-            for (int k = 0; k < N1; ++k) p = fma(sB[qz][k], x[k * N1 * N1], p);
-            sX[el][c][qz * N1 * N1 + qxy] = p;
-        }
+        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x)  // contract k: x at the points
+            geo_stage_z<N1>(t % (3 * N), sV[t / (3 * N)][0], sX[t / (3 * N)][0], &sB[0][0]);
         __syncthreads();
         for (int t = threadIdx.x; t < ne * N; t += blockDim.x) {
             const int el = t / N, q = t % N;
-            const int qx = q % N1, qy = (q / N1) % N1, qz = q / (N1 * N1);
             double J[3][3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double *P = sX[el][c];
-                double j0 = 0.0, j1 = 0.0, j2 = 0.0;
-#pragma unroll
-                for (int p = 0; p < N1; ++p) {
-                    j0 = fma(sDq[qx][p], P[(qz * N1 + qy) * N1 + p], j0);
-                    j1 = fma(sDq[qy][p], P[(qz * N1 + p) * N1 + qx], j1);
-                    j2 = fma(sDq[qz][p], P[(p * N1 + qy) * N1 + qx], j2);
-                }
-                J[c][0] = j0;
-                J[c][1] = j1;
-                J[c][2] = j2;
-            }
+            for (int c = 0; c < 3; ++c) geo_jacobian_row<N1>(q, c, sX[el][0], &sDq[0][0], J[c]);
             finish_point(J, w[q], e0 + el, (e0 + el) * N + q, jinv64, wdetj64, jinv32, wdetj32, status);
         }
     }

@@ -13,7 +13,7 @@
 // so each element reads only J^-1 and w det J (40 bytes per quadrature point
 // in FP32) besides its DOFs, while the reference gradients (shared by all
 // elements) stay in shared memory.
-#include "fe_device.cuh"
+#include "geometry_body.cuh"
 
 namespace {
 
@@ -177,6 +177,266 @@ __global__ void __launch_bounds__(THREADS) k_residual(const T *__restrict__ jinv
 //            contractions (z, y, x)
 // Each thread computes one whole 1-D line of a stage (n1 or nq outputs) with
 // the 1-D tables in registers; EPB elements per CTA, barriers between stages.
+// Per-element material of ne elements into shared memory: the 6x6 D (Voigt,
+// MATK 2), (lambda, mu) (MATK 1) or a scalar coefficient (1 without one).
+template <typename T, int MATK, int THREADS>
+__device__ __forceinline__ void load_material(int ne, long long e0, const double *__restrict__ mat, int mat_t,
+                                              T (*__restrict__ sM)[36])
+{
+    if constexpr (MATK == 2) {
+        for (int t = threadIdx.x; t < ne * 36; t += THREADS) {
+            const int el = t / 36, I = (t % 36) / 6, Kv = t % 6;
+            const long long e = e0 + el;
+            sM[el][t % 36] = (T)(mat_t ? mat[e * 36 + Kv * 6 + I] : mat[e * 36 + I * 6 + Kv]);
+        }
+    } else if constexpr (MATK == 1) {
+        for (int t = threadIdx.x; t < ne * 2; t += THREADS) sM[t / 2][t % 2] = (T)mat[e0 * 2 + t];
+    } else {
+        for (int t = threadIdx.x; t < ne; t += THREADS) sM[t][0] = mat ? (T)mat[e0 + t] : (T)1;
+    }
+}
+
+// The stages of k_residual_sf after the loads, for ne elements starting at e0
+// whose DOFs (sU), J^-1 (sJ), w det J (sW) and material (sM) are in shared
+// memory; B, D = 1-D tables (nq, n1) in registers.  Ends with r written.
+template <typename T, int N1, int NQ, int KIND, int MATK, int EPB, int THREADS>
+__device__ __forceinline__ void residual_sf_stages(
+    int ne, int nc, long long e0, T (*__restrict__ sU)[KIND == FK_LAPLACE ? 1 : 3][N1 * N1 * N1],
+    T (*__restrict__ sX)[KIND == FK_LAPLACE ? 1 : 3][KIND != FK_MASS ? 2 : 1][N1 * N1 * NQ],
+    T (*__restrict__ sY)[KIND == FK_LAPLACE ? 1 : 3][KIND != FK_MASS ? 3 : 1][N1 * NQ * NQ],
+    T (*__restrict__ sQ)[KIND == FK_LAPLACE ? 1 : 3][KIND != FK_MASS ? 3 : 1][NQ * NQ * NQ],
+    T (*__restrict__ sJ)[NQ * NQ * NQ][9], T (*__restrict__ sW)[NQ * NQ * NQ], T (*__restrict__ sM)[36],
+    const T (&B)[NQ][N1], const T (&D)[NQ][N1], T *__restrict__ r)
+{
+    constexpr int N = N1 * N1 * N1, Q = NQ * NQ * NQ;
+    constexpr bool GRAD = KIND != FK_MASS;
+    constexpr int NC = KIND == FK_LAPLACE ? 1 : 3;
+    constexpr int NM = GRAD ? 3 : 1;
+    (void)NC;
+    (void)NM;
+    // ---- phase 1, x: line (el, c, k, j) -> sX[0] = B_x U, sX[1] = D_x U at qx = 0..nq-1
+    for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
+        const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
+        T x[N1];
+#pragma unroll
+        for (int i = 0; i < N1; ++i) x[i] = sU[el][c][kj * N1 + i];
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) {
+            T v0 = 0, v1 = 0;
+#pragma unroll
+            for (int i = 0; i < N1; ++i) {
+                v0 = fma(B[qx][i], x[i], v0);
+                if constexpr (GRAD) v1 = fma(D[qx][i], x[i], v1);
+            }
+            sX[el][c][0][kj * NQ + qx] = v0;
+            if constexpr (GRAD) sX[el][c][1][kj * NQ + qx] = v1;
+        }
+    }
+    __syncthreads();
+    // ---- phase 1, y: line (el, c, k, qx) -> at qy: [0] B_y B_x, [1] D_y B_x, [2] B_y D_x
+    for (int t = threadIdx.x; t < ne * nc * N1 * NQ; t += THREADS) {
+        const int qx = t % NQ, k = (t / NQ) % N1, c = (t / (NQ * N1)) % nc, el = t / (NQ * N1 * nc);
+        T a0[N1], a1[N1];
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+            a0[j] = sX[el][c][0][(k * N1 + j) * NQ + qx];
+            if constexpr (GRAD) a1[j] = sX[el][c][1][(k * N1 + j) * NQ + qx];
+        }
+#pragma unroll
+        for (int qy = 0; qy < NQ; ++qy) {
+            T v0 = 0, v1 = 0, v2 = 0;
+#pragma unroll
+            for (int j = 0; j < N1; ++j) {
+                v0 = fma(B[qy][j], a0[j], v0);
+                if constexpr (GRAD) {
+                    v1 = fma(D[qy][j], a0[j], v1);
+                    v2 = fma(B[qy][j], a1[j], v2);
+                }
+            }
+            const int o = (k * NQ + qy) * NQ + qx;
+            sY[el][c][0][o] = v0;
+            if constexpr (GRAD) {
+                sY[el][c][1][o] = v1;
+                sY[el][c][2][o] = v2;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- phase 1, z: line (el, c, qy, qx) -> sQ[m] at qz = d u_c / d xi_m (or u_c)
+    for (int t = threadIdx.x; t < ne * nc * NQ * NQ; t += THREADS) {
+        const int qx = t % NQ, qy = (t / NQ) % NQ, c = (t / (NQ * NQ)) % nc, el = t / (NQ * NQ * nc);
+        T y0[N1], y1[N1], y2[N1];
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            const int o = (k * NQ + qy) * NQ + qx;
+            y0[k] = sY[el][c][0][o];
+            if constexpr (GRAD) {
+                y1[k] = sY[el][c][1][o];
+                y2[k] = sY[el][c][2][o];
+            }
+        }
+#pragma unroll
+        for (int qz = 0; qz < NQ; ++qz) {
+            const int q = (qz * NQ + qy) * NQ + qx;
+            T gx = 0, gy = 0, gz = 0;
+#pragma unroll
+            for (int k = 0; k < N1; ++k) {
+                if constexpr (GRAD) {
+                    gx = fma(B[qz][k], y2[k], gx);
+                    gy = fma(B[qz][k], y1[k], gy);
+                    gz = fma(D[qz][k], y0[k], gz);
+                } else {
+                    gx = fma(B[qz][k], y0[k], gx);
+                }
+            }
+            sQ[el][c][0][q] = gx;
+            if constexpr (GRAD) {
+                sQ[el][c][1][q] = gy;
+                sQ[el][c][2][q] = gz;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- pointwise flux, in place: F_c,m(q) with r = sum_q sum_m F_c,m dphi_a/dxi_m
+    for (int t = threadIdx.x; t < ne * Q; t += THREADS) {
+        const int el = t / Q, q = t % Q;
+        const T wd = sW[el][q];
+        if constexpr (KIND == FK_MASS) {
+            const T cw = sM[el][0] * wd;
+            for (int c = 0; c < nc; ++c) sQ[el][c][0][q] *= cw;
+        } else {
+            T Ji[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Ji[k] = sJ[el][q][k];
+            T H[NC][3];  // physical gradient H[c][j] = sum_m g[c][m] Jinv[m][j]
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const T g0 = sQ[el][c][0][q], g1 = sQ[el][c][1][q], g2 = sQ[el][c][2][q];
+#pragma unroll
+                for (int j = 0; j < 3; ++j) H[c][j] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
+            }
+            T S[NC][3];
+            if constexpr (KIND == FK_LAPLACE) {
+                const T cw = sM[el][0] * wd;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) S[0][j] = cw * H[0][j];
+            } else if constexpr (MATK == 1) {
+                // isotropic: sigma = lambda tr(e) I + 2 mu e
+                const T lam = sM[el][0] * wd, mu = sM[el][1] * wd;
+                const T tr = lam * (H[0][0] + H[1][1] + H[2][2]);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) S[i][j] = mu * (H[i][j] + H[j][i]) + (i == j ? tr : (T)0);
+            } else {
+                const T *Dm = sM[el];
+                const T eps[6] = {H[0][0], H[1][1], H[2][2], H[0][1] + H[1][0], H[0][2] + H[2][0],
+                                  H[1][2] + H[2][1]};
+                T sig[6];
+#pragma unroll
+                for (int I = 0; I < 6; ++I) {
+                    T acc = 0;
+#pragma unroll
+                    for (int Kv = 0; Kv < 6; ++Kv) acc = fma(Dm[I * 6 + Kv], eps[Kv], acc);
+                    sig[I] = wd * acc;
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) S[i][j] = sig[fe_voigt(i, j)];
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    sQ[el][c][m][q] = S[c][0] * Ji[m * 3] + S[c][1] * Ji[m * 3 + 1] + S[c][2] * Ji[m * 3 + 2];
+        }
+    }
+    __syncthreads();
+    // ---- phase 2, z^T: line (el, c, qy, qx) -> at k: [0] B_z F_x, [1] B_z F_y, [2] D_z F_z
+    for (int t = threadIdx.x; t < ne * nc * NQ * NQ; t += THREADS) {
+        const int qx = t % NQ, qy = (t / NQ) % NQ, c = (t / (NQ * NQ)) % nc, el = t / (NQ * NQ * nc);
+        T f0[NQ], f1[NQ], f2[NQ];
+#pragma unroll
+        for (int qz = 0; qz < NQ; ++qz) {
+            const int q = (qz * NQ + qy) * NQ + qx;
+            f0[qz] = sQ[el][c][0][q];
+            if constexpr (GRAD) {
+                f1[qz] = sQ[el][c][1][q];
+                f2[qz] = sQ[el][c][2][q];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < N1; ++k) {
+            T v0 = 0, v1 = 0, v2 = 0;
+#pragma unroll
+            for (int qz = 0; qz < NQ; ++qz) {
+                v0 = fma(B[qz][k], f0[qz], v0);
+                if constexpr (GRAD) {
+                    v1 = fma(B[qz][k], f1[qz], v1);
+                    v2 = fma(D[qz][k], f2[qz], v2);
+                }
+            }
+            const int o = (k * NQ + qy) * NQ + qx;
+            sY[el][c][0][o] = v0;
+            if constexpr (GRAD) {
+                sY[el][c][1][o] = v1;
+                sY[el][c][2][o] = v2;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- phase 2, y^T: line (el, c, k, qx) -> at j: [0] B_y [0], [1] D_y [1] + B_y [2]
+    for (int t = threadIdx.x; t < ne * nc * N1 * NQ; t += THREADS) {
+        const int qx = t % NQ, k = (t / NQ) % N1, c = (t / (NQ * N1)) % nc, el = t / (NQ * N1 * nc);
+        T y0[NQ], y1[NQ], y2[NQ];
+#pragma unroll
+        for (int qy = 0; qy < NQ; ++qy) {
+            const int o = (k * NQ + qy) * NQ + qx;
+            y0[qy] = sY[el][c][0][o];
+            if constexpr (GRAD) {
+                y1[qy] = sY[el][c][1][o];
+                y2[qy] = sY[el][c][2][o];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < N1; ++j) {
+            T v0 = 0, v1 = 0;
+#pragma unroll
+            for (int qy = 0; qy < NQ; ++qy) {
+                v0 = fma(B[qy][j], y0[qy], v0);
+                if constexpr (GRAD) v1 = fma(D[qy][j], y1[qy], fma(B[qy][j], y2[qy], v1));
+            }
+            sX[el][c][0][(k * N1 + j) * NQ + qx] = v0;
+            if constexpr (GRAD) sX[el][c][1][(k * N1 + j) * NQ + qx] = v1;
+        }
+    }
+    __syncthreads();
+    // ---- phase 2, x^T: line (el, c, k, j) -> r at i = D_x [0] + B_x [1] (mass: B_x [0])
+    for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
+        const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
+        T x0[NQ], x1[NQ];
+#pragma unroll
+        for (int qx = 0; qx < NQ; ++qx) {
+            x0[qx] = sX[el][c][0][kj * NQ + qx];
+            if constexpr (GRAD) x1[qx] = sX[el][c][1][kj * NQ + qx];
+        }
+        T *ro = r + (e0 + el) * (long long)nc * N + c * N + kj * N1;
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            T v = 0;
+#pragma unroll
+            for (int qx = 0; qx < NQ; ++qx) {
+                if constexpr (GRAD)
+                    v = fma(D[qx][i], x0[qx], fma(B[qx][i], x1[qx], v));
+                else
+                    v = fma(B[qx][i], x0[qx], v);
+            }
+            ro[i] = v;
+        }
+    }
+}
+
 template <typename T, int N1, int NQ, int KIND, int MATK, int EPB, int THREADS>
 __global__ void __launch_bounds__(THREADS) k_residual_sf(const T *__restrict__ jinv, const T *__restrict__ wdetj,
                                                          const T *__restrict__ b1d, const T *__restrict__ d1d,
@@ -219,239 +479,125 @@ __global__ void __launch_bounds__(THREADS) k_residual_sf(const T *__restrict__ j
             if (!ok) fe_report(status, FE_ERR_SHAPE, e0 + el);
             for (int c = 0; c < nc; ++c) sU[el][c][a] = ok ? u[node * nc + c] : (T)0;
         }
-        if constexpr (MATK == 2) {
-            for (int t = threadIdx.x; t < ne * 36; t += THREADS) {
-                const int el = t / 36, I = (t % 36) / 6, Kv = t % 6;
-                const long long e = e0 + el;
-                sM[el][t % 36] = (T)(mat_t ? mat[e * 36 + Kv * 6 + I] : mat[e * 36 + I * 6 + Kv]);
-            }
-        } else if constexpr (MATK == 1) {
-            for (int t = threadIdx.x; t < ne * 2; t += THREADS) sM[t / 2][t % 2] = (T)mat[e0 * 2 + t];
-        } else {
-            for (int t = threadIdx.x; t < ne; t += THREADS) sM[t][0] = mat ? (T)mat[e0 + t] : (T)1;
-        }
+        load_material<T, MATK, THREADS>(ne, e0, mat, mat_t, sM);
         __syncthreads();
-        // ---- phase 1, x: line (el, c, k, j) -> sX[0] = B_x U, sX[1] = D_x U at qx = 0..nq-1
-        for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
-            const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
-            T x[N1];
+        residual_sf_stages<T, N1, NQ, KIND, MATK, EPB, THREADS>(ne, nc, e0, sU, sX, sY, sQ, sJ, sW, sM, B, D, r);
+    }
+}
+
+// Residual of a float32-only geometry that is stale, with the geometry computed
+// here (n1 == nq tensor-product bases): per group of EPB elements the FP64
+// collocation stages of the geometry kernel (same roundings), whose float32
+// J^-1 and w det J are stored in the handle and kept in shared memory for the
+// stages of k_residual_sf.  The FP64 work of one group overlaps the float32
+// stages of the other CTAs on the SM.  The FP64 work buffers share the space
+// of the stage buffers, which are dead until the geometry is done.
+template <int N1, int KIND, int MATK, int EPB, int THREADS>
+struct ResGeoSmem {
+    static constexpr int N = N1 * N1 * N1, NQ = N1, Q = N;
+    static constexpr bool GRAD = KIND != FK_MASS;
+    static constexpr int NC = KIND == FK_LAPLACE ? 1 : 3, NM = GRAD ? 3 : 1;
+    static constexpr int LX = N1 * N1 * NQ, LY = N1 * NQ * NQ;
+    static constexpr int U = 0;                                   // float [EPB][NC][N]
+    static constexpr int X = U + EPB * NC * N * 4;                // float [EPB][NC][GRAD?2:1][LX]
+    static constexpr int Y = X + EPB * NC * (GRAD ? 2 : 1) * LX * 4;  // float [EPB][NC][NM][LY]
+    static constexpr int QV = Y + EPB * NC * NM * LY * 4;         // float [EPB][NC][NM][Q]
+    static constexpr int STAGE_END = QV + EPB * NC * NM * Q * 4;
+    static constexpr int G = (X + 7) / 8 * 8;                     // double [3][EPB][3][N], over the stage buffers
+    static constexpr int G_END = G + 3 * EPB * 3 * N * 8;
+    static constexpr int J = ((STAGE_END > G_END ? STAGE_END : G_END) + 15) / 16 * 16;  // float [EPB][Q][9]
+    static constexpr int W = J + EPB * Q * 9 * 4;                 // float [EPB][Q]
+    static constexpr int M = W + EPB * Q * 4;                     // float [EPB][36]
+    static constexpr int T64 = (M + EPB * 36 * 4 + 7) / 8 * 8;   // double B[N1][N1], Dq[N1][N1], w[Q]
+    static constexpr int BYTES = T64 + (2 * N1 * N1 + Q) * 8;
+};
+
+template <int N1, int KIND, int MATK, int EPB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_residual_geo(const double *__restrict__ coords,
+                                                          const int32_t *__restrict__ conn, long long E,
+                                                          long long n_nodes, const double *__restrict__ b1d64,
+                                                          const double *__restrict__ dq64,
+                                                          const double *__restrict__ w64,
+                                                          const float *__restrict__ b1d, const float *__restrict__ d1d,
+                                                          float *__restrict__ jinv_out, float *__restrict__ wdetj_out,
+                                                          int ncomp, const double *__restrict__ mat, int mat_t,
+                                                          const float *__restrict__ u, float *__restrict__ r,
+                                                          unsigned long long *__restrict__ status)
+{
+    using L = ResGeoSmem<N1, KIND, MATK, EPB, THREADS>;
+    using T = float;
+    constexpr int N = L::N, NQ = L::NQ, Q = L::Q, NC = L::NC, NM = L::NM, LX = L::LX, LY = L::LY;
+    constexpr bool GRAD = L::GRAD;
+    static_assert(L::BYTES <= 48 * 1024, "static shared memory above 48 KB");
+    __shared__ __align__(16) unsigned char raw[L::BYTES];
+    T(*sU)[NC][N] = reinterpret_cast<T(*)[NC][N]>(raw + L::U);
+    T(*sX)[NC][GRAD ? 2 : 1][LX] = reinterpret_cast<T(*)[NC][GRAD ? 2 : 1][LX]>(raw + L::X);
+    T(*sY)[NC][NM][LY] = reinterpret_cast<T(*)[NC][NM][LY]>(raw + L::Y);
+    T(*sQ)[NC][NM][Q] = reinterpret_cast<T(*)[NC][NM][Q]>(raw + L::QV);
+    T(*sJ)[Q][9] = reinterpret_cast<T(*)[Q][9]>(raw + L::J);
+    T(*sW)[Q] = reinterpret_cast<T(*)[Q]>(raw + L::W);
+    T(*sM)[36] = reinterpret_cast<T(*)[36]>(raw + L::M);
+    double *gX = reinterpret_cast<double *>(raw + L::G);  // [EPB][3][N] each
+    double *gU = gX + EPB * 3 * N;
+    double *gV = gU + EPB * 3 * N;
+    double *gB = reinterpret_cast<double *>(raw + L::T64);
+    double *gDq = gB + N1 * N1;
+    double *gw = gDq + N1 * N1;
+    for (int i = threadIdx.x; i < 2 * N1 * N1 + Q; i += THREADS)
+        gB[i] = i < N1 * N1 ? b1d64[i] : (i < 2 * N1 * N1 ? dq64[i - N1 * N1] : w64[i - 2 * N1 * N1]);
+    T B[NQ][N1], D[NQ][N1];
 #pragma unroll
-            for (int i = 0; i < N1; ++i) x[i] = sU[el][c][kj * N1 + i];
+    for (int q = 0; q < NQ; ++q)
 #pragma unroll
-            for (int qx = 0; qx < NQ; ++qx) {
-                T v0 = 0, v1 = 0;
-#pragma unroll
-                for (int i = 0; i < N1; ++i) {
-                    v0 = fma(B[qx][i], x[i], v0);
-                    if constexpr (GRAD) v1 = fma(D[qx][i], x[i], v1);
-                }
-                sX[el][c][0][kj * NQ + qx] = v0;
-                if constexpr (GRAD) sX[el][c][1][kj * NQ + qx] = v1;
-            }
+        for (int i = 0; i < N1; ++i) {
+            B[q][i] = b1d[q * N1 + i];
+            D[q][i] = d1d[q * N1 + i];
         }
+    const int nc = ncomp;
+    for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
+        const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
         __syncthreads();
-        // ---- phase 1, y: line (el, c, k, qx) -> at qy: [0] B_y B_x, [1] D_y B_x, [2] B_y D_x
-        for (int t = threadIdx.x; t < ne * nc * N1 * NQ; t += THREADS) {
-            const int qx = t % NQ, k = (t / NQ) % N1, c = (t / (NQ * N1)) % nc, el = t / (NQ * N1 * nc);
-            T a0[N1], a1[N1];
+        for (int t = threadIdx.x; t < ne * N; t += THREADS) {
+            const int el = t / N, a = t % N;
+            const long long node = conn[(e0 + el) * N + a];
+            const bool ok = (unsigned long long)node < (unsigned long long)n_nodes;  // never read outside
+            if (!ok) fe_report(status, FE_ERR_SHAPE, e0 + el);
+            const long long nd = ok ? node : 0;
 #pragma unroll
-            for (int j = 0; j < N1; ++j) {
-                a0[j] = sX[el][c][0][(k * N1 + j) * NQ + qx];
-                if constexpr (GRAD) a1[j] = sX[el][c][1][(k * N1 + j) * NQ + qx];
-            }
-#pragma unroll
-            for (int qy = 0; qy < NQ; ++qy) {
-                T v0 = 0, v1 = 0, v2 = 0;
-#pragma unroll
-                for (int j = 0; j < N1; ++j) {
-                    v0 = fma(B[qy][j], a0[j], v0);
-                    if constexpr (GRAD) {
-                        v1 = fma(D[qy][j], a0[j], v1);
-                        v2 = fma(B[qy][j], a1[j], v2);
-                    }
-                }
-                const int o = (k * NQ + qy) * NQ + qx;
-                sY[el][c][0][o] = v0;
-                if constexpr (GRAD) {
-                    sY[el][c][1][o] = v1;
-                    sY[el][c][2][o] = v2;
-                }
-            }
+            for (int c = 0; c < 3; ++c) gX[(el * 3 + c) * N + a] = coords[3 * nd + c];
+            for (int c = 0; c < nc; ++c) sU[el][c][a] = ok ? u[node * nc + c] : (T)0;
         }
+        load_material<T, MATK, THREADS>(ne, e0, mat, mat_t, sM);
         __syncthreads();
-        // ---- phase 1, z: line (el, c, qy, qx) -> sQ[m] at qz = d u_c / d xi_m (or u_c)
-        for (int t = threadIdx.x; t < ne * nc * NQ * NQ; t += THREADS) {
-            const int qx = t % NQ, qy = (t / NQ) % NQ, c = (t / (NQ * NQ)) % nc, el = t / (NQ * NQ * nc);
-            T y0[N1], y1[N1], y2[N1];
-#pragma unroll
-            for (int k = 0; k < N1; ++k) {
-                const int o = (k * NQ + qy) * NQ + qx;
-                y0[k] = sY[el][c][0][o];
-                if constexpr (GRAD) {
-                    y1[k] = sY[el][c][1][o];
-                    y2[k] = sY[el][c][2][o];
-                }
-            }
-#pragma unroll
-            for (int qz = 0; qz < NQ; ++qz) {
-                const int q = (qz * NQ + qy) * NQ + qx;
-                T gx = 0, gy = 0, gz = 0;
-#pragma unroll
-                for (int k = 0; k < N1; ++k) {
-                    if constexpr (GRAD) {
-                        gx = fma(B[qz][k], y2[k], gx);
-                        gy = fma(B[qz][k], y1[k], gy);
-                        gz = fma(D[qz][k], y0[k], gz);
-                    } else {
-                        gx = fma(B[qz][k], y0[k], gx);
-                    }
-                }
-                sQ[el][c][0][q] = gx;
-                if constexpr (GRAD) {
-                    sQ[el][c][1][q] = gy;
-                    sQ[el][c][2][q] = gz;
-                }
-            }
-        }
+        for (int t = threadIdx.x; t < ne * 3 * N; t += THREADS)  // geometry: contract i
+            geo_stage_x<N1>(t % (3 * N), gX + (t / (3 * N)) * 3 * N, gU + (t / (3 * N)) * 3 * N, gB);
         __syncthreads();
-        // ---- pointwise flux, in place: F_c,m(q) with r = sum_q sum_m F_c,m dphi_a/dxi_m
+        for (int t = threadIdx.x; t < ne * 3 * N; t += THREADS)  // contract j
+            geo_stage_y<N1>(t % (3 * N), gU + (t / (3 * N)) * 3 * N, gV + (t / (3 * N)) * 3 * N, gB);
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 3 * N; t += THREADS)  // contract k: x at the points
+            geo_stage_z<N1>(t % (3 * N), gV + (t / (3 * N)) * 3 * N, gX + (t / (3 * N)) * 3 * N, gB);
+        __syncthreads();
         for (int t = threadIdx.x; t < ne * Q; t += THREADS) {
             const int el = t / Q, q = t % Q;
-            const T wd = sW[el][q];
-            if constexpr (KIND == FK_MASS) {
-                const T cw = sM[el][0] * wd;
-                for (int c = 0; c < nc; ++c) sQ[el][c][0][q] *= cw;
-            } else {
-                T Ji[9];
+            double J[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) Ji[k] = sJ[el][q][k];
-                T H[NC][3];  // physical gradient H[c][j] = sum_m g[c][m] Jinv[m][j]
+            for (int c = 0; c < 3; ++c) geo_jacobian_row<N1>(q, c, gX + el * 3 * N, gDq, J + 3 * c);
+            float o[9], wd;
+            const double det = geo_point_f32(J, gw[q], o, wd);
+            const int bad = geo_det_status(det);
+            if (bad) fe_report(status, bad, e0 + el);
+            const long long idx = (e0 + el) * Q + q;
 #pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const T g0 = sQ[el][c][0][q], g1 = sQ[el][c][1][q], g2 = sQ[el][c][2][q];
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) H[c][j] = g0 * Ji[j] + g1 * Ji[3 + j] + g2 * Ji[6 + j];
-                }
-                T S[NC][3];
-                if constexpr (KIND == FK_LAPLACE) {
-                    const T cw = sM[el][0] * wd;
-#pragma unroll
-                    for (int j = 0; j < 3; ++j) S[0][j] = cw * H[0][j];
-                } else if constexpr (MATK == 1) {
-                    // isotropic: sigma = lambda tr(e) I + 2 mu e
-                    const T lam = sM[el][0] * wd, mu = sM[el][1] * wd;
-                    const T tr = lam * (H[0][0] + H[1][1] + H[2][2]);
-#pragma unroll
-                    for (int i = 0; i < 3; ++i)
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) S[i][j] = mu * (H[i][j] + H[j][i]) + (i == j ? tr : (T)0);
-                } else {
-                    const T *Dm = sM[el];
-                    const T eps[6] = {H[0][0], H[1][1], H[2][2], H[0][1] + H[1][0], H[0][2] + H[2][0],
-                                      H[1][2] + H[2][1]};
-                    T sig[6];
-#pragma unroll
-                    for (int I = 0; I < 6; ++I) {
-                        T acc = 0;
-#pragma unroll
-                        for (int Kv = 0; Kv < 6; ++Kv) acc = fma(Dm[I * 6 + Kv], eps[Kv], acc);
-                        sig[I] = wd * acc;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 3; ++i)
-#pragma unroll
-                        for (int j = 0; j < 3; ++j) S[i][j] = sig[fe_voigt(i, j)];
-                }
-#pragma unroll
-                for (int c = 0; c < NC; ++c)
-#pragma unroll
-                    for (int m = 0; m < 3; ++m)
-                        sQ[el][c][m][q] = S[c][0] * Ji[m * 3] + S[c][1] * Ji[m * 3 + 1] + S[c][2] * Ji[m * 3 + 2];
+            for (int k = 0; k < 9; ++k) {
+                jinv_out[idx * 9 + k] = o[k];
+                sJ[el][q][k] = o[k];
             }
+            wdetj_out[idx] = wd;
+            sW[el][q] = wd;
         }
         __syncthreads();
-        // ---- phase 2, z^T: line (el, c, qy, qx) -> at k: [0] B_z F_x, [1] B_z F_y, [2] D_z F_z
-        for (int t = threadIdx.x; t < ne * nc * NQ * NQ; t += THREADS) {
-            const int qx = t % NQ, qy = (t / NQ) % NQ, c = (t / (NQ * NQ)) % nc, el = t / (NQ * NQ * nc);
-            T f0[NQ], f1[NQ], f2[NQ];
-#pragma unroll
-            for (int qz = 0; qz < NQ; ++qz) {
-                const int q = (qz * NQ + qy) * NQ + qx;
-                f0[qz] = sQ[el][c][0][q];
-                if constexpr (GRAD) {
-                    f1[qz] = sQ[el][c][1][q];
-                    f2[qz] = sQ[el][c][2][q];
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < N1; ++k) {
-                T v0 = 0, v1 = 0, v2 = 0;
-#pragma unroll
-                for (int qz = 0; qz < NQ; ++qz) {
-                    v0 = fma(B[qz][k], f0[qz], v0);
-                    if constexpr (GRAD) {
-                        v1 = fma(B[qz][k], f1[qz], v1);
-                        v2 = fma(D[qz][k], f2[qz], v2);
-                    }
-                }
-                const int o = (k * NQ + qy) * NQ + qx;
-                sY[el][c][0][o] = v0;
-                if constexpr (GRAD) {
-                    sY[el][c][1][o] = v1;
-                    sY[el][c][2][o] = v2;
-                }
-            }
-        }
-        __syncthreads();
-        // ---- phase 2, y^T: line (el, c, k, qx) -> at j: [0] B_y [0], [1] D_y [1] + B_y [2]
-        for (int t = threadIdx.x; t < ne * nc * N1 * NQ; t += THREADS) {
-            const int qx = t % NQ, k = (t / NQ) % N1, c = (t / (NQ * N1)) % nc, el = t / (NQ * N1 * nc);
-            T y0[NQ], y1[NQ], y2[NQ];
-#pragma unroll
-            for (int qy = 0; qy < NQ; ++qy) {
-                const int o = (k * NQ + qy) * NQ + qx;
-                y0[qy] = sY[el][c][0][o];
-                if constexpr (GRAD) {
-                    y1[qy] = sY[el][c][1][o];
-                    y2[qy] = sY[el][c][2][o];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < N1; ++j) {
-                T v0 = 0, v1 = 0;
-#pragma unroll
-                for (int qy = 0; qy < NQ; ++qy) {
-                    v0 = fma(B[qy][j], y0[qy], v0);
-                    if constexpr (GRAD) v1 = fma(D[qy][j], y1[qy], fma(B[qy][j], y2[qy], v1));
-                }
-                sX[el][c][0][(k * N1 + j) * NQ + qx] = v0;
-                if constexpr (GRAD) sX[el][c][1][(k * N1 + j) * NQ + qx] = v1;
-            }
-        }
-        __syncthreads();
-        // ---- phase 2, x^T: line (el, c, k, j) -> r at i = D_x [0] + B_x [1] (mass: B_x [0])
-        for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
-            const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
-            T x0[NQ], x1[NQ];
-#pragma unroll
-            for (int qx = 0; qx < NQ; ++qx) {
-                x0[qx] = sX[el][c][0][kj * NQ + qx];
-                if constexpr (GRAD) x1[qx] = sX[el][c][1][kj * NQ + qx];
-            }
-            T *ro = r + (e0 + el) * (long long)nc * N + c * N + kj * N1;
-#pragma unroll
-            for (int i = 0; i < N1; ++i) {
-                T v = 0;
-#pragma unroll
-                for (int qx = 0; qx < NQ; ++qx) {
-                    if constexpr (GRAD)
-                        v = fma(D[qx][i], x0[qx], fma(B[qx][i], x1[qx], v));
-                    else
-                        v = fma(B[qx][i], x0[qx], v);
-                }
-                ro[i] = v;
-            }
-        }
+        residual_sf_stages<T, N1, NQ, KIND, MATK, EPB, THREADS>(ne, nc, e0, sU, sX, sY, sQ, sJ, sW, sM, B, D, r);
     }
 }
 
@@ -515,6 +661,50 @@ cudaError_t dispatch_sf(const fe_geometry_h *g, const fe_form_h *f, fe_material_
     if (n1 == 3 && nq == 4) return dispatch_sf_kind<T, 3, 4, (D ? 2 : 4), (D ? 1 : 2)>(g, f, mat, u, r, st, s);
     if (n1 == 4 && nq == 4) return dispatch_sf_kind<T, 4, 4, (D ? 2 : 4), 1>(g, f, mat, u, r, st, s);
     return cudaErrorInvalidValue;
+}
+
+template <int N1, int KIND, int MATK, int EPB>
+cudaError_t launch_res_geo(fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
+                           unsigned long long *st, cudaStream_t s)
+{
+    constexpr int THREADS = 256;
+    auto kern = k_residual_geo<N1, KIND, MATK, EPB, THREADS>;
+    static FeLaunchCache cache;
+    long long cap = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int dev, long long *v) {
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, THREADS, 0);
+            if (e2 != cudaSuccess) return e2;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            *v = (long long)per_sm * sms * 4;
+            return cudaSuccess;
+        },
+        &cap);
+    if (err != cudaSuccess) return err;
+    const long long E = g->mesh.n_elems;
+    long long blocks = (E + EPB - 1) / EPB;
+    if (blocks > cap) blocks = cap;
+    kern<<<(unsigned)blocks, THREADS, 0, s>>>(g->mesh.coords, g->mesh.conn, E, g->mesh.n_nodes, g->d_b1d, g->d_dq,
+                                               g->d_w64, g->d_b1d32, g->d_d1d32, g->d_jinv32, g->d_wdetj32, f->ncomp,
+                                               mat.data, mat.transposed, (const float *)u, (float *)r, st);
+    return cudaGetLastError();
+}
+
+template <int N1, int EPB>
+cudaError_t dispatch_res_geo(fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
+                             unsigned long long *st, cudaStream_t s)
+{
+    switch (f->kind) {
+    case FK_LAPLACE: return launch_res_geo<N1, FK_LAPLACE, 0, EPB>(g, f, mat, u, r, st, s);
+    case FK_MASS: return launch_res_geo<N1, FK_MASS, 0, EPB>(g, f, mat, u, r, st, s);
+    case FK_ELASTICITY:
+        if (mat.kind == FE_MAT_LAME) return launch_res_geo<N1, FK_ELASTICITY, 1, EPB>(g, f, mat, u, r, st, s);
+        return launch_res_geo<N1, FK_ELASTICITY, 2, EPB>(g, f, mat, u, r, st, s);
+    }
+    return cudaErrorNotSupported;
 }
 
 template <typename T, int N, int Q, int KIND, int EPB>
@@ -589,4 +779,24 @@ cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_ma
     if (g->d_b1d)
         return f64 ? dispatch_sf<double>(g, f, mat, u, r, st, s) : dispatch_sf<float>(g, f, mat, u, r, st, s);
     return f64 ? dispatch<double>(g, f, mat, u, r, st, s) : dispatch<float>(g, f, mat, u, r, st, s);
+}
+
+bool fe_residual_geometry_fusable(const fe_geometry_h *g, const fe_form_h *f)
+{
+    if (!g->d_dq || g->n1d != g->nq1d || g->n1d < 2 || g->n1d > 4 || !g->d_jinv32 || g->is_view) return false;
+    if (!(g->flags & FE_GEOM_STORE_F32) || (g->flags & FE_GEOM_STORE_F64)) return false;
+    return f->kind == FK_LAPLACE || f->kind == FK_MASS || f->kind == FK_ELASTICITY;
+}
+
+cudaError_t fe_launch_residual_geometry(fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u,
+                                        void *r, unsigned long long *st, cudaStream_t s)
+{
+    if (!fe_residual_geometry_fusable(g, f)) return cudaErrorNotSupported;
+    if (g->mesh.n_elems == 0) return cudaSuccess;
+    switch (g->n1d) {
+    case 2: return dispatch_res_geo<2, 16>(g, f, mat, u, r, st, s);
+    case 3: return dispatch_res_geo<3, 9>(g, f, mat, u, r, st, s);
+    case 4: return dispatch_res_geo<4, 2>(g, f, mat, u, r, st, s);
+    }
+    return cudaErrorNotSupported;
 }

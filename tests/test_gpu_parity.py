@@ -207,13 +207,77 @@ def test_deferred_geometry_matches_eager(ctx, prec):
     K_e = fe.eval_matrix(ctx, form, eager, args, prec)
     r_e = fe.eval_residual(ctx, form, eager, args, "f32")
     ctx.check()
+    # the deferred handle is settled by the same kernel: identical bits throughout
     np.testing.assert_array_equal(lazy.get(fe.GEOM_WDETJ, "f32").cpu().numpy(),
                                   eager.get(fe.GEOM_WDETJ, "f32").cpu().numpy())
-    np.testing.assert_allclose(lazy.get(fe.GEOM_JINV, "f32").cpu().numpy(),
-                               eager.get(fe.GEOM_JINV, "f32").cpu().numpy(), rtol=1e-6, atol=1e-6)
-    assert rel_matrix_error(K_l.cpu().numpy(), K_e.cpu().numpy().astype(np.float64)) <= 1e-6
-    assert rel_vector_error(r_l.cpu().numpy(), r_e.cpu().numpy().astype(np.float64)) <= 1e-6
+    np.testing.assert_array_equal(lazy.get(fe.GEOM_JINV, "f32").cpu().numpy(),
+                                  eager.get(fe.GEOM_JINV, "f32").cpu().numpy())
+    assert torch.equal(K_l, K_e)
+    assert torch.equal(r_l, r_e)
     assert rel_vector_error(r_l.cpu().numpy(), rref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("kind,material", [("laplace", None), ("mass1", None), ("mass3", None),
+                                           ("elasticity", fe.MAT_LAME), ("elasticity", fe.MAT_D66)])
+@pytest.mark.parametrize("p,n", [(1, (5, 4, 3)), (2, (4, 3, 3)), (3, (2, 2, 3))])
+def test_residual_computes_stale_geometry(ctx, kind, material, p, n):
+    """fe_eval_residual on a stale float32-only deferred handle computes the FP64
+    geometry in the residual kernel: r, the stored copy and the matrix that
+    follows equal the eager path's bit for bit, and r matches the oracle."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, kind, p, n, 95 + p, material or fe.MAT_LAME)
+    eager = fe.hex_geometry(ctx, P.m, p, p + 1, flags=fe.GEOM_STORE_F32)
+    lazy = fe.hex_geometry(ctx, P.m, p, p + 1, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    args = [None] * len(form.operands)
+    args[form.state_op] = _t(u, torch.float32)
+    args[0] = _t(mat, torch.float64)  # the material is operand 0 in the named forms
+    r_e = fe.eval_residual(ctx, form, eager, args, "f32")
+    for _ in range(2):
+        lazy.update()
+        r_l = fe.eval_residual(ctx, form, lazy, args, "f32")
+    ctx.check()
+    assert torch.equal(r_l, r_e)
+    assert torch.equal(lazy.get(fe.GEOM_JINV, "f32"), eager.get(fe.GEOM_JINV, "f32"))
+    assert torch.equal(lazy.get(fe.GEOM_WDETJ, "f32"), eager.get(fe.GEOM_WDETJ, "f32"))
+    assert torch.equal(fe.eval_matrix(ctx, form, lazy, args, "f32"), fe.eval_matrix(ctx, form, eager, args, "f32"))
+    assert rel_vector_error(r_l.cpu().numpy(), rref) <= TOL["f32"]
+
+
+def test_residual_computes_stale_geometry_many_groups_per_cta(ctx):
+    """About 37,000 Q2 elements: every CTA of the residual kernel takes several
+    groups of elements, the last one ragged."""
+    mesh = meshgen.structured_hex(34, 33, 33, 2, 0.15, 96)
+    P = Problem(ctx, mesh, 2, 3)
+    lam, mu = meshgen.lame_materials(mesh)
+    lm = _t(np.stack([lam, mu], 1), torch.float64)
+    u = _t(np.random.default_rng(97).standard_normal(3 * mesh.n_nodes), torch.float32)
+    form = fe.elasticity_form()
+    eager = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32)
+    lazy = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    r_l = fe.eval_residual(ctx, form, lazy, [lm, None, u], "f32")
+    r_e = fe.eval_residual(ctx, form, eager, [lm, None, u], "f32")
+    ctx.check()
+    assert torch.equal(r_l, r_e)
+    assert torch.equal(lazy.get(fe.GEOM_JINV, "f32"), eager.get(fe.GEOM_JINV, "f32"))
+    assert torch.equal(lazy.get(fe.GEOM_WDETJ, "f32"), eager.get(fe.GEOM_WDETJ, "f32"))
+    # the tensor-core precisions name the same float32 residual kernel
+    lazy.update()
+    r_b = fe.eval_residual(ctx, form, lazy, [lm, None, u], "bf16x3")
+    K_b = fe.eval_matrix(ctx, form, lazy, [lm, None, None], "bf16x3")
+    ctx.check()
+    assert torch.equal(r_b, r_e)
+    assert torch.equal(K_b, fe.eval_matrix(ctx, form, eager, [lm, None, None], "bf16x3"))
+
+
+def test_residual_with_stale_geometry_reports_nonpositive_detj(ctx):
+    mesh = meshgen.structured_hex(3, 2, 2, 2, 0.0, 0)
+    mesh.conn[7] = mesh.conn[7].reshape(3, 3, 3)[:, ::-1, :].reshape(-1)  # mirror element 7 in y
+    P = Problem(ctx, mesh, 2, 3)
+    ctx.status()  # the eager geometry of Problem reported it already: clear
+    lazy = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    lm = _t(np.ones((mesh.n_elems, 2)), torch.float64)
+    u = _t(np.zeros(3 * mesh.n_nodes), torch.float32)
+    fe.eval_residual(ctx, fe.elasticity_form(), lazy, [lm, None, u], "f32")
+    assert ctx.status() == (fe.FE_ERR_NONPOSITIVE_DETJ, 7)
 
 
 def test_deferred_geometry_settles_for_other_kernels(ctx):
