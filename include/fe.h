@@ -196,8 +196,14 @@ int fe_gm_rule_size(int s);
 #define FE_GEOM_STORE_F32 2u /* keep float32 copies (needed by the other precisions) */
 #define FE_GEOM_DEFERRED 4u  /* compute lazily: fe_geometry / fe_geometry_update only mark the
                                 geometry stale; the next call that reads it (evaluation or
-                                fe_geometry_get) computes it first, on its own stream.  The
-                                stale mark is host state: use a deferred handle from one stream. */
+                                fe_geometry_get) computes it first, on its own stream.  A
+                                handle that keeps only the float32 copy (FE_GEOM_STORE_F32)
+                                of a tensor-product hexahedron with n1d == nq1d is computed
+                                by fe_eval_residual itself (Laplace, mass or elasticity, any
+                                precision but FE_F64): one kernel for the FP64 geometry, the
+                                stored float32 copy and the residual, with the same bits as
+                                the separate geometry kernel.  The stale mark is host state:
+                                use a deferred handle from one stream. */
 
 /* Geometry of the reference mapping (Sec. 4.1): for every element e and
  * quadrature point q, J = sum_a x_a (x) grad_xi phi_a(q), det J, J^-1 and
