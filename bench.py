@@ -54,10 +54,12 @@ CV_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 81 * 8 + 27 * 4 + 81 * 81 * 8
 # last contraction and row assembly 56862
 CV_FLOPS_PER_ELEM = 972 + 1458 + 1944 + 1944 + 6804 + 20412 + 56862
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
-# FP64 operations (an FMA counts 2) of the collocation geometry of one Q2 element:
-# three 1-D interpolations (3 x 243 FMA), J on the points (729 FMA), per point
-# 9 cofactors (mul + FMA each) and det J (mul + 2 FMA)
-GEOMETRY_FLOPS_PER_ELEM_Q2 = 2 * (3 * 243 + 729) + Q2_Q * (9 * 3 + 5)
+# FP64 operations (an FMA counts 2) that the collocation geometry executes for one
+# Q2 element with 3x3x3 Gauss points: three 1-D interpolations of 27 lines each
+# (6 FMA a line: the middle point is the middle node), J on the points (81 lines of
+# 6 FMA + a subtraction and a multiply), per point 9 cofactors (mul + FMA each) and
+# det J (mul + 2 FMA) -- 1,701 FP64 instructions
+GEOMETRY_FLOPS_PER_ELEM_Q2 = 2 * 3 * 27 * 6 + 81 * (2 * 6 + 2) + Q2_Q * (9 * 3 + 5)
 
 
 # Adjoint: J = |R|^2 / 2 of the assembled Q2 elasticity residual on a 32^3 cube

@@ -1,6 +1,7 @@
 // C ABI of libfe (declarations and argument contracts in include/fe.h).
 // Host-side argument validation, handle management and kernel dispatch.
 #include <climits>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -218,6 +219,21 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
         double dq[64];
         if (e == cudaSuccess && basis->n1d == basis->nq1d &&
             fe_host_collocation_derivative(basis->n1d, basis->b1d, basis->d1d, dq)) {
+            // three points with the middle one on the middle node (B's middle row
+            // exactly (0, 1, 0)): the middle row of Dq is (-d, 0, d) up to rounding;
+            // made exact, the kernels use it to skip the trivial products
+            const double *B = basis->b1d;
+            if (basis->n1d == 3 && B[3] == 0.0 && B[4] == 1.0 && B[5] == 0.0) {
+                double sc = 0.0;
+                for (int i = 0; i < 9; ++i) sc = std::fmax(sc, std::fabs(dq[i]));
+                if (std::fabs(dq[4]) <= 1e-13 * sc && std::fabs(dq[3] + dq[5]) <= 1e-13 * sc) {
+                    const double d = 0.5 * (dq[5] - dq[3]);
+                    dq[3] = -d;
+                    dq[4] = 0.0;
+                    dq[5] = d;
+                    g->geo_center = 1;
+                }
+            }
             e = dev_alloc(&g->d_dq, n);
             if (e == cudaSuccess) e = cudaMemcpy(g->d_dq, dq, sizeof(double) * n, cudaMemcpyHostToDevice);
         }

@@ -28,6 +28,7 @@ struct fe_geometry_h {
     double *d_b1d, *d_d1d;               // (nq1d, n1d) each, or null
     float *d_b1d32, *d_d1d32;
     double *d_dq;  // (nq1d, nq1d) collocation derivative on the points when n1d == nq1d, or null
+    int geo_center;  // n1d == nq1d == 3 with the middle point on the middle node (see geometry_body.cuh)
     float *d_phi32, *d_dphi32;
     double *d_jinv64, *d_wdetj64;  // (E,Q,3,3), (E,Q)
     float *d_jinv32, *d_wdetj32;

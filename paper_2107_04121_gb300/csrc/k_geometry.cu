@@ -8,8 +8,8 @@
 //    1-D contractions per coordinate and derivative direction, 2 n1 nq (n1^2 +
 //    n1 nq + nq^2)... for Q2 1,944 DFMA per element instead of 6,561;
 //  - k_geometry_co (tensor-product bases with n1 == nq): x interpolated to
-//    the points, then the collocation derivative on the points (1,458 DFMA
-//    per Q2 element);
+//    the points, then the collocation derivative on the points (1,134 DFMA
+//    per Q2 element with 3x3x3 Gauss points);
 //  - k_geometry (any tabulated basis): one thread per (element, quadrature
 //    point), J = sum_a x_a (x) grad phi_a directly (9N DFMA per point).
 // Both finish each point with the same cofactor inverse (about 40 FP64
@@ -171,11 +171,13 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry_sf(const double *__re
 // Collocation form of the sum-factorised geometry, for n1 == nq: along one
 // axis the nq Gauss points fix a polynomial of degree n1 - 1, so the derivative
 // at the points is Dq (point values), Dq = D B^-1 (nq x nq).  Per element:
-//   P = B_z B_y B_x X       (x at the points: three 1-D contractions, 3 N n1 DFMA)
-//   J[c][m] = Dq along axis m of P[c]   (3 N n1 DFMA, fused with the inverse)
-// For Q2 that is 1,458 DFMA per element instead of 1,944, and J never passes
-// through shared memory.
-template <int N1, int EPB>
+//   P = B_z B_y B_x X       (x at the points: three 1-D contractions)
+//   J[c][m] = Dq along axis m of P[c]
+// one 1-D line per item (geometry_body.cuh); for Q2 1,458 DFMA per element, or
+// 1,134 when the middle Gauss point is the middle node (CENTER).  Per element
+// the shared buffer holds X (then P), U, V and J (9 N doubles over U, V and a
+// fourth block).
+template <int N1, int EPB, bool CENTER>
 __global__ void __launch_bounds__(kGeomThreads) k_geometry_co(const double *__restrict__ coords,
                                                               const int32_t *__restrict__ conn, long long E,
                                                               long long n_nodes, const double *__restrict__ b1d,
@@ -185,15 +187,13 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry_co(const double *__re
                                                               float *__restrict__ jinv32, float *__restrict__ wdetj32,
                                                               unsigned long long *__restrict__ status)
 {
-    constexpr int N = N1 * N1 * N1;
-    static_assert(8 * (2 * N1 * N1 + EPB * 3 * 3 * N) <= 48 * 1024, "static shared memory above 48 KB");
-    __shared__ double sB[N1][N1], sDq[N1][N1];
-    __shared__ double sX[EPB][3][N];  // nodal x [c][k][j][i], then x at the points [c][qz][qy][qx]
-    __shared__ double sU[EPB][3][N];  // [c][k][j][qx]
-    __shared__ double sV[EPB][3][N];  // [c][k][qy][qx]
+    constexpr int N = N1 * N1 * N1, L = N1 * N1;
+    static_assert(8 * (2 * N1 * N1 + EPB * 12 * N) <= 48 * 1024, "static shared memory above 48 KB");
+    __shared__ double sB[N1 * N1], sDq[N1 * N1];
+    __shared__ double sG[EPB][4][3 * N];
     for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) {
-        sB[i / N1][i % N1] = b1d[i];
-        sDq[i / N1][i % N1] = dq[i];
+        sB[i] = b1d[i];
+        sDq[i] = dq[i];
     }
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
         const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
@@ -206,24 +206,25 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry_co(const double *__re
                 node = 0;
             }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) sX[el][c][a] = coords[3 * node + c];
+            for (int c = 0; c < 3; ++c) sG[el][0][c * N + a] = coords[3 * node + c];
         }
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x)  // contract i
-            geo_stage_x<N1>(t % (3 * N), sX[t / (3 * N)][0], sU[t / (3 * N)][0], &sB[0][0]);
+        for (int t = threadIdx.x; t < ne * 3 * L; t += blockDim.x)  // contract i
+            geo_lines_x<N1, CENTER>(t % (3 * L), sG[t / (3 * L)][0], sG[t / (3 * L)][1], sB);
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x)  // contract j
-            geo_stage_y<N1>(t % (3 * N), sU[t / (3 * N)][0], sV[t / (3 * N)][0], &sB[0][0]);
+        for (int t = threadIdx.x; t < ne * 3 * L; t += blockDim.x)  // contract j
+            geo_lines_y<N1, CENTER>(t % (3 * L), sG[t / (3 * L)][1], sG[t / (3 * L)][2], sB);
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += blockDim.x)  // contract k: x at the points
-            geo_stage_z<N1>(t % (3 * N), sV[t / (3 * N)][0], sX[t / (3 * N)][0], &sB[0][0]);
+        for (int t = threadIdx.x; t < ne * 3 * L; t += blockDim.x)  // contract k: x at the points
+            geo_lines_z<N1, CENTER>(t % (3 * L), sG[t / (3 * L)][2], sG[t / (3 * L)][0], sB);
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 9 * L; t += blockDim.x)  // J on the points
+            geo_lines_jacobian<N1, CENTER>(t % (9 * L), sG[t / (9 * L)][0], sG[t / (9 * L)][1], sDq);
         __syncthreads();
         for (int t = threadIdx.x; t < ne * N; t += blockDim.x) {
             const int el = t / N, q = t % N;
-            double J[3][3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) geo_jacobian_row<N1>(q, c, sX[el][0], &sDq[0][0], J[c]);
-            finish_point(J, w[q], e0 + el, (e0 + el) * N + q, jinv64, wdetj64, jinv32, wdetj32, status);
+            finish_point(reinterpret_cast<const double(*)[3]>(sG[el][1] + q * 9), w[q], e0 + el, (e0 + el) * N + q,
+                         jinv64, wdetj64, jinv32, wdetj32, status);
         }
     }
 }
@@ -353,7 +354,7 @@ cudaError_t launch_geom_sf(const fe_geometry_h *g, unsigned long long *st, cudaS
     return cudaGetLastError();
 }
 
-template <int N1, int EPB>
+template <int N1, int EPB, bool CENTER = false>
 cudaError_t launch_geom_co(const fe_geometry_h *g, unsigned long long *st, cudaStream_t s)
 {
     static FeLaunchCache cache;
@@ -364,7 +365,7 @@ cudaError_t launch_geom_co(const fe_geometry_h *g, unsigned long long *st, cudaS
             int sms = 0, per_sm = 0;
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             cudaError_t e2 =
-                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_geometry_co<N1, EPB>, kGeomThreads, 0);
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_geometry_co<N1, EPB, CENTER>, kGeomThreads, 0);
             if (e2 != cudaSuccess) return e2;
             if (per_sm < 1) return cudaErrorInvalidConfiguration;
             *v = (long long)per_sm * sms * 8;
@@ -375,7 +376,7 @@ cudaError_t launch_geom_co(const fe_geometry_h *g, unsigned long long *st, cudaS
     long long blocks = (g->mesh.n_elems + EPB - 1) / EPB;
     if (blocks > cap) blocks = cap;
     const bool f64 = g->flags & FE_GEOM_STORE_F64, f32 = g->flags & FE_GEOM_STORE_F32;
-    k_geometry_co<N1, EPB><<<(unsigned)blocks, kGeomThreads, 0, s>>>(
+    k_geometry_co<N1, EPB, CENTER><<<(unsigned)blocks, kGeomThreads, 0, s>>>(
         g->mesh.coords, g->mesh.conn, g->mesh.n_elems, g->mesh.n_nodes, g->d_b1d, g->d_dq, g->d_w64,
         f64 ? g->d_jinv64 : nullptr, f64 ? g->d_wdetj64 : nullptr, f32 ? g->d_jinv32 : nullptr,
         f32 ? g->d_wdetj32 : nullptr, st);
@@ -391,7 +392,7 @@ cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *st, c
         const int n1 = g->n1d, nq = g->nq1d;
         if (g->d_dq && n1 == nq) {
             if (n1 == 2) return launch_geom_co<2, 32>(g, st, s);
-            if (n1 == 3) return launch_geom_co<3, 9>(g, st, s);
+            if (n1 == 3) return g->geo_center ? launch_geom_co<3, 9, true>(g, st, s) : launch_geom_co<3, 9>(g, st, s);
             if (n1 == 4) return launch_geom_co<4, 4>(g, st, s);
         }
         if (n1 == 2 && nq == 2) return launch_geom_sf<2, 2, 16>(g, st, s);

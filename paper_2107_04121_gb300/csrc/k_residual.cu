@@ -503,8 +503,8 @@ struct ResGeoSmem {
     static constexpr int Y = X + EPB * NC * (GRAD ? 2 : 1) * LX * 4;  // float [EPB][NC][NM][LY]
     static constexpr int QV = Y + EPB * NC * NM * LY * 4;         // float [EPB][NC][NM][Q]
     static constexpr int STAGE_END = QV + EPB * NC * NM * Q * 4;
-    static constexpr int G = (X + 7) / 8 * 8;                     // double [3][EPB][3][N], over the stage buffers
-    static constexpr int G_END = G + 3 * EPB * 3 * N * 8;
+    static constexpr int G = (X + 7) / 8 * 8;                     // double [EPB][4][3 N], over the stage buffers
+    static constexpr int G_END = G + EPB * 12 * N * 8;
     static constexpr int J = ((STAGE_END > G_END ? STAGE_END : G_END) + 15) / 16 * 16;  // float [EPB][Q][9]
     static constexpr int W = J + EPB * Q * 9 * 4;                 // float [EPB][Q]
     static constexpr int M = W + EPB * Q * 4;                     // float [EPB][36]
@@ -512,8 +512,8 @@ struct ResGeoSmem {
     static constexpr int BYTES = T64 + (2 * N1 * N1 + Q) * 8;
 };
 
-template <int N1, int KIND, int MATK, int EPB, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_residual_geo(const double *__restrict__ coords,
+template <int N1, int KIND, int MATK, int EPB, int THREADS, bool CENTER>
+__global__ void __launch_bounds__(THREADS, N1 == 3 ? 6 : 4) k_residual_geo(const double *__restrict__ coords,
                                                           const int32_t *__restrict__ conn, long long E,
                                                           long long n_nodes, const double *__restrict__ b1d64,
                                                           const double *__restrict__ dq64,
@@ -537,9 +537,9 @@ __global__ void __launch_bounds__(THREADS) k_residual_geo(const double *__restri
     T(*sJ)[Q][9] = reinterpret_cast<T(*)[Q][9]>(raw + L::J);
     T(*sW)[Q] = reinterpret_cast<T(*)[Q]>(raw + L::W);
     T(*sM)[36] = reinterpret_cast<T(*)[36]>(raw + L::M);
-    double *gX = reinterpret_cast<double *>(raw + L::G);  // [EPB][3][N] each
-    double *gU = gX + EPB * 3 * N;
-    double *gV = gU + EPB * 3 * N;
+    // per element: X (then P), U, V, and J (9 N doubles over U, V and a fourth block)
+    double(*gG)[4][3 * N] = reinterpret_cast<double(*)[4][3 * N]>(raw + L::G);
+    constexpr int LL = N1 * N1;
     double *gB = reinterpret_cast<double *>(raw + L::T64);
     double *gDq = gB + N1 * N1;
     double *gw = gDq + N1 * N1;
@@ -564,25 +564,26 @@ __global__ void __launch_bounds__(THREADS) k_residual_geo(const double *__restri
             if (!ok) fe_report(status, FE_ERR_SHAPE, e0 + el);
             const long long nd = ok ? node : 0;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) gX[(el * 3 + c) * N + a] = coords[3 * nd + c];
+            for (int c = 0; c < 3; ++c) gG[el][0][c * N + a] = coords[3 * nd + c];
             for (int c = 0; c < nc; ++c) sU[el][c][a] = ok ? u[node * nc + c] : (T)0;
         }
         load_material<T, MATK, THREADS>(ne, e0, mat, mat_t, sM);
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += THREADS)  // geometry: contract i
-            geo_stage_x<N1>(t % (3 * N), gX + (t / (3 * N)) * 3 * N, gU + (t / (3 * N)) * 3 * N, gB);
+        for (int t = threadIdx.x; t < ne * 3 * LL; t += THREADS)  // geometry: contract i
+            geo_lines_x<N1, CENTER>(t % (3 * LL), gG[t / (3 * LL)][0], gG[t / (3 * LL)][1], gB);
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += THREADS)  // contract j
-            geo_stage_y<N1>(t % (3 * N), gU + (t / (3 * N)) * 3 * N, gV + (t / (3 * N)) * 3 * N, gB);
+        for (int t = threadIdx.x; t < ne * 3 * LL; t += THREADS)  // contract j
+            geo_lines_y<N1, CENTER>(t % (3 * LL), gG[t / (3 * LL)][1], gG[t / (3 * LL)][2], gB);
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * 3 * N; t += THREADS)  // contract k: x at the points
-            geo_stage_z<N1>(t % (3 * N), gV + (t / (3 * N)) * 3 * N, gX + (t / (3 * N)) * 3 * N, gB);
+        for (int t = threadIdx.x; t < ne * 3 * LL; t += THREADS)  // contract k: x at the points
+            geo_lines_z<N1, CENTER>(t % (3 * LL), gG[t / (3 * LL)][2], gG[t / (3 * LL)][0], gB);
+        __syncthreads();
+        for (int t = threadIdx.x; t < ne * 9 * LL; t += THREADS)  // J on the points
+            geo_lines_jacobian<N1, CENTER>(t % (9 * LL), gG[t / (9 * LL)][0], gG[t / (9 * LL)][1], gDq);
         __syncthreads();
         for (int t = threadIdx.x; t < ne * Q; t += THREADS) {
             const int el = t / Q, q = t % Q;
-            double J[9];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) geo_jacobian_row<N1>(q, c, gX + el * 3 * N, gDq, J + 3 * c);
+            const double *J = gG[el][1] + q * 9;
             float o[9], wd;
             const double det = geo_point_f32(J, gw[q], o, wd);
             const int bad = geo_det_status(det);
@@ -663,12 +664,12 @@ cudaError_t dispatch_sf(const fe_geometry_h *g, const fe_form_h *f, fe_material_
     return cudaErrorInvalidValue;
 }
 
-template <int N1, int KIND, int MATK, int EPB>
+template <int N1, int KIND, int MATK, int EPB, bool CENTER>
 cudaError_t launch_res_geo(fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
                            unsigned long long *st, cudaStream_t s)
 {
     constexpr int THREADS = 256;
-    auto kern = k_residual_geo<N1, KIND, MATK, EPB, THREADS>;
+    auto kern = k_residual_geo<N1, KIND, MATK, EPB, THREADS, CENTER>;
     static FeLaunchCache cache;
     long long cap = 0;
     cudaError_t err = fe_cached_grid(
@@ -693,16 +694,16 @@ cudaError_t launch_res_geo(fe_geometry_h *g, const fe_form_h *f, fe_material_arg
     return cudaGetLastError();
 }
 
-template <int N1, int EPB>
+template <int N1, int EPB, bool CENTER>
 cudaError_t dispatch_res_geo(fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
                              unsigned long long *st, cudaStream_t s)
 {
     switch (f->kind) {
-    case FK_LAPLACE: return launch_res_geo<N1, FK_LAPLACE, 0, EPB>(g, f, mat, u, r, st, s);
-    case FK_MASS: return launch_res_geo<N1, FK_MASS, 0, EPB>(g, f, mat, u, r, st, s);
+    case FK_LAPLACE: return launch_res_geo<N1, FK_LAPLACE, 0, EPB, CENTER>(g, f, mat, u, r, st, s);
+    case FK_MASS: return launch_res_geo<N1, FK_MASS, 0, EPB, CENTER>(g, f, mat, u, r, st, s);
     case FK_ELASTICITY:
-        if (mat.kind == FE_MAT_LAME) return launch_res_geo<N1, FK_ELASTICITY, 1, EPB>(g, f, mat, u, r, st, s);
-        return launch_res_geo<N1, FK_ELASTICITY, 2, EPB>(g, f, mat, u, r, st, s);
+        if (mat.kind == FE_MAT_LAME) return launch_res_geo<N1, FK_ELASTICITY, 1, EPB, CENTER>(g, f, mat, u, r, st, s);
+        return launch_res_geo<N1, FK_ELASTICITY, 2, EPB, CENTER>(g, f, mat, u, r, st, s);
     }
     return cudaErrorNotSupported;
 }
@@ -794,9 +795,11 @@ cudaError_t fe_launch_residual_geometry(fe_geometry_h *g, const fe_form_h *f, fe
     if (!fe_residual_geometry_fusable(g, f)) return cudaErrorNotSupported;
     if (g->mesh.n_elems == 0) return cudaSuccess;
     switch (g->n1d) {
-    case 2: return dispatch_res_geo<2, 16>(g, f, mat, u, r, st, s);
-    case 3: return dispatch_res_geo<3, 9>(g, f, mat, u, r, st, s);
-    case 4: return dispatch_res_geo<4, 2>(g, f, mat, u, r, st, s);
+    case 2: return dispatch_res_geo<2, 16, false>(g, f, mat, u, r, st, s);
+    case 3:
+        return g->geo_center ? dispatch_res_geo<3, 9, true>(g, f, mat, u, r, st, s)
+                             : dispatch_res_geo<3, 9, false>(g, f, mat, u, r, st, s);
+    case 4: return dispatch_res_geo<4, 2, false>(g, f, mat, u, r, st, s);
     }
     return cudaErrorNotSupported;
 }
