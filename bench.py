@@ -54,6 +54,11 @@ CV_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 81 * 8 + 27 * 4 + 81 * 81 * 8
 # last contraction and row assembly 56862
 CV_FLOPS_PER_ELEM = 972 + 1458 + 1944 + 1944 + 6804 + 20412 + 56862
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
+# DRAM bytes (read + write) of one launch at 48^3 from an ncu capture of the current
+# kernels (dram__bytes_read.sum + dram__bytes_write.sum; the command is in
+# profiles/dram_traffic_q2_elasticity_48.md): the BF16x3 matrix kernel and the
+# geometry + residual kernel.  Other sizes or precisions report null.
+MEASURED_TRAFFIC_48 = {"matrix_bf16x3": 2962867456, "geometry_residual": 150187008}
 # FP64 operations (an FMA counts 2) that the collocation geometry executes for one
 # Q2 element with 3x3x3 Gauss points: three 1-D interpolations of 27 lines each
 # (6 FMA a line: the middle point is the middle node), J on the points (81 lines of
@@ -859,7 +864,8 @@ def main():
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
         "roofline": {"kernel": "k_matrix (fe_eval_matrix, %s)" % prec, "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "traffic": None, "bytes_per_elem": bytes_alg / wl.E, "avg_ms": mat_avg},
+                     "traffic": MEASURED_TRAFFIC_48["matrix_bf16x3"] if (args.n == 48 and prec == "bf16x3") else None,
+                     "bytes_per_elem": bytes_alg / wl.E, "avg_ms": mat_avg},
         "gpu_launches": kernels_per_step(prec) * args.steps,
         "step_parts_ms": parts,
     }
@@ -870,6 +876,7 @@ def main():
             "kernel": "k_residual_geo (FP64 geometry + r_e, f32)", "bound": "fp64", "achieved": gf,
             "peak": FP64_PEAK_TFLOPS_NOMINAL, "peak_source": "nominal", "unit": "TFLOP/s",
             "frac": gf / FP64_PEAK_TFLOPS_NOMINAL, "flops_per_elem": GEOMETRY_FLOPS_PER_ELEM_Q2,
+            "traffic": MEASURED_TRAFFIC_48["geometry_residual"] if args.n == 48 else None,
             "avg_ms": parts["geometry_and_residual"]}
     line["clocks"] = clk.summary()
     if ladder is not None:

@@ -156,8 +156,10 @@ fe_status fe_get_status(fe_ctx *ctx, fe_stream_t stream, long long *bad_elem);
 /* Library version as major*10000 + minor*100 + patch. */
 int fe_version(void);
 
-/* Text of the last CUDA error seen by a libfe call on the calling thread
- * (empty if none).  Static thread-local storage; never NULL. */
+/* Text that describes the failure of the latest fe_status call on the calling
+ * thread: the CUDA error, or the argument or shape problem where the call
+ * names one; empty after a call that succeeded or failed without a text.
+ * Static thread-local storage; never NULL. */
 const char *fe_last_error_message(void);
 
 /* ---- reference element (host) ----------------------------------------------- */

@@ -84,6 +84,8 @@ void free_geometry(fe_geometry_h *g)
 
 fe_status fe_status_from_cuda(cudaError_t e, const char *where) { return from_cuda(e, where); }
 
+void fe_clear_last_error() { g_last_error[0] = 0; }
+
 extern "C" {
 
 int fe_version(void) { return 100; }
@@ -108,6 +110,7 @@ const char *fe_status_str(fe_status s)
 
 fe_status fe_create(int device, fe_ctx **out)
 {
+    fe_clear_last_error();
     if (!out) return FE_ERR_INVALID_ARG;
     *out = nullptr;
     int n = 0;
@@ -140,6 +143,7 @@ fe_status fe_create(int device, fe_ctx **out)
 
 fe_status fe_destroy(fe_ctx *ctx)
 {
+    fe_clear_last_error();
     if (!ctx) return FE_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     cudaFree(ctx->d_status);
@@ -149,6 +153,7 @@ fe_status fe_destroy(fe_ctx *ctx)
 
 fe_status fe_get_status(fe_ctx *ctx, fe_stream_t stream, long long *bad_elem)
 {
+    fe_clear_last_error();
     if (!ctx) return FE_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     fe_status st = from_cuda(cudaStreamSynchronize(to_cuda(stream)), "fe_get_status sync");
@@ -168,6 +173,7 @@ fe_status fe_get_status(fe_ctx *ctx, fe_stream_t stream, long long *bad_elem)
 fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis, const fe_quadrature *quad,
                       unsigned flags, fe_geometry_h **out, fe_stream_t stream)
 {
+    fe_clear_last_error();
     if (!ctx || !out || !valid_mesh(mesh) || !basis || !quad || !basis->phi || !basis->dphi || !quad->weights)
         return FE_ERR_INVALID_ARG;
     *out = nullptr;
@@ -271,6 +277,7 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
 fe_status fe_geometry_view(fe_ctx *ctx, const fe_geometry_h *parent, long long e_begin, long long e_count,
                            fe_geometry_h **out)
 {
+    fe_clear_last_error();
     if (!ctx || !parent || !out || e_begin < 0 || e_count < 0 || e_begin + e_count > parent->mesh.n_elems)
         return FE_ERR_INVALID_ARG;
     if (parent->flags & FE_GEOM_DEFERRED) return FE_ERR_INVALID_ARG;  // views share computed storage
@@ -292,6 +299,7 @@ fe_status fe_geometry_view(fe_ctx *ctx, const fe_geometry_h *parent, long long e
 
 fe_status fe_geometry_update(fe_ctx *ctx, fe_geometry_h *geom, fe_stream_t stream)
 {
+    fe_clear_last_error();
     if (!ctx || !geom) return FE_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     if (geom->flags & FE_GEOM_DEFERRED) {
@@ -303,6 +311,7 @@ fe_status fe_geometry_update(fe_ctx *ctx, fe_geometry_h *geom, fe_stream_t strea
 
 fe_status fe_geometry_free(fe_geometry_h *geom)
 {
+    fe_clear_last_error();
     if (!geom) return FE_ERR_INVALID_ARG;
     cudaSetDevice(geom->device);
     free_geometry(geom);
@@ -312,6 +321,7 @@ fe_status fe_geometry_free(fe_geometry_h *geom)
 fe_status fe_geometry_get(fe_ctx *ctx, const fe_geometry_h *g, fe_geom_field field, fe_precision prec, void *out,
                           fe_stream_t stream)
 {
+    fe_clear_last_error();
     if (!ctx || !g || (!out && g->mesh.n_elems > 0)) return FE_ERR_INVALID_ARG;
     const bool f64 = prec == FE_F64;
     if (f64 ? !g->d_jinv64 : !g->d_jinv32) return FE_ERR_INVALID_ARG;
@@ -365,6 +375,7 @@ static fe_status eval_common(fe_ctx *ctx, const fe_form_h *form, const fe_geomet
 fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const void *const *args,
                          int diff_op, fe_precision prec, void *K_out, fe_stream_t stream)
 {
+    fe_clear_last_error();
     fe_material_args mat{};
     fe_status st = eval_common(ctx, form, g, args, prec, K_out, &mat);
     if (st) return st;
@@ -411,6 +422,7 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
 fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const void *const *args,
                            fe_precision prec, void *r_out, fe_stream_t stream)
 {
+    fe_clear_last_error();
     fe_material_args mat{};
     fe_status st = eval_common(ctx, form, g, args, prec, r_out, &mat);
     if (st) return st;
@@ -455,6 +467,7 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
 fe_status fe_eval_integral(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const void *const *args,
                            fe_precision prec, void *out, fe_stream_t stream)
 {
+    fe_clear_last_error();
     fe_material_args mat{};
     fe_status st = eval_common(ctx, form, g, args, prec, out, &mat);
     if (st) return st;
@@ -478,6 +491,7 @@ fe_status fe_eval_residual_adjoint(fe_ctx *ctx, const fe_form_h *form, const fe_
                                    const void *const *args, const void *rbar, fe_precision prec, void *d_mat,
                                    void *d_x_e, fe_stream_t stream)
 {
+    fe_clear_last_error();
     fe_material_args mat{};
     const bool empty = g && g->mesh.n_elems == 0;
     if (!d_mat && !d_x_e && !empty) return FE_ERR_INVALID_ARG;
@@ -500,6 +514,7 @@ fe_status fe_eval_residual_adjoint(fe_ctx *ctx, const fe_form_h *form, const fe_
 
 fe_status fe_assembly_create(fe_ctx *ctx, const fe_mesh *mesh, fe_assembly_h **out, fe_stream_t stream)
 {
+    fe_clear_last_error();
     if (!ctx || !out || !valid_mesh(mesh)) return FE_ERR_INVALID_ARG;
     *out = nullptr;
     cudaSetDevice(ctx->device);
@@ -532,6 +547,7 @@ fe_status fe_assembly_create(fe_ctx *ctx, const fe_mesh *mesh, fe_assembly_h **o
 
 fe_status fe_assembly_free(fe_assembly_h *a)
 {
+    fe_clear_last_error();
     if (!a) return FE_ERR_INVALID_ARG;
     cudaSetDevice(a->device);
     cudaFree(a->d_offsets);
@@ -543,6 +559,7 @@ fe_status fe_assembly_free(fe_assembly_h *a)
 fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *a, int ncomp, const void *r_e, fe_precision prec,
                              void *global_out, unsigned flags, fe_stream_t stream)
 {
+    fe_clear_last_error();
     if (!ctx || !a || (ncomp != 1 && ncomp != 3)) return FE_ERR_INVALID_ARG;
     if ((!r_e && a->mesh.n_elems > 0) || (!global_out && a->mesh.n_nodes > 0)) return FE_ERR_INVALID_ARG;
     if (flags & ~(FE_ASSEMBLE_ACCUMULATE | FE_ASSEMBLE_COMPENSATED)) return FE_ERR_INVALID_ARG;
@@ -555,6 +572,7 @@ fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *a, int ncomp, con
 fe_status fe_assemble_vector_noalloc(fe_ctx *ctx, const fe_mesh *mesh, int ncomp, const void *r_e,
                                      fe_precision prec, void *global_out, unsigned flags, fe_stream_t stream)
 {
+    fe_clear_last_error();
     if (!ctx || !valid_mesh(mesh) || (ncomp != 1 && ncomp != 3)) return FE_ERR_INVALID_ARG;
     if ((!r_e && mesh->n_elems > 0) || (!global_out && mesh->n_nodes > 0)) return FE_ERR_INVALID_ARG;
     if (flags & ~(FE_ASSEMBLE_ACCUMULATE | FE_ASSEMBLE_COMPENSATED)) return FE_ERR_INVALID_ARG;

@@ -127,6 +127,9 @@ cudaError_t fe_launch_assemble_noalloc(int device, const fe_mesh *mesh, int ncom
 
 // Status of a CUDA error, recorded as the thread's last error message (api.cu).
 fe_status fe_status_from_cuda(cudaError_t e, const char *where);
+// Every fe_status entry point starts with this: the message of
+// fe_last_error_message then always belongs to the latest call (api.cu).
+void fe_clear_last_error();
 // Settle a deferred geometry (api.cu): compute it now if it is stale.
 cudaError_t fe_settle_geometry(fe_geometry_h *g, unsigned long long *status, cudaStream_t s);
 

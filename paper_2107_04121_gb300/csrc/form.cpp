@@ -86,6 +86,7 @@ bool parse_material(const std::string &t, Sub &out)
 extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_operand *ops, int n_ops,
                                      fe_form_h **out)
 {
+    fe_clear_last_error();
     (void)ctx;
     if (!expr || !ops || !out || n_ops < 1 || n_ops > 8) return FE_ERR_INVALID_ARG;
     *out = nullptr;
@@ -290,12 +291,14 @@ extern "C" fe_status fe_form_compile(fe_ctx *ctx, const char *expr, const fe_ope
 
 extern "C" fe_status fe_form_free(fe_form_h *form)
 {
+    fe_clear_last_error();
     delete form;
     return FE_OK;
 }
 
 extern "C" fe_status fe_form_shape(const fe_form_h *form, int n_basis, int *n_rows, int *n_cols)
 {
+    fe_clear_last_error();
     if (!form || n_basis < 1) return FE_ERR_INVALID_ARG;
     if (form->eval) {
         if (n_rows) *n_rows = form->n_out;

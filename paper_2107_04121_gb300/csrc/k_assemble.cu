@@ -57,38 +57,6 @@ __global__ void k_sort(const int *__restrict__ offsets, long long n_nodes, int *
     }
 }
 
-template <typename T, bool COMPENSATED>
-__global__ void k_gather(const int *__restrict__ offsets, const int *__restrict__ entries, long long n_nodes,
-                         int N, int ncomp, const T *__restrict__ r, T *__restrict__ out, bool accumulate)
-{
-    const long long total = n_nodes * ncomp;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long node = idx / ncomp;
-        const int comp = (int)(idx - node * ncomp);
-        const int b = offsets[node], e = offsets[node + 1];
-        T s = accumulate ? out[idx] : (T)0;
-        T c = 0;
-        for (int p = b; p < e; ++p) {
-            const int ent = entries[p];
-            const int el = ent / N, a = ent - el * N;
-            const T x = r[(long long)el * ncomp * N + comp * N + a];
-            if (COMPENSATED) {
-                // Neumaier: keep the rounding error of every addition in c
-                const T t = s + x;
-                if (fabs(s) >= fabs(x))
-                    c += (s - t) + x;
-                else
-                    c += (x - t) + s;
-                s = t;
-            } else {
-                s += x;
-            }
-        }
-        out[idx] = COMPENSATED ? s + c : s;
-    }
-}
-
 unsigned grid_for(long long n, int threads)
 {
     long long b = (n + threads - 1) / threads;
@@ -96,6 +64,65 @@ unsigned grid_for(long long n, int threads)
     if (b < 1) b = 1;
     return (unsigned)b;
 }
+
+// Assembly by gathering: one thread per node sums, for each of its 1 or 3
+// components, the element-vector entries of the node's incidences in ascending
+// (e, a) order (the CSR order): deterministic, no atomics; Neumaier-compensated
+// in float32 when asked.
+template <typename T, bool COMPENSATED, int NC>
+__global__ void k_gather_nodes(const int *__restrict__ offsets, const int *__restrict__ entries, long long n_nodes,
+                               int N, const T *__restrict__ r, T *__restrict__ out, bool accumulate)
+{
+    for (long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x; node < n_nodes;
+         node += (long long)gridDim.x * blockDim.x) {
+        const int b = offsets[node], e = offsets[node + 1];
+        T s[NC], c[NC];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            s[k] = accumulate ? out[node * NC + k] : (T)0;
+            c[k] = 0;
+        }
+        for (int p = b; p < e; ++p) {
+            const int ent = entries[p];
+            const int el = ent / N, a = ent - el * N;
+            const T *re = r + (long long)el * NC * N + a;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                const T x = re[k * N];
+                if (COMPENSATED) {
+                    const T t = s[k] + x;
+                    if (fabs(s[k]) >= fabs(x))
+                        c[k] += (s[k] - t) + x;
+                    else
+                        c[k] += (x - t) + s[k];
+                    s[k] = t;
+                } else {
+                    s[k] += x;
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) out[node * NC + k] = COMPENSATED ? s[k] + c[k] : s[k];
+    }
+}
+
+template <typename T, bool COMPENSATED>
+cudaError_t launch_gather(const fe_assembly_h *a, int ncomp, const void *r, void *out, bool acc, cudaStream_t s)
+{
+    const long long n_nodes = a->mesh.n_nodes;
+    const int N = a->mesh.nodes_per_elem;
+    const unsigned grid = grid_for(n_nodes, 256);
+    if (ncomp == 3)
+        k_gather_nodes<T, COMPENSATED, 3><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, n_nodes, N, (const T *)r,
+                                                               (T *)out, acc);
+    else if (ncomp == 1)
+        k_gather_nodes<T, COMPENSATED, 1><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, n_nodes, N, (const T *)r,
+                                                               (T *)out, acc);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
 
 }  // namespace
 
@@ -139,18 +166,9 @@ cudaError_t fe_launch_assemble(const fe_assembly_h *a, int ncomp, bool f64, cons
     const long long total = a->mesh.n_nodes * ncomp;
     if (total == 0) return cudaSuccess;
     const bool acc = flags & FE_ASSEMBLE_ACCUMULATE;
-    const int N = a->mesh.nodes_per_elem;
-    const unsigned grid = grid_for(total, 256);
-    if (f64)
-        k_gather<double, false><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, a->mesh.n_nodes, N, ncomp,
-                                                     (const double *)r, (double *)out, acc);
-    else if (flags & FE_ASSEMBLE_COMPENSATED)
-        k_gather<float, true><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, a->mesh.n_nodes, N, ncomp,
-                                                   (const float *)r, (float *)out, acc);
-    else
-        k_gather<float, false><<<grid, 256, 0, s>>>(a->d_offsets, a->d_entries, a->mesh.n_nodes, N, ncomp,
-                                                    (const float *)r, (float *)out, acc);
-    return cudaGetLastError();
+    if (f64) return launch_gather<double, false>(a, ncomp, r, out, acc, s);
+    if (flags & FE_ASSEMBLE_COMPENSATED) return launch_gather<float, true>(a, ncomp, r, out, acc, s);
+    return launch_gather<float, false>(a, ncomp, r, out, acc, s);
 }
 
 // ---------------------------------------------------------------------------

@@ -323,6 +323,7 @@ extern "C" {
 fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, unsigned flags, fe_batch_h **out,
                           fe_stream_t stream)
 {
+    fe_clear_last_error();
     if (!ctx || !out || n_items < 1 || !items) return FE_ERR_INVALID_ARG;
     if (flags & ~(FE_BATCH_GEOMETRY | FE_BATCH_AUTOTUNE | FE_BATCH_GRAPH)) return FE_ERR_INVALID_ARG;
     *out = nullptr;
@@ -463,6 +464,7 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
 
 fe_status fe_batch_run(fe_ctx *ctx, fe_batch_h *batch, fe_stream_t stream)
 {
+    fe_clear_last_error();
     if (!ctx || !batch || batch->device != ctx->device) return FE_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -482,6 +484,7 @@ fe_status fe_batch_run(fe_ctx *ctx, fe_batch_h *batch, fe_stream_t stream)
 
 fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *elems_per_chunk, int *staging)
 {
+    fe_clear_last_error();
     if (!batch || item < 0 || item >= batch->n_items) return FE_ERR_INVALID_ARG;
     const Variant &v = kVariants[batch->items[item].variant];
     if (tile) *tile = v.tile;
@@ -492,6 +495,7 @@ fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *e
 
 fe_status fe_batch_free(fe_batch_h *batch)
 {
+    fe_clear_last_error();
     if (!batch) return FE_ERR_INVALID_ARG;
     cudaSetDevice(batch->device);
     free_plan(batch);

@@ -98,6 +98,7 @@ static void lagrange1d(int p, int k, double t, double *val, double *der)
 
 extern "C" fe_status fe_refbasis_hex(int p, int nq, double *points, double *weights, double *phi, double *dphi)
 {
+    fe_clear_last_error();
     if (p < 1 || p > 4 || nq < 1 || nq > 10) return FE_ERR_SHAPE;
     double g[16], gw[16];
     if (fe_host_gauss_legendre01(nq, g, gw)) return FE_ERR_SHAPE;
@@ -133,6 +134,7 @@ extern "C" fe_status fe_refbasis_hex(int p, int nq, double *points, double *weig
 
 extern "C" fe_status fe_refbasis_hex_1d(int p, int nq, double *b1d, double *d1d)
 {
+    fe_clear_last_error();
     if (p < 1 || p > 4 || nq < 1 || nq > 10 || !b1d || !d1d) return p < 1 || p > 4 || nq < 1 || nq > 10
                                                                           ? FE_ERR_SHAPE
                                                                           : FE_ERR_INVALID_ARG;
@@ -287,6 +289,7 @@ extern "C" int fe_gm_rule_size(int s)
 
 extern "C" fe_status fe_refbasis_tet(int p, int s, double *points, double *weights, double *phi, double *dphi)
 {
+    fe_clear_last_error();
     if (p < 1 || p > 3 || s < 0 || s > 6) return FE_ERR_SHAPE;
     double qp[3 * 512], qw[512];
     const int Q = gm_points(s, qp, qw);

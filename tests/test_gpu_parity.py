@@ -68,6 +68,14 @@ def test_inconsistent_tensor_factors_are_rejected(ctx):
     with pytest.raises(fe.FEError) as ei:
         fe.geometry(ctx, P.m, phi, dphi, w, b1d=b1d, d1d=d1d)
     assert ei.value.status == fe.FE_ERR_INVALID_ARG
+    assert "1-D factors" in str(ei.value)
+    # the next failing call reports its own problem, not this message
+    asm = fe.assembly_create(ctx, P.m)
+    r = torch.zeros((mesh.n_elems, 2 * 27), dtype=torch.float64, device="cuda")
+    with pytest.raises(fe.FEError) as ei:
+        fe.assemble_vector(ctx, asm, 2, r, "f64")
+    assert ei.value.status == fe.FE_ERR_INVALID_ARG
+    assert "1-D factors" not in str(ei.value)
 
 
 def test_geometry_update_follows_moved_nodes(ctx):
