@@ -309,6 +309,24 @@ def timed_steps(wl, prec, steps, warmup, ws, flush):
     return step_ms, mat_ms, parts
 
 
+def time_call(wl, flush, fn, reps=5, warmup=2):
+    """Median CUDA-event time (ms) of fn, L2 flushed before each call."""
+    torch = wl.torch
+    for _ in range(warmup):
+        fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    wl.ctx.check()
+    return statistics.median(ts)
+
+
 def rel_matrix_error(K, Kref):
     """max over elements of ||K_e - K_e^ref||_F / ||K_e^ref||_F."""
     K = np.asarray(K, dtype=np.float64)
@@ -670,6 +688,25 @@ def oracle_step(mesh, lam, mu, u, n_elems):
     oracle.assemble(conn, r, mesh.n_nodes, 3)
 
 
+def cpu_model():
+    """The host CPU's model string (x86 'model name', else Arm implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key) and ":" in line:
+                return line.split(":", 1)[1].strip()
+    parts = {}
+    for line in info:
+        if ":" in line:
+            k, v = (x.strip() for x in line.split(":", 1))
+            if k in ("CPU implementer", "CPU part") and k not in parts:
+                parts[k] = v
+    return ("Arm implementer %s part %s" % (parts.get("CPU implementer"), parts.get("CPU part"))) if parts else "unknown"
+
+
 def cpu_baseline(n, min_seconds=10.0):
     """The CPU-baseline leg: the FP64 oracle timed on the host cores over whole
     steps of the full workload, repeated until at least `min_seconds` have passed
@@ -680,16 +717,34 @@ def cpu_baseline(n, min_seconds=10.0):
     from paper_2107_04121_gb300 import meshgen
     mesh, lam, mu, u = meshgen.elasticity_q2_cube(n, seed=1)
     oracle_step(mesh, lam, mu, u, 64)
-    reps, t = 0, time.perf_counter()
+    reps, t, per = 0, time.perf_counter(), []
     while True:
+        t1 = time.perf_counter()
         oracle_step(mesh, lam, mu, u, mesh.n_elems)
+        per.append(time.perf_counter() - t1)
         reps += 1
         dt = time.perf_counter() - t
         if dt >= min_seconds:
             break
-    base = {"value": reps * mesh.n_elems / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    # the paper's statistic T^ww: the mean without the worst repetition
+    tww = statistics.mean(sorted(per)[:-1]) if len(per) > 1 else per[0]
+    base = {"value": reps * mesh.n_elems / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d full oracle steps over all %d elements (FP64 geometry, K_e, r_e, assembly), %.1f s"
-                      % (reps, mesh.n_elems, dt)}
+                      % (reps, mesh.n_elems, dt),
+            "step_s": {"median": statistics.median(per), "mean_without_worst": tww},
+            "cpu": cpu_model(), "affinity_cores": len(os.sched_getaffinity(0))}
+    # one core, on a sixteenth of the elements
+    n1 = max(1, mesh.n_elems // 16)
+    oracle.set_num_threads(1)
+    try:
+        t1 = time.perf_counter()
+        oracle_step(mesh, lam, mu, u, n1)
+        d1 = time.perf_counter() - t1
+    finally:
+        oracle.set_num_threads(cores)
+    base["single_thread"] = {"value": n1 / d1, "unit": UNIT, "sample": "one step over the first %d elements, %.1f s"
+                                                                        % (n1, d1)}
     rng = np.random.default_rng(7)
     E = mesh.n_elems
     idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, min(62, E), replace=False)]))
@@ -881,6 +936,18 @@ def main():
     line["clocks"] = clk.summary()
     if ladder is not None:
         line["precision_ladder"] = ladder
+    if not args.skip_extras and prec != "f64":
+        # the two residual variants: geometry computed in the residual kernel (the
+        # step above) against the geometry kernel followed by the residual on the
+        # stored float32 copy
+        K, r, g = wl.outputs(prec)
+        g32 = wl.geoms["f32"]
+        t_geo = time_call(wl, flush, lambda: g32.update())
+        t_res = time_call(wl, flush, lambda: wl.fe.eval_residual(wl.ctx, wl.form, g32, [wl.mat, None, wl.u32], prec,
+                                                                 out=r))
+        line["residual_variants_ms"] = {"geometry_in_residual_kernel": parts["geometry_and_residual"],
+                                        "stored_geometry": {"geometry": t_geo, "residual": t_res,
+                                                            "sum": t_geo + t_res}}
     if not args.skip_extras:
         wl.drop(prec)
         # plain FP64 path, same step

@@ -70,6 +70,8 @@ def lib():
         L.oracle_assemble.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, ctypes.c_longlong,
                                       ctypes.c_int, _D]
         L.oracle_num_threads.restype = ctypes.c_int
+        L.oracle_set_num_threads.argtypes = [ctypes.c_int]
+        L.oracle_set_num_threads.restype = None
         _lib = L
     return _lib
 
@@ -97,6 +99,11 @@ def _check(rc):
 
 def num_threads() -> int:
     return lib().oracle_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the following oracle calls (the arithmetic is the same)."""
+    lib().oracle_set_num_threads(int(n))
 
 
 def gauss_1d(n: int):

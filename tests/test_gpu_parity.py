@@ -352,6 +352,18 @@ def test_empty_mesh_is_a_no_op(ctx):
                                                        None, None], "f32")
     ctx.check()
     assert K.shape == (0, 81, 81)
+    # the step of the benchmark on no elements: deferred geometry computed by the
+    # residual kernel, tensor-core matrix, assembly of nothing
+    lazy = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    lazy.update()
+    lm0 = torch.zeros((0, 2), dtype=torch.float64, device="cuda")
+    u = torch.zeros(3 * mesh.n_nodes, dtype=torch.float32, device="cuda")
+    r = fe.eval_residual(ctx, fe.elasticity_form(), lazy, [lm0, None, u], "bf16x3")
+    K = fe.eval_matrix(ctx, fe.elasticity_form(), lazy, [lm0, None, None], "bf16x3")
+    gv = fe.assemble_vector(ctx, fe.assembly_create(ctx, m), 3, r, "f32", flags=fe.ASSEMBLE_COMPENSATED)
+    ctx.check()
+    assert r.shape == (0, 81) and K.shape == (0, 81, 81)
+    assert gv.shape == (3 * mesh.n_nodes,) and not torch.any(gv)
 
 
 def test_argument_errors(ctx):
