@@ -420,6 +420,14 @@ fe_status fe_assembly_free(fe_assembly_h *asm_h);
 fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *asm_h, int ncomp, const void *r_e, fe_precision prec,
                              void *global_out, unsigned flags, fe_stream_t stream);
 
+/* Diagnostic: rounds n float64 values (device array `in`) to float32 (device
+ * array `out`) with the rounding that the geometry kernels apply to the
+ * cofactors, det J and the weights of a float32 copy (nearest, ties to even:
+ * the same bits as a hardware conversion; computed with integer operations
+ * for normal results).  Errors: FE_ERR_INVALID_ARG (NULL arrays, n < 0),
+ * FE_ERR_CUDA. */
+fe_status fe_round_f32(fe_ctx *ctx, const double *in, float *out, long long n, fe_stream_t stream);
+
 /* One-shot assembly for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -569,6 +569,14 @@ fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *a, int ncomp, con
                      "fe_assemble_vector");
 }
 
+fe_status fe_round_f32(fe_ctx *ctx, const double *in, float *out, long long n, fe_stream_t stream)
+{
+    fe_clear_last_error();
+    if (!ctx || n < 0 || (n > 0 && (!in || !out))) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    return from_cuda(fe_launch_round_f32(in, out, n, to_cuda(stream)), "fe_round_f32");
+}
+
 fe_status fe_assemble_vector_noalloc(fe_ctx *ctx, const fe_mesh *mesh, int ncomp, const void *r_e,
                                      fe_precision prec, void *global_out, unsigned flags, fe_stream_t stream)
 {

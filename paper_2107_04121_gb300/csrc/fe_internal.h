@@ -127,6 +127,9 @@ cudaError_t fe_launch_assemble_noalloc(int device, const fe_mesh *mesh, int ncom
 
 // Status of a CUDA error, recorded as the thread's last error message (api.cu).
 fe_status fe_status_from_cuda(cudaError_t e, const char *where);
+// The float64 -> float32 rounding of the geometry kernels over an array (k_geometry.cu).
+cudaError_t fe_launch_round_f32(const double *in, float *out, long long n, cudaStream_t s);
+
 // Every fe_status entry point starts with this: the message of
 // fe_last_error_message then always belongs to the latest call (api.cu).
 void fe_clear_last_error();

@@ -121,17 +121,38 @@ __device__ __forceinline__ double geo_det(const double *J, double c00, double c0
     return __fma_rn(J[2], c02, __fma_rn(J[1], c01, __dmul_rn(J[0], c00)));
 }
 
+// Round an FP64 value to float32 (to nearest, ties to even) with integer
+// operations, off the FP64 pipe that the geometry saturates.  When the result is
+// a normal float32 (biased FP64 exponent 897 ... 1150): the top 23 mantissa bits
+// with the exponent rebiased by 1023 - 127 = 896 (a funnel shift of the two
+// words), plus one when the 29 dropped bits exceed half an ulp or equal it with
+// an odd result (a carry into the exponent is the correct rounding, up to
+// infinity).  Zero, subnormal results, infinities and NaN take the hardware
+// conversion.  Same bits as __double2float_rn for every input.
+__device__ __forceinline__ float geo_to_f32(double x)
+{
+    const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
+    const unsigned e11 = (hi >> 20) & 0x7FFu;
+    if (e11 - 897u <= 253u) {
+        unsigned f = __funnelshift_l(lo, (hi & 0x7FFFFFFFu) - 0x38000000u, 3);
+        const unsigned rem = lo & 0x1FFFFFFFu;
+        f += (unsigned)(rem > 0x10000000u) | ((unsigned)(rem == 0x10000000u) & f);
+        return __uint_as_float(f | (hi & 0x80000000u));
+    }
+    return __double2float_rn(x);
+}
+
 // float32 part of the stored copy: 1 / det J and w det J, both formed in
 // float32 from the rounded det J (the cofactors and det J carry the FP64
 // cancellation of distorted elements).
 __device__ __forceinline__ void geo_quotient_f32(double det, double wq, float &rf, float &wd)
 {
-    const float df = __double2float_rn(det);
+    const float df = geo_to_f32(det);
     rf = __fdiv_rn(1.0f, df);
-    wd = __fmul_rn(__double2float_rn(wq), df);
+    wd = __fmul_rn(geo_to_f32(wq), df);
 }
 
-__device__ __forceinline__ float geo_inverse_entry(double c, float rf) { return __fmul_rn(__double2float_rn(c), rf); }
+__device__ __forceinline__ float geo_inverse_entry(double c, float rf) { return __fmul_rn(geo_to_f32(c), rf); }
 
 // One quadrature point of a float32-only geometry: det J (returned, FP64), the
 // float32 J^-1 (row-major, o[m * 3 + j] = (J^-1)_mj) and w det J.

@@ -383,6 +383,12 @@ cudaError_t launch_geom_co(const fe_geometry_h *g, unsigned long long *st, cudaS
     return cudaGetLastError();
 }
 
+__global__ void k_round_f32(const double *__restrict__ in, float *__restrict__ out, long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = geo_to_f32(in[i]);
+}
+
 }  // namespace
 
 cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *st, cudaStream_t s)
@@ -424,5 +430,14 @@ cudaError_t fe_launch_geometry_G(const fe_geometry_h *g, bool f64, void *out, cu
     else
         k_expand_G<float><<<(unsigned)blocks, 256, 0, s>>>(g->d_jinv32, g->d_dphi32, g->mesh.n_elems, g->Q, g->N,
                                                            (float *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t fe_launch_round_f32(const double *in, float *out, long long n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    k_round_f32<<<(unsigned)blocks, 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
 }

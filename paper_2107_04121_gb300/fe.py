@@ -38,7 +38,7 @@ EXPORTED = [
     "fe_assembly_create",
     "fe_assembly_free",
     "fe_assemble_vector", "fe_assemble_vector_noalloc", "fe_batch_create", "fe_batch_run", "fe_batch_describe",
-    "fe_batch_free",
+    "fe_batch_free", "fe_round_f32",
 ]
 
 
@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_assembly_free.argtypes = [vp]
     L.fe_assemble_vector.argtypes = [vp, vp, i, vp, i, vp, ctypes.c_uint, vp]
     L.fe_assemble_vector_noalloc.argtypes = [vp, ctypes.POINTER(_Mesh), i, vp, i, vp, ctypes.c_uint, vp]
+    L.fe_round_f32.argtypes = [vp, vp, vp, ctypes.c_longlong, vp]
     for name in EXPORTED:
         if name not in ("fe_status_str", "fe_last_error_message", "fe_version"):
             getattr(L, name).restype = st
@@ -604,3 +605,14 @@ def convect_form(advection: int = STATE, gradient: int = STATE) -> Form:
 def elasticity_form(material: int = MAT_LAME) -> Form:
     return form_compile("IK,s(i:j)->I,s(k:l)->K",
                         [(MATERIAL, 1, material), (VIRTUAL, 3, MAT_NONE), (STATE, 3, MAT_NONE)])
+
+
+def round_f32(ctx: Context, x, stream=None):
+    """fe_round_f32: float64 device tensor -> float32, with the rounding of the
+    geometry kernels' float32 copy (diagnostic)."""
+    import torch
+    _dev(x, torch.float64, "in")
+    out = torch.empty(x.shape, dtype=torch.float32, device=x.device)
+    _check(_lib.fe_round_f32(ctx.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
+                             _stream_ptr(stream)), "fe_round_f32")
+    return out

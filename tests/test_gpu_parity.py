@@ -58,6 +58,34 @@ def test_direct_and_sum_factorised_geometry_agree(ctx, p, nq):
     ctx.check()
 
 
+def test_float32_rounding_of_the_geometry_matches_ieee(ctx):
+    """The integer float64 -> float32 rounding of the geometry kernels gives the
+    IEEE nearest-even result (numpy's conversion) bit for bit: ties either way,
+    carries into the exponent, the ends of the normal range, and the values that
+    take the hardware path (zero, subnormal results, overflow, inf, NaN)."""
+    rng = np.random.default_rng(98)
+    one_ulp32 = 2.0 ** -23
+    edge = [0.0, -0.0, 1.0, -1.0, 1.5, 1.0 + one_ulp32 / 2, 1.0 + 3 * one_ulp32 / 2, 1.0 + one_ulp32 / 2 + 2.0 ** -40,
+            1.0 + one_ulp32 / 2 - 2.0 ** -40, 2.0 - 2.0 ** -30, np.nextafter(2.0, 0.0),
+            float(np.finfo(np.float32).tiny), float(np.finfo(np.float32).tiny) * (1 - 2.0 ** -30),
+            float(np.finfo(np.float32).tiny) / 3, 1e-40, 1e-46, 2.0 ** -149, 2.0 ** -150, 3 * 2.0 ** -151,
+            float(np.finfo(np.float32).max), float(np.finfo(np.float32).max) * (1 + 2.0 ** -25),
+            float(np.finfo(np.float32).max) * (1 + 2.0 ** -23), 1e39, -1e39, 1e300, -1e-300, np.inf, -np.inf]
+    rand = [rng.standard_normal(20000) * 10.0 ** rng.uniform(-40, 40, 20000),
+            # float32 values plus exactly half their spacing: ties, to the even neighbour
+            (lambda f: f.astype(np.float64) + np.spacing(f).astype(np.float64) / 2)(
+                (rng.standard_normal(5000) * 10.0 ** rng.uniform(-30, 30, 5000)).astype(np.float32)),
+            rng.uniform(-1, 1, 20000)]
+    x = np.concatenate([np.array(edge)] + rand)
+    with np.errstate(over="ignore"):
+        want = x.astype(np.float32)
+    got = fe.round_f32(ctx, _t(x, torch.float64)).cpu().numpy()
+    ctx.check()
+    np.testing.assert_array_equal(got.view(np.uint32), want.view(np.uint32))
+    nan = fe.round_f32(ctx, _t(np.array([np.nan, -np.nan]), torch.float64)).cpu().numpy()
+    assert np.all(np.isnan(nan))
+
+
 def test_inconsistent_tensor_factors_are_rejected(ctx):
     mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
     P = Problem(ctx, mesh, 2, 3)
