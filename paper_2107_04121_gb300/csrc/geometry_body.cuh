@@ -174,8 +174,12 @@ __device__ __forceinline__ double geo_point_f32(const double *J, double wq, floa
 }
 
 // Status of a point's det J: positive and finite, else the error to report.
+// Read from the bits with integer operations (the FP64 pipe is the busy one):
+// an all-ones exponent is infinite or NaN, a set sign bit or +0 is not positive.
 __device__ __forceinline__ int geo_det_status(double det)
 {
-    if (det > 0.0 && isfinite(det)) return FE_OK;
-    return isfinite(det) ? FE_ERR_NONPOSITIVE_DETJ : FE_ERR_NONFINITE;
+    const unsigned hi = (unsigned)__double2hiint(det), lo = (unsigned)__double2loint(det);
+    if (((hi >> 20) & 0x7FFu) == 0x7FFu) return FE_ERR_NONFINITE;
+    if ((hi >> 31) != 0u || (hi | lo) == 0u) return FE_ERR_NONPOSITIVE_DETJ;
+    return FE_OK;
 }

@@ -130,6 +130,29 @@ def test_nonpositive_detj_is_reported(ctx):
     assert ctx.status() == (fe.FE_OK, -1)  # cleared
 
 
+@pytest.mark.parametrize("path", ["geometry", "residual"])
+def test_degenerate_and_nonfinite_geometry_are_reported(ctx, path):
+    """det J = 0 exactly (an element collapsed to a point) and a NaN coordinate, from
+    the geometry kernel and from the residual kernel that computes a stale geometry."""
+    mesh = meshgen.structured_hex(1, 1, 1, 2, 0.0, 0)
+    lm = _t(np.ones((1, 2)), torch.float64)
+    u = _t(np.zeros(3 * mesh.n_nodes), torch.float32)
+    for value, code in ((None, fe.FE_ERR_NONPOSITIVE_DETJ), (np.nan, fe.FE_ERR_NONFINITE)):
+        coords = mesh.coords.copy()
+        if value is None:
+            coords[:] = coords[0]
+        else:
+            coords[13, 1] = value
+        m = fe.Mesh(_t(coords, torch.float64), _t(mesh.conn, torch.int32))
+        ctx.status()
+        if path == "geometry":
+            fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32)
+        else:
+            lazy = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+            fe.eval_residual(ctx, fe.elasticity_form(), lazy, [lm, None, u], "f32")
+        assert ctx.status() == (code, 0)
+
+
 # ---- matrix and residual modes ----------------------------------------------------
 
 def _case(ctx, kind, p, n, seed, material=fe.MAT_LAME):
