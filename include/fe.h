@@ -420,6 +420,15 @@ fe_status fe_assembly_free(fe_assembly_h *asm_h);
 fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *asm_h, int ncomp, const void *r_e, fe_precision prec,
                              void *global_out, unsigned flags, fe_stream_t stream);
 
+/* Test hook for the bounded device waits: the next tensor-core matrix launch
+ * (fe_eval_matrix with FE_TF32X3, FE_BF16X3 or FE_BF16) on this context first
+ * waits on a device flag that nothing sets.  Its bounded wait (about two
+ * seconds) runs out, every CTA takes its abort path (the MMAs it issued are
+ * drained, its tensor memory freed) and FE_ERR_TIMEOUT is reported through
+ * fe_get_status; the context stays usable.  Errors: FE_ERR_INVALID_ARG,
+ * FE_ERR_CUDA. */
+fe_status fe_debug_hold_next_matrix(fe_ctx *ctx);
+
 /* Diagnostic: rounds n float64 values (device array `in`) to float32 (device
  * array `out`) with the rounding that the geometry kernels apply to the
  * cofactors, det J and the weights of a float32 copy (nearest, ties to even:

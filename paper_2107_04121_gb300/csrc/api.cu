@@ -12,7 +12,7 @@
 cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
                                   void *K, int sm_count, cudaStream_t s);
 cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
-                                void *K, int sm_count, unsigned long long *status, cudaStream_t s);
+                                void *K, int sm_count, unsigned long long *status, const int *hold, cudaStream_t s);
 
 // A deferred handle whose geometry is stale gets it computed before any use.
 static cudaError_t settle_geometry(fe_geometry_h *g, unsigned long long *status, cudaStream_t s)
@@ -147,6 +147,7 @@ fe_status fe_destroy(fe_ctx *ctx)
     if (!ctx) return FE_ERR_INVALID_ARG;
     cudaSetDevice(ctx->device);
     cudaFree(ctx->d_status);
+    cudaFree(ctx->d_hold);
     delete ctx;
     return FE_OK;
 }
@@ -414,7 +415,10 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
         if (form->kind != FK_ELASTICITY || form->mat != FE_MAT_LAME || !(g->N == 27 && g->Q == 27))
             return FE_ERR_UNSUPPORTED_SPEC;
         e = settle_geometry(gm, ctx->d_status, s);
-        if (e == cudaSuccess) e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, ctx->d_status, s);
+        const int *hold = ctx->hold_next_matrix ? ctx->d_hold : nullptr;
+        ctx->hold_next_matrix = 0;
+        if (e == cudaSuccess)
+            e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, ctx->d_status, hold, s);
     }
     return from_cuda(e, "fe_eval_matrix");
 }
@@ -567,6 +571,20 @@ fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *a, int ncomp, con
     cudaSetDevice(ctx->device);
     return from_cuda(fe_launch_assemble(a, ncomp, prec == FE_F64, r_e, global_out, flags, to_cuda(stream)),
                      "fe_assemble_vector");
+}
+
+fe_status fe_debug_hold_next_matrix(fe_ctx *ctx)
+{
+    fe_clear_last_error();
+    if (!ctx) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    if (!ctx->d_hold) {
+        cudaError_t e = dev_alloc(&ctx->d_hold, 1);
+        if (e == cudaSuccess) e = cudaMemset(ctx->d_hold, 0, sizeof(int));
+        if (e != cudaSuccess) return from_cuda(e, "fe_debug_hold_next_matrix");
+    }
+    ctx->hold_next_matrix = 1;
+    return FE_OK;
 }
 
 fe_status fe_round_f32(fe_ctx *ctx, const double *in, float *out, long long n, fe_stream_t stream)

@@ -14,6 +14,8 @@ struct fe_ctx {
     int device;
     int sm_count;
     unsigned long long *d_status;  // 2 words
+    int *d_hold;                   // test hook: a device flag that nothing sets (fe_debug_hold_next_matrix)
+    int hold_next_matrix;          // the next tensor-core matrix launch waits on d_hold
 };
 
 // Geometry handle: FP64-derived reference-mapping data, element-outermost so

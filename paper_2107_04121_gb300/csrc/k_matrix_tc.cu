@@ -327,13 +327,24 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     return true;
 }
 
+// The same wait bounded by time alone (the drain of an aborting CTA).
+__device__ __forceinline__ bool mbar_wait_cycles(uint32_t bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+    }
+    return true;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_matrix_tc(const float *__restrict__ jinv,
                                                                  const float *__restrict__ wdetj,
                                                                  const float *__restrict__ dphi, long long E,
                                                                  const double *__restrict__ lame,
                                                                  float *__restrict__ K,
-                                                                 unsigned long long *__restrict__ status)
+                                                                 unsigned long long *__restrict__ status,
+                                                                 const int *__restrict__ hold)
 {
     using P = TcSmem<MODE>;
     using L = typename P::L;
@@ -410,6 +421,8 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
                     for (int k = 0; k < 3; ++k) dreg[ci][g][v][k] = ok ? sDp[(q * 3 + k) * TC_N + a] : 0.0f;
                 }
         int n = 0;
+        int last_b = -1;  // thread 0: buffer and phase parity of the last MMA commit
+        uint32_t last_parity = 0;
         for (long long e = blockIdx.x; e < E; e += gridDim.x, ++n) {
             const int b = n & 1;
             unsigned char *opHi = smem + b * P::BUF + P::HI;
@@ -520,11 +533,31 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                                  smem_u32(full + b))
                              : "memory");
+                last_b = b;
+                last_parity = (uint32_t)((n >> 1) & 1);
             }
         }
+        // an aborting CTA frees its tensor memory only after the MMAs it issued are
+        // done (a commit completes when all earlier MMAs of the thread have)
+        if (ptid == 0 && *abort_flag && last_b >= 0) mbar_wait_cycles(smem_u32(full + last_b), last_parity);
     } else {
         // ------------------------------------------------------------ consumer
         const int ctid = tid;
+        if (hold) {
+            // test hook: wait on a flag that nothing sets, so that the bounded wait
+            // runs out and the abort path is taken
+            if (ctid == 0) {
+                const long long t0 = clock64();
+                while (*(volatile const int *)hold == 0) {
+                    if (clock64() - t0 > TC_WAIT_CYCLES) {
+                        *abort_flag = 1;
+                        fe_report(status, FE_ERR_TIMEOUT, blockIdx.x);
+                        break;
+                    }
+                }
+            }
+            named_sync(TC_BAR_CONS, TC_CONS);
+        }
         int n = 0;
         for (long long e = blockIdx.x; e < E; e += gridDim.x, ++n) {
             const int b = n & 1;
@@ -599,7 +632,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
 
 template <int MODE>
 cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int sm_count,
-                      unsigned long long *status, cudaStream_t s)
+                      unsigned long long *status, const int *hold, cudaStream_t s)
 {
     using P = TcSmem<MODE>;
     static_assert(P::BYTES <= 227 * 1024, "shared memory plan too large");
@@ -634,22 +667,22 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
     long long blocks = per_sm * sm_count;
     if (blocks > g->mesh.n_elems) blocks = g->mesh.n_elems;
     kern<<<(unsigned)blocks, TC_THREADS_WS, P::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->mesh.n_elems,
-                                                        mat.data, (float *)K, status);
+                                                        mat.data, (float *)K, status, hold);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
-                                void *K, int sm_count, unsigned long long *status, cudaStream_t s)
+                                void *K, int sm_count, unsigned long long *status, const int *hold, cudaStream_t s)
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
     if (f->kind != FK_ELASTICITY || mat.kind != FE_MAT_LAME || g->N != TC_N || g->Q != TC_Q)
         return cudaErrorNotSupported;
     switch (prec) {
-    case FE_TF32X3: return launch_tc<TC_TF32X3>(g, mat, K, sm_count, status, s);
-    case FE_BF16X3: return launch_tc<TC_BF16X3>(g, mat, K, sm_count, status, s);
-    case FE_BF16: return launch_tc<TC_BF16>(g, mat, K, sm_count, status, s);
+    case FE_TF32X3: return launch_tc<TC_TF32X3>(g, mat, K, sm_count, status, hold, s);
+    case FE_BF16X3: return launch_tc<TC_BF16X3>(g, mat, K, sm_count, status, hold, s);
+    case FE_BF16: return launch_tc<TC_BF16>(g, mat, K, sm_count, status, hold, s);
     default: return cudaErrorNotSupported;
     }
 }

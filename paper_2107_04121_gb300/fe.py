@@ -38,7 +38,7 @@ EXPORTED = [
     "fe_assembly_create",
     "fe_assembly_free",
     "fe_assemble_vector", "fe_assemble_vector_noalloc", "fe_batch_create", "fe_batch_run", "fe_batch_describe",
-    "fe_batch_free", "fe_round_f32",
+    "fe_batch_free", "fe_round_f32", "fe_debug_hold_next_matrix",
 ]
 
 
@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_assemble_vector.argtypes = [vp, vp, i, vp, i, vp, ctypes.c_uint, vp]
     L.fe_assemble_vector_noalloc.argtypes = [vp, ctypes.POINTER(_Mesh), i, vp, i, vp, ctypes.c_uint, vp]
     L.fe_round_f32.argtypes = [vp, vp, vp, ctypes.c_longlong, vp]
+    L.fe_debug_hold_next_matrix.argtypes = [vp]
     for name in EXPORTED:
         if name not in ("fe_status_str", "fe_last_error_message", "fe_version"):
             getattr(L, name).restype = st
@@ -616,3 +617,9 @@ def round_f32(ctx: Context, x, stream=None):
     _check(_lib.fe_round_f32(ctx.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.numel(),
                              _stream_ptr(stream)), "fe_round_f32")
     return out
+
+
+def debug_hold_next_matrix(ctx: Context):
+    """fe_debug_hold_next_matrix: the next tensor-core matrix launch waits on a
+    flag that nothing sets, times out and reports FE_ERR_TIMEOUT (test hook)."""
+    _check(_lib.fe_debug_hold_next_matrix(ctx.handle), "fe_debug_hold_next_matrix")

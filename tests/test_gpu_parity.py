@@ -1,5 +1,7 @@
 """GPU parity: libfe (through the C ABI) against the FP64 oracle, element by
 element, on seeded meshes that span several CTA tiles and a ragged tail."""
+import time
+
 import numpy as np
 import pytest
 
@@ -362,6 +364,27 @@ def test_deferred_geometry_reports_nonpositive_detj(ctx):
     lm = _t(np.ones((mesh.n_elems, 2)), torch.float64)
     fe.eval_matrix(ctx, fe.elasticity_form(), lazy, [lm, None, None], "bf16x3")
     assert ctx.status() == (fe.FE_ERR_NONPOSITIVE_DETJ, 5)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_tensor_core_wait_timeout_is_reported_and_the_context_recovers(ctx, prec):
+    """A tensor-core launch whose consumers wait on a flag that nothing sets: the
+    bounded wait runs out (about two seconds), every CTA drains its MMAs and leaves,
+    FE_ERR_TIMEOUT is reported, and the next launch on the context is a normal one."""
+    # 1,000 elements: two or three per CTA, so the producers also run into their
+    # bounded waits and drain the MMAs already issued
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (10, 10, 10), 97)
+    args = [_t(mat, torch.float64), None, None]
+    ctx.status()
+    fe.debug_hold_next_matrix(ctx)
+    t0 = time.time()
+    fe.eval_matrix(ctx, form, P.geom, args, prec)
+    st, bad = ctx.status()
+    assert st == fe.FE_ERR_TIMEOUT and bad >= 0
+    assert time.time() - t0 < 60
+    K = fe.eval_matrix(ctx, form, P.geom, args, prec)
+    ctx.check()
+    assert rel_matrix_error(K.cpu().numpy(), Kref) <= TOL[prec]
 
 
 def test_tensor_core_paths_reject_other_forms(ctx):
