@@ -446,7 +446,15 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
         const bool empty = g->mesh.n_elems == 0;
         if (!args || (!empty && (!args[form->grad_op] || !args[form->adv_op]))) return FE_ERR_INVALID_ARG;
         cudaStream_t s = to_cuda(stream);
-        cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, s);
+        fe_geometry_h *gm = const_cast<fe_geometry_h *>(g);
+        if (gm->pending && prec != FE_F64 && fe_convect_geometry_fusable(gm)) {
+            // stale float32-only deferred handle: the residual kernel computes it
+            cudaError_t e = fe_launch_convect_residual_geometry(gm, args[form->grad_op], args[form->adv_op], r_out,
+                                                                ctx->d_status, s);
+            if (e == cudaSuccess) gm->pending = 0;
+            return from_cuda(e, "fe_eval_residual");
+        }
+        cudaError_t e = settle_geometry(gm, ctx->d_status, s);
         if (e == cudaSuccess)
             e = fe_launch_convect(g, prec == FE_F64, args[form->grad_op], args[form->adv_op], 0, 0, nullptr, r_out,
                                   ctx->d_status, s);

@@ -106,6 +106,11 @@ cudaError_t fe_launch_residual_geometry(fe_geometry_h *g, const fe_form_h *f, fe
 cudaError_t fe_launch_convect(const fe_geometry_h *g, bool f64, const void *u, const void *w, int wrt_grad,
                               int wrt_adv, void *K, void *r, unsigned long long *status, cudaStream_t s);
 bool fe_convect_supported(const fe_geometry_h *g);
+// Convective residual of a stale float32-only deferred geometry with the
+// geometry computed in the same kernel (n1 == nq); stores the float32 copy.
+bool fe_convect_geometry_fusable(const fe_geometry_h *g);
+cudaError_t fe_launch_convect_residual_geometry(const fe_geometry_h *g, const void *u, const void *w, void *r,
+                                                unsigned long long *status, cudaStream_t s);
 // Generic kernels (runtime N, Q) of the remaining forms and of eval mode:
 // mode 0 residual (out (E, ncomp_test N)), 1 matrix (out (E, rows, cols)),
 // 2 eval (out (E, n_out)).  f0, f1, f2: the DOF vectors of the form's field

@@ -26,7 +26,7 @@
 //       matrix, so each row of K is written by consecutive threads (coalesced).
 // About 48 k FMA per Q2 element instead of the ~110 k of the point-by-point
 // sums; FP64 is compute-bound, FP32 is bound by the K write.
-#include "fe_device.cuh"
+#include "geometry_body.cuh"
 
 namespace {
 
@@ -50,16 +50,28 @@ struct CvPlan {
     static constexpr int PER_EL = R2 + R2N;
 };
 
-template <typename T, int N1, int NQ, bool MAT, int EPB, int THREADS>
+// Geometry computed in the residual kernel (a stale float32-only deferred
+// handle, n1 == nq): the mesh, the FP64 1-D tables and where the float32 copy goes.
+struct CvGeoArgs {
+    const double *coords;
+    const double *b1d, *dq, *w;  // (n1, n1) values at the points, derivative on the points, weights
+    float *jinv_out, *wdetj_out;
+};
+
+template <typename T, int N1, int NQ, bool MAT, int EPB, int THREADS, int GEO>
 __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ jinv, const T *__restrict__ wdetj,
                                                         const T *__restrict__ b1d, const T *__restrict__ d1d,
                                                         const int32_t *__restrict__ conn, long long E,
                                                         const T *__restrict__ u, const T *__restrict__ w, int same,
                                                         int wrt_grad, int wrt_adv, T *__restrict__ K,
                                                         T *__restrict__ r, long long n_nodes,
-                                                        unsigned long long *__restrict__ status)
+                                                        unsigned long long *__restrict__ status, const CvGeoArgs geo)
 {
+    // GEO: 0 = geometry read from the handle, 1 = computed here, 2 = computed here
+    // with the middle point on the middle node (three points per axis)
     using P = CvPlan<T, N1, NQ, MAT>;
+    static_assert(!GEO || (!MAT && N1 == NQ && sizeof(T) == 4), "in-kernel geometry: float32 residual, n1 == nq");
+    static_assert(!GEO || 12 * N1 * N1 * N1 * 2 <= P::R1N + P::R2N, "FP64 geometry fits the stage buffers");
     constexpr int N = P::N, Q = P::Q, LX = P::LX, LY = P::LY, PE = P::PER_EL;
     extern __shared__ __align__(16) unsigned char cv_smem[];
     T *sm = reinterpret_cast<T *>(cv_smem);
@@ -72,12 +84,19 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
             D[q][i] = d1d[q * N1 + i];
         }
     const int nf = same ? 3 : 6;  // interpolated vector fields: u, and w when it differs
+    // GEO tables after the per-element blocks: B, Dq (n1 x n1), w (Q), FP64
+    double *gT = reinterpret_cast<double *>(sm + ((EPB * PE + 1) / 2) * 2);
+    if constexpr (GEO != 0)
+        for (int i = threadIdx.x; i < 2 * N1 * N1 + Q; i += THREADS)
+            gT[i] = i < N1 * N1 ? geo.b1d[i] : (i < 2 * N1 * N1 ? geo.dq[i - N1 * N1] : geo.w[i - 2 * N1 * N1]);
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
         const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
         __syncthreads();
-        for (int t = threadIdx.x; t < ne * Q * 9; t += THREADS)
-            sm[(t / (Q * 9)) * PE + P::JI + t % (Q * 9)] = jinv[e0 * Q * 9 + t];
-        for (int t = threadIdx.x; t < ne * Q; t += THREADS) sm[(t / Q) * PE + P::WD + t % Q] = wdetj[e0 * Q + t];
+        if constexpr (GEO == 0) {
+            for (int t = threadIdx.x; t < ne * Q * 9; t += THREADS)
+                sm[(t / (Q * 9)) * PE + P::JI + t % (Q * 9)] = jinv[e0 * Q * 9 + t];
+            for (int t = threadIdx.x; t < ne * Q; t += THREADS) sm[(t / Q) * PE + P::WD + t % Q] = wdetj[e0 * Q + t];
+        }
         for (int t = threadIdx.x; t < ne * N; t += THREADS) {
             const int el = t / N, a = t % N;
             const long long node = conn[(e0 + el) * N + a];
@@ -88,6 +107,48 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
             for (int c = 0; c < 3; ++c) {
                 U[c * N + a] = ok ? u[node * 3 + c] : (T)0;
                 if (!same) U[(3 + c) * N + a] = ok ? w[node * 3 + c] : (T)0;
+            }
+            if constexpr (GEO != 0) {
+                // nodal x into the FP64 work area over the stage buffers: [X | U | V | -]
+                double *G = reinterpret_cast<double *>(sm + el * PE + P::R1);
+                const long long nd = ok ? node : 0;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) G[c * N + a] = geo.coords[3 * nd + c];
+            }
+        }
+        if constexpr (GEO != 0) {
+            // FP64 geometry of the group (the stages and roundings of the geometry kernel)
+            constexpr bool CENTER = GEO == 2;
+            constexpr int L = N1 * N1;
+            auto gbuf = [&](int el) { return reinterpret_cast<double *>(sm + el * PE + P::R1); };
+            __syncthreads();
+            for (int t = threadIdx.x; t < ne * 3 * L; t += THREADS)
+                geo_lines_x<N1, CENTER>(t % (3 * L), gbuf(t / (3 * L)), gbuf(t / (3 * L)) + 3 * N, gT);
+            __syncthreads();
+            for (int t = threadIdx.x; t < ne * 3 * L; t += THREADS)
+                geo_lines_y<N1, CENTER>(t % (3 * L), gbuf(t / (3 * L)) + 3 * N, gbuf(t / (3 * L)) + 6 * N, gT);
+            __syncthreads();
+            for (int t = threadIdx.x; t < ne * 3 * L; t += THREADS)
+                geo_lines_z<N1, CENTER>(t % (3 * L), gbuf(t / (3 * L)) + 6 * N, gbuf(t / (3 * L)), gT);
+            __syncthreads();
+            for (int t = threadIdx.x; t < ne * 9 * L; t += THREADS)
+                geo_lines_jacobian<N1, CENTER>(t % (9 * L), gbuf(t / (9 * L)), gbuf(t / (9 * L)) + 3 * N,
+                                               gT + N1 * N1);
+            __syncthreads();
+            for (int t = threadIdx.x; t < ne * Q; t += THREADS) {
+                const int el = t / Q, q = t % Q;
+                float o[9], wdq;
+                const double det = geo_point_f32(gbuf(el) + 3 * N + q * 9, gT[2 * N1 * N1 + q], o, wdq);
+                const int bad = geo_det_status(det);
+                if (bad) fe_report(status, bad, e0 + el);
+                const long long idx = (e0 + el) * Q + q;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    geo.jinv_out[idx * 9 + k] = o[k];
+                    sm[el * PE + P::JI + q * 9 + k] = o[k];
+                }
+                geo.wdetj_out[idx] = wdq;
+                sm[el * PE + P::WD + q] = wdq;
             }
         }
         __syncthreads();
@@ -358,15 +419,17 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
     }
 }
 
-template <typename T, int N1, int NQ, bool MAT, int EPB>
+template <typename T, int N1, int NQ, bool MAT, int EPB, int GEO = 0>
 cudaError_t launch_cv(const fe_geometry_h *g, const void *u, const void *w, int wrt_grad, int wrt_adv, void *K,
                       void *r, unsigned long long *st, cudaStream_t s)
 {
     using P = CvPlan<T, N1, NQ, MAT>;
     constexpr int THREADS = MAT ? ((EPB * 3 * P::N + 31) / 32) * 32 : 256;
-    constexpr size_t SMEM = sizeof(T) * (size_t)P::PER_EL * EPB;
+    // per-element blocks, then (GEO) the FP64 tables 8-byte aligned
+    constexpr size_t SMEM = sizeof(T) * (size_t)((P::PER_EL * EPB + 1) / 2 * 2) +
+                            (GEO ? sizeof(double) * (2 * N1 * N1 + P::Q) : 0);
     static_assert(SMEM <= 227 * 1024, "shared memory plan too large");
-    auto kern = k_convect_sf<T, N1, NQ, MAT, EPB, THREADS>;
+    auto kern = k_convect_sf<T, N1, NQ, MAT, EPB, THREADS, GEO>;
     static FeLaunchCache cache;
     long long cap = 0;
     cudaError_t err = fe_cached_grid(
@@ -389,10 +452,13 @@ cudaError_t launch_cv(const fe_geometry_h *g, const void *u, const void *w, int 
     if (blocks > cap) blocks = cap;
     constexpr bool f64 = sizeof(T) == 8;
     const int same = u == w;
+    CvGeoArgs geo{};
+    if (GEO) geo = CvGeoArgs{g->mesh.coords, g->d_b1d, g->d_dq, g->d_w64, g->d_jinv32, g->d_wdetj32};
     kern<<<(unsigned)blocks, THREADS, SMEM, s>>>(
         f64 ? (const T *)g->d_jinv64 : (const T *)g->d_jinv32, f64 ? (const T *)g->d_wdetj64 : (const T *)g->d_wdetj32,
         f64 ? (const T *)g->d_b1d : (const T *)g->d_b1d32, f64 ? (const T *)g->d_d1d : (const T *)g->d_d1d32,
-        g->mesh.conn, E, (const T *)u, (const T *)w, same, wrt_grad, wrt_adv, (T *)K, (T *)r, g->mesh.n_nodes, st);
+        g->mesh.conn, E, (const T *)u, (const T *)w, same, wrt_grad, wrt_adv, (T *)K, (T *)r, g->mesh.n_nodes, st,
+        geo);
     return cudaGetLastError();
 }
 
@@ -435,4 +501,25 @@ cudaError_t fe_launch_convect(const fe_geometry_h *g, bool f64, const void *u, c
     if (g->mesh.n_elems == 0) return cudaSuccess;
     return f64 ? dispatch_cv<double>(g, u, w, wrt_grad, wrt_adv, K, r, status, s)
                : dispatch_cv<float>(g, u, w, wrt_grad, wrt_adv, K, r, status, s);
+}
+
+bool fe_convect_geometry_fusable(const fe_geometry_h *g)
+{
+    return g->d_dq && g->d_jinv32 && !g->is_view && (g->flags & FE_GEOM_STORE_F32) &&
+           !(g->flags & FE_GEOM_STORE_F64) && g->n1d == g->nq1d && g->n1d >= 2 && g->n1d <= 4;
+}
+
+cudaError_t fe_launch_convect_residual_geometry(const fe_geometry_h *g, const void *u, const void *w, void *r,
+                                                unsigned long long *status, cudaStream_t s)
+{
+    if (!fe_convect_geometry_fusable(g)) return cudaErrorNotSupported;
+    if (g->mesh.n_elems == 0) return cudaSuccess;
+    switch (g->n1d) {
+    case 2: return launch_cv<float, 2, 2, false, 8, 1>(g, u, w, 0, 0, nullptr, r, status, s);
+    case 3:
+        return g->geo_center ? launch_cv<float, 3, 3, false, 8, 2>(g, u, w, 0, 0, nullptr, r, status, s)
+                             : launch_cv<float, 3, 3, false, 8, 1>(g, u, w, 0, 0, nullptr, r, status, s);
+    case 4: return launch_cv<float, 4, 4, false, 2, 1>(g, u, w, 0, 0, nullptr, r, status, s);
+    }
+    return cudaErrorNotSupported;
 }

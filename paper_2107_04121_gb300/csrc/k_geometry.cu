@@ -2,18 +2,20 @@
 // arXiv 2107.04121): J_ik = sum_a x_a,i d phi_a / d xi_k, det J, J^-1 and
 // w_q det J for every element and quadrature point, in FP64.
 //
-// Both kernels are FP64-pipe bound on GB300 (FP64 runs at 1/61 of the FP32
+// The kernels are FP64-pipe bound on GB300 (FP64 runs at 1/61 of the FP32
 // rate there), so what matters is the FP64 operation count:
-//  - k_geometry_sf (tensor-product bases): J by sum factorisation, three
-//    1-D contractions per coordinate and derivative direction, 2 n1 nq (n1^2 +
-//    n1 nq + nq^2)... for Q2 1,944 DFMA per element instead of 6,561;
 //  - k_geometry_co (tensor-product bases with n1 == nq): x interpolated to
 //    the points, then the collocation derivative on the points (1,134 DFMA
-//    per Q2 element with 3x3x3 Gauss points);
-//  - k_geometry (any tabulated basis): one thread per (element, quadrature
-//    point), J = sum_a x_a (x) grad phi_a directly (9N DFMA per point).
-// Both finish each point with the same cofactor inverse (about 40 FP64
-// operations).
+//    per Q2 element with 3x3x3 Gauss points, instead of 6,561 directly);
+//  - k_geometry_sf (tensor-product bases with n1 != nq, or when the collocation
+//    derivative cannot be formed): three 1-D contractions per coordinate and
+//    derivative direction;
+//  - k_geometry (any tabulated basis, e.g. tetrahedra): one thread per
+//    (element, quadrature point), J = sum_a x_a (x) grad phi_a directly (9N
+//    DFMA per point).
+// All finish each point with the same cofactor inverse (9 cofactors and det J:
+// 21 FP64 operations), whose float32 rounding uses integer operations
+// (geometry_body.cuh).
 #include "geometry_body.cuh"
 
 namespace {

@@ -56,6 +56,39 @@ def test_convect_matches_oracle(ctx, p, nq, n, roles, prec):
     assert er <= TOL[prec], er
 
 
+@pytest.mark.parametrize("roles", ["nonlinear", "wrt_u"])
+@pytest.mark.parametrize("p,n", [(1, (5, 4, 3)), (2, (5, 3, 3)), (3, (2, 2, 3)), (2, (20, 19, 18))])
+def test_convect_residual_computes_stale_geometry(ctx, p, n, roles):
+    """fe_eval_residual of the convective form on a stale float32-only deferred
+    handle computes the FP64 geometry in the residual kernel: r, the stored copy and
+    the matrix that follows equal the eager path's bit for bit (the largest case puts
+    several element groups on every CTA)."""
+    mesh = meshgen.structured_hex(*n, p, 0.15, 60 + p)
+    P = Problem(ctx, mesh, p, p + 1)
+    rng = np.random.default_rng(61 + p)
+    u = _t(rng.standard_normal(3 * mesh.n_nodes), torch.float32)
+    w = u if roles == "nonlinear" else _t(rng.standard_normal(3 * mesh.n_nodes), torch.float32)
+    gr, ad = ROLES[roles]
+    form = fe.convect_form(advection=ad, gradient=gr)
+    eager = fe.hex_geometry(ctx, P.m, p, p + 1, flags=fe.GEOM_STORE_F32)
+    lazy = fe.hex_geometry(ctx, P.m, p, p + 1, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    r_e = fe.eval_residual(ctx, form, eager, [None, u, w], "f32")
+    for _ in range(2):
+        lazy.update()
+        r_l = fe.eval_residual(ctx, form, lazy, [None, u, w], "f32")
+    ctx.check()
+    assert torch.equal(r_l, r_e)
+    assert torch.equal(lazy.get(fe.GEOM_JINV, "f32"), eager.get(fe.GEOM_JINV, "f32"))
+    assert torch.equal(lazy.get(fe.GEOM_WDETJ, "f32"), eager.get(fe.GEOM_WDETJ, "f32"))
+    assert torch.equal(fe.eval_matrix(ctx, form, lazy, [None, u, w], "f32"),
+                       fe.eval_matrix(ctx, form, eager, [None, u, w], "f32"))
+    if mesh.n_elems <= 100:
+        wdetJ, G, _ = P.oracle_geometry()
+        uh, wh = u.double().cpu().numpy(), w.double().cpu().numpy()
+        rref = oracle.residual_convect(mesh.conn, wdetJ, P.ref.phi, G, uh, wh)
+        assert rel_vector_error(r_l.cpu().numpy(), rref) <= TOL["f32"]
+
+
 def test_convect_smooth_field_config_small(ctx):
     """The smooth field sin(pi x) cos(pi y) a of the convection workload on a
     small cube; the assembled residual (compensated FP32) against the oracle's."""
