@@ -201,8 +201,9 @@ int fe_gm_rule_size(int s);
                                 fe_geometry_get) computes it first, on its own stream.  A
                                 handle that keeps only the float32 copy (FE_GEOM_STORE_F32)
                                 of a tensor-product hexahedron with n1d == nq1d is computed
-                                by fe_eval_residual itself (Laplace, mass or elasticity, any
-                                precision but FE_F64): one kernel for the FP64 geometry, the
+                                by fe_eval_residual itself (Laplace, mass, elasticity or the
+                                convective form, any precision but FE_F64): one kernel for the
+                                FP64 geometry, the
                                 stored float32 copy and the residual, with the same bits as
                                 the separate geometry kernel.  The stale mark is host state:
                                 use a deferred handle from one stream. */
