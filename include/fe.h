@@ -203,10 +203,9 @@ int fe_gm_rule_size(int s);
                                 of a tensor-product hexahedron with n1d == nq1d is computed
                                 by fe_eval_residual itself (Laplace, mass, elasticity or the
                                 convective form, any precision but FE_F64): one kernel for the
-                                FP64 geometry, the
-                                stored float32 copy and the residual, with the same bits as
-                                the separate geometry kernel.  The stale mark is host state:
-                                use a deferred handle from one stream. */
+                                FP64 geometry, the stored float32 copy and the residual, with
+                                the same bits as the separate geometry kernel.  The stale mark
+                                is host state: use a deferred handle from one stream. */
 
 /* Geometry of the reference mapping (Sec. 4.1): for every element e and
  * quadrature point q, J = sum_a x_a (x) grad_xi phi_a(q), det J, J^-1 and
