@@ -507,9 +507,10 @@ def convect_measure(n, device, ws, flush, ref, hbm_peak, steps=5, warmup=3):
 
 def adjoint_measure(n, device, flush, ref, steps=5, warmup=3):
     """One gradient step = forward (FP64 geometry, r_e, assembly, J) + backward
-    (geometry recomputed, adjoint kernel, assembly of dX, K Rbar for du), in FP32
-    and FP64, with the adjoint kernel timed alone; errors against the oracle
-    gradient (computed in the CPU-baseline leg)."""
+    (geometry recomputed, K Rbar for du, adjoint kernel, assembly of dX), in FP32
+    (the geometry computed by the residual kernels) and FP64, with the adjoint
+    kernel timed alone; errors against the oracle gradient (computed in the
+    CPU-baseline leg)."""
     import torch
 
     from paper_2107_04121_gb300 import autograd as fad

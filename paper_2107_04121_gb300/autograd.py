@@ -32,7 +32,9 @@ class ElasticityProblem:
         self.ctx, self.X, self.precision = ctx, X, precision
         self.conn = conn
         self.mesh = fe.Mesh(X, conn)
-        flags = fe.GEOM_STORE_F64 if precision == "f64" else fe.GEOM_STORE_F32
+        # float32: a deferred handle, whose geometry the first residual of each
+        # evaluation computes in the same kernel (fe_eval_residual)
+        flags = fe.GEOM_STORE_F64 if precision == "f64" else fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED
         self.geom = fe.hex_geometry(ctx, self.mesh, p, nq, flags=flags)
         self.form = fe.elasticity_form(fe.MAT_LAME)
         self.asm = fe.assembly_create(ctx, self.mesh)
@@ -73,6 +75,11 @@ class AssembledElasticityResidual(torch.autograd.Function):
         ud = u.detach().to(prob.dtype).contiguous()
         prob.geom.update()  # the geometry is recomputed, not kept from the forward
         dlam = dmu = dX = du = None
+        if need_u:
+            # first, so that (float32) this residual computes the geometry that the
+            # adjoint kernel then reads
+            r = fe.eval_residual(prob.ctx, prob.form, prob.geom, [mat, None, rbar], prob.precision)
+            du = prob._assemble(r).to(u.dtype)
         if need_mat or need_x:
             d_mat, d_xe = fe.eval_residual_adjoint(prob.ctx, prob.form, prob.geom, [mat, None, ud], rbar,
                                                    prob.precision, want_mat=need_mat, want_x=need_x)
@@ -81,9 +88,6 @@ class AssembledElasticityResidual(torch.autograd.Function):
                 dmu = d_mat[:, 1].to(mu.dtype)
             if need_x:
                 dX = prob._assemble(d_xe).view(-1, 3).to(prob.X.dtype)
-        if need_u:
-            r = fe.eval_residual(prob.ctx, prob.form, prob.geom, [mat, None, rbar], prob.precision)
-            du = prob._assemble(r).to(u.dtype)
         return dlam, dmu, dX, du, None
 
 
