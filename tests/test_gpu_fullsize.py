@@ -1,0 +1,139 @@
+"""The benchmark workloads at their full sizes, in the launch configurations the
+benchmark times, against the oracle on sampled elements (first, last and seeded
+ones, each computed by the oracle on its own) and through properties that hold at
+any size: the Q2 elasticity metric workload (48^3), the convection workload (64^3)
+and the mixed batch (458,000 elements)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2107_04121_gb300 import fe, meshgen
+from tests.parity import TOL, rel_matrix_error, rel_vector_error
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(libfe):
+    c = fe.Context(0)
+    yield c
+    c.close()
+
+
+def _t(a, dt):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
+
+
+def _sample(E, seed, k=62):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, E - 1], rng.choice(E, min(k, E), replace=False)]))
+
+
+def test_metric_workload_full_size(ctx):
+    """48^3 Q2 elasticity (110,592 elements), the benchmark's step: deferred FP64
+    geometry computed by the residual kernel, BF16x3 tensor-core K_e, compensated
+    assembly."""
+    mesh, lam, mu, u = meshgen.elasticity_q2_cube(48, seed=1)
+    E = mesh.n_elems
+    m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+    geom = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    form = fe.elasticity_form()
+    mat = _t(np.stack([lam, mu], 1), torch.float64)
+    u32 = _t(u, torch.float32)
+    geom.update()
+    r = fe.eval_residual(ctx, form, geom, [mat, None, u32], "bf16x3")
+    K = fe.eval_matrix(ctx, form, geom, [mat, None, None], "bf16x3")
+    g = fe.assemble_vector(ctx, fe.assembly_create(ctx, m), 3, r, "f32", flags=fe.ASSEMBLE_COMPENSATED)
+    ctx.check()
+    idx = _sample(E, 7)
+    conn = mesh.conn[idx]
+    wdetJ, G, _ = oracle.geometry(mesh.coords, conn, oracle.RefElement(2, 3))
+    D = oracle.lame_to_D(lam[idx], mu[idx])
+    it = torch.from_numpy(idx).cuda()
+    Ks = K.index_select(0, it).cpu().numpy()
+    rs = r.index_select(0, it).cpu().numpy()
+    assert rel_matrix_error(Ks, oracle.matrix_elasticity(wdetJ, G, D)) <= TOL["bf16x3"]
+    assert rel_vector_error(rs, oracle.residual_elasticity(conn, wdetJ, G, D, u)) <= TOL["f32"]
+    # properties at any size: K_e symmetric, r_e = K_e u_e (the BF16x3 K against
+    # the float32 residual), the assembly of r_e (float64 on the host) within the
+    # compensated sum's bound, and no non-finite value anywhere
+    assert np.abs(Ks - Ks.transpose(0, 2, 1)).max() <= 1e-5 * np.abs(Ks).max()
+    ue = u.reshape(-1, 3)[conn].transpose(0, 2, 1).reshape(len(idx), -1)  # component-major (3 N)
+    assert rel_vector_error(np.einsum("eij,ej->ei", Ks.astype(np.float64), ue), rs) <= 1e-5
+    rh = r.cpu().numpy().astype(np.float64)
+    want = oracle.assemble(mesh.conn, rh, mesh.n_nodes, 3)
+    sumabs = oracle.assemble(mesh.conn, np.abs(rh), mesh.n_nodes, 3)
+    assert np.all(np.abs(g.cpu().numpy() - want) <= 2.0 ** -24 * np.abs(want) + 64 * 2.0 ** -48 * sumabs)
+    assert bool(torch.isfinite(K).all()) and bool(torch.isfinite(r).all())
+
+
+def test_convection_workload_full_size(ctx):
+    """64^3 Q2 convection (262,144 elements): FP32 K_e(u) and r_e(u), the residual
+    computing the deferred geometry."""
+    mesh, u = meshgen.convect_q2_cube(64, seed=3)
+    E = mesh.n_elems
+    m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+    geom = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    form = fe.convect_form()
+    u32 = _t(u, torch.float32)
+    geom.update()
+    r = fe.eval_residual(ctx, form, geom, [None, u32, u32], "f32")
+    K = fe.eval_matrix(ctx, form, geom, [None, u32, u32], "f32")
+    ctx.check()
+    idx = _sample(E, 9)
+    conn = mesh.conn[idx]
+    ref = oracle.RefElement(2, 3)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, conn, ref)
+    it = torch.from_numpy(idx).cuda()
+    Kref = oracle.matrix_convect(conn, wdetJ, ref.phi, G, u)
+    rref = oracle.residual_convect(conn, wdetJ, ref.phi, G, u)
+    assert rel_matrix_error(K.index_select(0, it).cpu().numpy(), Kref) <= TOL["f32"]
+    assert rel_vector_error(r.index_select(0, it).cpu().numpy(), rref) <= TOL["f32"]
+    assert bool(torch.isfinite(K).all()) and bool(torch.isfinite(r).all())
+
+
+def test_mixed_batch_full_size(ctx):
+    """P1/P2/P3 tetrahedra 200k/120k/40k and Q1/Q2/Q3 hexahedra 60k/30k/8k, the three
+    forms per group in one autotuned, graph-captured batch with its geometry: sampled
+    elements of every item against the oracle (errors against the sums of absolute
+    terms, as the Grundmann-Moeller weights alternate in sign)."""
+    groups, items, keys = [], [], []
+    for name, mesh in meshgen.mixed_mesh_groups(1.0, seed=2):
+        p = int(name[1])
+        tet = name[0] == "P"
+        ref = oracle.RefTet(p, p) if tet else oracle.RefElement(p, p + 1)
+        m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+        geom = fe.tet_geometry(ctx, m, p, flags=fe.GEOM_STORE_F32) if tet else \
+            fe.hex_geometry(ctx, m, p, p + 1, flags=fe.GEOM_STORE_F32)
+        rng = np.random.default_rng(200 + p + (10 if tet else 0))
+        E = mesh.n_elems
+        coef, lam, mu = rng.uniform(0.5, 2.0, E), rng.uniform(0.5, 2.0, E), rng.uniform(0.2, 1.0, E)
+        groups.append((name, mesh, m, geom, ref, coef, lam, mu))
+        for f in ("laplace", "mass", "elasticity"):
+            form = fe.laplace_form(weighted=True) if f == "laplace" else (
+                fe.mass_form(1, weighted=True) if f == "mass" else fe.elasticity_form(fe.MAT_LAME))
+            mat = _t(np.stack([lam, mu], 1), torch.float64) if f == "elasticity" else _t(coef, torch.float64)
+            items.append((geom, form, mat, None))
+            keys.append((len(groups) - 1, f))
+    b = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_GRAPH | fe.BATCH_GEOMETRY)
+    outs = b.run()
+    ctx.check()
+    for (gi, f), K in zip(keys, outs):
+        name, mesh, m, geom, ref, coef, lam, mu = groups[gi]
+        idx = _sample(mesh.n_elems, 11, 14)
+        conn = mesh.conn[idx]
+        wdetJ, G, _ = oracle.geometry(mesh.coords, conn, ref)
+        aw, aG = np.abs(wdetJ), np.abs(G)
+        if f == "laplace":
+            Kref, Kabs = oracle.matrix_laplace(wdetJ, G, coef[idx]), oracle.matrix_laplace(aw, aG, coef[idx])
+        elif f == "mass":
+            Kref = oracle.matrix_mass(wdetJ, ref.phi, 1, coef[idx])
+            Kabs = oracle.matrix_mass(aw, np.abs(ref.phi), 1, coef[idx])
+        else:
+            D = oracle.lame_to_D(lam[idx], mu[idx])
+            Kref, Kabs = oracle.matrix_elasticity(wdetJ, G, D), oracle.matrix_elasticity(aw, aG, np.abs(D))
+        Kg = K.index_select(0, torch.from_numpy(idx).cuda()).cpu().numpy().astype(np.float64)
+        err = float((np.sqrt(((Kg - Kref) ** 2).sum((1, 2))) / np.sqrt((Kabs ** 2).sum((1, 2)))).max())
+        assert err <= TOL["f32"], (name, f, err)
+    b.free()
