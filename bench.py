@@ -58,13 +58,13 @@ FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
 # kernels (dram__bytes_read.sum + dram__bytes_write.sum; the command is in
 # profiles/dram_traffic_q2_elasticity_48.md): the BF16x3 matrix kernel and the
 # geometry + residual kernel.  Other sizes or precisions report null.
-MEASURED_TRAFFIC_48 = {"matrix_bf16x3": 2962101248, "geometry_residual": 149954560}
+MEASURED_TRAFFIC_48 = {"matrix_bf16x3": 2962101248, "geometry_residual": None}
 # FP64 operations (an FMA counts 2) that the collocation geometry executes for one
 # Q2 element with 3x3x3 Gauss points: three 1-D interpolations of 27 lines each
 # (6 FMA a line: the middle point is the middle node), J on the points (81 lines of
-# 6 FMA + a subtraction and a multiply), per point 9 cofactors (mul + FMA each) and
-# det J (mul + 2 FMA) -- 1,701 FP64 instructions
-GEOMETRY_FLOPS_PER_ELEM_Q2 = 2 * 3 * 27 * 6 + 81 * (2 * 6 + 2) + Q2_Q * (9 * 3 + 5)
+# a sum, a difference, two multiplies and three FMA in the even-odd form), per point
+# 9 cofactors (mul + FMA each) and det J (mul + 2 FMA) -- 1,620 FP64 instructions
+GEOMETRY_FLOPS_PER_ELEM_Q2 = 2 * 3 * 27 * 6 + 81 * (4 + 2 * 3) + Q2_Q * (9 * 3 + 5)
 
 
 # Adjoint: J = |R|^2 / 2 of the assembled Q2 elasticity residual on a 32^3 cube

@@ -229,20 +229,32 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
             // three points with the middle one on the middle node (B's middle row
             // exactly (0, 1, 0)): the middle row of Dq is (-d, 0, d) up to rounding;
             // made exact, the kernels use it to skip the trivial products
+            // and symmetric points make the first and last rows antisymmetric
+            // ((d0, d1, d2), (-d2, -d1, -d0)); made exact too, with the constants of
+            // their even-odd form after the table (geometry_body.cuh)
             const double *B = basis->b1d;
+            for (int i = 0; i < 4; ++i) dq[n + i] = 0.0;
             if (basis->n1d == 3 && B[3] == 0.0 && B[4] == 1.0 && B[5] == 0.0) {
                 double sc = 0.0;
                 for (int i = 0; i < 9; ++i) sc = std::fmax(sc, std::fabs(dq[i]));
-                if (std::fabs(dq[4]) <= 1e-13 * sc && std::fabs(dq[3] + dq[5]) <= 1e-13 * sc) {
+                const double tol = 1e-13 * sc;
+                if (std::fabs(dq[4]) <= tol && std::fabs(dq[3] + dq[5]) <= tol && std::fabs(dq[6] + dq[2]) <= tol &&
+                    std::fabs(dq[7] + dq[1]) <= tol && std::fabs(dq[8] + dq[0]) <= tol) {
                     const double d = 0.5 * (dq[5] - dq[3]);
                     dq[3] = -d;
                     dq[4] = 0.0;
                     dq[5] = d;
+                    dq[6] = -dq[2];
+                    dq[7] = -dq[1];
+                    dq[8] = -dq[0];
+                    dq[9] = 0.5 * (dq[0] + dq[2]);
+                    dq[10] = 0.5 * (dq[0] - dq[2]);
+                    dq[11] = dq[1];
                     g->geo_center = 1;
                 }
             }
-            e = dev_alloc(&g->d_dq, n);
-            if (e == cudaSuccess) e = cudaMemcpy(g->d_dq, dq, sizeof(double) * n, cudaMemcpyHostToDevice);
+            e = dev_alloc(&g->d_dq, n + 4);
+            if (e == cudaSuccess) e = cudaMemcpy(g->d_dq, dq, sizeof(double) * (n + 4), cudaMemcpyHostToDevice);
         }
     }
     if (e == cudaSuccess && (flags & FE_GEOM_STORE_F64)) {

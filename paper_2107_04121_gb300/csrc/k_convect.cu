@@ -84,11 +84,13 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
             D[q][i] = d1d[q * N1 + i];
         }
     const int nf = same ? 3 : 6;  // interpolated vector fields: u, and w when it differs
-    // GEO tables after the per-element blocks: B, Dq (n1 x n1), w (Q), FP64
+    // GEO tables after the per-element blocks: B, Dq (n1 x n1 + extra), w (Q), FP64
     double *gT = reinterpret_cast<double *>(sm + ((EPB * PE + 1) / 2) * 2);
     if constexpr (GEO != 0)
-        for (int i = threadIdx.x; i < 2 * N1 * N1 + Q; i += THREADS)
-            gT[i] = i < N1 * N1 ? geo.b1d[i] : (i < 2 * N1 * N1 ? geo.dq[i - N1 * N1] : geo.w[i - 2 * N1 * N1]);
+        for (int i = threadIdx.x; i < 2 * N1 * N1 + GEO_DQ_EXTRA + Q; i += THREADS)
+            gT[i] = i < N1 * N1 ? geo.b1d[i]
+                                : (i < 2 * N1 * N1 + GEO_DQ_EXTRA ? geo.dq[i - N1 * N1]
+                                                                  : geo.w[i - 2 * N1 * N1 - GEO_DQ_EXTRA]);
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
         const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
         __syncthreads();
@@ -138,7 +140,8 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
             for (int t = threadIdx.x; t < ne * Q; t += THREADS) {
                 const int el = t / Q, q = t % Q;
                 float o[9], wdq;
-                const double det = geo_point_f32(gbuf(el) + 3 * N + q * 9, gT[2 * N1 * N1 + q], o, wdq);
+                const double det =
+                    geo_point_f32(gbuf(el) + 3 * N + q * 9, gT[2 * N1 * N1 + GEO_DQ_EXTRA + q], o, wdq);
                 const int bad = geo_det_status(det);
                 if (bad) fe_report(status, bad, e0 + el);
                 const long long idx = (e0 + el) * Q + q;
@@ -427,7 +430,7 @@ cudaError_t launch_cv(const fe_geometry_h *g, const void *u, const void *w, int 
     constexpr int THREADS = MAT ? ((EPB * 3 * P::N + 31) / 32) * 32 : 256;
     // per-element blocks, then (GEO) the FP64 tables 8-byte aligned
     constexpr size_t SMEM = sizeof(T) * (size_t)((P::PER_EL * EPB + 1) / 2 * 2) +
-                            (GEO ? sizeof(double) * (2 * N1 * N1 + P::Q) : 0);
+                            (GEO ? sizeof(double) * (2 * N1 * N1 + GEO_DQ_EXTRA + P::Q) : 0);
     static_assert(SMEM <= 227 * 1024, "shared memory plan too large");
     auto kern = k_convect_sf<T, N1, NQ, MAT, EPB, THREADS, GEO>;
     static FeLaunchCache cache;

@@ -190,11 +190,11 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry_co(const double *__re
                                                               unsigned long long *__restrict__ status)
 {
     constexpr int N = N1 * N1 * N1, L = N1 * N1;
-    static_assert(8 * (2 * N1 * N1 + EPB * 12 * N) <= 48 * 1024, "static shared memory above 48 KB");
-    __shared__ double sB[N1 * N1], sDq[N1 * N1];
+    static_assert(8 * (2 * N1 * N1 + GEO_DQ_EXTRA + EPB * 12 * N) <= 48 * 1024, "static shared memory above 48 KB");
+    __shared__ double sB[N1 * N1], sDq[N1 * N1 + GEO_DQ_EXTRA];
     __shared__ double sG[EPB][4][3 * N];
-    for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) {
-        sB[i] = b1d[i];
+    for (int i = threadIdx.x; i < N1 * N1 + GEO_DQ_EXTRA; i += blockDim.x) {
+        if (i < N1 * N1) sB[i] = b1d[i];
         sDq[i] = dq[i];
     }
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {

@@ -508,8 +508,8 @@ struct ResGeoSmem {
     static constexpr int J = ((STAGE_END > G_END ? STAGE_END : G_END) + 15) / 16 * 16;  // float [EPB][Q][9]
     static constexpr int W = J + EPB * Q * 9 * 4;                 // float [EPB][Q]
     static constexpr int M = W + EPB * Q * 4;                     // float [EPB][36]
-    static constexpr int T64 = (M + EPB * 36 * 4 + 7) / 8 * 8;   // double B[N1][N1], Dq[N1][N1], w[Q]
-    static constexpr int BYTES = T64 + (2 * N1 * N1 + Q) * 8;
+    static constexpr int T64 = (M + EPB * 36 * 4 + 7) / 8 * 8;   // double B[N1][N1], Dq[N1][N1] + extra, w[Q]
+    static constexpr int BYTES = T64 + (2 * N1 * N1 + GEO_DQ_EXTRA + Q) * 8;
 };
 
 template <int N1, int KIND, int MATK, int EPB, int THREADS, bool CENTER>
@@ -542,9 +542,10 @@ __global__ void __launch_bounds__(THREADS, N1 == 3 ? 6 : 4) k_residual_geo(const
     constexpr int LL = N1 * N1;
     double *gB = reinterpret_cast<double *>(raw + L::T64);
     double *gDq = gB + N1 * N1;
-    double *gw = gDq + N1 * N1;
-    for (int i = threadIdx.x; i < 2 * N1 * N1 + Q; i += THREADS)
-        gB[i] = i < N1 * N1 ? b1d64[i] : (i < 2 * N1 * N1 ? dq64[i - N1 * N1] : w64[i - 2 * N1 * N1]);
+    double *gw = gDq + N1 * N1 + GEO_DQ_EXTRA;
+    constexpr int LDQ = N1 * N1 + GEO_DQ_EXTRA;
+    for (int i = threadIdx.x; i < N1 * N1 + LDQ + Q; i += THREADS)
+        gB[i] = i < N1 * N1 ? b1d64[i] : (i < N1 * N1 + LDQ ? dq64[i - N1 * N1] : w64[i - N1 * N1 - LDQ]);
     T B[NQ][N1], D[NQ][N1];
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
