@@ -826,6 +826,13 @@ def cpu_info():
     return model
 
 
+def workload_description(n, E):
+    """The metric's workload, as both arms name it in their `config`."""
+    return ("Q2 linear elasticity, %d^3 = %d hexes (27 nodes, 27 Gauss points), +-0.15h interior "
+            "perturbation seed 1, per-element Lame lambda~U[0.5,2], mu~U[0.2,1], u~N(0,1); step = FP64 "
+            "geometry + r_e + K_e (81x81) + assembly" % (n, E))
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
@@ -848,8 +855,8 @@ def run_reference(args, ws, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "Q2 linear elasticity, %d^3 hexes, K_e (81x81) + r_e + assembly" % args.n,
-                       "sample_elements": sample},
+            "config": {"workload": workload_description(args.n, mesh.n_elems), "elements": mesh.n_elems,
+                       "geometry_dtype": "f64", "contraction": "f64 (oracle)", "sample_elements": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -920,10 +927,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if prec != "f64" else "f64", "data": "synthetic",
-        "config": {"workload": "Q2 linear elasticity, %d^3 = %d hexes (27 nodes, 27 Gauss points), "
-                               "+-0.15h interior perturbation seed 1, per-element Lame lambda~U[0.5,2], "
-                               "mu~U[0.2,1], u~N(0,1); step = FP64 geometry (computed by the residual "
-                               "kernel) + r_e + K_e (81x81) + compensated assembly" % (args.n, wl.E),
+        "config": {"workload": workload_description(args.n, wl.E),
                    "elements": wl.E, "geometry_dtype": "f64", "contraction": prec,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
         "roofline": {"kernel": "k_matrix (fe_eval_matrix, %s)" % prec, "bound": "hbm", "achieved": achieved,
