@@ -98,15 +98,21 @@ def parse_args():
 
 # ---- distributed plumbing (replicas: every rank evaluates its own mesh) -------------
 
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """One process per GPU from torchrun's environment: NCCL on GPUs (gloo where there
+    is none, e.g. the multi-process tests on the host)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        backend = backend or ("nccl" if torch.cuda.is_available() else "gloo")
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        else:
+            dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -117,13 +123,23 @@ def barrier(ws):
 
 
 def max_over_ranks(x, ws):
+    """The maximum of x over the ranks (the job's time is its slowest rank's)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(step_ms, units_per_step, steps, ws):
+    """Whole-job throughput of replicas: every rank processes units_per_step per step,
+    the job takes as long as its slowest rank (max over ranks of the summed step times).
+    Returns (units per second, ms per step)."""
+    total_ms = max_over_ranks(sum(step_ms), ws)
+    return ws * units_per_step * steps / (total_ms / 1e3), total_ms / steps
 
 
 # ---- clocks --------------------------------------------------------------------------
@@ -917,9 +933,7 @@ def main():
             prec = DEFAULT_MIXED  # no oracle sample on this rank: the precision the N = 1 run selects
     with ClockSampler(local) as clk:
         step_ms, mat_ms, parts = timed_steps(wl, prec, args.steps, args.warmup, ws, flush)
-    total_ms = max_over_ranks(sum(step_ms), ws)
-    ms_per_step = total_ms / args.steps
-    value = ws * wl.E * args.steps / (total_ms / 1e3)
+    value, ms_per_step = job_rate(step_ms, wl.E, args.steps, ws)
     mat_avg = sum(mat_ms) / len(mat_ms)
     bytes_alg = wl.E * (MATRIX_BYTES_PER_ELEM_F64 if prec == "f64" else MATRIX_BYTES_PER_ELEM_F32)
     achieved = bytes_alg / (mat_avg / 1e3) / 1e9
