@@ -17,12 +17,13 @@
 // is kept.  Registers and shared memory are allocated per kernel, so one kernel
 // holding every variant would run all of them at the occupancy of the heaviest
 // (Q2 elasticity with 3x3 tiles: 128 registers).  The variants are therefore
-// split in two classes, each with its own persistent kernel: "light" (at most
-// 85 registers and 75 KB of shared memory: 3 CTAs per SM) and "heavy" (2 CTAs
-// per SM); the two run concurrently on two streams.  A plan can be captured in
-// a CUDA graph together with the geometry of every group (FP64 J, det J, J^-1),
-// so that one graph launch evaluates the whole batch.  FP32 element matrices
-// from FP64 geometry.
+// split in three classes, each with its own persistent kernel: "light" (at most
+// 80 registers and 75 KB of shared memory: 3 CTAs per SM), "heavy" (2 CTAs per
+// SM) and the 4x4-tile Q3 elasticity variant (1 CTA per SM); the three run
+// concurrently on three streams (measured faster than one after another).  A
+// plan can be captured in a CUDA graph together with the geometry of every
+// group (FP64 J, det J, J^-1), so that one graph launch evaluates the whole
+// batch.  FP32 element matrices from FP64 geometry.
 #include <cstdio>
 #include <cstring>
 #include <new>
