@@ -94,7 +94,11 @@ typedef struct {
 
 /* Mesh: device arrays, caller-owned, valid for as long as any handle made from
  * them is used.  coords (n_nodes, 3) float64; conn (n_elems, nodes_per_elem)
- * int32 indices into coords. */
+ * int32 indices into coords.  Node indices and the (element, local node)
+ * incidences are 32-bit: every call that takes a mesh returns
+ * FE_ERR_INVALID_ARG, before any launch, when n_nodes or n_elems *
+ * nodes_per_elem exceeds 2^31 - 1.  Element outputs (K, r) are indexed with
+ * 64 bits and may hold more than 2^31 entries. */
 typedef struct {
     const double *coords;
     long long n_nodes;

@@ -137,3 +137,52 @@ def test_mixed_batch_full_size(ctx):
         err = float((np.sqrt(((Kg - Kref) ** 2).sum((1, 2))) / np.sqrt((Kabs ** 2).sum((1, 2)))).max())
         assert err <= TOL["f32"], (name, f, err)
     b.free()
+
+
+def test_element_matrices_past_2_31_entries(ctx):
+    """70^3 Q2 elasticity (343,000 elements): K holds 2.25e9 entries; element
+    327,310 straddles entry 2^31 and the later ones start past it (byte 2^33 in
+    float32, 2^34 in FP64);
+    the benchmark's step (deferred geometry, BF16x3 tensor-core K_e, compensated
+    assembly), the float32 CUDA-core and the FP64 matrix kernels, sampled on both
+    sides of that boundary against the oracle."""
+    mesh, lam, mu, u = meshgen.elasticity_q2_cube(70, seed=5)
+    E = mesh.n_elems
+    first_past = -(-(2 ** 31) // (81 * 81))  # first element starting past entry 2^31
+    assert E * 81 * 81 > 2 ** 31 and first_past < E
+    rng = np.random.default_rng(13)
+    idx = np.unique(np.concatenate([[0, first_past - 2, first_past - 1, first_past, E - 1],
+                                    rng.integers(first_past, E, 24)]))
+    m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+    form = fe.elasticity_form()
+    mat = _t(np.stack([lam, mu], 1), torch.float64)
+    u32 = _t(u, torch.float32)
+    conn = mesh.conn[idx]
+    wdetJ, G, _ = oracle.geometry(mesh.coords, conn, oracle.RefElement(2, 3))
+    D = oracle.lame_to_D(lam[idx], mu[idx])
+    Kref = oracle.matrix_elasticity(wdetJ, G, D)
+    it = torch.from_numpy(idx).cuda()
+
+    gd = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    gd.update()
+    r = fe.eval_residual(ctx, form, gd, [mat, None, u32], "bf16x3")
+    K = fe.eval_matrix(ctx, form, gd, [mat, None, None], "bf16x3")
+    g = fe.assemble_vector(ctx, fe.assembly_create(ctx, m), 3, r, "f32", flags=fe.ASSEMBLE_COMPENSATED)
+    ctx.check()
+    assert rel_matrix_error(K.index_select(0, it).cpu().numpy(), Kref) <= TOL["bf16x3"]
+    assert rel_vector_error(r.index_select(0, it).cpu().numpy(),
+                            oracle.residual_elasticity(conn, wdetJ, G, D, u)) <= TOL["f32"]
+    rh = r.cpu().numpy().astype(np.float64)
+    want = oracle.assemble(mesh.conn, rh, mesh.n_nodes, 3)
+    sumabs = oracle.assemble(mesh.conn, np.abs(rh), mesh.n_nodes, 3)
+    assert np.all(np.abs(g.cpu().numpy() - want) <= 2.0 ** -24 * np.abs(want) + 64 * 2.0 ** -48 * sumabs)
+    del r, g, gd
+
+    gs = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F64 | fe.GEOM_STORE_F32)
+    fe.eval_matrix(ctx, form, gs, [mat, None, None], "f32", out=K)
+    ctx.check()
+    assert rel_matrix_error(K.index_select(0, it).cpu().numpy(), Kref) <= TOL["f32"]
+    del K
+    K64 = fe.eval_matrix(ctx, form, gs, [mat, None, None], "f64")
+    ctx.check()
+    assert rel_matrix_error(K64.index_select(0, it).cpu().numpy(), Kref) <= TOL["f64"]

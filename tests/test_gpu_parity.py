@@ -88,6 +88,27 @@ def test_float32_rounding_of_the_geometry_matches_ieee(ctx):
     assert np.all(np.isnan(nan))
 
 
+def test_meshes_past_the_32_bit_index_range_are_rejected(ctx):
+    """Node indices and the (element, local node) incidences of the assembly lists
+    are 32-bit: a mesh whose node count or n_elems * N exceeds 2^31 - 1 is rejected
+    on the host before any launch (here the descriptor overstates its sizes, and
+    nothing past the real arrays is read); the same descriptor with its true
+    sizes is accepted."""
+    mesh = meshgen.structured_hex(1, 1, 1, 2, 0.0, 0)
+    m = fe.Mesh(torch.from_numpy(mesh.coords).cuda(), torch.from_numpy(mesh.conn).cuda())
+    for field, value in (("n_elems", (2 ** 31 - 1) // 27 + 1), ("n_nodes", 2 ** 31)):
+        saved = getattr(m.struct, field)
+        setattr(m.struct, field, value)
+        for call in (lambda: fe.assembly_create(ctx, m), lambda: fe.hex_geometry(ctx, m, 2, 3)):
+            with pytest.raises(fe.FEError) as ei:
+                call()
+            assert ei.value.status == fe.FE_ERR_INVALID_ARG
+        setattr(m.struct, field, saved)
+    fe.hex_geometry(ctx, m, 2, 3)
+    fe.assembly_create(ctx, m)
+    ctx.check()
+
+
 def test_inconsistent_tensor_factors_are_rejected(ctx):
     mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
     P = Problem(ctx, mesh, 2, 3)
