@@ -274,6 +274,27 @@ def test_tensor_core_elasticity_matches_oracle(ctx, prec, tol):
     assert np.abs(Kh - Kh.transpose(0, 2, 1)).max() <= 10 * tol * np.abs(Kh).max()
 
 
+@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4), ("bf16", 2e-2)])
+def test_tensor_core_pipeline_many_elements_per_cta(ctx, prec, tol):
+    """2,352 elements: every persistent CTA of the tensor-core kernel runs 5 or 6
+    elements through its two operand buffers and its accumulator (buffer reuse,
+    accumulator hand-back, ragged split over the CTAs).  Every element against the
+    oracle, in the benchmark's step: deferred geometry computed by the residual
+    kernel, then K_e."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (14, 14, 12), 83)
+    E = P.mesh.n_elems
+    assert E == 2352 and E > 5 * 152 * 3
+    geom = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    args = [_t(mat, torch.float64), None, _t(u, torch.float32)]
+    geom.update()
+    r = fe.eval_residual(ctx, form, geom, args, prec)
+    K = fe.eval_matrix(ctx, form, geom, args, prec)
+    ctx.check()
+    err = rel_matrix_error(K.cpu().numpy(), Kref)
+    assert err <= tol, err
+    assert rel_vector_error(r.cpu().numpy(), rref) <= TOL["f32"]
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16"])
 def test_deferred_geometry_matches_eager(ctx, prec):
     """A deferred float32-only geometry is computed by the first call that reads it;
