@@ -626,9 +626,10 @@ def mixed_setup(scale, device):
 
 def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
     """The mixed-mesh batch: one CUDA-graph launch = FP64 geometry of the six
-    groups + the persistent matrix kernel over all 18 (group, form) items,
-    autotuned; beside it the same work as separate per-item launches, and the
-    persistent kernel alone against the HBM roofline."""
+    groups + the matrices of all 18 (group, form) items under the autotuned
+    schedule (persistent class kernels or one launch per item); beside it each
+    schedule's matrix launches alone, the same work as separate per-item calls
+    from Python, and the chosen schedule's matrices against the HBM roofline."""
     import torch
 
     from paper_2107_04121_gb300 import fe
@@ -637,7 +638,9 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
     t0 = time.perf_counter()
     batch = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_GRAPH | fe.BATCH_GEOMETRY)
     plan_s = time.perf_counter() - t0
-    mats_only = fe.Batch(ctx, [(g, f, m, K) for (g, f, m, _), K in zip(items, batch.outputs)], fe.BATCH_AUTOTUNE)
+    same_out = [(g, f, m, K) for (g, f, m, _), K in zip(items, batch.outputs)]
+    mats_p = fe.Batch(ctx, same_out, fe.BATCH_AUTOTUNE | fe.BATCH_PERSISTENT)
+    mats_l = fe.Batch(ctx, same_out, fe.BATCH_LAUNCHES)
 
     def timed(fn):
         for _ in range(warmup):
@@ -661,12 +664,15 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
             fe.eval_matrix(ctx, f, g, [m, None, None], "f32", out=K)
 
     ms_graph = timed(batch.run)
-    ms_kernel = timed(mats_only.run)
+    ms_persistent = timed(mats_p.run)
+    ms_launches = timed(mats_l.run)
     ms_sep = timed(separate)
+    schedule = batch.schedule()
+    ms_kernel = ms_launches if schedule == "launches" else ms_persistent
     ctx.check()
     n_el = sum(g["mesh"].n_elems for g in groups)
-    # algorithmic bytes of the persistent kernel: per item and element, J^-1 and
-    # w det J (FP32, Q x 10 values), the material (8 or 16 B) and the K_e write
+    # algorithmic bytes of the matrices: per item and element, J^-1 and w det J
+    # (FP32, Q x 10 values), the material (8 or 16 B) and the K_e write
     kbytes = 0
     for (g, f, m, _), K in zip(items, batch.outputs):
         E = K.shape[0]
@@ -677,8 +683,10 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
                            "/".join(str(g["mesh"].n_elems) for g in groups[3:])),
            "elements": n_el, "items": len(items), "plan_seconds": plan_s,
            "graph_ms": ms_graph, "value": n_el / (ms_graph / 1e3), "unit": UNIT + " (all 3 forms per element)",
-           "persistent_kernel_ms": ms_kernel, "separate_launches_ms": ms_sep,
-           "roofline": {"kernel": "k_batch (persistent, 18 items)", "bound": "hbm",
+           "schedule": schedule, "persistent_kernels_ms": ms_persistent, "per_item_launches_ms": ms_launches,
+           "separate_calls_ms": ms_sep,
+           "roofline": {"kernel": ("k_matrix_sym, one launch per item on 3 streams" if schedule == "launches"
+                                   else "k_batch, persistent class kernels") + " (18 items)", "bound": "hbm",
                         "achieved": kbytes / (ms_kernel / 1e3) / 1e9, "unit": "GB/s", "bytes": kbytes},
            "configs": {"%s/%s" % (items_g["name"], f): batch.describe(k)
                        for k, (items_g, f) in enumerate((g, f) for g in groups for f in MIXED_FORMS)}}
@@ -694,7 +702,8 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
                 errs["%s/%s" % (g["name"], f)] = e
         out["rel_err_vs_abs_terms"] = errs
     batch.free()
-    mats_only.free()
+    mats_p.free()
+    mats_l.free()
     ctx.close()
     return out
 

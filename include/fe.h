@@ -373,20 +373,32 @@ typedef struct {
     void *K_out;
 } fe_batch_item;
 
-#define FE_BATCH_GEOMETRY 1u /* every run recomputes the geometry of each item's handle first */
-#define FE_BATCH_AUTOTUNE 2u /* time every candidate configuration at creation, keep the fastest */
-#define FE_BATCH_GRAPH 4u    /* capture the run (geometry and matrices) in a CUDA graph at creation */
+#define FE_BATCH_GEOMETRY 1u   /* every run recomputes the geometry of each item's handle first */
+#define FE_BATCH_AUTOTUNE 2u   /* time every candidate configuration at creation, keep the fastest */
+#define FE_BATCH_GRAPH 4u      /* capture the run (geometry and matrices) in a CUDA graph at creation */
+#define FE_BATCH_PERSISTENT 8u /* schedule: the persistent class kernels (the default without AUTOTUNE) */
+#define FE_BATCH_LAUNCHES 16u  /* schedule: one launch per item of the kernel fe_eval_matrix uses */
 
 /* A batch evaluates matrix mode (Algorithm 2) for many items, e.g. the groups
  * of a mixed mesh of P1-P3 tetrahedra and Q1-Q3 hexahedra with the Laplace,
- * mass and elasticity forms, in persistent kernels: the items' elements are
- * cut into chunks and resident CTAs stride over a work list.  One persistent
- * kernel per register class of the chosen configurations (at most three:
- * light, heavy, and 4x4-tile Q3 elasticity, 3, 2 and 1 CTAs per SM), the
- * classes running concurrently on forked streams.  Every (element, form) pair has candidate configurations (node
- * tile, elements per chunk, output staging); FE_BATCH_AUTOTUNE times each on
- * the item's own elements (writing its K_out) and keeps the fastest, otherwise
- * the first is used.  FE_F32 arithmetic from the FP32 copy of the FP64
+ * mass and elasticity forms, under one of two schedules:
+ * - persistent: the items' elements are cut into chunks and resident CTAs
+ *   stride over a work list, one persistent kernel per register class of the
+ *   chosen configurations (at most three: light, heavy, and 4x4-tile Q3
+ *   elasticity, 3, 2 and 1 CTAs per SM), the classes running concurrently on
+ *   forked streams.  Every (element, form) pair has candidate configurations
+ *   (node tile, elements per chunk, output staging); FE_BATCH_AUTOTUNE times
+ *   each on the item's own elements (writing its K_out) and keeps the fastest,
+ *   otherwise the first is used;
+ * - launches: one launch per item of the kernel that fe_eval_matrix runs for
+ *   it (compiled, and occupied, for that item alone), the items spread over the
+ *   caller's stream and two forked streams, largest first, each to the least
+ *   loaded stream.
+ * FE_BATCH_PERSISTENT or FE_BATCH_LAUNCHES fixes the schedule (not both); with
+ * neither, FE_BATCH_AUTOTUNE times both schedules' matrix launches at creation
+ * and keeps the faster, and without it the persistent schedule is used.  Both
+ * schedules compute every entry with the same sums, in an order that may
+ * differ in the last float32 bits.  FE_F32 arithmetic from the FP32 copy of the FP64
  * geometry, so every geometry must store FE_GEOM_STORE_F32.  Supported: the
  * weighted Laplacian, the (vector) mass and Lame elasticity on the (N, Q)
  * pairs of fe_geometry.  The paper has no batched evaluator (it evaluates one
@@ -397,11 +409,15 @@ typedef struct {
 fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, unsigned flags, fe_batch_h **out,
                           fe_stream_t stream);
 /* Run the batch on `stream` (one graph launch with FE_BATCH_GRAPH, otherwise
- * the geometry launches and one persistent kernel launch). */
+ * the geometry launches and the matrix launches of the schedule). */
 fe_status fe_batch_run(fe_ctx *ctx, fe_batch_h *batch, fe_stream_t stream);
-/* The configuration chosen for item `item`: node tile, elements per chunk,
- * staging (1: bulk-copied row blocks, 0: direct stores); any may be NULL. */
+/* The persistent-schedule configuration of item `item`: node tile, elements
+ * per chunk, staging (1: bulk-copied row blocks, 0: direct stores); any may be
+ * NULL.  Under the launches schedule the item runs fe_eval_matrix's kernel. */
 fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *elems_per_chunk, int *staging);
+/* The schedule of a batch: *per_item_launches = 1 for one launch per item,
+ * 0 for the persistent class kernels.  Errors: FE_ERR_INVALID_ARG (NULL). */
+fe_status fe_batch_schedule(const fe_batch_h *batch, int *per_item_launches);
 fe_status fe_batch_free(fe_batch_h *batch);
 
 /* ---- assembly ------------------------------------------------------------------- */

@@ -9,8 +9,6 @@
 
 #include "fe_internal.h"
 
-cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
-                                  void *K, int sm_count, cudaStream_t s);
 cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
                                 void *K, int sm_count, unsigned long long *status, const int *hold, cudaStream_t s);
 

@@ -90,6 +90,9 @@ struct fe_material_args {
 // Launchers (return cudaError_t of the launch; argument checks done by the API).
 cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *d_status, cudaStream_t s);
 cudaError_t fe_launch_geometry_G(const fe_geometry_h *g, bool f64, void *out, cudaStream_t s);
+// Matrix mode on the CUDA cores (FP32 or FP64) for the (N, Q) pairs of fe_supported_nq.
+cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
+                                  void *K, int sm_count, cudaStream_t s);
 cudaError_t fe_launch_matrix(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
                              void *K, int sm_count, cudaStream_t s);
 cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,

@@ -24,6 +24,13 @@
 // plan can be captured in a CUDA graph together with the geometry of every
 // group (FP64 J, det J, J^-1), so that one graph launch evaluates the whole
 // batch.  FP32 element matrices from FP64 geometry.
+//
+// A second schedule launches, per item, the standalone kernel of
+// fe_eval_matrix (each compiled for its item alone, so each runs at its own
+// occupancy), the items spread over the caller's stream and the two side
+// streams by longest-processing-time-first assignment.  Autotuning times both
+// schedules and keeps the faster; either one can be captured in the graph.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -213,20 +220,23 @@ struct fe_batch_h {
     cudaStream_t capture_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    // per-item schedule: fe_eval_matrix's kernel for every item on its lane
+    // (0: the caller's stream, 1 and 2: the side streams)
+    int launches = 0;
+    int sm_count = 0;
+    std::vector<const fe_form_h *> forms;
+    std::vector<const fe_geometry_h *> igeom;
+    std::vector<fe_material_args> mats;
+    std::vector<int> lane;
 };
 
 namespace {
 
-cudaError_t enqueue(fe_batch_h *b, cudaStream_t s)
+// Matrices, persistent schedule: class 0 on the caller's stream, classes 1
+// and 2 forked onto the side streams.
+cudaError_t enqueue_persistent(fe_batch_h *b, cudaStream_t s)
 {
     cudaError_t e = cudaSuccess;
-    if (b->flags & FE_BATCH_GEOMETRY)
-        for (fe_geometry_h *g : b->geoms) {
-            g->pending = 0;
-            e = fe_launch_geometry(g, b->d_status, s);
-            if (e != cudaSuccess) return e;
-        }
-    // class 0 on the caller's stream, classes 1 and 2 forked onto side streams
     int used = 0;
     for (int c = 1; c < kClasses; ++c) used += b->chunks[c] > 0;
     if (used > 0) {
@@ -246,6 +256,67 @@ cudaError_t enqueue(fe_batch_h *b, cudaStream_t s)
         e = cudaEventRecord(b->join[c - 1], b->side[c - 1]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[c - 1], 0);
     }
+    return e;
+}
+
+// Matrices, per-item schedule: each item's fe_eval_matrix kernel on its lane.
+cudaError_t enqueue_items(fe_batch_h *b, cudaStream_t s)
+{
+    cudaError_t e = cudaEventRecord(b->fork, s);
+    for (int c = 0; c < kClasses - 1 && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(b->side[c], b->fork, 0);
+    for (int i = 0; i < b->n_items && e == cudaSuccess; ++i) {
+        if (b->items[i].E == 0) continue;
+        const int l = b->lane[i];
+        e = fe_launch_matrix_simt(b->igeom[i], b->forms[i], b->mats[i], false, b->items[i].K, b->sm_count,
+                                  l == 0 ? s : b->side[l - 1]);
+    }
+    for (int c = 0; c < kClasses - 1 && e == cudaSuccess; ++c) {
+        e = cudaEventRecord(b->join[c], b->side[c]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[c], 0);
+    }
+    return e;
+}
+
+cudaError_t enqueue_matrices(fe_batch_h *b, cudaStream_t s)
+{
+    return b->launches ? enqueue_items(b, s) : enqueue_persistent(b, s);
+}
+
+cudaError_t enqueue(fe_batch_h *b, cudaStream_t s)
+{
+    if (b->flags & FE_BATCH_GEOMETRY)
+        for (fe_geometry_h *g : b->geoms) {
+            g->pending = 0;
+            const cudaError_t e = fe_launch_geometry(g, b->d_status, s);
+            if (e != cudaSuccess) return e;
+        }
+    return enqueue_matrices(b, s);
+}
+
+// Median of three timed runs (after one warm-up) of the batch's matrix launches
+// under its current schedule.
+cudaError_t time_schedule(fe_batch_h *b, cudaStream_t s, float *ms)
+{
+    cudaEvent_t a, z;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&z);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    float t[3] = {0.f, 0.f, 0.f};
+    for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(a, s);
+        if (e == cudaSuccess) e = enqueue_matrices(b, s);
+        if (e == cudaSuccess) e = cudaEventRecord(z, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(z);
+        if (e == cudaSuccess && r > 0) e = cudaEventElapsedTime(&t[r - 1], a, z);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    std::sort(t, t + 3);
+    *ms = t[1];
     return e;
 }
 
@@ -326,7 +397,10 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
 {
     fe_clear_last_error();
     if (!ctx || !out || n_items < 1 || !items) return FE_ERR_INVALID_ARG;
-    if (flags & ~(FE_BATCH_GEOMETRY | FE_BATCH_AUTOTUNE | FE_BATCH_GRAPH)) return FE_ERR_INVALID_ARG;
+    if (flags & ~(FE_BATCH_GEOMETRY | FE_BATCH_AUTOTUNE | FE_BATCH_GRAPH | FE_BATCH_PERSISTENT | FE_BATCH_LAUNCHES))
+        return FE_ERR_INVALID_ARG;
+    const bool force_persistent = flags & FE_BATCH_PERSISTENT, force_launches = flags & FE_BATCH_LAUNCHES;
+    if (force_persistent && force_launches) return FE_ERR_INVALID_ARG;
     *out = nullptr;
     cudaSetDevice(ctx->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -336,6 +410,8 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
     b->n_items = n_items;
     b->flags = flags;
     b->d_status = ctx->d_status;
+    b->sm_count = ctx->sm_count;
+    b->launches = force_launches ? 1 : 0;
     // validate and describe the items
     std::vector<std::vector<int>> cand(n_items);
     for (int i = 0; i < n_items; ++i) {
@@ -372,6 +448,13 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         it.ncomp = f->ncomp;
         it.mat_t = f->mat_transposed;
         b->items.push_back(it);
+        b->forms.push_back(f);
+        b->igeom.push_back(g);
+        fe_material_args ma{};
+        ma.kind = f->mat_op >= 0 ? f->mat : FE_MAT_NONE;
+        ma.data = f->mat_op >= 0 ? (const double *)x.material : nullptr;
+        ma.transposed = f->mat_op >= 0 ? f->mat_transposed : 0;
+        b->mats.push_back(ma);
         fe_geometry_h *gm = const_cast<fe_geometry_h *>(g);
         bool seen = false;
         for (fe_geometry_h *h : b->geoms) seen = seen || h == gm;
@@ -388,7 +471,7 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         if (e == cudaSuccess) e = fe_settle_geometry(g, ctx->d_status, s);
     // autotune: time every candidate on each item alone; items of the same
     // (element, form, components) share the result
-    if (e == cudaSuccess && (flags & FE_BATCH_AUTOTUNE)) {
+    if (e == cudaSuccess && (flags & FE_BATCH_AUTOTUNE) && !force_launches) {
         struct Key {
             int N, Q, kind, ncomp, variant;
         };
@@ -440,6 +523,37 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         e = cudaMemcpyAsync(b->d_items, dev.data(), sizeof(BatchItemDev) * (size_t)n_items, cudaMemcpyHostToDevice, s);
     for (int cls = 0; cls < kClasses && e == cudaSuccess; ++cls)
         if (b->chunks[cls] > 0) e = class_grid(cls, b->smem[cls] > 0 ? b->smem[cls] : 1024, &b->grid[cls]);
+    // lanes of the per-item schedule: largest first, each to the least loaded
+    // stream (work ~ bytes of K written + float32 geometry read)
+    {
+        std::vector<int> order(n_items);
+        std::vector<double> cost(n_items);
+        for (int i = 0; i < n_items; ++i) {
+            const fe_geometry_h *g = b->igeom[i];
+            const double n = (double)b->forms[i]->ncomp * g->N;
+            cost[i] = (double)b->items[i].E * (4.0 * n * n + 40.0 * g->Q);
+            order[i] = i;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+        double load[kClasses] = {0.0, 0.0, 0.0};
+        b->lane.assign(n_items, 0);
+        for (int i : order) {
+            int l = 0;
+            for (int c = 1; c < kClasses; ++c)
+                if (load[c] < load[l]) l = c;
+            b->lane[i] = l;
+            load[l] += cost[i];
+        }
+    }
+    // schedule: fixed by a flag, else timed when autotuning (matrix launches only)
+    if (e == cudaSuccess && !force_persistent && !force_launches && (flags & FE_BATCH_AUTOTUNE)) {
+        float t[2] = {0.f, 0.f};
+        for (int mode = 0; mode < 2 && e == cudaSuccess; ++mode) {
+            b->launches = mode;
+            e = time_schedule(b, s, &t[mode]);
+        }
+        b->launches = t[1] < t[0] ? 1 : 0;
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     // CUDA graph of the whole batch, captured on a private stream
     if (e == cudaSuccess && (flags & FE_BATCH_GRAPH)) {
@@ -491,6 +605,14 @@ fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *e
     if (tile) *tile = v.tile;
     if (elems_per_chunk) *elems_per_chunk = v.epb;
     if (staging) *staging = v.stage == STAGE_BULK ? 1 : 0;
+    return FE_OK;
+}
+
+fe_status fe_batch_schedule(const fe_batch_h *batch, int *per_item_launches)
+{
+    fe_clear_last_error();
+    if (!batch || !per_item_launches) return FE_ERR_INVALID_ARG;
+    *per_item_launches = batch->launches;
     return FE_OK;
 }
 

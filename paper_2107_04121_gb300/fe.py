@@ -28,7 +28,7 @@ MAT_NONE, MAT_SCALAR, MAT_LAME, MAT_D66, MAT_M33 = 0, 1, 2, 3, 4
 GEOM_STORE_F64, GEOM_STORE_F32, GEOM_DEFERRED = 1, 2, 4
 GEOM_WDETJ, GEOM_JINV, GEOM_G = 0, 1, 2
 ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
-BATCH_GEOMETRY, BATCH_AUTOTUNE, BATCH_GRAPH = 1, 2, 4
+BATCH_GEOMETRY, BATCH_AUTOTUNE, BATCH_GRAPH, BATCH_PERSISTENT, BATCH_LAUNCHES = 1, 2, 4, 8, 16
 
 EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
@@ -38,7 +38,7 @@ EXPORTED = [
     "fe_assembly_create",
     "fe_assembly_free",
     "fe_assemble_vector", "fe_assemble_vector_noalloc", "fe_batch_create", "fe_batch_run", "fe_batch_describe",
-    "fe_batch_free", "fe_round_f32", "fe_debug_hold_next_matrix",
+    "fe_batch_schedule", "fe_batch_free", "fe_round_f32", "fe_debug_hold_next_matrix",
 ]
 
 
@@ -115,6 +115,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_batch_create.argtypes = [vp, ctypes.POINTER(_BatchItem), i, ctypes.c_uint, ctypes.POINTER(vp), vp]
     L.fe_batch_run.argtypes = [vp, vp, vp]
     L.fe_batch_describe.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.fe_batch_schedule.argtypes = [vp, ctypes.POINTER(i)]
     L.fe_batch_free.argtypes = [vp]
     L.fe_assembly_create.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(vp), vp]
     L.fe_assembly_free.argtypes = [vp]
@@ -474,8 +475,10 @@ def eval_residual_adjoint(ctx: Context, form: Form, geom: Geometry, args, rbar, 
 
 class Batch:
     """fe_batch_create / fe_batch_run: element matrices of many (geometry, form)
-    items in one persistent launch.  items: list of (geometry, form, material
-    tensor or None, K_out tensor or None); the tensors are kept alive here."""
+    items, by persistent class kernels or one launch per item (BATCH_PERSISTENT,
+    BATCH_LAUNCHES, or timed with BATCH_AUTOTUNE).  items: list of (geometry,
+    form, material tensor or None, K_out tensor or None); the tensors are kept
+    alive here."""
 
     def __init__(self, ctx: Context, items, flags: int = 0, stream=None):
         import torch
@@ -508,6 +511,12 @@ class Batch:
         _check(_lib.fe_batch_describe(self._h, item, ctypes.byref(t), ctypes.byref(e), ctypes.byref(s)),
                "fe_batch_describe")
         return {"tile": t.value, "elems_per_chunk": e.value, "staging": "bulk" if s.value else "direct"}
+
+    def schedule(self) -> str:
+        """'launches' (one kernel launch per item) or 'persistent' (the class kernels)."""
+        v = ctypes.c_int()
+        _check(_lib.fe_batch_schedule(self._h, ctypes.byref(v)), "fe_batch_schedule")
+        return "launches" if v.value else "persistent"
 
     def free(self):
         if self._h:

@@ -1,6 +1,7 @@
-"""GPU parity of the batched persistent matrix evaluation (fe_batch_*) on a
-scaled-down mixed mesh: P1-P3 tetrahedra and Q1-Q3 hexahedra with the
-weighted Laplacian, weighted mass and Lame elasticity, against the oracle."""
+"""GPU parity of the batched matrix evaluation (fe_batch_*, both schedules:
+persistent class kernels and one launch per item) on a scaled-down mixed mesh:
+P1-P3 tetrahedra and Q1-Q3 hexahedra with the weighted Laplacian, weighted mass
+and Lame elasticity, against the oracle."""
 import numpy as np
 import pytest
 
@@ -88,7 +89,9 @@ def _items(groups):
     return items, keys
 
 
-@pytest.mark.parametrize("flags", [0, fe.BATCH_AUTOTUNE | fe.BATCH_GRAPH | fe.BATCH_GEOMETRY])
+@pytest.mark.parametrize("flags", [0, fe.BATCH_AUTOTUNE | fe.BATCH_GRAPH | fe.BATCH_GEOMETRY,
+                                   fe.BATCH_PERSISTENT | fe.BATCH_AUTOTUNE | fe.BATCH_GRAPH,
+                                   fe.BATCH_LAUNCHES, fe.BATCH_LAUNCHES | fe.BATCH_GRAPH | fe.BATCH_GEOMETRY])
 def test_batch_matches_oracle(ctx, groups, flags):
     items, keys = _items(groups)
     b = fe.Batch(ctx, items, flags)
@@ -114,10 +117,37 @@ def test_batch_runs_are_reproducible_and_graph_equals_eager(ctx, groups):
         assert torch.equal(a, c)  # same configurations (no autotuning): identical results
 
 
-def test_batch_geometry_flag_follows_moved_nodes(ctx, groups):
+def test_batch_schedules(ctx, groups):
+    """The schedule flags are honoured, autotuning picks one of the two, and the
+    per-item schedule is reproducible, equal in a graph and eagerly, and agrees
+    with the persistent one to float32 rounding."""
+    items, keys = _items(groups)
+    fresh = lambda: [(g, f, m, None) for g, f, m, _ in items]
+    assert fe.Batch(ctx, fresh(), 0).schedule() == "persistent"
+    assert fe.Batch(ctx, fresh(), fe.BATCH_PERSISTENT | fe.BATCH_AUTOTUNE).schedule() == "persistent"
+    assert fe.Batch(ctx, fresh(), fe.BATCH_AUTOTUNE).schedule() in ("persistent", "launches")
+    with pytest.raises(fe.FEError) as ei:
+        fe.Batch(ctx, fresh(), fe.BATCH_PERSISTENT | fe.BATCH_LAUNCHES)
+    assert ei.value.status == fe.FE_ERR_INVALID_ARG
+    per_item = fe.Batch(ctx, fresh(), fe.BATCH_LAUNCHES)
+    assert per_item.schedule() == "launches"
+    first = [K.clone() for K in per_item.run()]
+    again = per_item.run()
+    graph = fe.Batch(ctx, fresh(), fe.BATCH_LAUNCHES | fe.BATCH_GRAPH)
+    g_out = graph.run()
+    persistent = fe.Batch(ctx, fresh(), 0).run()
+    ctx.check()
+    for (g, f), a, b2, c, p in zip(keys, first, again, g_out, persistent):
+        assert torch.equal(a, b2) and torch.equal(a, c), (g.name, f)
+        scale = float(p.abs().max())
+        assert float((a - p).abs().max()) <= 1e-5 * scale, (g.name, f)
+
+
+@pytest.mark.parametrize("schedule", [fe.BATCH_PERSISTENT, fe.BATCH_LAUNCHES])
+def test_batch_geometry_flag_follows_moved_nodes(ctx, groups, schedule):
     g = groups[4]  # Q2 hexahedra
     items = [(g.geom, _form("elasticity"), g.material("elasticity"), None)]
-    b = fe.Batch(ctx, items, fe.BATCH_GEOMETRY | fe.BATCH_GRAPH)
+    b = fe.Batch(ctx, items, fe.BATCH_GEOMETRY | fe.BATCH_GRAPH | schedule)
     X0 = g.coords.clone()
     rng = np.random.default_rng(3)
     moved = g.mesh.coords.copy()
