@@ -65,6 +65,10 @@ MEASURED_TRAFFIC_48 = {"matrix_bf16x3": 2962232320, "geometry_residual": 1503910
 # a sum, a difference, two multiplies and three FMA in the even-odd form), per point
 # 9 cofactors (mul + FMA each) and det J (mul + 2 FMA) -- 1,620 FP64 instructions
 GEOMETRY_FLOPS_PER_ELEM_Q2 = 2 * 3 * 27 * 6 + 81 * (4 + 2 * 3) + Q2_Q * (9 * 3 + 5)
+GEOMETRY_FP64_INSTR_PER_ELEM_Q2 = 3 * 27 * 6 + 81 * 7 + Q2_Q * (9 * 2 + 3)
+# FP64 lanes per clock per SM: a dependent-chain-free DFMA loop measured 1.19 TFLOP/s
+# on GB300 at 1.96 GHz over 152 SMs, i.e. 2 lanes per clock per SM
+FP64_LANES_PER_CLK_SM = 2
 
 
 # Adjoint: J = |R|^2 / 2 of the assembled Q2 elasticity residual on a 32^3 cube
@@ -960,16 +964,27 @@ def main():
         "gpu_launches": kernels_per_step(prec) * args.steps,
         "step_parts_ms": parts,
     }
+    line["clocks"] = clk.summary()
     if prec != "f64":
-        # the kernel that computes the FP64 geometry and the residual: FP64-bound
-        gf = wl.E * GEOMETRY_FLOPS_PER_ELEM_Q2 / (parts["geometry_and_residual"] / 1e3) / 1e12
+        # the kernel that computes the FP64 geometry and the residual: FP64-bound.
+        # Flops against the nominal rate, and FP64 instructions (a third of them
+        # 1-flop adds and multiplies) against the issue rate at the sampled clock
+        t_gr = parts["geometry_and_residual"] / 1e3
+        gf = wl.E * GEOMETRY_FLOPS_PER_ELEM_Q2 / t_gr / 1e12
+        mhz = line["clocks"].get("sm_mhz") or line["clocks"].get("sm_max_mhz") or 2070.0
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        issue_peak = FP64_LANES_PER_CLK_SM * sms * mhz * 1e6 / 1e9
+        issue = wl.E * GEOMETRY_FP64_INSTR_PER_ELEM_Q2 / t_gr / 1e9
         line["roofline_geometry_residual"] = {
             "kernel": "k_residual_geo (FP64 geometry + r_e, f32)", "bound": "fp64", "achieved": gf,
             "peak": FP64_PEAK_TFLOPS_NOMINAL, "peak_source": "nominal", "unit": "TFLOP/s",
             "frac": gf / FP64_PEAK_TFLOPS_NOMINAL, "flops_per_elem": GEOMETRY_FLOPS_PER_ELEM_Q2,
+            "fp64_issue": {"instructions_per_elem": GEOMETRY_FP64_INSTR_PER_ELEM_Q2, "achieved": issue,
+                           "peak": issue_peak, "unit": "G lane-instructions/s", "frac": issue / issue_peak,
+                           "peak_basis": "%d FP64 lanes per clock per SM (measured) x %d SMs x median SM clock "
+                                         "%.0f MHz" % (FP64_LANES_PER_CLK_SM, sms, mhz)},
             "traffic": MEASURED_TRAFFIC_48["geometry_residual"] if args.n == 48 else None,
             "avg_ms": parts["geometry_and_residual"]}
-    line["clocks"] = clk.summary()
     if ladder is not None:
         line["precision_ladder"] = ladder
     if not args.skip_extras and prec != "f64":
