@@ -58,7 +58,7 @@ FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
 # kernels (dram__bytes_read.sum + dram__bytes_write.sum; the command is in
 # profiles/dram_traffic_q2_elasticity_48.md): the BF16x3 matrix kernel and the
 # geometry + residual kernel.  Other sizes or precisions report null.
-MEASURED_TRAFFIC_48 = {"matrix_bf16x3": 2962232320, "geometry_residual": 150391040}
+MEASURED_TRAFFIC_48 = {"matrix_bf16x3": 2962232320, "geometry_residual": 144459520}
 # FP64 operations (an FMA counts 2) that the collocation geometry executes for one
 # Q2 element with 3x3x3 Gauss points: three 1-D interpolations of 27 lines each
 # (6 FMA a line: the middle point is the middle node), J on the points (81 lines of

@@ -513,7 +513,7 @@ struct ResGeoSmem {
 };
 
 template <int N1, int KIND, int MATK, int EPB, int THREADS, bool CENTER>
-__global__ void __launch_bounds__(THREADS, N1 == 3 ? 6 : 4) k_residual_geo(const double *__restrict__ coords,
+__global__ void __launch_bounds__(THREADS, N1 == 3 ? 7 : 4) k_residual_geo(const double *__restrict__ coords,
                                                           const int32_t *__restrict__ conn, long long E,
                                                           long long n_nodes, const double *__restrict__ b1d64,
                                                           const double *__restrict__ dq64,
@@ -669,7 +669,7 @@ template <int N1, int KIND, int MATK, int EPB, bool CENTER>
 cudaError_t launch_res_geo(fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
                            unsigned long long *st, cudaStream_t s)
 {
-    constexpr int THREADS = 256;
+    constexpr int THREADS = N1 == 3 ? 192 : 256;  // Q2: 7 elements in 6 warps, 7 CTAs per SM
     auto kern = k_residual_geo<N1, KIND, MATK, EPB, THREADS, CENTER>;
     static FeLaunchCache cache;
     long long cap = 0;
@@ -798,8 +798,8 @@ cudaError_t fe_launch_residual_geometry(fe_geometry_h *g, const fe_form_h *f, fe
     switch (g->n1d) {
     case 2: return dispatch_res_geo<2, 16, false>(g, f, mat, u, r, st, s);
     case 3:
-        return g->geo_center ? dispatch_res_geo<3, 9, true>(g, f, mat, u, r, st, s)
-                             : dispatch_res_geo<3, 9, false>(g, f, mat, u, r, st, s);
+        return g->geo_center ? dispatch_res_geo<3, 7, true>(g, f, mat, u, r, st, s)
+                             : dispatch_res_geo<3, 7, false>(g, f, mat, u, r, st, s);
     case 4: return dispatch_res_geo<4, 2, false>(g, f, mat, u, r, st, s);
     }
     return cudaErrorNotSupported;

@@ -346,9 +346,10 @@ def test_residual_computes_stale_geometry(ctx, kind, material, p, n):
 
 
 def test_residual_computes_stale_geometry_many_groups_per_cta(ctx):
-    """About 37,000 Q2 elements: every CTA of the residual kernel takes several
-    groups of elements, the last one ragged."""
-    mesh = meshgen.structured_hex(34, 33, 33, 2, 0.15, 96)
+    """60,800 Q2 elements: the residual kernel's grid is capped at four waves of
+    resident CTAs (4 x 7 x 152 of 7 elements on GB300), so every CTA takes at
+    least two groups of elements; the last group is ragged."""
+    mesh = meshgen.structured_hex(40, 40, 38, 2, 0.15, 96)
     P = Problem(ctx, mesh, 2, 3)
     lam, mu = meshgen.lame_materials(mesh)
     lm = _t(np.stack([lam, mu], 1), torch.float64)
