@@ -64,14 +64,14 @@ __device__ __forceinline__ void geo_line_deriv(const double *__restrict__ x, int
         out[0] = __fma_rn(Dq[N1 * N1 + 1], o, t);
         out[so] = __dmul_rn(-Dq[1 * N1 + 2], o);
         out[2 * so] = __fma_rn(Dq[N1 * N1 + 1], o, -t);
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int q = 0; q < N1; ++q) {
-        double acc = 0.0;
+        for (int q = 0; q < N1; ++q) {
+            double acc = 0.0;
 #pragma unroll
-        for (int p = 0; p < N1; ++p) acc = __fma_rn(Dq[q * N1 + p], v[p], acc);
-        out[q * so] = acc;
+            for (int p = 0; p < N1; ++p) acc = __fma_rn(Dq[q * N1 + p], v[p], acc);
+            out[q * so] = acc;
+        }
     }
 }
 

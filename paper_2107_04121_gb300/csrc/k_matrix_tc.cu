@@ -37,7 +37,6 @@
 namespace {
 
 constexpr int TC_N = 27, TC_Q = 27;
-constexpr int TC_THREADS = 128;
 constexpr int TC_M = 128;        // MMA rows
 constexpr int TC_NCOL = 96;      // MMA columns
 constexpr int TC_KPAD = 32;      // quadrature points, padded

@@ -326,12 +326,10 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
         // ((k, b0+y), (i, a0+x)); emit(i, k, x, y, v, vt) receives both values
         auto for_entries = [&](auto &&emit) {
             if constexpr (KIND == FK_ELASTICITY) {
-                const S *C = sC + el * 81;  // general D: C_ijkl read from shared memory
 #pragma unroll
                 for (int x = 0; x < T; ++x)
 #pragma unroll
                     for (int y = 0; y < T; ++y) {
-                        const S tr = acc[0][0][x][y] + acc[1][1][x][y] + acc[2][2][x][y];
 #pragma unroll
                         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -339,9 +337,10 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
                                 S v, vt;
                                 if constexpr (MATK == 1) {
                                     v = lam * acc[i][k][x][y] + mu * acc[k][i][x][y];
-                                    if (i == k) v += mu * tr;
+                                    if (i == k) v += mu * (acc[0][0][x][y] + acc[1][1][x][y] + acc[2][2][x][y]);
                                     vt = v;  // symmetric D: K is symmetric
                                 } else {
+                                    const S *C = sC + el * 81;  // general D: C_ijkl read from shared memory
                                     v = 0;
                                     vt = 0;
 #pragma unroll
