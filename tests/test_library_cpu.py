@@ -155,3 +155,17 @@ def test_null_arguments_are_rejected(libfe):
     assert libfe.fe_destroy(None) == fe.FE_ERR_INVALID_ARG
     assert libfe.fe_geometry_free(None) == fe.FE_ERR_INVALID_ARG
     assert libfe.fe_assembly_free(None) == fe.FE_ERR_INVALID_ARG
+    # every entry point rejects a NULL context or handle before touching the device
+    v = ctypes.c_int()
+    assert libfe.fe_geometry_view(None, None, 0, 0, ctypes.byref(h)) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_geometry_update(None, None, None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_geometry_get(None, None, 0, 0, None, None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_assembly_create(None, None, ctypes.byref(h), None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_assemble_vector_noalloc(None, None, 3, None, 0, None, 0, None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_batch_create(None, None, 0, 0, ctypes.byref(h), None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_batch_run(None, None, None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_batch_describe(None, 0, None, None, None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_batch_schedule(None, ctypes.byref(v)) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_batch_free(None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_round_f32(None, None, None, 0, None) == fe.FE_ERR_INVALID_ARG
+    assert libfe.fe_debug_hold_next_matrix(None) == fe.FE_ERR_INVALID_ARG
