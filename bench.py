@@ -377,6 +377,16 @@ def sampled_errors(wl, precs, ref):
     return out, len(idx)
 
 
+def e2e_job_summary(per_ms, units, h2d, d2h, ws):
+    """The job's end-to-end figures from one rank's step times: the link is shared with
+    the host, so a rank's step is its median (mean and worst beside it); the job's step
+    is the slowest rank's, and the rate and the bytes moved are the whole job's."""
+    ms = max_over_ranks(statistics.median(per_ms), ws)
+    return {"value": ws * units / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+            "mean_ms": max_over_ranks(statistics.mean(per_ms), ws), "max_ms": max_over_ranks(max(per_ms), ws),
+            "h2d_bytes_per_step": ws * h2d, "d2h_bytes_per_step": ws * d2h}
+
+
 def e2e_measure(wl, prec, steps, ws=1, chunks=8):
     """Same step through the public API with host buffers: pinned H2D of the inputs
     (coordinates, connectivity, materials, DOFs) and D2H of every result (K_e, r_e,
@@ -439,13 +449,9 @@ def e2e_measure(wl, prec, steps, ws=1, chunks=8):
         b.synchronize()
         per.append(a.elapsed_time(b))
     wl.ctx.check()
-    # the link is shared with the host: the median step, with the mean and the worst beside it
-    ms = max_over_ranks(statistics.median(per), ws)
     for v in views:
         v.free()
-    return {"value": ws * wl.E / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-            "mean_ms": max_over_ranks(statistics.mean(per), ws), "max_ms": max_over_ranks(max(per), ws),
-            "h2d_bytes_per_step": ws * h2d, "d2h_bytes_per_step": ws * d2h, "chunks": len(ranges),
+    return {**e2e_job_summary(per, wl.E, h2d, d2h, ws), "chunks": len(ranges),
             "note": "bound by the device-to-host link (about 194 GB/s for pinned copies and for SM stores to "
                     "host memory on this machine)"}
 

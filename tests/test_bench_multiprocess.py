@@ -1,6 +1,7 @@
 """The multi-GPU path of bench.py (replicas, one process per GPU) on the host: two
-gloo ranks check the max over ranks, the barrier, the whole-job throughput of
-replicas and that the oracle's reference arm prints only on rank 0."""
+gloo ranks check the max over ranks, the barrier, the whole-job throughput and
+end-to-end figures of replicas and that the oracle's reference arm prints only on
+rank 0."""
 import json
 import os
 import socket
@@ -35,6 +36,8 @@ def _rank_main(rank, port, out_dir):
     # replicas: each rank processes 1,000 units per step; rank 1 is slower
     step_ms = [2.0, 2.0, 2.0] if rank == 0 else [3.0, 3.0, 3.0]
     got["rate"], got["ms_per_step"] = bench.job_rate(step_ms, 1000, 3, ws)
+    # end to end: each rank's median step, the job's is the slower rank's
+    got["e2e"] = bench.e2e_job_summary([10.0, 12.0, 11.0] if rank == 0 else [20.0, 24.0, 21.0], 1000, 100, 200, ws)
     dist.destroy_process_group()
     with open(os.path.join(out_dir, "rank%d.json" % rank), "w") as f:
         json.dump(got, f)
@@ -49,6 +52,11 @@ def test_two_gloo_ranks_aggregate_like_the_benchmark(tmp_path):
         # 2 ranks x 1,000 units x 3 steps in the slower rank's 9 ms
         assert got["ms_per_step"] == pytest.approx(3.0)
         assert got["rate"] == pytest.approx(2 * 1000 * 3 / 9e-3)
+        e2e = got["e2e"]
+        assert e2e["ms_per_step"] == 21.0 and e2e["max_ms"] == 24.0
+        assert e2e["mean_ms"] == pytest.approx(65.0 / 3)
+        assert e2e["value"] == pytest.approx(2 * 1000 / 21e-3)
+        assert (e2e["h2d_bytes_per_step"], e2e["d2h_bytes_per_step"]) == (200, 400)
 
 
 def test_reference_arm_prints_on_rank_0_only(capsys):
