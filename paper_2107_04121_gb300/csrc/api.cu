@@ -627,7 +627,8 @@ fe_status fe_assemble_vector_noalloc(fe_ctx *ctx, const fe_mesh *mesh, int ncomp
                       1 << 21);
         return FE_ERR_SHAPE;
     }
-    cudaSetDevice(ctx->device);
+    cudaError_t dev_err = cudaSetDevice(ctx->device);
+    if (dev_err != cudaSuccess) return from_cuda(dev_err, "fe_assemble_vector_noalloc");
     return from_cuda(fe_launch_assemble_noalloc(ctx->device, mesh, ncomp, prec == FE_F64, r_e, global_out, flags,
                                                 ctx->d_status, to_cuda(stream)),
                      "fe_assemble_vector_noalloc");

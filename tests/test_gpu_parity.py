@@ -257,10 +257,15 @@ def test_elasticity_general_D_and_transposed_spec(ctx, prec):
     assert rel_matrix_error(Kt.cpu().numpy(), Kref) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4), ("bf16", 2e-2)])
+# raw BF16 (8-bit significands, no split) is below the 1e-5 bar by design: its
+# error is a stated figure (2.4e-3 measured at the 48^3 workload), gated at 5e-3
+TC_TOL = [("tf32x3", TOL["tf32x3"]), ("bf16x3", TOL["bf16x3"]), ("bf16", 5e-3)]
+
+
+@pytest.mark.parametrize("prec,tol", TC_TOL)
 def test_tensor_core_elasticity_matches_oracle(ctx, prec, tol):
-    """tcgen05 split-precision paths (Q2, Lame): TF32x3 within the FP32 tolerance;
-    BF16x3 and raw BF16 against their stated bounds."""
+    """tcgen05 split-precision paths (Q2, Lame): TF32x3 and BF16x3 within the 1e-5
+    bar on every element; raw BF16 against its stated figure."""
     P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (4, 4, 5), 81)
     args = [_t(mat, torch.float64), None, None]
     K = fe.eval_matrix(ctx, form, P.geom, args, prec)
@@ -274,7 +279,7 @@ def test_tensor_core_elasticity_matches_oracle(ctx, prec, tol):
     assert np.abs(Kh - Kh.transpose(0, 2, 1)).max() <= 10 * tol * np.abs(Kh).max()
 
 
-@pytest.mark.parametrize("prec,tol", [("tf32x3", 1e-5), ("bf16x3", 1e-4), ("bf16", 2e-2)])
+@pytest.mark.parametrize("prec,tol", TC_TOL)
 def test_tensor_core_pipeline_many_elements_per_cta(ctx, prec, tol):
     """2,352 elements: every persistent CTA of the tensor-core kernel runs 5 or 6
     elements through its two operand buffers and its accumulator (buffer reuse,

@@ -61,3 +61,32 @@ def test_noalloc_rejects_meshes_beyond_its_workspace(libfe):
     assert b"524288" in fe.load_library().fe_last_error_message()
     ctx.check()
     ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_noalloc_reports_out_of_range_nodes_and_assembles_the_rest(libfe, prec):
+    """A node index outside the mesh is reported on the device (FE_ERR_SHAPE with
+    the element index, read by fe_get_status) and that incidence is skipped: every
+    global entry equals the allocating path's on the valid mesh with that
+    incidence's contributions set to zero."""
+    ctx = fe.Context(0)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    mesh, m = _mesh((3, 3, 2), 1, 5)
+    bad_e, bad_a = 7, 2
+    conn = mesh.conn.copy()
+    conn[bad_e, bad_a] = mesh.n_nodes + 11
+    m_bad = fe.Mesh(m.coords, torch.from_numpy(conn).cuda())
+    rng = np.random.default_rng(72)
+    N = mesh.nodes_per_elem
+    r = torch.from_numpy(rng.standard_normal((mesh.n_elems, 3 * N))).to("cuda", dt)
+    out = torch.full((mesh.n_nodes * 3,), float("nan"), dtype=dt, device="cuda")
+    fe.assemble_vector_noalloc(ctx, m_bad, 3, r, out, prec, flags=fe.ASSEMBLE_COMPENSATED if prec == "f32" else 0)
+    st, elem = ctx.status()
+    assert st == fe.FE_ERR_SHAPE and elem == bad_e
+    r0 = r.clone()
+    r0[bad_e, bad_a::N] = 0  # the skipped incidence, all three components
+    want = fe.assemble_vector(ctx, fe.assembly_create(ctx, m), 3, r0, prec,
+                              flags=fe.ASSEMBLE_COMPENSATED if prec == "f32" else 0)
+    ctx.check()
+    assert torch.equal(out, want)
+    ctx.close()
