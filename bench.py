@@ -38,6 +38,13 @@ Q2_N, Q2_Q = 27, 27
 # w det J (27 qp x 10 floats), the Lame pair (2 doubles), write K_e (81 x 81 floats)
 MATRIX_BYTES_PER_ELEM_F32 = Q2_Q * 10 * 4 + 16 + 81 * 81 * 4
 MATRIX_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 16 + 81 * 81 * 8
+# the tensor-core matrix kernel that computes the deferred FP64 geometry itself:
+# read the 27 x 3 coordinates (gathered, counted once per element), the
+# connectivity and the Lame pair; write K_e and the handle's float32 J^-1, w det J
+MATRIX_GEO_BYTES_PER_ELEM = Q2_N * 3 * 8 + Q2_N * 4 + 16 + 81 * 81 * 4 + Q2_Q * 10 * 4
+# the residual on the stored float32 geometry: read J^-1, w det J, the connectivity,
+# the gathered u_e and the Lame pair, write r_e
+RESIDUAL_BYTES_PER_ELEM = Q2_Q * 10 * 4 + Q2_N * 4 + 81 * 4 + 16 + 81 * 4
 
 
 # Navier-Stokes convection 'i,i.j,j' (Eq. fe2) on a 64^3 Q2 cube, +-0.1h seed 3,
@@ -54,11 +61,11 @@ CV_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 81 * 8 + 27 * 4 + 81 * 81 * 8
 # last contraction and row assembly 56862
 CV_FLOPS_PER_ELEM = 972 + 1458 + 1944 + 1944 + 6804 + 20412 + 56862
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
-# DRAM bytes (read + write) of one launch at 48^3 from an ncu capture of the current
-# kernels (dram__bytes_read.sum + dram__bytes_write.sum; the command is in
-# profiles/dram_traffic_q2_elasticity_48.md): the BF16x3 matrix kernel and the
-# geometry + residual kernel.  Other sizes or precisions report null.
-MEASURED_TRAFFIC_48 = {"matrix_bf16x3": 2962232320, "geometry_residual": 144459520}
+# DRAM bytes (read + write) of one launch of the step's matrix kernel, per precision
+# key "matrix_geo_<prec>", from an ncu capture of the current kernel (the command is
+# in profiles/); empty until the kernel that computes the geometry is captured,
+# and then null for every other size or precision.
+MEASURED_TRAFFIC_48 = {}
 # FP64 operations (an FMA counts 2) that the collocation geometry executes for one
 # Q2 element with 3x3x3 Gauss points: three 1-D interpolations of 27 lines each
 # (6 FMA a line: the middle point is the middle node), J on the points (81 lines of
@@ -243,27 +250,38 @@ class Workload:
         self.bufs.pop(prec, None)
         self.torch.cuda.empty_cache()
 
-    PARTS = ("geometry_and_residual", "matrix", "assembly")
+    @staticmethod
+    def matrix_first(prec):
+        """Tensor-core precisions: the matrix kernel computes the stale deferred FP64
+        geometry itself (beside the K_e stream) and the residual reads its float32
+        copy; otherwise the residual kernel computes it and the matrix follows."""
+        return prec in ("tf32x3", "bf16x3", "bf16")
+
+    def parts(self, prec):
+        if self.matrix_first(prec):
+            return ("matrix_with_geometry", "residual", "assembly")
+        return ("geometry_and_residual", "matrix", "assembly")
 
     def step(self, prec, ev=None):
-        """One step; `ev` (optional) gets four CUDA events recorded at the start,
-        after the geometry + residual, after the matrix and after the assembly."""
+        """One step; `ev` (optional) gets four CUDA events recorded at the start and
+        after each of the three parts (parts(prec) names them)."""
         fe = self.fe
         K, r, g = self.outputs(prec)
         rec = (lambda i: ev[i].record()) if ev else (lambda i: None)
         rec(0)
-        if prec == "f64":
-            geom = self.geoms["f64"]
-            geom.update()
-            fe.eval_residual(self.ctx, self.form, geom, [self.mat, None, self.u64], prec, out=r)
+        geom = self.geoms["f64" if prec == "f64" else "f32d"]
+        u = self.u64 if prec == "f64" else self.u32
+        geom.update()
+        if self.matrix_first(prec):
+            fe.eval_matrix(self.ctx, self.form, geom, [self.mat, None, None], prec, out=K)
+            rec(1)
+            fe.eval_residual(self.ctx, self.form, geom, [self.mat, None, u], prec, out=r)
         else:
-            # stale deferred geometry: the residual kernel computes it (FP64) and
-            # stores the float32 copy that the matrix kernel reads
-            geom = self.geoms["f32d"]
-            geom.update()
-            fe.eval_residual(self.ctx, self.form, geom, [self.mat, None, self.u32], prec, out=r)
-        rec(1)
-        fe.eval_matrix(self.ctx, self.form, geom, [self.mat, None, None], prec, out=K)
+            # FP64: the geometry kernel (an eager handle); f32: the stale deferred
+            # geometry computed by the residual kernel, whose copy the matrix reads
+            fe.eval_residual(self.ctx, self.form, geom, [self.mat, None, u], prec, out=r)
+            rec(1)
+            fe.eval_matrix(self.ctx, self.form, geom, [self.mat, None, None], prec, out=K)
         rec(2)
         fe.assemble_vector(self.ctx, self.asm, 3, r, prec, out=g,
                            flags=0 if prec == "f64" else fe.ASSEMBLE_COMPENSATED)
@@ -271,8 +289,9 @@ class Workload:
 
 
 def kernels_per_step(prec):
-    # FP64: geometry, residual, matrix, assembly; mixed: geometry + residual in
-    # one kernel, matrix, assembly
+    # FP64: geometry, residual, matrix, assembly; tensor-core precisions: the matrix
+    # kernel computing the geometry, the residual, the assembly; f32: geometry +
+    # residual in one kernel, matrix, assembly
     return 4 if prec == "f64" else 3
 LADDER = ["f32", "tf32x3", "bf16x3", "bf16"]
 DEFAULT_MIXED = "bf16x3"
@@ -362,8 +381,10 @@ def timed_steps(wl, prec, steps, warmup, ws, flush):
     barrier(ws)
     wl.ctx.check()
     step_ms = [e[0].elapsed_time(e[3]) for e in ev]
-    mat_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    parts = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev) for i, name in enumerate(wl.PARTS)}
+    mi = 0 if wl.matrix_first(prec) else 1
+    mat_ms = [e[mi].elapsed_time(e[mi + 1]) for e in ev]
+    parts = {name: statistics.mean(e[i].elapsed_time(e[i + 1]) for e in ev)
+             for i, name in enumerate(wl.parts(prec))}
     return step_ms, mat_ms, parts
 
 
@@ -521,7 +542,12 @@ class ConvectWorkload:
     outputs = Workload.outputs
     drop = Workload.drop
 
-    PARTS = ("geometry_and_residual", "matrix", "assembly")
+    @staticmethod
+    def matrix_first(prec):
+        return False
+
+    def parts(self, prec):
+        return ("geometry_and_residual", "matrix", "assembly")
 
     def step(self, prec, ev=None):
         """FP32: the deferred geometry is computed (FP64) by the residual kernel,
@@ -1010,8 +1036,13 @@ def main():
         step_ms, mat_ms, parts = timed_steps(wl, prec, args.steps, args.warmup, ws, flush)
     value, ms_per_step = job_rate(step_ms, wl.E, args.steps, ws)
     mat_avg = sum(mat_ms) / len(mat_ms)
-    bytes_alg = wl.E * (MATRIX_BYTES_PER_ELEM_F64 if prec == "f64" else MATRIX_BYTES_PER_ELEM_F32)
+    fused = wl.matrix_first(prec)
+    mat_bytes = MATRIX_GEO_BYTES_PER_ELEM if fused else (MATRIX_BYTES_PER_ELEM_F64 if prec == "f64"
+                                                         else MATRIX_BYTES_PER_ELEM_F32)
+    bytes_alg = wl.E * mat_bytes
     achieved = bytes_alg / (mat_avg / 1e3) / 1e9
+    kname = ("k_matrix_tc<%s> with its geometry warps (fe_eval_matrix computing the deferred FP64 geometry)" % prec
+             if fused else "k_matrix (fe_eval_matrix, %s)" % prec)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1019,50 +1050,71 @@ def main():
         "config": {"workload": workload_description(args.n, wl.E), "elements": wl.E,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": "replicas"},
         "contraction": prec, "geometry_dtype": "f64",
-        "roofline": {"kernel": "k_matrix (fe_eval_matrix, %s)" % prec, "bound": "hbm", "achieved": achieved,
+        "roofline": {"kernel": kname, "bound": "hbm", "achieved": achieved,
                      "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "traffic": MEASURED_TRAFFIC_48["matrix_bf16x3"] if (args.n == 48 and prec == "bf16x3") else None,
-                     "bytes_per_elem": bytes_alg / wl.E, "avg_ms": mat_avg},
+                     "traffic": MEASURED_TRAFFIC_48.get("matrix_geo_" + prec) if (args.n == 48 and fused) else None,
+                     "bytes_per_elem": mat_bytes, "avg_ms": mat_avg},
         "gpu_launches": kernels_per_step(prec) * args.steps,
         "step_parts_ms": parts,
     }
     line["clocks"] = clk.summary()
     if prec != "f64":
-        # the kernel that computes the FP64 geometry and the residual: FP64-bound.
-        # Flops against the nominal rate, and FP64 instructions (a third of them
-        # 1-flop adds and multiplies) against the issue rate at the sampled clock
-        t_gr = parts["geometry_and_residual"] / 1e3
-        gf = wl.E * GEOMETRY_FLOPS_PER_ELEM_Q2 / t_gr / 1e12
+        # FP64 geometry: lane-instructions per element against the issue peak of the
+        # FP64 units (2 lanes per clock per SM) at the sampled clock, over the time of
+        # the kernel that computes it (the matrix kernel's geometry warps, or the
+        # geometry + residual kernel)
+        t_geo = (parts["matrix_with_geometry"] if fused else parts["geometry_and_residual"]) / 1e3
         mhz = line["clocks"].get("sm_mhz") or line["clocks"].get("sm_max_mhz") or 2070.0
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         issue_peak = FP64_LANES_PER_CLK_SM * sms * mhz * 1e6 / 1e9
-        issue = wl.E * GEOMETRY_FP64_INSTR_PER_ELEM_Q2 / t_gr / 1e9
-        line["roofline_geometry_residual"] = {
-            "kernel": "k_residual_geo (FP64 geometry + r_e, f32)", "bound": "fp64", "achieved": gf,
-            "peak": FP64_PEAK_TFLOPS_NOMINAL, "peak_source": "nominal", "unit": "TFLOP/s",
-            "frac": gf / FP64_PEAK_TFLOPS_NOMINAL, "flops_per_elem": GEOMETRY_FLOPS_PER_ELEM_Q2,
-            "fp64_issue": {"instructions_per_elem": GEOMETRY_FP64_INSTR_PER_ELEM_Q2, "achieved": issue,
-                           "peak": issue_peak, "unit": "G lane-instructions/s", "frac": issue / issue_peak,
-                           "peak_basis": "%d FP64 lanes per clock per SM (measured) x %d SMs x median SM clock "
-                                         "%.0f MHz" % (FP64_LANES_PER_CLK_SM, sms, mhz)},
-            "traffic": MEASURED_TRAFFIC_48["geometry_residual"] if args.n == 48 else None,
-            "avg_ms": parts["geometry_and_residual"]}
+        issue = wl.E * GEOMETRY_FP64_INSTR_PER_ELEM_Q2 / t_geo / 1e9
+        line["roofline_fp64_geometry"] = {
+            "kernel": kname if fused else "k_residual_geo (FP64 geometry + r_e, f32)", "bound": "fp64",
+            "instructions_per_elem": GEOMETRY_FP64_INSTR_PER_ELEM_Q2, "achieved": issue, "peak": issue_peak,
+            "unit": "G FP64 lane-instructions/s", "frac": issue / issue_peak,
+            "peak_basis": "%d FP64 lanes per clock per SM (measured) x %d SMs x median SM clock %.0f MHz"
+                          % (FP64_LANES_PER_CLK_SM, sms, mhz),
+            "avg_ms": t_geo * 1e3}
+        # the whole step against its floor: the larger of its algorithmic bytes at the
+        # HBM copy rate and its FP64 geometry at the FP64 issue peak
+        asm_bytes = 81 * 4 + Q2_N * 4 + (wl.mesh.n_nodes + 1) * 4 / wl.E + wl.mesh.n_nodes * 3 * 4 / wl.E
+        step_bytes = MATRIX_GEO_BYTES_PER_ELEM + RESIDUAL_BYTES_PER_ELEM + asm_bytes
+        t_hbm = wl.E * step_bytes / (hbm_peak * 1e9) * 1e3
+        t_fp64 = wl.E * GEOMETRY_FP64_INSTR_PER_ELEM_Q2 / (issue_peak * 1e9) * 1e3
+        floor = max(t_hbm, t_fp64)
+        line["roofline_step"] = {
+            "bound": "hbm" if t_hbm >= t_fp64 else "fp64", "floor_ms": floor, "ms_per_step": ms_per_step,
+            "frac": floor / ms_per_step, "bytes_per_elem": step_bytes, "hbm_ms": t_hbm, "fp64_ms": t_fp64,
+            "basis": "step bytes (matrix with geometry, residual, assembly) / measured HBM copy rate vs FP64 "
+                     "geometry lane-instructions / FP64 issue peak; frac = floor / ms_per_step"}
     if ladder is not None:
         line["precision_ladder"] = ladder
     if prec_note:
         line["precision_note"] = prec_note
     if not args.skip_extras and prec != "f64":
-        # the two residual variants: geometry computed in the residual kernel (the
-        # step above) against the geometry kernel followed by the residual on the
-        # stored float32 copy
+        # the step's geometry variants, timed alone: the tensor-core kernel computing
+        # it, the residual kernel computing it, and the geometry kernel followed by
+        # the residual and the matrix on the stored float32 copy
         K, r, g = wl.outputs(prec)
-        g32 = wl.geoms["f32"]
+        g32, gd = wl.geoms["f32"], wl.geoms["f32d"]
+        mat_args = [wl.mat, None, None]
+        res_args = [wl.mat, None, wl.u32]
+        def fused_matrix():
+            gd.update()
+            wl.fe.eval_matrix(wl.ctx, wl.form, gd, mat_args, prec, out=K)
+        def fused_residual():
+            gd.update()
+            wl.fe.eval_residual(wl.ctx, wl.form, gd, res_args, prec, out=r)
+        t_fm = time_call(wl, flush, fused_matrix) if wl.matrix_first(prec) else None
+        t_fr = time_call(wl, flush, fused_residual)
         t_geo = time_call(wl, flush, lambda: g32.update())
-        t_res = time_call(wl, flush, lambda: wl.fe.eval_residual(wl.ctx, wl.form, g32, [wl.mat, None, wl.u32], prec,
-                                                                 out=r))
-        line["residual_variants_ms"] = {"geometry_in_residual_kernel": parts["geometry_and_residual"],
-                                        "stored_geometry": {"geometry": t_geo, "residual": t_res,
-                                                            "sum": t_geo + t_res}}
+        t_res = time_call(wl, flush, lambda: wl.fe.eval_residual(wl.ctx, wl.form, g32, res_args, prec, out=r))
+        t_mat = time_call(wl, flush, lambda: wl.fe.eval_matrix(wl.ctx, wl.form, g32, mat_args, prec, out=K))
+        line["geometry_variants_ms"] = {
+            "matrix_kernel_computing_geometry": t_fm, "residual_kernel_computing_geometry": t_fr,
+            "stored_geometry": {"geometry": t_geo, "residual": t_res, "matrix": t_mat},
+            "steps_without_assembly": {"matrix_first": None if t_fm is None else t_fm + t_res,
+                                       "residual_first": t_fr + t_mat, "geometry_first": t_geo + t_res + t_mat}}
     if not args.skip_extras:
         wl.drop(prec)
         # plain FP64 path, same step

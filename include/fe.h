@@ -208,8 +208,15 @@ int fe_gm_rule_size(int s);
                                 by fe_eval_residual itself (Laplace, mass, elasticity or the
                                 convective form, any precision but FE_F64): one kernel for the
                                 FP64 geometry, the stored float32 copy and the residual, with
-                                the same bits as the separate geometry kernel.  The stale mark
-                                is host state: use a deferred handle from one stream. */
+                                the same bits as the separate geometry kernel.  Such a handle of
+                                27-node hexahedra with 3 x 3 x 3 Gauss points is also computed
+                                by fe_eval_matrix itself in the tensor-core precisions (Lame
+                                elasticity): warps of the tensor-core kernel compute the FP64
+                                geometry beside the K_e stream and store the float32 copy, same
+                                bits again.  A call that reports an error (e.g. FE_ERR_TIMEOUT)
+                                leaves the geometry it was computing undefined until the next
+                                fe_geometry_update.  The stale mark is host state: use a
+                                deferred handle from one stream. */
 
 /* Geometry of the reference mapping (Sec. 4.1): for every element e and
  * quadrature point q, J = sum_a x_a (x) grad_xi phi_a(q), det J, J^-1 and
@@ -309,8 +316,10 @@ fe_status fe_form_shape(const fe_form_h *form, int n_basis, int *n_rows, int *n_
  * (n_elems, n_rows, n_cols), float64 for FE_F64 else float32.
  * FE_F64 and FE_F32 cover every form and element; the tensor-core precisions
  * (FE_TF32X3, FE_BF16X3, FE_BF16) cover linear elasticity with FE_MAT_LAME
- * materials on 27-node hexahedra with 27 points.  A tensor-core wait that
- * times out is reported as FE_ERR_TIMEOUT through fe_get_status.
+ * materials on 27-node hexahedra with 27 points; on a stale float32-only
+ * deferred handle they compute its geometry in the same launch (see
+ * FE_GEOM_DEFERRED).  A tensor-core wait that times out is reported as
+ * FE_ERR_TIMEOUT through fe_get_status.
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_SHAPE, FE_ERR_UNSUPPORTED_SPEC (e.g. a
  * precision without a kernel for this form), FE_ERR_CUDA. */
 fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const void *const *args,

@@ -10,7 +10,9 @@
 #include "fe_internal.h"
 
 cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
-                                void *K, int sm_count, unsigned long long *status, const int *hold, cudaStream_t s);
+                                void *K, int sm_count, unsigned long long *status, const int *hold,
+                                bool with_geometry, cudaStream_t s);
+bool fe_matrix_tc_geometry_fusable(const fe_geometry_h *g);
 
 // A deferred handle whose geometry is stale gets it computed before any use.
 static cudaError_t settle_geometry(fe_geometry_h *g, unsigned long long *status, cudaStream_t s)
@@ -424,11 +426,15 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
         // tensor-core kernels: Q2 elasticity (27 nodes, 27 points) with Lame materials
         if (form->kind != FK_ELASTICITY || form->mat != FE_MAT_LAME || !(g->N == 27 && g->Q == 27))
             return FE_ERR_UNSUPPORTED_SPEC;
-        e = settle_geometry(gm, ctx->d_status, s);
+        // a stale float32-only deferred handle: the tensor-core kernel computes the
+        // FP64 geometry of its elements itself and stores the float32 copy
+        const bool fused = fe_matrix_tc_geometry_fusable(gm);
+        e = fused ? cudaSuccess : settle_geometry(gm, ctx->d_status, s);
         const int *hold = ctx->hold_next_matrix ? ctx->d_hold : nullptr;
         ctx->hold_next_matrix = 0;
         if (e == cudaSuccess)
-            e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, ctx->d_status, hold, s);
+            e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, ctx->d_status, hold, fused, s);
+        if (fused && e == cudaSuccess) gm->pending = 0;
     }
     return from_cuda(e, "fe_eval_matrix");
 }

@@ -30,9 +30,25 @@
 //     (g) the 26,244-byte element matrix is written by one bulk copy, and
 //         empty[n % 2] hands the buffer and the accumulator back
 // so the operand build and MMAs of element n+1 overlap the epilogue of n.
+//
+// With a stale float32-only deferred geometry (Q2, 3x3x3 Gauss points) two
+// more warps per CTA compute the FP64 geometry themselves, one element at a time
+// (lanes = 1-D lines of the collocation stages of the geometry kernel, same
+// roundings, same bits): each stores the float32 J^-1 and w det J of the handle
+// and puts sqrt(w det J) J^-1 and the Lame pair into a ring
+// of shared-memory slots that replaces phase (a).  The geometry is bound by the
+// FP64 units, the rest of the kernel by shared memory and HBM, so the two overlap
+// instead of running one after the other.  On GB300 every SM sub-partition has
+// its own FP64 unit, which takes about 64 cycles per warp-instruction whatever
+// the number of active lanes, and the warps of co-resident CTAs sit on the
+// sub-partitions in turn, so that six geometry warps share four units unevenly;
+// element n of a CTA goes to its geometry warp n % 2.  (Claiming elements from a
+// grid-wide counter, with the producers taking whichever slot is filled first,
+// measured 4% slower: shared memory, not the FP64 units, sets the pace.)
 #include <cuda_bf16.h>
 
 #include "fe_device.cuh"
+#include "geometry_body.cuh"
 
 namespace {
 
@@ -47,6 +63,7 @@ constexpr int TC_EX_STRIDE = 28;  // floats per row of the exchange blocks (16-b
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;  // about two seconds at 2 GHz
 
 enum TcMode { TC_TF32X3 = 0, TC_BF16X3 = 1, TC_BF16 = 2 };
+constexpr int TC_NGEO = 2;  // geometry warps per CTA (GEO)
 
 // K-major, non-swizzled canonical layout: 8-row x 16-byte core matrices; the
 // K chunks of one 8-row group are adjacent (LBO = 128 B), 8-row groups follow
@@ -277,7 +294,7 @@ __device__ __forceinline__ void epilogue_rows(int I, const float *d, const float
                           kst + (I * TC_N + a) * TC_NROW + Kb * TC_N, kst + (Kb * TC_N) * TC_NROW + I * TC_N + a);
 }
 
-template <int MODE>
+template <int MODE, bool GEO>
 struct TcSmem {
     static constexpr int EB = MODE == TC_TF32X3 ? 4 : 2;
     using L = OpLayout<EB>;
@@ -295,11 +312,24 @@ struct TcSmem {
     // the table lives in the staging area
     static constexpr int DP = KS;
     static_assert(TC_Q * 3 * TC_N * 4 <= KS_BYTES, "reference gradients fit the staging area");
-    static constexpr int JW = (KS + KS_BYTES + 15) / 16 * 16;          // [2][27][12] sqrt(w det J) J^-1
-    static constexpr int LM = JW + 2 * TC_Q * TC_JW_STRIDE * 4;        // [2][2] lambda, mu
-    // full[2], empty[2], tmem slot, abort flag, accfree[2]
-    static constexpr int MISC = (LM + 16 + 15) / 16 * 16;
-    static constexpr int BYTES = MISC + 64;
+    // sqrt(w det J) J^-1 of the elements in flight: [2][27][12] filled by the
+    // producers, or (GEO) a ring of RING slots [27][12] + (lambda, mu, pad) filled
+    // by the geometry warp
+    static constexpr int RING = GEO ? 6 : 0;                            // a multiple of TC_NGEO
+    static constexpr int SLOT = TC_Q * TC_JW_STRIDE + 4;               // floats per ring slot
+    static constexpr int JW = (KS + KS_BYTES + 15) / 16 * 16;
+    static constexpr int JW_BYTES = GEO ? RING * SLOT * 4 : 2 * TC_Q * TC_JW_STRIDE * 4;
+    static constexpr int LM = JW + JW_BYTES;                            // [2][2] lambda, mu
+    // GEO: FP64 stage buffers of each geometry warp [4][81] (x / points, two
+    // interpolation stages, J over the last three) and their tables B[9], Dq[9 + 4], w[27]
+    static constexpr int GS = (LM + 16 + 15) / 16 * 16;
+    static constexpr int GS_WARP = 4 * 3 * TC_N;                        // doubles per geometry warp
+    static constexpr int GT = GS + (GEO ? TC_NGEO * GS_WARP * 8 : 0);
+    static constexpr int GT_LEN = 9 + 9 + GEO_DQ_EXTRA + TC_Q;
+    // full[2], empty[2], tmem slot, abort flag, accfree[2]; GEO: geo_full[RING], geo_empty[RING]
+    static constexpr int MISC = (GT + (GEO ? GT_LEN * 8 : 0) + 15) / 16 * 16;
+    static constexpr int GFULL = MISC + 64, GEMPTY = GFULL + 8 * RING;
+    static constexpr int BYTES = MISC + 64 + 16 * RING;
     // accumulators in tensor memory: one when three CTAs fit an SM (the MMAs of
     // element n+1 wait only for element n's read-out; the other CTAs hide it),
     // two when only two CTAs fit (512 columns per SM)
@@ -336,17 +366,27 @@ __device__ __forceinline__ bool mbar_wait_cycles(uint32_t bar, uint32_t parity)
     return true;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_matrix_tc(const float *__restrict__ jinv,
-                                                                 const float *__restrict__ wdetj,
-                                                                 const float *__restrict__ dphi, long long E,
-                                                                 const double *__restrict__ lame,
-                                                                 float *__restrict__ K,
-                                                                 unsigned long long *__restrict__ status,
-                                                                 const int *__restrict__ hold)
+// The arrays of the geometry warp (GEO): the mesh, the FP64 tables of the
+// collocation stages and the handle's float32 copy it writes.
+struct TcGeoArgs {
+    const double *coords;
+    const int32_t *conn;
+    long long n_nodes;
+    const double *b1d, *dq, *w;  // B (3 x 3), Dq (3 x 3) + GEO_DQ_EXTRA, w (27)
+    float *jinv_out, *wdetj_out;
+};
+
+constexpr int TC_GEO_WARP = 6;  // first geometry warp
+
+template <int MODE, bool GEO>
+__global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE == TC_TF32X3 ? 2 : 3)
+    k_matrix_tc(const float *__restrict__ jinv, const float *__restrict__ wdetj, const float *__restrict__ dphi,
+                long long E, const double *__restrict__ lame, float *__restrict__ K,
+                unsigned long long *__restrict__ status, const int *__restrict__ hold, TcGeoArgs geo)
 {
-    using P = TcSmem<MODE>;
+    using P = TcSmem<MODE, GEO>;
     using L = typename P::L;
+    constexpr int NTHREADS = TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0);
     extern __shared__ __align__(1024) unsigned char smem[];
     float *ks = reinterpret_cast<float *>(smem + P::KS);
     float *sJw = reinterpret_cast<float *>(smem + P::JW);
@@ -357,10 +397,17 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + P::MISC + 32);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + P::MISC + 36);
     uint64_t *accfree = reinterpret_cast<uint64_t *>(smem + P::MISC + 40);  // [NACC] accumulator read out
+    uint64_t *geo_full = reinterpret_cast<uint64_t *>(smem + P::GFULL);    // [RING] slot filled
+    uint64_t *geo_empty = reinterpret_cast<uint64_t *>(smem + P::GEMPTY);  // [RING] slot read
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    for (int i = tid; i < TC_Q * 3 * TC_N; i += TC_THREADS_WS) sDp[i] = dphi[i];
+    for (int i = tid; i < TC_Q * 3 * TC_N; i += NTHREADS) sDp[i] = dphi[i];
+    if constexpr (GEO) {
+        double *gt = reinterpret_cast<double *>(smem + P::GT);
+        for (int i = tid; i < P::GT_LEN; i += NTHREADS)
+            gt[i] = i < 9 ? geo.b1d[i] : (i < 18 + GEO_DQ_EXTRA ? geo.dq[i - 9] : geo.w[i - 18 - GEO_DQ_EXTRA]);
+    }
     if (tid == 0) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -370,6 +417,10 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
 #pragma unroll
         for (int b = 0; b < P::NACC; ++b)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(accfree + b)), "r"(1) : "memory");
+        for (int b = 0; b < P::RING; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(geo_full + b)), "r"(1) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(geo_empty + b)), "r"(1) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         *abort_flag = 0;
     }
@@ -384,23 +435,112 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp >= 3) {
+    if (GEO && warp >= TC_GEO_WARP) {
+        // ------------------------------------------------------------ geometry
+        // one 1-D line per lane; the connectivity is read two elements ahead and
+        // the coordinates one, so that no load waits on another
+        if constexpr (GEO) {
+            const int gw_id = warp - TC_GEO_WARP;
+            double *gS = reinterpret_cast<double *>(smem + P::GS) + gw_id * P::GS_WARP;  // [4][81]
+            const double *gB = reinterpret_cast<const double *>(smem + P::GT);
+            const double *gDq = gB + 9;
+            const double *gw = gDq + 9 + GEO_DQ_EXTRA;
+            float *ring = reinterpret_cast<float *>(smem + P::JW);
+            double px[3] = {0.0, 0.0, 0.0};  // this lane's node of the next element
+            double plm = 0.0;                // lanes 27, 28: its lambda, mu
+            long long pnode = 0;             // this lane's node index of the element after
+            auto fetch_node = [&](long long e) {
+                if (e < E && lane < TC_N) pnode = geo.conn[e * TC_N + lane];
+            };
+            auto fetch = [&](long long e) {  // with pnode = the node of element e
+                if (e >= E) return;
+                if (lane < TC_N) {
+                    const bool ok = (unsigned long long)pnode < (unsigned long long)geo.n_nodes;  // never read outside
+                    if (!ok) fe_report(status, FE_ERR_SHAPE, e);
+                    const long long nd = ok ? pnode : 0;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) px[c] = geo.coords[3 * nd + c];
+                } else if (lane < TC_N + 2) {
+                    plm = lame[2 * e + lane - TC_N];
+                }
+            };
+            // element n of this CTA goes to geometry warp n % TC_NGEO, ring slot n % RING
+            const long long stride = (long long)gridDim.x * TC_NGEO;
+            long long e = blockIdx.x + (long long)gw_id * gridDim.x;
+            fetch_node(e);
+            fetch(e);
+            fetch_node(e + stride);
+            for (int n = gw_id; e < E; e += stride, n += TC_NGEO) {
+                const int sl = n % P::RING;
+                float *slot = ring + sl * P::SLOT;
+                // the slot is free once the producers have read its previous element
+                if (n >= P::RING) {
+                    if (lane == 0 &&
+                        !mbar_wait_bounded(smem_u32(geo_empty + sl), ((n / P::RING) - 1) & 1, abort_flag)) {
+                        *abort_flag = 1;
+                        fe_report(status, FE_ERR_TIMEOUT, e);
+                    }
+                    __syncwarp();
+                    if (*abort_flag) break;
+                }
+                if (lane < TC_N) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) gS[c * TC_N + lane] = px[c];
+                }
+                const float lm = (float)plm;
+                fetch(e + stride);
+                fetch_node(e + 2 * stride);
+                __syncwarp();
+                if (lane < TC_N) geo_lines_x<3, true>(lane, gS, gS + 81, gB);  // contract i
+                __syncwarp();
+                if (lane < TC_N) geo_lines_y<3, true>(lane, gS + 81, gS + 162, gB);  // contract j
+                __syncwarp();
+                if (lane < TC_N) geo_lines_z<3, true>(lane, gS + 162, gS, gB);  // contract k: x at the points
+                __syncwarp();
+                // J on the points: 81 lines, three per lane (the third for lanes < 17)
+                geo_lines_jacobian<3, true>(lane, gS, gS + 81, gDq);
+                geo_lines_jacobian<3, true>(lane + 32, gS, gS + 81, gDq);
+                if (lane + 64 < 3 * TC_N) geo_lines_jacobian<3, true>(lane + 64, gS, gS + 81, gDq);
+                __syncwarp();
+                if (lane < TC_Q) {
+                    float o[9], wd;
+                    const double det = geo_point_f32(gS + 81 + lane * 9, gw[lane], o, wd);
+                    const int bad = geo_det_status(det);
+                    if (bad) fe_report(status, bad, e);
+                    const long long idx = e * TC_Q + lane;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) geo.jinv_out[idx * 9 + k] = o[k];
+                    geo.wdetj_out[idx] = wd;
+                    const float sw = sqrtf(wd);
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) slot[lane * TC_JW_STRIDE + k] = sw * o[k];
+                } else if (lane < TC_Q + 2) {
+                    slot[TC_Q * TC_JW_STRIDE + lane - TC_Q] = lm;
+                }
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(geo_full + sl))
+                                            : "memory");
+            }
+        }
+    } else if (warp >= 3) {
         // ------------------------------------------------------------ producer
         const int ptid = tid - TC_CONS, pw = warp - 3;
         constexpr int NPF = (TC_Q * 9 + TC_PROD - 1) / TC_PROD;  // 3 per thread
         float pj[NPF], pwt[NPF];
         double plm = 0.0;
         auto prefetch = [&](long long e) {
-            if (e >= E) return;
+            if constexpr (!GEO) {
+                if (e >= E) return;
 #pragma unroll
-            for (int u = 0; u < NPF; ++u) {
-                const int t = ptid + u * TC_PROD;
-                if (t < TC_Q * 9) {
-                    pj[u] = jinv[e * TC_Q * 9 + t];
-                    pwt[u] = wdetj[e * TC_Q + t / 9];
+                for (int u = 0; u < NPF; ++u) {
+                    const int t = ptid + u * TC_PROD;
+                    if (t < TC_Q * 9) {
+                        pj[u] = jinv[e * TC_Q * 9 + t];
+                        pwt[u] = wdetj[e * TC_Q + t / 9];
+                    }
                 }
+                if (ptid < 2) plm = lame[2 * e + ptid];
             }
-            if (ptid < 2) plm = lame[2 * e + ptid];
         };
         prefetch(blockIdx.x);
         constexpr int SEGV = 4 / P::EB;            // points per 4-byte segment: 1 (tf32) or 2 (bf16)
@@ -423,10 +563,21 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
         int last_b = -1;  // thread 0: buffer and phase parity of the last MMA commit
         uint32_t last_parity = 0;
         for (long long e = blockIdx.x; e < E; e += gridDim.x, ++n) {
+            const int sl = GEO ? n % (GEO ? P::RING : 1) : 0;  // GEO: ring slot of element n
+            if constexpr (GEO) {
+                // (a) the geometry warp's ring slot of element n
+                if (ptid == 0 && !mbar_wait_bounded(smem_u32(geo_full + sl), (n / (GEO ? P::RING : 1)) & 1,
+                                                    abort_flag)) {
+                    *abort_flag = 1;
+                    fe_report(status, FE_ERR_TIMEOUT, e);
+                }
+                named_sync(TC_BAR_PROD, TC_PROD);
+                if (*abort_flag) break;
+            }
             const int b = n & 1;
             unsigned char *opHi = smem + b * P::BUF + P::HI;
             unsigned char *opLo = smem + b * P::BUF + P::LO;
-            float *jw = sJw + b * TC_Q * TC_JW_STRIDE;
+            float *jw = GEO ? sJw + sl * P::SLOT : sJw + b * TC_Q * TC_JW_STRIDE;
             // the buffer and its accumulator are free once element n-2's epilogue is done
             if (n >= 2) {
                 if (ptid == 0 && !mbar_wait_bounded(smem_u32(empty + b), ((n >> 1) - 1) & 1, abort_flag)) {
@@ -437,15 +588,20 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
                 if (*abort_flag) break;
                 tc_fence_after();
             }
-            // (a) geometry of the element, then start fetching the next one
+            if constexpr (GEO) {
+                // the Lame pair for the consumers
+                if (ptid < 2) sLM[2 * b + ptid] = jw[TC_Q * TC_JW_STRIDE + ptid];
+            } else {
+                // (a) geometry of the element, then start fetching the next one
 #pragma unroll
-            for (int u = 0; u < NPF; ++u) {
-                const int t = ptid + u * TC_PROD;
-                if (t < TC_Q * 9) jw[(t / 9) * TC_JW_STRIDE + t % 9] = sqrtf(pwt[u]) * pj[u];
+                for (int u = 0; u < NPF; ++u) {
+                    const int t = ptid + u * TC_PROD;
+                    if (t < TC_Q * 9) jw[(t / 9) * TC_JW_STRIDE + t % 9] = sqrtf(pwt[u]) * pj[u];
+                }
+                if (ptid < 2) sLM[2 * b + ptid] = (float)plm;
+                prefetch(e + gridDim.x);
+                named_sync(TC_BAR_PROD, TC_PROD);
             }
-            if (ptid < 2) sLM[2 * b + ptid] = (float)plm;
-            prefetch(e + gridDim.x);
-            named_sync(TC_BAR_PROD, TC_PROD);
 
             // (b) X[(j,a)][q] split into hi/lo: lane (r, seg) owns node a = 8 g + r and
             // the points of its 4-byte segment, for the three row blocks j; warp pw
@@ -503,6 +659,8 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
             }
             fence_async_smem();  // operand writes -> tensor-core (async) proxy
             named_sync(TC_BAR_PROD, TC_PROD);
+            if (GEO && ptid == 0)  // the ring slot has been read: back to the geometry warp
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(geo_empty + sl)) : "memory");
 
             // (c) MMA chain into the accumulator once the consumers have read out
             // element n-1's: D = sum over K steps of hi*hi (+ hi*lo + lo*hi)
@@ -629,15 +787,19 @@ __global__ void __launch_bounds__(TC_THREADS_WS, MODE == TC_TF32X3 ? 2 : 3) k_ma
                      : "memory");
 }
 
-template <int MODE>
+template <int MODE, bool GEO>
 cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int sm_count,
                       unsigned long long *status, const int *hold, cudaStream_t s)
 {
-    using P = TcSmem<MODE>;
+    using P = TcSmem<MODE, GEO>;
     static_assert(P::BYTES <= 227 * 1024, "shared memory plan too large");
-    auto kern = k_matrix_tc<MODE>;
+    static_assert(MODE == TC_TF32X3 || 3 * (P::BYTES + 1024) <= 228 * 1024, "three CTAs per SM in the BF16 modes");
+    constexpr int NTHREADS = TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0);
+    auto kern = k_matrix_tc<MODE, GEO>;
     // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA),
-    // registers, and the 512 tensor-memory columns of which every CTA holds TC_TMEM_COLS
+    // registers, and the 512 tensor-memory columns of which every CTA holds
+    // NACC x TC_TMEM_COLS (a persistent CTA waiting for columns would stall in
+    // tcgen05.alloc)
     static FeLaunchCache cache;
     long long per_sm = 0;
     cudaError_t err = fe_cached_grid(
@@ -654,7 +816,9 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
             e2 = cudaFuncGetAttributes(&fa, kern);
             if (e2 != cudaSuccess) return e2;
             int n = smem_sm / (P::BYTES + 1024);
-            const int by_regs = regs_sm / (((fa.numRegs + 7) / 8 * 8) * TC_THREADS_WS);
+            // registers: whole warps in each of the four sub-partitions (regs_sm / 4 each)
+            const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
+            const int by_regs = 4 * ((regs_sm / 4) / warp_regs) / (NTHREADS / 32);
             if (by_regs < n) n = by_regs;
             if (n * P::NACC * TC_TMEM_COLS > 512) n = 512 / (P::NACC * TC_TMEM_COLS);
             if (n < 1) return cudaErrorInvalidConfiguration;
@@ -665,23 +829,55 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
     if (err != cudaSuccess) return err;
     long long blocks = per_sm * sm_count;
     if (blocks > g->mesh.n_elems) blocks = g->mesh.n_elems;
-    kern<<<(unsigned)blocks, TC_THREADS_WS, P::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->mesh.n_elems,
-                                                        mat.data, (float *)K, status, hold);
+    TcGeoArgs geo{};
+    if (GEO) {
+        geo.coords = g->mesh.coords;
+        geo.conn = g->mesh.conn;
+        geo.n_nodes = g->mesh.n_nodes;
+        geo.b1d = g->d_b1d;
+        geo.dq = g->d_dq;
+        geo.w = g->d_w64;
+        geo.jinv_out = g->d_jinv32;
+        geo.wdetj_out = g->d_wdetj32;
+    }
+    kern<<<(unsigned)blocks, NTHREADS, P::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->mesh.n_elems,
+                                                      mat.data, (float *)K, status, hold, geo);
     return cudaGetLastError();
+}
+
+template <bool GEO>
+cudaError_t dispatch_tc(const fe_geometry_h *g, fe_material_args mat, fe_precision prec, void *K, int sm_count,
+                        unsigned long long *status, const int *hold, cudaStream_t s)
+{
+    switch (prec) {
+    case FE_TF32X3: return launch_tc<TC_TF32X3, GEO>(g, mat, K, sm_count, status, hold, s);
+    case FE_BF16X3: return launch_tc<TC_BF16X3, GEO>(g, mat, K, sm_count, status, hold, s);
+    case FE_BF16: return launch_tc<TC_BF16, GEO>(g, mat, K, sm_count, status, hold, s);
+    default: return cudaErrorNotSupported;
+    }
 }
 
 }  // namespace
 
+bool fe_matrix_tc_geometry_fusable(const fe_geometry_h *g)
+{
+    // a stale deferred handle keeping only the float32 copy, Q2 with 3 x 3 x 3
+    // Gauss points whose middle point is the middle node (collocation stages)
+    return g->pending && g->d_dq && g->geo_center && g->n1d == 3 && g->nq1d == 3 && g->N == TC_N &&
+           g->Q == TC_Q && g->d_jinv32 && !g->is_view && (g->flags & FE_GEOM_STORE_F32) &&
+           !(g->flags & FE_GEOM_STORE_F64);
+}
+
 cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
-                                void *K, int sm_count, unsigned long long *status, const int *hold, cudaStream_t s)
+                                void *K, int sm_count, unsigned long long *status, const int *hold,
+                                bool with_geometry, cudaStream_t s)
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
     if (f->kind != FK_ELASTICITY || mat.kind != FE_MAT_LAME || g->N != TC_N || g->Q != TC_Q)
         return cudaErrorNotSupported;
-    switch (prec) {
-    case FE_TF32X3: return launch_tc<TC_TF32X3>(g, mat, K, sm_count, status, hold, s);
-    case FE_BF16X3: return launch_tc<TC_BF16X3>(g, mat, K, sm_count, status, hold, s);
-    case FE_BF16: return launch_tc<TC_BF16>(g, mat, K, sm_count, status, hold, s);
-    default: return cudaErrorNotSupported;
+    if (with_geometry) {
+        if (!fe_matrix_tc_geometry_fusable(g)) return cudaErrorNotSupported;
+        return dispatch_tc<true>(g, mat, prec, K, sm_count, status, hold, s);
     }
+    return dispatch_tc<false>(g, mat, prec, K, sm_count, status, hold, s);
 }

@@ -31,9 +31,9 @@ def _sample(E, seed, k=62):
 
 
 def test_metric_workload_full_size(ctx):
-    """48^3 Q2 elasticity (110,592 elements), the benchmark's step: deferred FP64
-    geometry computed by the residual kernel, BF16x3 tensor-core K_e, compensated
-    assembly."""
+    """48^3 Q2 elasticity (110,592 elements), the benchmark's step: the BF16x3
+    tensor-core kernel computing the deferred FP64 geometry, the FP32 residual on
+    its stored copy, compensated assembly."""
     mesh, lam, mu, u = meshgen.elasticity_q2_cube(48, seed=1)
     E = mesh.n_elems
     m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
@@ -42,8 +42,8 @@ def test_metric_workload_full_size(ctx):
     mat = _t(np.stack([lam, mu], 1), torch.float64)
     u32 = _t(u, torch.float32)
     geom.update()
-    r = fe.eval_residual(ctx, form, geom, [mat, None, u32], "bf16x3")
     K = fe.eval_matrix(ctx, form, geom, [mat, None, None], "bf16x3")
+    r = fe.eval_residual(ctx, form, geom, [mat, None, u32], "bf16x3")
     g = fe.assemble_vector(ctx, fe.assembly_create(ctx, m), 3, r, "f32", flags=fe.ASSEMBLE_COMPENSATED)
     ctx.check()
     idx = _sample(E, 7)
@@ -76,9 +76,9 @@ def _elementwise_rel_errors(Kg, Kref):
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 def test_metric_workload_every_element(ctx, prec):
-    """48^3 Q2 elasticity, the benchmark's step (deferred FP64 geometry computed by
-    the residual kernel, FP32 r_e, split-precision tensor-core K_e): all 110,592
-    element matrices against the oracle, each within the 1e-5 bar
+    """48^3 Q2 elasticity, the benchmark's step (the split-precision tensor-core
+    kernel computing the deferred FP64 geometry, the FP32 residual on its stored
+    copy): all 110,592 element matrices against the oracle, each within the 1e-5 bar
     (max_e ||K_e - K_ref||_F / ||K_ref||_F), and the residual array within 1e-5
     (||r - r_ref||_2 / ||r_ref||_2), in chunks of 13,824 elements."""
     mesh, lam, mu, u = meshgen.elasticity_q2_cube(48, seed=1)
@@ -88,8 +88,8 @@ def test_metric_workload_every_element(ctx, prec):
     form = fe.elasticity_form()
     mat = _t(np.stack([lam, mu], 1), torch.float64)
     geom.update()
-    r = fe.eval_residual(ctx, form, geom, [mat, None, _t(u, torch.float32)], prec)
     K = fe.eval_matrix(ctx, form, geom, [mat, None, None], prec)
+    r = fe.eval_residual(ctx, form, geom, [mat, None, _t(u, torch.float32)], prec)
     ctx.check()
     ref = oracle.RefElement(2, 3)
     worst, r_num, r_den = 0.0, 0.0, 0.0
@@ -189,9 +189,9 @@ def test_element_matrices_past_2_31_entries(ctx):
     """70^3 Q2 elasticity (343,000 elements): K holds 2.25e9 entries; element
     327,310 straddles entry 2^31 and the later ones start past it (byte 2^33 in
     float32, 2^34 in FP64);
-    the benchmark's step (deferred geometry, BF16x3 tensor-core K_e, compensated
-    assembly), the float32 CUDA-core and the FP64 matrix kernels, sampled on both
-    sides of that boundary against the oracle."""
+    the benchmark's step (the BF16x3 tensor-core kernel computing the deferred
+    geometry, the residual, compensated assembly), the float32 CUDA-core and the
+    FP64 matrix kernels, sampled on both sides of that boundary against the oracle."""
     mesh, lam, mu, u = meshgen.elasticity_q2_cube(70, seed=5)
     E = mesh.n_elems
     first_past = -(-(2 ** 31) // (81 * 81))  # first element starting past entry 2^31
@@ -211,8 +211,8 @@ def test_element_matrices_past_2_31_entries(ctx):
 
     gd = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
     gd.update()
-    r = fe.eval_residual(ctx, form, gd, [mat, None, u32], "bf16x3")
     K = fe.eval_matrix(ctx, form, gd, [mat, None, None], "bf16x3")
+    r = fe.eval_residual(ctx, form, gd, [mat, None, u32], "bf16x3")
     g = fe.assemble_vector(ctx, fe.assembly_create(ctx, m), 3, r, "f32", flags=fe.ASSEMBLE_COMPENSATED)
     ctx.check()
     assert rel_matrix_error(K.index_select(0, it).cpu().numpy(), Kref) <= TOL["bf16x3"]

@@ -153,10 +153,11 @@ def test_nonpositive_detj_is_reported(ctx):
     assert ctx.status() == (fe.FE_OK, -1)  # cleared
 
 
-@pytest.mark.parametrize("path", ["geometry", "residual"])
+@pytest.mark.parametrize("path", ["geometry", "residual", "matrix"])
 def test_degenerate_and_nonfinite_geometry_are_reported(ctx, path):
     """det J = 0 exactly (an element collapsed to a point) and a NaN coordinate, from
-    the geometry kernel and from the residual kernel that computes a stale geometry."""
+    the geometry kernel and from the residual and tensor-core matrix kernels that
+    compute a stale geometry."""
     mesh = meshgen.structured_hex(1, 1, 1, 2, 0.0, 0)
     lm = _t(np.ones((1, 2)), torch.float64)
     u = _t(np.zeros(3 * mesh.n_nodes), torch.float32)
@@ -170,9 +171,12 @@ def test_degenerate_and_nonfinite_geometry_are_reported(ctx, path):
         ctx.status()
         if path == "geometry":
             fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32)
-        else:
+        elif path == "residual":
             lazy = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
             fe.eval_residual(ctx, fe.elasticity_form(), lazy, [lm, None, u], "f32")
+        else:
+            lazy = fe.hex_geometry(ctx, m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+            fe.eval_matrix(ctx, fe.elasticity_form(), lazy, [lm, None, None], "bf16x3")
         assert ctx.status() == (code, 0)
 
 
@@ -298,6 +302,37 @@ def test_tensor_core_pipeline_many_elements_per_cta(ctx, prec, tol):
     err = rel_matrix_error(K.cpu().numpy(), Kref)
     assert err <= tol, err
     assert rel_vector_error(r.cpu().numpy(), rref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("prec,tol", TC_TOL)
+def test_tensor_core_kernel_computes_stale_geometry(ctx, prec, tol):
+    """fe_eval_matrix first on a stale float32-only deferred handle: the geometry
+    warp of the tensor-core kernel computes the FP64 geometry (5,184 elements, 11-12
+    per CTA, so that the ring of geometry slots wraps around).  The stored float32
+    copy equals the geometry kernel's bit for bit, K_e equals the kernel on the
+    eager geometry bit for bit and matches the oracle, and the residual that follows
+    on the now computed handle equals the eager path's."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (18, 18, 16), 87)
+    E = P.mesh.n_elems
+    assert E == 5184 and E > 11 * 152 * 3
+    eager = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32)
+    lazy = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    args = [_t(mat, torch.float64), None, _t(u, torch.float32)]
+    for _ in range(2):  # a second update re-marks the handle stale
+        lazy.update()
+        K_l = fe.eval_matrix(ctx, form, lazy, args, prec)
+    r_l = fe.eval_residual(ctx, form, lazy, args, "f32")
+    K_e = fe.eval_matrix(ctx, form, eager, args, prec)
+    r_e = fe.eval_residual(ctx, form, eager, args, "f32")
+    ctx.check()
+    np.testing.assert_array_equal(lazy.get(fe.GEOM_WDETJ, "f32").cpu().numpy(),
+                                  eager.get(fe.GEOM_WDETJ, "f32").cpu().numpy())
+    np.testing.assert_array_equal(lazy.get(fe.GEOM_JINV, "f32").cpu().numpy(),
+                                  eager.get(fe.GEOM_JINV, "f32").cpu().numpy())
+    assert torch.equal(K_l, K_e)
+    assert torch.equal(r_l, r_e)
+    assert rel_matrix_error(K_l.cpu().numpy(), Kref) <= tol
+    assert rel_vector_error(r_l.cpu().numpy(), rref) <= TOL["f32"]
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "bf16"])
@@ -433,6 +468,27 @@ def test_tensor_core_wait_timeout_is_reported_and_the_context_recovers(ctx, prec
     K = fe.eval_matrix(ctx, form, P.geom, args, prec)
     ctx.check()
     assert rel_matrix_error(K.cpu().numpy(), Kref) <= TOL[prec]
+
+
+def test_tensor_core_timeout_with_the_geometry_warp(ctx):
+    """The same bounded wait in the kernel that computes a stale geometry: the
+    consumers wait on a flag that nothing sets, the geometry warp and the producers
+    give up too, FE_ERR_TIMEOUT is reported; after fe_geometry_update (the aborted
+    launch left the deferred geometry undefined) the next launch is a normal one."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 2, (10, 10, 10), 98)
+    args = [_t(mat, torch.float64), None, None]
+    lazy = fe.hex_geometry(ctx, P.m, 2, 3, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    ctx.status()
+    fe.debug_hold_next_matrix(ctx)
+    t0 = time.time()
+    fe.eval_matrix(ctx, form, lazy, args, "bf16x3")
+    st, bad = ctx.status()
+    assert st == fe.FE_ERR_TIMEOUT and bad >= 0
+    assert time.time() - t0 < 60
+    lazy.update()
+    K = fe.eval_matrix(ctx, form, lazy, args, "bf16x3")
+    ctx.check()
+    assert rel_matrix_error(K.cpu().numpy(), Kref) <= TOL["bf16x3"]
 
 
 def test_tensor_core_paths_reject_other_forms(ctx):
