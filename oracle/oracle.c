@@ -791,6 +791,78 @@ int oracle_residual_stokes_t(long long n_elems, int N, int Q, const int32_t *con
     return OR_OK;
 }
 
+/* Stokes coupling 'i.i,0' between fields of different orders (Tab. ewfd; Sec. 5
+ * names the coupling of fields, which SfePy lets carry different orders): a
+ * vector field on the geometry's basis (N nodes, physical gradients G) and a
+ * scalar field on a second basis over the same elements (Np nodes, values psi
+ * (Q, Np) at the same quadrature points, DOFs through its own connectivity),
+ * e.g. a Q2 velocity with a Q1 pressure or P2 with P1:
+ *   B[(i,a), b] = sum_q wdetJ G[i][a] psi_b                     (rows 3N, columns Np)
+ *   r[(i,a)]    = sum_q wdetJ G[i][a] p_h,  p_h = sum_b psi_b p[conn_p[e][b]]
+ *   rt[b]       = sum_q wdetJ psi_b div(u_h), u_h on the geometry's basis via conn
+ * (the transposed coupling 'i.i,0' (u, q) has the matrix B^T). */
+int oracle_matrix_stokes_mixed(long long n_elems, int N, int Np, int Q, const double *wdetJ, const double *G,
+                               const double *psi, double *B)
+{
+    if (n_elems < 0 || !wdetJ || !G || !psi || !B) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e)
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < Np; ++b) {
+                    double s = 0.0;
+                    for (int q = 0; q < Q; ++q)
+                        s += wdetJ[(size_t)e * Q + q] * G[(((size_t)e * Q + q) * 3 + i) * N + a] *
+                             psi[(size_t)q * Np + b];
+                    B[(size_t)e * 3 * N * Np + (size_t)(i * N + a) * Np + b] = s;
+                }
+    return OR_OK;
+}
+
+int oracle_residual_stokes_mixed(long long n_elems, int N, int Np, int Q, const int32_t *conn_p,
+                                 const double *wdetJ, const double *G, const double *psi, const double *p,
+                                 double *r)
+{
+    if (n_elems < 0 || Np > 512 || !conn_p || !wdetJ || !G || !psi || !p || !r) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double pe[512];
+        gather_scalar(Np, conn_p + (size_t)e * Np, p, pe);
+        double *re = r + (size_t)e * 3 * N;
+        for (int c = 0; c < 3 * N; ++c) re[c] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            double ph = 0.0;
+            for (int b = 0; b < Np; ++b) ph += psi[(size_t)q * Np + b] * pe[b];
+            const double wd = wdetJ[(size_t)e * Q + q];
+            for (int i = 0; i < 3; ++i)
+                for (int a = 0; a < N; ++a) re[i * N + a] += wd * G[(((size_t)e * Q + q) * 3 + i) * N + a] * ph;
+        }
+    }
+    return OR_OK;
+}
+
+int oracle_residual_stokes_t_mixed(long long n_elems, int N, int Np, int Q, const int32_t *conn,
+                                   const double *wdetJ, const double *G, const double *psi, const double *u,
+                                   double *r)
+{
+    if (n_elems < 0 || N > 512 || !conn || !wdetJ || !G || !psi || !u || !r) return OR_BAD_ARG;
+#pragma omp parallel for schedule(static)
+    for (long long e = 0; e < n_elems; ++e) {
+        double ue[3 * 512];
+        gather_vec(N, conn + (size_t)e * N, u, ue);
+        double *re = r + (size_t)e * Np;
+        for (int b = 0; b < Np; ++b) re[b] = 0.0;
+        for (int q = 0; q < Q; ++q) {
+            double div = 0.0;
+            for (int i = 0; i < 3; ++i)
+                for (int a = 0; a < N; ++a) div += ue[i * N + a] * G[(((size_t)e * Q + q) * 3 + i) * N + a];
+            const double wd = wdetJ[(size_t)e * Q + q];
+            for (int b = 0; b < Np; ++b) re[b] += wd * psi[(size_t)q * Np + b] * div;
+        }
+    }
+    return OR_OK;
+}
+
 /* 'eval' mode: the integral over each element of a form whose operands all
  * carry DOFs (Sec. 5.1, evaluation modes), out (E, n_out):
  *   kind 0 Laplace      c sum_q wdetJ grad u . grad w           (scalar fields)

@@ -65,6 +65,12 @@ def lib():
         L.oracle_residual_stokes.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D, _D]
         L.oracle_residual_stokes_t.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, _D, _D, _D,
                                                _D]
+        L.oracle_matrix_stokes_mixed.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                                 _D, _D]
+        L.oracle_residual_stokes_mixed.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I,
+                                                   _D, _D, _D, _D, _D]
+        L.oracle_residual_stokes_t_mixed.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                     _I, _D, _D, _D, _D, _D]
         L.oracle_eval_form.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int, _I,
                                        _D, _D, _D, _D, _D, _D, _D, _D, _D]
         L.oracle_assemble.argtypes = [ctypes.c_longlong, ctypes.c_int, ctypes.c_int, _I, _D, ctypes.c_longlong,
@@ -344,6 +350,41 @@ def residual_stokes_t(conn, wdetJ, G, phi, u):
     conn = np.ascontiguousarray(conn, dtype=np.int32)
     r = np.zeros((E, N))
     _check(lib().oracle_residual_stokes_t(E, N, Q, _i(conn), _d(wdetJ), _d(G), _d(_f64(phi)), _d(_f64(u)), _d(r)))
+    return r
+
+
+def matrix_stokes_mixed(wdetJ, G, psi):
+    """Stokes coupling 'i.i,0' of a vector field on the geometry's basis (G: E, Q, 3, N)
+    and a scalar field on a second basis (psi: Q, Np at the same points):
+    B[(i,a), b] = sum_q wdetJ G[i][a] psi_b, shape (E, 3N, Np); the transposed
+    coupling has B^T."""
+    E, Q, _, N = G.shape
+    psi = _f64(psi)
+    Np = psi.shape[1]
+    B = np.zeros((E, 3 * N, Np))
+    _check(lib().oracle_matrix_stokes_mixed(E, N, Np, Q, _d(wdetJ), _d(G), _d(psi), _d(B)))
+    return B
+
+
+def residual_stokes_mixed(conn_p, wdetJ, G, psi, p):
+    """r[(i,a)] = sum_q wdetJ G[i][a] p_h, p_h = sum_b psi_b p[conn_p[e][b]]."""
+    E, Q, _, N = G.shape
+    psi = _f64(psi)
+    conn_p = np.ascontiguousarray(conn_p, dtype=np.int32)
+    r = np.zeros((E, 3 * N))
+    _check(lib().oracle_residual_stokes_mixed(E, N, psi.shape[1], Q, _i(conn_p), _d(wdetJ), _d(G), _d(psi),
+                                              _d(_f64(p)), _d(r)))
+    return r
+
+
+def residual_stokes_t_mixed(conn, wdetJ, G, psi, u):
+    """r[b] = sum_q wdetJ psi_b div(u_h), u_h on the geometry's basis via conn."""
+    E, Q, _, N = G.shape
+    psi = _f64(psi)
+    conn = np.ascontiguousarray(conn, dtype=np.int32)
+    r = np.zeros((E, psi.shape[1]))
+    _check(lib().oracle_residual_stokes_t_mixed(E, N, psi.shape[1], Q, _i(conn), _d(wdetJ), _d(G), _d(psi),
+                                                _d(_f64(u)), _d(r)))
     return r
 
 

@@ -228,6 +228,23 @@ def tet_mesh(target: int, p: int, rng: np.random.Generator) -> TetMesh:
                    rng=rng)
 
 
+def vertex_connectivity(mesh):
+    """Connectivity of the order-1 field on the vertices of an order-p mesh (the
+    scalar field of a mixed-order pair, e.g. a Q1 or P1 pressure beside a Q2 or P2
+    velocity): (E, 8) for hexahedra in the reference order of Q1 nodes (x fastest),
+    numbered on the (nx+1)(ny+1)(nz+1) vertex grid; (E, 4) for tetrahedra in the P1
+    lattice order, numbered like the mesh's vertex nodes (which come first).
+    Returns (conn, n_vertices).  Topology only."""
+    if isinstance(mesh, TetMesh):
+        L = _lattice(mesh.order)
+        loc = [int(np.where(L[:, b] == mesh.order)[0][0]) for b in range(4)]
+        conn = np.ascontiguousarray(mesh.conn[:, loc])
+        return conn, int(conn.max()) + 1 if conn.size else 0
+    nx, ny, nz = mesh.shape
+    q1 = structured_hex(nx, ny, nz, 1)
+    return q1.conn, q1.n_nodes
+
+
 def mixed_mesh_groups(scale: float = 1.0, seed: int = 2):
     """The mixed-element workload: P1, P2, P3 tetrahedra (200k, 120k, 40k,
     Delaunay meshes drawn from one stream of seed `seed` in that order) and Q1,

@@ -154,3 +154,16 @@ def box_stokes_blocks(p, h):
     m, d, xm, xd = moments_1d(p)
     h = np.asarray(h, dtype=float)
     return [_kron3(*[d.T if e == i else m * h[e] for e in range(3)]) for i in range(3)]
+
+
+def box_stokes_mixed_blocks(pu, pp, h):
+    """B_i[a][b] = int_box (d phi_a / d x_i) psi_b with phi of order pu and psi of
+    order pp (equispaced Lagrange, tensor products): on axis i the factor
+    int L_a^(pu)' L_b^(pp) (the 1/h and h cancel), int L_a^(pu) L_b^(pp) h elsewhere."""
+    Lu, Lp = lagrange_polys(pu), lagrange_polys(pp)
+    dLu = [_pder(x) for x in Lu]
+    f = lambda M: np.array([[float(x) for x in row] for row in M])
+    mm = f([[_pint01(_pmul(Lu[a], Lp[b])) for b in range(pp + 1)] for a in range(pu + 1)])
+    dm = f([[_pint01(_pmul(dLu[a], Lp[b])) for b in range(pp + 1)] for a in range(pu + 1)])
+    h = np.asarray(h, dtype=float)
+    return [_kron3(*[dm if e == i else mm * h[e] for e in range(3)]) for i in range(3)]

@@ -762,3 +762,82 @@ def test_eval_mode_equals_bilinear_form_of_the_matrices(distorted):
     ue = np.concatenate([u3[3 * mesh.conn + i] for i in range(3)], 1)
     we = np.concatenate([w3[3 * mesh.conn + i] for i in range(3)], 1)
     np.testing.assert_allclose(e2, np.einsum("ea,eab,eb->e", we, KE, ue), rtol=1e-11, atol=1e-13)
+
+
+# -- mixed-order Stokes pair (Q2/Q1, P2/P1) ------------------------------------------------
+
+def test_mixed_order_stokes_on_box_matches_exact_integrals():
+    """Q2 velocity, Q1 pressure on a box: B_i[a][b] = int d_i phi_a psi_b from exact
+    rational 1-D integrals of the two Lagrange bases; the residual of the coupling
+    is B p_e and that of the transposed coupling sum_i B_i^T u_i."""
+    h = (0.5, 0.7, 1.3)
+    mesh = meshgen.structured_hex(1, 1, 1, 2, 0.0, 0, lengths=h)
+    mesh.coords[:] += np.array([0.25, -1.0, 3.0])
+    ref_u, ref_p = oracle.RefElement(2, 3), oracle.RefElement(1, 3)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref_u)
+    Bs = exact_fe.box_stokes_mixed_blocks(2, 1, h)
+    want = np.concatenate(Bs, 0)
+    B = oracle.matrix_stokes_mixed(wdetJ, G, ref_p.phi)[0]
+    assert B.shape == (81, 8)
+    assert np.abs(B - want).max() <= 1e-13 * np.abs(want).max()
+    conn_p, n_p = meshgen.vertex_connectivity(mesh)
+    assert conn_p.shape == (1, 8) and n_p == 8
+    rng = np.random.default_rng(5)
+    p = rng.standard_normal(n_p)
+    rs = oracle.residual_stokes_mixed(conn_p, wdetJ, G, ref_p.phi, p)[0]
+    np.testing.assert_allclose(rs, want @ p[conn_p[0]], atol=1e-12)
+    u = rng.standard_normal(3 * mesh.n_nodes)
+    rt = oracle.residual_stokes_t_mixed(mesh.conn, wdetJ, G, ref_p.phi, u)[0]
+    ue = u.reshape(-1, 3)[mesh.conn[0]]
+    np.testing.assert_allclose(rt, sum(Bs[i].T @ ue[:, i] for i in range(3)), atol=1e-12)
+
+
+def test_mixed_order_stokes_with_equal_bases_is_the_stokes_coupling():
+    """With the velocity's own basis as the second basis the mixed functions are the
+    equal-order coupling, bit for bit (the same sums in the same order)."""
+    mesh = meshgen.structured_hex(2, 2, 1, 2, 0.15, 9)
+    ref = oracle.RefElement(2, 3)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    np.testing.assert_array_equal(oracle.matrix_stokes_mixed(wdetJ, G, ref.phi),
+                                  oracle.matrix_stokes(wdetJ, G, ref.phi))
+    rng = np.random.default_rng(6)
+    p, u = rng.standard_normal(mesh.n_nodes), rng.standard_normal(3 * mesh.n_nodes)
+    np.testing.assert_array_equal(oracle.residual_stokes_mixed(mesh.conn, wdetJ, G, ref.phi, p),
+                                  oracle.residual_stokes(mesh.conn, wdetJ, G, ref.phi, p))
+    np.testing.assert_array_equal(oracle.residual_stokes_t_mixed(mesh.conn, wdetJ, G, ref.phi, u),
+                                  oracle.residual_stokes_t(mesh.conn, wdetJ, G, ref.phi, u))
+
+
+@pytest.mark.parametrize("kind", ["Q2/Q1", "P2/P1"])
+def test_mixed_order_stokes_invariants_on_distorted_meshes(kind):
+    """Distorted Q2 hexahedra and Delaunay P2 tetrahedra with the order-1 pressure on
+    their vertices: sum_a B[(i,a), b] = 0 (sum_a d_i phi_a = 0); for a linear
+    velocity u = A x + c, div u = tr A, so the transposed residual sums to tr A times
+    the element volume (the basis psi sums to one, the rules integrate w det J
+    exactly), and on straight-sided tetrahedra each entry is tr A V_e / 4; r = B p_e
+    and r_T = B^T u_e."""
+    if kind == "Q2/Q1":
+        mesh = meshgen.structured_hex(3, 2, 2, 2, 0.15, 10)
+        ref_u, ref_p = oracle.RefElement(2, 3), oracle.RefElement(1, 3)
+    else:
+        mesh = meshgen.tet_mesh(40, 2, np.random.default_rng(11))
+        ref_u, ref_p = oracle.RefTet(2, 2), oracle.RefTet(1, 2)
+    conn_p, n_p = meshgen.vertex_connectivity(mesh)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref_u)
+    B = oracle.matrix_stokes_mixed(wdetJ, G, ref_p.phi)
+    E, N = mesh.n_elems, ref_u.N
+    scale = np.abs(B).max()
+    assert np.abs(B.reshape(E, 3, N, -1).sum(2)).max() <= 1e-13 * scale * N
+    rng = np.random.default_rng(12)
+    A, c = rng.standard_normal((3, 3)), rng.standard_normal(3)
+    u = (mesh.coords @ A.T + c).ravel()
+    rt = oracle.residual_stokes_t_mixed(mesh.conn, wdetJ, G, ref_p.phi, u)
+    vol = wdetJ.sum(1)
+    np.testing.assert_allclose(rt.sum(1), np.trace(A) * vol, rtol=1e-12, atol=1e-14)
+    if kind == "P2/P1":
+        np.testing.assert_allclose(rt, np.repeat(np.trace(A) * vol[:, None] / 4, 4, 1), rtol=1e-11, atol=1e-14)
+    ue = u.reshape(-1, 3)[mesh.conn].transpose(0, 2, 1).reshape(E, 3 * N)
+    np.testing.assert_allclose(rt, np.einsum("erb,er->eb", B, ue), rtol=1e-12, atol=1e-13 * np.abs(rt).max())
+    p = rng.standard_normal(n_p)
+    rs = oracle.residual_stokes_mixed(conn_p, wdetJ, G, ref_p.phi, p)
+    np.testing.assert_allclose(rs, np.einsum("erb,eb->er", B, p[conn_p]), rtol=1e-12, atol=1e-13 * np.abs(rs).max())
