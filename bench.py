@@ -96,9 +96,10 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=48, help="cube edge in elements (48 -> 110,592 hexes)")
-    ap.add_argument("--workload", choices=["elasticity", "convection", "mixed"], default="elasticity",
+    ap.add_argument("--workload", choices=["elasticity", "convection", "mixed", "fp64units"], default="elasticity",
                     help="convection: only the Navier-Stokes convection workload on an n^3 cube (both "
-                         "precisions); mixed: only the mixed-mesh batch; no oracle, one JSON line")
+                         "precisions); mixed: only the mixed-mesh batch; fp64units: the DFMA and FP64 MMA "
+                         "rates (fe_diag_fp64); no oracle, one JSON line")
     ap.add_argument("--scale", type=float, default=1.0, help="mixed workload: scale of every group")
     ap.add_argument("--prec", default="auto",
                     help="contraction precision of the headline path; auto = fastest of the ladder within 1e-5")
@@ -784,6 +785,37 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
     return out
 
 
+def fp64_units(device, steps=2048):
+    """FP64 rates of the device from fe_diag_fp64: DFMA chains and FP64 tensor-core
+    MMA chains (mma.sync m8n8k4), one CTA of W warps per SM, ILP independent chains
+    per lane; FMAs per clock per SM at the sampled clock, and TFLOP/s."""
+    import torch
+
+    from paper_2107_04121_gb300 import fe
+    ctx = fe.Context(device)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    out = torch.empty(sms * 32 * 32, dtype=torch.float64, device="cuda")
+    rows = []
+    with ClockSampler(device) as clk:
+        for kind, name, per_step in ((0, "dfma", 32), (1, "dmma_m8n8k4", 256)):
+            for warps, ilp in ((1, 1), (2, 1), (4, 1), (8, 1), (16, 1), (4, 2), (4, 4), (8, 4)):
+                fe.diag_fp64(ctx, kind, warps, ilp, steps, out)  # warm-up
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fe.diag_fp64(ctx, kind, warps, ilp, steps, out)
+                b.record()
+                b.synchronize()
+                ms = a.elapsed_time(b)
+                fmas = sms * warps * ilp * steps * per_step
+                rows.append({"kind": name, "warps_per_sm": warps, "ilp": ilp, "ms": ms,
+                             "tflops": 2 * fmas / (ms * 1e-3) / 1e12, "fma_per_clk_sm_at_2070": fmas / (ms * 1e-3) / sms
+                             / 2.07e9})
+    ctx.check()
+    ctx.close()
+    best = {k: max(r["tflops"] for r in rows if r["kind"] == k) for k in ("dfma", "dmma_m8n8k4")}
+    return {"rows": rows, "best_tflops": best, "clocks": clk.summary()}
+
+
 # ---- CPU oracle (baseline / reference arm) ------------------------------------------------
 
 def oracle_step(mesh, lam, mu, u, n_elems):
@@ -981,6 +1013,10 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
+    if args.workload == "fp64units":
+        if rank == 0:
+            print(json.dumps({"workload": "fp64units", **fp64_units(local)}), flush=True)
+        return
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     if args.workload in ("convection", "mixed"):
         if args.workload == "convection":

@@ -140,6 +140,7 @@ typedef struct fe_geometry_h fe_geometry_h;
 typedef struct fe_form_h fe_form_h;
 typedef struct fe_assembly_h fe_assembly_h;
 typedef struct fe_batch_h fe_batch_h;
+typedef struct fe_field_h fe_field_h;
 
 /* ---- context ------------------------------------------------------------- */
 
@@ -156,6 +157,16 @@ const char *fe_status_str(fe_status s);
  * the first device-detected error since the last call; *bad_elem (optional)
  * receives the smallest offending element index, or -1. */
 fe_status fe_get_status(fe_ctx *ctx, fe_stream_t stream, long long *bad_elem);
+
+/* Diagnostic with no counterpart in the paper: the FP64 rates that decide where
+ * the library computes in FP64.  Launches one CTA of `warps` warps (1..32) on
+ * every SM of the context's device; each lane runs `ilp` (1, 2 or 4)
+ * independent chains of `steps` (>= 1) dependent operations: kind 0 a DFMA
+ * (one lane-FMA per lane and step), kind 1 the FP64 tensor-core MMA
+ * mma.sync.m8n8k4 (256 FMAs per warp and step).  `out` is a caller-owned
+ * device array of (SM count x warps x 32) doubles that keeps the chains alive.
+ * The caller times the launch on `stream`.  Errors: FE_ERR_INVALID_ARG. */
+fe_status fe_diag_fp64(fe_ctx *ctx, int kind, int warps, int ilp, int steps, double *out, fe_stream_t stream);
 
 /* Library version as major*10000 + minor*100 + patch. */
 int fe_version(void);
@@ -332,6 +343,53 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
  * with the FE_F32 kernels.  Errors as fe_eval_matrix. */
 fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const void *const *args,
                            fe_precision prec, void *r_out, fe_stream_t stream);
+
+/* ---- fields of different orders (mixed-order pairs) ------------------------------ */
+
+/* A scalar field on a second basis over the elements of `geom`, for the Stokes
+ * coupling "i.i,0" (Tab. ewfd) between fields of different orders, e.g. a Q1
+ * pressure beside a Q2 velocity or P1 beside P2 (Taylor-Hood pairs; the
+ * coupling of two fields is the Stokes row of Tab. ewfd, and the paper's
+ * SfePy setting lets each field carry its own order).
+ *   psi      host array (Q, n_basis): the field's reference basis at the
+ *            quadrature points of `geom`, in the point order of the rule given to
+ *            fe_geometry (e.g. fe_refbasis_hex(1, 3, ...) beside a Q2 basis with
+ *            3 x 3 x 3 points; fe_refbasis_tet(1, s, ...) beside P2 with rule s);
+ *            copied
+ *   conn     device int32 (n_elems of geom, n_basis): the field's DOF numbering
+ *            per element, borrowed (must stay valid while the handle is used)
+ *   n_nodes  number of the field's DOFs
+ * Free with fe_field_free.  Errors: FE_ERR_INVALID_ARG (null arguments),
+ * FE_ERR_SHAPE (n_basis outside 1..64, n_nodes out of range), FE_ERR_OOM. */
+fe_status fe_field_create(fe_ctx *ctx, const fe_geometry_h *geom, const double *psi, int n_basis,
+                          const int32_t *conn, long long n_nodes, fe_field_h **out);
+fe_status fe_field_free(fe_field_h *field);
+
+/* Matrix mode of the Stokes coupling "i.i,0" whose scalar operand lives on
+ * `field` and whose vector operand on the basis of `geom`:
+ *   (VIRTUAL vector, STATE scalar)  K[e][(i,a)][b] = sum_q w det J G_q[i][a] psi_q[b],
+ *                                   K_out (n_elems, 3 N, n_basis of field)
+ *   (STATE vector, VIRTUAL scalar)  the transposed element matrices,
+ *                                   K_out (n_elems, n_basis of field, 3 N)
+ * with G = J^-T grad_xi phi of the geometry's basis (rows component-major like
+ * every vector element output).  diff_op must be the FE_STATE operand.
+ * FE_F64 or FE_F32 (output dtype as fe_eval_matrix).  Errors:
+ * FE_ERR_INVALID_ARG, FE_ERR_SHAPE (field of another mesh size or point count),
+ * FE_ERR_UNSUPPORTED_SPEC (other forms or precisions), FE_ERR_CUDA. */
+fe_status fe_eval_matrix_mixed(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const fe_field_h *field,
+                               const void *const *args, int diff_op, fe_precision prec, void *K_out,
+                               fe_stream_t stream);
+
+/* Residual mode of the same coupling: args[state operand] is the scalar field's
+ * DOF vector (field n_nodes; the rows of r_out (n_elems, 3 N) are the vector
+ * test function's) or, for the transposed coupling, the vector field's DOF
+ * vector (3 * mesh n_nodes; r_out (n_elems, n_basis of field)); float64 for
+ * FE_F64 else float32.  An out-of-range DOF index in either connectivity is
+ * reported as FE_ERR_SHAPE through fe_get_status.  Errors as
+ * fe_eval_matrix_mixed. */
+fe_status fe_eval_residual_mixed(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom,
+                                 const fe_field_h *field, const void *const *args, fe_precision prec, void *r_out,
+                                 fe_stream_t stream);
 
 /* Adjoint of residual mode (a vector-Jacobian product).  For an adjoint DOF
  * vector rbar (n_nodes * 3, device array, float64 for FE_F64 else float32),

@@ -492,6 +492,101 @@ fe_status fe_eval_residual(fe_ctx *ctx, const fe_form_h *form, const fe_geometry
     return from_cuda(e, "fe_eval_residual");
 }
 
+fe_status fe_field_create(fe_ctx *ctx, const fe_geometry_h *g, const double *psi, int n_basis, const int32_t *conn,
+                          long long n_nodes, fe_field_h **out)
+{
+    fe_clear_last_error();
+    if (!ctx || !g || !psi || !out || (!conn && g->mesh.n_elems > 0)) return FE_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_basis < 1 || n_basis > 64 || n_nodes < 0 || n_nodes > INT_MAX ||
+        g->mesh.n_elems * (long long)n_basis > INT_MAX)
+        return FE_ERR_SHAPE;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return from_cuda(e, "fe_field_create");
+    fe_field_h *f = new (std::nothrow) fe_field_h();
+    if (!f) return FE_ERR_OOM;
+    f->device = ctx->device;
+    f->n_elems = g->mesh.n_elems;
+    f->n_basis = n_basis;
+    f->Q = g->Q;
+    f->n_nodes = n_nodes;
+    f->conn = conn;
+    const size_t n = (size_t)g->Q * n_basis;
+    std::vector<float> psi32(n);
+    for (size_t k = 0; k < n; ++k) psi32[k] = (float)psi[k];
+    e = dev_alloc(&f->d_psi64, n);
+    if (e == cudaSuccess) e = dev_alloc(&f->d_psi32, n);
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_psi64, psi, sizeof(double) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(f->d_psi32, psi32.data(), sizeof(float) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(f->d_psi64);
+        cudaFree(f->d_psi32);
+        delete f;
+        return from_cuda(e, "fe_field_create");
+    }
+    *out = f;
+    return FE_OK;
+}
+
+fe_status fe_field_free(fe_field_h *f)
+{
+    fe_clear_last_error();
+    if (!f) return FE_ERR_INVALID_ARG;
+    cudaSetDevice(f->device);
+    cudaFree(f->d_psi64);
+    cudaFree(f->d_psi32);
+    delete f;
+    return FE_OK;
+}
+
+// The Stokes coupling with its scalar operand on a second field: checks shared by
+// matrix and residual mode.
+static fe_status mixed_common(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const fe_field_h *f,
+                              fe_precision prec, void *out)
+{
+    fe_material_args mat{};
+    fe_status st = eval_common(ctx, form, g, nullptr, prec, out, &mat);
+    if (st) return st;
+    if (!f) return FE_ERR_INVALID_ARG;
+    if (form->kind != FK_STOKES && form->kind != FK_STOKES_T) return FE_ERR_UNSUPPORTED_SPEC;
+    if (form->eval) return FE_ERR_INVALID_ARG;
+    if (f->n_elems != g->mesh.n_elems || f->Q != g->Q) return FE_ERR_SHAPE;
+    return FE_OK;
+}
+
+fe_status fe_eval_matrix_mixed(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const fe_field_h *f,
+                               const void *const *args, int diff_op, fe_precision prec, void *K_out,
+                               fe_stream_t stream)
+{
+    fe_clear_last_error();
+    (void)args;
+    fe_status st = mixed_common(ctx, form, g, f, prec, K_out);
+    if (st) return st;
+    if (diff_op != form->state_op) return FE_ERR_INVALID_ARG;
+    if (prec != FE_F64 && prec != FE_F32) return FE_ERR_UNSUPPORTED_SPEC;
+    cudaStream_t s = to_cuda(stream);
+    cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, s);
+    if (e == cudaSuccess)
+        e = fe_launch_stokes_mixed(g, f, prec == FE_F64, form->kind == FK_STOKES_T, 1, nullptr, K_out, ctx->d_status,
+                                   s);
+    return from_cuda(e, "fe_eval_matrix_mixed");
+}
+
+fe_status fe_eval_residual_mixed(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const fe_field_h *f,
+                                 const void *const *args, fe_precision prec, void *r_out, fe_stream_t stream)
+{
+    fe_clear_last_error();
+    fe_status st = mixed_common(ctx, form, g, f, prec, r_out);
+    if (st) return st;
+    if (!args || (!args[form->state_op] && g->mesh.n_elems > 0)) return FE_ERR_INVALID_ARG;
+    cudaStream_t s = to_cuda(stream);
+    cudaError_t e = settle_geometry(const_cast<fe_geometry_h *>(g), ctx->d_status, s);
+    if (e == cudaSuccess)
+        e = fe_launch_stokes_mixed(g, f, prec == FE_F64, form->kind == FK_STOKES_T, 0, args[form->state_op], r_out,
+                                   ctx->d_status, s);
+    return from_cuda(e, "fe_eval_residual_mixed");
+}
+
 fe_status fe_eval_integral(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *g, const void *const *args,
                            fe_precision prec, void *out, fe_stream_t stream)
 {
@@ -609,6 +704,17 @@ fe_status fe_debug_hold_next_matrix(fe_ctx *ctx)
     }
     ctx->hold_next_matrix = 1;
     return FE_OK;
+}
+
+fe_status fe_diag_fp64(fe_ctx *ctx, int kind, int warps, int ilp, int steps, double *out, fe_stream_t stream)
+{
+    fe_clear_last_error();
+    if (!ctx || !out || (kind != 0 && kind != 1) || warps < 1 || warps > 32 || steps < 1 ||
+        (ilp != 1 && ilp != 2 && ilp != 4))
+        return FE_ERR_INVALID_ARG;
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = fe_launch_diag_fp64(kind, ctx->sm_count, warps, ilp, steps, out, to_cuda(stream));
+    return from_cuda(e, "fe_diag_fp64");
 }
 
 fe_status fe_round_f32(fe_ctx *ctx, const double *in, float *out, long long n, fe_stream_t stream)

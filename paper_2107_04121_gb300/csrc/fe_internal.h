@@ -72,6 +72,19 @@ struct fe_form_h {
     int n_out;                    // values per element in eval mode
 };
 
+// A scalar field on a second basis over the elements of a geometry (the second
+// field of a mixed-order pair): its reference values at the geometry's points
+// and its borrowed connectivity.
+struct fe_field_h {
+    int device;
+    long long n_elems;
+    int n_basis, Q;
+    long long n_nodes;
+    const int32_t *conn;  // (n_elems, n_basis), borrowed
+    double *d_psi64;      // (Q, n_basis)
+    float *d_psi32;
+};
+
 struct fe_assembly_h {
     int device;
     fe_mesh mesh;
@@ -127,6 +140,11 @@ cudaError_t fe_launch_generic(const fe_geometry_h *g, const fe_form_h *f, fe_mat
 // may be null.
 cudaError_t fe_launch_adjoint(const fe_geometry_h *g, bool f64, const double *lame, const void *u,
                               const void *rbar, void *dmat, void *dxe, unsigned long long *status, cudaStream_t s);
+// Stokes coupling with its scalar operand on `f` (k_mixed.cu): transposed = the
+// scalar field is the test field; mode 0 residual (field = p, or u for the
+// transposed coupling), 1 matrix.
+cudaError_t fe_launch_stokes_mixed(const fe_geometry_h *g, const fe_field_h *f, bool f64, bool transposed, int mode,
+                                   const void *field, void *out, unsigned long long *status, cudaStream_t s);
 cudaError_t fe_launch_assembly_build(fe_assembly_h *a, int *d_flag, cudaStream_t s);
 cudaError_t fe_launch_assemble(const fe_assembly_h *a, int ncomp, bool f64, const void *r, void *out,
                                unsigned flags, cudaStream_t s);
@@ -137,6 +155,8 @@ cudaError_t fe_launch_assemble_noalloc(int device, const fe_mesh *mesh, int ncom
 
 // Status of a CUDA error, recorded as the thread's last error message (api.cu).
 fe_status fe_status_from_cuda(cudaError_t e, const char *where);
+// FP64 rate diagnostic (k_diag.cu): kind 0 DFMA chains, 1 FP64 MMA chains.
+cudaError_t fe_launch_diag_fp64(int kind, int sms, int warps, int ilp, int steps, double *out, cudaStream_t s);
 // The float64 -> float32 rounding of the geometry kernels over an array (k_geometry.cu).
 cudaError_t fe_launch_round_f32(const double *in, float *out, long long n, cudaStream_t s);
 

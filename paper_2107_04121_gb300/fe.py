@@ -39,6 +39,7 @@ EXPORTED = [
     "fe_assembly_free",
     "fe_assemble_vector", "fe_assemble_vector_noalloc", "fe_batch_create", "fe_batch_run", "fe_batch_describe",
     "fe_batch_schedule", "fe_batch_free", "fe_round_f32", "fe_debug_hold_next_matrix",
+    "fe_field_create", "fe_field_free", "fe_eval_matrix_mixed", "fe_eval_residual_mixed", "fe_diag_fp64",
 ]
 
 
@@ -112,6 +113,11 @@ def load_library(path: str = LIB_PATH):
     L.fe_eval_residual.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, vp, vp]
     L.fe_eval_residual_adjoint.argtypes = [vp, vp, vp, ctypes.POINTER(vp), vp, i, vp, vp, vp]
     L.fe_eval_integral.argtypes = [vp, vp, vp, ctypes.POINTER(vp), i, vp, vp]
+    L.fe_field_create.argtypes = [vp, vp, dp, i, vp, ll, ctypes.POINTER(vp)]
+    L.fe_field_free.argtypes = [vp]
+    L.fe_diag_fp64.argtypes = [vp, i, i, i, i, vp, vp]
+    L.fe_eval_matrix_mixed.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp), i, i, vp, vp]
+    L.fe_eval_residual_mixed.argtypes = [vp, vp, vp, vp, ctypes.POINTER(vp), i, vp, vp]
     L.fe_batch_create.argtypes = [vp, ctypes.POINTER(_BatchItem), i, ctypes.c_uint, ctypes.POINTER(vp), vp]
     L.fe_batch_run.argtypes = [vp, vp, vp]
     L.fe_batch_describe.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
@@ -430,6 +436,102 @@ def eval_residual(ctx: Context, form: Form, geom: Geometry, args, precision="f64
                                  _prec(precision),
                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)), "fe_eval_residual")
     return out
+
+
+class Field:
+    """fe_field_create: a scalar field on a second basis over the elements of a
+    geometry (the second field of a mixed-order pair): psi (Q, n_basis) float64
+    host array at the geometry's points, conn (n_elems, n_basis) int32 device
+    tensor (borrowed), n_nodes DOFs."""
+
+    def __init__(self, ctx: Context, geom: Geometry, psi, conn, n_nodes: int):
+        import torch
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        _dev(conn, torch.int32, "conn")
+        if psi.ndim != 2 or psi.shape[0] != geom.Q or conn.dim() != 2 or conn.shape[1] != psi.shape[1] \
+                or conn.shape[0] != geom.mesh.n_elems:
+            raise ValueError("psi must be (Q, n_basis) and conn (n_elems, n_basis)")
+        self.geom, self.conn, self.n_basis, self.n_nodes = geom, conn, psi.shape[1], int(n_nodes)
+        self._h = ctypes.c_void_p()
+        _check(_lib.fe_field_create(ctx.handle, geom._h, psi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    self.n_basis, ctypes.c_void_p(conn.data_ptr()), self.n_nodes,
+                                    ctypes.byref(self._h)), "fe_field_create")
+
+    def free(self):
+        if self._h:
+            _lib.fe_field_free(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def _mixed_args(form: Form, args, geom: Geometry, field: Field, dtype):
+    """Operand pointers of a Stokes coupling whose scalar operand is on `field`."""
+    if len(args) != len(form.operands):
+        raise ValueError("expected %d operands, got %d" % (len(form.operands), len(args)))
+    ptrs = (ctypes.c_void_p * len(form.operands))()
+    for k, (a, (role, ncomp, mk)) in enumerate(zip(args, form.operands)):
+        if a is not None:
+            _dev(a, dtype, "DOF vector of operand %d" % k)
+            want = field.n_nodes if ncomp == 1 else geom.mesh.n_nodes * ncomp
+            if a.numel() != want:
+                raise ValueError("DOF vector of operand %d must have %d entries" % (k, want))
+        ptrs[k] = None if a is None else a.data_ptr()
+    return ptrs
+
+
+def eval_matrix_mixed(ctx: Context, form: Form, geom: Geometry, field: Field, args, precision="f64", out=None,
+                      stream=None):
+    """fe_eval_matrix_mixed: the Stokes coupling with its scalar operand on `field`:
+    (E, 3 N, Np) with the vector test function, (E, Np, 3 N) with the scalar one."""
+    import torch
+    E, N, Np = geom.mesh.n_elems, geom.N, field.n_basis
+    vec_test = form.operands[[r for r, _, _ in form.operands].index(VIRTUAL)][1] == 3
+    shape = (E, 3 * N, Np) if vec_test else (E, Np, 3 * N)
+    if out is None:
+        out = torch.empty(shape, dtype=_out_dtype(precision), device=geom.mesh.coords.device)
+    _dev(out, _out_dtype(precision), "K_out")
+    if tuple(out.shape) != shape:
+        raise ValueError("K_out must have shape %s" % (shape,))
+    _check(_lib.fe_eval_matrix_mixed(ctx.handle, form._h, geom._h, field._h,
+                                     _mixed_args(form, args, geom, field, _out_dtype(precision)), form.state_op,
+                                     _prec(precision), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "fe_eval_matrix_mixed")
+    return out
+
+
+def eval_residual_mixed(ctx: Context, form: Form, geom: Geometry, field: Field, args, precision="f64", out=None,
+                        stream=None):
+    """fe_eval_residual_mixed: residuals (E, 3 N) with the vector test function,
+    (E, Np) with the scalar one; the unknown's DOF vector in its operand slot."""
+    import torch
+    E, N, Np = geom.mesh.n_elems, geom.N, field.n_basis
+    vec_test = form.operands[[r for r, _, _ in form.operands].index(VIRTUAL)][1] == 3
+    shape = (E, 3 * N) if vec_test else (E, Np)
+    if out is None:
+        out = torch.empty(shape, dtype=_out_dtype(precision), device=geom.mesh.coords.device)
+    _dev(out, _out_dtype(precision), "r_out")
+    if tuple(out.shape) != shape:
+        raise ValueError("r_out must have shape %s" % (shape,))
+    _check(_lib.fe_eval_residual_mixed(ctx.handle, form._h, geom._h, field._h,
+                                       _mixed_args(form, args, geom, field, _out_dtype(precision)),
+                                       _prec(precision), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+           "fe_eval_residual_mixed")
+    return out
+
+
+def diag_fp64(ctx: Context, kind: int, warps: int, ilp: int, steps: int, out, stream=None):
+    """fe_diag_fp64: launch the FP64 rate diagnostic (kind 0 DFMA, 1 FP64 MMA) with
+    one CTA of `warps` warps per SM; `out` a float64 device tensor of
+    SMs x warps x 32 entries.  Time it with CUDA events on `stream`."""
+    import torch
+    _dev(out, torch.float64, "out")
+    _check(_lib.fe_diag_fp64(ctx.handle, kind, warps, ilp, steps, ctypes.c_void_p(out.data_ptr()),
+                             _stream_ptr(stream)), "fe_diag_fp64")
 
 
 def eval_integral(ctx: Context, form: Form, geom: Geometry, args, precision="f64", out=None, stream=None):

@@ -137,3 +137,66 @@ def test_eval_and_weak_mode_misuse_is_rejected(ctx):
     fw = fe.laplace_form()
     with pytest.raises(fe.FEError):
         fe.eval_integral(ctx, fw, geom, [None, u], "f32")
+
+
+# ---- the Stokes coupling between fields of different orders (Taylor-Hood pairs) ----------
+
+def _mixed_case(ctx, kind, seed):
+    if kind == "Q2/Q1":
+        mesh = meshgen.structured_hex(5, 4, 3, 2, 0.15, seed)
+        m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+        geom = fe.hex_geometry(ctx, m, 2, 3)
+        ref_u, ref_p = oracle.RefElement(2, 3), oracle.RefElement(1, 3)
+        psi = fe.refbasis_hex(1, 3)[2]  # the library's Q1 basis at the 3 x 3 x 3 points
+    else:
+        mesh = meshgen.tet_mesh(97, 2, np.random.default_rng(seed))
+        m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+        geom = fe.tet_geometry(ctx, m, 2)
+        ref_u, ref_p = oracle.RefTet(2, 2), oracle.RefTet(1, 2)
+        psi = fe.refbasis_tet(1, 2)[2]  # the library's P1 basis at the rule of P2
+    conn_p, n_p = meshgen.vertex_connectivity(mesh)
+    field = fe.Field(ctx, geom, psi, _t(conn_p, torch.int32), n_p)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref_u)
+    return mesh, geom, field, conn_p, n_p, ref_p, wdetJ, G
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kind", ["Q2/Q1", "P2/P1"])
+def test_mixed_order_stokes_matches_oracle(ctx, kind, prec):
+    """The coupling div(v) p with a Q1 (P1) pressure beside a Q2 (P2) velocity and
+    its transpose q div(u): element matrices (3N x Np and Np x 3N) and residuals
+    against the oracle on distorted hexahedra and Delaunay tetrahedra."""
+    mesh, geom, field, conn_p, n_p, ref_p, wdetJ, G = _mixed_case(ctx, kind, 130)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    tol = TOL[prec] * (20 if kind == "P2/P1" else 1)  # alternating GM weights (see test_gpu_tets)
+    rng = np.random.default_rng(131)
+    p, u = rng.standard_normal(n_p), rng.standard_normal(3 * mesh.n_nodes)
+    Bref = oracle.matrix_stokes_mixed(wdetJ, G, ref_p.phi)
+    fs = fe.form_compile("i.i,0", [(V, 3, NONE), (S, 1, NONE)])
+    ft = fe.form_compile("i.i,0", [(S, 3, NONE), (V, 1, NONE)])
+    B = fe.eval_matrix_mixed(ctx, fs, geom, field, [None, None], prec)
+    Bt = fe.eval_matrix_mixed(ctx, ft, geom, field, [None, None], prec)
+    r = fe.eval_residual_mixed(ctx, fs, geom, field, [None, _t(p, dt)], prec)
+    rt = fe.eval_residual_mixed(ctx, ft, geom, field, [_t(u, dt), None], prec)
+    ctx.check()
+    E, N, Np = mesh.n_elems, geom.N, field.n_basis
+    assert B.shape == (E, 3 * N, Np) and Bt.shape == (E, Np, 3 * N)
+    assert _rel(B.cpu().numpy(), Bref) <= tol
+    assert _rel(Bt.cpu().numpy(), Bref.transpose(0, 2, 1)) <= tol
+    assert rel_vector_error(r.cpu().numpy(), oracle.residual_stokes_mixed(conn_p, wdetJ, G, ref_p.phi, p)) <= tol
+    assert rel_vector_error(rt.cpu().numpy(),
+                            oracle.residual_stokes_t_mixed(mesh.conn, wdetJ, G, ref_p.phi, u)) <= tol
+    field.free()
+
+
+def test_mixed_order_stokes_reports_out_of_range_pressure_nodes(ctx):
+    mesh, geom, field, conn_p, n_p, ref_p, wdetJ, G = _mixed_case(ctx, "Q2/Q1", 132)
+    bad = conn_p.copy()
+    bad[4, 3] = n_p + 7
+    fb = fe.Field(ctx, geom, fe.refbasis_hex(1, 3)[2], _t(bad, torch.int32), n_p)
+    fs = fe.form_compile("i.i,0", [(V, 3, NONE), (S, 1, NONE)])
+    ctx.status()
+    fe.eval_residual_mixed(ctx, fs, geom, fb, [None, _t(np.ones(n_p), torch.float64)], "f64")
+    assert ctx.status() == (fe.FE_ERR_SHAPE, 4)
+    fb.free()
+    field.free()
