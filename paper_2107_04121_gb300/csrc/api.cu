@@ -77,6 +77,7 @@ void free_geometry(fe_geometry_h *g)
     cudaFree(g->d_wdetj64);
     cudaFree(g->d_jinv32);
     cudaFree(g->d_wdetj32);
+    cudaFree(g->d_xi);
     delete g;
 }
 
@@ -264,6 +265,17 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
     if (e == cudaSuccess && (flags & FE_GEOM_STORE_F32)) {
         e = dev_alloc(&g->d_jinv32, (size_t)E * Q * 9);
         if (e == cudaSuccess) e = dev_alloc(&g->d_wdetj32, (size_t)E * Q);
+    }
+    if (e == cudaSuccess && !tensor && (flags & FE_GEOM_STORE_F32) && !(flags & FE_GEOM_STORE_F64)) {
+        // the library's tetrahedron basis in a float32-only handle: straight-sided
+        // elements get J from their vertices (the float64 copy, when kept, follows
+        // the isoparametric sum at every point)
+        double xi[64 * 3];
+        g->simplex_p = fe_host_simplex_order(N, Q, basis->phi, xi);
+        if (g->simplex_p) {
+            e = dev_alloc(&g->d_xi, (size_t)N * 3);
+            if (e == cudaSuccess) e = cudaMemcpy(g->d_xi, xi, sizeof(double) * N * 3, cudaMemcpyHostToDevice);
+        }
     }
     // the tables are tiny; synchronous copies keep the host buffers' lifetime simple
     if (e == cudaSuccess) e = cudaMemcpy(g->d_phi64, basis->phi, sizeof(double) * Q * N, cudaMemcpyHostToDevice);

@@ -35,6 +35,10 @@ struct fe_geometry_h {
     double *d_jinv64, *d_wdetj64;  // (E,Q,3,3), (E,Q)
     float *d_jinv32, *d_wdetj32;
     int pending;  // deferred handle: the stored geometry is stale (host-side, stream-ordered use)
+    // float32-only handle whose basis is the library's order-p tetrahedron basis:
+    // straight-sided elements take J from their vertices (k_geometry_simplex)
+    int simplex_p;
+    double *d_xi;  // (N, 3) reference positions of the nodes (lattice points / p)
     int is_view;  // aliases a parent's storage for a range of its elements (owns nothing)
 };
 
@@ -166,6 +170,10 @@ void fe_clear_last_error();
 // Settle a deferred geometry (api.cu): compute it now if it is stale.
 cudaError_t fe_settle_geometry(fe_geometry_h *g, unsigned long long *status, cudaStream_t s);
 
+// The order p (1..3) when phi (Q, N) is the library's order-p tetrahedron basis at
+// a Grundmann-Moller rule (fe_refbasis_tet), else 0 (refelem.cpp); xi (N, 3)
+// receives its node positions.
+int fe_host_simplex_order(int N, int Q, const double *phi, double *xi);
 // Which (N, Q) pairs have kernels.
 bool fe_supported_nq(int N, int Q);
 

@@ -12,7 +12,9 @@
 //    derivative direction;
 //  - k_geometry (any tabulated basis, e.g. tetrahedra): one thread per
 //    (element, quadrature point), J = sum_a x_a (x) grad phi_a directly (9N
-//    DFMA per point).
+//    DFMA per point);
+//  - k_geometry_simplex (the library's tetrahedron basis, float32-only
+//    handles): J of a straight-sided element from its vertices, once.
 // All finish each point with the same cofactor inverse (9 cofactors and det J:
 // 21 FP64 operations), whose float32 rounding uses integer operations
 // (geometry_body.cuh).
@@ -279,6 +281,90 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry(const double *__restr
     }
 }
 
+// Tetrahedra of the library's order-p basis, float32-only handles: one thread
+// per element.  When every node lies on the affine image of its lattice point
+// (x_a = x_0 + J xi_a to 1e-12 of the element's size: straight edges and faces)
+// J is the constant [x_1 - x_0, x_2 - x_0, x_3 - x_0] of the vertices and the
+// inverse is formed once (21 FP64 operations per element instead of 9N + 21 per
+// point); otherwise the point loop of k_geometry.  Same float32 roundings.
+template <int N>
+__global__ void __launch_bounds__(kGeomThreads) k_geometry_simplex(
+    const double *__restrict__ coords, const int32_t *__restrict__ conn, long long E, long long n_nodes, int Q,
+    const double *__restrict__ dphi, const double *__restrict__ w, const double *__restrict__ xi, int p,
+    float *__restrict__ jinv32, float *__restrict__ wdetj32, unsigned long long *__restrict__ status)
+{
+    // local indices of the vertices (0,0,0), (p,0,0), (0,p,0), (0,0,p) in the lattice order
+    const int v1 = p, v2 = (p + 1) * (p + 2) / 2 - 1, v3 = N - 1;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
+        const int32_t *ce = conn + e * N;
+        auto node_xyz = [&](int a, double x[3]) {
+            long long node = __ldg(ce + a);
+            if ((unsigned long long)node >= (unsigned long long)n_nodes) {  // never read outside coords
+                fe_report(status, FE_ERR_SHAPE, e);
+                node = 0;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] = __ldg(coords + 3 * node + c);
+        };
+        double x0[3], xv[3][3];
+        node_xyz(0, x0);
+        node_xyz(v1, xv[0]);
+        node_xyz(v2, xv[1]);
+        node_xyz(v3, xv[2]);
+        double J[3][3];
+        double size = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int m = 0; m < 3; ++m) {
+                J[c][m] = __dsub_rn(xv[m][c], x0[c]);
+                size = fmax(size, fabs(J[c][m]));
+            }
+        bool straight = true;
+        for (int a = 1; a < N && straight; ++a) {
+            if (a == v1 || a == v2 || a == v3) continue;
+            double x[3];
+            node_xyz(a, x);
+            const double *xa = xi + 3 * a;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double pred = fma(J[c][2], __ldg(xa + 2), fma(J[c][1], __ldg(xa + 1), fma(J[c][0], __ldg(xa), x0[c])));
+                if (!(fabs(x[c] - pred) <= 1e-12 * size)) straight = false;
+            }
+        }
+        if (straight) {
+            float o[9], wd0;
+            const double det = geo_point_f32(&J[0][0], __ldg(w), o, wd0);
+            const int bad = geo_det_status(det);
+            if (bad) fe_report(status, bad, e);
+            const float df = geo_to_f32(det);
+            for (int q = 0; q < Q; ++q) {
+                const long long idx = e * Q + q;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) jinv32[idx * 9 + k] = o[k];
+                wdetj32[idx] = q == 0 ? wd0 : __fmul_rn(geo_to_f32(__ldg(w + q)), df);
+            }
+        } else {
+            for (int q = 0; q < Q; ++q) {
+                const double *d0 = dphi + (size_t)(q * 3) * N;
+                double Jq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+                for (int a = 0; a < N; ++a) {
+                    double x[3];
+                    node_xyz(a, x);
+                    const double g0 = __ldg(d0 + a), g1 = __ldg(d0 + N + a), g2 = __ldg(d0 + 2 * N + a);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        Jq[c][0] = fma(x[c], g0, Jq[c][0]);
+                        Jq[c][1] = fma(x[c], g1, Jq[c][1]);
+                        Jq[c][2] = fma(x[c], g2, Jq[c][2]);
+                    }
+                }
+                finish_point(Jq, __ldg(w + q), e, e * Q + q, nullptr, nullptr, jinv32, wdetj32, status);
+            }
+        }
+    }
+}
+
 // G[e][q][j][a] = sum_k dphi[q][k][a] (J^-1)_kj from a stored J^-1 copy.
 template <typename T>
 __global__ void k_expand_G(const T *__restrict__ jinv, const T *__restrict__ dphi, long long E, int Q, int N,
@@ -324,6 +410,17 @@ cudaError_t launch_geom(const fe_geometry_h *g, unsigned long long *st, cudaStre
     k_geometry<N><<<(unsigned)blocks, kGeomThreads, smem, s>>>(
         g->mesh.coords, g->mesh.conn, g->mesh.n_elems, g->mesh.n_nodes, g->Q, g->d_dphi64, g->d_w64, f64 ? g->d_jinv64 : nullptr,
         f64 ? g->d_wdetj64 : nullptr, f32 ? g->d_jinv32 : nullptr, f32 ? g->d_wdetj32 : nullptr, st);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_geom_simplex(const fe_geometry_h *g, unsigned long long *st, cudaStream_t s)
+{
+    long long blocks = (g->mesh.n_elems + kGeomThreads - 1) / kGeomThreads;
+    if (blocks > (1ll << 30)) blocks = 1ll << 30;
+    k_geometry_simplex<N><<<(unsigned)blocks, kGeomThreads, 0, s>>>(
+        g->mesh.coords, g->mesh.conn, g->mesh.n_elems, g->mesh.n_nodes, g->Q, g->d_dphi64, g->d_w64, g->d_xi,
+        g->simplex_p, g->d_jinv32, g->d_wdetj32, st);
     return cudaGetLastError();
 }
 
@@ -410,6 +507,14 @@ cudaError_t fe_launch_geometry(const fe_geometry_h *g, unsigned long long *st, c
         if (n1 == 3 && nq == 3) return launch_geom_sf<3, 3, 8>(g, st, s);
         if (n1 == 3 && nq == 4) return launch_geom_sf<3, 4, 4>(g, st, s);
         if (n1 == 4 && nq == 4) return launch_geom_sf<4, 4, 2>(g, st, s);
+    }
+    if (g->simplex_p && g->d_xi && g->d_jinv32 && !g->d_jinv64) {
+        switch (g->N) {
+        case 4: return launch_geom_simplex<4>(g, st, s);
+        case 10: return launch_geom_simplex<10>(g, st, s);
+        case 20: return launch_geom_simplex<20>(g, st, s);
+        default: break;
+        }
     }
     switch (g->N) {
     case 8: return launch_geom<8>(g, st, s);

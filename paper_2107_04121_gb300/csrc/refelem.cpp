@@ -10,6 +10,7 @@
 #include <cmath>
 #include <utility>
 #include <cstring>
+#include <vector>
 
 #include "fe_internal.h"
 
@@ -328,4 +329,30 @@ extern "C" fe_status fe_refbasis_tet(int p, int s, double *points, double *weigh
         }
     }
     return FE_OK;
+}
+
+int fe_host_simplex_order(int N, int Q, const double *phi, double *xi)
+{
+    for (int p = 1; p <= 3; ++p) {
+        if (N != (p + 1) * (p + 2) * (p + 3) / 6) continue;
+        for (int s = 0; s <= 6; ++s) {
+            if (fe_gm_rule_size(s) != Q) continue;
+            std::vector<double> ref((size_t)Q * N);
+            if (fe_refbasis_tet(p, s, nullptr, nullptr, ref.data(), nullptr) != FE_OK) continue;
+            bool same = true;
+            for (size_t k = 0; k < ref.size() && same; ++k) same = std::fabs(ref[k] - phi[k]) <= 1e-13;
+            if (!same) continue;
+            // lattice points (i, j, k) / p, x fastest (the basis' node order)
+            int a = 0;
+            for (int k = 0; k <= p; ++k)
+                for (int j = 0; j <= p - k; ++j)
+                    for (int i = 0; i <= p - k - j; ++i, ++a) {
+                        xi[3 * a] = (double)i / p;
+                        xi[3 * a + 1] = (double)j / p;
+                        xi[3 * a + 2] = (double)k / p;
+                    }
+            return p;
+        }
+    }
+    return 0;
 }

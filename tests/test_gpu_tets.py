@@ -92,3 +92,34 @@ def test_tet_refbasis_matches_oracle(libfe):
             np.testing.assert_allclose(w, ow, rtol=1e-13, atol=1e-16)
             np.testing.assert_allclose(phi, ophi, atol=1e-13)
             np.testing.assert_allclose(dphi, odphi, atol=1e-12)
+
+
+@pytest.mark.parametrize("p,E", [(1, 301), (2, 157), (3, 83)])
+def test_float32_tet_geometry_straight_and_curved(ctx, p, E):
+    """A float32-only handle of the library's tetrahedron basis: straight-sided
+    elements take J from their vertices (once per element), elements whose edge
+    nodes moved off the straight edges take the isoparametric sum at every point;
+    both against the oracle's FP64 geometry (float32 copies: a few float32 ulps)."""
+    mesh = meshgen.tet_mesh(E, p, np.random.default_rng(85 + p))
+    coords = mesh.coords.copy()
+    if p > 1:
+        # bend the edges of the first elements: move their non-vertex nodes
+        h = np.abs(coords[mesh.conn[:5, 1]] - coords[mesh.conn[:5, 0]]).max()
+        rng = np.random.default_rng(86)
+        moved = np.unique(mesh.conn[:5, 1:p])
+        coords[moved] += 0.05 * h * rng.uniform(-1, 1, (len(moved), 3))
+    ref = oracle.RefTet(p, p)
+    wdetJ, _, Jinv = oracle.geometry(coords, mesh.conn, ref, want_Jinv=True)
+    m = fe.Mesh(_t(coords, torch.float64), _t(mesh.conn, torch.int32))
+    g32 = fe.tet_geometry(ctx, m, p, flags=fe.GEOM_STORE_F32)
+    ctx.check()
+    wd = g32.get(fe.GEOM_WDETJ, "f32").cpu().numpy().astype(np.float64)
+    ji = g32.get(fe.GEOM_JINV, "f32").cpu().numpy().astype(np.float64)
+    assert np.abs(wd - wdetJ).max() <= 4e-7 * np.abs(wdetJ).max()
+    # per element and point, J^-1 against its own scale
+    sc = np.abs(Jinv).reshape(E, -1).max(1)[:, None, None, None]
+    assert (np.abs(ji - Jinv) / sc).max() <= 4e-7
+    if p > 1:
+        # the bent elements really differ from the straight-edged map
+        wd_straight, _, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+        assert np.abs(wdetJ[:5] - wd_straight[:5]).max() > 1e-4 * np.abs(wdetJ[:5]).max()
