@@ -286,7 +286,9 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry(const double *__restr
 // (x_a = x_0 + J xi_a to 1e-12 of the element's size: straight edges and faces)
 // J is the constant [x_1 - x_0, x_2 - x_0, x_3 - x_0] of the vertices and the
 // inverse is formed once (21 FP64 operations per element instead of 9N + 21 per
-// point); otherwise the point loop of k_geometry.  Same float32 roundings.
+// point); the warp then writes the Q copies of such elements together, one
+// element at a time, with consecutive lanes on consecutive floats.  Elements
+// with bent edges take the point loop of k_geometry.  Same float32 roundings.
 template <int N>
 __global__ void __launch_bounds__(kGeomThreads) k_geometry_simplex(
     const double *__restrict__ coords, const int32_t *__restrict__ conn, long long E, long long n_nodes, int Q,
@@ -295,72 +297,91 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry_simplex(
 {
     // local indices of the vertices (0,0,0), (p,0,0), (0,p,0), (0,0,p) in the lattice order
     const int v1 = p, v2 = (p + 1) * (p + 2) / 2 - 1, v3 = N - 1;
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (long long)gridDim.x * blockDim.x) {
-        const int32_t *ce = conn + e * N;
-        auto node_xyz = [&](int a, double x[3]) {
-            long long node = __ldg(ce + a);
-            if ((unsigned long long)node >= (unsigned long long)n_nodes) {  // never read outside coords
-                fe_report(status, FE_ERR_SHAPE, e);
-                node = 0;
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // warp-uniform loop: the 32 lanes take 32 consecutive elements
+    for (long long base = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < E; base += stride) {
+        const long long e = base + lane;
+        const bool live = e < E;
+        bool straight = false;
+        float o[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, df = 0.f;
+        if (live) {
+            const int32_t *ce = conn + e * N;
+            auto node_xyz = [&](int a, double x[3]) {
+                long long node = __ldg(ce + a);
+                if ((unsigned long long)node >= (unsigned long long)n_nodes) {  // never read outside coords
+                    fe_report(status, FE_ERR_SHAPE, e);
+                    node = 0;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) x[c] = __ldg(coords + 3 * node + c);
+            };
+            double x0[3], xv[3][3];
+            node_xyz(0, x0);
+            node_xyz(v1, xv[0]);
+            node_xyz(v2, xv[1]);
+            node_xyz(v3, xv[2]);
+            double J[3][3];
+            double size = 0.0;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int m = 0; m < 3; ++m) {
+                    J[c][m] = __dsub_rn(xv[m][c], x0[c]);
+                    size = fmax(size, fabs(J[c][m]));
+                }
+            straight = true;
+            for (int a = 1; a < N && straight; ++a) {
+                if (a == v1 || a == v2 || a == v3) continue;
+                double x[3];
+                node_xyz(a, x);
+                const double *xa = xi + 3 * a;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const double pred =
+                        fma(J[c][2], __ldg(xa + 2), fma(J[c][1], __ldg(xa + 1), fma(J[c][0], __ldg(xa), x0[c])));
+                    if (!(fabs(x[c] - pred) <= 1e-12 * size)) straight = false;
+                }
             }
+            if (straight) {
+                float wd0;
+                const double det = geo_point_f32(&J[0][0], __ldg(w), o, wd0);
+                const int bad = geo_det_status(det);
+                if (bad) fe_report(status, bad, e);
+                df = geo_to_f32(det);
+            } else {
+                for (int q = 0; q < Q; ++q) {
+                    const double *d0 = dphi + (size_t)(q * 3) * N;
+                    double Jq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+                    for (int a = 0; a < N; ++a) {
+                        double x[3];
+                        node_xyz(a, x);
+                        const double g0 = __ldg(d0 + a), g1 = __ldg(d0 + N + a), g2 = __ldg(d0 + 2 * N + a);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) x[c] = __ldg(coords + 3 * node + c);
-        };
-        double x0[3], xv[3][3];
-        node_xyz(0, x0);
-        node_xyz(v1, xv[0]);
-        node_xyz(v2, xv[1]);
-        node_xyz(v3, xv[2]);
-        double J[3][3];
-        double size = 0.0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int m = 0; m < 3; ++m) {
-                J[c][m] = __dsub_rn(xv[m][c], x0[c]);
-                size = fmax(size, fabs(J[c][m]));
-            }
-        bool straight = true;
-        for (int a = 1; a < N && straight; ++a) {
-            if (a == v1 || a == v2 || a == v3) continue;
-            double x[3];
-            node_xyz(a, x);
-            const double *xa = xi + 3 * a;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double pred = fma(J[c][2], __ldg(xa + 2), fma(J[c][1], __ldg(xa + 1), fma(J[c][0], __ldg(xa), x0[c])));
-                if (!(fabs(x[c] - pred) <= 1e-12 * size)) straight = false;
+                        for (int c = 0; c < 3; ++c) {
+                            Jq[c][0] = fma(x[c], g0, Jq[c][0]);
+                            Jq[c][1] = fma(x[c], g1, Jq[c][1]);
+                            Jq[c][2] = fma(x[c], g2, Jq[c][2]);
+                        }
+                    }
+                    finish_point(Jq, __ldg(w + q), e, e * Q + q, nullptr, nullptr, jinv32, wdetj32, status);
+                }
             }
         }
-        if (straight) {
-            float o[9], wd0;
-            const double det = geo_point_f32(&J[0][0], __ldg(w), o, wd0);
-            const int bad = geo_det_status(det);
-            if (bad) fe_report(status, bad, e);
-            const float df = geo_to_f32(det);
-            for (int q = 0; q < Q; ++q) {
-                const long long idx = e * Q + q;
+        // the straight elements' Q copies of J^-1 and w det J = fl(w_q) fl(det J), written
+        // by the whole warp element by element (each element's block is contiguous)
+        unsigned todo = __ballot_sync(0xffffffffu, live && straight);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1;
+            float ol[9];
 #pragma unroll
-                for (int k = 0; k < 9; ++k) jinv32[idx * 9 + k] = o[k];
-                wdetj32[idx] = q == 0 ? wd0 : __fmul_rn(geo_to_f32(__ldg(w + q)), df);
-            }
-        } else {
-            for (int q = 0; q < Q; ++q) {
-                const double *d0 = dphi + (size_t)(q * 3) * N;
-                double Jq[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-                for (int a = 0; a < N; ++a) {
-                    double x[3];
-                    node_xyz(a, x);
-                    const double g0 = __ldg(d0 + a), g1 = __ldg(d0 + N + a), g2 = __ldg(d0 + 2 * N + a);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        Jq[c][0] = fma(x[c], g0, Jq[c][0]);
-                        Jq[c][1] = fma(x[c], g1, Jq[c][1]);
-                        Jq[c][2] = fma(x[c], g2, Jq[c][2]);
-                    }
-                }
-                finish_point(Jq, __ldg(w + q), e, e * Q + q, nullptr, nullptr, jinv32, wdetj32, status);
-            }
+            for (int k = 0; k < 9; ++k) ol[k] = __shfl_sync(0xffffffffu, o[k], l);
+            const float dl = __shfl_sync(0xffffffffu, df, l);
+            const long long el = base + l;
+            float *jo = jinv32 + el * Q * 9;
+            for (int i = lane; i < Q * 9; i += 32) jo[i] = ol[i % 9];
+            for (int i = lane; i < Q; i += 32) wdetj32[el * Q + i] = __fmul_rn(geo_to_f32(__ldg(w + i)), dl);
         }
     }
 }
