@@ -482,6 +482,13 @@ fe_status fe_batch_run(fe_ctx *ctx, fe_batch_h *batch, fe_stream_t stream);
  * per chunk, staging (1: bulk-copied row blocks, 0: direct stores); any may be
  * NULL.  Under the launches schedule the item runs fe_eval_matrix's kernel. */
 fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *elems_per_chunk, int *staging);
+/* The contraction path of item `item` in the batch's schedule: *path = 0 for
+ * the Gram blocks on the CUDA cores (FP32), 1 for the TF32x3 Gram on the tensor
+ * cores (Lame elasticity of 27-node hexahedra with 27 points, chosen by
+ * FE_BATCH_AUTOTUNE in the per-item schedule when it is faster; max element
+ * error 6.5e-7 against the FP64 oracle on the 48^3 workload).  Errors:
+ * FE_ERR_INVALID_ARG. */
+fe_status fe_batch_describe_path(const fe_batch_h *batch, int item, int *path);
 /* The schedule of a batch: *per_item_launches = 1 for one launch per item,
  * 0 for the persistent class kernels.  Errors: FE_ERR_INVALID_ARG (NULL). */
 fe_status fe_batch_schedule(const fe_batch_h *batch, int *per_item_launches);

@@ -9,10 +9,6 @@
 
 #include "fe_internal.h"
 
-cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
-                                void *K, int sm_count, unsigned long long *status, const int *hold,
-                                bool with_geometry, cudaStream_t s);
-bool fe_matrix_tc_geometry_fusable(const fe_geometry_h *g);
 
 // A deferred handle whose geometry is stale gets it computed before any use.
 static cudaError_t settle_geometry(fe_geometry_h *g, unsigned long long *status, cudaStream_t s)

@@ -112,6 +112,12 @@ cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe
                                   void *K, int sm_count, cudaStream_t s);
 cudaError_t fe_launch_matrix(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
                              void *K, int sm_count, cudaStream_t s);
+// Matrix mode on the tensor cores (k_matrix_tc.cu): Lame elasticity, 27 nodes, 27
+// points; with_geometry: a stale float32-only deferred handle computed in the launch.
+cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
+                                void *K, int sm_count, unsigned long long *status, const int *hold,
+                                bool with_geometry, cudaStream_t s);
+bool fe_matrix_tc_geometry_fusable(const fe_geometry_h *g);
 cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
                                const void *u, void *r, unsigned long long *status, cudaStream_t s);
 // Residual of a stale float32-only deferred geometry with the geometry computed

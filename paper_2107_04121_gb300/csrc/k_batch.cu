@@ -28,8 +28,11 @@
 // A second schedule launches, per item, the standalone kernel of
 // fe_eval_matrix (each compiled for its item alone, so each runs at its own
 // occupancy), the items spread over the caller's stream and the two side
-// streams by longest-processing-time-first assignment.  Autotuning times both
-// schedules and keeps the faster; either one can be captured in the graph.
+// streams by longest-processing-time-first assignment.  In this schedule an
+// item of Lame elasticity on 27-node hexahedra may take a second contraction
+// path, the TF32x3 Gram on the tensor cores (k_matrix_tc), when autotuning finds
+// it faster.  Autotuning times both schedules and keeps the faster; either one
+// can be captured in the graph.
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -228,6 +231,10 @@ struct fe_batch_h {
     std::vector<const fe_geometry_h *> igeom;
     std::vector<fe_material_args> mats;
     std::vector<int> lane;
+    // contraction path of each item in the per-item schedule: 0 the Gram blocks on
+    // the CUDA cores (k_matrix_sym), 1 the TF32x3 Gram on the tensor cores
+    // (k_matrix_tc; Lame elasticity of 27-node hexahedra with 27 points)
+    std::vector<int> path;
 };
 
 namespace {
@@ -267,8 +274,11 @@ cudaError_t enqueue_items(fe_batch_h *b, cudaStream_t s)
     for (int i = 0; i < b->n_items && e == cudaSuccess; ++i) {
         if (b->items[i].E == 0) continue;
         const int l = b->lane[i];
-        e = fe_launch_matrix_simt(b->igeom[i], b->forms[i], b->mats[i], false, b->items[i].K, b->sm_count,
-                                  l == 0 ? s : b->side[l - 1]);
+        cudaStream_t ls = l == 0 ? s : b->side[l - 1];
+        e = b->path[i] ? fe_launch_matrix_tc(b->igeom[i], b->forms[i], b->mats[i], FE_TF32X3, b->items[i].K,
+                                             b->sm_count, b->d_status, nullptr, false, ls)
+                       : fe_launch_matrix_simt(b->igeom[i], b->forms[i], b->mats[i], false, b->items[i].K,
+                                               b->sm_count, ls);
     }
     for (int c = 0; c < kClasses - 1 && e == cudaSuccess; ++c) {
         e = cudaEventRecord(b->join[c], b->side[c]);
@@ -373,6 +383,37 @@ cudaError_t time_variant(BatchItemDev it, int id, BatchItemDev *d_tmp, cudaStrea
     return cudaSuccess;
 }
 
+// Median of five timed runs (after one warm-up) of item i's standalone kernel
+// on contraction path `path` (0 CUDA cores, 1 tensor cores).
+cudaError_t time_path(fe_batch_h *b, int i, int path, cudaStream_t s, float *ms)
+{
+    cudaEvent_t a, z;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&z);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int r = 0; r < 6 && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(a, s);
+        if (e == cudaSuccess)
+            e = path ? fe_launch_matrix_tc(b->igeom[i], b->forms[i], b->mats[i], FE_TF32X3, b->items[i].K,
+                                           b->sm_count, b->d_status, nullptr, false, s)
+                     : fe_launch_matrix_simt(b->igeom[i], b->forms[i], b->mats[i], false, b->items[i].K,
+                                             b->sm_count, s);
+        if (e == cudaSuccess) e = cudaEventRecord(z, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(z);
+        if (e == cudaSuccess && r > 0) e = cudaEventElapsedTime(&t[r - 1], a, z);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(z);
+    std::sort(t, t + 5);
+    *ms = t[2];
+    return e;
+}
+
 void free_plan(fe_batch_h *b)
 {
     if (!b) return;
@@ -455,6 +496,7 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         ma.data = f->mat_op >= 0 ? (const double *)x.material : nullptr;
         ma.transposed = f->mat_op >= 0 ? f->mat_transposed : 0;
         b->mats.push_back(ma);
+        b->path.push_back(0);
         fe_geometry_h *gm = const_cast<fe_geometry_h *>(g);
         bool seen = false;
         for (fe_geometry_h *h : b->geoms) seen = seen || h == gm;
@@ -500,6 +542,21 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
             }
             it.variant = best_id;
             done.push_back({g->N, g->Q, items[i].form->kind, it.ncomp, best_id});
+        }
+    }
+    // contraction path per item (per-item schedule): the tensor-core TF32x3 Gram
+    // where it applies and runs faster than the CUDA-core kernel
+    if (e == cudaSuccess && (flags & FE_BATCH_AUTOTUNE) && !force_persistent) {
+        for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
+            const fe_geometry_h *g = b->igeom[i];
+            const fe_form_h *f = b->forms[i];
+            if (b->items[i].E == 0 || f->kind != FK_ELASTICITY || f->mat != FE_MAT_LAME || f->mat_transposed ||
+                g->N != 27 || g->Q != 27)
+                continue;
+            float t0 = 0.f, t1 = 0.f;
+            e = time_path(b, i, 0, s, &t0);
+            if (e == cudaSuccess) e = time_path(b, i, 1, s, &t1);
+            if (e == cudaSuccess && t1 < t0) b->path[i] = 1;
         }
     }
     // work lists: one per class, the items grouped by class on the device
@@ -605,6 +662,14 @@ fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *e
     if (tile) *tile = v.tile;
     if (elems_per_chunk) *elems_per_chunk = v.epb;
     if (staging) *staging = v.stage == STAGE_BULK ? 1 : 0;
+    return FE_OK;
+}
+
+fe_status fe_batch_describe_path(const fe_batch_h *batch, int item, int *path)
+{
+    fe_clear_last_error();
+    if (!batch || !path || item < 0 || item >= batch->n_items) return FE_ERR_INVALID_ARG;
+    *path = batch->launches ? batch->path[item] : 0;
     return FE_OK;
 }
 

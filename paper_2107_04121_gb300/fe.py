@@ -40,6 +40,7 @@ EXPORTED = [
     "fe_assemble_vector", "fe_assemble_vector_noalloc", "fe_batch_create", "fe_batch_run", "fe_batch_describe",
     "fe_batch_schedule", "fe_batch_free", "fe_round_f32", "fe_debug_hold_next_matrix",
     "fe_field_create", "fe_field_free", "fe_eval_matrix_mixed", "fe_eval_residual_mixed", "fe_diag_fp64",
+    "fe_batch_describe_path",
 ]
 
 
@@ -121,6 +122,7 @@ def load_library(path: str = LIB_PATH):
     L.fe_batch_create.argtypes = [vp, ctypes.POINTER(_BatchItem), i, ctypes.c_uint, ctypes.POINTER(vp), vp]
     L.fe_batch_run.argtypes = [vp, vp, vp]
     L.fe_batch_describe.argtypes = [vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.fe_batch_describe_path.argtypes = [vp, i, ctypes.POINTER(i)]
     L.fe_batch_schedule.argtypes = [vp, ctypes.POINTER(i)]
     L.fe_batch_free.argtypes = [vp]
     L.fe_assembly_create.argtypes = [vp, ctypes.POINTER(_Mesh), ctypes.POINTER(vp), vp]
@@ -612,7 +614,10 @@ class Batch:
         t, e, s = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(_lib.fe_batch_describe(self._h, item, ctypes.byref(t), ctypes.byref(e), ctypes.byref(s)),
                "fe_batch_describe")
-        return {"tile": t.value, "elems_per_chunk": e.value, "staging": "bulk" if s.value else "direct"}
+        pth = ctypes.c_int()
+        _check(_lib.fe_batch_describe_path(self._h, item, ctypes.byref(pth)), "fe_batch_describe_path")
+        return {"tile": t.value, "elems_per_chunk": e.value, "staging": "bulk" if s.value else "direct",
+                "path": "tensor-core tf32x3 Gram" if pth.value else "cuda-core Gram blocks"}
 
     def schedule(self) -> str:
         """'launches' (one kernel launch per item) or 'persistent' (the class kernels)."""

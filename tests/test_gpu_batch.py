@@ -168,6 +168,25 @@ def test_batch_geometry_flag_follows_moved_nodes(ctx, groups, schedule):
     ctx.check()
 
 
+def test_batch_contraction_path_is_reported(ctx, groups):
+    """The per-item schedule may run the Q2 Lame elasticity item on the tensor
+    cores (TF32x3 Gram); every other item, and every item of the persistent
+    schedule, on the CUDA cores; the tensor-core item matches the oracle."""
+    items, keys = _items(groups)
+    b = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_LAUNCHES)
+    outs = b.run()
+    ctx.check()
+    for k, ((g, f), K) in enumerate(zip(keys, outs)):
+        path = b.describe(k)["path"]
+        if path.startswith("tensor"):
+            assert g.name == "Q2" and f == "elasticity"
+        assert _err(K, g.reference(f), g.tet) <= TOL["f32"], (g.name, f, path)
+    b.free()
+    bp = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_PERSISTENT)
+    assert all(bp.describe(k)["path"].startswith("cuda") for k in range(len(keys)))
+    bp.free()
+
+
 def test_batch_autotune_choice_is_a_candidate(ctx, groups):
     items, keys = _items(groups)
     b = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE)
