@@ -201,7 +201,7 @@ __device__ __forceinline__ void load_material(int ne, long long e0, const double
 // memory; B, D = 1-D tables (nq, n1) in registers.  Ends with r written.
 template <typename T, int N1, int NQ, int KIND, int MATK, int EPB, int THREADS>
 __device__ __forceinline__ void residual_sf_stages(
-    int ne, int nc, long long e0, T (*__restrict__ sU)[KIND == FK_LAPLACE ? 1 : 3][N1 * N1 * N1],
+    int ne, int nc_rt, long long e0, T (*__restrict__ sU)[KIND == FK_LAPLACE ? 1 : 3][N1 * N1 * N1],
     T (*__restrict__ sX)[KIND == FK_LAPLACE ? 1 : 3][KIND != FK_MASS ? 2 : 1][N1 * N1 * NQ],
     T (*__restrict__ sY)[KIND == FK_LAPLACE ? 1 : 3][KIND != FK_MASS ? 3 : 1][N1 * NQ * NQ],
     T (*__restrict__ sQ)[KIND == FK_LAPLACE ? 1 : 3][KIND != FK_MASS ? 3 : 1][NQ * NQ * NQ],
@@ -212,8 +212,10 @@ __device__ __forceinline__ void residual_sf_stages(
     constexpr bool GRAD = KIND != FK_MASS;
     constexpr int NC = KIND == FK_LAPLACE ? 1 : 3;
     constexpr int NM = GRAD ? 3 : 1;
-    (void)NC;
     (void)NM;
+    // components: known at compile time except for the mass form (scalar or
+    // vector), so that the stage index arithmetic divides by constants
+    const int nc = KIND == FK_MASS ? nc_rt : NC;
     // ---- phase 1, x: line (el, c, k, j) -> sX[0] = B_x U, sX[1] = D_x U at qx = 0..nq-1
     for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
         const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
