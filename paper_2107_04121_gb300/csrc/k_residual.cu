@@ -199,7 +199,7 @@ __device__ __forceinline__ void load_material(int ne, long long e0, const double
 // The stages of k_residual_sf after the loads, for ne elements starting at e0
 // whose DOFs (sU), J^-1 (sJ), w det J (sW) and material (sM) are in shared
 // memory; B, D = 1-D tables (nq, n1) in registers.  Ends with r written.
-template <typename T, int N1, int NQ, int KIND, int MATK, int EPB, int THREADS>
+template <typename T, int N1, int NQ, int KIND, int MATK, int EPB, int THREADS, bool WARP = false>
 __device__ __forceinline__ void residual_sf_stages(
     int ne, int nc_rt, long long e0, T (*__restrict__ sU)[KIND == FK_LAPLACE ? 1 : 3][N1 * N1 * N1],
     T (*__restrict__ sX)[KIND == FK_LAPLACE ? 1 : 3][KIND != FK_MASS ? 2 : 1][N1 * N1 * NQ],
@@ -216,8 +216,16 @@ __device__ __forceinline__ void residual_sf_stages(
     // components: known at compile time except for the mass form (scalar or
     // vector), so that the stage index arithmetic divides by constants
     const int nc = KIND == FK_MASS ? nc_rt : NC;
+    // WARP: one warp works through the stages of its own element (lanes = lines
+    // or points), with warp-level instead of block-level synchronisation
+    const int tid0 = WARP ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+    constexpr int STRIDE = WARP ? 32 : THREADS;
+    auto stage_sync = [] {
+        if constexpr (WARP) __syncwarp();
+        else __syncthreads();
+    };
     // ---- phase 1, x: line (el, c, k, j) -> sX[0] = B_x U, sX[1] = D_x U at qx = 0..nq-1
-    for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
+    for (int t = tid0; t < ne * nc * N1 * N1; t += STRIDE) {
         const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
         T x[N1];
 #pragma unroll
@@ -234,9 +242,9 @@ __device__ __forceinline__ void residual_sf_stages(
             if constexpr (GRAD) sX[el][c][1][kj * NQ + qx] = v1;
         }
     }
-    __syncthreads();
+    stage_sync();
     // ---- phase 1, y: line (el, c, k, qx) -> at qy: [0] B_y B_x, [1] D_y B_x, [2] B_y D_x
-    for (int t = threadIdx.x; t < ne * nc * N1 * NQ; t += THREADS) {
+    for (int t = tid0; t < ne * nc * N1 * NQ; t += STRIDE) {
         const int qx = t % NQ, k = (t / NQ) % N1, c = (t / (NQ * N1)) % nc, el = t / (NQ * N1 * nc);
         T a0[N1], a1[N1];
 #pragma unroll
@@ -263,9 +271,9 @@ __device__ __forceinline__ void residual_sf_stages(
             }
         }
     }
-    __syncthreads();
+    stage_sync();
     // ---- phase 1, z: line (el, c, qy, qx) -> sQ[m] at qz = d u_c / d xi_m (or u_c)
-    for (int t = threadIdx.x; t < ne * nc * NQ * NQ; t += THREADS) {
+    for (int t = tid0; t < ne * nc * NQ * NQ; t += STRIDE) {
         const int qx = t % NQ, qy = (t / NQ) % NQ, c = (t / (NQ * NQ)) % nc, el = t / (NQ * NQ * nc);
         T y0[N1], y1[N1], y2[N1];
 #pragma unroll
@@ -298,9 +306,9 @@ __device__ __forceinline__ void residual_sf_stages(
             }
         }
     }
-    __syncthreads();
+    stage_sync();
     // ---- pointwise flux, in place: F_c,m(q) with r = sum_q sum_m F_c,m dphi_a/dxi_m
-    for (int t = threadIdx.x; t < ne * Q; t += THREADS) {
+    for (int t = tid0; t < ne * Q; t += STRIDE) {
         const int el = t / Q, q = t % Q;
         const T wd = sW[el][q];
         if constexpr (KIND == FK_MASS) {
@@ -354,9 +362,9 @@ __device__ __forceinline__ void residual_sf_stages(
                     sQ[el][c][m][q] = S[c][0] * Ji[m * 3] + S[c][1] * Ji[m * 3 + 1] + S[c][2] * Ji[m * 3 + 2];
         }
     }
-    __syncthreads();
+    stage_sync();
     // ---- phase 2, z^T: line (el, c, qy, qx) -> at k: [0] B_z F_x, [1] B_z F_y, [2] D_z F_z
-    for (int t = threadIdx.x; t < ne * nc * NQ * NQ; t += THREADS) {
+    for (int t = tid0; t < ne * nc * NQ * NQ; t += STRIDE) {
         const int qx = t % NQ, qy = (t / NQ) % NQ, c = (t / (NQ * NQ)) % nc, el = t / (NQ * NQ * nc);
         T f0[NQ], f1[NQ], f2[NQ];
 #pragma unroll
@@ -387,9 +395,9 @@ __device__ __forceinline__ void residual_sf_stages(
             }
         }
     }
-    __syncthreads();
+    stage_sync();
     // ---- phase 2, y^T: line (el, c, k, qx) -> at j: [0] B_y [0], [1] D_y [1] + B_y [2]
-    for (int t = threadIdx.x; t < ne * nc * N1 * NQ; t += THREADS) {
+    for (int t = tid0; t < ne * nc * N1 * NQ; t += STRIDE) {
         const int qx = t % NQ, k = (t / NQ) % N1, c = (t / (NQ * N1)) % nc, el = t / (NQ * N1 * nc);
         T y0[NQ], y1[NQ], y2[NQ];
 #pragma unroll
@@ -413,9 +421,9 @@ __device__ __forceinline__ void residual_sf_stages(
             if constexpr (GRAD) sX[el][c][1][(k * N1 + j) * NQ + qx] = v1;
         }
     }
-    __syncthreads();
+    stage_sync();
     // ---- phase 2, x^T: line (el, c, k, j) -> r at i = D_x [0] + B_x [1] (mass: B_x [0])
-    for (int t = threadIdx.x; t < ne * nc * N1 * N1; t += THREADS) {
+    for (int t = tid0; t < ne * nc * N1 * N1; t += STRIDE) {
         const int kj = t % (N1 * N1), c = (t / (N1 * N1)) % nc, el = t / (N1 * N1 * nc);
         T x0[NQ], x1[NQ];
 #pragma unroll
@@ -484,6 +492,115 @@ __global__ void __launch_bounds__(THREADS) k_residual_sf(const T *__restrict__ j
         load_material<T, MATK, THREADS>(ne, e0, mat, mat_t, sM);
         __syncthreads();
         residual_sf_stages<T, N1, NQ, KIND, MATK, EPB, THREADS>(ne, nc, e0, sU, sX, sY, sQ, sJ, sW, sM, B, D, r);
+    }
+}
+
+// Float32 residual of Q2 hexahedra with 3 x 3 x 3 points, one element per warp:
+// the same stages as k_residual_sf (lanes = the 27 lines or points of the
+// element; Laplace uses 9 lines), synchronised within the warp only, with the
+// inputs of the warp's next element (J^-1, w det J, the gathered DOFs, the
+// material) loaded into registers while the stages of the current one run, and
+// the connectivity two elements ahead.  Each warp has its own stage buffers.
+template <int KIND, int MATK, int WPC>
+__global__ void __launch_bounds__(WPC * 32) k_residual_sfw(const float *__restrict__ jinv,
+                                                         const float *__restrict__ wdetj,
+                                                         const float *__restrict__ b1d, const float *__restrict__ d1d,
+                                                         const int32_t *__restrict__ conn, long long E, int ncomp,
+                                                         const double *__restrict__ mat, int mat_t,
+                                                         const float *__restrict__ u, float *__restrict__ r,
+                                                         long long n_nodes, unsigned long long *__restrict__ status)
+{
+    constexpr int N1 = 3, NQ = 3, N = 27, Q = 27;
+    constexpr bool GRAD = KIND != FK_MASS;
+    constexpr int NC = KIND == FK_LAPLACE ? 1 : 3;  // max components
+    constexpr int NM = GRAD ? 3 : 1;
+    constexpr int LX = N1 * N1 * NQ, LY = N1 * NQ * NQ;
+    constexpr int NJ = (Q * 9 + 31) / 32;  // J^-1 loads per lane
+    __shared__ float sU[WPC][1][NC][N];
+    __shared__ float sX[WPC][1][NC][GRAD ? 2 : 1][LX];
+    __shared__ float sY[WPC][1][NC][NM][LY];
+    __shared__ float sQ[WPC][1][NC][NM][Q];
+    __shared__ float sJ[WPC][1][Q][9];
+    __shared__ float sW[WPC][1][Q];
+    __shared__ float sM[WPC][1][36];
+    float B[NQ][N1], D[NQ][N1];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int i = 0; i < N1; ++i) {
+            B[q][i] = b1d[q * N1 + i];
+            D[q][i] = d1d[q * N1 + i];
+        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nc = ncomp;
+    const long long gstride = (long long)gridDim.x * WPC;
+    float pj[NJ], pw = 0.0f, pu[NC], pm[2] = {0.0f, 0.0f};
+    int pnode = 0;
+    auto fetch_node = [&](long long e) {
+        if (e < E && lane < N) pnode = conn[e * N + lane];
+    };
+    auto fetch = [&](long long e) {  // with pnode = the lane's node of element e
+        if (e >= E) return;
+#pragma unroll
+        for (int i = 0; i < NJ; ++i) {
+            const int t = lane + 32 * i;
+            if (GRAD && t < Q * 9) pj[i] = jinv[e * (Q * 9) + t];
+        }
+        if (lane < Q) pw = wdetj[e * Q + lane];
+        if (lane < N) {
+            const bool ok = (unsigned)pnode < (unsigned long long)n_nodes;  // never read outside u
+            if (!ok) fe_report(status, FE_ERR_SHAPE, e);
+            const long long nd = ok ? pnode : 0;
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (c < nc) pu[c] = ok ? u[nd * nc + c] : 0.0f;
+        }
+        if constexpr (MATK == 2) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int t = lane + 32 * h;
+                if (t < 36) {
+                    const int I = t / 6, Kv = t % 6;
+                    pm[h] = (float)(mat_t ? mat[e * 36 + Kv * 6 + I] : mat[e * 36 + I * 6 + Kv]);
+                }
+            }
+        } else if constexpr (MATK == 1) {
+            if (lane < 2) pm[0] = (float)mat[e * 2 + lane];
+        } else {
+            if (lane == 0) pm[0] = mat ? (float)mat[e] : 1.0f;
+        }
+    };
+    long long e = (long long)blockIdx.x * WPC + w;
+    fetch_node(e);
+    fetch(e);
+    fetch_node(e + gstride);
+    for (; e < E; e += gstride) {
+        __syncwarp();  // the stages of the previous element are done with the buffers
+#pragma unroll
+        for (int i = 0; i < NJ; ++i) {
+            const int t = lane + 32 * i;
+            if (GRAD && t < Q * 9) (&sJ[w][0][0][0])[t] = pj[i];
+        }
+        if (lane < Q) sW[w][0][lane] = pw;
+        if (lane < N) {
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                if (c < nc) sU[w][0][c][lane] = pu[c];
+        }
+        if constexpr (MATK == 2) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (lane + 32 * h < 36) sM[w][0][lane + 32 * h] = pm[h];
+        } else if constexpr (MATK == 1) {
+            if (lane < 2) sM[w][0][lane] = pm[0];
+        } else {
+            if (lane == 0) sM[w][0][0] = pm[0];
+        }
+        fetch(e + gstride);
+        fetch_node(e + 2 * gstride);
+        __syncwarp();
+        residual_sf_stages<float, N1, NQ, KIND, MATK, 1, 32, true>(1, nc, e, sU[w], sX[w], sY[w], sQ[w], sJ[w], sW[w],
+                                                                   sM[w], B, D, r);
     }
 }
 
@@ -637,6 +754,49 @@ cudaError_t launch_res_sf(const fe_geometry_h *g, const fe_form_h *f, fe_materia
     return cudaGetLastError();
 }
 
+template <int KIND, int MATK>
+cudaError_t launch_res_sfw(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
+                           unsigned long long *st, cudaStream_t s)
+{
+    constexpr int WPC = 8;
+    auto kern = k_residual_sfw<KIND, MATK, WPC>;
+    static FeLaunchCache cache;
+    long long cap = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int dev, long long *v) {
+            int sms = 0, per_sm = 0;
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaError_t e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WPC * 32, 0);
+            if (e2 != cudaSuccess) return e2;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            *v = (long long)per_sm * sms;  // one resident wave; warps stride over the elements
+            return cudaSuccess;
+        },
+        &cap);
+    if (err != cudaSuccess) return err;
+    const long long E = g->mesh.n_elems;
+    long long blocks = (E + WPC - 1) / WPC;
+    if (blocks > cap) blocks = cap;
+    kern<<<(unsigned)blocks, WPC * 32, 0, s>>>(g->d_jinv32, g->d_wdetj32, g->d_b1d32, g->d_d1d32, g->mesh.conn, E,
+                                                f->ncomp, mat.data, mat.transposed, (const float *)u, (float *)r,
+                                                g->mesh.n_nodes, st);
+    return cudaGetLastError();
+}
+
+cudaError_t dispatch_sfw(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
+                         unsigned long long *st, cudaStream_t s)
+{
+    switch (f->kind) {
+    case FK_LAPLACE: return launch_res_sfw<FK_LAPLACE, 0>(g, f, mat, u, r, st, s);
+    case FK_MASS: return launch_res_sfw<FK_MASS, 0>(g, f, mat, u, r, st, s);
+    case FK_ELASTICITY:
+        if (mat.kind == FE_MAT_LAME) return launch_res_sfw<FK_ELASTICITY, 1>(g, f, mat, u, r, st, s);
+        return launch_res_sfw<FK_ELASTICITY, 2>(g, f, mat, u, r, st, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 template <typename T, int N1, int NQ, int EPB_S, int EPB_V>
 cudaError_t dispatch_sf_kind(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, const void *u, void *r,
                              unsigned long long *st, cudaStream_t s)
@@ -661,7 +821,10 @@ cudaError_t dispatch_sf(const fe_geometry_h *g, const fe_form_h *f, fe_material_
     constexpr bool D = sizeof(T) == 8;
     if (n1 == 2 && nq == 2) return dispatch_sf_kind<T, 2, 2, 16, 8>(g, f, mat, u, r, st, s);
     if (n1 == 2 && nq == 3) return dispatch_sf_kind<T, 2, 3, 8, 4>(g, f, mat, u, r, st, s);
-    if (n1 == 3 && nq == 3) return dispatch_sf_kind<T, 3, 3, (D ? 4 : 8), (D ? 2 : 9)>(g, f, mat, u, r, st, s);
+    if (n1 == 3 && nq == 3) {
+        if constexpr (!D) return dispatch_sfw(g, f, mat, u, r, st, s);  // float32: one element per warp
+        return dispatch_sf_kind<T, 3, 3, 4, 2>(g, f, mat, u, r, st, s);
+    }
     if (n1 == 3 && nq == 4) return dispatch_sf_kind<T, 3, 4, (D ? 2 : 4), (D ? 1 : 2)>(g, f, mat, u, r, st, s);
     if (n1 == 4 && nq == 4) return dispatch_sf_kind<T, 4, 4, (D ? 2 : 4), 1>(g, f, mat, u, r, st, s);
     return cudaErrorInvalidValue;
