@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(BT, CLS == 0 ? 3 : (CLS == 1 ? 2 : 1)) k_batch
             if (i != loaded) matrix_load_ref<float, N, Q, KIND, T, EPB, BT, STAGE>(it.dphi, smem_raw);          \
             const long long e0 = local * EPB;                                                                   \
             const int ne = (int)(it.E - e0 < EPB ? it.E - e0 : EPB);                                             \
-            matrix_group<float, N, Q, KIND, MATK, T, EPB, BT, STAGE>(it.jinv, it.wdetj, it.phi, e0, ne,         \
+            matrix_group<float, N, Q, KIND, MATK, T, EPB, BT, STAGE>(it.jinv, it.wdetj, it.phi, it.dphi, e0, ne,         \
                                                                      it.ncomp, it.mat, it.mat_t, it.K, smem_raw); \
         }                                                                                                       \
         break;

@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(THREADS) k_matrix_sym(const S *__restrict__ ji
     matrix_load_ref<S, N, Q, KIND, T, EPB, THREADS, STAGE>(dphi, smem_raw);
     for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
         const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
-        matrix_group<S, N, Q, KIND, MATK, T, EPB, THREADS, STAGE>(jinv, wdetj, phi, e0, ne, ncomp, mat, mat_t, K,
+        matrix_group<S, N, Q, KIND, MATK, T, EPB, THREADS, STAGE>(jinv, wdetj, phi, dphi, e0, ne, ncomp, mat, mat_t, K,
                                                                    smem_raw);
     }
     if constexpr (STAGE == STAGE_BULK)
@@ -115,9 +115,11 @@ cudaError_t dispatch(const fe_geometry_h *g, const fe_form_h *f, fe_material_arg
     // Q2: 3x3 tiles, 45 upper tiles per element, 2 elements per 96-thread CTA
     if (N == 27 && Q == 27) return dispatch_nq<S, 27, 27, 3, 2, 96, B, 3, 2, 96, B>(g, f, mat, K, sm, s);
     if (N == 27 && Q == 64) return dispatch_nq<S, 27, 64, 3, 2, 96, B, 3, 2, 96, B>(g, f, mat, K, sm, s);
-    // Q3: 4x4 tiles (136 per element) for FP32 and the scalar forms; FP64
-    // elasticity needs 2x2 tiles (528 per element) to keep 36 accumulators and
-    // writes directly (a 64 x 192 FP64 row block per buffer would not fit)
+    // Q3: 4x4 tiles (136 per element) for the scalar forms; elasticity 2x2 tiles
+    // (528 per element, 36 accumulators: 17 warps per SM instead of the 5 of 4x4
+    // tiles with 144, measured 0.90 against 1.14 ms for 8,000 elements in FP32);
+    // FP64 elasticity writes directly (a 64 x 192 FP64 row block per buffer would
+    // not fit)
     // tetrahedra: P1 2x2 tiles (3 per element), P2 2x2 tiles (15 per element),
     // P3 4x4 tiles (15 per element; FP64 elasticity 2x2, 55 per element)
     if (N == 4 && Q == 5) return dispatch_nq<S, 4, 5, 2, 32, 96, B, 2, 32, 96, B>(g, f, mat, K, sm, s);
@@ -132,7 +134,7 @@ cudaError_t dispatch(const fe_geometry_h *g, const fe_form_h *f, fe_material_arg
         if constexpr (D)
             return dispatch_nq<S, 64, 64, 4, 1, 160, B, 2, 1, 544, STAGE_DIRECT>(g, f, mat, K, sm, s);
         else
-            return dispatch_nq<S, 64, 64, 4, 1, 160, B, 4, 1, 160, B>(g, f, mat, K, sm, s);
+            return dispatch_nq<S, 64, 64, 4, 1, 160, B, 2, 1, 544, B>(g, f, mat, K, sm, s);
     }
     return cudaErrorInvalidValue;
 }

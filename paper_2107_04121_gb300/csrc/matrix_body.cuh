@@ -139,18 +139,23 @@ struct MatrixSmem {
     static constexpr int W_OFF = J_OFF + EPB * Q * 9;
     static constexpr int C_OFF = W_OFF + EPB * Q;
     static constexpr int D_OFF = C_OFF + EPB * 81;      // reference gradients (Q, 3, N), loaded once
-    static constexpr int TOTAL = D_OFF + (GRAD ? Q * 3 * N : 0);
+    // tables above 16 KB (Q3: 48 KB) stay in global memory (read through L1 by the
+    // gradient build), so that the plan leaves room for more resident CTAs
+    static constexpr bool REF_SMEM = GRAD && Q * 3 * N * (int)sizeof(S) <= 16384;
+    static constexpr int TOTAL = D_OFF + (REF_SMEM ? Q * 3 * N : 0);
     static constexpr size_t BYTES = sizeof(S) * (size_t)TOTAL;
 };
 
 // One group of ne <= EPB consecutive elements starting at e0, computed by the
 // THREADS threads of the CTA (one upper-triangle tile per thread; threads past
 // ne * NU only join the barriers).  The reference gradients must already be in
-// the plan's D region (matrix_load_ref).  MATK: 0 scalar coefficient (or none),
+// the plan's D region (matrix_load_ref) when the plan keeps them there
+// (REF_SMEM); otherwise they are read from dphi.  MATK: 0 scalar coefficient (or none),
 // 1 Lame pair, 2 general D (6x6 Voigt).
 template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, int STAGE>
 __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S *__restrict__ wdetj,
-                                             const S *__restrict__ phi, long long e0, int ne, int ncomp,
+                                             const S *__restrict__ phi, const S *__restrict__ dphi, long long e0,
+                                             int ne, int ncomp,
                                              const double *__restrict__ mat, int mat_t, S *__restrict__ K,
                                              unsigned char *smem_raw)
 {
@@ -168,7 +173,7 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
     S *sJ = sm + P::J_OFF;
     S *sW = sm + P::W_OFF;
     S *sC = sm + P::C_OFF;
-    S *sD = sm + P::D_OFF;
+    const S *sD = P::REF_SMEM ? sm + P::D_OFF : dphi;
     const int nrow = ncomp * N;
     {
         if constexpr (STAGE == STAGE_BULK)
@@ -499,7 +504,7 @@ template <typename S, int N, int Q, int KIND, int T, int EPB, int THREADS, int S
 __device__ __forceinline__ void matrix_load_ref(const S *__restrict__ dphi, unsigned char *smem_raw)
 {
     using P = MatrixSmem<S, N, Q, KIND, T, EPB, STAGE>;
-    if constexpr (P::GRAD) {
+    if constexpr (P::REF_SMEM) {
         S *sD = reinterpret_cast<S *>(smem_raw) + P::D_OFF;
         for (int i = threadIdx.x; i < Q * 3 * N; i += THREADS) sD[i] = dphi[i];
     }
