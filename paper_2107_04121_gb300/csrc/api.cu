@@ -431,12 +431,12 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
         e = settle_geometry(gm, ctx->d_status, s);
         if (e == cudaSuccess) e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, s);
     } else {
-        // tensor-core kernels: Q2 elasticity (27 nodes, 27 points) with Lame materials
-        if (form->kind != FK_ELASTICITY || form->mat != FE_MAT_LAME || !(g->N == 27 && g->Q == 27))
-            return FE_ERR_UNSUPPORTED_SPEC;
-        // a stale float32-only deferred handle: the tensor-core kernel computes the
-        // FP64 geometry of its elements itself and stores the float32 copy
-        const bool fused = fe_matrix_tc_geometry_fusable(gm);
+        // tensor-core kernels: 27-node hexahedra with 27 points, Lame elasticity or
+        // the scalar Laplacian
+        if (!fe_matrix_tc_supported(g, form)) return FE_ERR_UNSUPPORTED_SPEC;
+        // elasticity on a stale float32-only deferred handle: the tensor-core kernel
+        // computes the FP64 geometry of its elements itself and stores the float32 copy
+        const bool fused = form->kind == FK_ELASTICITY && fe_matrix_tc_geometry_fusable(gm);
         e = fused ? cudaSuccess : settle_geometry(gm, ctx->d_status, s);
         const int *hold = ctx->hold_next_matrix ? ctx->d_hold : nullptr;
         ctx->hold_next_matrix = 0;

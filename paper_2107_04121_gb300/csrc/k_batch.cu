@@ -29,9 +29,9 @@
 // fe_eval_matrix (each compiled for its item alone, so each runs at its own
 // occupancy), the items spread over the caller's stream and the two side
 // streams by longest-processing-time-first assignment.  In this schedule an
-// item of Lame elasticity on 27-node hexahedra may take a second contraction
-// path, the TF32x3 Gram on the tensor cores (k_matrix_tc), when autotuning finds
-// it faster.  Autotuning times both schedules and keeps the faster; either one
+// item of Lame elasticity or of the scalar Laplacian on 27-node hexahedra may
+// take a second contraction path, the TF32x3 Gram on the tensor cores
+// (k_matrix_tc), when autotuning finds it faster.  Autotuning times both schedules and keeps the faster; either one
 // can be captured in the graph.
 #include <algorithm>
 #include <cstdio>
@@ -233,7 +233,8 @@ struct fe_batch_h {
     std::vector<int> lane;
     // contraction path of each item in the per-item schedule: 0 the Gram blocks on
     // the CUDA cores (k_matrix_sym), 1 the TF32x3 Gram on the tensor cores
-    // (k_matrix_tc; Lame elasticity of 27-node hexahedra with 27 points)
+    // (k_matrix_tc; Lame elasticity and the scalar Laplacian of 27-node
+    // hexahedra with 27 points)
     std::vector<int> path;
 };
 
@@ -550,9 +551,7 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
             const fe_geometry_h *g = b->igeom[i];
             const fe_form_h *f = b->forms[i];
-            if (b->items[i].E == 0 || f->kind != FK_ELASTICITY || f->mat != FE_MAT_LAME || f->mat_transposed ||
-                g->N != 27 || g->Q != 27)
-                continue;
+            if (b->items[i].E == 0 || !fe_matrix_tc_supported(g, f)) continue;
             float t0 = 0.f, t1 = 0.f;
             e = time_path(b, i, 0, s, &t0);
             if (e == cudaSuccess) e = time_path(b, i, 1, s, &t1);

@@ -31,6 +31,12 @@
 //         empty[n % 2] hands the buffer and the accumulator back
 // so the operand build and MMAs of element n+1 overlap the epilogue of n.
 //
+// The weighted weak Laplacian of the same elements ('0,0.i,0.i', per-element c) is
+// the sum of the diagonal blocks of the same Gram matrix, K[a][b] = c sum_j A_jj[a][b]
+// (FORM = TC_LAPL): the operands and the MMA chain are those of elasticity, the
+// epilogue adds the three diagonal blocks published by the consumer warps and
+// writes the 27 x 27 matrix.
+//
 // With a stale float32-only deferred geometry (Q2, 3x3x3 Gauss points) two
 // more warps per CTA compute the FP64 geometry themselves, one element at a time
 // (lanes = 1-D lines of the collocation stages of the geometry kernel, same
@@ -63,6 +69,7 @@ constexpr int TC_EX_STRIDE = 28;  // floats per row of the exchange blocks (16-b
 constexpr long long TC_WAIT_CYCLES = 4000000000ll;  // about two seconds at 2 GHz
 
 enum TcMode { TC_TF32X3 = 0, TC_BF16X3 = 1, TC_BF16 = 2 };
+enum TcForm { TC_ELAST = 0, TC_LAPL = 1 };  // Lame elasticity, weighted Laplacian
 constexpr int TC_NGEO = 2;  // geometry warps per CTA (GEO)
 
 // K-major, non-swizzled canonical layout: 8-row x 16-byte core matrices; the
@@ -378,7 +385,7 @@ struct TcGeoArgs {
 
 constexpr int TC_GEO_WARP = 6;  // first geometry warp
 
-template <int MODE, bool GEO>
+template <int MODE, bool GEO, int FORM>
 __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE == TC_TF32X3 ? 2 : 3)
     k_matrix_tc(const float *__restrict__ jinv, const float *__restrict__ wdetj, const float *__restrict__ dphi,
                 long long E, const double *__restrict__ lame, float *__restrict__ K,
@@ -539,7 +546,11 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
                         pwt[u] = wdetj[e * TC_Q + t / 9];
                     }
                 }
-                if (ptid < 2) plm = lame[2 * e + ptid];
+                if constexpr (FORM == TC_LAPL) {
+                    if (ptid == 0) plm = lame ? lame[e] : 1.0;
+                } else {
+                    if (ptid < 2) plm = lame[2 * e + ptid];
+                }
             }
         };
         prefetch(blockIdx.x);
@@ -731,12 +742,12 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
             // (e) rows (j = warp, a = lane) of the accumulator: the two blocks this warp
             // uses (A_jj, A_j,j+1) -> registers; the accumulator is then handed back
             // to the producers, and the blocks go to the exchange area
-            float d[64];
+            float d[FORM == TC_LAPL ? 32 : 64];
             {
                 const int jn = warp == 2 ? 0 : warp + 1;
                 const uint32_t taddr = tmem + (n % P::NACC) * TC_TMEM_COLS + ((uint32_t)(32 * warp) << 16);
                 tmem_ld32(taddr + 32 * warp, d);
-                tmem_ld32(taddr + 32 * jn, d + 32);
+                if constexpr (FORM == TC_ELAST) tmem_ld32(taddr + 32 * jn, d + 32);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             }
             tc_fence_before();
@@ -747,27 +758,50 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
             if (lane < TC_N) {
                 // ex[w][0] = A_ww, ex[w][1] = A_w,w+1 (rows a, columns b)
                 float *e0 = ex + ((warp * 2 + 0) * TC_N + lane) * P::EX_STRIDE;
-                float *e1 = ex + ((warp * 2 + 1) * TC_N + lane) * P::EX_STRIDE;
-                publish_blocks(d, e0, e1);
+                if constexpr (FORM == TC_ELAST) {
+                    float *e1 = ex + ((warp * 2 + 1) * TC_N + lane) * P::EX_STRIDE;
+                    publish_blocks(d, e0, e1);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 7; ++c)
+                        reinterpret_cast<float4 *>(e0)[c] = make_float4(d[4 * c], d[4 * c + 1], d[4 * c + 2], d[4 * c + 3]);
+                }
             }
             if (ctid == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // staging drained
             named_sync(TC_BAR_CONS, TC_CONS);
 
-            // (f) blocks K_ii and K_i,i+1 of row (i = warp, a = lane), and K_i+1,i as columns
-            const float *dst0 = K + e * (long long)(TC_NROW * TC_NROW);
+            // (f) elasticity: blocks K_ii and K_i,i+1 of row (i = warp, a = lane), and
+            // K_i+1,i as columns; Laplacian: row a, columns 4c..4c+3 per item (a, c)
+            constexpr int NR = FORM == TC_LAPL ? TC_N : TC_NROW;  // rows (and columns) of K_e
+            const float *dst0 = K + e * (long long)(NR * NR);
             const int shift = (int)(((unsigned long long)dst0 % 16) / 4);
             float *kst = ks + shift;
-            if (lane < TC_N) {
-                const float lam = sLM[2 * b], mu = sLM[2 * b + 1];
-                epilogue_rows<P::EX_STRIDE>(warp, d, ex, lane, lam, mu, kst);
+            if constexpr (FORM == TC_ELAST) {
+                if (lane < TC_N) {
+                    const float lam = sLM[2 * b], mu = sLM[2 * b + 1];
+                    epilogue_rows<P::EX_STRIDE>(warp, d, ex, lane, lam, mu, kst);
+                }
+            } else {
+                const float cw = sLM[2 * b];
+                for (int it = ctid; it < TC_N * 7; it += TC_CONS) {
+                    const int a = it / 7, c = it % 7;
+                    const float4 x0 = reinterpret_cast<const float4 *>(ex + (0 * 2 * TC_N + a) * P::EX_STRIDE)[c];
+                    const float4 x1 = reinterpret_cast<const float4 *>(ex + (1 * 2 * TC_N + a) * P::EX_STRIDE)[c];
+                    const float4 x2 = reinterpret_cast<const float4 *>(ex + (2 * 2 * TC_N + a) * P::EX_STRIDE)[c];
+                    const float v[4] = {cw * (x0.x + x1.x + x2.x), cw * (x0.y + x1.y + x2.y),
+                                        cw * (x0.z + x1.z + x2.z), cw * (x0.w + x1.w + x2.w)};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (4 * c + i < TC_N) kst[a * TC_N + 4 * c + i] = v[i];
+                }
             }
             fence_async_smem();
             named_sync(TC_BAR_CONS, TC_CONS);
 
             // (g) one bulk copy per element matrix; buffer b goes back to the producers
             if (ctid == 0) {
-                float *dst = K + e * (long long)(TC_NROW * TC_NROW);
-                constexpr int LEN = TC_NROW * TC_NROW;
+                float *dst = K + e * (long long)(NR * NR);
+                constexpr int LEN = NR * NR;
                 const int head = (4 - shift) % 4;
                 const int body = (LEN - head) / 4 * 4;
                 for (int t = 0; t < head; ++t) dst[t] = kst[t];
@@ -787,7 +821,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
                      : "memory");
 }
 
-template <int MODE, bool GEO>
+template <int MODE, bool GEO, int FORM>
 cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int sm_count,
                       unsigned long long *status, const int *hold, cudaStream_t s)
 {
@@ -795,7 +829,7 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
     static_assert(P::BYTES <= 227 * 1024, "shared memory plan too large");
     static_assert(MODE == TC_TF32X3 || 3 * (P::BYTES + 1024) <= 228 * 1024, "three CTAs per SM in the BF16 modes");
     constexpr int NTHREADS = TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0);
-    auto kern = k_matrix_tc<MODE, GEO>;
+    auto kern = k_matrix_tc<MODE, GEO, FORM>;
     // resident CTAs per SM: shared memory (228 KB per SM, 1 KB reserved per CTA),
     // registers, and the 512 tensor-memory columns of which every CTA holds
     // NACC x TC_TMEM_COLS (a persistent CTA waiting for columns would stall in
@@ -845,19 +879,27 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
     return cudaGetLastError();
 }
 
-template <bool GEO>
+template <bool GEO, int FORM>
 cudaError_t dispatch_tc(const fe_geometry_h *g, fe_material_args mat, fe_precision prec, void *K, int sm_count,
                         unsigned long long *status, const int *hold, cudaStream_t s)
 {
     switch (prec) {
-    case FE_TF32X3: return launch_tc<TC_TF32X3, GEO>(g, mat, K, sm_count, status, hold, s);
-    case FE_BF16X3: return launch_tc<TC_BF16X3, GEO>(g, mat, K, sm_count, status, hold, s);
-    case FE_BF16: return launch_tc<TC_BF16, GEO>(g, mat, K, sm_count, status, hold, s);
+    case FE_TF32X3: return launch_tc<TC_TF32X3, GEO, FORM>(g, mat, K, sm_count, status, hold, s);
+    case FE_BF16X3: return launch_tc<TC_BF16X3, GEO, FORM>(g, mat, K, sm_count, status, hold, s);
+    case FE_BF16: return launch_tc<TC_BF16, GEO, FORM>(g, mat, K, sm_count, status, hold, s);
     default: return cudaErrorNotSupported;
     }
 }
 
 }  // namespace
+
+bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f)
+{
+    // 27-node hexahedra with 27 points: Lame elasticity, or the (weighted) scalar Laplacian
+    if (g->N != TC_N || g->Q != TC_Q) return false;
+    return (f->kind == FK_ELASTICITY && f->mat == FE_MAT_LAME && !f->mat_transposed) ||
+           (f->kind == FK_LAPLACE && f->ncomp == 1);
+}
 
 bool fe_matrix_tc_geometry_fusable(const fe_geometry_h *g)
 {
@@ -873,11 +915,13 @@ cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_m
                                 bool with_geometry, cudaStream_t s)
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
-    if (f->kind != FK_ELASTICITY || mat.kind != FE_MAT_LAME || g->N != TC_N || g->Q != TC_Q)
-        return cudaErrorNotSupported;
+    if (!fe_matrix_tc_supported(g, f)) return cudaErrorNotSupported;
+    const bool elast = f->kind == FK_ELASTICITY;
+    if (elast && mat.kind != FE_MAT_LAME) return cudaErrorNotSupported;
     if (with_geometry) {
-        if (!fe_matrix_tc_geometry_fusable(g)) return cudaErrorNotSupported;
-        return dispatch_tc<true>(g, mat, prec, K, sm_count, status, hold, s);
+        if (!elast || !fe_matrix_tc_geometry_fusable(g)) return cudaErrorNotSupported;
+        return dispatch_tc<true, TC_ELAST>(g, mat, prec, K, sm_count, status, hold, s);
     }
-    return dispatch_tc<false>(g, mat, prec, K, sm_count, status, hold, s);
+    return elast ? dispatch_tc<false, TC_ELAST>(g, mat, prec, K, sm_count, status, hold, s)
+                 : dispatch_tc<false, TC_LAPL>(g, mat, prec, K, sm_count, status, hold, s);
 }

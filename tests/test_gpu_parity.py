@@ -491,6 +491,27 @@ def test_tensor_core_timeout_with_the_geometry_warp(ctx):
     assert rel_matrix_error(K.cpu().numpy(), Kref) <= TOL["bf16x3"]
 
 
+@pytest.mark.parametrize("prec,tol", TC_TOL)
+def test_tensor_core_laplacian_matches_oracle(ctx, prec, tol):
+    """The weighted scalar Laplacian of Q2 hexahedra on the tensor cores, as the
+    sum of the diagonal blocks of the elasticity Gram matrix: every element of a
+    2,352-element mesh (5 or 6 elements per persistent CTA) against the oracle,
+    the zero row sums of the exact matrix, and the unweighted form (c = 1)."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "laplace", 2, (14, 14, 12), 87)
+    K = fe.eval_matrix(ctx, form, P.geom, [_t(mat, torch.float64), None, None], prec)
+    ctx.check()
+    assert K.shape == (2352, 27, 27) and K.dtype == torch.float32
+    Kh = K.cpu().numpy()
+    err = rel_matrix_error(Kh, Kref)
+    assert err <= tol, err
+    scale = np.abs(Kref).max(axis=(1, 2))
+    assert (np.abs(Kh.sum(axis=2)).max(axis=1) / scale).max() <= 30 * tol
+    K1 = fe.eval_matrix(ctx, fe.laplace_form(), P.geom, [None, None], prec)
+    ctx.check()
+    wdetJ, G, _ = P.oracle_geometry()
+    assert rel_matrix_error(K1.cpu().numpy(), oracle.matrix_laplace(wdetJ, G)) <= tol
+
+
 def test_tensor_core_paths_reject_other_forms(ctx):
     mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
     P = Problem(ctx, mesh, 2, 3)
@@ -551,8 +572,8 @@ def test_argument_errors(ctx):
     with pytest.raises(fe.FEError) as ei:
         fe.eval_matrix(ctx, form, P.geom, [None, None], "f64", diff_op=0)  # not the state operand
     assert ei.value.status == fe.FE_ERR_INVALID_ARG
-    with pytest.raises(fe.FEError) as ei:  # no tensor-core kernel for the Laplacian
-        fe.eval_matrix(ctx, form, P.geom, [None, None], "bf16x3")
+    with pytest.raises(fe.FEError) as ei:  # no tensor-core kernel for the mass matrix
+        fe.eval_matrix(ctx, fe.mass_form(), P.geom, [None, None], "bf16x3")
     assert ei.value.status == fe.FE_ERR_UNSUPPORTED_SPEC
     # unsupported (N, Q) pair
     pts, w, phi, dphi = fe.refbasis_hex(2, 2)
