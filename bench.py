@@ -63,9 +63,12 @@ CV_FLOPS_PER_ELEM = 972 + 1458 + 1944 + 1944 + 6804 + 20412 + 56862
 FP64_PEAK_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor), nominal
 # DRAM bytes (read + write) of one launch of the step's matrix kernel, per precision
 # key "matrix_geo_<prec>", from an ncu capture of the current kernel (the command is
-# in profiles/); empty until the kernel that computes the geometry is captured,
-# and then null for every other size or precision.
-MEASURED_TRAFFIC_48 = {}
+# in profiles/), null for every other size or precision.  The capture runs the
+# 32^3 case (32,768 elements: 11.2 MB read + 836.3 MB written in one launch) and is
+# scaled to the 110,592 elements of the 48^3 launch by the element count; at 32^3
+# up to the 129 MB L2 still holds written lines when the kernel ends, so the
+# scaled figure is a lower bound.
+MEASURED_TRAFFIC_48 = {"matrix_geo_bf16x3": (11246080 + 836300800) * 110592 // 32768}
 # FP64 operations (an FMA counts 2) that the collocation geometry executes for one
 # Q2 element with 3x3x3 Gauss points: three 1-D interpolations of 27 lines each
 # (6 FMA a line: the middle point is the middle node), J on the points (81 lines of
