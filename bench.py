@@ -720,7 +720,7 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
     plan_s = time.perf_counter() - t0
     same_out = [(g, f, m, K) for (g, f, m, _), K in zip(items, batch.outputs)]
     mats_p = fe.Batch(ctx, same_out, fe.BATCH_AUTOTUNE | fe.BATCH_PERSISTENT)
-    mats_l = fe.Batch(ctx, same_out, fe.BATCH_LAUNCHES)
+    mats_l = fe.Batch(ctx, same_out, fe.BATCH_AUTOTUNE | fe.BATCH_LAUNCHES)  # contraction paths tuned
 
     def timed(fn):
         for _ in range(warmup):

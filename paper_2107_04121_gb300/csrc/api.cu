@@ -432,8 +432,8 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
         if (e == cudaSuccess) e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, s);
     } else {
         // tensor-core kernels: 27-node hexahedra with 27 points, Lame elasticity or
-        // the scalar Laplacian
-        if (!fe_matrix_tc_supported(g, form)) return FE_ERR_UNSUPPORTED_SPEC;
+        // the scalar Laplacian; 64-node hexahedra with 64 points, Lame elasticity (TF32x3)
+        if (!fe_matrix_tc_supported(g, form, prec)) return FE_ERR_UNSUPPORTED_SPEC;
         // elasticity on a stale float32-only deferred handle: the tensor-core kernel
         // computes the FP64 geometry of its elements itself and stores the float32 copy
         const bool fused = form->kind == FK_ELASTICITY && fe_matrix_tc_geometry_fusable(gm);

@@ -117,9 +117,12 @@ cudaError_t fe_launch_matrix(const fe_geometry_h *g, const fe_form_h *f, fe_mate
 cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
                                 void *K, int sm_count, unsigned long long *status, const int *hold,
                                 bool with_geometry, cudaStream_t s);
-// Whether the tensor-core matrix kernel covers the form on these elements
-// (27-node hexahedra with 27 points: Lame elasticity, the scalar Laplacian).
-bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f);
+// Whether a tensor-core matrix kernel covers the form on these elements in this
+// precision (27-node hexahedra with 27 points: Lame elasticity, the scalar
+// Laplacian; 64-node hexahedra with 64 points: Lame elasticity in TF32x3).
+bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f, fe_precision prec);
+cudaError_t fe_launch_matrix_tc64(const fe_geometry_h *g, fe_material_args mat, fe_precision prec, void *K,
+                                  int sm_count, unsigned long long *status, cudaStream_t s);
 bool fe_matrix_tc_geometry_fusable(const fe_geometry_h *g);
 cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
                                const void *u, void *r, unsigned long long *status, cudaStream_t s);

@@ -551,7 +551,7 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
             const fe_geometry_h *g = b->igeom[i];
             const fe_form_h *f = b->forms[i];
-            if (b->items[i].E == 0 || !fe_matrix_tc_supported(g, f)) continue;
+            if (b->items[i].E == 0 || !fe_matrix_tc_supported(g, f, FE_TF32X3)) continue;
             float t0 = 0.f, t1 = 0.f;
             e = time_path(b, i, 0, s, &t0);
             if (e == cudaSuccess) e = time_path(b, i, 1, s, &t1);

@@ -51,10 +51,9 @@
 // element n of a CTA goes to its geometry warp n % 2.  (Claiming elements from a
 // grid-wide counter, with the producers taking whichever slot is filled first,
 // measured 4% slower: shared memory, not the FP64 units, sets the pace.)
-#include <cuda_bf16.h>
-
 #include "fe_device.cuh"
 #include "geometry_body.cuh"
+#include "tc_device.cuh"
 
 namespace {
 
@@ -66,174 +65,8 @@ constexpr int TC_TMEM_COLS = 128;
 constexpr int TC_NROW = 3 * TC_N;  // 81
 constexpr int TC_JW_STRIDE = 12;  // floats per point of the staged sqrt(w det J) J^-1 (16-byte rows)
 constexpr int TC_EX_STRIDE = 28;  // floats per row of the exchange blocks (16-byte rows, conflict-free float4)
-constexpr long long TC_WAIT_CYCLES = 4000000000ll;  // about two seconds at 2 GHz
-
-enum TcMode { TC_TF32X3 = 0, TC_BF16X3 = 1, TC_BF16 = 2 };
 enum TcForm { TC_ELAST = 0, TC_LAPL = 1 };  // Lame elasticity, weighted Laplacian
 constexpr int TC_NGEO = 2;  // geometry warps per CTA (GEO)
-
-// K-major, non-swizzled canonical layout: 8-row x 16-byte core matrices; the
-// K chunks of one 8-row group are adjacent (LBO = 128 B), 8-row groups follow
-// each other (SBO = all K chunks of a group).
-template <int EB>
-struct OpLayout {
-    static constexpr int CHUNK = 16 / EB;         // K values per core-matrix row
-    static constexpr int KCHUNKS = TC_KPAD / CHUNK;  // 8 (4-byte) or 4 (2-byte)
-    static constexpr int LBO = 128;
-    static constexpr int SBO = KCHUNKS * 128;
-    static constexpr int BYTES = (TC_M / 8) * SBO;  // 16 KB or 8 KB
-    __device__ static int offset(int m, int k)
-    {
-        return (m >> 3) * SBO + (k / CHUNK) * LBO + (m & 7) * 16 + (k % CHUNK) * EB;
-    }
-};
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// tcgen05 shared-memory matrix descriptor: start address, LBO, SBO (all >> 4),
-// descriptor version 1 (bits 46-47), no base offset, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, int lbo, int sbo)
-{
-    uint64_t d = (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= 1ull << 46;
-    return d;
-}
-
-// Instruction descriptor of kind::tf32 / kind::f16: FP32 accumulator (bits 4-5),
-// A and B formats (bits 7-9, 10-12: 1 = BF16, 2 = TF32), both K-major,
-// N >> 3 (bits 17-22), M >> 4 (bits 24-28).
-__host__ __device__ constexpr uint32_t instr_desc(uint32_t fmt)
-{
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(TC_NCOL >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-}
-
-template <int MODE>
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate)
-{
-    if constexpr (MODE == TC_TF32X3) {
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(instr_desc(2)), "r"(accumulate)
-            : "memory");
-    } else {
-        asm volatile(
-            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-            "l"(a), "l"(b), "r"(instr_desc(1)), "r"(accumulate)
-            : "memory");
-    }
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
-{
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ void bulk_store(void *gdst, const void *ssrc, unsigned bytes)
-{
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_u32(ssrc)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-// split x into hi + lo in the operand format; returns the two 32-bit or 16-bit patterns
-template <int MODE>
-__device__ __forceinline__ void split(float x, uint32_t &hi, uint32_t &lo)
-{
-    if constexpr (MODE == TC_TF32X3) {
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
-        const float r = x - __uint_as_float(hi);
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
-    } else {
-        const __nv_bfloat16 h = __float2bfloat16_rn(x);
-        const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-        hi = (uint32_t)__bfloat16_as_ushort(h);
-        lo = (uint32_t)__bfloat16_as_ushort(l);
-    }
-}
-
-// Two values in bf16 (x1 in the upper half, x0 in the lower), with the bf16
-// rounding of the residuals x - hi in lo: hi + lo carries about 16 bits of x.
-__device__ __forceinline__ uint32_t pack_bf16x2(float x1, float x0)
-{
-    uint32_t r;
-    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
-    return r;
-}
-
-__device__ __forceinline__ void split_bf16x2(float x1, float x0, uint32_t &hi, uint32_t &lo)
-{
-    hi = pack_bf16x2(x1, x0);
-    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
-    lo = pack_bf16x2(x1 - h1, x0 - h0);
-}
-
-// One operand tile of phase (b): this lane's node a and points q of its 4-byte
-// segment, for the three gradient rows j.  All shared-memory reads happen
-// before the stores (the buffers do not alias).
-template <int MODE, int SEGV, int CHUNK>
-__device__ __forceinline__ void operand_tile(const float *__restrict__ dp, const float *__restrict__ jw, int a, int q0,
-                                             unsigned char *__restrict__ hi, unsigned char *__restrict__ lo,
-                                             const int *__restrict__ off)
-{
-    uint32_t hv[3] = {0, 0, 0}, lv[3] = {0, 0, 0};
-    float x[SEGV][3];
-#pragma unroll
-    for (int v = 0; v < SEGV; ++v) {
-        const int q = q0 + v;
-        const bool ok = a < TC_N && q < TC_Q;
-        const int qq = ok ? q : 0, aa = ok ? a : 0;
-        const float d0 = dp[qq * 3 * TC_N + aa], d1 = dp[qq * 3 * TC_N + TC_N + aa],
-                    d2 = dp[qq * 3 * TC_N + 2 * TC_N + aa];
-        float J[9];
-#pragma unroll
-        for (int t = 0; t < 9; ++t) J[t] = jw[qq * 9 + t];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) x[v][j] = ok ? d0 * J[j] + d1 * J[3 + j] + d2 * J[6 + j] : 0.0f;
-    }
-#pragma unroll
-    for (int v = 0; v < SEGV; ++v)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            uint32_t h, l;
-            split<MODE>(x[v][j], h, l);
-            hv[j] |= h << (16 * v);
-            lv[j] |= l << (16 * v);
-        }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        *reinterpret_cast<uint32_t *>(hi + off[j]) = hv[j];
-        if constexpr (MODE != TC_BF16) *reinterpret_cast<uint32_t *>(lo + off[j]) = lv[j];
-    }
-}
 
 // Diagonal block of K_e for row (i, a): own A_ii[a][.] from registers, the
 // other warps' diagonal blocks from the exchange area; all reads before stores.
@@ -304,7 +137,7 @@ __device__ __forceinline__ void epilogue_rows(int I, const float *d, const float
 template <int MODE, bool GEO>
 struct TcSmem {
     static constexpr int EB = MODE == TC_TF32X3 ? 4 : 2;
-    using L = OpLayout<EB>;
+    using L = OpLayout<EB, TC_KPAD, TC_M>;
     // per buffer: hi and lo operands; the exchange area [3 warps][2 blocks][27][28]
     // floats of the epilogue reuses them once the buffer's MMAs have completed
     static constexpr int EX_STRIDE = TC_EX_STRIDE;
@@ -347,31 +180,6 @@ constexpr int TC_CONS = 96;               // consumer threads (warps 0-2)
 constexpr int TC_PROD = 96;               // producer threads (warps 3-5)
 constexpr int TC_THREADS_WS = TC_CONS + TC_PROD;
 constexpr int TC_BAR_PROD = 1, TC_BAR_CONS = 2;  // named barriers
-
-__device__ __forceinline__ void named_sync(int id, int n)
-{
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-// Wait on an mbarrier phase, giving up after TC_WAIT_CYCLES or when the CTA aborts.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, volatile int *abort_flag)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (*abort_flag || clock64() - t0 > TC_WAIT_CYCLES) return false;
-    }
-    return true;
-}
-
-// The same wait bounded by time alone (the drain of an aborting CTA).
-__device__ __forceinline__ bool mbar_wait_cycles(uint32_t bar, uint32_t parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > TC_WAIT_CYCLES) return false;
-    }
-    return true;
-}
 
 // The arrays of the geometry warp (GEO): the mesh, the FP64 tables of the
 // collocation stages and the handle's float32 copy it writes.
@@ -691,11 +499,11 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
 #pragma unroll
                 for (int s = 0; s < NSTEP; ++s) {
                     const uint64_t dh = smem_desc(hi + s * KSTEP_BYTES, L::LBO, L::SBO);
-                    mma<MODE>(d_tmem, dh, dh, s > 0 ? 1u : 0u);
+                    mma<MODE, TC_M, TC_NCOL>(d_tmem, dh, dh, s > 0 ? 1u : 0u);
                     if constexpr (MODE != TC_BF16) {
                         const uint64_t dl = smem_desc(lo + s * KSTEP_BYTES, L::LBO, L::SBO);
-                        mma<MODE>(d_tmem, dh, dl, 1u);
-                        mma<MODE>(d_tmem, dl, dh, 1u);
+                        mma<MODE, TC_M, TC_NCOL>(d_tmem, dh, dl, 1u);
+                        mma<MODE, TC_M, TC_NCOL>(d_tmem, dl, dh, 1u);
                     }
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -893,12 +701,14 @@ cudaError_t dispatch_tc(const fe_geometry_h *g, fe_material_args mat, fe_precisi
 
 }  // namespace
 
-bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f)
+bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f, fe_precision prec)
 {
+    const bool lame = f->kind == FK_ELASTICITY && f->mat == FE_MAT_LAME && !f->mat_transposed;
+    // 64-node hexahedra with 64 points: Lame elasticity in TF32x3 (k_matrix_tc64.cu)
+    if (g->N == 64 && g->Q == 64) return lame && prec == FE_TF32X3;
     // 27-node hexahedra with 27 points: Lame elasticity, or the (weighted) scalar Laplacian
     if (g->N != TC_N || g->Q != TC_Q) return false;
-    return (f->kind == FK_ELASTICITY && f->mat == FE_MAT_LAME && !f->mat_transposed) ||
-           (f->kind == FK_LAPLACE && f->ncomp == 1);
+    return lame || (f->kind == FK_LAPLACE && f->ncomp == 1);
 }
 
 bool fe_matrix_tc_geometry_fusable(const fe_geometry_h *g)
@@ -915,7 +725,11 @@ cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_m
                                 bool with_geometry, cudaStream_t s)
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
-    if (!fe_matrix_tc_supported(g, f)) return cudaErrorNotSupported;
+    if (!fe_matrix_tc_supported(g, f, prec)) return cudaErrorNotSupported;
+    if (g->N == 64) {
+        if (with_geometry || hold) return cudaErrorNotSupported;
+        return fe_launch_matrix_tc64(g, mat, prec, K, sm_count, status, s);
+    }
     const bool elast = f->kind == FK_ELASTICITY;
     if (elast && mat.kind != FE_MAT_LAME) return cudaErrorNotSupported;
     if (with_geometry) {

@@ -512,6 +512,26 @@ def test_tensor_core_laplacian_matches_oracle(ctx, prec, tol):
     assert rel_matrix_error(K1.cpu().numpy(), oracle.matrix_laplace(wdetJ, G)) <= tol
 
 
+def test_tensor_core_q3_elasticity_matches_oracle(ctx):
+    """Q3 Lame elasticity (64-node hexahedra, 4 x 4 x 4 points) on the tensor cores in
+    TF32x3: the 192-row Gram in two MMA tiles, K_e staged by 64-row blocks; every
+    element of a 384-element mesh (two or three elements per persistent CTA) against
+    the oracle, symmetry, and BF16 precisions rejected for this element."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, "elasticity", 3, (8, 8, 6), 89)
+    args = [_t(mat, torch.float64), None, None]
+    K = fe.eval_matrix(ctx, form, P.geom, args, "tf32x3")
+    ctx.check()
+    assert K.shape == (384, 192, 192) and K.dtype == torch.float32
+    Kh = K.cpu().numpy()
+    err = rel_matrix_error(Kh, Kref)
+    assert err <= TOL["tf32x3"], err
+    assert np.abs(Kh - Kh.transpose(0, 2, 1)).max() <= 10 * TOL["tf32x3"] * np.abs(Kh).max()
+    for prec in ("bf16x3", "bf16"):
+        with pytest.raises(fe.FEError) as ei:
+            fe.eval_matrix(ctx, form, P.geom, args, prec)
+        assert ei.value.status == fe.FE_ERR_UNSUPPORTED_SPEC
+
+
 def test_tensor_core_paths_reject_other_forms(ctx):
     mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
     P = Problem(ctx, mesh, 2, 3)
