@@ -119,10 +119,12 @@ cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_m
                                 bool with_geometry, cudaStream_t s);
 // Whether a tensor-core matrix kernel covers the form on these elements in this
 // precision (27-node hexahedra with 27 points: Lame elasticity, the scalar
-// Laplacian; 64-node hexahedra with 64 points: Lame elasticity in TF32x3).
+// Laplacian; 64-node hexahedra with 64 points, TF32x3: Lame elasticity, the
+// scalar Laplacian and the scalar mass matrix).
 bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f, fe_precision prec);
-cudaError_t fe_launch_matrix_tc64(const fe_geometry_h *g, fe_material_args mat, fe_precision prec, void *K,
-                                  int sm_count, unsigned long long *status, cudaStream_t s);
+cudaError_t fe_launch_matrix_tc64(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat,
+                                  fe_precision prec, void *K, int sm_count, unsigned long long *status,
+                                  cudaStream_t s);
 bool fe_matrix_tc_geometry_fusable(const fe_geometry_h *g);
 cudaError_t fe_launch_residual(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
                                const void *u, void *r, unsigned long long *status, cudaStream_t s);

@@ -704,8 +704,10 @@ cudaError_t dispatch_tc(const fe_geometry_h *g, fe_material_args mat, fe_precisi
 bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f, fe_precision prec)
 {
     const bool lame = f->kind == FK_ELASTICITY && f->mat == FE_MAT_LAME && !f->mat_transposed;
-    // 64-node hexahedra with 64 points: Lame elasticity in TF32x3 (k_matrix_tc64.cu)
-    if (g->N == 64 && g->Q == 64) return lame && prec == FE_TF32X3;
+    // 64-node hexahedra with 64 points, TF32x3 (k_matrix_tc64.cu): Lame elasticity,
+    // the scalar Laplacian and the scalar mass matrix
+    if (g->N == 64 && g->Q == 64)
+        return prec == FE_TF32X3 && (lame || ((f->kind == FK_LAPLACE || f->kind == FK_MASS) && f->ncomp == 1));
     // 27-node hexahedra with 27 points: Lame elasticity, or the (weighted) scalar Laplacian
     if (g->N != TC_N || g->Q != TC_Q) return false;
     return lame || (f->kind == FK_LAPLACE && f->ncomp == 1);
@@ -728,7 +730,7 @@ cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_m
     if (!fe_matrix_tc_supported(g, f, prec)) return cudaErrorNotSupported;
     if (g->N == 64) {
         if (with_geometry || hold) return cudaErrorNotSupported;
-        return fe_launch_matrix_tc64(g, mat, prec, K, sm_count, status, s);
+        return fe_launch_matrix_tc64(g, f, mat, prec, K, sm_count, status, s);
     }
     const bool elast = f->kind == FK_ELASTICITY;
     if (elast && mat.kind != FE_MAT_LAME) return cudaErrorNotSupported;

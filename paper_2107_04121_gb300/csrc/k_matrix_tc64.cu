@@ -29,10 +29,19 @@
 //       group of four warps stages a 64 x 192 row block of K_e (contiguous in
 //       global memory) and writes it with one bulk copy; the group of quarters
 //       0-1 does the row blocks 0 and 2, the other group the row block 1.
+// The weighted scalar Laplacian and mass matrix of the same elements ('0,0.i,0.i',
+// '0,i,i', per-element c) take the same kernel (FORM): the Laplacian is
+// c sum_j A_jj, for which the MMAs compute only the diagonal blocks (first tile
+// against columns 0-127, second tile against columns 128-191); the mass matrix
+// is the Gram matrix of sqrt(w det J) phi (64 rows, one tile against 64 columns).
+// Both write a 64 x 64 K_e with one bulk copy.
+//
 // The exchange area and group 0-1's staging reuse the operand buffer once the
 // MMAs are done, so the next element's operands are built after those bulk
 // copies have been read.  Every mbarrier wait is bounded: a timeout is reported
 // as FE_ERR_TIMEOUT and the CTA drains its MMAs and frees tensor memory.
+#include <type_traits>
+
 #include "fe_device.cuh"
 #include "tc_device.cuh"
 
@@ -46,6 +55,7 @@ constexpr int T6_TMEM_COLS = 512;       // tiles at columns 0 and 256 (192 each)
 constexpr int T6_EX = 68;               // floats per row of the exchange blocks (16-byte rows)
 constexpr int T6_JW = 12;               // floats per point of the staged sqrt(w det J) J^-1
 constexpr int T6_BAR_G0 = 1, T6_BAR_G1 = 2;  // named barriers of the two warp groups
+enum T6Form { T6_ELAST = 0, T6_LAPL = 1, T6_MASS = 2 };
 
 struct T6Smem {
     using L = OpLayout<4, T6_Q, T6_OPROWS>;         // TF32 operands: 64 KB each
@@ -72,11 +82,13 @@ __device__ __forceinline__ void store_row32(float *dst, const float *v)
         reinterpret_cast<float4 *>(dst)[c] = make_float4(v[4 * c], v[4 * c + 1], v[4 * c + 2], v[4 * c + 3]);
 }
 
+template <int FORM>
 __global__ void __launch_bounds__(T6_THREADS, 1)
     k_matrix_tc64(const float *__restrict__ jinv, const float *__restrict__ wdetj, const float *__restrict__ dphi,
-                  long long E, const double *__restrict__ lame, float *__restrict__ K,
-                  unsigned long long *__restrict__ status)
+                  const float *__restrict__ phi, long long E, const double *__restrict__ lame,
+                  float *__restrict__ K, unsigned long long *__restrict__ status)
 {
+    constexpr int NR = FORM == T6_ELAST ? T6_ROWS : T6_N;  // rows (and columns) of K_e
     using P = T6Smem;
     using L = P::L;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -117,11 +129,15 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
         for (int k = 0; k < NPF; ++k) {
             const int t = tid + k * T6_THREADS;
             if (t < T6_Q * 9) {
-                pj[k] = jinv[e * (T6_Q * 9) + t];
+                if constexpr (FORM != T6_MASS) pj[k] = jinv[e * (T6_Q * 9) + t];
                 pw[k] = wdetj[e * T6_Q + t / 9];
             }
         }
-        if (tid < 2) plm = lame[2 * e + tid];
+        if constexpr (FORM == T6_ELAST) {
+            if (tid < 2) plm = lame[2 * e + tid];
+        } else {
+            if (tid == 0) plm = lame ? lame[e] : 1.0;
+        }
     };
     prefetch(blockIdx.x);
 
@@ -137,7 +153,13 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
 #pragma unroll
         for (int k = 0; k < NPF; ++k) {
             const int t = tid + k * T6_THREADS;
-            if (t < T6_Q * 9) sJw[(t / 9) * T6_JW + t % 9] = sqrtf(pw[k]) * pj[k];
+            if (t < T6_Q * 9) {
+                if constexpr (FORM == T6_MASS) {
+                    if (t % 9 == 0) sJw[(t / 9) * T6_JW] = sqrtf(pw[k]);  // sqrt(w det J) alone
+                } else {
+                    sJw[(t / 9) * T6_JW + t % 9] = sqrtf(pw[k]) * pj[k];
+                }
+            }
         }
         if (tid < 2) sLM[tid] = (float)plm;
         prefetch(e + gridDim.x);
@@ -155,6 +177,19 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
             unsigned char *hi = smem + P::HI, *lo = smem + P::LO;
             const int r = lane >> 2, kk = lane & 3;
             const int q = 4 * ((T6_Q / 8) * hk + warp) + kk;
+            if constexpr (FORM == T6_MASS) {
+                // rows a: sqrt(w det J) phi_a(q)
+                const float sw = sJw[q * T6_JW];
+                const float *pq = phi + q * T6_N + r;
+#pragma unroll 4
+                for (int ig = 0; ig < T6_N / 8; ++ig) {
+                    uint32_t h, l;
+                    split<TC_TF32X3>(sw * __ldg(pq + 8 * ig), h, l);
+                    const int off = L::offset(8 * ig + r, q);
+                    *reinterpret_cast<uint32_t *>(hi + off) = h;
+                    *reinterpret_cast<uint32_t *>(lo + off) = l;
+                }
+            } else {
             float jq[9];
 #pragma unroll
             for (int t = 0; t < 9; ++t) jq[t] = sJw[q * T6_JW + t];
@@ -173,25 +208,36 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                     *reinterpret_cast<uint32_t *>(lo + off) = l;
                 }
             }
+            }
             fence_async_smem();  // operand writes -> tensor-core (async) proxy
             __syncthreads();
             if (issuer) {
                 tc_fence_after();
                 const uint32_t hs = smem_u32(smem + P::HI), ls = smem_u32(smem + P::LO);
-#pragma unroll
-                for (int tile = 0; tile < 2; ++tile) {
-                    const uint32_t d_tmem = tmem + 256 * tile;
-                    const uint32_t arow = (uint32_t)(tile * 16 * L::SBO);  // first row 128 tile
+                // one chain of 3 products per K step: rows from `arow`, columns from `brow`
+                auto chain = [&](uint32_t d_tmem, uint32_t arow, uint32_t brow, auto ncols) {
+                    constexpr int NC = decltype(ncols)::value;
 #pragma unroll
                     for (int s2 = hk * NSTEP / 2; s2 < (hk + 1) * NSTEP / 2; ++s2) {
                         const uint64_t ah = smem_desc(hs + arow + s2 * KSTEP_BYTES, L::LBO, L::SBO);
                         const uint64_t al = smem_desc(ls + arow + s2 * KSTEP_BYTES, L::LBO, L::SBO);
-                        const uint64_t bh = smem_desc(hs + s2 * KSTEP_BYTES, L::LBO, L::SBO);
-                        const uint64_t bl = smem_desc(ls + s2 * KSTEP_BYTES, L::LBO, L::SBO);
-                        mma<TC_TF32X3, 128, T6_ROWS>(d_tmem, ah, bh, s2 > 0 ? 1u : 0u);
-                        mma<TC_TF32X3, 128, T6_ROWS>(d_tmem, ah, bl, 1u);
-                        mma<TC_TF32X3, 128, T6_ROWS>(d_tmem, al, bh, 1u);
+                        const uint64_t bh = smem_desc(hs + brow + s2 * KSTEP_BYTES, L::LBO, L::SBO);
+                        const uint64_t bl = smem_desc(ls + brow + s2 * KSTEP_BYTES, L::LBO, L::SBO);
+                        mma<TC_TF32X3, 128, NC>(d_tmem, ah, bh, s2 > 0 ? 1u : 0u);
+                        mma<TC_TF32X3, 128, NC>(d_tmem, ah, bl, 1u);
+                        mma<TC_TF32X3, 128, NC>(d_tmem, al, bh, 1u);
                     }
+                };
+                const uint32_t row128 = (uint32_t)(16 * L::SBO);  // byte offset of operand row 128
+                if constexpr (FORM == T6_ELAST) {
+                    chain(tmem, 0u, 0u, std::integral_constant<int, T6_ROWS>{});
+                    chain(tmem + 256, row128, 0u, std::integral_constant<int, T6_ROWS>{});
+                } else if constexpr (FORM == T6_LAPL) {
+                    // diagonal blocks only: rows 0-127 x columns 0-127, rows 128-191 x columns 128-191
+                    chain(tmem, 0u, 0u, std::integral_constant<int, 128>{});
+                    chain(tmem + 256, row128, row128, std::integral_constant<int, T6_N>{});
+                } else {
+                    chain(tmem, 0u, 0u, std::integral_constant<int, T6_N>{});
                 }
                 if (hk == 1) {
                     asm volatile(
@@ -212,6 +258,8 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
         if (*abort_flag) break;
         tc_fence_after();
 
+        // (d) epilogue
+        if constexpr (FORM == T6_ELAST) {
         // (d) epilogue
         const float lam = sLM[0], mu = sLM[1];
         float *exd = reinterpret_cast<float *>(smem + P::EXD);
@@ -287,6 +335,56 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
         }
+        } else {
+            // Laplacian K = c sum_j A_jj, mass matrix K = c A_00: 64 x 64, one bulk copy
+            const float cw = sLM[0];
+            float *dstg = K + e * (long long)(NR * NR);
+            const int shift = (int)(((unsigned long long)dstg % 16) / 4);
+            float *stg = reinterpret_cast<float *>(smem + P::STG0) + shift;
+            float v[32];
+            const int bl = 32 * (sp & 1) + lane;  // row b of the block held by this lane
+            if constexpr (FORM == T6_MASS) {
+                if (sp < 2) {  // A_00 is symmetric: lane b writes column b of K
+                    tmem_ld32(tmem + tlane + 32 * half, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int t = 0; t < 32; ++t) stg[(32 * half + t) * T6_N + bl] = cw * v[t];
+                }
+            } else {
+                float *exd = reinterpret_cast<float *>(smem + P::EXD);
+                if (sp < 2) {  // A_00 (first tile) and A_22 (second tile, its columns 0-63)
+                    tmem_ld32(tmem + tlane + 32 * half, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    store_row32(exd + (0 * T6_N + bl) * T6_EX + 32 * half, v);
+                    tmem_ld32(tmem + 256 + tlane + 32 * half, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    store_row32(exd + (2 * T6_N + bl) * T6_EX + 32 * half, v);
+                } else {  // A_11: first tile, rows 64-127, columns 64-127
+                    tmem_ld32(tmem + tlane + 64 + 32 * half, v);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    store_row32(exd + (1 * T6_N + bl) * T6_EX + 32 * half, v);
+                }
+                __syncthreads();
+                const int b2 = tid & 63, a0 = (tid >> 6) * 16;  // column b2, rows a0 .. a0 + 15
+#pragma unroll
+                for (int t = 0; t < 16; ++t) {
+                    const int a2 = a0 + t;
+                    stg[a2 * T6_N + b2] = cw * (exd[(0 * T6_N + a2) * T6_EX + b2] + exd[(1 * T6_N + a2) * T6_EX + b2] +
+                                                exd[(2 * T6_N + a2) * T6_EX + b2]);
+                }
+            }
+            fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                constexpr int LEN = T6_N * T6_N;
+                const int head = (4 - shift) % 4;
+                const int body = (LEN - head) / 4 * 4;
+                for (int t = 0; t < head; ++t) dstg[t] = stg[t];
+                for (int t = head + body; t < LEN; ++t) dstg[t] = stg[t];
+                bulk_store(dstg + head, stg + head, (unsigned)(body * 4));
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            }
+        }
         tc_fence_before();  // this element's tensor-memory loads before the next MMAs
     }
     // an aborting CTA frees its tensor memory only after the MMAs it issued are done
@@ -300,29 +398,40 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                      : "memory");
 }
 
-}  // namespace
-
-cudaError_t fe_launch_matrix_tc64(const fe_geometry_h *g, fe_material_args mat, fe_precision prec, void *K,
-                                  int sm_count, unsigned long long *status, cudaStream_t s)
+template <int FORM>
+cudaError_t launch_tc64(const fe_geometry_h *g, fe_material_args mat, void *K, int sm_count,
+                        unsigned long long *status, cudaStream_t s)
 {
-    if (g->mesh.n_elems == 0) return cudaSuccess;
-    if (g->N != T6_N || g->Q != T6_Q || mat.kind != FE_MAT_LAME || prec != FE_TF32X3) return cudaErrorNotSupported;
+    auto kern = k_matrix_tc64<FORM>;
     static FeLaunchCache cache;
     long long per_sm = 0;
     cudaError_t err = fe_cached_grid(
         cache,
         [&](int, long long *v) {
-            cudaError_t e2 =
-                cudaFuncSetAttribute(k_matrix_tc64, cudaFuncAttributeMaxDynamicSharedMemorySize, T6Smem::BYTES);
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T6Smem::BYTES);
             if (e2 != cudaSuccess) return e2;
-            *v = 1;  // 448 of the 512 tensor-memory columns: one CTA per SM
+            *v = 1;  // up to 448 of the 512 tensor-memory columns: one CTA per SM
             return cudaSuccess;
         },
         &per_sm);
     if (err != cudaSuccess) return err;
     long long blocks = per_sm * sm_count;
     if (blocks > g->mesh.n_elems) blocks = g->mesh.n_elems;
-    k_matrix_tc64<<<(unsigned)blocks, T6_THREADS, T6Smem::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32,
-                                                                      g->mesh.n_elems, mat.data, (float *)K, status);
+    kern<<<(unsigned)blocks, T6_THREADS, T6Smem::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->d_phi32,
+                                                             g->mesh.n_elems, mat.data, (float *)K, status);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t fe_launch_matrix_tc64(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat,
+                                  fe_precision prec, void *K, int sm_count, unsigned long long *status,
+                                  cudaStream_t s)
+{
+    if (g->mesh.n_elems == 0) return cudaSuccess;
+    if (g->N != T6_N || g->Q != T6_Q || prec != FE_TF32X3) return cudaErrorNotSupported;
+    if (f->kind == FK_ELASTICITY && mat.kind == FE_MAT_LAME) return launch_tc64<T6_ELAST>(g, mat, K, sm_count, status, s);
+    if (f->kind == FK_LAPLACE && f->ncomp == 1) return launch_tc64<T6_LAPL>(g, mat, K, sm_count, status, s);
+    if (f->kind == FK_MASS && f->ncomp == 1) return launch_tc64<T6_MASS>(g, mat, K, sm_count, status, s);
+    return cudaErrorNotSupported;
 }

@@ -532,6 +532,21 @@ def test_tensor_core_q3_elasticity_matches_oracle(ctx):
         assert ei.value.status == fe.FE_ERR_UNSUPPORTED_SPEC
 
 
+@pytest.mark.parametrize("kind", ["laplace", "mass1"])
+def test_tensor_core_q3_scalar_forms_match_oracle(ctx, kind):
+    """The weighted scalar Laplacian (diagonal Gram blocks only) and mass matrix
+    (Gram of sqrt(w det J) phi) of Q3 hexahedra on the tensor cores in TF32x3: every
+    element of a 384-element mesh against the oracle, and symmetry."""
+    P, form, mat, u, Kref, rref, _ = _case(ctx, kind, 3, (8, 8, 6), 91)
+    K = fe.eval_matrix(ctx, form, P.geom, [_t(mat, torch.float64), None, None], "tf32x3")
+    ctx.check()
+    assert K.shape == (384, 64, 64) and K.dtype == torch.float32
+    Kh = K.cpu().numpy()
+    err = rel_matrix_error(Kh, Kref)
+    assert err <= TOL["tf32x3"], err
+    assert np.abs(Kh - Kh.transpose(0, 2, 1)).max() <= 10 * TOL["tf32x3"] * np.abs(Kh).max()
+
+
 def test_tensor_core_paths_reject_other_forms(ctx):
     mesh = meshgen.structured_hex(2, 2, 2, 2, 0.0, 0)
     P = Problem(ctx, mesh, 2, 3)
