@@ -99,11 +99,14 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--n", type=int, default=48, help="cube edge in elements (48 -> 110,592 hexes)")
-    ap.add_argument("--workload", choices=["elasticity", "convection", "mixed", "fp64units"], default="elasticity",
+    ap.add_argument("--workload", choices=["elasticity", "convection", "mixed", "paths", "fp64units"],
+                    default="elasticity",
                     help="convection: only the Navier-Stokes convection workload on an n^3 cube (both "
-                         "precisions); mixed: only the mixed-mesh batch; fp64units: the DFMA and FP64 MMA "
-                         "rates (fe_diag_fp64); no oracle, one JSON line")
-    ap.add_argument("--scale", type=float, default=1.0, help="mixed workload: scale of every group")
+                         "precisions); mixed: only the mixed-mesh batch; paths: each mixed-mesh item's matrix "
+                         "on the CUDA-core and the tensor-core contraction path, timed apart; fp64units: the "
+                         "DFMA and FP64 MMA rates (fe_diag_fp64); no oracle, one JSON line")
+    ap.add_argument("--scale", type=float, default=1.0, help="mixed and paths workloads: scale of every group")
+    ap.add_argument("--groups", default="", help="paths workload: comma-separated groups (e.g. Q2,Q3); all if empty")
     ap.add_argument("--prec", default="auto",
                     help="contraction precision of the headline path; auto = fastest of the ladder within 1e-5")
     ap.add_argument("--skip-extras", action="store_true",
@@ -788,6 +791,49 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
     return out
 
 
+def paths_measure(device, flush, steps, warmup, scale=1.0, groups=""):
+    """Each mixed-mesh item's element matrices (FP32 from a stored FP32 geometry) on
+    the CUDA-core path ("f32") and, where a tensor-core kernel covers the item, on the
+    TF32x3 tensor-core path: the median of `steps` CUDA-event timings after `warmup`
+    untimed calls, L2 flushed before each -- the choice the batch autotuner makes."""
+    import torch
+
+    from paper_2107_04121_gb300 import fe
+    ctx, grps, forms = mixed_setup(scale, device)
+    want = {g for g in groups.split(",") if g}
+    out = {}
+    for g in grps:
+        if want and g["name"] not in want:
+            continue
+        for fname in MIXED_FORMS:
+            f, mat, E = forms[fname], g["mats"][fname], g["mesh"].n_elems
+            n = g["geom"].N * (3 if fname == "elasticity" else 1)
+            K = torch.empty((E, n, n), dtype=torch.float32, device="cuda")
+            row = {}
+            for prec in ("f32", "tf32x3"):
+                try:
+                    fe.eval_matrix(ctx, f, g["geom"], [mat, None, None], prec, out=K)
+                except fe.FEError:
+                    continue
+                for _ in range(warmup):
+                    fe.eval_matrix(ctx, f, g["geom"], [mat, None, None], prec, out=K)
+                ts = []
+                for _ in range(steps):
+                    flush.zero_()
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record()
+                    fe.eval_matrix(ctx, f, g["geom"], [mat, None, None], prec, out=K)
+                    b.record()
+                    b.synchronize()
+                    ts.append(a.elapsed_time(b))
+                row["cuda_core_ms" if prec == "f32" else "tensor_core_ms"] = statistics.median(ts)
+            out["%s/%s" % (g["name"], fname)] = dict(row, elements=E)
+            del K
+    ctx.check()
+    ctx.close()
+    return out
+
+
 def fp64_units(device, steps=2048):
     """FP64 rates of the device from fe_diag_fp64: DFMA chains and FP64 tensor-core
     MMA chains (mma.sync m8n8k4), one CTA of W warps per SM, ILP independent chains
@@ -1021,6 +1067,12 @@ def main():
             print(json.dumps({"workload": "fp64units", **fp64_units(local)}), flush=True)
         return
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    if args.workload == "paths":
+        if rank == 0:
+            print(json.dumps({"workload": "paths", "steps": args.steps, "warmup": args.warmup,
+                              "items": paths_measure(local, flush, max(args.steps, 1), args.warmup, args.scale,
+                                                     args.groups)}), flush=True)
+        return
     if args.workload in ("convection", "mixed"):
         if args.workload == "convection":
             res = convect_measure(args.n, local, ws, flush, None, hbm_peak, args.steps, args.warmup)
