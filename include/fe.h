@@ -325,12 +325,15 @@ fe_status fe_form_shape(const fe_form_h *form, int n_basis, int *n_rows, int *n_
  * sums over them, as Eq. fe4 does for the convective term),
  * integrated with the quadrature of `geom`; K_out is a device array
  * (n_elems, n_rows, n_cols), float64 for FE_F64 else float32.
- * FE_F64 and FE_F32 cover every form and element; the tensor-core precisions
- * (FE_TF32X3, FE_BF16X3, FE_BF16) cover linear elasticity with FE_MAT_LAME
- * materials and the (weighted) scalar Laplacian on 27-node hexahedra with 27
- * points; for elasticity on a stale float32-only deferred handle they compute
- * its geometry in the same launch (see FE_GEOM_DEFERRED).  A tensor-core wait that times out is reported as
- * FE_ERR_TIMEOUT through fe_get_status.
+ * FE_F64 and FE_F32 cover every form and element.  The tensor-core precisions
+ * cover: on 27-node hexahedra with 27 points (FE_TF32X3, FE_BF16X3, FE_BF16)
+ * linear elasticity with FE_MAT_LAME materials and the (weighted) scalar
+ * Laplacian, for elasticity on a stale float32-only deferred handle computing its
+ * geometry in the same launch (see FE_GEOM_DEFERRED); on 64-node hexahedra with
+ * 64 points (FE_TF32X3) Lame elasticity, the scalar Laplacian and the scalar mass
+ * matrix; on 20-node tetrahedra with the 35-point Grundmann-Moller rule
+ * (FE_TF32X3) Lame elasticity and the scalar Laplacian.  A tensor-core wait that
+ * times out is reported as FE_ERR_TIMEOUT through fe_get_status.
  * Errors: FE_ERR_INVALID_ARG, FE_ERR_SHAPE, FE_ERR_UNSUPPORTED_SPEC (e.g. a
  * precision without a kernel for this form), FE_ERR_CUDA. */
 fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h *geom, const void *const *args,
@@ -484,10 +487,10 @@ fe_status fe_batch_run(fe_ctx *ctx, fe_batch_h *batch, fe_stream_t stream);
 fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *elems_per_chunk, int *staging);
 /* The contraction path of item `item` in the batch's schedule: *path = 0 for
  * the Gram blocks on the CUDA cores (FP32), 1 for the TF32x3 Gram on the tensor
- * cores (Lame elasticity or the scalar Laplacian of 27-node hexahedra with 27
- * points, chosen by FE_BATCH_AUTOTUNE in the per-item schedule when it is
- * faster; max element error of elasticity 6.5e-7 against the FP64 oracle on
- * the 48^3 workload).  Errors:
+ * cores (the items fe_eval_matrix covers with FE_TF32X3, chosen by
+ * FE_BATCH_AUTOTUNE in the per-item schedule when it is faster; max element
+ * error of Q2 elasticity 6.5e-7 against the FP64 oracle on the 48^3
+ * workload).  Errors:
  * FE_ERR_INVALID_ARG. */
 fe_status fe_batch_describe_path(const fe_batch_h *batch, int item, int *path);
 /* The schedule of a batch: *per_item_launches = 1 for one launch per item,
@@ -516,7 +519,8 @@ fe_status fe_assemble_vector(fe_ctx *ctx, const fe_assembly_h *asm_h, int ncomp,
                              void *global_out, unsigned flags, fe_stream_t stream);
 
 /* Test hook for the bounded device waits: the next tensor-core matrix launch
- * (fe_eval_matrix with FE_TF32X3, FE_BF16X3 or FE_BF16) on this context first
+ * on 27-node hexahedra (fe_eval_matrix with FE_TF32X3, FE_BF16X3 or FE_BF16;
+ * launches on other elements leave the hook armed) on this context first
  * waits on a device flag that nothing sets.  Its bounded wait (about two
  * seconds) runs out, every CTA takes its abort path (the MMAs it issued are
  * drained, its tensor memory freed) and FE_ERR_TIMEOUT is reported through

@@ -201,6 +201,19 @@ fe_status fe_geometry(fe_ctx *ctx, const fe_mesh *mesh, const fe_refbasis *basis
     if (e == cudaSuccess) e = dev_alloc(&g->d_phi64, (size_t)Q * N);
     if (e == cudaSuccess) e = dev_alloc(&g->d_dphi64, (size_t)Q * 3 * N);
     if (e == cudaSuccess) e = dev_alloc(&g->d_w64, (size_t)Q);
+    {
+        // points by weight sign, each group padded to a multiple of 8 slots
+        int np = 0, nn = 0;
+        for (int q = 0; q < Q; ++q) (quad->weights[q] >= 0.0 ? np : nn)++;
+        g->n_wpos = np;
+        g->n_wneg = nn;
+        const int p8 = (np + 7) / 8 * 8, n8 = (nn + 7) / 8 * 8;
+        for (int k = 0; k < 64; ++k) g->slot_q[k] = -1;
+        if (p8 + n8 <= 64) {
+            int ip = 0, in = p8;
+            for (int q = 0; q < Q; ++q) g->slot_q[quad->weights[q] >= 0.0 ? ip++ : in++] = (signed char)q;
+        }
+    }
     if (e == cudaSuccess) e = dev_alloc(&g->d_phi32, (size_t)Q * N);
     if (e == cudaSuccess) e = dev_alloc(&g->d_dphi32, (size_t)Q * 3 * N);
     if (e == cudaSuccess && tensor) {
@@ -431,15 +444,19 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
         e = settle_geometry(gm, ctx->d_status, s);
         if (e == cudaSuccess) e = fe_launch_matrix_simt(g, form, mat, prec == FE_F64, K_out, ctx->sm_count, s);
     } else {
-        // tensor-core kernels: 27-node hexahedra with 27 points, Lame elasticity or
-        // the scalar Laplacian; 64-node hexahedra with 64 points, Lame elasticity (TF32x3)
+        // tensor-core kernels: 27-node hexahedra with 27 points (Lame elasticity, the
+        // scalar Laplacian); 64-node hexahedra with 64 points (TF32x3: Lame elasticity,
+        // the scalar Laplacian, the scalar mass matrix); 20-node tetrahedra with the
+        // 35-point rule (TF32x3: Lame elasticity, the scalar Laplacian)
         if (!fe_matrix_tc_supported(g, form, prec)) return FE_ERR_UNSUPPORTED_SPEC;
         // elasticity on a stale float32-only deferred handle: the tensor-core kernel
         // computes the FP64 geometry of its elements itself and stores the float32 copy
         const bool fused = form->kind == FK_ELASTICITY && fe_matrix_tc_geometry_fusable(gm);
         e = fused ? cudaSuccess : settle_geometry(gm, ctx->d_status, s);
-        const int *hold = ctx->hold_next_matrix ? ctx->d_hold : nullptr;
-        ctx->hold_next_matrix = 0;
+        // the wait test hook acts on the 27-node kernel; it stays armed across the others
+        const bool holdable = g->N == 27;
+        const int *hold = holdable && ctx->hold_next_matrix ? ctx->d_hold : nullptr;
+        if (holdable) ctx->hold_next_matrix = 0;
         if (e == cudaSuccess)
             e = fe_launch_matrix_tc(g, form, mat, prec, K_out, ctx->sm_count, ctx->d_status, hold, fused, s);
         if (fused && e == cudaSuccess) gm->pending = 0;

@@ -40,6 +40,11 @@ struct fe_geometry_h {
     int simplex_p;
     double *d_xi;  // (N, 3) reference positions of the nodes (lattice points / p)
     int is_view;  // aliases a parent's storage for a range of its elements (owns nothing)
+    // quadrature points ordered by the sign of their weight (positive first), for the
+    // tensor-core kernels of rules with negative weights: counts and the point of each
+    // slot of a K dimension padded to 8 per sign group (-1: padding)
+    int n_wpos, n_wneg;
+    signed char slot_q[64];
 };
 
 enum fe_form_kind {
@@ -120,8 +125,13 @@ cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_m
 // Whether a tensor-core matrix kernel covers the form on these elements in this
 // precision (27-node hexahedra with 27 points: Lame elasticity, the scalar
 // Laplacian; 64-node hexahedra with 64 points, TF32x3: Lame elasticity, the
-// scalar Laplacian and the scalar mass matrix).
+// scalar Laplacian and the scalar mass matrix; P3 tetrahedra with 35 points,
+// TF32x3: Lame elasticity and the scalar Laplacian).
 bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f, fe_precision prec);
+cudaError_t fe_launch_matrix_tcs(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat,
+                                 fe_precision prec, void *K, int sm_count, unsigned long long *status,
+                                 cudaStream_t s);
+bool fe_matrix_tcs_supported(const fe_geometry_h *g, const fe_form_h *f, fe_precision prec);
 cudaError_t fe_launch_matrix_tc64(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat,
                                   fe_precision prec, void *K, int sm_count, unsigned long long *status,
                                   cudaStream_t s);

@@ -177,8 +177,12 @@ cudaError_t batch_grid(size_t smem, long long *grid)
         cache,
         [&](int, long long *v) {
             *v = 1;
-            return cudaFuncSetAttribute(k_batch<CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)kMaxSmem[CLS]);
+            cudaError_t e2 = cudaFuncSetAttribute(k_batch<CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                  (int)kMaxSmem[CLS]);
+            if (e2 != cudaSuccess) return e2;
+            // the whole carveout as shared memory, so that the occupancy below counts
+            // every CTA the shared memory of an SM holds
+            return cudaFuncSetAttribute(k_batch<CLS>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         },
         &set);
     if (e != cudaSuccess) return e;

@@ -703,6 +703,8 @@ cudaError_t dispatch_tc(const fe_geometry_h *g, fe_material_args mat, fe_precisi
 
 bool fe_matrix_tc_supported(const fe_geometry_h *g, const fe_form_h *f, fe_precision prec)
 {
+    // P3 tetrahedra with the 35-point Grundmann-Moller rule, TF32x3 (k_matrix_tcs.cu)
+    if (g->N == 20 && g->Q == 35) return fe_matrix_tcs_supported(g, f, prec);
     const bool lame = f->kind == FK_ELASTICITY && f->mat == FE_MAT_LAME && !f->mat_transposed;
     // 64-node hexahedra with 64 points, TF32x3 (k_matrix_tc64.cu): Lame elasticity,
     // the scalar Laplacian and the scalar mass matrix
@@ -728,9 +730,10 @@ cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_m
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
     if (!fe_matrix_tc_supported(g, f, prec)) return cudaErrorNotSupported;
-    if (g->N == 64) {
+    if (g->N == 64 || g->N == 20) {
         if (with_geometry || hold) return cudaErrorNotSupported;
-        return fe_launch_matrix_tc64(g, f, mat, prec, K, sm_count, status, s);
+        return g->N == 64 ? fe_launch_matrix_tc64(g, f, mat, prec, K, sm_count, status, s)
+                          : fe_launch_matrix_tcs(g, f, mat, prec, K, sm_count, status, s);
     }
     const bool elast = f->kind == FK_ELASTICITY;
     if (elast && mat.kind != FE_MAT_LAME) return cudaErrorNotSupported;

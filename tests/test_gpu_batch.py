@@ -169,10 +169,10 @@ def test_batch_geometry_flag_follows_moved_nodes(ctx, groups, schedule):
 
 
 def test_batch_contraction_path_is_reported(ctx, groups):
-    """The per-item schedule may run the Q2 elasticity and Laplace items and the Q3
-    elasticity, Laplace and mass items on the tensor cores (TF32x3 Gram); every other
-    item, and every item of the persistent schedule, on the CUDA cores; the
-    tensor-core items match the oracle."""
+    """The per-item schedule may run the Q2 elasticity and Laplace items, the Q3
+    elasticity, Laplace and mass items and the P3 elasticity and Laplace items on
+    the tensor cores (TF32x3 Gram); every other item, and every item of the
+    persistent schedule, on the CUDA cores; the tensor-core items match the oracle."""
     items, keys = _items(groups)
     b = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_LAUNCHES)
     outs = b.run()
@@ -181,7 +181,7 @@ def test_batch_contraction_path_is_reported(ctx, groups):
         path = b.describe(k)["path"]
         if path.startswith("tensor"):
             assert (g.name, f) in (("Q2", "elasticity"), ("Q2", "laplace"), ("Q3", "elasticity"),
-                                   ("Q3", "laplace"), ("Q3", "mass"))
+                                   ("Q3", "laplace"), ("Q3", "mass"), ("P3", "elasticity"), ("P3", "laplace"))
         assert _err(K, g.reference(f), g.tet) <= TOL["f32"], (g.name, f, path)
     b.free()
     bp = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_PERSISTENT)

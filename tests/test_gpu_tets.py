@@ -123,3 +123,41 @@ def test_float32_tet_geometry_straight_and_curved(ctx, p, E):
         # the bent elements really differ from the straight-edged map
         wd_straight, _, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
         assert np.abs(wdetJ[:5] - wd_straight[:5]).max() > 1e-4 * np.abs(wdetJ[:5]).max()
+
+
+@pytest.mark.parametrize("kind", ["laplace", "elasticity"])
+def test_tensor_core_p3_matches_oracle(ctx, kind):
+    """P3 Lame elasticity and the weighted Laplacian on the tensor cores (TF32x3):
+    the Grundmann-Moller points ordered by weight sign, the negative ones entering
+    through a negated operand copy.  Every element of a 1,201-element mesh (several
+    elements per persistent CTA, a ragged last round) against the oracle, on the
+    scale of the sums of absolute terms (the rule's weights alternate in sign), and
+    symmetry."""
+    E = 1201
+    mesh = meshgen.tet_mesh(E, 3, np.random.default_rng(93))
+    ref = oracle.RefTet(3, 3)
+    wdetJ, G, _ = oracle.geometry(mesh.coords, mesh.conn, ref)
+    aw, aG = np.abs(wdetJ), np.abs(G)
+    rng = np.random.default_rng(94)
+    m = fe.Mesh(_t(mesh.coords, torch.float64), _t(mesh.conn, torch.int32))
+    geom = fe.tet_geometry(ctx, m, 3, flags=fe.GEOM_STORE_F32)
+    if kind == "laplace":
+        coef = rng.uniform(0.5, 2.0, E)
+        form, mat = fe.laplace_form(weighted=True), coef
+        Kref, Kabs = oracle.matrix_laplace(wdetJ, G, coef), oracle.matrix_laplace(aw, aG, coef)
+    else:
+        lam, mu = meshgen.lame_materials(mesh)
+        form, mat = fe.elasticity_form(fe.MAT_LAME), np.stack([lam, mu], 1)
+        D = oracle.lame_to_D(lam, mu)
+        Kref, Kabs = oracle.matrix_elasticity(wdetJ, G, D), oracle.matrix_elasticity(aw, aG, np.abs(D))
+    K = fe.eval_matrix(ctx, form, geom, [_t(mat, torch.float64), None, None], "tf32x3")
+    ctx.check()
+    Kg = K.cpu().numpy().astype(np.float64)
+    assert Kg.shape == Kref.shape
+    ek = float((np.sqrt(((Kg - Kref) ** 2).sum((1, 2))) / np.sqrt((Kabs ** 2).sum((1, 2)))).max())
+    assert ek <= TOL["tf32x3"], ek
+    scale = np.abs(Kabs).max()
+    assert np.abs(Kg - Kg.transpose(0, 2, 1)).max() <= 10 * TOL["tf32x3"] * scale
+    with pytest.raises(fe.FEError) as ei:
+        fe.eval_matrix(ctx, form, geom, [_t(mat, torch.float64), None, None], "bf16x3")
+    assert ei.value.status == fe.FE_ERR_UNSUPPORTED_SPEC
