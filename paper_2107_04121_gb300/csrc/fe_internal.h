@@ -115,6 +115,12 @@ cudaError_t fe_launch_geometry_G(const fe_geometry_h *g, bool f64, void *out, cu
 // Matrix mode on the CUDA cores (FP32 or FP64) for the (N, Q) pairs of fe_supported_nq.
 cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, bool f64,
                                   void *K, int sm_count, cudaStream_t s);
+// Lame elasticity (lame: lambda, mu per element) and the weighted scalar Laplacian
+// (coef per element, 1 where NULL) of the same FP32 geometry from one set of Gram
+// blocks on the CUDA cores: K (E, 3N, 3N) and K2 (E, N, N), float32.
+bool fe_matrix_pair_supported(const fe_geometry_h *g);
+cudaError_t fe_launch_matrix_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef, void *K2,
+                                  int sm_count, cudaStream_t s);
 cudaError_t fe_launch_matrix(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
                              void *K, int sm_count, cudaStream_t s);
 // Matrix mode on the tensor cores (k_matrix_tc.cu): Lame elasticity, 27 nodes, 27

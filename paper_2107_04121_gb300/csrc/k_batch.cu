@@ -240,6 +240,10 @@ struct fe_batch_h {
     // (k_matrix_tc; Lame elasticity and the scalar Laplacian of 27-node
     // hexahedra with 27 points)
     std::vector<int> path;
+    // shared Gram blocks (per-item schedule): a Lame elasticity item and a scalar
+    // Laplacian item on the same geometry computed by one CUDA-core launch, the
+    // Laplacian as c sum_j A_jj of the elasticity's Gram blocks; partner index or -1
+    std::vector<int> pair;
 };
 
 namespace {
@@ -271,6 +275,23 @@ cudaError_t enqueue_persistent(fe_batch_h *b, cudaStream_t s)
     return e;
 }
 
+// Item i's kernel in the per-item schedule: fe_eval_matrix's kernel on its path, or,
+// for a shared-Gram pair, one launch from the elasticity item (the Laplacian item
+// launches nothing).
+cudaError_t launch_item(fe_batch_h *b, int i, cudaStream_t s)
+{
+    const int j = b->pair[i];
+    if (j >= 0) {
+        if (b->forms[i]->kind != FK_ELASTICITY) return cudaSuccess;
+        return fe_launch_matrix_pair(b->igeom[i], b->mats[i].data, b->items[i].K, b->mats[j].data, b->items[j].K,
+                                     b->sm_count, s);
+    }
+    return b->path[i] ? fe_launch_matrix_tc(b->igeom[i], b->forms[i], b->mats[i], FE_TF32X3, b->items[i].K,
+                                            b->sm_count, b->d_status, nullptr, false, s)
+                      : fe_launch_matrix_simt(b->igeom[i], b->forms[i], b->mats[i], false, b->items[i].K,
+                                              b->sm_count, s);
+}
+
 // Matrices, per-item schedule: each item's fe_eval_matrix kernel on its lane.
 cudaError_t enqueue_items(fe_batch_h *b, cudaStream_t s)
 {
@@ -280,10 +301,7 @@ cudaError_t enqueue_items(fe_batch_h *b, cudaStream_t s)
         if (b->items[i].E == 0) continue;
         const int l = b->lane[i];
         cudaStream_t ls = l == 0 ? s : b->side[l - 1];
-        e = b->path[i] ? fe_launch_matrix_tc(b->igeom[i], b->forms[i], b->mats[i], FE_TF32X3, b->items[i].K,
-                                             b->sm_count, b->d_status, nullptr, false, ls)
-                       : fe_launch_matrix_simt(b->igeom[i], b->forms[i], b->mats[i], false, b->items[i].K,
-                                               b->sm_count, ls);
+        e = launch_item(b, i, ls);
     }
     for (int c = 0; c < kClasses - 1 && e == cudaSuccess; ++c) {
         e = cudaEventRecord(b->join[c], b->side[c]);
@@ -388,10 +406,14 @@ cudaError_t time_variant(BatchItemDev it, int id, BatchItemDev *d_tmp, cudaStrea
     return cudaSuccess;
 }
 
-// Median of five timed runs (after one warm-up) of item i's standalone kernel
-// on contraction path `path` (0 CUDA cores, 1 tensor cores).
-cudaError_t time_path(fe_batch_h *b, int i, int path, cudaStream_t s, float *ms)
+// Median of five timed runs (after one warm-up) of item i's kernel in the per-item
+// schedule with path `path` (0 CUDA cores, 1 tensor cores) and partner `partner`
+// (a shared-Gram pair when >= 0).
+cudaError_t time_path(fe_batch_h *b, int i, int path, int partner, cudaStream_t s, float *ms)
 {
+    const int keep_path = b->path[i], keep_pair = b->pair[i];
+    b->path[i] = path;
+    b->pair[i] = partner;
     cudaEvent_t a, z;
     cudaError_t e = cudaEventCreate(&a);
     if (e != cudaSuccess) return e;
@@ -403,17 +425,15 @@ cudaError_t time_path(fe_batch_h *b, int i, int path, cudaStream_t s, float *ms)
     float t[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (int r = 0; r < 6 && e == cudaSuccess; ++r) {
         e = cudaEventRecord(a, s);
-        if (e == cudaSuccess)
-            e = path ? fe_launch_matrix_tc(b->igeom[i], b->forms[i], b->mats[i], FE_TF32X3, b->items[i].K,
-                                           b->sm_count, b->d_status, nullptr, false, s)
-                     : fe_launch_matrix_simt(b->igeom[i], b->forms[i], b->mats[i], false, b->items[i].K,
-                                             b->sm_count, s);
+        if (e == cudaSuccess) e = launch_item(b, i, s);
         if (e == cudaSuccess) e = cudaEventRecord(z, s);
         if (e == cudaSuccess) e = cudaEventSynchronize(z);
         if (e == cudaSuccess && r > 0) e = cudaEventElapsedTime(&t[r - 1], a, z);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(z);
+    b->path[i] = keep_path;
+    b->pair[i] = keep_pair;
     std::sort(t, t + 5);
     *ms = t[2];
     return e;
@@ -443,7 +463,8 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
 {
     fe_clear_last_error();
     if (!ctx || !out || n_items < 1 || !items) return FE_ERR_INVALID_ARG;
-    if (flags & ~(FE_BATCH_GEOMETRY | FE_BATCH_AUTOTUNE | FE_BATCH_GRAPH | FE_BATCH_PERSISTENT | FE_BATCH_LAUNCHES))
+    if (flags & ~(FE_BATCH_GEOMETRY | FE_BATCH_AUTOTUNE | FE_BATCH_GRAPH | FE_BATCH_PERSISTENT | FE_BATCH_LAUNCHES |
+                  FE_BATCH_SHARED_GRAM))
         return FE_ERR_INVALID_ARG;
     const bool force_persistent = flags & FE_BATCH_PERSISTENT, force_launches = flags & FE_BATCH_LAUNCHES;
     if (force_persistent && force_launches) return FE_ERR_INVALID_ARG;
@@ -502,6 +523,7 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
         ma.transposed = f->mat_op >= 0 ? f->mat_transposed : 0;
         b->mats.push_back(ma);
         b->path.push_back(0);
+        b->pair.push_back(-1);
         fe_geometry_h *gm = const_cast<fe_geometry_h *>(g);
         bool seen = false;
         for (fe_geometry_h *h : b->geoms) seen = seen || h == gm;
@@ -557,9 +579,44 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
             const fe_form_h *f = b->forms[i];
             if (b->items[i].E == 0 || !fe_matrix_tc_supported(g, f, FE_TF32X3)) continue;
             float t0 = 0.f, t1 = 0.f;
-            e = time_path(b, i, 0, s, &t0);
-            if (e == cudaSuccess) e = time_path(b, i, 1, s, &t1);
+            e = time_path(b, i, 0, -1, s, &t0);
+            if (e == cudaSuccess) e = time_path(b, i, 1, -1, s, &t1);
             if (e == cudaSuccess && t1 < t0) b->path[i] = 1;
+        }
+    }
+    // shared Gram blocks: a Lame elasticity item and a scalar Laplacian item on the
+    // same geometry in one launch, where that beats the two items' chosen kernels
+    // (timed), or always with FE_BATCH_SHARED_GRAM
+    const bool share_all = flags & FE_BATCH_SHARED_GRAM;
+    if (e == cudaSuccess && !force_persistent && ((flags & FE_BATCH_AUTOTUNE) || share_all)) {
+        for (int i = 0; i < n_items && e == cudaSuccess; ++i) {
+            const fe_form_h *f = b->forms[i];
+            if (b->items[i].E == 0 || f->kind != FK_ELASTICITY || b->mats[i].kind != FE_MAT_LAME ||
+                b->mats[i].transposed || !fe_matrix_pair_supported(b->igeom[i]))
+                continue;
+            int j = -1;
+            for (int k = 0; k < n_items && j < 0; ++k)
+                if (b->pair[k] < 0 && b->igeom[k] == b->igeom[i] && b->forms[k]->kind == FK_LAPLACE &&
+                    b->forms[k]->ncomp == 1)
+                    j = k;
+            if (j < 0) continue;
+            if (share_all) {
+                b->pair[i] = j;
+                b->pair[j] = i;
+                continue;
+            }
+            float ti = 0.f, tj = 0.f, tp = 0.f;
+            e = time_path(b, i, b->path[i], -1, s, &ti);
+            if (e == cudaSuccess) e = time_path(b, j, b->path[j], -1, s, &tj);
+            if (e == cudaSuccess) {
+                b->pair[j] = i;  // the partner's launch is skipped while i is timed as a pair
+                e = time_path(b, i, 0, j, s, &tp);
+                b->pair[j] = -1;
+            }
+            if (e == cudaSuccess && tp < ti + tj) {
+                b->pair[i] = j;
+                b->pair[j] = i;
+            }
         }
     }
     // work lists: one per class, the items grouped by class on the device
@@ -594,6 +651,12 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
             cost[i] = (double)b->items[i].E * (4.0 * n * n + 40.0 * g->Q);
             order[i] = i;
         }
+        // a shared-Gram pair runs as one launch on the elasticity item's lane
+        for (int i = 0; i < n_items; ++i)
+            if (b->pair[i] >= 0 && b->forms[i]->kind == FK_LAPLACE) {
+                cost[b->pair[i]] += cost[i];
+                cost[i] = 0.0;
+            }
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
         double load[kClasses] = {0.0, 0.0, 0.0};
         b->lane.assign(n_items, 0);
@@ -672,7 +735,7 @@ fe_status fe_batch_describe_path(const fe_batch_h *batch, int item, int *path)
 {
     fe_clear_last_error();
     if (!batch || !path || item < 0 || item >= batch->n_items) return FE_ERR_INVALID_ARG;
-    *path = batch->launches ? batch->path[item] : 0;
+    *path = !batch->launches ? 0 : batch->pair[item] >= 0 ? 2 : batch->path[item];
     return FE_OK;
 }
 

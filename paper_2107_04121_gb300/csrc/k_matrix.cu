@@ -142,6 +142,57 @@ cudaError_t dispatch(const fe_geometry_h *g, const fe_form_h *f, fe_material_arg
     return cudaErrorInvalidValue;
 }
 
+// Lame elasticity and the weighted scalar Laplacian of the same elements from one
+// set of Gram blocks: K_L = c sum_j A_jj is the trace the Lame epilogue already
+// forms, written as a fourth bulk-staged row block into K2 (FP32).
+template <int N, int Q, int T, int EPB, int THREADS>
+__global__ void __launch_bounds__(THREADS) k_matrix_pair(const float *__restrict__ jinv, const float *__restrict__ wdetj,
+                                                         const float *__restrict__ dphi, long long E,
+                                                         const double *__restrict__ lame, float *__restrict__ K,
+                                                         const double *__restrict__ coef, float *__restrict__ K2)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    matrix_load_ref<float, N, Q, FK_ELASTICITY, T, EPB, THREADS, STAGE_BULK>(dphi, smem_raw);
+    for (long long e0 = (long long)blockIdx.x * EPB; e0 < E; e0 += (long long)gridDim.x * EPB) {
+        const int ne = (int)((E - e0) < EPB ? (E - e0) : EPB);
+        matrix_group<float, N, Q, FK_ELASTICITY, 1, T, EPB, THREADS, STAGE_BULK, true>(
+            jinv, wdetj, nullptr, dphi, e0, ne, 3, lame, 0, K, smem_raw, K2, coef);
+    }
+    if (threadIdx.x == 0) bulk_wait_read<0>();  // shared memory must outlive the copies' reads
+}
+
+template <int N, int Q, int T, int EPB, int THREADS>
+cudaError_t launch_pair(const fe_geometry_h *g, const double *lame, float *K, const double *coef, float *K2,
+                        int sm_count, cudaStream_t s)
+{
+    using P = MatrixSmem<float, N, Q, FK_ELASTICITY, T, EPB, STAGE_BULK>;
+    static_assert(EPB * (N / T) * (N / T + 1) / 2 <= THREADS, "one tile per thread");
+    static_assert(P::BYTES <= 227 * 1024, "shared memory plan exceeds one CTA's limit");
+    auto kern = k_matrix_pair<N, Q, T, EPB, THREADS>;
+    static FeLaunchCache cache;
+    long long per_sm = 0;
+    cudaError_t err = fe_cached_grid(
+        cache,
+        [&](int, long long *v) {
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::BYTES);
+            if (e2 != cudaSuccess) return e2;
+            int n = 0;
+            e2 = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, THREADS, P::BYTES);
+            if (e2 != cudaSuccess) return e2;
+            if (n < 1) return cudaErrorInvalidConfiguration;
+            *v = n;
+            return cudaSuccess;
+        },
+        &per_sm);
+    if (err != cudaSuccess) return err;
+    const long long E = g->mesh.n_elems;
+    long long blocks = (E + EPB - 1) / EPB;
+    const long long cap = per_sm * sm_count * 4;
+    if (blocks > cap) blocks = cap;
+    kern<<<(unsigned)blocks, THREADS, P::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, E, lame, K, coef, K2);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 bool fe_supported_nq(int N, int Q)
@@ -156,4 +207,28 @@ cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
     return f64 ? dispatch<double>(g, f, mat, K, sm_count, s) : dispatch<float>(g, f, mat, K, sm_count, s);
+}
+
+bool fe_matrix_pair_supported(const fe_geometry_h *g)
+{
+    return fe_supported_nq(g->N, g->Q) && g->d_jinv32 && g->d_dphi32;
+}
+
+cudaError_t fe_launch_matrix_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef, void *K2,
+                                  int sm_count, cudaStream_t s)
+{
+    if (g->mesh.n_elems == 0) return cudaSuccess;
+    if (!fe_matrix_pair_supported(g)) return cudaErrorNotSupported;
+    float *Ke = (float *)K, *Kl = (float *)K2;
+    const int N = g->N, Q = g->Q;
+    // the elasticity tiles of the FP32 dispatch above
+    if (N == 8 && Q == 8) return launch_pair<8, 8, 2, 12, 128>(g, lame, Ke, coef, Kl, sm_count, s);
+    if (N == 8 && Q == 27) return launch_pair<8, 27, 2, 12, 128>(g, lame, Ke, coef, Kl, sm_count, s);
+    if (N == 27 && Q == 27) return launch_pair<27, 27, 3, 2, 96>(g, lame, Ke, coef, Kl, sm_count, s);
+    if (N == 27 && Q == 64) return launch_pair<27, 64, 3, 2, 96>(g, lame, Ke, coef, Kl, sm_count, s);
+    if (N == 4 && Q == 5) return launch_pair<4, 5, 2, 32, 96>(g, lame, Ke, coef, Kl, sm_count, s);
+    if (N == 10 && Q == 15) return launch_pair<10, 15, 2, 8, 128>(g, lame, Ke, coef, Kl, sm_count, s);
+    if (N == 20 && Q == 35) return launch_pair<20, 35, 2, 4, 256>(g, lame, Ke, coef, Kl, sm_count, s);
+    if (N == 64 && Q == 64) return launch_pair<64, 64, 2, 1, 544>(g, lame, Ke, coef, Kl, sm_count, s);
+    return cudaErrorNotSupported;
 }

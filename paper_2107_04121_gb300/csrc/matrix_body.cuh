@@ -151,14 +151,19 @@ struct MatrixSmem {
 // ne * NU only join the barriers).  The reference gradients must already be in
 // the plan's D region (matrix_load_ref) when the plan keeps them there
 // (REF_SMEM); otherwise they are read from dphi.  MATK: 0 scalar coefficient (or none),
-// 1 Lame pair, 2 general D (6x6 Voigt).
-template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, int STAGE>
+// 1 Lame pair, 2 general D (6x6 Voigt).  LAP2 (Lame elasticity, bulk staging): the
+// weighted scalar Laplacian of the same elements, c sum_j A_jj, is written to K2 from
+// the same Gram blocks (c from mat2, 1 where mat2 is NULL).
+template <typename S, int N, int Q, int KIND, int MATK, int T, int EPB, int THREADS, int STAGE, bool LAP2 = false>
 __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S *__restrict__ wdetj,
                                              const S *__restrict__ phi, const S *__restrict__ dphi, long long e0,
                                              int ne, int ncomp,
                                              const double *__restrict__ mat, int mat_t, S *__restrict__ K,
-                                             unsigned char *smem_raw)
+                                             unsigned char *smem_raw, S *__restrict__ K2 = nullptr,
+                                             const double *__restrict__ mat2 = nullptr)
 {
+    static_assert(!LAP2 || (KIND == FK_ELASTICITY && MATK == 1 && STAGE == STAGE_BULK),
+                  "the shared-Gram Laplacian rides on the bulk-staged Lame elasticity");
     using P = MatrixSmem<S, N, Q, KIND, T, EPB, STAGE>;
     constexpr bool GRAD = P::GRAD;
     constexpr int TP = P::TP, NP = P::NP, NT = N / T, NU = NT * (NT + 1) / 2;
@@ -192,6 +197,8 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
             }
         } else if constexpr (MATK == 1) {
             for (int i = threadIdx.x; i < ne * 2; i += THREADS) sC[i] = (S)mat[e0 * 2 + i];
+            if constexpr (LAP2)
+                for (int i = threadIdx.x; i < ne; i += THREADS) sC[2 * EPB + i] = mat2 ? (S)mat2[e0 + i] : (S)1;
         } else {
             for (int i = threadIdx.x; i < ne; i += THREADS) sC[i] = mat ? (S)mat[e0 + i] : (S)1;
         }
@@ -377,9 +384,13 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
             constexpr int V = P::V;
             const int nblk = ncomp;
             const int blk_len = N * nrow;  // elements of one row block of one matrix
+            // destination of row block pb of element e_l (pass nblk: the Laplacian into K2)
+            auto dst_of = [&](int e_l, int pb) -> S * {
+                if (LAP2 && pb == nblk) return K2 + (e0 + e_l) * (long long)(N * N);
+                return K + (e0 + e_l) * (long long)nrow * nrow + (long long)pb * blk_len;
+            };
             auto shift_of = [&](int e_l, int pb) {
-                const S *gd = K + (e0 + e_l) * (long long)nrow * nrow + (long long)pb * blk_len;
-                return (int)(((unsigned long long)gd % 16) / sizeof(S));
+                return (int)(((unsigned long long)dst_of(e_l, pb) % 16) / sizeof(S));
             };
             // entry ((i, a0+x), (k, b0+y)) of the elasticity matrix and of its mirror
             auto kval = [&](int i, int k, int x, int y) -> S {
@@ -410,13 +421,24 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
                     return v;
                 }
             };
-            for (int pb = 0; pb < nblk; ++pb) {
+            for (int pb = 0; pb < nblk + (LAP2 ? 1 : 0); ++pb) {
                 const int buf = pb & 1;
                 if (pb >= 2 && threadIdx.x == 0) bulk_wait_read<1>();  // buffer of pass pb-2 drained
                 __syncthreads();  // pass 0: everyone is done reading G
                 if (active) {
                     S *slot = sK + (buf * EPB + el) * P::SLOT + shift_of(el, pb);
-                    if constexpr (KIND == FK_ELASTICITY) {
+                    if (LAP2 && pb == nblk) {
+                        // c (A_00 + A_11 + A_22) of the tile and its mirror
+                        const S c = sC[2 * EPB + el];
+#pragma unroll
+                        for (int x = 0; x < T; ++x)
+#pragma unroll
+                            for (int y = 0; y < T; ++y) {
+                                const S v = c * (acc[0][0][x][y] + acc[1][1][x][y] + acc[2][2][x][y]);
+                                slot[(a0 + x) * N + b0 + y] = v;
+                                if (mirror) slot[(b0 + y) * N + a0 + x] = v;
+                            }
+                    } else if constexpr (KIND == FK_ELASTICITY) {
                         // rows of block pb: direct entries with i == pb, mirror entries with k == pb
 #pragma unroll
                         for (int pc = 0; pc < 3; ++pc) {
@@ -446,14 +468,15 @@ __device__ __forceinline__ void matrix_group(const S *__restrict__ jinv, const S
                 fence_proxy_async();  // make the staged values visible to the bulk-copy engine
                 __syncthreads();
                 if (threadIdx.x == 0) {
+                    const int len = LAP2 && pb == nblk ? N * N : blk_len;
                     for (int e_l = 0; e_l < ne; ++e_l) {
                         const int sh = shift_of(e_l, pb);
                         const S *src = sK + (buf * EPB + e_l) * P::SLOT + sh;
-                        S *dst = K + (e0 + e_l) * (long long)nrow * nrow + (long long)pb * blk_len;
-                        const int head = (V - sh) % V < blk_len ? (V - sh) % V : blk_len;
-                        const int body = (blk_len - head) / V * V;
+                        S *dst = dst_of(e_l, pb);
+                        const int head = (V - sh) % V < len ? (V - sh) % V : len;
+                        const int body = (len - head) / V * V;
                         for (int t = 0; t < head; ++t) dst[t] = src[t];
-                        for (int t = head + body; t < blk_len; ++t) dst[t] = src[t];
+                        for (int t = head + body; t < len; ++t) dst[t] = src[t];
                         if (body > 0) bulk_store(dst + head, src + head, (unsigned)(body * sizeof(S)));
                     }
                     bulk_commit();

@@ -29,6 +29,7 @@ GEOM_STORE_F64, GEOM_STORE_F32, GEOM_DEFERRED = 1, 2, 4
 GEOM_WDETJ, GEOM_JINV, GEOM_G = 0, 1, 2
 ASSEMBLE_ACCUMULATE, ASSEMBLE_COMPENSATED = 1, 2
 BATCH_GEOMETRY, BATCH_AUTOTUNE, BATCH_GRAPH, BATCH_PERSISTENT, BATCH_LAUNCHES = 1, 2, 4, 8, 16
+BATCH_SHARED_GRAM = 32
 
 EXPORTED = [
     "fe_create", "fe_destroy", "fe_status_str", "fe_get_status", "fe_version", "fe_last_error_message",
@@ -616,8 +617,10 @@ class Batch:
                "fe_batch_describe")
         pth = ctypes.c_int()
         _check(_lib.fe_batch_describe_path(self._h, item, ctypes.byref(pth)), "fe_batch_describe_path")
+        paths = {0: "cuda-core Gram blocks", 1: "tensor-core tf32x3 Gram",
+                 2: "cuda-core Gram blocks shared by elasticity and Laplacian"}
         return {"tile": t.value, "elems_per_chunk": e.value, "staging": "bulk" if s.value else "direct",
-                "path": "tensor-core tf32x3 Gram" if pth.value else "cuda-core Gram blocks"}
+                "path": paths[pth.value]}
 
     def schedule(self) -> str:
         """'launches' (one kernel launch per item) or 'persistent' (the class kernels)."""

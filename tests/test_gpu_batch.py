@@ -171,8 +171,9 @@ def test_batch_geometry_flag_follows_moved_nodes(ctx, groups, schedule):
 def test_batch_contraction_path_is_reported(ctx, groups):
     """The per-item schedule may run the Q2 elasticity and Laplace items, the Q3
     elasticity, Laplace and mass items and the P3 elasticity and Laplace items on
-    the tensor cores (TF32x3 Gram); every other item, and every item of the
-    persistent schedule, on the CUDA cores; the tensor-core items match the oracle."""
+    the tensor cores (TF32x3 Gram), and an elasticity item with the Laplace item of
+    its geometry on shared Gram blocks; every other item, and every item of the
+    persistent schedule, on the CUDA cores; every item matches the oracle."""
     items, keys = _items(groups)
     b = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_LAUNCHES)
     outs = b.run()
@@ -182,11 +183,49 @@ def test_batch_contraction_path_is_reported(ctx, groups):
         if path.startswith("tensor"):
             assert (g.name, f) in (("Q2", "elasticity"), ("Q2", "laplace"), ("Q3", "elasticity"),
                                    ("Q3", "laplace"), ("Q3", "mass"), ("P3", "elasticity"), ("P3", "laplace"))
+        if "shared" in path:
+            assert f in ("elasticity", "laplace")
         assert _err(K, g.reference(f), g.tet) <= TOL["f32"], (g.name, f, path)
     b.free()
     bp = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE | fe.BATCH_PERSISTENT)
     assert all(bp.describe(k)["path"].startswith("cuda") for k in range(len(keys)))
     bp.free()
+
+
+def test_batch_shared_gram_pairs(ctx, groups):
+    """BATCH_SHARED_GRAM: each Lame elasticity item and the weighted Laplacian item
+    of its geometry come from one CUDA-core launch (the Laplacian as c sum_j A_jj of
+    the elasticity's Gram blocks); both match the oracle on every group (several
+    elements per CTA, ragged last groups), the mass items keep their own kernels,
+    every output is written (the buffers start as NaN), and runs are reproducible,
+    eagerly and in a graph."""
+    items, keys = _items(groups)
+
+    def fresh():
+        out = []
+        for (gm, f, m, _), (g, fname) in zip(items, keys):
+            n = g.mesh.nodes_per_elem * (3 if fname == "elasticity" else 1)
+            out.append((gm, f, m, torch.full((g.mesh.n_elems, n, n), float("nan"), device="cuda")))
+        return out
+
+    b = fe.Batch(ctx, fresh(), fe.BATCH_LAUNCHES | fe.BATCH_SHARED_GRAM)
+    outs = b.run()
+    ctx.check()
+    for k, ((g, f), K) in enumerate(zip(keys, outs)):
+        path = b.describe(k)["path"]
+        assert ("shared" in path) == (f != "mass"), (g.name, f, path)
+        e = _err(K, g.reference(f), g.tet)
+        assert e <= TOL["f32"], (g.name, f, e)
+    first = [K.clone() for K in outs]
+    again = b.run()
+    bg = fe.Batch(ctx, fresh(), fe.BATCH_LAUNCHES | fe.BATCH_SHARED_GRAM | fe.BATCH_GRAPH)
+    g_out = bg.run()
+    ctx.check()
+    for a, c, d in zip(first, again, g_out):
+        assert torch.equal(a, c)
+        assert torch.equal(a, d)
+    b.free()
+    bg.free()
 
 
 def test_batch_autotune_choice_is_a_candidate(ctx, groups):
