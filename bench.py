@@ -754,12 +754,19 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
     ms_kernel = ms_launches if schedule == "launches" else ms_persistent
     ctx.check()
     n_el = sum(g["mesh"].n_elems for g in groups)
-    # algorithmic bytes of the matrices: per item and element, J^-1 and w det J
-    # (FP32, Q x 10 values), the material (8 or 16 B) and the K_e write
+    # algorithmic bytes of the matrices: J^-1 and w det J of each group once (FP32,
+    # Q x 10 values per element; the job needs them once however many forms read
+    # them), and per item and element the material (8 or 16 B) and the K_e write
     kbytes = 0
+    seen = set()
     for (g, f, m, _), K in zip(items, batch.outputs):
         E = K.shape[0]
-        kbytes += E * (g.Q * 10 * 4 + m.element_size() * m.numel() // max(E, 1) + K[0].numel() * 4)
+        if id(g) not in seen:
+            seen.add(id(g))
+            kbytes += E * g.Q * 10 * 4
+        kbytes += E * (m.element_size() * m.numel() // max(E, 1) + K[0].numel() * 4)
+    paths = [batch.describe(k)["path"] for k in range(len(items))]
+    launches = len(items) - sum("shared" in p for p in paths) // 2
     out = {"workload": "mixed mesh: P1/P2/P3 tets %s, Q1/Q2/Q3 hexes %s; weighted Laplace + weighted mass + Lame "
                        "elasticity matrices, FP32 from FP64 geometry" % (
                            "/".join(str(g["mesh"].n_elems) for g in groups[:3]),
@@ -768,8 +775,11 @@ def mixed_measure(device, flush, ref, steps=5, warmup=3, scale=1.0):
            "graph_ms": ms_graph, "value": n_el / (ms_graph / 1e3), "unit": UNIT + " (all 3 forms per element)",
            "schedule": schedule, "persistent_kernels_ms": ms_persistent, "per_item_launches_ms": ms_launches,
            "separate_calls_ms": ms_sep,
-           "roofline": {"kernel": ("k_matrix_sym, one launch per item on 3 streams" if schedule == "launches"
-                                   else "k_batch, persistent class kernels") + " (18 items)", "bound": "hbm",
+           "roofline": {"kernel": ("the items' matrix kernels on 3 streams, %d launches (elasticity and Laplacian "
+                                   "items of a geometry sharing one launch where the autotuner paired them)"
+                                   % launches if schedule == "launches"
+                                   else "k_batch, persistent class kernels") + " (%d items)" % len(items),
+                        "bound": "hbm",
                         "achieved": kbytes / (ms_kernel / 1e3) / 1e9, "unit": "GB/s", "bytes": kbytes},
            "configs": {"%s/%s" % (items_g["name"], f): batch.describe(k)
                        for k, (items_g, f) in enumerate((g, f) for g in groups for f in MIXED_FORMS)}}

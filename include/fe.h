@@ -467,10 +467,11 @@ typedef struct {
  *   loaded stream.  A Lame elasticity item and a scalar Laplacian item on the
  *   same geometry may share one CUDA-core launch instead: its Gram blocks
  *   A_jl give the elasticity matrix and, as c sum_j A_jj, the Laplacian.
- *   FE_BATCH_AUTOTUNE times the shared launch against the two items' own
- *   kernels and keeps it where it is faster; FE_BATCH_SHARED_GRAM pairs every
- *   such couple without timing (each elasticity item with the first unpaired
- *   Laplacian item of its geometry).
+ *   FE_BATCH_AUTOTUNE times the shared launch (on the CUDA cores, and on the
+ *   tensor cores for 64-node hexahedra) against the two items' own kernels and
+ *   keeps it where it is faster; FE_BATCH_SHARED_GRAM pairs every such couple
+ *   without timing (each elasticity item with the first unpaired Laplacian
+ *   item of its geometry; on the tensor cores where that kernel exists).
  * FE_BATCH_PERSISTENT or FE_BATCH_LAUNCHES fixes the schedule (not both); with
  * neither, FE_BATCH_AUTOTUNE times both schedules' matrix launches at creation
  * and keeps the faster, and without it the persistent schedule is used.  Both
@@ -497,11 +498,10 @@ fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *e
  * cores (the items fe_eval_matrix covers with FE_TF32X3, chosen by
  * FE_BATCH_AUTOTUNE in the per-item schedule when it is faster; max element
  * error of Q2 elasticity 6.5e-7 against the FP64 oracle on the 48^3
- * workload), 2 for a Lame elasticity item and a scalar Laplacian item on the
- * same geometry computed by one CUDA-core launch from the same Gram blocks
- * A_jl (the Laplacian is c sum_j A_jj; both items report 2; chosen by
- * FE_BATCH_AUTOTUNE in the per-item schedule when the one launch is faster than
- * the two items' own kernels).  Errors:
+ * workload), 2 (CUDA cores) or 3 (tensor cores, TF32x3, 64-node hexahedra)
+ * for a Lame elasticity item and a scalar Laplacian item on the same geometry
+ * computed by one launch from the same Gram blocks A_jl (the Laplacian is
+ * c sum_j A_jj; both items report the pair's value).  Errors:
  * FE_ERR_INVALID_ARG. */
 fe_status fe_batch_describe_path(const fe_batch_h *batch, int item, int *path);
 /* The schedule of a batch: *per_item_launches = 1 for one launch per item,

@@ -276,15 +276,18 @@ cudaError_t enqueue_persistent(fe_batch_h *b, cudaStream_t s)
 }
 
 // Item i's kernel in the per-item schedule: fe_eval_matrix's kernel on its path, or,
-// for a shared-Gram pair, one launch from the elasticity item (the Laplacian item
-// launches nothing).
+// for a shared-Gram pair, one launch from the elasticity item on its path (CUDA
+// cores, or the tensor cores for 64-node hexahedra; the Laplacian item launches
+// nothing).
 cudaError_t launch_item(fe_batch_h *b, int i, cudaStream_t s)
 {
     const int j = b->pair[i];
     if (j >= 0) {
         if (b->forms[i]->kind != FK_ELASTICITY) return cudaSuccess;
-        return fe_launch_matrix_pair(b->igeom[i], b->mats[i].data, b->items[i].K, b->mats[j].data, b->items[j].K,
-                                     b->sm_count, s);
+        return b->path[i] ? fe_launch_matrix_tc_pair(b->igeom[i], b->mats[i].data, b->items[i].K, b->mats[j].data,
+                                                      b->items[j].K, b->sm_count, b->d_status, s)
+                          : fe_launch_matrix_pair(b->igeom[i], b->mats[i].data, b->items[i].K, b->mats[j].data,
+                                                  b->items[j].K, b->sm_count, s);
     }
     return b->path[i] ? fe_launch_matrix_tc(b->igeom[i], b->forms[i], b->mats[i], FE_TF32X3, b->items[i].K,
                                             b->sm_count, b->d_status, nullptr, false, s)
@@ -600,22 +603,23 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
                     b->forms[k]->ncomp == 1)
                     j = k;
             if (j < 0) continue;
-            if (share_all) {
+            const bool tc_pair = fe_matrix_tc_pair_supported(b->igeom[i]);
+            if (share_all) {  // on the tensor cores where a shared kernel exists
                 b->pair[i] = j;
                 b->pair[j] = i;
+                b->path[i] = tc_pair ? 1 : 0;
                 continue;
             }
-            float ti = 0.f, tj = 0.f, tp = 0.f;
+            float ti = 0.f, tj = 0.f, tp = 0.f, tq = 0.f;
             e = time_path(b, i, b->path[i], -1, s, &ti);
             if (e == cudaSuccess) e = time_path(b, j, b->path[j], -1, s, &tj);
-            if (e == cudaSuccess) {
-                b->pair[j] = i;  // the partner's launch is skipped while i is timed as a pair
-                e = time_path(b, i, 0, j, s, &tp);
-                b->pair[j] = -1;
-            }
-            if (e == cudaSuccess && tp < ti + tj) {
+            if (e == cudaSuccess) e = time_path(b, i, 0, j, s, &tp);
+            if (e == cudaSuccess && tc_pair) e = time_path(b, i, 1, j, s, &tq);
+            const bool use_tc = tc_pair && tq < tp;
+            if (e == cudaSuccess && (use_tc ? tq : tp) < ti + tj) {
                 b->pair[i] = j;
                 b->pair[j] = i;
+                b->path[i] = use_tc ? 1 : 0;
             }
         }
     }
@@ -735,7 +739,10 @@ fe_status fe_batch_describe_path(const fe_batch_h *batch, int item, int *path)
 {
     fe_clear_last_error();
     if (!batch || !path || item < 0 || item >= batch->n_items) return FE_ERR_INVALID_ARG;
-    *path = !batch->launches ? 0 : batch->pair[item] >= 0 ? 2 : batch->path[item];
+    const int partner = batch->pair[item];
+    if (!batch->launches) *path = 0;
+    else if (partner < 0) *path = batch->path[item];
+    else *path = 2 + batch->path[batch->forms[item]->kind == FK_ELASTICITY ? item : partner];
     return FE_OK;
 }
 

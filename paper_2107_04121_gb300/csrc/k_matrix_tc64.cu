@@ -34,7 +34,10 @@
 // c sum_j A_jj, for which the MMAs compute only the diagonal blocks (first tile
 // against columns 0-127, second tile against columns 128-191); the mass matrix
 // is the Gram matrix of sqrt(w det J) phi (64 rows, one tile against 64 columns).
-// Both write a 64 x 64 K_e with one bulk copy.
+// Both write a 64 x 64 K_e with one bulk copy.  The pair mode is elasticity that
+// also writes the weighted Laplacian of the same elements, c sum_j A_jj, from the
+// diagonal blocks its epilogue publishes anyway (staged and copied out by the warp
+// group with one row block, into a second output).
 //
 // The exchange area and group 0-1's staging reuse the operand buffer once the
 // MMAs are done, so the next element's operands are built after those bulk
@@ -55,7 +58,7 @@ constexpr int T6_TMEM_COLS = 512;       // tiles at columns 0 and 256 (192 each)
 constexpr int T6_EX = 68;               // floats per row of the exchange blocks (16-byte rows)
 constexpr int T6_JW = 12;               // floats per point of the staged sqrt(w det J) J^-1
 constexpr int T6_BAR_G0 = 1, T6_BAR_G1 = 2;  // named barriers of the two warp groups
-enum T6Form { T6_ELAST = 0, T6_LAPL = 1, T6_MASS = 2 };
+enum T6Form { T6_ELAST = 0, T6_LAPL = 1, T6_MASS = 2, T6_PAIR = 3 };
 
 struct T6Smem {
     using L = OpLayout<4, T6_Q, T6_OPROWS>;         // TF32 operands: 64 KB each
@@ -72,6 +75,9 @@ struct T6Smem {
     static constexpr int LM = JW + T6_Q * T6_JW * 4;                    // lambda, mu
     static constexpr int MISC = (LM + 16 + 15) / 16 * 16;               // mbarrier, tmem slot, abort flag
     static constexpr int BYTES = MISC + 16;
+    static constexpr int LSTG = BYTES;                                  // pair mode: [64][64] (+4) Laplacian
+    static constexpr int BYTES_PAIR = LSTG + (T6_N * T6_N + 4) * 4;
+    static_assert(BYTES_PAIR <= 227 * 1024, "pair mode fits one CTA");
 };
 
 // 32 consecutive floats of an exchange row as eight 16-byte stores.
@@ -86,9 +92,11 @@ template <int FORM>
 __global__ void __launch_bounds__(T6_THREADS, 1)
     k_matrix_tc64(const float *__restrict__ jinv, const float *__restrict__ wdetj, const float *__restrict__ dphi,
                   const float *__restrict__ phi, long long E, const double *__restrict__ lame,
-                  float *__restrict__ K, unsigned long long *__restrict__ status)
+                  float *__restrict__ K, unsigned long long *__restrict__ status, const double *__restrict__ coef,
+                  float *__restrict__ K2)
 {
-    constexpr int NR = FORM == T6_ELAST ? T6_ROWS : T6_N;  // rows (and columns) of K_e
+    constexpr bool ELAST = FORM == T6_ELAST || FORM == T6_PAIR;
+    constexpr int NR = ELAST ? T6_ROWS : T6_N;  // rows (and columns) of K_e
     using P = T6Smem;
     using L = P::L;
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -133,8 +141,9 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                 pw[k] = wdetj[e * T6_Q + t / 9];
             }
         }
-        if constexpr (FORM == T6_ELAST) {
+        if constexpr (ELAST) {
             if (tid < 2) plm = lame[2 * e + tid];
+            if (FORM == T6_PAIR && tid == 2) plm = coef ? coef[e] : 1.0;
         } else {
             if (tid == 0) plm = lame ? lame[e] : 1.0;
         }
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                 }
             }
         }
-        if (tid < 2) sLM[tid] = (float)plm;
+        if (tid < (FORM == T6_PAIR ? 3 : 2)) sLM[tid] = (float)plm;
         prefetch(e + gridDim.x);
         __syncthreads();
         // (b, c) X[(j,a)][q] split into TF32 hi/lo, then the MMAs, in two halves of
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                     }
                 };
                 const uint32_t row128 = (uint32_t)(16 * L::SBO);  // byte offset of operand row 128
-                if constexpr (FORM == T6_ELAST) {
+                if constexpr (ELAST) {
                     chain(tmem, 0u, 0u, std::integral_constant<int, T6_ROWS>{});
                     chain(tmem + 256, row128, 0u, std::integral_constant<int, T6_ROWS>{});
                 } else if constexpr (FORM == T6_LAPL) {
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
         tc_fence_after();
 
         // (d) epilogue
-        if constexpr (FORM == T6_ELAST) {
+        if constexpr (ELAST) {
         // (d) epilogue
         const float lam = sLM[0], mu = sLM[1];
         float *exd = reinterpret_cast<float *>(smem + P::EXD);
@@ -335,6 +344,35 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             }
         }
+        if constexpr (FORM == T6_PAIR) {
+            // the group with one row block: K_L[a][b] = c sum_j A_jj[a][b] from the
+            // published diagonal blocks (intact until the next element's operands)
+            if (grp) {
+                const float cw = sLM[2];
+                float *dl = K2 + e * (long long)(T6_N * T6_N);
+                const int sh = (int)(((unsigned long long)dl % 16) / 4);
+                float *sl = reinterpret_cast<float *>(smem + P::LSTG) + sh;
+                const int gt = 64 * half + 32 * (sp - 2) + lane;  // 0 .. 127 within the group
+                const int b2 = gt & 63, a0 = (gt >> 6) * 32;      // column b2, rows a0 .. a0 + 31
+#pragma unroll 8
+                for (int t = 0; t < 32; ++t) {
+                    const int a2 = a0 + t;
+                    sl[a2 * T6_N + b2] = cw * (exd[(0 * T6_N + a2) * T6_EX + b2] + exd[(1 * T6_N + a2) * T6_EX + b2] +
+                                               exd[(2 * T6_N + a2) * T6_EX + b2]);
+                }
+                fence_async_smem();
+                named_sync(T6_BAR_G1, 128);
+                if (copier) {
+                    constexpr int LEN = T6_N * T6_N;
+                    const int head = (4 - sh) % 4;
+                    const int body = (LEN - head) / 4 * 4;
+                    for (int t = 0; t < head; ++t) dl[t] = sl[t];
+                    for (int t = head + body; t < LEN; ++t) dl[t] = sl[t];
+                    bulk_store(dl + head, sl + head, (unsigned)(body * 4));
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+            }
+        }
         } else {
             // Laplacian K = c sum_j A_jj, mass matrix K = c A_00: 64 x 64, one bulk copy
             const float cw = sLM[0];
@@ -400,15 +438,17 @@ __global__ void __launch_bounds__(T6_THREADS, 1)
 
 template <int FORM>
 cudaError_t launch_tc64(const fe_geometry_h *g, fe_material_args mat, void *K, int sm_count,
-                        unsigned long long *status, cudaStream_t s)
+                        unsigned long long *status, cudaStream_t s, const double *coef = nullptr,
+                        void *K2 = nullptr)
 {
     auto kern = k_matrix_tc64<FORM>;
+    constexpr int BYTES = FORM == T6_PAIR ? T6Smem::BYTES_PAIR : T6Smem::BYTES;
     static FeLaunchCache cache;
     long long per_sm = 0;
     cudaError_t err = fe_cached_grid(
         cache,
         [&](int, long long *v) {
-            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, T6Smem::BYTES);
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, BYTES);
             if (e2 != cudaSuccess) return e2;
             *v = 1;  // up to 448 of the 512 tensor-memory columns: one CTA per SM
             return cudaSuccess;
@@ -417,8 +457,8 @@ cudaError_t launch_tc64(const fe_geometry_h *g, fe_material_args mat, void *K, i
     if (err != cudaSuccess) return err;
     long long blocks = per_sm * sm_count;
     if (blocks > g->mesh.n_elems) blocks = g->mesh.n_elems;
-    kern<<<(unsigned)blocks, T6_THREADS, T6Smem::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->d_phi32,
-                                                             g->mesh.n_elems, mat.data, (float *)K, status);
+    kern<<<(unsigned)blocks, T6_THREADS, BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->d_phi32,
+                                                     g->mesh.n_elems, mat.data, (float *)K, status, coef, (float *)K2);
     return cudaGetLastError();
 }
 
@@ -434,4 +474,20 @@ cudaError_t fe_launch_matrix_tc64(const fe_geometry_h *g, const fe_form_h *f, fe
     if (f->kind == FK_LAPLACE && f->ncomp == 1) return launch_tc64<T6_LAPL>(g, mat, K, sm_count, status, s);
     if (f->kind == FK_MASS && f->ncomp == 1) return launch_tc64<T6_MASS>(g, mat, K, sm_count, status, s);
     return cudaErrorNotSupported;
+}
+
+bool fe_matrix_tc_pair_supported(const fe_geometry_h *g)
+{
+    return g->N == T6_N && g->Q == T6_Q && g->d_jinv32 && g->d_dphi32;
+}
+
+cudaError_t fe_launch_matrix_tc_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef,
+                                     void *K2, int sm_count, unsigned long long *status, cudaStream_t s)
+{
+    if (g->mesh.n_elems == 0) return cudaSuccess;
+    if (!fe_matrix_tc_pair_supported(g)) return cudaErrorNotSupported;
+    fe_material_args mat{};
+    mat.kind = FE_MAT_LAME;
+    mat.data = lame;
+    return launch_tc64<T6_PAIR>(g, mat, K, sm_count, status, s, coef, K2);
 }

@@ -618,7 +618,8 @@ class Batch:
         pth = ctypes.c_int()
         _check(_lib.fe_batch_describe_path(self._h, item, ctypes.byref(pth)), "fe_batch_describe_path")
         paths = {0: "cuda-core Gram blocks", 1: "tensor-core tf32x3 Gram",
-                 2: "cuda-core Gram blocks shared by elasticity and Laplacian"}
+                 2: "cuda-core Gram blocks shared by elasticity and Laplacian",
+                 3: "tensor-core tf32x3 Gram shared by elasticity and Laplacian"}
         return {"tile": t.value, "elems_per_chunk": e.value, "staging": "bulk" if s.value else "direct",
                 "path": paths[pth.value]}
 
