@@ -468,7 +468,7 @@ typedef struct {
  *   same geometry may share one CUDA-core launch instead: its Gram blocks
  *   A_jl give the elasticity matrix and, as c sum_j A_jj, the Laplacian.
  *   FE_BATCH_AUTOTUNE times the shared launch (on the CUDA cores, and on the
- *   tensor cores for 64-node hexahedra) against the two items' own kernels and
+ *   tensor cores for 27- and 64-node hexahedra) against the two items' own kernels and
  *   keeps it where it is faster; FE_BATCH_SHARED_GRAM pairs every such couple
  *   without timing (each elasticity item with the first unpaired Laplacian
  *   item of its geometry; on the tensor cores where that kernel exists).
@@ -498,7 +498,7 @@ fe_status fe_batch_describe(const fe_batch_h *batch, int item, int *tile, int *e
  * cores (the items fe_eval_matrix covers with FE_TF32X3, chosen by
  * FE_BATCH_AUTOTUNE in the per-item schedule when it is faster; max element
  * error of Q2 elasticity 6.5e-7 against the FP64 oracle on the 48^3
- * workload), 2 (CUDA cores) or 3 (tensor cores, TF32x3, 64-node hexahedra)
+ * workload), 2 (CUDA cores) or 3 (tensor cores, TF32x3, 27- and 64-node hexahedra)
  * for a Lame elasticity item and a scalar Laplacian item on the same geometry
  * computed by one launch from the same Gram blocks A_jl (the Laplacian is
  * c sum_j A_jj; both items report the pair's value).  Errors:

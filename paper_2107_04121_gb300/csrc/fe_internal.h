@@ -121,10 +121,14 @@ cudaError_t fe_launch_matrix_simt(const fe_geometry_h *g, const fe_form_h *f, fe
 bool fe_matrix_pair_supported(const fe_geometry_h *g);
 cudaError_t fe_launch_matrix_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef, void *K2,
                                   int sm_count, cudaStream_t s);
-// The same pair on the tensor cores (TF32x3; 64-node hexahedra with 64 points).
+// The same pair on the tensor cores (TF32x3; 27-node hexahedra with 27 points in
+// k_matrix_tc.cu, 64-node hexahedra with 64 points in k_matrix_tc64.cu).
 bool fe_matrix_tc_pair_supported(const fe_geometry_h *g);
 cudaError_t fe_launch_matrix_tc_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef,
                                      void *K2, int sm_count, unsigned long long *status, cudaStream_t s);
+bool fe_matrix_tc64_pair_supported(const fe_geometry_h *g);
+cudaError_t fe_launch_matrix_tc64_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef,
+                                       void *K2, int sm_count, unsigned long long *status, cudaStream_t s);
 cudaError_t fe_launch_matrix(const fe_geometry_h *g, const fe_form_h *f, fe_material_args mat, fe_precision prec,
                              void *K, int sm_count, cudaStream_t s);
 // Matrix mode on the tensor cores (k_matrix_tc.cu): Lame elasticity, 27 nodes, 27

@@ -277,8 +277,8 @@ cudaError_t enqueue_persistent(fe_batch_h *b, cudaStream_t s)
 
 // Item i's kernel in the per-item schedule: fe_eval_matrix's kernel on its path, or,
 // for a shared-Gram pair, one launch from the elasticity item on its path (CUDA
-// cores, or the tensor cores for 64-node hexahedra; the Laplacian item launches
-// nothing).
+// cores, or the tensor cores for 27- and 64-node hexahedra; the Laplacian item
+// launches nothing).
 cudaError_t launch_item(fe_batch_h *b, int i, cudaStream_t s)
 {
     const int j = b->pair[i];

@@ -35,7 +35,9 @@
 // the sum of the diagonal blocks of the same Gram matrix, K[a][b] = c sum_j A_jj[a][b]
 // (FORM = TC_LAPL): the operands and the MMA chain are those of elasticity, the
 // epilogue adds the three diagonal blocks published by the consumer warps and
-// writes the 27 x 27 matrix.
+// writes the 27 x 27 matrix.  FORM = TC_PAIR (TF32x3) is elasticity that also writes
+// that Laplacian of the same elements, with its own coefficient, into a second
+// output: both from one Gram matrix.
 //
 // With a stale float32-only deferred geometry (Q2, 3x3x3 Gauss points) two
 // more warps per CTA compute the FP64 geometry themselves, one element at a time
@@ -65,7 +67,7 @@ constexpr int TC_TMEM_COLS = 128;
 constexpr int TC_NROW = 3 * TC_N;  // 81
 constexpr int TC_JW_STRIDE = 12;  // floats per point of the staged sqrt(w det J) J^-1 (16-byte rows)
 constexpr int TC_EX_STRIDE = 28;  // floats per row of the exchange blocks (16-byte rows, conflict-free float4)
-enum TcForm { TC_ELAST = 0, TC_LAPL = 1 };  // Lame elasticity, weighted Laplacian
+enum TcForm { TC_ELAST = 0, TC_LAPL = 1, TC_PAIR = 2 };  // Lame elasticity, weighted Laplacian, both
 constexpr int TC_NGEO = 2;  // geometry warps per CTA (GEO)
 
 // Diagonal block of K_e for row (i, a): own A_ii[a][.] from registers, the
@@ -170,6 +172,10 @@ struct TcSmem {
     static constexpr int MISC = (GT + (GEO ? GT_LEN * 8 : 0) + 15) / 16 * 16;
     static constexpr int GFULL = MISC + 64, GEMPTY = GFULL + 8 * RING;
     static constexpr int BYTES = MISC + 64 + 16 * RING;
+    // TC_PAIR: the Laplacian's staging (27 x 27 + 4 floats) and its coefficient [2]
+    static constexpr int LS = (BYTES + 15) / 16 * 16;
+    static constexpr int LC = (LS + (TC_N * TC_N + 4) * 4 + 15) / 16 * 16;
+    static constexpr int BYTES_PAIR = LC + 16;
     // accumulators in tensor memory: one when three CTAs fit an SM (the MMAs of
     // element n+1 wait only for element n's read-out; the other CTAs hide it),
     // two when only two CTAs fit (512 columns per SM)
@@ -197,8 +203,11 @@ template <int MODE, bool GEO, int FORM>
 __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE == TC_TF32X3 ? 2 : 3)
     k_matrix_tc(const float *__restrict__ jinv, const float *__restrict__ wdetj, const float *__restrict__ dphi,
                 long long E, const double *__restrict__ lame, float *__restrict__ K,
-                unsigned long long *__restrict__ status, const int *__restrict__ hold, TcGeoArgs geo)
+                unsigned long long *__restrict__ status, const int *__restrict__ hold, TcGeoArgs geo,
+                const double *__restrict__ coef, float *__restrict__ K2)
 {
+    static_assert(FORM != TC_PAIR || (MODE == TC_TF32X3 && !GEO), "the pair runs TF32x3 on a stored geometry");
+    constexpr bool ELASTF = FORM != TC_LAPL;  // elasticity (alone or with the Laplacian)
     using P = TcSmem<MODE, GEO>;
     using L = typename P::L;
     constexpr int NTHREADS = TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0);
@@ -358,6 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
                     if (ptid == 0) plm = lame ? lame[e] : 1.0;
                 } else {
                     if (ptid < 2) plm = lame[2 * e + ptid];
+                    if (FORM == TC_PAIR && ptid == 2) plm = coef ? coef[e] : 1.0;
                 }
             }
         };
@@ -418,6 +428,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
                     if (t < TC_Q * 9) jw[(t / 9) * TC_JW_STRIDE + t % 9] = sqrtf(pwt[u]) * pj[u];
                 }
                 if (ptid < 2) sLM[2 * b + ptid] = (float)plm;
+                if (FORM == TC_PAIR && ptid == 2) reinterpret_cast<float *>(smem + P::LC)[b] = (float)plm;
                 prefetch(e + gridDim.x);
                 named_sync(TC_BAR_PROD, TC_PROD);
             }
@@ -550,12 +561,12 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
             // (e) rows (j = warp, a = lane) of the accumulator: the two blocks this warp
             // uses (A_jj, A_j,j+1) -> registers; the accumulator is then handed back
             // to the producers, and the blocks go to the exchange area
-            float d[FORM == TC_LAPL ? 32 : 64];
+            float d[ELASTF ? 64 : 32];
             {
                 const int jn = warp == 2 ? 0 : warp + 1;
                 const uint32_t taddr = tmem + (n % P::NACC) * TC_TMEM_COLS + ((uint32_t)(32 * warp) << 16);
                 tmem_ld32(taddr + 32 * warp, d);
-                if constexpr (FORM == TC_ELAST) tmem_ld32(taddr + 32 * jn, d + 32);
+                if constexpr (ELASTF) tmem_ld32(taddr + 32 * jn, d + 32);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
             }
             tc_fence_before();
@@ -566,7 +577,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
             if (lane < TC_N) {
                 // ex[w][0] = A_ww, ex[w][1] = A_w,w+1 (rows a, columns b)
                 float *e0 = ex + ((warp * 2 + 0) * TC_N + lane) * P::EX_STRIDE;
-                if constexpr (FORM == TC_ELAST) {
+                if constexpr (ELASTF) {
                     float *e1 = ex + ((warp * 2 + 1) * TC_N + lane) * P::EX_STRIDE;
                     publish_blocks(d, e0, e1);
                 } else {
@@ -580,17 +591,23 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
 
             // (f) elasticity: blocks K_ii and K_i,i+1 of row (i = warp, a = lane), and
             // K_i+1,i as columns; Laplacian: row a, columns 4c..4c+3 per item (a, c)
-            constexpr int NR = FORM == TC_LAPL ? TC_N : TC_NROW;  // rows (and columns) of K_e
+            constexpr int NR = ELASTF ? TC_NROW : TC_N;  // rows (and columns) of K_e
             const float *dst0 = K + e * (long long)(NR * NR);
             const int shift = (int)(((unsigned long long)dst0 % 16) / 4);
             float *kst = ks + shift;
-            if constexpr (FORM == TC_ELAST) {
+            // the Laplacian c sum_j A_jj (TC_LAPL into kst; TC_PAIR into its own staging)
+            float *lst = kst;
+            if constexpr (FORM == TC_PAIR)
+                lst = reinterpret_cast<float *>(smem + P::LS) +
+                      (int)(((unsigned long long)(K2 + e * (long long)(TC_N * TC_N)) % 16) / 4);
+            if constexpr (ELASTF) {
                 if (lane < TC_N) {
                     const float lam = sLM[2 * b], mu = sLM[2 * b + 1];
                     epilogue_rows<P::EX_STRIDE>(warp, d, ex, lane, lam, mu, kst);
                 }
-            } else {
-                const float cw = sLM[2 * b];
+            }
+            if constexpr (FORM != TC_ELAST) {
+                const float cw = FORM == TC_PAIR ? reinterpret_cast<const float *>(smem + P::LC)[b] : sLM[2 * b];
                 for (int it = ctid; it < TC_N * 7; it += TC_CONS) {
                     const int a = it / 7, c = it % 7;
                     const float4 x0 = reinterpret_cast<const float4 *>(ex + (0 * 2 * TC_N + a) * P::EX_STRIDE)[c];
@@ -600,7 +617,7 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
                                         cw * (x0.z + x1.z + x2.z), cw * (x0.w + x1.w + x2.w)};
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
-                        if (4 * c + i < TC_N) kst[a * TC_N + 4 * c + i] = v[i];
+                        if (4 * c + i < TC_N) lst[a * TC_N + 4 * c + i] = v[i];
                 }
             }
             fence_async_smem();
@@ -615,6 +632,15 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
                 for (int t = 0; t < head; ++t) dst[t] = kst[t];
                 for (int t = head + body; t < LEN; ++t) dst[t] = kst[t];
                 bulk_store(dst + head, kst + head, (unsigned)(body * 4));
+                if constexpr (FORM == TC_PAIR) {
+                    float *dl = K2 + e * (long long)(TC_N * TC_N);
+                    constexpr int LL = TC_N * TC_N;
+                    const int hl = (int)((4 - ((unsigned long long)dl % 16) / 4) % 4);
+                    const int bdl = (LL - hl) / 4 * 4;
+                    for (int t = 0; t < hl; ++t) dl[t] = lst[t];
+                    for (int t = hl + bdl; t < LL; ++t) dl[t] = lst[t];
+                    bulk_store(dl + hl, lst + hl, (unsigned)(bdl * 4));
+                }
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(empty + b)) : "memory");
             }
@@ -631,10 +657,12 @@ __global__ void __launch_bounds__(TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0), MODE
 
 template <int MODE, bool GEO, int FORM>
 cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int sm_count,
-                      unsigned long long *status, const int *hold, cudaStream_t s)
+                      unsigned long long *status, const int *hold, cudaStream_t s, const double *coef = nullptr,
+                      void *K2 = nullptr)
 {
     using P = TcSmem<MODE, GEO>;
-    static_assert(P::BYTES <= 227 * 1024, "shared memory plan too large");
+    constexpr int SMEM = FORM == TC_PAIR ? P::BYTES_PAIR : P::BYTES;
+    static_assert(SMEM <= 227 * 1024, "shared memory plan too large");
     static_assert(MODE == TC_TF32X3 || 3 * (P::BYTES + 1024) <= 228 * 1024, "three CTAs per SM in the BF16 modes");
     constexpr int NTHREADS = TC_THREADS_WS + (GEO ? 32 * TC_NGEO : 0);
     auto kern = k_matrix_tc<MODE, GEO, FORM>;
@@ -647,7 +675,7 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
     cudaError_t err = fe_cached_grid(
         cache,
         [&](int dev, long long *v) {
-            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P::BYTES);
+            cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
             if (e2 != cudaSuccess) return e2;
             e2 = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             if (e2 != cudaSuccess) return e2;
@@ -657,7 +685,7 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
             cudaFuncAttributes fa{};
             e2 = cudaFuncGetAttributes(&fa, kern);
             if (e2 != cudaSuccess) return e2;
-            int n = smem_sm / (P::BYTES + 1024);
+            int n = smem_sm / (SMEM + 1024);
             // registers: whole warps in each of the four sub-partitions (regs_sm / 4 each)
             const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;
             const int by_regs = 4 * ((regs_sm / 4) / warp_regs) / (NTHREADS / 32);
@@ -682,8 +710,8 @@ cudaError_t launch_tc(const fe_geometry_h *g, fe_material_args mat, void *K, int
         geo.jinv_out = g->d_jinv32;
         geo.wdetj_out = g->d_wdetj32;
     }
-    kern<<<(unsigned)blocks, NTHREADS, P::BYTES, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->mesh.n_elems,
-                                                      mat.data, (float *)K, status, hold, geo);
+    kern<<<(unsigned)blocks, NTHREADS, SMEM, s>>>(g->d_jinv32, g->d_wdetj32, g->d_dphi32, g->mesh.n_elems,
+                                                  mat.data, (float *)K, status, hold, geo, coef, (float *)K2);
     return cudaGetLastError();
 }
 
@@ -743,4 +771,22 @@ cudaError_t fe_launch_matrix_tc(const fe_geometry_h *g, const fe_form_h *f, fe_m
     }
     return elast ? dispatch_tc<false, TC_ELAST>(g, mat, prec, K, sm_count, status, hold, s)
                  : dispatch_tc<false, TC_LAPL>(g, mat, prec, K, sm_count, status, hold, s);
+}
+
+bool fe_matrix_tc_pair_supported(const fe_geometry_h *g)
+{
+    if (g->N == TC_N && g->Q == TC_Q) return g->d_jinv32 && g->d_dphi32;
+    return fe_matrix_tc64_pair_supported(g);
+}
+
+cudaError_t fe_launch_matrix_tc_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef,
+                                     void *K2, int sm_count, unsigned long long *status, cudaStream_t s)
+{
+    if (g->mesh.n_elems == 0) return cudaSuccess;
+    if (!fe_matrix_tc_pair_supported(g)) return cudaErrorNotSupported;
+    if (g->N != TC_N) return fe_launch_matrix_tc64_pair(g, lame, K, coef, K2, sm_count, status, s);
+    fe_material_args mat{};
+    mat.kind = FE_MAT_LAME;
+    mat.data = lame;
+    return launch_tc<TC_TF32X3, false, TC_PAIR>(g, mat, K, sm_count, status, nullptr, s, coef, K2);
 }

@@ -476,16 +476,16 @@ cudaError_t fe_launch_matrix_tc64(const fe_geometry_h *g, const fe_form_h *f, fe
     return cudaErrorNotSupported;
 }
 
-bool fe_matrix_tc_pair_supported(const fe_geometry_h *g)
+bool fe_matrix_tc64_pair_supported(const fe_geometry_h *g)
 {
     return g->N == T6_N && g->Q == T6_Q && g->d_jinv32 && g->d_dphi32;
 }
 
-cudaError_t fe_launch_matrix_tc_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef,
-                                     void *K2, int sm_count, unsigned long long *status, cudaStream_t s)
+cudaError_t fe_launch_matrix_tc64_pair(const fe_geometry_h *g, const double *lame, void *K, const double *coef,
+                                       void *K2, int sm_count, unsigned long long *status, cudaStream_t s)
 {
     if (g->mesh.n_elems == 0) return cudaSuccess;
-    if (!fe_matrix_tc_pair_supported(g)) return cudaErrorNotSupported;
+    if (!fe_matrix_tc64_pair_supported(g)) return cudaErrorNotSupported;
     fe_material_args mat{};
     mat.kind = FE_MAT_LAME;
     mat.data = lame;

@@ -195,7 +195,7 @@ def test_batch_contraction_path_is_reported(ctx, groups):
 def test_batch_shared_gram_pairs(ctx, groups):
     """BATCH_SHARED_GRAM: each Lame elasticity item and the weighted Laplacian item
     of its geometry come from one launch (the Laplacian as c sum_j A_jj of the
-    elasticity's Gram blocks; tensor cores for Q3, CUDA cores for the other
+    elasticity's Gram blocks; tensor cores for Q2 and Q3, CUDA cores for the other
     groups); both match the oracle on every group (several
     elements per CTA, ragged last groups), the mass items keep their own kernels,
     every output is written (the buffers start as NaN), and runs are reproducible,
@@ -215,8 +215,8 @@ def test_batch_shared_gram_pairs(ctx, groups):
     for k, ((g, f), K) in enumerate(zip(keys, outs)):
         path = b.describe(k)["path"]
         assert ("shared" in path) == (f != "mass"), (g.name, f, path)
-        if f != "mass":  # the shared tensor-core kernel exists for 64-node hexahedra
-            assert path.startswith("tensor") == (g.name == "Q3"), (g.name, f, path)
+        if f != "mass":  # shared tensor-core kernels exist for Q2 and Q3 hexahedra
+            assert path.startswith("tensor") == (g.name in ("Q2", "Q3")), (g.name, f, path)
         e = _err(K, g.reference(f), g.tet)
         assert e <= TOL["f32"], (g.name, f, e)
     first = [K.clone() for K in outs]
