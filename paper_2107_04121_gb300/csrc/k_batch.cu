@@ -244,6 +244,10 @@ struct fe_batch_h {
     // Laplacian item on the same geometry computed by one CUDA-core launch, the
     // Laplacian as c sum_j A_jj of the elasticity's Gram blocks; partner index or -1
     std::vector<int> pair;
+    // per-item schedule with FE_BATCH_GEOMETRY: the lane that recomputes each
+    // geometry (that of its largest item) and the event the other lanes wait on
+    std::vector<int> geo_lane;
+    std::vector<cudaEvent_t> geo_done;
 };
 
 namespace {
@@ -295,15 +299,40 @@ cudaError_t launch_item(fe_batch_h *b, int i, cudaStream_t s)
                                               b->sm_count, s);
 }
 
-// Matrices, per-item schedule: each item's fe_eval_matrix kernel on its lane.
-cudaError_t enqueue_items(fe_batch_h *b, cudaStream_t s)
+// Index of item i's geometry in b->geoms.
+int geo_index(const fe_batch_h *b, int i)
+{
+    for (size_t k = 0; k < b->geoms.size(); ++k)
+        if (b->geoms[k] == b->igeom[i]) return (int)k;
+    return -1;
+}
+
+// Matrices, per-item schedule: each item's fe_eval_matrix kernel on its lane.  With
+// `geometry`, each geometry is recomputed first on its own lane, and an item on
+// another lane waits for it, so that one group's geometry overlaps the matrices of
+// the groups already done.
+cudaError_t enqueue_items(fe_batch_h *b, cudaStream_t s, bool geometry = false)
 {
     cudaError_t e = cudaEventRecord(b->fork, s);
     for (int c = 0; c < kClasses - 1 && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(b->side[c], b->fork, 0);
+    auto lane_stream = [&](int l) { return l == 0 ? s : b->side[l - 1]; };
+    if (geometry)
+        for (size_t k = 0; k < b->geoms.size() && e == cudaSuccess; ++k) {
+            fe_geometry_h *g = b->geoms[k];
+            g->pending = 0;
+            e = fe_launch_geometry(g, b->d_status, lane_stream(b->geo_lane[k]));
+            if (e == cudaSuccess) e = cudaEventRecord(b->geo_done[k], lane_stream(b->geo_lane[k]));
+        }
     for (int i = 0; i < b->n_items && e == cudaSuccess; ++i) {
         if (b->items[i].E == 0) continue;
         const int l = b->lane[i];
-        cudaStream_t ls = l == 0 ? s : b->side[l - 1];
+        cudaStream_t ls = lane_stream(l);
+        if (geometry) {
+            // the geometry of the item (and, for a shared-Gram pair, of its partner: the same)
+            const int k = geo_index(b, i);
+            if (k >= 0 && b->geo_lane[k] != l) e = cudaStreamWaitEvent(ls, b->geo_done[k], 0);
+            if (e != cudaSuccess) break;
+        }
         e = launch_item(b, i, ls);
     }
     for (int c = 0; c < kClasses - 1 && e == cudaSuccess; ++c) {
@@ -320,6 +349,7 @@ cudaError_t enqueue_matrices(fe_batch_h *b, cudaStream_t s)
 
 cudaError_t enqueue(fe_batch_h *b, cudaStream_t s)
 {
+    if ((b->flags & FE_BATCH_GEOMETRY) && b->launches) return enqueue_items(b, s, true);
     if (b->flags & FE_BATCH_GEOMETRY)
         for (fe_geometry_h *g : b->geoms) {
             g->pending = 0;
@@ -453,6 +483,8 @@ void free_plan(fe_batch_h *b)
         if (b->join[c]) cudaEventDestroy(b->join[c]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
+    for (cudaEvent_t ev : b->geo_done)
+        if (ev) cudaEventDestroy(ev);
     if (b->d_items) cudaFree(b->d_items);
     delete b;
 }
@@ -671,6 +703,17 @@ fe_status fe_batch_create(fe_ctx *ctx, const fe_batch_item *items, int n_items, 
             b->lane[i] = l;
             load[l] += cost[i];
         }
+        // each geometry on the lane of its largest item
+        b->geo_lane.assign(b->geoms.size(), -1);
+        for (int i : order) {
+            const int k = geo_index(b, i);
+            if (k >= 0 && b->geo_lane[k] < 0) b->geo_lane[k] = b->lane[i];
+        }
+        for (int &l : b->geo_lane)
+            if (l < 0) l = 0;
+        b->geo_done.assign(b->geoms.size(), nullptr);
+        for (size_t k = 0; k < b->geoms.size() && e == cudaSuccess; ++k)
+            e = cudaEventCreateWithFlags(&b->geo_done[k], cudaEventDisableTiming);
     }
     // schedule: fixed by a flag, else timed when autotuning (matrix launches only)
     if (e == cudaSuccess && !force_persistent && !force_launches && (flags & FE_BATCH_AUTOTUNE)) {
