@@ -231,6 +231,30 @@ def test_batch_shared_gram_pairs(ctx, groups):
     bg.free()
 
 
+def test_batch_shared_gram_unweighted_laplacian(ctx, groups):
+    """A shared-Gram pair whose Laplacian has no coefficient (c = 1 on every element)
+    on every group, against the oracle."""
+    items, keys = [], []
+    for g in groups:
+        items.append((g.geom, _form("elasticity"), g.material("elasticity"), None))
+        items.append((g.geom, fe.laplace_form(weighted=False), None, None))
+        keys += [(g, "elasticity"), (g, "laplace")]
+    b = fe.Batch(ctx, items, fe.BATCH_LAUNCHES | fe.BATCH_SHARED_GRAM)
+    outs = b.run()
+    ctx.check()
+    for k, ((g, f), K) in enumerate(zip(keys, outs)):
+        assert "shared" in b.describe(k)["path"], (g.name, f)
+        if f == "elasticity":
+            ref = g.reference(f)
+        else:
+            wdetJ, G, _ = oracle.geometry(g.mesh.coords, g.mesh.conn, g.ref)
+            one = np.ones(g.mesh.n_elems)
+            ref = (oracle.matrix_laplace(wdetJ, G, one), oracle.matrix_laplace(np.abs(wdetJ), np.abs(G), one))
+        e = _err(K, ref, g.tet)
+        assert e <= TOL["f32"], (g.name, f, e)
+    b.free()
+
+
 def test_batch_autotune_choice_is_a_candidate(ctx, groups):
     items, keys = _items(groups)
     b = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE)
