@@ -46,7 +46,12 @@ struct CvPlan {
     static constexpr int R1N = MAT && NF * T1N > R1N_I ? NF * T1N : R1N_I;
     static constexpr int R2 = R1 + R1N;                         // point values [6][4][Q] | T2
     static constexpr int R2N_P = 6 * 4 * Q;
-    static constexpr int R2N = MAT && NF * T2N > R2N_P ? NF * T2N : R2N_P;
+    // T2 keeps 11 fields (the nine H_ab, c_x, and c_y + c_z, which the last contraction
+    // only uses summed) at a field stride of 3 mod 32 words, so that the lanes of one
+    // warp reading three fields (the column blocks b) fall on disjoint banks
+    static constexpr int NF2 = 11;
+    static constexpr int FS = T2N + ((3 - T2N % 32) % 32 + 32) % 32;
+    static constexpr int R2N = MAT && NF2 * FS > R2N_P ? NF2 * FS : R2N_P;
     static constexpr int PER_EL = R2 + R2N;
 };
 
@@ -344,29 +349,40 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
                     }
             }
             __syncthreads();
-            // ---- step 2: T2[f][qx][ky][ly][kz][lz] = sum_qy B[qy][ky] R[qy][ly] T1[f][qx][qy][kz][lz]
-            for (int t = threadIdx.x; t < ne * nfl * NQ * N1 * N1; t += THREADS) {
-                const int kzlz = t % (N1 * N1), qx = (t / (N1 * N1)) % NQ, f = f0 + (t / (N1 * N1 * NQ)) % nfl,
-                          el = t / (N1 * N1 * NQ * nfl);
-                const T *T1 = sm + el * PE + P::R1 + (f * NQ + qx) * NQ * N1 * N1 + kzlz;
-                T *T2 = sm + el * PE + P::R2 + (f * NQ + qx) * N1 * N1 * N1 * N1 + kzlz;
-                const bool dy = f == 10;
-                T bt[NQ][N1];
+            // ---- step 2: T2[f][qx][ky][ly][kz][lz] = sum_qy B[qy][ky] R[qy][ly] T1[f][qx][qy][kz][lz];
+            // output field 10 holds the sum of the fields 10 and 11 (each contracted, then added)
+            const int fo1 = f1 == 12 ? 11 : f1, nfo = fo1 - f0;
+            for (int t = threadIdx.x; t < ne * nfo * NQ * N1 * N1; t += THREADS) {
+                const int kzlz = t % (N1 * N1), qx = (t / (N1 * N1)) % NQ, fo = f0 + (t / (N1 * N1 * NQ)) % nfo,
+                          el = t / (N1 * N1 * NQ * nfo);
+                T *T2 = sm + el * PE + P::R2 + fo * P::FS + qx * N1 * N1 * N1 * N1 + kzlz;
+                T res[N1][N1];
+                auto contract = [&](int f, bool first) {
+                    const T *T1 = sm + el * PE + P::R1 + (f * NQ + qx) * NQ * N1 * N1 + kzlz;
+                    const bool dy = f == 10;
+                    T bt[NQ][N1];
 #pragma unroll
-                for (int qy = 0; qy < NQ; ++qy) {
-                    const T tq = T1[qy * N1 * N1];
+                    for (int qy = 0; qy < NQ; ++qy) {
+                        const T tq = T1[qy * N1 * N1];
 #pragma unroll
-                    for (int ky = 0; ky < N1; ++ky) bt[qy][ky] = B[qy][ky] * tq;
-                }
+                        for (int ky = 0; ky < N1; ++ky) bt[qy][ky] = B[qy][ky] * tq;
+                    }
+#pragma unroll
+                    for (int ky = 0; ky < N1; ++ky)
+#pragma unroll
+                        for (int ly = 0; ly < N1; ++ly) {
+                            T v = 0;
+#pragma unroll
+                            for (int qy = 0; qy < NQ; ++qy) v = fma(bt[qy][ky], dy ? D[qy][ly] : B[qy][ly], v);
+                            res[ky][ly] = first ? v : res[ky][ly] + v;
+                        }
+                };
+                contract(fo, true);
+                if (fo == 10) contract(11, false);
 #pragma unroll
                 for (int ky = 0; ky < N1; ++ky)
 #pragma unroll
-                    for (int ly = 0; ly < N1; ++ly) {
-                        T v = 0;
-#pragma unroll
-                        for (int qy = 0; qy < NQ; ++qy) v = fma(bt[qy][ky], dy ? D[qy][ly] : B[qy][ly], v);
-                        T2[(ky * N1 + ly) * N1 * N1] = v;
-                    }
+                    for (int ly = 0; ly < N1; ++ly) T2[(ky * N1 + ly) * N1 * N1] = res[ky][ly];
             }
             __syncthreads();
             // ---- step 3: one thread per column (b, l); rows (a, k) in order
@@ -387,7 +403,7 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
                         }
                 }
                 const T *T2 = sm + el * PE + P::R2 + ly * N1 * N1 + lz;
-                constexpr int FS = NQ * N1 * N1 * N1 * N1;  // field stride
+                constexpr int FS = P::FS;                   // field stride
                 constexpr int QS = N1 * N1 * N1 * N1;       // qx stride
                 T *Ke = K + (e0 + el) * (long long)(9 * N * N) + col;
 #pragma unroll
@@ -404,8 +420,7 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
                                 const int o = qx * QS + ky * N1 * N1 * N1 + kz * N1;
                                 T v = 0;
                                 if (wrt_adv) v = Bl[qx] * T2[f * FS + o];
-                                if (diag)
-                                    v += Bl[qx] * (T2[10 * FS + o] + T2[11 * FS + o]) + Dl[qx] * T2[9 * FS + o];
+                                if (diag) v += Bl[qx] * T2[10 * FS + o] + Dl[qx] * T2[9 * FS + o];  // c_y + c_z, c_x
                                 mv[qx] = v;
                             }
 #pragma unroll
