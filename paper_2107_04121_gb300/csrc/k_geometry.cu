@@ -330,8 +330,11 @@ __global__ void __launch_bounds__(kGeomThreads) k_geometry_simplex(
                     J[c][m] = __dsub_rn(xv[m][c], x0[c]);
                     size = fmax(size, fabs(J[c][m]));
                 }
+            // every node checked (no early exit), so that the node loads of all edges and
+            // faces are in flight together
             straight = true;
-            for (int a = 1; a < N && straight; ++a) {
+#pragma unroll
+            for (int a = 1; a < N; ++a) {
                 if (a == v1 || a == v2 || a == v3) continue;
                 double x[3];
                 node_xyz(a, x);
