@@ -255,6 +255,33 @@ def test_batch_shared_gram_unweighted_laplacian(ctx, groups):
     b.free()
 
 
+def test_batch_shared_gram_tensor_cores_several_elements_per_cta(ctx):
+    """The tensor-core shared-Gram launches (Q2: k_matrix_tc pair form, two CTAs per
+    SM; Q3: k_matrix_tc64 pair mode, one CTA per SM) on meshes larger than their
+    persistent grids, so that each CTA computes several elements and reuses its
+    Laplacian staging: every element of both outputs against the oracle."""
+    for p, dims, seed in ((2, (14, 14, 12), 71), (3, (8, 8, 6), 72)):
+        mesh = meshgen.structured_hex(*dims, p, 0.1, seed)
+        g = Group.__new__(Group)
+        g.name, g.mesh, g.tet = "Q%d" % p, mesh, False
+        g.ref = oracle.RefElement(p, p + 1)
+        g.coords = _t(mesh.coords, torch.float64)
+        g.m = fe.Mesh(g.coords, _t(mesh.conn, torch.int32))
+        g.geom = fe.hex_geometry(ctx, g.m, p, p + 1, flags=fe.GEOM_STORE_F32)
+        rng = np.random.default_rng(seed)
+        E = mesh.n_elems
+        g.coef, g.lam, g.mu = rng.uniform(0.5, 2.0, E), rng.uniform(0.5, 2.0, E), rng.uniform(0.2, 1.0, E)
+        items = [(g.geom, _form(f), g.material(f), None) for f in ("elasticity", "laplace")]
+        b = fe.Batch(ctx, items, fe.BATCH_LAUNCHES | fe.BATCH_SHARED_GRAM)
+        outs = b.run()
+        ctx.check()
+        for k, f in enumerate(("elasticity", "laplace")):
+            assert b.describe(k)["path"].startswith("tensor") and "shared" in b.describe(k)["path"]
+            e = _err(outs[k], g.reference(f), False)
+            assert e <= TOL["tf32x3"], (p, f, e)
+        b.free()
+
+
 def test_batch_autotune_choice_is_a_candidate(ctx, groups):
     items, keys = _items(groups)
     b = fe.Batch(ctx, items, fe.BATCH_AUTOTUNE)
