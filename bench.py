@@ -54,6 +54,9 @@ CONVECT_N = 64
 # (27 points x 10 values), the 27 x 3 gathered velocities, the connectivity,
 # and the K_e write (81 x 81)
 CV_BYTES_PER_ELEM_F32 = Q2_Q * 10 * 4 + 81 * 4 + 27 * 4 + 81 * 81 * 4
+# the FP32 matrix kernel computing the deferred geometry: the 27 nodes' FP64
+# coordinates instead of J^-1 and w det J, which it writes as the handle's float32 copy
+CV_GEO_BYTES_PER_ELEM_F32 = 27 * 3 * 8 + 81 * 4 + 27 * 4 + 81 * 81 * 4 + Q2_Q * 10 * 4
 CV_BYTES_PER_ELEM_F64 = Q2_Q * 10 * 8 + 81 * 8 + 27 * 4 + 81 * 81 * 8
 # floating-point operations per element of the sum-factorised convective matrix
 # kernel (3x3x3 points, both terms; FMA = 2): interpolation x, y, z stages
@@ -551,14 +554,19 @@ class ConvectWorkload:
 
     @staticmethod
     def matrix_first(prec):
-        return False
+        """FP32: the matrix kernel computes the stale deferred FP64 geometry (its FP64
+        stages beside the other CTAs' float32 contractions) and the residual reads the
+        float32 copy."""
+        return prec == "f32"
 
     def parts(self, prec):
+        if self.matrix_first(prec):
+            return ("geometry_and_matrix", "residual", "assembly")
         return ("geometry_and_residual", "matrix", "assembly")
 
     def step(self, prec, ev=None):
-        """FP32: the deferred geometry is computed (FP64) by the residual kernel,
-        then K_e(u) and the assembly; FP64: geometry kernel, residual, K_e(u), assembly."""
+        """FP32: the deferred geometry is computed (FP64) by the matrix kernel, then
+        r_e(u) and the assembly; FP64: geometry kernel, residual, K_e(u), assembly."""
         fe = self.fe
         K, r, g = self.outputs(prec)
         u = self.u64 if prec == "f64" else self.u32
@@ -566,9 +574,14 @@ class ConvectWorkload:
         geom = self.geoms[prec]
         rec(0)
         geom.update()
-        fe.eval_residual(self.ctx, self.form, geom, [None, u, u], prec, out=r)
-        rec(1)
-        fe.eval_matrix(self.ctx, self.form, geom, [None, u, u], prec, out=K)
+        if self.matrix_first(prec):
+            fe.eval_matrix(self.ctx, self.form, geom, [None, u, u], prec, out=K)
+            rec(1)
+            fe.eval_residual(self.ctx, self.form, geom, [None, u, u], prec, out=r)
+        else:
+            fe.eval_residual(self.ctx, self.form, geom, [None, u, u], prec, out=r)
+            rec(1)
+            fe.eval_matrix(self.ctx, self.form, geom, [None, u, u], prec, out=K)
         rec(2)
         fe.assemble_vector(self.ctx, self.asm, 3, r, prec, out=g,
                            flags=0 if prec == "f64" else fe.ASSEMBLE_COMPENSATED)
@@ -581,8 +594,8 @@ def convect_measure(n, device, ws, flush, ref, hbm_peak, steps=5, warmup=3):
     oracle (reference computed in the CPU-baseline leg)."""
     cw = ConvectWorkload(n, device)
     out = {"workload": "Navier-Stokes convection 'i,i.j,j', Q2 hexahedra, %d^3 = %d elements, +-0.1h seed 3, "
-                       "u = a sin(pi x) cos(pi y); step = FP64 geometry (FP32: computed by the residual "
-                       "kernel) + r_e(u) + K_e(u) (Eq. fe4) + assembly" % (n, cw.E), "elements": cw.E}
+                       "u = a sin(pi x) cos(pi y); step = FP64 geometry (FP32: computed by the matrix "
+                       "kernel) + K_e(u) (Eq. fe4) + r_e(u) + assembly" % (n, cw.E), "elements": cw.E}
     for prec in ("f32", "f64"):
         st, mt, parts = timed_steps(cw, prec, steps, warmup, ws, flush)
         t = max_over_ranks(sum(st), ws)
@@ -590,10 +603,23 @@ def convect_measure(n, device, ws, flush, ref, hbm_peak, steps=5, warmup=3):
         d = {"value": ws * cw.E * steps / (t / 1e3), "unit": UNIT, "ms_per_step": t / steps, "matrix_ms": mat,
              "parts_ms": parts}
         if prec == "f32":
-            ach = cw.E * CV_BYTES_PER_ELEM_F32 / (mat / 1e3) / 1e9
-            d["roofline"] = {"kernel": "k_convect_sf (matrix, f32)", "bound": "hbm", "achieved": ach,
-                             "peak": hbm_peak, "unit": "GB/s", "frac": ach / hbm_peak,
-                             "bytes_per_elem": CV_BYTES_PER_ELEM_F32}
+            b_el = CV_GEO_BYTES_PER_ELEM_F32 if cw.matrix_first(prec) else CV_BYTES_PER_ELEM_F32
+            ach = cw.E * b_el / (mat / 1e3) / 1e9
+            d["roofline"] = {"kernel": "k_convect_sf (matrix, f32%s)" % (", computing the deferred FP64 geometry"
+                                                                        if cw.matrix_first(prec) else ""),
+                             "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                             "frac": ach / hbm_peak, "bytes_per_elem": b_el}
+            if cw.matrix_first(prec):
+                # the same matrix kernel on the stored float32 geometry (the handle is
+                # current after the steps), timed alone
+                K, _, _ = cw.outputs(prec)
+                geom = cw.geoms[prec]
+                t_m = time_call(cw, flush, lambda: cw.fe.eval_matrix(cw.ctx, cw.form, geom, [None, cw.u32, cw.u32],
+                                                                     prec, out=K))
+                a2 = cw.E * CV_BYTES_PER_ELEM_F32 / (t_m / 1e3) / 1e9
+                d["matrix_stored_geometry"] = {"ms": t_m, "roofline": {
+                    "kernel": "k_convect_sf (matrix, f32, stored geometry)", "bound": "hbm", "achieved": a2,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": a2 / hbm_peak, "bytes_per_elem": CV_BYTES_PER_ELEM_F32}}
         else:
             ach = cw.E * CV_FLOPS_PER_ELEM / (mat / 1e3) / 1e12
             d["roofline"] = {"kernel": "k_convect_sf (matrix, f64)", "bound": "fp64", "achieved": ach,

@@ -224,7 +224,9 @@ int fe_gm_rule_size(int s);
                                 by fe_eval_matrix itself in the tensor-core precisions (Lame
                                 elasticity): warps of the tensor-core kernel compute the FP64
                                 geometry beside the K_e stream and store the float32 copy, same
-                                bits again.  A call that reports an error (e.g. FE_ERR_TIMEOUT)
+                                bits again; and by fe_eval_matrix of the convective form in
+                                FE_F32 (the matrix kernel runs the geometry stages first, same
+                                bits).  A call that reports an error (e.g. FE_ERR_TIMEOUT)
                                 leaves the geometry it was computing undefined until the next
                                 fe_geometry_update.  The stale mark is host state: use a
                                 deferred handle from one stream. */

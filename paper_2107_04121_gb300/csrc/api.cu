@@ -424,6 +424,13 @@ fe_status fe_eval_matrix(fe_ctx *ctx, const fe_form_h *form, const fe_geometry_h
         if (!fe_convect_supported(g)) return FE_ERR_UNSUPPORTED_SPEC;
         const bool empty = g->mesh.n_elems == 0;
         if (!args || (!empty && (!args[form->grad_op] || !args[form->adv_op]))) return FE_ERR_INVALID_ARG;
+        if (gm->pending && prec != FE_F64 && fe_convect_geometry_fusable(gm)) {
+            // stale float32-only deferred handle: the matrix kernel computes it
+            e = fe_launch_convect_matrix_geometry(gm, args[form->grad_op], args[form->adv_op], form->wrt_grad,
+                                                  form->wrt_adv, K_out, ctx->d_status, s);
+            if (e == cudaSuccess) gm->pending = 0;
+            return from_cuda(e, "fe_eval_matrix");
+        }
         e = settle_geometry(gm, ctx->d_status, s);
         if (e == cudaSuccess)
             e = fe_launch_convect(g, prec == FE_F64, args[form->grad_op], args[form->adv_op], form->wrt_grad,

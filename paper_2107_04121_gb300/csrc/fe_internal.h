@@ -169,6 +169,10 @@ bool fe_convect_supported(const fe_geometry_h *g);
 bool fe_convect_geometry_fusable(const fe_geometry_h *g);
 cudaError_t fe_launch_convect_residual_geometry(const fe_geometry_h *g, const void *u, const void *w, void *r,
                                                 unsigned long long *status, cudaStream_t s);
+// The same for the convective matrix (Eq. fe4): the FP32 matrix kernel of a stale
+// float32-only deferred geometry computes it first and stores the float32 copy.
+cudaError_t fe_launch_convect_matrix_geometry(const fe_geometry_h *g, const void *u, const void *w, int wrt_grad,
+                                              int wrt_adv, void *K, unsigned long long *status, cudaStream_t s);
 // Generic kernels (runtime N, Q) of the remaining forms and of eval mode:
 // mode 0 residual (out (E, ncomp_test N)), 1 matrix (out (E, rows, cols)),
 // 2 eval (out (E, n_out)).  f0, f1, f2: the DOF vectors of the form's field

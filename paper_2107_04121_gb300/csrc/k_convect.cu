@@ -52,7 +52,7 @@ struct CvPlan {
     static constexpr int NF2 = 11;
     static constexpr int FS = T2N + ((3 - T2N % 32) % 32 + 32) % 32;
     static constexpr int R2N = MAT && NF2 * FS > R2N_P ? NF2 * FS : R2N_P;
-    static constexpr int PER_EL = R2 + R2N;
+    static constexpr int PER_EL = (R2 + R2N + 1) / 2 * 2;  // even: the FP64 geometry area of each element
 };
 
 // Geometry computed in the residual kernel (a stale float32-only deferred
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(THREADS) k_convect_sf(const T *__restrict__ ji
     // GEO: 0 = geometry read from the handle, 1 = computed here, 2 = computed here
     // with the middle point on the middle node (three points per axis)
     using P = CvPlan<T, N1, NQ, MAT>;
-    static_assert(!GEO || (!MAT && N1 == NQ && sizeof(T) == 4), "in-kernel geometry: float32 residual, n1 == nq");
+    static_assert(!GEO || (N1 == NQ && sizeof(T) == 4), "in-kernel geometry: float32 kernels, n1 == nq");
     static_assert(!GEO || 12 * N1 * N1 * N1 * 2 <= P::R1N + P::R2N, "FP64 geometry fits the stage buffers");
     constexpr int N = P::N, Q = P::Q, LX = P::LX, LY = P::LY, PE = P::PER_EL;
     extern __shared__ __align__(16) unsigned char cv_smem[];
@@ -539,6 +539,21 @@ cudaError_t fe_launch_convect_residual_geometry(const fe_geometry_h *g, const vo
         return g->geo_center ? launch_cv<float, 3, 3, false, 7, 2>(g, u, w, 0, 0, nullptr, r, status, s)
                              : launch_cv<float, 3, 3, false, 7, 1>(g, u, w, 0, 0, nullptr, r, status, s);
     case 4: return launch_cv<float, 4, 4, false, 2, 1>(g, u, w, 0, 0, nullptr, r, status, s);
+    }
+    return cudaErrorNotSupported;
+}
+
+cudaError_t fe_launch_convect_matrix_geometry(const fe_geometry_h *g, const void *u, const void *w, int wrt_grad,
+                                              int wrt_adv, void *K, unsigned long long *status, cudaStream_t s)
+{
+    if (!fe_convect_geometry_fusable(g)) return cudaErrorNotSupported;
+    if (g->mesh.n_elems == 0) return cudaSuccess;
+    switch (g->n1d) {
+    case 2: return launch_cv<float, 2, 2, true, 8, 1>(g, u, w, wrt_grad, wrt_adv, K, nullptr, status, s);
+    case 3:
+        return g->geo_center ? launch_cv<float, 3, 3, true, 3, 2>(g, u, w, wrt_grad, wrt_adv, K, nullptr, status, s)
+                             : launch_cv<float, 3, 3, true, 3, 1>(g, u, w, wrt_grad, wrt_adv, K, nullptr, status, s);
+    case 4: return launch_cv<float, 4, 4, true, 1, 1>(g, u, w, wrt_grad, wrt_adv, K, nullptr, status, s);
     }
     return cudaErrorNotSupported;
 }

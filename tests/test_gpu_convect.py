@@ -89,6 +89,40 @@ def test_convect_residual_computes_stale_geometry(ctx, p, n, roles):
         assert rel_vector_error(r_l.cpu().numpy(), rref) <= TOL["f32"]
 
 
+@pytest.mark.parametrize("roles", ["nonlinear", "wrt_u", "wrt_w"])
+@pytest.mark.parametrize("p,n", [(1, (5, 4, 3)), (2, (5, 3, 3)), (3, (2, 2, 3)), (2, (20, 19, 18))])
+def test_convect_matrix_computes_stale_geometry(ctx, p, n, roles):
+    """fe_eval_matrix of the convective form on a stale float32-only deferred handle
+    computes the FP64 geometry in the matrix kernel: K, the stored copy and the
+    residual that follows equal the eager path's bit for bit (the largest case puts
+    several element groups on every CTA), and K matches the oracle on small meshes."""
+    mesh = meshgen.structured_hex(*n, p, 0.15, 80 + p)
+    P = Problem(ctx, mesh, p, p + 1)
+    rng = np.random.default_rng(81 + p)
+    u = _t(rng.standard_normal(3 * mesh.n_nodes), torch.float32)
+    w = u if roles == "nonlinear" else _t(rng.standard_normal(3 * mesh.n_nodes), torch.float32)
+    gr, ad = ROLES[roles]
+    form = fe.convect_form(advection=ad, gradient=gr)
+    eager = fe.hex_geometry(ctx, P.m, p, p + 1, flags=fe.GEOM_STORE_F32)
+    lazy = fe.hex_geometry(ctx, P.m, p, p + 1, flags=fe.GEOM_STORE_F32 | fe.GEOM_DEFERRED)
+    K_e = fe.eval_matrix(ctx, form, eager, [None, u, w], "f32")
+    for _ in range(2):
+        lazy.update()
+        K_l = fe.eval_matrix(ctx, form, lazy, [None, u, w], "f32")
+    ctx.check()
+    assert torch.equal(K_l, K_e)
+    assert torch.equal(lazy.get(fe.GEOM_JINV, "f32"), eager.get(fe.GEOM_JINV, "f32"))
+    assert torch.equal(lazy.get(fe.GEOM_WDETJ, "f32"), eager.get(fe.GEOM_WDETJ, "f32"))
+    assert torch.equal(fe.eval_residual(ctx, form, lazy, [None, u, w], "f32"),
+                       fe.eval_residual(ctx, form, eager, [None, u, w], "f32"))
+    if mesh.n_elems <= 100:
+        wdetJ, G, _ = P.oracle_geometry()
+        uh, wh = u.double().cpu().numpy(), w.double().cpu().numpy()
+        Kref = oracle.matrix_convect(mesh.conn, wdetJ, P.ref.phi, G, uh, wh, wrt_u=gr == fe.STATE,
+                                     wrt_w=ad == fe.STATE)
+        assert rel_matrix_error(K_l.cpu().numpy(), Kref) <= TOL["f32"]
+
+
 def test_convect_smooth_field_config_small(ctx):
     """The smooth field sin(pi x) cos(pi y) a of the convection workload on a
     small cube; the assembled residual (compensated FP32) against the oracle's."""
