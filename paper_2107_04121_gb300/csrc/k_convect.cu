@@ -25,7 +25,10 @@
 //       contraction runs with one thread per column (b, l) of the element
 //       matrix, so each row of K is written by consecutive threads (coalesced).
 // About 48 k FMA per Q2 element instead of the ~110 k of the point-by-point
-// sums; FP64 is compute-bound, FP32 is bound by the K write.
+// sums; FP64 is compute-bound, FP32 is bound by shared memory and the barriers
+// between the stages (the K write alone would take about 60% of its time).  A stale
+// float32-only deferred handle is computed by the FP32 residual or matrix kernel
+// that reads it first: the geometry stages run at the start of each element group.
 #include "geometry_body.cuh"
 
 namespace {
@@ -55,7 +58,7 @@ struct CvPlan {
     static constexpr int PER_EL = (R2 + R2N + 1) / 2 * 2;  // even: the FP64 geometry area of each element
 };
 
-// Geometry computed in the residual kernel (a stale float32-only deferred
+// Geometry computed in the FP32 residual or matrix kernel (a stale float32-only deferred
 // handle, n1 == nq): the mesh, the FP64 1-D tables and where the float32 copy goes.
 struct CvGeoArgs {
     const double *coords;
