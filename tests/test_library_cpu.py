@@ -169,3 +169,20 @@ def test_null_arguments_are_rejected(libfe):
     assert libfe.fe_batch_free(None) == fe.FE_ERR_INVALID_ARG
     assert libfe.fe_round_f32(None, None, None, 0, None) == fe.FE_ERR_INVALID_ARG
     assert libfe.fe_debug_hold_next_matrix(None) == fe.FE_ERR_INVALID_ARG
+
+
+def test_header_flag_values_match_the_binding():
+    """Every flag the header defines (#define FE_<NAME> <value>u) that the Python
+    binding also names (<NAME>) has the same value there, so that the binding passes
+    what the library reads."""
+    import re
+
+    from paper_2107_04121_gb300 import fe
+    text = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+FE_(\w+)\s+(\d+)u?\b", text))
+    shared = {k: int(v) for k, v in defs.items() if hasattr(fe, k)}
+    for name in ("BATCH_GEOMETRY", "BATCH_AUTOTUNE", "BATCH_GRAPH", "BATCH_PERSISTENT", "BATCH_LAUNCHES",
+                 "BATCH_SHARED_GRAM", "GEOM_STORE_F64", "GEOM_STORE_F32", "GEOM_DEFERRED"):
+        assert name in shared, name
+    for name, value in shared.items():
+        assert getattr(fe, name) == value, (name, getattr(fe, name), value)
